@@ -1,0 +1,307 @@
+"""FP64 CPU oracle for "Fitting Galaxies on GPUs" (Barsdell, Barnes & Fluke).
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously correct
+statement of the galaxy-fitting loop (Sec. 2, steps 1-5; Sec. 3 items 1-3) in
+double precision.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.  It
+shares no code with the CUDA library: the C source lives in ``gfo.c`` and is
+built by :func:`build` with gcc into ``liboracle.so`` beside it.
+
+Every function takes and returns numpy float64 arrays; the parameter layout
+per component is
+    Sersic  : x0, y0, I_e, r_e, n, q, pa_deg, c
+    ExpDisk : x0, y0, I_0, r_s, q, pa_deg, c
+    Sky     : s0
+
+Parity status: every function here is pinned by the tests in
+``tests/test_oracle_*.py`` against closed forms, library special functions,
+brute force or invariants -- except the generalised-radius boxiness term
+(c != 0), whose flux factor has no closed form in the paper: parity unpinned
+beyond self-consistency (two-resolution grid integration).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "liboracle.so")
+SRC = os.path.join(HERE, "gfo.c")
+
+SERSIC, EXPDISK, SKY = 1, 2, 3
+NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1}
+CONVERGED, BADINPUT, NOCONV, MAXITER = 0, 1, 3, 8
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile gfo.c into liboracle.so with gcc (portable flags, OpenMP)."""
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
+        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "gfo.h"))
+    ):
+        return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+           "-D_GNU_SOURCE", SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class Desc(C.Structure):
+    _fields_ = [("H", C.c_int), ("W", C.c_int), ("P", C.c_int), ("ncomp", C.c_int),
+                ("kinds", C.c_int * 8), ("os_factor", C.c_int), ("os_box", C.c_int),
+                ("os_x0", C.c_int), ("os_y0", C.c_int)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("lambda0", C.c_double), ("lambda_up", C.c_double),
+                ("lambda_down", C.c_double), ("lambda_min", C.c_double),
+                ("lambda_max", C.c_double), ("ftol", C.c_double), ("xtol", C.c_double),
+                ("fd_rel", C.c_double), ("max_iter", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [("chi2", C.c_double), ("lam", C.c_double), ("iters", C.c_int),
+                ("accepted", C.c_int), ("status", C.c_int)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(LIB)
+            dp = C.POINTER(C.c_double)
+            L.gfo_bn.restype = C.c_double
+            L.gfo_bn.argtypes = [C.c_double]
+            L.gfo_gammainc_lower.restype = C.c_double
+            L.gfo_gammainc_lower.argtypes = [C.c_double, C.c_double]
+            L.gfo_sersic_flux.restype = C.c_double
+            L.gfo_sersic_flux.argtypes = [C.c_double] * 4
+            L.gfo_comp_value.restype = C.c_double
+            L.gfo_comp_value.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double]
+            L.gfo_model_ext.restype = C.c_int
+            L.gfo_model_ext.argtypes = [C.POINTER(Desc), dp, C.c_int, C.c_int, dp]
+            L.gfo_convolve_direct.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp]
+            L.gfo_convolve_fft.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp]
+            L.gfo_fft.argtypes = [C.c_int, dp, dp, C.c_int]
+            L.gfo_fft_size.restype = C.c_int
+            L.gfo_fft_size.argtypes = [C.c_int]
+            L.gfo_chi2.restype = C.c_double
+            L.gfo_chi2.argtypes = [C.c_int, dp, dp, dp]
+            L.gfo_eval.restype = C.c_double
+            L.gfo_eval.argtypes = [C.POINTER(Desc), dp, dp, dp, dp, C.c_int, dp]
+            L.gfo_jacobian.restype = C.c_double
+            L.gfo_jacobian.argtypes = [C.POINTER(Desc), dp, C.c_char_p, dp, dp, dp, C.c_int,
+                                       C.c_double, C.c_int, dp, dp, dp, dp]
+            L.gfo_default_bounds.argtypes = [C.POINTER(Desc), dp, dp]
+            L.gfo_default_opts.argtypes = [C.POINTER(Opts)]
+            L.gfo_fd_step.restype = C.c_double
+            L.gfo_fd_step.argtypes = [C.POINTER(Desc), C.c_int, C.c_double, C.c_double]
+            L.gfo_slot_is_linear.restype = C.c_int
+            L.gfo_slot_is_linear.argtypes = [C.POINTER(Desc), C.c_int]
+            L.gfo_lm_fit.restype = C.c_int
+            L.gfo_lm_fit.argtypes = [C.POINTER(Desc), dp, C.c_char_p, dp, dp, dp, dp, dp,
+                                     C.c_int, C.POINTER(Opts), C.POINTER(Result)]
+            L.gfo_lm_fit_batch.restype = C.c_int
+            L.gfo_lm_fit_batch.argtypes = [C.c_int, C.POINTER(Desc), dp, C.c_char_p, dp,
+                                           C.POINTER(C.c_int64), dp, dp,
+                                           C.POINTER(C.c_int64), C.c_int, C.POINTER(Opts),
+                                           C.POINTER(Result)]
+            L.gfo_num_threads.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_desc(H, W, P, kinds, os_factor=1, os_box=0, os_x0=-1, os_y0=-1) -> Desc:
+    d = Desc()
+    d.H, d.W, d.P, d.ncomp = int(H), int(W), int(P), len(kinds)
+    for i, k in enumerate(kinds):
+        d.kinds[i] = int(k)
+    d.os_factor, d.os_box, d.os_x0, d.os_y0 = int(os_factor), int(os_box), int(os_x0), int(os_y0)
+    return d
+
+
+def nslots(kinds) -> int:
+    return sum(NSLOTS[k] for k in kinds)
+
+
+def bn(n: float) -> float:
+    return lib().gfo_bn(float(n))
+
+
+def gammainc_lower(a: float, x: float) -> float:
+    return lib().gfo_gammainc_lower(float(a), float(x))
+
+
+def sersic_flux(Ie, re, n, q) -> float:
+    return lib().gfo_sersic_flux(float(Ie), float(re), float(n), float(q))
+
+
+def comp_value(kind, p, x, y) -> float:
+    p = _f64(p)
+    b = bn(p[4]) if kind == SERSIC else 0.0
+    return lib().gfo_comp_value(int(kind), _dp(p), float(x), float(y), b)
+
+
+def model_ext(desc: Desc, params, comp: int = -1, unit_amp: bool = False) -> np.ndarray:
+    c = (desc.P - 1) // 2
+    out = np.empty((desc.H + 2 * c, desc.W + 2 * c), np.float64)
+    p = _f64(params)
+    rc = lib().gfo_model_ext(C.byref(desc), _dp(p), int(comp), int(unit_amp), _dp(out))
+    if rc != 0:
+        raise ValueError("bad component kind")
+    return out
+
+
+def convolve_direct(ext, psf) -> np.ndarray:
+    ext, psf = _f64(ext), _f64(psf)
+    P = psf.shape[0]
+    H, W = ext.shape[0] - (P - 1), ext.shape[1] - (P - 1)
+    out = np.empty((H, W), np.float64)
+    lib().gfo_convolve_direct(H, W, P, _dp(ext), _dp(psf), _dp(out))
+    return out
+
+
+def convolve_fft(ext, psf) -> np.ndarray:
+    ext, psf = _f64(ext), _f64(psf)
+    P = psf.shape[0]
+    H, W = ext.shape[0] - (P - 1), ext.shape[1] - (P - 1)
+    out = np.empty((H, W), np.float64)
+    lib().gfo_convolve_fft(H, W, P, _dp(ext), _dp(psf), _dp(out))
+    return out
+
+
+def fft(x, sign=-1) -> np.ndarray:
+    x = np.asarray(x, np.complex128)
+    re = np.ascontiguousarray(x.real.copy())
+    im = np.ascontiguousarray(x.imag.copy())
+    lib().gfo_fft(len(x), _dp(re), _dp(im), int(sign))
+    return re + 1j * im
+
+
+def fft_size(n: int) -> int:
+    return lib().gfo_fft_size(int(n))
+
+
+def chi2(d, sigma, m) -> float:
+    d, sigma, m = _f64(d), _f64(sigma), _f64(m)
+    return lib().gfo_chi2(d.size, _dp(d), _dp(sigma), _dp(m))
+
+
+def render(desc: Desc, params, psf, method: int = 0) -> np.ndarray:
+    """Steps 1-2: the convolved model on the stamp."""
+    out = np.empty((desc.H, desc.W), np.float64)
+    p, psf = _f64(params), _f64(psf)
+    lib().gfo_eval(C.byref(desc), _dp(p), _dp(psf), None, None, int(method), _dp(out))
+    return out
+
+
+def evaluate(desc: Desc, params, psf, img, sigma, method: int = 0):
+    """Steps 1-3: (chi2, convolved model)."""
+    out = np.empty((desc.H, desc.W), np.float64)
+    p, psf, img, sigma = _f64(params), _f64(psf), _f64(img), _f64(sigma)
+    x2 = lib().gfo_eval(C.byref(desc), _dp(p), _dp(psf), _dp(img), _dp(sigma), int(method),
+                        _dp(out))
+    return x2, out
+
+
+def _fixed_bytes(fixed, ns):
+    if fixed is None:
+        return None
+    f = np.ascontiguousarray(np.asarray(fixed, np.uint8).reshape(-1))
+    assert f.size % ns == 0
+    return f.tobytes()
+
+
+def jacobian(desc: Desc, params, fixed, psf, img, sigma, method=0, fd_rel=1e-3,
+             central=False):
+    """Returns dict(J [nfree,H,W], A, g, chi2, model)."""
+    ns = nslots([desc.kinds[i] for i in range(desc.ncomp)])
+    fb = _fixed_bytes(fixed, ns)
+    nfree = ns if fixed is None else int(ns - np.count_nonzero(np.asarray(fixed)))
+    J = np.empty((nfree, desc.H, desc.W), np.float64)
+    A = np.empty((nfree, nfree), np.float64)
+    g = np.empty(nfree, np.float64)
+    m = np.empty((desc.H, desc.W), np.float64)
+    p, psf, img, sigma = _f64(params), _f64(psf), _f64(img), _f64(sigma)
+    x2 = lib().gfo_jacobian(C.byref(desc), _dp(p), fb, _dp(psf), _dp(img), _dp(sigma),
+                            int(method), float(fd_rel), int(central), _dp(J), _dp(A), _dp(g),
+                            _dp(m))
+    return dict(J=J, A=A, g=g, chi2=x2, model=m)
+
+
+def default_bounds(desc: Desc):
+    ns = nslots([desc.kinds[i] for i in range(desc.ncomp)])
+    lo, hi = np.empty(ns), np.empty(ns)
+    lib().gfo_default_bounds(C.byref(desc), _dp(lo), _dp(hi))
+    return lo, hi
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().gfo_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def fd_step(desc: Desc, slot: int, v: float, fd_rel: float = 1e-3) -> float:
+    return lib().gfo_fd_step(C.byref(desc), int(slot), float(v), float(fd_rel))
+
+
+def slot_is_linear(desc: Desc, slot: int) -> bool:
+    return bool(lib().gfo_slot_is_linear(C.byref(desc), int(slot)))
+
+
+def lm_fit(desc: Desc, params, fixed, psf, img, sigma, method=0, opts: Opts | None = None,
+           lo=None, hi=None):
+    """Returns (params, dict(chi2, lambda, iters, accepted, status))."""
+    ns = nslots([desc.kinds[i] for i in range(desc.ncomp)])
+    p = np.array(params, np.float64, copy=True)
+    psf, img, sigma = _f64(psf), _f64(img), _f64(sigma)
+    lo, hi = _f64(lo), _f64(hi)
+    r = Result()
+    lib().gfo_lm_fit(C.byref(desc), _dp(p), _fixed_bytes(fixed, ns), _dp(lo), _dp(hi),
+                     _dp(psf), _dp(img), _dp(sigma), int(method),
+                     C.byref(opts) if opts is not None else None, C.byref(r))
+    return p, dict(chi2=r.chi2, lam=r.lam, iters=r.iters, accepted=r.accepted,
+                   status=r.status)
+
+
+def lm_fit_batch(descs, params, fixed, psf_flat, psf_off, img_flat, sigma_flat, pix_off,
+                 method=0, opts: Opts | None = None):
+    """Independent fits, OpenMP across stamps.  params: [nb, nslots] (copied)."""
+    nb = len(descs)
+    arr = (Desc * nb)(*descs)
+    p = np.array(params, np.float64, copy=True)
+    ns = p.shape[1]
+    res = (Result * nb)()
+    po = np.ascontiguousarray(psf_off, np.int64)
+    xo = np.ascontiguousarray(pix_off, np.int64)
+    lib().gfo_lm_fit_batch(nb, arr, _dp(p), _fixed_bytes(fixed, ns), _dp(_f64(psf_flat)),
+                           po.ctypes.data_as(C.POINTER(C.c_int64)), _dp(_f64(img_flat)),
+                           _dp(_f64(sigma_flat)), xo.ctypes.data_as(C.POINTER(C.c_int64)),
+                           int(method), C.byref(opts) if opts is not None else None, res)
+    out = [dict(chi2=r.chi2, lam=r.lam, iters=r.iters, accepted=r.accepted, status=r.status)
+           for r in res]
+    return p, out
+
+
+def num_threads() -> int:
+    return lib().gfo_num_threads()

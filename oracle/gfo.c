@@ -1,0 +1,744 @@
+/*
+ * gfo.c -- FP64 CPU oracle for "Fitting Galaxies on GPUs" (Barsdell, Barnes &
+ * Fluke).  TEST INFRASTRUCTURE ONLY: loaded by the tests, by the smoke check
+ * and by the CPU-baseline leg of the benchmark, never by the product path.
+ *
+ * Each function states the definition it follows.  The paper fixes the five
+ * steps of the loop (Sec. 2) and names the algorithms inside steps 1-3
+ * (Sec. 3: transform, FFT + transform, transform + reduce); the profile
+ * formulas, the oversampling rule, the chi^2 weights and the LM variant are
+ * the standard definitions the paper leaves implicit.  Every such reading is
+ * listed in the repository's design doc.
+ */
+#include "gfo.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------ slots */
+
+int gfo_comp_nslots(int kind)
+{
+    switch (kind) {
+    case GFO_SERSIC: return 8;
+    case GFO_EXPDISK: return 7;
+    case GFO_SKY: return 1;
+    default: return -1;
+    }
+}
+
+int gfo_nslots(const gfo_desc* d)
+{
+    int n = 0;
+    for (int k = 0; k < d->ncomp; ++k) n += gfo_comp_nslots(d->kinds[k]);
+    return n;
+}
+
+/* which component owns slot s, and the slot's index inside it */
+static void slot_owner(const gfo_desc* d, int s, int* comp, int* local, int* base)
+{
+    int off = 0;
+    for (int k = 0; k < d->ncomp; ++k) {
+        int ns = gfo_comp_nslots(d->kinds[k]);
+        if (s < off + ns) {
+            *comp = k;
+            *local = s - off;
+            *base = off;
+            return;
+        }
+        off += ns;
+    }
+    *comp = -1;
+    *local = -1;
+    *base = -1;
+}
+
+/* The amplitude slots (I_e, I_0) and the sky level enter the model linearly. */
+int gfo_slot_is_linear(const gfo_desc* d, int s)
+{
+    int k, l, b;
+    slot_owner(d, s, &k, &l, &b);
+    if (k < 0) return 0;
+    if (d->kinds[k] == GFO_SKY) return 1;
+    return l == 2;
+}
+
+/* slot semantics: 0 = position, 1 = amplitude, 2 = radius, 3 = Sersic n,
+ * 4 = axis ratio, 5 = position angle, 6 = boxiness, 7 = sky */
+static int slot_role(const gfo_desc* d, int s)
+{
+    int k, l, b;
+    slot_owner(d, s, &k, &l, &b);
+    if (k < 0) return -1;
+    int kind = d->kinds[k];
+    if (kind == GFO_SKY) return 7;
+    if (l <= 1) return 0;
+    if (l == 2) return 1;
+    if (l == 3) return 2;
+    if (kind == GFO_SERSIC) {
+        static const int r[8] = {0, 0, 1, 2, 3, 4, 5, 6};
+        return r[l];
+    }
+    {
+        static const int r[7] = {0, 0, 1, 2, 4, 5, 6};
+        return r[l];
+    }
+}
+
+/* ------------------------------------------------------------- b_n, flux */
+
+/* P(a, x) = gamma(a, x) / Gamma(a) by the power series
+ * gamma(a, x) = x^a e^{-x} sum_{k>=0} x^k / (a (a+1) ... (a+k)). */
+double gfo_gammainc_lower(double a, double x)
+{
+    if (x <= 0.0) return 0.0;
+    double term = 1.0 / a, sum = term;
+    for (int k = 1; k < 100000; ++k) {
+        term *= x / (a + k);
+        sum += term;
+        if (term < sum * 1e-17) break;
+    }
+    return exp(a * log(x) - x - lgamma(a)) * sum;
+}
+
+/* b_n solves gamma(2n, b_n) = Gamma(2n)/2, i.e. P(2n, b_n) = 1/2, so that the
+ * effective radius r_e encloses half of the total light.  The median of a
+ * Gamma(a) variate lies in (0, a), so plain bisection on that bracket. */
+double gfo_bn(double n)
+{
+    double a = 2.0 * n, lo = 0.0, hi = a;
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (gfo_gammainc_lower(a, mid) < 0.5)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* Total flux of I_e exp(-b_n((r/r_e)^{1/n} - 1)) over the ellipse family
+ * (boxiness 0): 2 pi q I_e r_e^2 n e^{b_n} Gamma(2n) / b_n^{2n}. */
+double gfo_sersic_flux(double Ie, double re, double n, double q)
+{
+    double b = gfo_bn(n);
+    return 2.0 * M_PI * q * Ie * re * re * n * exp(b + lgamma(2.0 * n) - 2.0 * n * log(b));
+}
+
+/* ------------------------------------------------------------------ model */
+
+/* Surface brightness of one component at (x, y).
+ * Rotation: theta = pa_deg * pi / 180, counter-clockwise from +x to the major
+ * axis; x' = dx cos + dy sin, y' = -dx sin + dy cos.
+ * Generalised radius: r = (|x'|^C + |y'/q|^C)^{1/C}, C = c + 2.
+ * Sersic: I_e exp(-b_n ((r/r_e)^{1/n} - 1)); exponential disk: I_0 exp(-r/r_s). */
+double gfo_comp_value(int kind, const double* p, double x, double y, double bn)
+{
+    if (kind == GFO_SKY) return p[0];
+    double x0 = p[0], y0 = p[1], amp = p[2], rs = p[3];
+    double n = 1.0, q, pa, c;
+    if (kind == GFO_SERSIC) {
+        n = p[4];
+        q = p[5];
+        pa = p[6];
+        c = p[7];
+    } else {
+        q = p[4];
+        pa = p[5];
+        c = p[6];
+    }
+    double th = pa * M_PI / 180.0;
+    double dx = x - x0, dy = y - y0;
+    double xp = dx * cos(th) + dy * sin(th);
+    double yp = -dx * sin(th) + dy * cos(th);
+    double C = c + 2.0;
+    double r = pow(pow(fabs(xp), C) + pow(fabs(yp / q), C), 1.0 / C);
+    if (kind == GFO_SERSIC) return amp * exp(-bn * (pow(r / rs, 1.0 / n) - 1.0));
+    return amp * exp(-r / rs);
+}
+
+static void os_block(const gfo_desc* d, int* bx0, int* by0)
+{
+    *bx0 = d->os_x0 >= 0 ? d->os_x0 : (d->W - d->os_box) / 2;
+    *by0 = d->os_y0 >= 0 ? d->os_y0 : (d->H - d->os_box) / 2;
+}
+
+/* Pixel value: the profile at the pixel centre, except inside the B x B
+ * oversampling block, where it is the mean of s x s samples placed at
+ * x = j - 1/2 + (b + 1/2)/s, y = i - 1/2 + (a + 1/2)/s. */
+static double comp_pixel_bn(const gfo_desc* d, int kind, const double* p, int i, int j,
+                            double bn)
+{
+    int s = d->os_factor, B = d->os_box;
+    if (kind != GFO_SKY && s > 1 && B > 0) {
+        int bx0, by0;
+        os_block(d, &bx0, &by0);
+        if (i >= by0 && i < by0 + B && j >= bx0 && j < bx0 + B) {
+            double acc = 0.0;
+            for (int a = 0; a < s; ++a)
+                for (int b = 0; b < s; ++b) {
+                    double y = i - 0.5 + (a + 0.5) / s;
+                    double x = j - 0.5 + (b + 0.5) / s;
+                    acc += gfo_comp_value(kind, p, x, y, bn);
+                }
+            return acc / ((double)s * s);
+        }
+    }
+    return gfo_comp_value(kind, p, (double)j, (double)i, bn);
+}
+
+double gfo_comp_pixel(const gfo_desc* d, int kind, const double* p, int i, int j)
+{
+    double bn = kind == GFO_SERSIC ? gfo_bn(p[4]) : 0.0;
+    return comp_pixel_bn(d, kind, p, i, j, bn);
+}
+
+/* Step 1 (transform): sum of the components on the extended grid. */
+int gfo_model_ext(const gfo_desc* d, const double* params, int comp, int unit_amp,
+                  double* out)
+{
+    int c = (d->P - 1) / 2;
+    int He = d->H + 2 * c, We = d->W + 2 * c;
+    memset(out, 0, sizeof(double) * (size_t)He * We);
+    int off = 0;
+    for (int k = 0; k < d->ncomp; ++k) {
+        int kind = d->kinds[k], ns = gfo_comp_nslots(kind);
+        if (ns < 0) return -1;
+        if (comp < 0 || comp == k) {
+            double p[8];
+            memcpy(p, params + off, sizeof(double) * ns);
+            if (unit_amp) p[kind == GFO_SKY ? 0 : 2] = 1.0;
+            double bn = kind == GFO_SERSIC ? gfo_bn(p[4]) : 0.0;
+            for (int ie = 0; ie < He; ++ie)
+                for (int je = 0; je < We; ++je)
+                    out[(size_t)ie * We + je] += comp_pixel_bn(d, kind, p, ie - c, je - c, bn);
+        }
+        off += ns;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------ convolution */
+
+/* Step 2 by its definition: out(i,j) = sum_{v,u} psf[v][u] E[i+2c-v][j+2c-u]. */
+void gfo_convolve_direct(int H, int W, int P, const double* ext, const double* psf,
+                         double* out)
+{
+    int c = (P - 1) / 2, We = W + 2 * c;
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            double acc = 0.0;
+            for (int v = 0; v < P; ++v)
+                for (int u = 0; u < P; ++u)
+                    acc += psf[v * P + u] * ext[(size_t)(i + 2 * c - v) * We + (j + 2 * c - u)];
+            out[(size_t)i * W + j] = acc;
+        }
+}
+
+int gfo_fft_size(int n)
+{
+    for (int m = n > 1 ? n : 1;; ++m) {
+        int r = m;
+        while (r % 2 == 0) r /= 2;
+        while (r % 3 == 0) r /= 3;
+        while (r % 5 == 0) r /= 5;
+        if (r == 1) return m;
+    }
+}
+
+static int smallest_factor(int n)
+{
+    for (int p = 2; p * p <= n; ++p)
+        if (n % p == 0) return p;
+    return n;
+}
+
+/* Decimation-in-time mixed-radix DFT.
+ * X[k] = sum_j x[j] w^{jk}, w = exp(sign 2 pi i / n).  With n = p m and the
+ * p decimated sequences x[jp + r], Y_r = DFT_m(x[. p + r]) and
+ * X[k + q m] = sum_r w_n^{r (k + q m)} Y_r[k].
+ * tw holds exp(2 pi i t / N) for the top-level N; w_n^t = tw[t * N / n]. */
+static void fft_rec(int n, const double* ire, const double* iim, int stride, double* ore,
+                    double* oim, int sign, const double* twr, const double* twi, int N)
+{
+    if (n == 1) {
+        ore[0] = ire[0];
+        oim[0] = iim[0];
+        return;
+    }
+    int p = smallest_factor(n), m = n / p;
+    for (int r = 0; r < p; ++r)
+        fft_rec(m, ire + (size_t)r * stride, iim + (size_t)r * stride, stride * p, ore + r * m,
+                oim + r * m, sign, twr, twi, N);
+    double* tr = (double*)malloc(sizeof(double) * p);
+    double* ti = (double*)malloc(sizeof(double) * p);
+    int tstep = N / n;
+    for (int k = 0; k < m; ++k) {
+        for (int q = 0; q < p; ++q) {
+            double sr = 0.0, si = 0.0;
+            for (int r = 0; r < p; ++r) {
+                long long e = ((long long)r * (k + q * m)) % n;
+                double wr = twr[e * tstep], wi = sign * twi[e * tstep];
+                double yr = ore[r * m + k], yi = oim[r * m + k];
+                sr += yr * wr - yi * wi;
+                si += yr * wi + yi * wr;
+            }
+            tr[q] = sr;
+            ti[q] = si;
+        }
+        for (int q = 0; q < p; ++q) {
+            ore[q * m + k] = tr[q];
+            oim[q * m + k] = ti[q];
+        }
+    }
+    free(tr);
+    free(ti);
+}
+
+void gfo_fft(int n, double* re, double* im, int sign)
+{
+    double* twr = (double*)malloc(sizeof(double) * n);
+    double* twi = (double*)malloc(sizeof(double) * n);
+    double* cr = (double*)malloc(sizeof(double) * n);
+    double* ci = (double*)malloc(sizeof(double) * n);
+    for (int t = 0; t < n; ++t) {
+        twr[t] = cos(2.0 * M_PI * t / n);
+        twi[t] = sin(2.0 * M_PI * t / n);
+    }
+    memcpy(cr, re, sizeof(double) * n);
+    memcpy(ci, im, sizeof(double) * n);
+    fft_rec(n, cr, ci, 1, re, im, sign, twr, twi, n);
+    free(twr);
+    free(twi);
+    free(cr);
+    free(ci);
+}
+
+/* 2-D DFT: 1-D transforms along every row, then along every column. */
+static void fft2(int ny, int nx, double* re, double* im, int sign)
+{
+    for (int y = 0; y < ny; ++y) gfo_fft(nx, re + (size_t)y * nx, im + (size_t)y * nx, sign);
+    double* cr = (double*)malloc(sizeof(double) * ny);
+    double* ci = (double*)malloc(sizeof(double) * ny);
+    for (int x = 0; x < nx; ++x) {
+        for (int y = 0; y < ny; ++y) {
+            cr[y] = re[(size_t)y * nx + x];
+            ci[y] = im[(size_t)y * nx + x];
+        }
+        gfo_fft(ny, cr, ci, sign);
+        for (int y = 0; y < ny; ++y) {
+            re[(size_t)y * nx + x] = cr[y];
+            im[(size_t)y * nx + x] = ci[y];
+        }
+    }
+    free(cr);
+    free(ci);
+}
+
+/* Step 2 in Fourier space (Sec. 3, item 2): the circular convolution at a
+ * padded size Ny x Nx >= the extended grid, with the PSF wrapped so that its
+ * centre sits at (0, 0), equals the direct sum on the valid region. */
+void gfo_convolve_fft(int H, int W, int P, const double* ext, const double* psf,
+                      double* out)
+{
+    int c = (P - 1) / 2, He = H + 2 * c, We = W + 2 * c;
+    int ny = gfo_fft_size(He), nx = gfo_fft_size(We);
+    size_t n = (size_t)ny * nx;
+    double* ar = (double*)calloc(n, sizeof(double));
+    double* ai = (double*)calloc(n, sizeof(double));
+    double* br = (double*)calloc(n, sizeof(double));
+    double* bi = (double*)calloc(n, sizeof(double));
+    for (int y = 0; y < He; ++y)
+        for (int x = 0; x < We; ++x) ar[(size_t)y * nx + x] = ext[(size_t)y * We + x];
+    for (int v = 0; v < P; ++v)
+        for (int u = 0; u < P; ++u) {
+            int y = ((v - c) % ny + ny) % ny, x = ((u - c) % nx + nx) % nx;
+            br[(size_t)y * nx + x] += psf[v * P + u];
+        }
+    fft2(ny, nx, ar, ai, -1);
+    fft2(ny, nx, br, bi, -1);
+    for (size_t t = 0; t < n; ++t) {
+        double r = ar[t] * br[t] - ai[t] * bi[t];
+        double i = ar[t] * bi[t] + ai[t] * br[t];
+        ar[t] = r;
+        ai[t] = i;
+    }
+    fft2(ny, nx, ar, ai, +1);
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j)
+            out[(size_t)i * W + j] = ar[(size_t)(i + c) * nx + (j + c)] / (double)n;
+    free(ar);
+    free(ai);
+    free(br);
+    free(bi);
+}
+
+/* ------------------------------------------------------------------- chi2 */
+
+typedef struct {
+    double s, c;
+} nsum;
+
+/* Neumaier's compensated summation */
+static void nsum_add(nsum* a, double t)
+{
+    double s = a->s + t;
+    if (fabs(a->s) >= fabs(t))
+        a->c += (a->s - s) + t;
+    else
+        a->c += (t - s) + a->s;
+    a->s = s;
+}
+
+static int pixel_valid(double d, double s) { return isfinite(d) && isfinite(s) && s > 0.0; }
+
+/* Step 3 (transform + reduce): sum of ((d - m)/sigma)^2 over valid pixels. */
+double gfo_chi2(int npix, const double* d, const double* sigma, const double* m)
+{
+    nsum a = {0.0, 0.0};
+    for (int t = 0; t < npix; ++t) {
+        if (!pixel_valid(d[t], sigma[t])) continue;
+        double z = (d[t] - m[t]) / sigma[t];
+        nsum_add(&a, z * z);
+    }
+    return a.s + a.c;
+}
+
+static void convolve(int method, int H, int W, int P, const double* ext, const double* psf,
+                     double* out)
+{
+    if (method == 1)
+        gfo_convolve_fft(H, W, P, ext, psf, out);
+    else
+        gfo_convolve_direct(H, W, P, ext, psf, out);
+}
+
+/* Steps 1-3 for one parameter vector. */
+double gfo_eval(const gfo_desc* d, const double* params, const double* psf,
+                const double* img, const double* sigma, int method, double* model_out)
+{
+    int c = (d->P - 1) / 2;
+    size_t ne = (size_t)(d->H + 2 * c) * (d->W + 2 * c), np = (size_t)d->H * d->W;
+    double* ext = (double*)malloc(sizeof(double) * ne);
+    double* m = model_out ? model_out : (double*)malloc(sizeof(double) * np);
+    gfo_model_ext(d, params, -1, 0, ext);
+    convolve(method, d->H, d->W, d->P, ext, psf, m);
+    double x2 = (img && sigma) ? gfo_chi2((int)np, img, sigma, m) : 0.0;
+    free(ext);
+    if (!model_out) free(m);
+    return x2;
+}
+
+/* ---------------------------------------------------------------- Jacobian */
+
+/* FD step: positions use fd_rel pixels (they are origin-relative); the other
+ * nonlinear slots use fd_rel * max(|v|, 1). */
+double gfo_fd_step(const gfo_desc* d, int slot, double v, double fd_rel)
+{
+    int role = slot_role(d, slot);
+    if (role == 0) return fd_rel;
+    return fd_rel * fmax(fabs(v), 1.0);
+}
+
+/* Jacobian of the convolved model with respect to the free slots:
+ * linear slots (amplitudes, sky) by the exact column, the convolution of the
+ * component with unit amplitude; nonlinear slots by forward (or central)
+ * differences of the full convolved model.  A = J^T W J, g = J^T W r with
+ * W = diag(1/sigma^2) on valid pixels and r = d - m. */
+double gfo_jacobian(const gfo_desc* d, const double* params, const uint8_t* fixed,
+                    const double* psf, const double* img, const double* sigma,
+                    int method, double fd_rel, int central, double* J, double* A,
+                    double* g, double* model_out)
+{
+    int c = (d->P - 1) / 2, ns = gfo_nslots(d);
+    size_t ne = (size_t)(d->H + 2 * c) * (d->W + 2 * c), np = (size_t)d->H * d->W;
+    double* ext = (double*)malloc(sizeof(double) * ne);
+    double* m0 = (double*)malloc(sizeof(double) * np);
+    double* mp = (double*)malloc(sizeof(double) * np);
+    double* mm = (double*)malloc(sizeof(double) * np);
+    int nfree = 0;
+    int freeslot[GFO_MAX_SLOTS];
+    for (int s = 0; s < ns; ++s)
+        if (!fixed || !fixed[s]) freeslot[nfree++] = s;
+    double* Jl = (double*)malloc(sizeof(double) * np * (nfree > 0 ? nfree : 1));
+    double pp[GFO_MAX_SLOTS];
+
+    gfo_model_ext(d, params, -1, 0, ext);
+    convolve(method, d->H, d->W, d->P, ext, psf, m0);
+    for (int f = 0; f < nfree; ++f) {
+        int s = freeslot[f], k, l, b;
+        slot_owner(d, s, &k, &l, &b);
+        double* col = Jl + (size_t)f * np;
+        if (gfo_slot_is_linear(d, s)) {
+            gfo_model_ext(d, params, k, 1, ext);
+            convolve(method, d->H, d->W, d->P, ext, psf, col);
+            continue;
+        }
+        double h = gfo_fd_step(d, s, params[s], fd_rel);
+        memcpy(pp, params, sizeof(double) * ns);
+        pp[s] = params[s] + h;
+        gfo_model_ext(d, pp, -1, 0, ext);
+        convolve(method, d->H, d->W, d->P, ext, psf, mp);
+        if (central) {
+            pp[s] = params[s] - h;
+            gfo_model_ext(d, pp, -1, 0, ext);
+            convolve(method, d->H, d->W, d->P, ext, psf, mm);
+            for (size_t t = 0; t < np; ++t) col[t] = (mp[t] - mm[t]) / (2.0 * h);
+        } else {
+            for (size_t t = 0; t < np; ++t) col[t] = (mp[t] - m0[t]) / h;
+        }
+    }
+    double x2 = 0.0;
+    if (img && sigma) {
+        x2 = gfo_chi2((int)np, img, sigma, m0);
+        for (int a = 0; a < nfree; ++a) {
+            nsum ga = {0.0, 0.0};
+            for (size_t t = 0; t < np; ++t) {
+                if (!pixel_valid(img[t], sigma[t])) continue;
+                double w = 1.0 / (sigma[t] * sigma[t]);
+                nsum_add(&ga, w * Jl[(size_t)a * np + t] * (img[t] - m0[t]));
+            }
+            if (g) g[a] = ga.s + ga.c;
+            for (int bb = 0; bb < nfree; ++bb) {
+                nsum aa = {0.0, 0.0};
+                for (size_t t = 0; t < np; ++t) {
+                    if (!pixel_valid(img[t], sigma[t])) continue;
+                    double w = 1.0 / (sigma[t] * sigma[t]);
+                    nsum_add(&aa, w * Jl[(size_t)a * np + t] * Jl[(size_t)bb * np + t]);
+                }
+                if (A) A[a * nfree + bb] = aa.s + aa.c;
+            }
+        }
+    }
+    if (J) memcpy(J, Jl, sizeof(double) * np * nfree);
+    if (model_out) memcpy(model_out, m0, sizeof(double) * np);
+    free(ext);
+    free(m0);
+    free(mp);
+    free(mm);
+    free(Jl);
+    return x2;
+}
+
+/* ------------------------------------------------------------------- LM */
+
+void gfo_default_opts(gfo_lm_opts* o)
+{
+    o->lambda0 = 1e-3;
+    o->lambda_up = 10.0;
+    o->lambda_down = 0.1;
+    o->lambda_min = 1e-12;
+    o->lambda_max = 1e12;
+    o->ftol = 1e-8;
+    o->xtol = 1e-8;
+    o->fd_rel = 1e-3;
+    o->max_iter = 200;
+}
+
+/* Default box: I >= 0, radii >= 0.1, n in [0.2, 10], q in [0.05, 1],
+ * boxiness in [-1.9, 2]; positions and sky free; position angles are wrapped
+ * into [0, 180) instead of clamped. */
+void gfo_default_bounds(const gfo_desc* d, double* lo, double* hi)
+{
+    int ns = gfo_nslots(d);
+    for (int s = 0; s < ns; ++s) {
+        lo[s] = -INFINITY;
+        hi[s] = INFINITY;
+        switch (slot_role(d, s)) {
+        case 1: lo[s] = 0.0; break;
+        case 2: lo[s] = 0.1; break;
+        case 3: lo[s] = 0.2; hi[s] = 10.0; break;
+        case 4: lo[s] = 0.05; hi[s] = 1.0; break;
+        case 6: lo[s] = -1.9; hi[s] = 2.0; break;
+        default: break;
+        }
+    }
+}
+
+static void project(const gfo_desc* d, double* p, const double* lo, const double* hi)
+{
+    int ns = gfo_nslots(d);
+    for (int s = 0; s < ns; ++s) {
+        if (slot_role(d, s) == 5) {
+            double a = fmod(p[s], 180.0);
+            if (a < 0.0) a += 180.0;
+            if (a >= 180.0) a -= 180.0;
+            p[s] = a;
+            continue;
+        }
+        if (p[s] < lo[s]) p[s] = lo[s];
+        if (p[s] > hi[s]) p[s] = hi[s];
+    }
+}
+
+/* scale of slot s in the step-size test |delta| / max(|p|, scale) */
+static double xtol_scale(const gfo_desc* d, int s)
+{
+    int role = slot_role(d, s);
+    if (role == 1) return 1e-30;
+    if (role == 7) return 1e-3;
+    return 1.0;
+}
+
+/* Cholesky solve of the SPD system M x = b (n <= 16); returns 0 on failure. */
+static int cholesky_solve(int n, const double* M, const double* b, double* x)
+{
+    double L[GFO_MAX_FREE * GFO_MAX_FREE];
+    memset(L, 0, sizeof(L));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = M[i * n + j];
+            for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            if (i == j) {
+                if (!(s > 0.0) || !isfinite(s)) return 0;
+                L[i * n + i] = sqrt(s);
+            } else {
+                L[i * n + j] = s / L[j * n + j];
+            }
+        }
+    double y[GFO_MAX_FREE];
+    for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+        y[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+        x[i] = s / L[i * n + i];
+    }
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(x[i])) return 0;
+    return 1;
+}
+
+/* Levenberg-Marquardt (Marquardt's diagonal damping), steps 4 and 5 of the
+ * loop.  One trial = solve (A + lambda diag A) delta = g, project p + delta
+ * into the box, evaluate chi^2 there; accept if chi^2 falls (lambda shrinks,
+ * a new Jacobian is taken), otherwise reject (lambda grows).  Finishing
+ * criteria: the scaled step falls below xtol, or an accepted step lowers
+ * chi^2 by less than ftol relative (converged); lambda exceeds lambda_max
+ * (no convergence); max_iter trials (iteration cap). */
+int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
+               const double* lo_in, const double* hi_in, const double* psf,
+               const double* img, const double* sigma, int method,
+               const gfo_lm_opts* opts_in, gfo_lm_result* res)
+{
+    gfo_lm_opts o;
+    if (opts_in)
+        o = *opts_in;
+    else
+        gfo_default_opts(&o);
+    int ns = gfo_nslots(d);
+    double lo[GFO_MAX_SLOTS], hi[GFO_MAX_SLOTS];
+    gfo_default_bounds(d, lo, hi);
+    if (lo_in) memcpy(lo, lo_in, sizeof(double) * ns);
+    if (hi_in) memcpy(hi, hi_in, sizeof(double) * ns);
+    int fs[GFO_MAX_SLOTS], nfree = 0;
+    for (int s = 0; s < ns; ++s)
+        if (!fixed || !fixed[s]) fs[nfree++] = s;
+    gfo_lm_result r = {0.0, o.lambda0, 0, 0, GFO_MAXITER};
+    if (nfree == 0 || nfree > GFO_MAX_FREE) {
+        r.status = GFO_BADINPUT;
+        if (res) *res = r;
+        return r.status;
+    }
+    double p[GFO_MAX_SLOTS], pt[GFO_MAX_SLOTS];
+    memcpy(p, params, sizeof(double) * ns);
+    project(d, p, lo, hi);
+    double A[GFO_MAX_FREE * GFO_MAX_FREE], g[GFO_MAX_FREE], M[GFO_MAX_FREE * GFO_MAX_FREE];
+    double rhs[GFO_MAX_FREE], delta[GFO_MAX_FREE];
+    double lambda = o.lambda0;
+    double chi2 = gfo_jacobian(d, p, fixed, psf, img, sigma, method, o.fd_rel, 0, NULL, A, g,
+                               NULL);
+    while (r.iters < o.max_iter) {
+        for (int i = 0; i < nfree; ++i) {
+            rhs[i] = g[i];
+            for (int j = 0; j < nfree; ++j) M[i * nfree + j] = A[i * nfree + j];
+        }
+        for (int i = 0; i < nfree; ++i) {
+            if (A[i * nfree + i] > 0.0) {
+                M[i * nfree + i] = A[i * nfree + i] * (1.0 + lambda);
+            } else {
+                /* a slot with no influence on the model is held this step */
+                for (int j = 0; j < nfree; ++j) M[i * nfree + j] = M[j * nfree + i] = 0.0;
+                M[i * nfree + i] = 1.0;
+                rhs[i] = 0.0;
+            }
+        }
+        r.iters++;
+        int ok = cholesky_solve(nfree, M, rhs, delta);
+        if (ok) {
+            double step = 0.0;
+            for (int i = 0; i < nfree; ++i) {
+                double den = fmax(fabs(p[fs[i]]), xtol_scale(d, fs[i]));
+                step = fmax(step, fabs(delta[i]) / den);
+            }
+            if (step < o.xtol) {
+                r.status = GFO_CONVERGED;
+                break;
+            }
+            memcpy(pt, p, sizeof(double) * ns);
+            for (int i = 0; i < nfree; ++i) pt[fs[i]] += delta[i];
+            project(d, pt, lo, hi);
+            double chi2t = gfo_eval(d, pt, psf, img, sigma, method, NULL);
+            if (isfinite(chi2t) && chi2t < chi2) {
+                double rel = (chi2 - chi2t) / chi2;
+                memcpy(p, pt, sizeof(double) * ns);
+                r.accepted++;
+                lambda = fmax(lambda * o.lambda_down, o.lambda_min);
+                if (rel < o.ftol) {
+                    chi2 = chi2t;
+                    r.status = GFO_CONVERGED;
+                    break;
+                }
+                chi2 = gfo_jacobian(d, p, fixed, psf, img, sigma, method, o.fd_rel, 0, NULL, A,
+                                    g, NULL);
+                continue;
+            }
+        }
+        lambda *= o.lambda_up;
+        if (lambda > o.lambda_max) {
+            r.status = GFO_NOCONV;
+            break;
+        }
+    }
+    r.chi2 = chi2;
+    r.lambda = lambda;
+    memcpy(params, p, sizeof(double) * ns);
+    if (res) *res = r;
+    return r.status;
+}
+
+int gfo_lm_fit_batch(int nb, const gfo_desc* ds, double* params, const uint8_t* fixed,
+                     const double* psf, const int64_t* psf_off, const double* img,
+                     const double* sigma, const int64_t* pix_off, int method,
+                     const gfo_lm_opts* opts, gfo_lm_result* res)
+{
+    int ns = gfo_nslots(&ds[0]);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < nb; ++b)
+        gfo_lm_fit(&ds[b], params + (size_t)b * ns, fixed ? fixed + (size_t)b * ns : NULL, NULL,
+                   NULL, psf + psf_off[b], img + pix_off[b], sigma + pix_off[b], method, opts,
+                   &res[b]);
+    return 0;
+}
+
+int gfo_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,142 @@
+/*
+ * gfo.h -- FP64 CPU oracle for the galaxy-fitting loop of Barsdell, Barnes &
+ * Fluke, "Fitting Galaxies on GPUs" (Sec. 2, steps 1-5; Sec. 3, items 1-3).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the plain, slow, obviously
+ * correct statement of what the GPU path computes.  Only the test suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it.  It shares
+ * no source, header, table or helper with the CUDA library, and neither side
+ * includes or links the other.
+ *
+ * Everything is double precision, plain loops, no blocking or fusion.
+ * OpenMP is used only across independent stamps (gfo_lm_fit_batch).
+ *
+ * Conventions (the paper names the steps only; each reading is listed in
+ * the design doc of the repository):
+ *   - pixel (row i, column j) of an H x W stamp has its centre at (x=j, y=i);
+ *   - the model is evaluated on the halo-extended grid E of
+ *     (H+2c) x (W+2c) pixels, c = (P-1)/2 for an odd P x P PSF; grid pixel
+ *     (ie, je) is stamp pixel (ie-c, je-c);
+ *   - the convolved image on the stamp is the true (flipped-kernel) sum
+ *     out(i,j) = sum_{v,u} psf[v][u] * E[i+2c-v][j+2c-u].
+ *
+ * Parameter slots per component, in order:
+ *   Sersic  (kind 1): x0, y0, I_e, r_e, n, q, pa_deg, c     (8 slots)
+ *   ExpDisk (kind 2): x0, y0, I_0, r_s, q, pa_deg, c         (7 slots)
+ *   Sky     (kind 3): s0                                     (1 slot)
+ */
+#ifndef GFO_H
+#define GFO_H
+#include <stdint.h>
+
+#define GFO_SERSIC 1
+#define GFO_EXPDISK 2
+#define GFO_SKY 3
+#define GFO_MAX_COMP 8
+#define GFO_MAX_SLOTS 64
+#define GFO_MAX_FREE 16
+
+/* LM status words */
+#define GFO_CONVERGED 0
+#define GFO_MAXITER 8
+#define GFO_NOCONV 3
+#define GFO_BADINPUT 1
+
+typedef struct {
+    int H, W;        /* stamp rows, columns */
+    int P;           /* PSF side, odd */
+    int ncomp;
+    int kinds[GFO_MAX_COMP];
+    int os_factor;   /* s: s x s sub-samples per pixel inside the block (1 = off) */
+    int os_box;      /* B: block side in pixels */
+    int os_x0, os_y0;/* block origin in stamp pixels; -1 = centred on the stamp */
+} gfo_desc;
+
+typedef struct {
+    double lambda0, lambda_up, lambda_down, lambda_min, lambda_max;
+    double ftol, xtol, fd_rel;
+    int max_iter;
+} gfo_lm_opts;
+
+typedef struct {
+    double chi2;
+    double lambda;
+    int iters;       /* trial steps taken (accepted + rejected) */
+    int accepted;
+    int status;
+} gfo_lm_result;
+
+int gfo_comp_nslots(int kind);
+int gfo_nslots(const gfo_desc* d);
+
+/* b_n: the root of P(2n, b) = 1/2 (regularised lower incomplete gamma). */
+double gfo_bn(double n);
+/* regularised lower incomplete gamma P(a, x), series form */
+double gfo_gammainc_lower(double a, double x);
+/* closed-form total flux of an elliptical (c = 0) Sersic component */
+double gfo_sersic_flux(double Ie, double re, double n, double q);
+
+/* surface brightness of one component at a point (amplitude taken from p) */
+double gfo_comp_value(int kind, const double* p, double x, double y, double bn);
+
+/* value of one component averaged over stamp pixel (i, j) with the desc's
+ * oversampling rule; i, j may lie in the halo. */
+double gfo_comp_pixel(const gfo_desc* d, int kind, const double* p, int i, int j);
+
+/* Step 1: the model on the extended grid; out has (H+2c)*(W+2c) entries.
+ * comp = -1: all components summed; comp = k >= 0: component k only.
+ * unit_amp = 1: component k with its amplitude slot set to 1. */
+int gfo_model_ext(const gfo_desc* d, const double* params, int comp, int unit_amp,
+                  double* out);
+
+/* Step 2, by the definition: out (H*W) from ext ((H+2c)*(W+2c)) */
+void gfo_convolve_direct(int H, int W, int P, const double* ext, const double* psf,
+                         double* out);
+/* Step 2, via the oracle's own FP64 mixed-radix FFT (circular at the padded
+ * size, exact on the valid region) */
+void gfo_convolve_fft(int H, int W, int P, const double* ext, const double* psf,
+                      double* out);
+/* one complex DFT of length n by the oracle's FFT (sign -1 forward, +1 inverse,
+ * unnormalised); re/im in place */
+void gfo_fft(int n, double* re, double* im, int sign);
+int gfo_fft_size(int n); /* smallest 2^a 3^b 5^c >= n */
+
+/* Step 3: chi^2 over pixels with finite d, sigma > 0 (Neumaier sum) */
+double gfo_chi2(int npix, const double* d, const double* sigma, const double* m);
+
+/* Steps 1-3 for one parameter vector: convolved model on the stamp and chi^2.
+ * method 0 = direct, 1 = FFT. */
+double gfo_eval(const gfo_desc* d, const double* params, const double* psf,
+                const double* img, const double* sigma, int method, double* model_out);
+
+/* Step 4 input: Jacobian columns for the free slots (fixed[s] == 0).
+ * J: nfree x H*W (may be NULL), A: nfree^2, g: nfree, returns chi^2 at params.
+ * central = 1 uses central differences for the nonlinear slots. */
+double gfo_jacobian(const gfo_desc* d, const double* params, const uint8_t* fixed,
+                    const double* psf, const double* img, const double* sigma,
+                    int method, double fd_rel, int central, double* J, double* A,
+                    double* g, double* model_out);
+
+/* default bounds for every slot */
+void gfo_default_bounds(const gfo_desc* d, double* lo, double* hi);
+void gfo_default_opts(gfo_lm_opts* o);
+/* the FD step for slot s at value v (absolute) */
+double gfo_fd_step(const gfo_desc* d, int slot, double v, double fd_rel);
+int gfo_slot_is_linear(const gfo_desc* d, int slot);
+
+/* Steps 4-5: Levenberg-Marquardt from params (in/out) */
+int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
+               const double* lo, const double* hi, const double* psf,
+               const double* img, const double* sigma, int method,
+               const gfo_lm_opts* opts, gfo_lm_result* res);
+
+/* independent stamps, OpenMP across stamps.  Stamp b uses desc ds[b],
+ * params + b*nslots, psf + psf_off[b], img/sigma + pix_off[b]. */
+int gfo_lm_fit_batch(int nb, const gfo_desc* ds, double* params, const uint8_t* fixed,
+                     const double* psf, const int64_t* psf_off, const double* img,
+                     const double* sigma, const int64_t* pix_off, int method,
+                     const gfo_lm_opts* opts, gfo_lm_result* res);
+
+int gfo_num_threads(void);
+
+#endif

@@ -1,0 +1,190 @@
+"""Pins of the oracle's model evaluation (step 1 of the loop, Sec. 2; a
+"transform" in Sec. 3): rotation convention, generalised radius, Sersic and
+exponential-disk profiles, enclosed light, oversampling and block placement."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1101_2254_gb300 import synth
+
+S, E, K = oracle.SERSIC, oracle.EXPDISK, oracle.SKY
+
+
+def sersic(x0=10.0, y0=-3.0, Ie=1.7, re=6.0, n=2.5, q=0.55, pa=30.0, c=0.0):
+    return np.array([x0, y0, Ie, re, n, q, pa, c])
+
+
+def test_major_axis_direction_is_ccw_from_x():
+    # a point at distance r_e along the major axis (angle PA from +x, CCW toward +y)
+    p = sersic()
+    th = math.radians(p[6])
+    x, y = p[0] + p[3] * math.cos(th), p[1] + p[3] * math.sin(th)
+    assert abs(oracle.comp_value(S, p, x, y) - p[2]) < 1e-13
+    # at distance q r_e along the minor axis
+    x, y = p[0] - p[5] * p[3] * math.sin(th), p[1] + p[5] * p[3] * math.cos(th)
+    assert abs(oracle.comp_value(S, p, x, y) - p[2]) < 1e-13
+    # the mirrored direction (clockwise) is not on the isophote
+    x, y = p[0] + p[3] * math.cos(-th), p[1] + p[3] * math.sin(-th)
+    assert abs(oracle.comp_value(S, p, x, y) - p[2]) > 1e-3
+
+
+def test_boxiness_closed_form_on_diagonal():
+    # with x' = t and y'/q = t, r = (2 t^C)^{1/C} = t 2^{1/C}, C = c + 2
+    for c in (-0.7, 0.0, 0.9, 1.6):
+        p = sersic(c=c, n=1.0)
+        th = math.radians(p[6])
+        t = 4.0
+        xp, yp = t, p[5] * t
+        x = p[0] + xp * math.cos(th) - yp * math.sin(th)
+        y = p[1] + xp * math.sin(th) + yp * math.cos(th)
+        r = t * 2.0 ** (1.0 / (c + 2.0))
+        b = oracle.bn(1.0)
+        want = p[2] * math.exp(-b * (r / p[3] - 1.0))
+        assert abs(oracle.comp_value(S, p, x, y) - want) < 1e-13 * want
+        # and on the major axis the radius is |x'| for any c
+        x = p[0] + t * math.cos(th)
+        y = p[1] + t * math.sin(th)
+        want = p[2] * math.exp(-b * (t / p[3] - 1.0))
+        assert abs(oracle.comp_value(S, p, x, y) - want) < 1e-13 * want
+
+
+def test_expdisk_equals_sersic_one():
+    b1 = oracle.bn(1.0)
+    I0, rs = 2.3, 7.0
+    pd = np.array([1.0, 2.0, I0, rs, 0.4, 77.0, 0.3])
+    ps = np.array([1.0, 2.0, I0 * math.exp(-b1), b1 * rs, 1.0, 0.4, 77.0, 0.3])
+    for (x, y) in [(1.0, 2.0), (5.0, -3.0), (-10.0, 14.0), (30.0, 2.5)]:
+        a, b = oracle.comp_value(E, pd, x, y), oracle.comp_value(S, ps, x, y)
+        assert abs(a - b) < 1e-13 * max(a, 1e-300)
+    # I(r_s) = I_0 / e on the major axis
+    th = math.radians(77.0)
+    v = oracle.comp_value(E, pd, 1.0 + rs * math.cos(th), 2.0 + rs * math.sin(th))
+    assert abs(v - I0 / math.e) < 1e-13
+
+
+def _enclosed(kind, p, R, nt=96, nphi=96):
+    """Light inside the generalised ellipse r <= R, integrated in the
+    component's own frame: x' = rho cos(phi), y' = q rho sin(phi), with the
+    substitution rho = r_e t^n that makes the Sersic integrand smooth."""
+    n = p[4] if kind == S else 1.0
+    q = p[5] if kind == S else p[4]
+    re = p[3]
+    th = math.radians(p[6] if kind == S else p[5])
+    tmax = (R / re) ** (1.0 / n)
+    tg, tw = np.polynomial.legendre.leggauss(nt)
+    t = 0.5 * tmax * (tg + 1.0)
+    wt = 0.5 * tmax * tw
+    phi = (np.arange(nphi) + 0.5) * 2 * math.pi / nphi
+    tot = 0.0
+    for ti, wi in zip(t, wt):
+        rho = re * ti ** n
+        drho = re * n * ti ** (n - 1.0)
+        for ph in phi:
+            xp, yp = rho * math.cos(ph), q * rho * math.sin(ph)
+            x = p[0] + xp * math.cos(th) - yp * math.sin(th)
+            y = p[1] + xp * math.sin(th) + yp * math.cos(th)
+            tot += wi * (2 * math.pi / nphi) * q * rho * drho * oracle.comp_value(kind, p, x, y)
+    return tot
+
+
+@pytest.mark.parametrize("n", [0.5, 1.0, 2.5, 4.0])
+def test_effective_radius_encloses_half_the_light(n):
+    p = sersic(n=n)
+    F = oracle.sersic_flux(p[2], p[3], n, p[5])
+    assert abs(_enclosed(S, p, p[3]) - 0.5 * F) < 1e-9 * F
+    # and a wider aperture encloses F P(2n, b (R/r_e)^{1/n})
+    from scipy.special import gammainc
+    R = 3.0 * p[3]
+    want = F * gammainc(2 * n, oracle.bn(n) * 3.0 ** (1.0 / n))
+    assert abs(_enclosed(S, p, R) - want) < 1e-9 * F
+
+
+def test_pixel_grid_sums_to_closed_form_flux():
+    # n = 1/2 and n = 1 decay fast enough that a 96x96 grid holds all the light;
+    # 8x8 oversampling everywhere approximates the cell integrals.
+    for n, tol in [(0.5, 2e-5), (1.0, 2e-4)]:
+        d = oracle.make_desc(96, 96, 1, [S], os_factor=8, os_box=96)
+        p = np.array([47.3, 48.1, 1.0, 5.0, n, 0.6, 30.0, 0.0])
+        tot = oracle.model_ext(d, p).sum()
+        F = oracle.sersic_flux(1.0, 5.0, n, 0.6)
+        assert abs(tot - F) < tol * F
+
+
+def test_position_angle_symmetries():
+    d = oracle.make_desc(40, 40, 5, [S, K])
+    p = np.array([19.5, 19.5, 1.0, 6.0, 1.5, 0.5, 20.0, 0.0, 0.05])
+    m = oracle.model_ext(d, p)
+    # PA and PA + 180 give the same image
+    p2 = p.copy(); p2[6] += 180.0
+    assert np.array_equal(oracle.model_ext(d, p2), m) or np.abs(oracle.model_ext(d, p2) - m).max() < 1e-12
+    # PA -> 90 - PA is the transpose when the centre is on the diagonal (x <-> y reflection)
+    p3 = p.copy(); p3[6] = 90.0 - p[6]
+    assert np.abs(oracle.model_ext(d, p3) - m.T).max() < 1e-12 * m.max()
+    # q = 1: no dependence on PA
+    p4 = p.copy(); p4[5] = 1.0
+    p5 = p4.copy(); p5[6] = 71.0
+    assert np.abs(oracle.model_ext(d, p4) - oracle.model_ext(d, p5)).max() < 1e-12 * m.max()
+
+
+def test_extended_grid_geometry_and_sky():
+    # grid pixel (ie, je) is stamp pixel (ie - c, je - c) with centre (x=j, y=i)
+    d = oracle.make_desc(20, 30, 7, [S, K])
+    p = np.array([12.0, 8.0, 1.0, 3.0, 1.0, 1.0, 0.0, 0.0, 0.25])
+    m = oracle.model_ext(d, p)
+    assert m.shape == (26, 36)
+    c = 3
+    # the centre pixel holds I_e e^{b_1} + sky
+    assert abs(m[8 + c, 12 + c] - (math.exp(oracle.bn(1.0)) + 0.25)) < 1e-12
+    # components separately and with unit amplitude
+    ms = oracle.model_ext(d, p, comp=0)
+    sky = oracle.model_ext(d, p, comp=1)
+    assert np.allclose(sky, 0.25, rtol=0, atol=0)
+    assert np.abs(ms + sky - m).max() < 1e-14
+    p2 = p.copy(); p2[2] = 3.5
+    assert np.abs(oracle.model_ext(d, p2, comp=0, unit_amp=True) - ms).max() < 1e-15
+
+
+def test_oversampling_converges_to_cell_integral():
+    # the pixel mean of s x s midpoint samples converges to the cell integral
+    # as 1/s^2 (a misplaced sample offset would leave a 1/s error)
+    p = np.array([0.2, -0.1, 1.0, 1.5, 0.5, 0.8, 10.0, 0.0])
+    i, j = 1, 0
+    g, w = np.polynomial.legendre.leggauss(24)
+    cell = 0.0
+    for a, wa in zip(g, w):
+        for b, wb in zip(g, w):
+            cell += 0.25 * wa * wb * oracle.comp_value(S, p, j + 0.5 * b, i + 0.5 * a)
+    errs = []
+    for s in (4, 8, 16):
+        d = oracle.make_desc(3, 3, 1, [S], os_factor=s, os_box=3, os_x0=0, os_y0=0)
+        v = oracle.model_ext(d, p)[i, j]
+        errs.append(abs(v - cell))
+    assert errs[2] < 1e-4 * cell
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+    # s = 1 is the centre sample
+    d = oracle.make_desc(3, 3, 1, [S], os_factor=1, os_box=3)
+    assert oracle.model_ext(d, p)[i, j] == oracle.comp_value(S, p, j, i)
+
+
+def test_oversampling_block_placement():
+    # B x B block centred on the stamp: rows and columns floor((H-B)/2) .. +B-1
+    d1 = oracle.make_desc(16, 20, 3, [S], os_factor=1, os_box=0)
+    d5 = oracle.make_desc(16, 20, 3, [S], os_factor=5, os_box=4)
+    p = np.array([9.3, 7.6, 1.0, 2.0, 2.0, 0.7, 33.0, 0.0])
+    c = 1
+    diff = np.abs(oracle.model_ext(d5, p) - oracle.model_ext(d1, p)) > 0
+    rows, cols = np.nonzero(diff)
+    assert rows.min() - c == 6 and rows.max() - c == 9
+    assert cols.min() - c == 8 and cols.max() - c == 11
+    # an explicit origin moves it
+    d5b = oracle.make_desc(16, 20, 3, [S], os_factor=5, os_box=4, os_x0=1, os_y0=2)
+    rows, cols = np.nonzero(np.abs(oracle.model_ext(d5b, p) - oracle.model_ext(d1, p)) > 0)
+    assert rows.min() - c == 2 and cols.min() - c == 1
+
+
+def test_stamp64_central_intensity():
+    # the 64x64 workload's n = 4 component peaks at I_e e^{b_4} = 2141.47354...
+    p = np.array([32.3, 31.7, 1.0, 8.0, 4.0, 0.7, 30.0, 0.0])
+    assert abs(oracle.comp_value(S, p, 32.3, 31.7) - 2141.47354) < 1e-4
