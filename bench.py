@@ -1,0 +1,385 @@
+"""Throughput of the galaxy-fitting loop on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gf|reference]
+                    [--workload stamp512|stamp64]
+
+A step is one complete Levenberg-Marquardt fit (steps 1-5 of the loop) of the
+workload's stamp from its 20 %-perturbed start, inputs resident on the device;
+`value` is fits per second over all ranks.  The default workload is the
+512x512 bulge + disk + sky stamp with a 65x65 Moffat PSF, 10x10 oversampling
+in the central 20x20 pixels and 15 free parameters.
+
+Under torchrun every rank fits its own copy of the stamp (stamps are
+independent: weak scaling, no collective on the data path); the barrier and
+the max over ranks of the timed region stay.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (rank 0
+only), on a bounded sample: per step one oracle Jacobian and one oracle
+evaluation of the same stamp, scaled to fits/s by the oracle's own iteration
+counts for this fit (stored by tests/golden/make_golden.py).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fits/s to oracle chi2 (512x512 bulge+disk+sky, Moffat 65x65 PSF, 15-param LM)"
+METRIC64 = "fits/s to oracle chi2 (64x64 Sersic+sky, Gaussian 25x25 PSF, 8-param LM)"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gf", choices=["gf", "reference"])
+    ap.add_argument("--workload", default="stamp512", choices=["stamp512", "stamp64"])
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(name):
+    from paper_1101_2254_gb300 import synth
+    return synth.stamp512() if name == "stamp512" else synth.stamp64()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_count, mhz):
+    # 128 FP32 lanes per SM, one FMA (2 FLOP) per lane per clock
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ the GPU arm
+def run_gf(args):
+    import torch
+    import torch.distributed as dist
+    ws_, rank, local = dist_env()
+    if ws_ > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1101_2254_gb300 import build, gf, synth
+    build.build()
+    st = workload(args.workload)
+    d = gf.make_desc(st.H, st.W, st.P, st.kinds, st.os_factor, st.os_box)
+    psf_d = torch.as_tensor(st.psf).to(dev)
+    # true image rendered by the library, noise from the seeded generator
+    ext = gf.model(d, st.params)
+    m_true = gf.convolve(d, ext, psf_d).cpu().numpy()
+    img_h, sig_h = synth.add_noise(m_true, st.noise_seed)
+    img_p = torch.as_tensor(img_h).pin_memory()
+    sig_p = torch.as_tensor(sig_h).pin_memory()
+    psf_p = torch.as_tensor(st.psf).pin_memory()
+    img_d, sig_d = img_p.to(dev), sig_p.to(dev)
+    p0 = st.guess()
+    ws = gf.Workspace(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def fit():
+        return gf.lm_fit(d, p0, st.fixed, img_d, sig_d, psf_d, ws=ws)
+
+    for _ in range(max(args.warmup, 0)):
+        p, res = fit()
+    torch.cuda.synchronize()
+    if ws_ > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    results = []
+    step_ms = []
+    with ClockSampler(local) as clk, gf.Profiler() as prof:
+        launches0 = gf.launch_count()
+        for _ in range(args.steps):
+            flush.zero_()  # evict the previous fit's data from L2 (untimed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p, res = fit()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            results.append(res)
+        launches = gf.launch_count() - launches0
+    torch.cuda.synchronize()
+    total_ms = float(sum(step_ms))
+    if ws_ > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_ms = float(t.item())
+    fits = args.steps * ws_
+    value = fits / (total_ms / 1e3)
+
+    # end to end through the public API: pinned host inputs copied in every step,
+    # parameters come back to the host inside the call
+    e2e_ms = []
+    img_e = torch.empty_like(img_d)
+    sig_e = torch.empty_like(sig_d)
+    psf_e = torch.empty_like(psf_d)
+    for k in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        img_e.copy_(img_p, non_blocking=True)
+        sig_e.copy_(sig_p, non_blocking=True)
+        psf_e.copy_(psf_p, non_blocking=True)
+        pe, re_ = gf.lm_fit(d, p0, st.fixed, img_e, sig_e, psf_e, ws=ws)
+        e1.record(stream)
+        e1.synchronize()
+        if k > 0:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = float(sum(e2e_ms))
+    if ws_ > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = args.steps * ws_ / (e2e_total / 1e3)
+    h2d = img_p.numel() * 4 + sig_p.numel() * 4 + psf_p.numel() * 4
+    d2h = 8 * len(p0) + 32
+
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    clocks = clk.summary()
+    pr = prof.result
+    dom = max(("model", "conv", "reduce"), key=lambda k: pr[k]["ms"])
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    if dom == "conv":
+        achieved = pr["conv"]["work"] / (pr["conv"]["ms"] / 1e3) / 1e12
+        peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+        roof = {"bound": "alu", "kernel": "k_conv_direct", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 "
+                               f"FLOP x {sm_max:.0f} MHz (max clock)",
+                "launches": pr["conv"]["launches"],
+                "avg_launch_ms": pr["conv"]["ms"] / max(pr["conv"]["launches"], 1)}
+    else:
+        achieved = pr[dom]["work"] / (pr[dom]["ms"] / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_kind} HBM copy", "launches": pr[dom]["launches"],
+                "avg_launch_ms": pr[dom]["ms"] / max(pr[dom]["launches"], 1)}
+    chan_evals = pr["conv"]["work"] / (2.0 * st.P * st.P * st.H * st.W)
+    alg_bytes = pr["model"]["work"] + pr["reduce"]["work"]
+    line = {
+        "metric": METRIC if args.workload == "stamp512" else METRIC64,
+        "value": value, "unit": "fits/s", "n_gpus": ws_, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded: params, PSF, noise; true image rendered by the library)",
+        "config": {"workload": args.workload, "stamp": [st.H, st.W], "psf": st.P,
+                   "components": "sersic+expdisk+sky" if args.workload == "stamp512"
+                   else "sersic+sky", "free_params": st.nfree,
+                   "oversampling": [st.os_factor, st.os_box], "conv": "direct",
+                   "l2": "flushed between steps (256 MB write, untimed)",
+                   "parallelism": f"replicas{ws_}"},
+        "e2e": {"value": e2e_value, "unit": "fits/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "evals_per_s": chan_evals * ws_ / (total_ms / 1e3),
+        "alg_hbm_gbs": alg_bytes / (total_ms / 1e3) / 1e9,
+        "kernel_ms": {k: v["ms"] / args.steps for k, v in pr.items()},
+        "lm": {"iters": results[-1]["iters"], "accepted": results[-1]["accepted"],
+               "status": results[-1]["status"], "chi2": results[-1]["chi2"]},
+        "clocks": clocks,
+        "peaks": peak_kind,
+    }
+    if rank == 0 and ws_ == 1:
+        line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=20.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws_ > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ the oracle
+def _oracle_setup(name):
+    import oracle
+    st = workload(name)
+    d = oracle.make_desc(st.H, st.W, st.P, st.kinds, st.os_factor, st.os_box)
+    method = 1 if name == "stamp512" else 0
+    m_true = oracle.render(d, st.params, st.psf, method=method)
+    from paper_1101_2254_gb300 import synth
+    img, sig = synth.add_noise(m_true, st.noise_seed)
+    return oracle, st, d, img, sig, method
+
+
+def _golden_counts(name):
+    path = os.path.join(ROOT, "tests", "golden", f"{name}.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            g = json.load(fh)
+        return g["accepted"] + 1, g["iters"], "tests/golden/" + os.path.basename(path)
+    return None
+
+
+def _oracle_iteration(oracle, st, d, img, sig, method):
+    p0 = st.guess()
+    t0 = time.perf_counter()
+    oracle.jacobian(d, p0, st.fixed, st.psf, img, sig, method=method)
+    t1 = time.perf_counter()
+    oracle.evaluate(d, p0, st.psf, img, sig, method=method)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def cpu_baseline(name, budget_s=20.0):
+    """The oracle as it stands, on the host cores, on a bounded sample."""
+    oracle, st, d, img, sig, method = _oracle_setup(name)
+    counts = _golden_counts(name)
+    if name == "stamp64" or counts is None:
+        # whole fits, repeated within the budget
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            _, res = oracle.lm_fit(d, st.guess(), st.fixed, st.psf, img, sig, method=method)
+            n += 1
+            if time.perf_counter() - t0 > budget_s or n >= 50:
+                break
+        dt = time.perf_counter() - t0
+        return {"value": n / dt, "unit": "fits/s", "cores": 1, "kind": "oracle",
+                "sample": f"{n} complete oracle LM fits of the {name} stamp"}
+    n_jac, n_eval, src = counts
+    tj, te, n = [], [], 0
+    t0 = time.perf_counter()
+    while n < 1 or (time.perf_counter() - t0 < budget_s and n < 5):
+        a, b = _oracle_iteration(oracle, st, d, img, sig, method)
+        tj.append(a)
+        te.append(b)
+        n += 1
+    s_fit = n_jac * float(np.mean(tj)) + n_eval * float(np.mean(te))
+    return {"value": 1.0 / s_fit, "unit": "fits/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} oracle Jacobian + evaluation pairs of the {name} stamp (FFT "
+                      f"convolution), scaled by the oracle's own counts for this fit "
+                      f"({n_jac} Jacobians, {n_eval} evaluations; {src})"}
+
+
+def run_reference(args):
+    ws_, rank, local = dist_env()
+    if rank != 0:
+        return
+    oracle, st, d, img, sig, method = _oracle_setup(args.workload)
+    counts = _golden_counts(args.workload)
+    for _ in range(max(0, min(args.warmup, 1))):
+        _oracle_iteration(oracle, st, d, img, sig, method)
+    tj, te = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        a, b = _oracle_iteration(oracle, st, d, img, sig, method)
+        tj.append(a)
+        te.append(b)
+    wall = time.perf_counter() - t0
+    if counts is None:
+        n_jac, n_eval, src = 1, 1, "one Jacobian + one evaluation per fit (no stored counts)"
+    else:
+        n_jac, n_eval, src = counts
+    s_fit = n_jac * float(np.mean(tj)) + n_eval * float(np.mean(te))
+    value = 1.0 / s_fit
+    sample = (f"per step one oracle Jacobian + one evaluation of the {args.workload} stamp; "
+              f"fits/s = 1 / ({n_jac} Jacobians + {n_eval} evaluations) ({src})")
+    line = {"impl": "reference", "metric": METRIC if args.workload == "stamp512" else METRIC64,
+            "value": value, "unit": "fits/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "config": {"workload": args.workload},
+            "cpu_baseline": {"value": value, "unit": "fits/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "fits/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gf(a)

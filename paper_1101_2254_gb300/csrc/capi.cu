@@ -1,0 +1,813 @@
+// capi.cu -- the extern "C" boundary of libgf.so (declared in include/gf.h).
+//
+// Host code only: argument validation, the workspace layout, the per-stamp
+// block tables, and the order of kernel launches.  Every step of the fitting
+// loop runs in the kernels of model.cu, conv_*.cu, reduce.cu and lm.cu.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gf_internal.cuh"
+
+std::atomic<long long> g_launch_count{0};
+
+static thread_local std::string g_err;
+
+static gf_status fail(gf_status s, const std::string& msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define GF_CUDA(expr)                                                                  \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(GF_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+cudaError_t ensure_smem_optin(const void* func, int bytes, int* cache)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && cache[dev] >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) cache[dev] = bytes;
+    return e;
+}
+
+size_t conv_direct_smem(int P);
+
+// ------------------------------------------------------------ profiling
+// Off unless gf_prof_enable() received a device counter array.  When on, each
+// kernel class launch is bracketed by CUDA events on its stream, and the
+// kernels add their algorithmic work to the caller's counters.
+namespace prof {
+struct Rec {
+    int cls;
+    long long launches;
+    cudaEvent_t e0, e1;
+};
+std::mutex mu;
+unsigned long long* work_dev = nullptr;
+std::vector<Rec> pending;
+std::vector<cudaEvent_t> pool;
+double ms[PROF_CLASSES];
+long long launches[PROF_CLASSES];
+
+cudaEvent_t get_event()
+{
+    cudaEvent_t e = nullptr;
+    if (!pool.empty()) {
+        e = pool.back();
+        pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+}  // namespace prof
+
+struct ProfScope {
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr;
+    long long n0 = 0;
+    ProfScope(int c, cudaStream_t st) : cls(c), s(st)
+    {
+        if (!prof::work_dev) return;
+        std::lock_guard<std::mutex> g(prof::mu);
+        e0 = prof::get_event();
+        if (e0) cudaEventRecord(e0, s);
+        n0 = g_launch_count.load();
+    }
+    ~ProfScope()
+    {
+        if (!e0) return;
+        std::lock_guard<std::mutex> g(prof::mu);
+        cudaEvent_t e1 = prof::get_event();
+        if (!e1) return;
+        cudaEventRecord(e1, s);
+        prof::pending.push_back({cls, g_launch_count.load() - n0, e0, e1});
+    }
+};
+
+namespace {
+
+int comp_slots(int kind)
+{
+    switch (kind) {
+    case GF_SERSIC: return 8;
+    case GF_EXPDISK: return 7;
+    case GF_SKY: return 1;
+    default: return -1;
+    }
+}
+
+int resolve_method(const gf_desc* d)
+{
+    if (d->conv_method == GF_CONV_AUTO)
+        return d->psf_size <= GF_DIRECT_MAX_PSF ? GF_CONV_DIRECT : GF_CONV_FFT;
+    return d->conv_method;
+}
+
+// Structure checks shared by every call; H and W are checked per stamp.
+gf_status check_structure(const gf_desc* d)
+{
+    if (!d) return fail(GF_EINVAL, "desc is NULL");
+    const int P = d->psf_size;
+    if (P < 1 || P > GF_MAX_PSF || P % 2 == 0)
+        return fail(GF_EINVAL, "psf_size must be odd and in [1, " + std::to_string(GF_MAX_PSF) + "]");
+    if (d->ncomp < 1 || d->ncomp > GF_MAX_COMP) return fail(GF_EINVAL, "ncomp out of range");
+    int nsky = 0, nprof = 0;
+    for (int k = 0; k < d->ncomp; ++k) {
+        if (comp_slots(d->kinds[k]) < 0) return fail(GF_EINVAL, "unknown component kind");
+        if (d->kinds[k] == GF_SKY)
+            ++nsky;
+        else
+            ++nprof;
+    }
+    if (nsky > 1) return fail(GF_EINVAL, "at most one sky component");
+    if (nprof < 1) return fail(GF_EINVAL, "at least one Sersic or exponential-disk component");
+    if (d->os_factor < 1 || d->os_factor > 64) return fail(GF_EINVAL, "os_factor out of [1, 64]");
+    if (d->os_box < 0) return fail(GF_EINVAL, "os_box < 0");
+    const int m = resolve_method(d);
+    if (m != GF_CONV_DIRECT && m != GF_CONV_FFT) return fail(GF_EINVAL, "unknown conv_method");
+    if (m == GF_CONV_DIRECT && P > GF_DIRECT_MAX_PSF)
+        return fail(GF_EINVAL, "direct convolution supports psf_size <= " +
+                                   std::to_string(GF_DIRECT_MAX_PSF));
+    if (m == GF_CONV_FFT) return fail(GF_EINVAL, "FFT convolution is not available in this build");
+    return GF_OK;
+}
+
+gf_status check_stamp(const gf_desc* d, int H, int W)
+{
+    if (H < 1 || W < 1) return fail(GF_EINVAL, "stamp H and W must be >= 1");
+    if ((long long)H * W > (1LL << 31) - 1) return fail(GF_EINVAL, "stamp too large");
+    if (d->os_factor > 1 && d->os_box > 0) {
+        if (d->os_box > H || d->os_box > W) return fail(GF_EINVAL, "os_box exceeds the stamp");
+        const int x0 = d->os_x0 >= 0 ? d->os_x0 : (W - d->os_box) / 2;
+        const int y0 = d->os_y0 >= 0 ? d->os_y0 : (H - d->os_box) / 2;
+        if (x0 + d->os_box > W || y0 + d->os_box > H)
+            return fail(GF_EINVAL, "oversampling block leaves the stamp");
+    }
+    return GF_OK;
+}
+
+int nslots_of(const gf_desc* d)
+{
+    int n = 0;
+    for (int k = 0; k < d->ncomp; ++k) n += comp_slots(d->kinds[k]);
+    return n;
+}
+
+void default_opts(gf_lm_opts* o)
+{
+    o->lambda0 = 1e-3;
+    o->lambda_up = 10.0;
+    o->lambda_down = 0.1;
+    o->lambda_min = 1e-12;
+    o->lambda_max = 1e12;
+    o->ftol = 1e-6;
+    o->xtol = 1e-6;
+    o->fd_rel = 1e-3;
+    o->max_iter = 200;
+}
+
+gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* lo,
+                         const double* hi, const gf_lm_opts* opts, Structure* S)
+{
+    memset(S, 0, sizeof(*S));
+    S->ncomp = d->ncomp;
+    S->sky_slot = -1;
+    S->sky_jcol = -1;
+    int s = 0;
+    for (int k = 0; k < d->ncomp; ++k) {
+        const int kind = d->kinds[k];
+        S->kinds[k] = kind;
+        S->slot0[k] = s;
+        if (kind != GF_SKY) S->nprofile++;
+        const int ns = comp_slots(kind);
+        for (int l = 0; l < ns; ++l, ++s) {
+            int role;
+            if (kind == GF_SKY) {
+                role = R_SKY;
+                S->sky_slot = s;
+            } else if (l <= 1) {
+                role = R_POS;
+            } else if (l == 2) {
+                role = R_AMP;
+            } else if (l == 3) {
+                role = R_RAD;
+            } else if (kind == GF_SERSIC) {
+                static const int r[8] = {0, 0, 1, 2, R_N, R_Q, R_PA, R_BOXY};
+                role = r[l];
+            } else {
+                static const int r[7] = {0, 0, 1, 2, R_Q, R_PA, R_BOXY};
+                role = r[l];
+            }
+            S->role[s] = role;
+            S->owner[s] = k;
+            double l0 = -INFINITY, h0 = INFINITY;
+            switch (role) {
+            case R_AMP: l0 = 0.0; break;
+            case R_RAD: l0 = 0.1; break;
+            case R_N: l0 = 0.2; h0 = 10.0; break;
+            case R_Q: l0 = 0.05; h0 = 1.0; break;
+            case R_BOXY: l0 = -1.9; h0 = 2.0; break;
+            default: break;
+            }
+            S->lo[s] = lo ? lo[s] : l0;
+            S->hi[s] = hi ? hi[s] : h0;
+        }
+    }
+    S->nslots = s;
+    if (s > GF_MAX_SLOTS) return fail(GF_EINVAL, "too many parameter slots");
+    int nf = 0, nfd = 0;
+    for (int t = 0; t < s; ++t) {
+        if (fixed && fixed[t]) continue;
+        if (nf >= GF_MAX_FREE)
+            return fail(GF_EINVAL, "more than " + std::to_string(GF_MAX_FREE) + " free slots");
+        if (S->role[t] == R_SKY) S->sky_jcol = nf;
+        if (S->role[t] != R_AMP && S->role[t] != R_SKY) ++nfd;
+        S->freeslot[nf++] = t;
+    }
+    S->nfree = nf;
+    S->nchan = S->nprofile + nfd;
+    if (S->nchan > GF_MAX_CHAN) return fail(GF_EINVAL, "too many channels");
+    S->nacc = nf * (nf + 1) / 2 + nf + 1;
+    if (opts)
+        S->opts = *opts;
+    else
+        default_opts(&S->opts);
+    if (!(S->opts.fd_rel > 0.0)) S->opts.fd_rel = 1e-3;
+    return GF_OK;
+}
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+enum { NEED_JAC = 1, NEED_TRIAL = 2, NEED_LM = 4, NEED_CHI2 = 8 };
+
+struct Layout {
+    size_t S, st, pre, params, chan_jac, chan_trial, lm, psum, ext_jac, ext_trial, y_jac,
+        y_trial, part_jac, part_trial, active, exp, blob_end, total;
+    int count, nchan, nacc, nslots;
+    int tot_model, tot_os, tot_conv, tot_red;
+};
+
+struct Plan {
+    Layout L;
+    std::vector<StampInfo> st;
+    std::vector<int> pre;  // 4 * (count + 1): model, os, conv, red
+};
+
+// Build the stamp table, the block tables and the workspace layout.
+void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, const int* W,
+                const int64_t* pix_off, const int64_t* psf_off, int need, Plan* pl)
+{
+    const int P = d->psf_size, c = (P - 1) / 2;
+    pl->st.resize(count);
+    pl->pre.assign(4 * (count + 1), 0);
+    int* pm = pl->pre.data();
+    int* po = pm + (count + 1);
+    int* pc = po + (count + 1);
+    int* pr = pc + (count + 1);
+    long long e1 = 0, y1 = 0;
+    for (int b = 0; b < count; ++b) {
+        StampInfo& s = pl->st[b];
+        memset(&s, 0, sizeof(s));
+        s.H = H[b];
+        s.W = W[b];
+        s.P = P;
+        s.c = c;
+        s.He = s.H + 2 * c;
+        s.We = s.W + 2 * c;
+        s.os_factor = d->os_factor;
+        s.os_box = (d->os_factor > 1) ? d->os_box : 0;
+        if (s.os_box == 0) s.os_factor = 1;
+        s.os_x0 = d->os_x0 >= 0 ? d->os_x0 : (s.W - s.os_box) / 2;
+        s.os_y0 = d->os_y0 >= 0 ? d->os_y0 : (s.H - s.os_box) / 2;
+        s.nchan = S.nchan;
+        s.pix_off = pix_off ? pix_off[b] : y1;
+        s.psf_off = psf_off ? psf_off[b] : 0;
+        s.ext1_off = e1;
+        s.y1_off = y1;
+        e1 += (long long)s.He * s.We;
+        y1 += (long long)s.H * s.W;
+        const long long ne = (long long)s.He * s.We;
+        pm[b + 1] = pm[b] + (int)((ne + MODEL_THREADS - 1) / MODEL_THREADS);
+        const int nb2 = s.os_factor > 1 ? s.os_box * s.os_box : 0;
+        po[b + 1] = po[b] + (nb2 + OS_WARPS - 1) / OS_WARPS;
+        pc[b + 1] = pc[b] + ((s.H + CONV_TY - 1) / CONV_TY) * ((s.W + CONV_TX - 1) / CONV_TX);
+        pr[b + 1] = pr[b] + (int)(((long long)s.H * s.W + RED_PIX - 1) / RED_PIX);
+    }
+    Layout& L = pl->L;
+    memset(&L, 0, sizeof(L));
+    L.count = count;
+    L.nchan = S.nchan;
+    L.nacc = S.nacc;
+    L.nslots = S.nslots;
+    L.tot_model = pm[count];
+    L.tot_os = po[count];
+    L.tot_conv = pc[count];
+    L.tot_red = pr[count];
+    size_t o = 0;
+    L.S = o;
+    o += al(sizeof(Structure));
+    L.st = o;
+    o += al(sizeof(StampInfo) * count);
+    L.pre = o;
+    o += al(sizeof(int) * 4 * (count + 1));
+    L.params = o;
+    o += al(sizeof(double) * (size_t)count * S.nslots);
+    L.blob_end = o;
+    L.chan_trial = o;
+    o += al(sizeof(Channel) * (size_t)count);
+    L.psum = o;
+    o += al(sizeof(float) * (size_t)count);
+    L.active = o;
+    o += al(sizeof(int) * 4);
+    if (need & (NEED_JAC | NEED_LM)) {
+        L.chan_jac = o;
+        o += al(sizeof(Channel) * (size_t)count * S.nchan);
+        L.ext_jac = o;
+        o += al(sizeof(float) * (size_t)S.nchan * e1);
+        L.y_jac = o;
+        o += al(sizeof(float) * (size_t)S.nchan * y1);
+        L.part_jac = o;
+        o += al(sizeof(float) * (size_t)L.tot_red * S.nacc);
+    }
+    if (need & (NEED_TRIAL | NEED_LM)) {
+        L.ext_trial = o;
+        o += al(sizeof(float) * (size_t)e1);
+        L.y_trial = o;
+        o += al(sizeof(float) * (size_t)y1);
+    }
+    if (need & (NEED_TRIAL | NEED_LM | NEED_CHI2)) {
+        L.part_trial = o;
+        o += al(sizeof(float) * (size_t)L.tot_red);
+    }
+    if (need & NEED_LM) {
+        L.lm = o;
+        o += al(sizeof(LMState) * (size_t)count);
+        L.exp = o;
+        o += al(sizeof(double) * (size_t)count * (S.nslots + 5));
+    }
+    L.total = o;
+}
+
+// the host image of [0, blob_end): Structure, stamp table, block tables, params
+std::vector<uint8_t> make_blob(const Plan& pl, const Structure& S, const double* params)
+{
+    const Layout& L = pl.L;
+    std::vector<uint8_t> blob(L.blob_end, 0);
+    memcpy(blob.data() + L.S, &S, sizeof(S));
+    memcpy(blob.data() + L.st, pl.st.data(), sizeof(StampInfo) * L.count);
+    memcpy(blob.data() + L.pre, pl.pre.data(), sizeof(int) * pl.pre.size());
+    if (params) memcpy(blob.data() + L.params, params, sizeof(double) * (size_t)L.count * S.nslots);
+    return blob;
+}
+
+template <class T>
+T* at(void* ws, size_t off)
+{
+    return reinterpret_cast<T*>(static_cast<uint8_t*>(ws) + off);
+}
+
+PassArgs base_args(void* ws, const Layout& L, const float* psf, const float* img,
+                   const float* sig, int P)
+{
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.count = L.count;
+    a.st = at<StampInfo>(ws, L.st);
+    a.S = at<Structure>(ws, L.S);
+    const int* pre = at<int>(ws, L.pre);
+    a.pre_model = pre;
+    a.pre_os = pre + (L.count + 1);
+    a.pre_conv = pre + 2 * (L.count + 1);
+    a.pre_red = pre + 3 * (L.count + 1);
+    a.tot_model = L.tot_model;
+    a.tot_os = L.tot_os;
+    a.tot_conv = L.tot_conv;
+    a.tot_red = L.tot_red;
+    a.psf = psf;
+    a.psf_sum = at<float>(ws, L.psum);
+    a.img = img;
+    a.sig = sig;
+    a.P = P;
+    a.phase = PH_NONE;
+    a.work = prof::work_dev;
+    return a;
+}
+
+PassArgs jac_args(void* ws, const Layout& L, const PassArgs& base)
+{
+    PassArgs a = base;
+    a.chan = at<Channel>(ws, L.chan_jac);
+    a.chan_stride = L.nchan;
+    a.nchan = L.nchan;
+    a.ext = at<float>(ws, L.ext_jac);
+    a.y = at<float>(ws, L.y_jac);
+    a.partial = at<float>(ws, L.part_jac);
+    a.nacc = L.nacc;
+    return a;
+}
+
+PassArgs trial_args(void* ws, const Layout& L, const PassArgs& base)
+{
+    PassArgs a = base;
+    a.chan = at<Channel>(ws, L.chan_trial);
+    a.chan_stride = 1;
+    a.nchan = 1;
+    a.ext = at<float>(ws, L.ext_trial);
+    a.y = at<float>(ws, L.y_trial);
+    a.partial = at<float>(ws, L.part_trial);
+    a.nacc = 1;
+    return a;
+}
+
+gf_status check_ws(void* ws, size_t bytes, size_t need)
+{
+    if (!ws) return fail(GF_EINVAL, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0)
+        return fail(GF_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < need)
+        return fail(GF_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
+    return GF_OK;
+}
+
+gf_status upload(void* ws, const std::vector<uint8_t>& blob, cudaStream_t s)
+{
+    GF_CUDA(cudaMemcpyAsync(ws, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
+    return GF_OK;
+}
+
+gf_status run_conv(const PassArgs& a, int method, cudaStream_t s)
+{
+    ProfScope ps(PROF_CONV, s);
+    if (method == GF_CONV_DIRECT) {
+        GF_CUDA(launch_conv_direct(a, s));
+        return GF_OK;
+    }
+    return fail(GF_EINVAL, "FFT convolution is not available in this build");
+}
+
+gf_status jac_pass(const PassArgs& a, int method, const double* params, double* A, double* g,
+                   double* x2, cudaStream_t s)
+{
+    {
+        ProfScope ps(PROF_LM, s);
+        GF_CUDA(launch_prep_jac(a, params, s));
+    }
+    {
+        ProfScope ps(PROF_MODEL, s);
+        GF_CUDA(launch_model(a, s));
+    }
+    gf_status r = run_conv(a, method, s);
+    if (r != GF_OK) return r;
+    ProfScope ps(PROF_REDUCE, s);
+    GF_CUDA(launch_reduce_jac(a, s));
+    GF_CUDA(launch_final_jac(a, A, g, x2, s));
+    return GF_OK;
+}
+
+gf_status trial_pass(const PassArgs& a, int method, cudaStream_t s, double* x2)
+{
+    {
+        ProfScope ps(PROF_MODEL, s);
+        GF_CUDA(launch_model(a, s));
+    }
+    gf_status r = run_conv(a, method, s);
+    if (r != GF_OK) return r;
+    ProfScope ps(PROF_REDUCE, s);
+    GF_CUDA(launch_reduce_chi2(a, s));
+    GF_CUDA(launch_final_chi2(a, x2, s));
+    return GF_OK;
+}
+
+}  // namespace
+
+// ================================================================ the C ABI
+
+extern "C" {
+
+int gf_version(void) { return 100; }
+
+long long gf_launch_count(void) { return g_launch_count.load(); }
+
+void gf_prof_enable(unsigned long long* work_dev)
+{
+    std::lock_guard<std::mutex> g(prof::mu);
+    prof::work_dev = work_dev;
+}
+
+int gf_prof_times(double* ms_out, long long* launches_out)
+{
+    std::lock_guard<std::mutex> g(prof::mu);
+    int st = GF_OK;
+    for (auto& r : prof::pending) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(r.e1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+            prof::ms[r.cls] += ms;
+            prof::launches[r.cls] += r.launches;
+        } else {
+            st = GF_ECUDA;
+        }
+        prof::pool.push_back(r.e0);
+        prof::pool.push_back(r.e1);
+    }
+    prof::pending.clear();
+    for (int c = 0; c < PROF_CLASSES; ++c) {
+        if (ms_out) ms_out[c] = prof::ms[c];
+        if (launches_out) launches_out[c] = prof::launches[c];
+        prof::ms[c] = 0.0;
+        prof::launches[c] = 0;
+    }
+    return st;
+}
+
+const char* gf_last_error(void) { return g_err.c_str(); }
+
+int gf_nslots(const gf_desc* d)
+{
+    if (check_structure(d) != GF_OK) return -1;
+    return nslots_of(d);
+}
+
+void gf_default_opts(gf_lm_opts* opts)
+{
+    if (opts) default_opts(opts);
+}
+
+static int need_of(int call)
+{
+    switch (call) {
+    case GF_CALL_CHI2: return NEED_CHI2;
+    case GF_CALL_EVAL: return NEED_TRIAL;
+    case GF_CALL_JACOBIAN: return NEED_JAC;
+    case GF_CALL_LM_FIT: return NEED_LM;
+    default: return 0;
+    }
+}
+
+size_t gf_workspace_size(const gf_desc* d, const uint8_t* fixed, int call)
+{
+    if (check_structure(d) != GF_OK || check_stamp(d, d->H, d->W) != GF_OK) return 0;
+    Structure S;
+    if (make_structure(d, fixed, nullptr, nullptr, nullptr, &S) != GF_OK) return 0;
+    Plan pl;
+    plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, need_of(call), &pl);
+    return pl.L.total;
+}
+
+size_t gf_workspace_size_batch(const gf_desc* d, const gf_batch* b, const uint8_t* fixed)
+{
+    if (!b || b->count < 1 || !b->H || !b->W) return 0;
+    if (check_structure(d) != GF_OK) return 0;
+    for (int i = 0; i < b->count; ++i)
+        if (check_stamp(d, b->H[i], b->W[i]) != GF_OK) return 0;
+    Structure S;
+    if (make_structure(d, fixed, nullptr, nullptr, nullptr, &S) != GF_OK) return 0;
+    Plan pl;
+    plan_batch(d, S, b->count, b->H, b->W, b->pix_off, b->psf_off, NEED_LM, &pl);
+    return pl.L.total;
+}
+
+gf_status gf_model(const gf_desc* d, const double* params, float* out, void* ws, size_t ws_bytes,
+                   gf_stream stream)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    if ((r = check_stamp(d, d->H, d->W)) != GF_OK) return r;
+    if (!params || !out) return fail(GF_EINVAL, "params or output is NULL");
+    Structure S;
+    if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, &S)) != GF_OK) return r;
+    Plan pl;
+    plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, 0, &pl);
+    if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
+    PassArgs a = base_args(ws, pl.L, nullptr, nullptr, nullptr, d->psf_size);
+    a.chan = at<Channel>(ws, pl.L.chan_trial);
+    a.chan_stride = 1;
+    a.nchan = 1;
+    a.ext = out;
+    GF_CUDA(launch_prep_sum(a, at<double>(ws, pl.L.params), 0, s));
+    GF_CUDA(launch_model(a, s));
+    return GF_OK;
+}
+
+gf_status gf_convolve(const gf_desc* d, const float* ext, const float* psf, float* out, void* ws,
+                      size_t ws_bytes, gf_stream stream)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    if ((r = check_stamp(d, d->H, d->W)) != GF_OK) return r;
+    if (!ext || !psf || !out) return fail(GF_EINVAL, "NULL buffer");
+    Structure S;
+    if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, &S)) != GF_OK) return r;
+    Plan pl;
+    plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, 0, &pl);
+    if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = upload(ws, make_blob(pl, S, nullptr), s)) != GF_OK) return r;
+    PassArgs a = base_args(ws, pl.L, psf, nullptr, nullptr, d->psf_size);
+    a.nchan = 1;
+    a.chan_stride = 1;
+    a.ext = const_cast<float*>(ext);
+    a.y = out;
+    return run_conv(a, resolve_method(d), s);
+}
+
+gf_status gf_chi2(const gf_desc* d, const float* model, const float* img, const float* sig,
+                  double* chi2, void* ws, size_t ws_bytes, gf_stream stream)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    if ((r = check_stamp(d, d->H, d->W)) != GF_OK) return r;
+    if (!model || !img || !sig || !chi2) return fail(GF_EINVAL, "NULL buffer");
+    Structure S;
+    if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, &S)) != GF_OK) return r;
+    Plan pl;
+    plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, NEED_CHI2, &pl);
+    if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the given model as one channel of weight 1
+    std::vector<uint8_t> blob = make_blob(pl, S, nullptr);
+    if ((r = upload(ws, blob, s)) != GF_OK) return r;
+    Channel ch;
+    memset(&ch, 0, sizeof(ch));
+    ch.type = CH_SUM;
+    ch.jcol = -1;
+    ch.mweight = 1.0f;
+    GF_CUDA(cudaMemcpyAsync(at<Channel>(ws, pl.L.chan_trial), &ch, sizeof(ch),
+                            cudaMemcpyHostToDevice, s));
+    PassArgs a = base_args(ws, pl.L, nullptr, img, sig, d->psf_size);
+    a.chan = at<Channel>(ws, pl.L.chan_trial);
+    a.chan_stride = 1;
+    a.nchan = 1;
+    a.y = const_cast<float*>(model);
+    a.partial = at<float>(ws, pl.L.part_trial);
+    GF_CUDA(launch_reduce_chi2(a, s));
+    GF_CUDA(launch_final_chi2(a, chi2, s));
+    return GF_OK;
+}
+
+gf_status gf_eval(const gf_desc* d, const double* params, const float* img, const float* sig,
+                  const float* psf, float* model_out, double* chi2, void* ws, size_t ws_bytes,
+                  gf_stream stream)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    if ((r = check_stamp(d, d->H, d->W)) != GF_OK) return r;
+    if (!params || !img || !sig || !psf || !chi2) return fail(GF_EINVAL, "NULL argument");
+    Structure S;
+    if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, &S)) != GF_OK) return r;
+    Plan pl;
+    plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, NEED_TRIAL, &pl);
+    if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
+    PassArgs a = trial_args(ws, pl.L, base_args(ws, pl.L, psf, img, sig, d->psf_size));
+    a.m_out = model_out;
+    GF_CUDA(launch_prep_sum(a, at<double>(ws, pl.L.params), 0, s));
+    return trial_pass(a, resolve_method(d), s, chi2);
+}
+
+gf_status gf_jacobian(const gf_desc* d, const double* params, const uint8_t* fixed, double fd_rel,
+                      const float* img, const float* sig, const float* psf, float* J_out,
+                      double* A, double* g, double* chi2, void* ws, size_t ws_bytes,
+                      gf_stream stream)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    if ((r = check_stamp(d, d->H, d->W)) != GF_OK) return r;
+    if (!params || !img || !sig || !psf || !A || !g || !chi2)
+        return fail(GF_EINVAL, "NULL argument");
+    gf_lm_opts o;
+    default_opts(&o);
+    if (fd_rel > 0.0) o.fd_rel = fd_rel;
+    Structure S;
+    if ((r = make_structure(d, fixed, nullptr, nullptr, &o, &S)) != GF_OK) return r;
+    if (S.nfree < 1) return fail(GF_EINVAL, "no free slots");
+    Plan pl;
+    plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, NEED_JAC, &pl);
+    if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
+    PassArgs a = jac_args(ws, pl.L, base_args(ws, pl.L, psf, img, sig, d->psf_size));
+    a.J_out = J_out;
+    GF_CUDA(launch_psf_sum(1, a.st, psf, const_cast<float*>(a.psf_sum), s));
+    return jac_pass(a, resolve_method(d), at<double>(ws, pl.L.params), A, g, chi2, s);
+}
+
+static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params,
+                             const uint8_t* fixed, const double* lo, const double* hi,
+                             const float* img, const float* sig, const float* psf,
+                             const gf_lm_opts* opts, gf_lm_result* res, void* ws, size_t ws_bytes,
+                             gf_stream stream)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    if (!b || b->count < 1 || !b->H || !b->W) return fail(GF_EINVAL, "bad batch");
+    for (int i = 0; i < b->count; ++i)
+        if ((r = check_stamp(d, b->H[i], b->W[i])) != GF_OK) return r;
+    if (!params || !img || !sig || !psf || !res) return fail(GF_EINVAL, "NULL argument");
+    if (opts && !(opts->max_iter >= 1 && opts->lambda_up > 1.0 && opts->lambda_down > 0.0 &&
+                  opts->lambda_down < 1.0 && opts->lambda0 > 0.0))
+        return fail(GF_EINVAL, "bad LM options");
+    Structure S;
+    if ((r = make_structure(d, fixed, lo, hi, opts, &S)) != GF_OK) return r;
+    if (S.nfree < 1) return fail(GF_EINVAL, "no free slots");
+    Plan pl;
+    plan_batch(d, S, b->count, b->H, b->W, b->pix_off, b->psf_off, NEED_LM, &pl);
+    if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Layout& L = pl.L;
+    if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
+    const int method = resolve_method(d);
+    PassArgs base = base_args(ws, L, psf, img, sig, d->psf_size);
+    LMState* lm = at<LMState>(ws, L.lm);
+    PassArgs aj = jac_args(ws, L, base);
+    aj.lm = lm;
+    aj.phase = PH_NEED_JAC;
+    PassArgs at_ = trial_args(ws, L, base);
+    at_.lm = lm;
+    at_.phase = PH_TRIAL;
+    int* active = at<int>(ws, L.active);
+    GF_CUDA(launch_psf_sum(L.count, base.st, psf, const_cast<float*>(base.psf_sum), s));
+    GF_CUDA(launch_lm_init(L.count, base.S, lm, at<double>(ws, L.params), s));
+    const int max_bodies = S.opts.max_iter + 2;
+    int bodies = 0;
+    for (;;) {
+        const int K = bodies < 8 ? 2 : 4;
+        for (int k = 0; k < K && bodies < max_bodies; ++k, ++bodies) {
+            if ((r = jac_pass(aj, method, nullptr, nullptr, nullptr, nullptr, s)) != GF_OK)
+                return r;
+            {
+                ProfScope ps(PROF_LM, s);
+                GF_CUDA(launch_lm_solve(aj, at<Channel>(ws, L.chan_trial), s));
+            }
+            if ((r = trial_pass(at_, method, s, nullptr)) != GF_OK) return r;
+            ProfScope ps(PROF_LM, s);
+            GF_CUDA(cudaMemsetAsync(active, 0, sizeof(int), s));
+            GF_CUDA(launch_lm_update(at_, active, s));
+        }
+        int h_active = 0;
+        GF_CUDA(cudaMemcpyAsync(&h_active, active, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GF_CUDA(cudaStreamSynchronize(s));
+        if (h_active == 0 || bodies >= max_bodies) break;
+    }
+    double* ex = at<double>(ws, L.exp);
+    GF_CUDA(launch_lm_export(L.count, base.S, lm, ex, s));
+    const int stride = S.nslots + 5;
+    std::vector<double> hx((size_t)L.count * stride);
+    GF_CUDA(cudaMemcpyAsync(hx.data(), ex, sizeof(double) * hx.size(), cudaMemcpyDeviceToHost, s));
+    GF_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < L.count; ++i) {
+        const double* o = hx.data() + (size_t)i * stride;
+        memcpy(params + (size_t)i * S.nslots, o, sizeof(double) * S.nslots);
+        res[i].chi2 = o[S.nslots];
+        res[i].lambda = o[S.nslots + 1];
+        res[i].iters = (int)o[S.nslots + 2];
+        res[i].accepted = (int)o[S.nslots + 3];
+        res[i].status = (int)o[S.nslots + 4];
+    }
+    return GF_OK;
+}
+
+gf_status gf_lm_fit_batch(const gf_desc* d, const gf_batch* b, double* params,
+                          const uint8_t* fixed, const float* img, const float* sig,
+                          const float* psf, const gf_lm_opts* opts, gf_lm_result* res, void* ws,
+                          size_t ws_bytes, gf_stream stream)
+{
+    return lm_fit_impl(d, b, params, fixed, nullptr, nullptr, img, sig, psf, opts, res, ws,
+                       ws_bytes, stream);
+}
+
+gf_status gf_lm_fit(const gf_desc* d, double* params, const uint8_t* fixed, const double* lo,
+                    const double* hi, const float* img, const float* sig, const float* psf,
+                    const gf_lm_opts* opts, gf_lm_result* res, void* ws, size_t ws_bytes,
+                    gf_stream stream)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    int H = d->H, W = d->W;
+    int64_t zero = 0;
+    gf_batch b;
+    b.count = 1;
+    b.H = &H;
+    b.W = &W;
+    b.pix_off = &zero;
+    b.psf_off = &zero;
+    return lm_fit_impl(d, &b, params, fixed, lo, hi, img, sig, psf, opts, res, ws, ws_bytes,
+                       stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// conv_direct.cu -- step 2 of the fitting loop (Sec. 2 item 2) as a tiled
+// direct sum, for PSFs up to GF_DIRECT_MAX_PSF pixels on a side.
+//
+//   out(i, j) = sum_{v,u} psf[v][u] * E[i+2c-v][j+2c-u]
+//             = sum_{v,u} k[v][u]   * E[i+v][j+u],   k[v][u] = psf[P-1-v][P-1-u]
+//
+// One CTA (4 warps) computes a 32 x 64 output tile of one channel.  The flipped
+// PSF (rows padded with zeros to a multiple of 4 taps) and the (32+P-1) x
+// (64+P4) halo tile of the channel grid are staged in shared memory.  A warp
+// covers 16 x 32 outputs with lanes arranged 4 (rows) x 8 (columns); a thread
+// owns a 4 x 4 block.  For each tap row v and each group of 4 taps, a thread
+// issues one broadcast 16-byte load of the taps and one 16-byte load of the
+// next 4 grid values per output row, then 64 FMAs: 5 shared loads per 64 FMAs.
+// Eight lanes of a quarter-warp read 128 contiguous bytes, so the grid loads
+// are free of bank conflicts; the tap loads are broadcasts.
+//
+// The work is bound by the FP32 FMA pipe (2 P^2 flop per output pixel against
+// 8 bytes of HBM traffic), not by HBM.
+#include "gf_internal.cuh"
+
+namespace {
+
+constexpr int TY = CONV_TY, TX = CONV_TX, NT = 128;
+
+__global__ void __launch_bounds__(NT) k_conv_direct(PassArgs a)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int blk = blockIdx.x;
+    const int b = find_stamp(a.pre_conv, a.count, blk);
+    if (a.lm && a.lm[b].phase != a.phase) return;
+    const int ch = blockIdx.y;
+    const StampInfo st = a.st[b];
+    const int P = st.P, P4 = (P + 3) & ~3;
+    const int SW = TX + P4, SH = TY + P - 1;
+    const int tiles_x = (st.W + TX - 1) / TX;
+    const int t = blk - a.pre_conv[b];
+    const int ty0 = (t / tiles_x) * TY, tx0 = (t % tiles_x) * TX;
+
+    float* ks = smem;               // P x P4 flipped taps
+    float* es = smem + P * P4;      // SH x SW grid tile (P*P4 is a multiple of 4)
+    const float* psf = a.psf + st.psf_off;
+    for (int idx = threadIdx.x; idx < P * P4; idx += NT) {
+        const int v = idx / P4, u = idx - v * P4;
+        ks[idx] = (u < P) ? __ldg(&psf[(P - 1 - v) * P + (P - 1 - u)]) : 0.0f;
+    }
+    const float* E = a.ext + ext_index(st, a.nchan, ch);
+    for (int idx = threadIdx.x; idx < SH * SW; idx += NT) {
+        const int r = idx / SW, col = idx - r * SW;
+        const int gy = ty0 + r, gx = tx0 + col;
+        es[idx] = (gy < st.He && gx < st.We) ? __ldg(&E[(long long)gy * st.We + gx]) : 0.0f;
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = (warp >> 1) * 16 + (lane >> 3) * 4;
+    const int c0 = (warp & 1) * 32 + (lane & 7) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) acc[r][o] = 0.0f;
+
+    for (int v = 0; v < P; ++v) {
+        const float* kr = ks + v * P4;
+        const float* er = es + (r0 + v) * SW + c0;
+        float4 w0[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) w0[r] = *reinterpret_cast<const float4*>(er + r * SW);
+#pragma unroll 2
+        for (int m = 0; m < P4; m += 4) {
+            const float4 kk = *reinterpret_cast<const float4*>(kr + m);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float4 w1 = *reinterpret_cast<const float4*>(er + r * SW + m + 4);
+                const float win[8] = {w0[r].x, w0[r].y, w0[r].z, w0[r].w,
+                                      w1.x,    w1.y,    w1.z,    w1.w};
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    float x = acc[r][o];
+                    x = fmaf(kk.x, win[o], x);
+                    x = fmaf(kk.y, win[o + 1], x);
+                    x = fmaf(kk.z, win[o + 2], x);
+                    x = fmaf(kk.w, win[o + 3], x);
+                    acc[r][o] = x;
+                }
+                w0[r] = w1;
+            }
+        }
+    }
+
+    if (a.work && threadIdx.x == 0) {
+        const unsigned long long rows = (unsigned long long)min(TY, st.H - ty0);
+        const unsigned long long cols = (unsigned long long)min(TX, st.W - tx0);
+        atomicAdd(&a.work[PROF_CONV], 2ull * (unsigned long long)P * P * rows * cols);
+    }
+    float* Y = a.y + y_index(st, a.nchan, ch);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int oy = ty0 + r0 + r;
+        if (oy >= st.H) continue;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const int ox = tx0 + c0 + o;
+            if (ox < st.W) Y[(long long)oy * st.W + ox] = acc[r][o];
+        }
+    }
+}
+
+}  // namespace
+
+size_t conv_direct_smem(int P)
+{
+    const int P4 = (P + 3) & ~3;
+    return sizeof(float) * ((size_t)P * P4 + (size_t)(TY + P - 1) * (TX + P4));
+}
+
+cudaError_t launch_conv_direct(const PassArgs& a, cudaStream_t s)
+{
+    if (a.tot_conv <= 0) return cudaSuccess;
+    static int optin[64];
+    const size_t sm = conv_direct_smem(a.P);
+    cudaError_t e = ensure_smem_optin((const void*)k_conv_direct, (int)sm, optin);
+    if (e != cudaSuccess) return e;
+    k_conv_direct<<<dim3(a.tot_conv, a.nchan), NT, sm, s>>>(a);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}

@@ -1,0 +1,259 @@
+// gf_internal.cuh -- device-side data structures and the per-pixel profile
+// evaluation shared by the kernels of libgf.so.
+//
+// Layout of the work: a call processes a batch of stamps (a single-stamp call is
+// a batch of one).  Each stamp carries up to GF_MAX_CHAN "channels": an image on
+// the halo-extended grid that the convolution turns into one column of the
+// Jacobian or into the model.  Channel kinds:
+//   CH_SUM    sky + all components at one parameter vector (the model, step 1)
+//   CH_SHAPE  component k with unit amplitude (exact amplitude column)
+//   CH_FD     amp_k (S_k(p + h e_s) - S_k(p)) / h for a nonlinear slot s
+// Convolved channels are combined per pixel into the model
+//   m = sum_ch mweight_ch * Y_ch + sky_const
+// and the Jacobian columns; chi^2 and J^T W J, J^T W r are reduced from there.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/gf.h"
+
+#define GF_MAX_CHAN 24
+#define GF_NACC_MAX (GF_MAX_FREE * (GF_MAX_FREE + 1) / 2 + GF_MAX_FREE + 1)
+
+enum { CH_SUM = 0, CH_SHAPE = 1, CH_FD = 2 };
+
+// LM phases of a stamp
+enum { PH_NEED_JAC = 0, PH_SOLVE = 1, PH_TRIAL = 2, PH_DONE = 3, PH_NONE = 99 };
+
+// slot roles
+enum { R_POS = 0, R_AMP = 1, R_RAD = 2, R_N = 3, R_Q = 4, R_PA = 5, R_BOXY = 6, R_SKY = 7 };
+
+// Float32 constants of one component at one parameter vector.
+struct CompConst {
+    float x0h, x0l, y0h, y0l;  // centre split hi + lo so that x - x0 keeps ~48 bits
+    float cs, sn, invq;        // rotation and axis ratio
+    float C, invC;             // generalised-radius exponent C = c + 2
+    float amp;                 // amplitude (1 for unit shapes)
+    float invr;                // 1 / r_e or 1 / r_s
+    float invn;                // 1 / n (1 for the disk)
+    float b0, b;               // I = amp * exp(b0 - b * (r invr)^invn)
+    int kind;                  // GF_SERSIC / GF_EXPDISK / GF_SKY
+    int ellipse;               // C == 2 exactly: r by sqrt
+};
+
+struct Channel {
+    int type;       // CH_*
+    int comp;       // component index (CH_SHAPE, CH_FD)
+    int jcol;       // Jacobian column or -1
+    float mweight;  // weight of the convolved channel in the model
+    float scale;    // CH_FD: amp / h_eff
+    float sky;      // CH_SUM: sky level added on the grid
+    int ncomp;
+    float msky;     // channel 0 of a pass: constant added to the convolved model
+    CompConst cc[GF_MAX_COMP];  // all components at the channel's parameter vector
+    CompConst pert;             // CH_FD: component `comp` at p + h e_s (unit amplitude)
+};
+
+// Static description of one stamp inside a call.
+struct StampInfo {
+    int H, W, P, c;
+    int He, We;
+    int os_factor, os_box, os_x0, os_y0;  // block origin resolved
+    int nchan;                             // channels of the Jacobian pass
+    int pad;
+    long long pix_off;   // into image / sigma / model (H*W elements)
+    long long psf_off;   // into the PSF array (P*P)
+    long long ext1_off;  // sum of He*We over the earlier stamps
+    long long y1_off;    // sum of H*W over the earlier stamps
+};
+
+// channel k of stamp b in a pass of nchan channels per stamp
+__host__ __device__ __forceinline__ long long ext_index(const StampInfo& st, int nchan, int k)
+{
+    return (long long)nchan * st.ext1_off + (long long)k * st.He * st.We;
+}
+__host__ __device__ __forceinline__ long long y_index(const StampInfo& st, int nchan, int k)
+{
+    return (long long)nchan * st.y1_off + (long long)k * st.H * st.W;
+}
+
+// Structure shared by all stamps of a call (kinds, free slots, bounds, options).
+struct Structure {
+    int ncomp, nslots, nfree, nprofile;
+    int kinds[GF_MAX_COMP];
+    int slot0[GF_MAX_COMP];         // first slot of each component
+    int freeslot[GF_MAX_FREE];      // slot index of each free parameter
+    int role[GF_MAX_SLOTS];         // R_* per slot
+    int owner[GF_MAX_SLOTS];        // component per slot
+    int sky_slot;                   // -1 if no sky component
+    int sky_jcol;                   // Jacobian column of the sky, -1 if held
+    int nchan;                      // Jacobian-pass channels per stamp
+    int nacc;                       // accumulators of the Jacobian reduction
+    double lo[GF_MAX_SLOTS], hi[GF_MAX_SLOTS];
+    gf_lm_opts opts;
+};
+
+// Per-stamp LM state, resident on the device for the whole fit.
+struct LMState {
+    double p[GF_MAX_SLOTS];
+    double pt[GF_MAX_SLOTS];
+    double A[GF_MAX_FREE * GF_MAX_FREE];
+    double g[GF_MAX_FREE];
+    double chi2, chi2t, lambda, psum;
+    int iters, accepted, status, phase;
+};
+
+// ------------------------------------------------------------ device helpers
+
+__device__ __forceinline__ float comp_eval(const CompConst& k, float xi, float yi, float ox,
+                                           float oy)
+{
+    // dx = x - x0 with x = xi + ox: the integer part against the hi word is exact
+    // near the centre (Sterbenz), the sub-pixel offset absorbs the lo word.
+    float dx = (xi - k.x0h) + (ox - k.x0l);
+    float dy = (yi - k.y0h) + (oy - k.y0l);
+    float xp = fmaf(dx, k.cs, dy * k.sn);
+    float yp = fmaf(dy, k.cs, -dx * k.sn) * k.invq;
+    float r;
+    if (k.ellipse) {
+        r = sqrtf(fmaf(xp, xp, yp * yp));
+    } else {
+        float ax = exp2f(k.C * log2f(fabsf(xp)));
+        float ay = exp2f(k.C * log2f(fabsf(yp)));
+        r = exp2f(k.invC * log2f(ax + ay));
+    }
+    float t = r * k.invr;
+    float u = (k.invn == 1.0f) ? t : exp2f(k.invn * log2f(t));
+    return k.amp * expf(fmaf(-k.b, u, k.b0));
+}
+
+// value of a channel at grid point (xi + ox, yi + oy)
+__device__ __forceinline__ float channel_value(const Channel& ch, float xi, float yi, float ox,
+                                               float oy)
+{
+    if (ch.type == CH_SUM) {
+        float v = ch.sky;
+        for (int k = 0; k < ch.ncomp; ++k)
+            if (ch.cc[k].kind != GF_SKY) v += comp_eval(ch.cc[k], xi, yi, ox, oy);
+        return v;
+    }
+    if (ch.type == CH_SHAPE) return comp_eval(ch.cc[ch.comp], xi, yi, ox, oy);
+    float a = comp_eval(ch.pert, xi, yi, ox, oy);
+    float b = comp_eval(ch.cc[ch.comp], xi, yi, ox, oy);
+    return (a - b) * ch.scale;
+}
+
+// Neumaier compensated accumulation in float32
+struct CSum {
+    float s, c;
+};
+__device__ __forceinline__ void csum_add(CSum& a, float t)
+{
+    float s = a.s + t;
+    if (fabsf(a.s) >= fabsf(t))
+        a.c += (a.s - s) + t;
+    else
+        a.c += (t - s) + a.s;
+    a.s = s;
+}
+// merge two compensated sums (error-free TwoSum of the heads)
+__device__ __forceinline__ CSum csum_merge(CSum a, CSum b)
+{
+    float s = a.s + b.s;
+    float bb = s - a.s;
+    float err = (a.s - (s - bb)) + (b.s - bb);
+    CSum r;
+    r.s = s;
+    r.c = a.c + b.c + err;
+    return r;
+}
+
+// stamp index of a block from an exclusive prefix table (upper_bound - 1)
+__device__ __forceinline__ int find_stamp(const int* prefix, int count, int blk)
+{
+    int lo = 0, hi = count;  // prefix[lo] <= blk < prefix[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= blk)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------- host-side launch
+// Arguments of the kernel passes; each .cu file implements its own launcher.
+
+struct PassArgs {
+    int count;                 // stamps
+    const StampInfo* st;       // [count]
+    const Structure* S;        // one
+    LMState* lm;               // [count] or null (no phase filtering)
+    int phase;                 // process stamps whose lm->phase == phase (if lm)
+    const Channel* chan;       // [count * chan_stride]
+    int chan_stride;           // channels reserved per stamp
+    int nchan;                 // channels processed per stamp in this pass
+    float* ext;                // channel grids: ext + ext_index(st[b], nchan, k)
+    float* y;                  // convolved channels: y + y_index(st[b], nchan, k)
+    const float* psf;
+    const float* psf_sum;      // [count] sum of each PSF (float)
+    const float* img;
+    const float* sig;
+    float* partial;            // reduction partials
+    int nacc;                  // accumulators per reduce block
+    float* J_out;              // optional Jacobian output (nfree x H x W per stamp, packed)
+    float* m_out;              // optional model output (H x W per stamp, packed at pix_off)
+    // block tables (exclusive prefixes, [count + 1])
+    const int* pre_model;
+    const int* pre_os;
+    const int* pre_conv;
+    const int* pre_red;
+    int tot_model, tot_os, tot_conv, tot_red;
+    int P;                     // PSF side (uniform across the stamps of a call)
+    unsigned long long* work;  // profiling: algorithmic work per kernel class, or null
+};
+
+enum { PROF_MODEL = 0, PROF_CONV = 1, PROF_REDUCE = 2, PROF_LM = 3, PROF_CLASSES = 4 };
+
+// per-device one-time opt-in to large dynamic shared memory for a kernel
+cudaError_t ensure_smem_optin(const void* func, int bytes, int* cache_per_device);
+
+// every kernel launch of the library increments this counter
+extern std::atomic<long long> g_launch_count;
+#define GF_COUNT_LAUNCH() g_launch_count.fetch_add(1, std::memory_order_relaxed)
+
+// kernel launchers (return cudaGetLastError())
+cudaError_t launch_model(const PassArgs& a, cudaStream_t s);
+cudaError_t launch_conv_direct(const PassArgs& a, cudaStream_t s);
+cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s);
+cudaError_t launch_reduce_chi2(const PassArgs& a, cudaStream_t s);
+cudaError_t launch_final_jac(const PassArgs& a, double* A_out, double* g_out, double* chi2_out,
+                             cudaStream_t s);
+cudaError_t launch_final_chi2(const PassArgs& a, double* chi2_out, cudaStream_t s);
+cudaError_t launch_psf_sum(int count, const StampInfo* st, const float* psf, float* out,
+                           cudaStream_t s);
+
+// parameter / channel preparation and the LM steps (lm.cu)
+cudaError_t launch_prep_sum(const PassArgs& a, const double* params, int use_trial,
+                            cudaStream_t s);
+cudaError_t launch_prep_jac(const PassArgs& a, const double* params, cudaStream_t s);
+cudaError_t launch_lm_init(int count, const Structure* S, LMState* lm, const double* p0,
+                           cudaStream_t s);
+cudaError_t launch_lm_solve(const PassArgs& a, Channel* trial_chan, cudaStream_t s);
+cudaError_t launch_lm_update(const PassArgs& a, int* active_count, cudaStream_t s);
+cudaError_t launch_lm_export(int count, const Structure* S, const LMState* lm, double* out,
+                             cudaStream_t s);
+
+// conv tile shape of the direct kernel
+#define CONV_TY 32
+#define CONV_TX 64
+// pixels per block of the reductions
+#define RED_THREADS 256
+#define RED_CHUNKS 4
+#define RED_PIX (RED_THREADS * RED_CHUNKS)
+#define MODEL_THREADS 256
+#define OS_WARPS 8

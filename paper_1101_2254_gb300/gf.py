@@ -1,0 +1,365 @@
+"""Thin Python binding of libgf.so (the C ABI in include/gf.h).
+
+Argument marshalling only: every step of the fitting loop runs in the CUDA
+kernels behind the C ABI.  PyTorch supplies device memory (tensors, the
+workspace) and the CUDA stream.  There is no fallback: if the library is
+missing or fails to load, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgf.so")
+
+SERSIC, EXPDISK, SKY = 1, 2, 3
+NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1}
+CONV_AUTO, CONV_DIRECT, CONV_FFT = 0, 1, 2
+CALL_MODEL, CALL_CONVOLVE, CALL_CHI2, CALL_EVAL, CALL_JACOBIAN, CALL_LM_FIT = range(6)
+OK, EINVAL, ECUDA, ENOCONV, ESINGULAR, ENONFINITE, ETIMEOUT, ENOMEM, EMAXITER = range(9)
+MAX_COMP = 8
+
+
+class GFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"gf status {status}: {msg}")
+        self.status = status
+
+
+class Desc(C.Structure):
+    _fields_ = [("H", C.c_int), ("W", C.c_int), ("psf_size", C.c_int), ("ncomp", C.c_int),
+                ("kinds", C.c_int * MAX_COMP), ("os_factor", C.c_int), ("os_box", C.c_int),
+                ("os_x0", C.c_int), ("os_y0", C.c_int), ("conv_method", C.c_int)]
+
+
+class LMOpts(C.Structure):
+    _fields_ = [("lambda0", C.c_double), ("lambda_up", C.c_double),
+                ("lambda_down", C.c_double), ("lambda_min", C.c_double),
+                ("lambda_max", C.c_double), ("ftol", C.c_double), ("xtol", C.c_double),
+                ("fd_rel", C.c_double), ("max_iter", C.c_int)]
+
+
+class LMResult(C.Structure):
+    _fields_ = [("chi2", C.c_double), ("lam", C.c_double), ("iters", C.c_int),
+                ("accepted", C.c_int), ("status", C.c_int)]
+
+
+class Batch(C.Structure):
+    _fields_ = [("count", C.c_int), ("H", C.POINTER(C.c_int)), ("W", C.POINTER(C.c_int)),
+                ("pix_off", C.POINTER(C.c_int64)), ("psf_off", C.POINTER(C.c_int64))]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libgf.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_1101_2254_gb300.build`")
+            L = C.CDLL(LIB_PATH)
+            vp, dp, fp = C.c_void_p, C.POINTER(C.c_double), C.c_void_p
+            pd = C.POINTER(Desc)
+            L.gf_version.restype = C.c_int
+            L.gf_last_error.restype = C.c_char_p
+            L.gf_nslots.restype = C.c_int
+            L.gf_nslots.argtypes = [pd]
+            L.gf_workspace_size.restype = C.c_size_t
+            L.gf_workspace_size.argtypes = [pd, C.c_char_p, C.c_int]
+            L.gf_workspace_size_batch.restype = C.c_size_t
+            L.gf_workspace_size_batch.argtypes = [pd, C.POINTER(Batch), C.c_char_p]
+            L.gf_default_opts.argtypes = [C.POINTER(LMOpts)]
+            L.gf_model.restype = C.c_int
+            L.gf_model.argtypes = [pd, dp, fp, vp, C.c_size_t, vp]
+            L.gf_convolve.restype = C.c_int
+            L.gf_convolve.argtypes = [pd, fp, fp, fp, vp, C.c_size_t, vp]
+            L.gf_chi2.restype = C.c_int
+            L.gf_chi2.argtypes = [pd, fp, fp, fp, vp, vp, C.c_size_t, vp]
+            L.gf_eval.restype = C.c_int
+            L.gf_eval.argtypes = [pd, dp, fp, fp, fp, fp, vp, vp, C.c_size_t, vp]
+            L.gf_jacobian.restype = C.c_int
+            L.gf_jacobian.argtypes = [pd, dp, C.c_char_p, C.c_double, fp, fp, fp, fp, vp, vp,
+                                      vp, vp, C.c_size_t, vp]
+            L.gf_lm_fit.restype = C.c_int
+            L.gf_lm_fit.argtypes = [pd, dp, C.c_char_p, dp, dp, fp, fp, fp,
+                                    C.POINTER(LMOpts), C.POINTER(LMResult), vp, C.c_size_t, vp]
+            L.gf_lm_fit_batch.restype = C.c_int
+            L.gf_lm_fit_batch.argtypes = [pd, C.POINTER(Batch), dp, C.c_char_p, fp, fp, fp,
+                                          C.POINTER(LMOpts), C.POINTER(LMResult), vp,
+                                          C.c_size_t, vp]
+            L.gf_launch_count.restype = C.c_longlong
+            L.gf_prof_enable.argtypes = [vp]
+            L.gf_prof_times.restype = C.c_int
+            L.gf_prof_times.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+            _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        raise GFError(status, lib().gf_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _fixed(fixed):
+    if fixed is None:
+        return None
+    return np.ascontiguousarray(np.asarray(fixed, np.uint8).reshape(-1)).tobytes()
+
+
+def _cuda_f32(t, shape=None):
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda, "expected a CUDA tensor"
+    assert t.dtype == torch.float32 and t.is_contiguous(), "expected contiguous float32"
+    if shape is not None:
+        assert t.numel() == int(np.prod(shape)), f"expected {shape} elements, got {t.shape}"
+    return t
+
+
+def make_desc(H, W, psf_size, kinds, os_factor=1, os_box=0, os_x0=-1, os_y0=-1,
+              conv_method=CONV_AUTO) -> Desc:
+    d = Desc()
+    d.H, d.W, d.psf_size, d.ncomp = int(H), int(W), int(psf_size), len(kinds)
+    for i, k in enumerate(kinds):
+        d.kinds[i] = int(k)
+    d.os_factor, d.os_box, d.os_x0, d.os_y0 = int(os_factor), int(os_box), int(os_x0), int(os_y0)
+    d.conv_method = int(conv_method)
+    return d
+
+
+def nslots(d: Desc) -> int:
+    return lib().gf_nslots(C.byref(d))
+
+
+def default_opts(**kw) -> LMOpts:
+    o = LMOpts()
+    lib().gf_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Workspace:
+    """A reusable device workspace (a torch uint8 tensor), grown on demand."""
+
+    def __init__(self, device=None):
+        self.t = None
+        self.device = device
+
+    def get(self, nbytes: int):
+        import torch
+        if nbytes == 0:
+            raise GFError(EINVAL, lib().gf_last_error().decode() or "workspace size 0")
+        if self.t is None or self.t.numel() < nbytes:
+            self.t = torch.empty(int(nbytes), dtype=torch.uint8,
+                                 device=self.device or "cuda")
+        return C.c_void_p(self.t.data_ptr()), C.c_size_t(self.t.numel())
+
+
+_default_ws = {}
+
+
+def _ws(ws):
+    import torch
+    if ws is not None:
+        return ws
+    dev = torch.cuda.current_device()
+    if dev not in _default_ws:
+        _default_ws[dev] = Workspace(device=f"cuda:{dev}")
+    return _default_ws[dev]
+
+
+def model(d: Desc, params, out=None, ws=None, stream=None):
+    """Step 1: the model on the extended grid ((H+2c) x (W+2c) float32)."""
+    import torch
+    c = (d.psf_size - 1) // 2
+    shape = (d.H + 2 * c, d.W + 2 * c)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    _cuda_f32(out, shape)
+    p = _f64(params)
+    w, n = _ws(ws).get(lib().gf_workspace_size(C.byref(d), None, CALL_MODEL))
+    _check(lib().gf_model(C.byref(d), _dp(p), _ptr(out), w, n, _stream(stream)))
+    return out
+
+
+def convolve(d: Desc, ext, psf, out=None, ws=None, stream=None):
+    """Step 2: H x W valid convolution of an extended grid with the PSF."""
+    import torch
+    c = (d.psf_size - 1) // 2
+    _cuda_f32(ext, (d.H + 2 * c, d.W + 2 * c))
+    _cuda_f32(psf, (d.psf_size, d.psf_size))
+    if out is None:
+        out = torch.empty((d.H, d.W), dtype=torch.float32, device="cuda")
+    _cuda_f32(out, (d.H, d.W))
+    w, n = _ws(ws).get(lib().gf_workspace_size(C.byref(d), None, CALL_CONVOLVE))
+    _check(lib().gf_convolve(C.byref(d), _ptr(ext), _ptr(psf), _ptr(out), w, n, _stream(stream)))
+    return out
+
+
+def chi2(d: Desc, model_t, img, sig, out=None, ws=None, stream=None):
+    """Step 3: chi^2 (float64 device scalar tensor)."""
+    import torch
+    for t in (model_t, img, sig):
+        _cuda_f32(t, (d.H, d.W))
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+    w, n = _ws(ws).get(lib().gf_workspace_size(C.byref(d), None, CALL_CHI2))
+    _check(lib().gf_chi2(C.byref(d), _ptr(model_t), _ptr(img), _ptr(sig), _ptr(out), w, n,
+                         _stream(stream)))
+    return out
+
+
+def evaluate(d: Desc, params, img, sig, psf, want_model=True, ws=None, stream=None):
+    """Steps 1-3: (chi2 device tensor, convolved model or None)."""
+    import torch
+    for t in (img, sig):
+        _cuda_f32(t, (d.H, d.W))
+    _cuda_f32(psf, (d.psf_size, d.psf_size))
+    m = torch.empty((d.H, d.W), dtype=torch.float32, device="cuda") if want_model else None
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    p = _f64(params)
+    w, n = _ws(ws).get(lib().gf_workspace_size(C.byref(d), None, CALL_EVAL))
+    _check(lib().gf_eval(C.byref(d), _dp(p), _ptr(img), _ptr(sig), _ptr(psf), _ptr(m),
+                         _ptr(out), w, n, _stream(stream)))
+    return out, m
+
+
+def jacobian(d: Desc, params, fixed, img, sig, psf, fd_rel=1e-3, want_J=True, ws=None,
+             stream=None):
+    """Jacobian columns and normal equations: dict(J, A, g, chi2) of device tensors."""
+    import torch
+    for t in (img, sig):
+        _cuda_f32(t, (d.H, d.W))
+    _cuda_f32(psf, (d.psf_size, d.psf_size))
+    ns = nslots(d)
+    fx = np.zeros(ns, np.uint8) if fixed is None else np.asarray(fixed, np.uint8)
+    nf = int(ns - np.count_nonzero(fx))
+    J = torch.empty((nf, d.H, d.W), dtype=torch.float32, device="cuda") if want_J else None
+    A = torch.empty((nf, nf), dtype=torch.float64, device="cuda")
+    g = torch.empty(nf, dtype=torch.float64, device="cuda")
+    x2 = torch.empty(1, dtype=torch.float64, device="cuda")
+    p = _f64(params)
+    fb = _fixed(fx)
+    w, n = _ws(ws).get(lib().gf_workspace_size(C.byref(d), fb, CALL_JACOBIAN))
+    _check(lib().gf_jacobian(C.byref(d), _dp(p), fb, float(fd_rel), _ptr(img), _ptr(sig),
+                             _ptr(psf), _ptr(J), _ptr(A), _ptr(g), _ptr(x2), w, n,
+                             _stream(stream)))
+    return dict(J=J, A=A, g=g, chi2=x2)
+
+
+def _res(r: LMResult):
+    return dict(chi2=r.chi2, lam=r.lam, iters=r.iters, accepted=r.accepted, status=r.status)
+
+
+def lm_fit(d: Desc, params, fixed, img, sig, psf, opts: LMOpts | None = None, lo=None, hi=None,
+           ws=None, stream=None):
+    """Steps 1-5 for one stamp: (params, result dict).  Synchronises the stream."""
+    for t in (img, sig):
+        _cuda_f32(t, (d.H, d.W))
+    _cuda_f32(psf, (d.psf_size, d.psf_size))
+    p = np.array(params, np.float64, copy=True)
+    fb = _fixed(fixed)
+    r = LMResult()
+    w, n = _ws(ws).get(lib().gf_workspace_size(C.byref(d), fb, CALL_LM_FIT))
+    _check(lib().gf_lm_fit(C.byref(d), _dp(p), fb, _dp(_f64(lo) if lo is not None else None),
+                           _dp(_f64(hi) if hi is not None else None), _ptr(img), _ptr(sig),
+                           _ptr(psf), C.byref(opts) if opts is not None else None, C.byref(r),
+                           w, n, _stream(stream)))
+    return p, _res(r)
+
+
+def make_batch(Hs, Ws, pix_off=None, psf_off=None, psf_size=None):
+    """A gf_batch over packed stamps (row-major, stamp after stamp) and PSFs."""
+    Hs = np.ascontiguousarray(Hs, np.int32)
+    Ws = np.ascontiguousarray(Ws, np.int32)
+    if pix_off is None:
+        pix_off = np.concatenate([[0], np.cumsum(Hs.astype(np.int64) * Ws)[:-1]])
+    if psf_off is None:
+        psf_off = np.arange(len(Hs), dtype=np.int64) * int(psf_size) ** 2
+    pix_off = np.ascontiguousarray(pix_off, np.int64)
+    psf_off = np.ascontiguousarray(psf_off, np.int64)
+    b = Batch()
+    b.count = len(Hs)
+    b.H = Hs.ctypes.data_as(C.POINTER(C.c_int))
+    b.W = Ws.ctypes.data_as(C.POINTER(C.c_int))
+    b.pix_off = pix_off.ctypes.data_as(C.POINTER(C.c_int64))
+    b.psf_off = psf_off.ctypes.data_as(C.POINTER(C.c_int64))
+    b._keep = (Hs, Ws, pix_off, psf_off)
+    return b
+
+
+def lm_fit_batch(d: Desc, batch: Batch, params, fixed, img, sig, psf,
+                 opts: LMOpts | None = None, ws=None, stream=None):
+    """Steps 1-5 for a batch of stamps: (params [count, nslots], list of result dicts)."""
+    p = np.array(params, np.float64, copy=True)
+    fb = _fixed(fixed)
+    res = (LMResult * batch.count)()
+    w, n = _ws(ws).get(lib().gf_workspace_size_batch(C.byref(d), C.byref(batch), fb))
+    _check(lib().gf_lm_fit_batch(C.byref(d), C.byref(batch), _dp(p), fb, _ptr(img), _ptr(sig),
+                                 _ptr(psf), C.byref(opts) if opts is not None else None, res,
+                                 w, n, _stream(stream)))
+    return p, [_res(r) for r in res]
+
+
+PROF_CLASSES = ("model", "conv", "reduce", "lm")
+
+
+def launch_count() -> int:
+    """Kernels launched by libgf.so since it was loaded."""
+    return int(lib().gf_launch_count())
+
+
+class Profiler:
+    """Per-kernel-class device time (CUDA events on the launching stream) and
+    algorithmic work counted by the kernels themselves, while active."""
+
+    def __init__(self):
+        import torch
+        self.work = torch.zeros(len(PROF_CLASSES), dtype=torch.int64, device="cuda")
+
+    def __enter__(self):
+        self.work.zero_()
+        lib().gf_prof_times(None, None)  # drop anything recorded before
+        lib().gf_prof_enable(C.c_void_p(self.work.data_ptr()))
+        self.launch0 = launch_count()
+        return self
+
+    def __exit__(self, *exc):
+        lib().gf_prof_enable(None)
+        self.launches_total = launch_count() - self.launch0
+        ms = (C.c_double * len(PROF_CLASSES))()
+        n = (C.c_longlong * len(PROF_CLASSES))()
+        lib().gf_prof_times(ms, n)
+        w = self.work.cpu().tolist()
+        self.result = {k: dict(ms=ms[i], launches=n[i], work=w[i])
+                       for i, k in enumerate(PROF_CLASSES)}
+        return False

@@ -1,0 +1,93 @@
+"""CPU-only checks of the C ABI: libgf.so builds, loads without a GPU, exports
+every function include/gf.h declares, and rejects bad arguments before any
+launch (no CUDA call is reached, so these run on a machine without a GPU)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def gf():
+    from paper_1101_2254_gb300 import build, gf
+    build.build()
+    return gf
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "gf.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gf_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(gf):
+    names = declared_functions()
+    assert "gf_lm_fit" in names and "gf_model" in names and len(names) >= 12
+    lib = gf.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", gf.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (gf_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_version_and_slots(gf):
+    assert gf.lib().gf_version() >= 100
+    d = gf.make_desc(64, 64, 25, [gf.SERSIC, gf.SKY])
+    assert gf.nslots(d) == 9
+    d = gf.make_desc(64, 64, 25, [gf.SERSIC, gf.EXPDISK, gf.SKY])
+    assert gf.nslots(d) == 16
+
+
+@pytest.mark.parametrize("bad", [
+    dict(psf_size=24), dict(psf_size=0), dict(kinds=[gf_k] if (gf_k := 9) else []),
+    dict(kinds=[3, 3]), dict(kinds=[3]), dict(H=0), dict(os_factor=5, os_box=80),
+    dict(os_factor=0), dict(conv_method=1, psf_size=129), dict(conv_method=7),
+])
+def test_invalid_desc_rejected_before_launch(gf, bad):
+    kw = dict(H=64, W=64, psf_size=25, kinds=[1, 3], os_factor=1, os_box=0, conv_method=0)
+    kw.update(bad)
+    d = gf.make_desc(kw["H"], kw["W"], kw["psf_size"], kw["kinds"], kw["os_factor"],
+                     kw["os_box"], conv_method=kw["conv_method"])
+    L = gf.lib()
+    p = np.zeros(16)
+    st = L.gf_model(C.byref(d), p.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(16), None, 0,
+                    None)
+    assert st == gf.EINVAL
+    assert len(L.gf_last_error()) > 0
+    assert L.gf_workspace_size(C.byref(d), None, gf.CALL_LM_FIT) == 0
+
+
+def test_null_and_workspace_checks(gf):
+    L = gf.lib()
+    d = gf.make_desc(64, 64, 25, [1, 3])
+    p = np.zeros(9)
+    dp = p.ctypes.data_as(C.POINTER(C.c_double))
+    assert L.gf_model(C.byref(d), dp, None, None, 0, None) == gf.EINVAL
+    # workspace missing / misaligned / too small
+    assert L.gf_model(C.byref(d), dp, C.c_void_p(256), None, 0, None) == gf.EINVAL
+    assert L.gf_model(C.byref(d), dp, C.c_void_p(256), C.c_void_p(1000), 10**9, None) == gf.EINVAL
+    assert L.gf_model(C.byref(d), dp, C.c_void_p(256), C.c_void_p(1024), 8, None) == gf.ENOMEM
+    # too many free slots for the LM
+    d3 = gf.make_desc(64, 64, 25, [1, 2, 2])   # 22 slots
+    assert L.gf_workspace_size(C.byref(d3), None, gf.CALL_LM_FIT) == 0
+    fixed = np.zeros(22, np.uint8); fixed[[7, 14, 21, 20, 19, 18]] = 1
+    assert L.gf_workspace_size(C.byref(d3), fixed.tobytes(), gf.CALL_LM_FIT) > 0
+
+
+def test_workspace_sizes_scale(gf):
+    L = gf.lib()
+    small = gf.make_desc(64, 64, 25, [1, 3])
+    big = gf.make_desc(512, 512, 65, [1, 2, 3])
+    fixed = np.zeros(16, np.uint8); fixed[14] = 1
+    a = L.gf_workspace_size(C.byref(small), None, gf.CALL_LM_FIT)
+    b = L.gf_workspace_size(C.byref(big), fixed.tobytes(), gf.CALL_LM_FIT)
+    assert 0 < a < b
+    # the 512x512 Jacobian pass holds 14 channel grids of 576^2 floats and 14 outputs of 512^2
+    assert b > 14 * 4 * (576 * 576 + 512 * 512)

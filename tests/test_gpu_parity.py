@@ -1,0 +1,213 @@
+"""GPU parity: every call of the C ABI against the FP64 oracle on the same
+seeded inputs (steps 1-5 of the fitting loop, Sec. 2)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1101_2254_gb300 import synth
+
+from gpu_util import (CHI2_REL, PARAM_REL, assert_pix_close, gpu_desc, noisy_image, oracle_desc,
+                      param_rel_err)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1101_2254_gb300 import build, gf
+    build.build()
+    gf.lib()
+    return gf
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def stamp_cases():
+    rng = np.random.default_rng(123)
+    cases = [synth.stamp64()]
+    # ragged sizes, two profile kinds, boxy isophotes, an off-centre block
+    kinds = [synth.SERSIC, synth.EXPDISK, synth.SKY]
+    p = synth.random_params(kinds, rng, 37, 53, boxy=True)
+    cases.append(synth.Stamp(37, 53, kinds, p, np.zeros(16, np.uint8), synth.random_psf(7, 4),
+                             os_factor=3, os_box=5, name="ragged37x53"))
+    p = synth.random_params([synth.SERSIC], rng, 70, 130)
+    cases.append(synth.Stamp(70, 130, [synth.SERSIC], p, np.zeros(8, np.uint8),
+                             synth.moffat_psf(33, 3.0), os_factor=4, os_box=10, name="70x130"))
+    p = synth.random_params([synth.EXPDISK, synth.SKY], rng, 1, 1)
+    cases.append(synth.Stamp(1, 1, [synth.EXPDISK, synth.SKY], p, np.zeros(8, np.uint8),
+                             synth.gaussian_psf(3, 1.5), name="1x1"))
+    return cases
+
+
+@pytest.mark.parametrize("case", stamp_cases(), ids=lambda s: s.name)
+def test_model_parity(gf, case):
+    d = gpu_desc(gf, case)
+    g = gf.model(d, case.params).cpu().numpy()
+    o = oracle.model_ext(oracle_desc(case), case.params)
+    assert_pix_close(g, o, what=f"model {case.name}")
+
+
+def test_model_parity_stamp512(gf):
+    st = synth.stamp512()
+    g = gf.model(gpu_desc(gf, st), st.params).cpu().numpy()
+    o = oracle.model_ext(oracle_desc(st), st.params)
+    assert_pix_close(g, o, what="model stamp512")
+
+
+@pytest.mark.parametrize("H,W,P", [(64, 64, 25), (70, 130, 33), (33, 65, 65), (1, 1, 1),
+                                   (5, 3, 3), (100, 200, 3), (31, 63, 9), (64, 64, 127)])
+def test_convolve_parity(gf, H, W, P):
+    rng = np.random.default_rng(H * 7 + W * 3 + P)
+    c = (P - 1) // 2
+    ext = rng.uniform(0.0, 2.0, (H + 2 * c, W + 2 * c)).astype(np.float32)
+    psf = synth.random_psf(P, P)
+    d = gf.make_desc(H, W, P, [synth.SERSIC], conv_method=gf.CONV_DIRECT)
+    g = gf.convolve(d, cuda(ext), cuda(psf)).cpu().numpy()
+    o = oracle.convolve_direct(ext.astype(np.float64), psf.astype(np.float64))
+    assert_pix_close(g, o, what=f"conv {H}x{W} P{P}")
+
+
+def test_convolve_delta_is_bit_exact_crop(gf):
+    H, W, P = 45, 77, 17
+    c = (P - 1) // 2
+    ext = np.random.default_rng(1).standard_normal((H + 2 * c, W + 2 * c)).astype(np.float32)
+    psf = np.zeros((P, P), np.float32)
+    psf[c, c] = 1.0
+    d = gf.make_desc(H, W, P, [synth.SERSIC])
+    g = gf.convolve(d, cuda(ext), cuda(psf)).cpu().numpy()
+    assert np.array_equal(g, ext[c:-c, c:-c])
+
+
+def test_chi2_parity_and_invalid_pixels(gf):
+    rng = np.random.default_rng(5)
+    H, W = 75, 130
+    m = rng.uniform(0, 10, (H, W)).astype(np.float32)
+    img = (m + rng.standard_normal((H, W))).astype(np.float32)
+    sig = rng.uniform(0.5, 2.0, (H, W)).astype(np.float32)
+    sig[3, 4] = 0.0
+    sig[10, 11] = -1.0
+    img[20, 21] = np.nan
+    sig[30, 31] = np.inf
+    d = gf.make_desc(H, W, 3, [synth.SERSIC])
+    g = gf.chi2(d, cuda(m), cuda(img), cuda(sig)).item()
+    o = oracle.chi2(img, sig, m)
+    assert abs(g - o) <= CHI2_REL * o
+    assert abs(g - o) <= 1e-6 * o  # compensated sums do much better than the bound
+
+
+@pytest.mark.parametrize("case", stamp_cases()[:3], ids=lambda s: s.name)
+def test_eval_parity(gf, case):
+    m_true, img, sig = noisy_image(case)
+    p = case.guess()
+    d = gpu_desc(gf, case)
+    x2, m = gf.evaluate(d, p, cuda(img), cuda(sig), cuda(case.psf))
+    xo, mo = oracle.evaluate(oracle_desc(case), p, case.psf, img, sig)
+    assert_pix_close(m.cpu().numpy(), mo, what=f"eval model {case.name}")
+    assert abs(x2.item() - xo) <= CHI2_REL * xo
+
+
+@pytest.mark.parametrize("case", stamp_cases()[:3], ids=lambda s: s.name)
+def test_jacobian_parity(gf, case):
+    m_true, img, sig = noisy_image(case)
+    p = case.guess()
+    d = gpu_desc(gf, case)
+    r = gf.jacobian(d, p, case.fixed, cuda(img), cuda(sig), cuda(case.psf))
+    o = oracle.jacobian(oracle_desc(case), p, case.fixed, case.psf, img, sig)
+    J, Jo = r["J"].cpu().numpy(), o["J"]
+    assert J.shape == Jo.shape
+    for f in range(J.shape[0]):
+        scale = np.abs(Jo[f]).max()
+        err = np.abs(J[f] - Jo[f]).max()
+        assert err <= 2e-3 * scale, (case.name, f, err, scale)
+    A, Ao = r["A"].cpu().numpy(), o["A"]
+    dA = np.abs(A - Ao) / np.sqrt(np.outer(np.diag(Ao), np.diag(Ao)))
+    assert dA.max() < 5e-3, dA.max()
+    g, go = r["g"].cpu().numpy(), o["g"]
+    gscale = np.sqrt(np.diag(Ao) * o["chi2"])
+    assert np.all(np.abs(g - go) <= 5e-3 * gscale), (g, go)
+    assert abs(r["chi2"].item() - o["chi2"]) <= CHI2_REL * o["chi2"]
+
+
+def _free(st):
+    return [i for i in range(st.nslots) if not st.fixed[i]]
+
+
+def test_lm_fit_stamp64_matches_oracle(gf):
+    st = synth.stamp64()
+    m_true, img, sig = noisy_image(st)
+    od = oracle_desc(st)
+    po, ro = oracle.lm_fit(od, st.guess(), st.fixed, st.psf, img, sig)
+    assert ro["status"] == oracle.CONVERGED
+    pg, rg = gf.lm_fit(gpu_desc(gf, st), st.guess(), st.fixed, cuda(img), cuda(sig),
+                       cuda(st.psf))
+    assert rg["status"] == gf.OK, rg
+    # the oracle's chi^2 at the GPU's parameters reaches the oracle's minimum
+    xg, _ = oracle.evaluate(od, pg, st.psf, img, sig)
+    assert xg <= ro["chi2"] * (1 + CHI2_REL), (xg, ro["chi2"])
+    assert abs(rg["chi2"] - xg) <= CHI2_REL * xg
+    err = param_rel_err(pg, po, _free(st))
+    assert err.max() < PARAM_REL, (err, pg, po)
+
+
+def test_lm_fit_noiseless_recovers_truth(gf):
+    st = synth.stamp64()
+    m_true, _, sig = noisy_image(st)
+    pg, rg = gf.lm_fit(gpu_desc(gf, st), st.guess(), st.fixed, cuda(m_true), cuda(sig),
+                       cuda(st.psf))
+    assert rg["status"] == gf.OK, rg
+    assert rg["chi2"] <= 1e-4 * m_true.size
+    err = param_rel_err(pg, st.params, _free(st))
+    assert err.max() < PARAM_REL, err
+
+
+def small_batch(n=6, seed=3):
+    sts = synth.batch_stamps(n, seed=seed, smin=24, smax=90, psf_size=15)
+    return sts
+
+
+def test_lm_batch_equals_single_stamp_fits(gf):
+    sts = small_batch()
+    d0 = sts[0]
+    imgs, sigs, psfs, Hs, Ws, p0 = [], [], [], [], [], []
+    for st in sts:
+        m, img, sig = noisy_image(st)
+        imgs.append(img.ravel()); sigs.append(sig.ravel()); psfs.append(st.psf.ravel())
+        Hs.append(st.H); Ws.append(st.W); p0.append(st.guess())
+    d = gf.make_desc(1, 1, d0.P, d0.kinds, d0.os_factor, 8)
+    b = gf.make_batch(Hs, Ws, psf_size=d0.P)
+    pb, rb = gf.lm_fit_batch(d, b, np.array(p0), d0.fixed, cuda(np.concatenate(imgs)),
+                             cuda(np.concatenate(sigs)), cuda(np.concatenate(psfs)))
+    for i, st in enumerate(sts):
+        ds = gf.make_desc(st.H, st.W, st.P, st.kinds, st.os_factor, 8)
+        ps, rs = gf.lm_fit(ds, p0[i], st.fixed, cuda(imgs[i]), cuda(sigs[i]), cuda(st.psf))
+        assert np.array_equal(pb[i], ps), (i, pb[i], ps)
+        assert rb[i]["iters"] == rs["iters"] and rb[i]["status"] == rs["status"]
+        assert rb[i]["chi2"] == rs["chi2"]
+
+
+def test_lm_batch_matches_oracle(gf):
+    sts = small_batch(5, seed=9)
+    d0 = sts[0]
+    imgs, sigs, psfs, Hs, Ws, p0, oracle_res = [], [], [], [], [], [], []
+    for st in sts:
+        m, img, sig = noisy_image(st)
+        imgs.append(img.ravel()); sigs.append(sig.ravel()); psfs.append(st.psf.ravel())
+        Hs.append(st.H); Ws.append(st.W); p0.append(st.guess())
+        od = oracle.make_desc(st.H, st.W, st.P, st.kinds, st.os_factor, 8)
+        oracle_res.append((od, img, sig, oracle.lm_fit(od, st.guess(), st.fixed, st.psf, img, sig)))
+    d = gf.make_desc(1, 1, d0.P, d0.kinds, d0.os_factor, 8)
+    b = gf.make_batch(Hs, Ws, psf_size=d0.P)
+    pb, rb = gf.lm_fit_batch(d, b, np.array(p0), d0.fixed, cuda(np.concatenate(imgs)),
+                             cuda(np.concatenate(sigs)), cuda(np.concatenate(psfs)))
+    for i, st in enumerate(sts):
+        od, img, sig, (po, ro) = oracle_res[i]
+        xg, _ = oracle.evaluate(od, pb[i], st.psf, img, sig)
+        assert xg <= ro["chi2"] * (1 + CHI2_REL), (i, xg, ro)
