@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gf", choices=["gf", "reference"])
     ap.add_argument("--workload", default="stamp512", choices=["stamp512", "stamp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle timing (for profiler runs)")
     return ap.parse_args()
 
 
@@ -272,7 +274,7 @@ def run_gf(args):
         "clocks": clocks,
         "peaks": peak_kind,
     }
-    if rank == 0 and ws_ == 1:
+    if rank == 0 and ws_ == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=20.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
