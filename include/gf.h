@@ -219,6 +219,40 @@ gf_status gf_lm_fit_batch(const gf_desc* d, const gf_batch* b, double* params_ho
                           const gf_lm_opts* opts, gf_lm_result* result_host, void* ws,
                           size_t ws_bytes, gf_stream stream);
 
+/* ------------------------------------------------- allocation-free evaluation
+ * No counterpart in the paper: an interface for callers that cannot allocate
+ * device memory at all -- for example a plugin whose host application owns
+ * the whole device heap, or a latency-critical pipeline that may not call
+ * cudaMalloc (which can synchronise the device) once it is running, and so
+ * cannot provide the workspace the other calls need.
+ *
+ * gf_eval_static computes exactly what gf_eval computes (steps 1-3: the
+ * convolved model and chi^2 of one stamp), but keeps its scratch in a
+ * fixed device array of GF_STATIC_SCRATCH_BYTES (16 MiB) inside libgf.so.
+ * Every GPU that loads the library holds that array until the process exits.
+ * The call allocates nothing and calls no allocating routine; the caller still
+ * passes the inputs (image, sigma, PSF) and outputs (model_dev may be NULL,
+ * chi2_dev one double) in its own device memory.
+ *   - A stamp whose scratch (about 4 bytes per extended-grid pixel plus 4 per
+ *     stamp pixel) exceeds the array is rejected with GF_ENOMEM and a message,
+ *     before any launch.  A 1024x1024 stamp with a 65x65 PSF fits; 2048x2048
+ *     does not.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents.
+ *     Every byte a call reads is written earlier by the same call, so nothing
+ *     needs clearing, but calls whose work overlaps on the GPU (different
+ *     streams, or different host threads) race on the array: serialise them. */
+#define GF_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* Bytes of the static scratch array (GF_STATIC_SCRATCH_BYTES). */
+size_t gf_static_scratch_bytes(void);
+
+gf_status gf_eval_static(const gf_desc* d, const double* params_host, const float* image_dev,
+                         const float* sigma_dev, const float* psf_dev, float* model_dev,
+                         double* chi2_dev, gf_stream stream);
+
 /* ------------------------------------------------------------ diagnostics
  * Not part of the method; used to measure the library (no counterpart in the
  * paper).  Kernel classes: 0 model evaluation, 1 convolution, 2 reductions,

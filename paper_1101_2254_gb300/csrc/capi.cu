@@ -811,3 +811,82 @@ gf_status gf_lm_fit(const gf_desc* d, double* params, const uint8_t* fixed, cons
 }
 
 }  // extern "C"
+
+// ======================================================= allocation-free eval
+// gf_eval_static: steps 1-3 like gf_eval, with its scratch in a file-scope
+// device array instead of a caller workspace (see include/gf.h).
+static __device__ __align__(256) unsigned char g_static_scratch[GF_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kStaticBlobMax = 4096;
+
+// the call's tables and parameters, passed by value so that no host-to-device
+// copy is needed
+struct StaticBlob {
+    unsigned char bytes[kStaticBlobMax];
+};
+
+__global__ void k_static_blob(StaticBlob blob, int n, unsigned char* dst)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = blob.bytes[i];
+}
+
+std::mutex g_static_mu;
+void* g_static_addr[64];
+
+// Device address of g_static_scratch on the current device, looked up once per
+// device (host code cannot use the symbol itself: on the host it only names a
+// stand-in object, not device memory).
+gf_status static_scratch_address(void** out)
+{
+    int dev = 0;
+    GF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(GF_ECUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        GF_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return GF_OK;
+}
+
+}  // namespace
+
+extern "C" size_t gf_static_scratch_bytes(void) { return GF_STATIC_SCRATCH_BYTES; }
+
+extern "C" gf_status gf_eval_static(const gf_desc* d, const double* params, const float* img,
+                                    const float* sig, const float* psf, float* model_out,
+                                    double* chi2, gf_stream stream)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    if ((r = check_stamp(d, d->H, d->W)) != GF_OK) return r;
+    if (!params || !img || !sig || !psf || !chi2) return fail(GF_EINVAL, "NULL argument");
+    Structure S;
+    if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, &S)) != GF_OK) return r;
+    Plan pl;
+    plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, NEED_TRIAL, &pl);
+    if (pl.L.total > GF_STATIC_SCRATCH_BYTES)
+        return fail(GF_ENOMEM, "gf_eval_static: this stamp needs " + std::to_string(pl.L.total) +
+                                   " bytes of scratch; the static scratch holds " +
+                                   std::to_string((size_t)GF_STATIC_SCRATCH_BYTES) +
+                                   " bytes (use gf_eval with a workspace)");
+    if (pl.L.blob_end > (size_t)kStaticBlobMax)
+        return fail(GF_ENOMEM, "gf_eval_static: call tables exceed the by-value limit");
+    void* ws = nullptr;
+    if ((r = static_scratch_address(&ws)) != GF_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    const std::vector<uint8_t> blob = make_blob(pl, S, params);
+    StaticBlob sb;
+    memcpy(sb.bytes, blob.data(), blob.size());
+    k_static_blob<<<1, 256, 0, s>>>(sb, (int)blob.size(), static_cast<unsigned char*>(ws));
+    GF_COUNT_LAUNCH();
+    GF_CUDA(cudaGetLastError());
+    PassArgs a = trial_args(ws, pl.L, base_args(ws, pl.L, psf, img, sig, d->psf_size));
+    a.m_out = model_out;
+    GF_CUDA(launch_prep_sum(a, at<double>(ws, pl.L.params), 0, s));
+    return trial_pass(a, resolve_method(d), s, chi2);
+}

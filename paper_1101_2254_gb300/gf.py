@@ -95,6 +95,9 @@ def lib():
             L.gf_lm_fit_batch.argtypes = [pd, C.POINTER(Batch), dp, C.c_char_p, fp, fp, fp,
                                           C.POINTER(LMOpts), C.POINTER(LMResult), vp,
                                           C.c_size_t, vp]
+            L.gf_static_scratch_bytes.restype = C.c_size_t
+            L.gf_eval_static.restype = C.c_int
+            L.gf_eval_static.argtypes = [pd, dp, fp, fp, fp, fp, vp, vp]
             L.gf_launch_count.restype = C.c_longlong
             L.gf_prof_enable.argtypes = [vp]
             L.gf_prof_times.restype = C.c_int
