@@ -174,7 +174,7 @@ def run_gf(args):
     torch.cuda.synchronize()
     results = []
     step_ms = []
-    with ClockSampler(local) as clk, gf.Profiler() as prof:
+    with ClockSampler(local) as clk:
         launches0 = gf.launch_count()
         for _ in range(args.steps):
             flush.zero_()  # evict the previous fit's data from L2 (untimed)
@@ -187,6 +187,14 @@ def run_gf(args):
             step_ms.append(e0.elapsed_time(e1))
             results.append(res)
         launches = gf.launch_count() - launches0
+    torch.cuda.synchronize()
+    # the same K fits again with the library's profiler on: per-class device
+    # time from CUDA events on the launching stream and the kernels' own count
+    # of their algorithmic work (profiled fits launch without the CUDA graph)
+    with gf.Profiler() as prof:
+        for _ in range(args.steps):
+            flush.zero_()
+            fit()
     torch.cuda.synchronize()
     total_ms = float(sum(step_ms))
     if ws_ > 1:
@@ -235,7 +243,9 @@ def run_gf(args):
     if dom == "conv":
         achieved = pr["conv"]["work"] / (pr["conv"]["ms"] / 1e3) / 1e12
         peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
-        roof = {"bound": "alu", "kernel": "k_conv_direct", "achieved": achieved, "peak": peak,
+        kname = ("k_fft_rows_fwd + k_fft_cols + k_fft_rows_inv (5 N log2 N FLOP per transform)"
+                 if st.P >= 41 else "k_conv_direct (2 P^2 FLOP per output)")
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 "
                                f"FLOP x {sm_max:.0f} MHz (max clock)",
@@ -248,7 +258,7 @@ def run_gf(args):
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{peak_kind} HBM copy", "launches": pr[dom]["launches"],
                 "avg_launch_ms": pr[dom]["ms"] / max(pr[dom]["launches"], 1)}
-    chan_evals = pr["conv"]["work"] / (2.0 * st.P * st.P * st.H * st.W)
+    chan_evals = None if st.P >= 41 else pr["conv"]["work"] / (2.0 * st.P * st.P * st.H * st.W)
     alg_bytes = pr["model"]["work"] + pr["reduce"]["work"]
     line = {
         "metric": METRIC if args.workload == "stamp512" else METRIC64,
@@ -259,16 +269,17 @@ def run_gf(args):
         "config": {"workload": args.workload, "stamp": [st.H, st.W], "psf": st.P,
                    "components": "sersic+expdisk+sky" if args.workload == "stamp512"
                    else "sersic+sky", "free_params": st.nfree,
-                   "oversampling": [st.os_factor, st.os_box], "conv": "direct",
+                   "oversampling": [st.os_factor, st.os_box],
+                   "conv": "fft" if st.P >= 41 else "direct",
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "parallelism": f"replicas{ws_}"},
         "e2e": {"value": e2e_value, "unit": "fits/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roof,
-        "evals_per_s": chan_evals * ws_ / (total_ms / 1e3),
+        "evals_per_s": (chan_evals * ws_ / (total_ms / 1e3)) if chan_evals else None,
         "alg_hbm_gbs": alg_bytes / (total_ms / 1e3) / 1e9,
-        "kernel_ms": {k: v["ms"] / args.steps for k, v in pr.items()},
+        "kernel_ms_per_fit": {k: v["ms"] / args.steps for k, v in pr.items()},
         "lm": {"iters": results[-1]["iters"], "accepted": results[-1]["accepted"],
                "status": results[-1]["status"], "chi2": results[-1]["chi2"]},
         "clocks": clocks,

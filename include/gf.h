@@ -79,15 +79,17 @@ typedef enum {
 typedef enum { GF_SERSIC = 1, GF_EXPDISK = 2, GF_SKY = 3 } gf_comp_kind;
 
 typedef enum {
-    GF_CONV_AUTO = 0,   /* direct for P <= GF_DIRECT_MAX_PSF, else FFT */
+    GF_CONV_AUTO = 0,   /* direct for P < GF_AUTO_FFT_PSF, else FFT */
     GF_CONV_DIRECT = 1, /* tiled direct sum, PSF and halo tile in shared memory */
-    GF_CONV_FFT = 2     /* shared-memory mixed-radix FFT, 2^a 3^b 5^c sizes */
+    GF_CONV_FFT = 2     /* shared-memory mixed-radix FFT, 2^a 3^b 5^c sizes up to 4096;
+                           the stamps of one call must share H and W */
 } gf_conv_method;
 
 #define GF_MAX_COMP 8
 #define GF_MAX_SLOTS 64
 #define GF_MAX_FREE 16
 #define GF_DIRECT_MAX_PSF 127
+#define GF_AUTO_FFT_PSF 41
 #define GF_MAX_PSF 1023
 
 /* Model structure of one stamp (or of every stamp of a batch). */

@@ -627,8 +627,10 @@ static int cholesky_solve(int n, const double* M, const double* b, double* x)
  * into the box, evaluate chi^2 there; accept if chi^2 falls (lambda shrinks,
  * a new Jacobian is taken), otherwise reject (lambda grows).  Finishing
  * criteria: the scaled step falls below xtol, or an accepted step lowers
- * chi^2 by less than ftol relative (converged); lambda exceeds lambda_max
- * (no convergence); max_iter trials (iteration cap). */
+ * chi^2 by less than ftol relative while the linearised model also predicts
+ * a relative fall below ftol (converged; the predicted fall of the damped step
+ * is delta^T (g + lambda diag(A) delta)); lambda exceeds lambda_max (no
+ * convergence); max_iter trials (iteration cap). */
 int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
                const double* lo_in, const double* hi_in, const double* psf,
                const double* img, const double* sigma, int method,
@@ -688,6 +690,11 @@ int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
                 r.status = GFO_CONVERGED;
                 break;
             }
+            double pred = 0.0;
+            for (int i = 0; i < nfree; ++i) {
+                double d = A[i * nfree + i] > 0.0 ? A[i * nfree + i] : 0.0;
+                pred += delta[i] * (rhs[i] + lambda * d * delta[i]);
+            }
             memcpy(pt, p, sizeof(double) * ns);
             for (int i = 0; i < nfree; ++i) pt[fs[i]] += delta[i];
             project(d, pt, lo, hi);
@@ -697,7 +704,7 @@ int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
                 memcpy(p, pt, sizeof(double) * ns);
                 r.accepted++;
                 lambda = fmax(lambda * o.lambda_down, o.lambda_min);
-                if (rel < o.ftol) {
+                if (rel < o.ftol && pred / chi2 < o.ftol) {
                     chi2 = chi2t;
                     r.status = GFO_CONVERGED;
                     break;

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "conv_fft.cuh"
 #include "gf_internal.cuh"
 
 std::atomic<long long> g_launch_count{0};
@@ -111,7 +112,7 @@ int comp_slots(int kind)
 int resolve_method(const gf_desc* d)
 {
     if (d->conv_method == GF_CONV_AUTO)
-        return d->psf_size <= GF_DIRECT_MAX_PSF ? GF_CONV_DIRECT : GF_CONV_FFT;
+        return d->psf_size < GF_AUTO_FFT_PSF ? GF_CONV_DIRECT : GF_CONV_FFT;
     return d->conv_method;
 }
 
@@ -140,13 +141,67 @@ gf_status check_structure(const gf_desc* d)
     if (m == GF_CONV_DIRECT && P > GF_DIRECT_MAX_PSF)
         return fail(GF_EINVAL, "direct convolution supports psf_size <= " +
                                    std::to_string(GF_DIRECT_MAX_PSF));
-    if (m == GF_CONV_FFT) return fail(GF_EINVAL, "FFT convolution is not available in this build");
     return GF_OK;
 }
+
+// smallest 2^a 3^b 5^c >= n (even: a >= 1)
+int fft_len(int n, bool even)
+{
+    for (int m = n > 1 ? n : 1;; ++m) {
+        if (even && (m & 1)) continue;
+        int r = m;
+        while (r % 2 == 0) r /= 2;
+        while (r % 3 == 0) r /= 3;
+        while (r % 5 == 0) r /= 5;
+        if (r == 1) return m;
+    }
+}
+
+FFTPlan make_fft_plan(int n)
+{
+    FFTPlan p;
+    memset(&p, 0, sizeof(p));
+    p.n = n;
+    int m = n;
+    while (m % 4 == 0 && p.nst < FFT_MAX_STAGES) p.radix[p.nst++] = 4, m /= 4;
+    while (m % 2 == 0 && p.nst < FFT_MAX_STAGES) p.radix[p.nst++] = 2, m /= 2;
+    while (m % 3 == 0 && p.nst < FFT_MAX_STAGES) p.radix[p.nst++] = 3, m /= 3;
+    while (m % 5 == 0 && p.nst < FFT_MAX_STAGES) p.radix[p.nst++] = 5, m /= 5;
+    return p;
+}
+
+// columns per CTA of the column pass: the largest power of two <= 16 whose two
+// buffers and twiddles stay within ~100 KB of shared memory
+int choose_cpc(int Ny)
+{
+    int cpc = 16;
+    while (cpc > 1 && fft_col_smem(Ny, cpc) > 100 * 1024) cpc /= 2;
+    return cpc;
+}
+
+// the FFT method needs one geometry for the whole call and sizes within limits
+gf_status check_fft(const gf_desc* d, int count, const int* H, const int* W)
+{
+    if (resolve_method(d) != GF_CONV_FFT) return GF_OK;
+    const int c = (d->psf_size - 1) / 2;
+    for (int b = 1; b < count; ++b)
+        if (H[b] != H[0] || W[b] != W[0])
+            return fail(GF_EINVAL, "FFT convolution needs stamps of one size per call");
+    if (fft_len(H[0] + 2 * c, false) > GF_FFT_MAX || fft_len(W[0] + 2 * c, true) > GF_FFT_MAX)
+        return fail(GF_EINVAL, "FFT size exceeds " + std::to_string(GF_FFT_MAX));
+    return GF_OK;
+}
+
+int fft_len(int n, bool even);
 
 gf_status check_stamp(const gf_desc* d, int H, int W)
 {
     if (H < 1 || W < 1) return fail(GF_EINVAL, "stamp H and W must be >= 1");
+    if (resolve_method(d) == GF_CONV_FFT) {
+        const int c = (d->psf_size - 1) / 2;
+        if (fft_len(H + 2 * c, false) > GF_FFT_MAX || fft_len(W + 2 * c, true) > GF_FFT_MAX)
+            return fail(GF_EINVAL, "FFT size exceeds " + std::to_string(GF_FFT_MAX));
+    }
     if ((long long)H * W > (1LL << 31) - 1) return fail(GF_EINVAL, "stamp too large");
     if (d->os_factor > 1 && d->os_box > 0) {
         if (d->os_box > H || d->os_box > W) return fail(GF_EINVAL, "os_box exceeds the stamp");
@@ -255,6 +310,7 @@ enum { NEED_JAC = 1, NEED_TRIAL = 2, NEED_LM = 4, NEED_CHI2 = 8 };
 struct Layout {
     size_t S, st, pre, params, chan_jac, chan_trial, lm, psum, ext_jac, ext_trial, y_jac,
         y_trial, part_jac, part_trial, active, exp, blob_end, total;
+    size_t tw_x, tw_y, hhat, psfgrid, spec_jac, spec_trial;
     int count, nchan, nacc, nslots;
     int tot_model, tot_os, tot_conv, tot_red;
 };
@@ -263,6 +319,8 @@ struct Plan {
     Layout L;
     std::vector<StampInfo> st;
     std::vector<int> pre;  // 4 * (count + 1): model, os, conv, red
+    int method;            // GF_CONV_DIRECT or GF_CONV_FFT
+    int Nx, Ny, cpc;       // FFT geometry (method FFT)
 };
 
 // Build the stamp table, the block tables and the workspace layout.
@@ -357,6 +415,29 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         L.exp = o;
         o += al(sizeof(double) * (size_t)count * (S.nslots + 5));
     }
+    pl->method = resolve_method(d);
+    if (pl->method == GF_CONV_FFT) {
+        const StampInfo& s0 = pl->st[0];
+        pl->Nx = fft_len(s0.We, true);
+        pl->Ny = fft_len(s0.He, false);
+        pl->cpc = choose_cpc(pl->Ny);
+        const size_t Kx = pl->Nx / 2 + 1;
+        L.tw_x = o;
+        o += al(sizeof(float2) * pl->Nx);
+        L.tw_y = o;
+        o += al(sizeof(float2) * pl->Ny);
+        L.hhat = o;
+        o += al(sizeof(float2) * (size_t)count * pl->Ny * Kx);
+        L.psfgrid = o;
+        o += al(sizeof(float) * (size_t)count * pl->Ny * pl->Nx);
+        if (need & (NEED_JAC | NEED_LM)) {
+            L.spec_jac = o;
+            o += al(sizeof(float2) * (size_t)count * S.nchan * s0.He * Kx);
+        }
+        // the trial pass, gf_eval and gf_convolve use one channel per stamp
+        L.spec_trial = o;
+        o += al(sizeof(float2) * (size_t)count * s0.He * Kx);
+    }
     L.total = o;
 }
 
@@ -447,18 +528,52 @@ gf_status upload(void* ws, const std::vector<uint8_t>& blob, cudaStream_t s)
     return GF_OK;
 }
 
-gf_status run_conv(const PassArgs& a, int method, cudaStream_t s)
+FFTArgs fft_args(void* ws, const Plan& pl)
+{
+    FFTArgs f;
+    memset(&f, 0, sizeof(f));
+    f.Nx = pl.Nx;
+    f.Ny = pl.Ny;
+    f.cpc = pl.cpc;
+    f.px = make_fft_plan(pl.Nx);
+    f.py = make_fft_plan(pl.Ny);
+    f.tw_x = at<float2>(ws, pl.L.tw_x);
+    f.tw_y = at<float2>(ws, pl.L.tw_y);
+    f.hhat = at<float2>(ws, pl.L.hhat);
+    f.psfgrid = at<float>(ws, pl.L.psfgrid);
+    f.st0 = pl.st[0];
+    f.flops_row = (float)(5.0 * pl.Nx * log2((double)pl.Nx));
+    f.flops_col = (float)(pl.cpc * (2.0 * 5.0 * pl.Ny * log2((double)pl.Ny) + 6.0 * pl.Ny));
+    return f;
+}
+
+// per-call set-up of the convolution: twiddles and PSF spectra (FFT method)
+gf_status setup_conv(void* ws, const Plan& pl, const float* psf, cudaStream_t s)
+{
+    if (pl.method != GF_CONV_FFT) return GF_OK;
+    ProfScope ps(PROF_CONV, s);
+    const FFTArgs f = fft_args(ws, pl);
+    GF_CUDA(launch_fft_twiddles(f, s));
+    GF_CUDA(launch_fft_psf(f, pl.L.count, at<StampInfo>(ws, pl.L.st), psf, s));
+    return GF_OK;
+}
+
+// step 2 for the pass `a`; spec is the pass's spectrum scratch (FFT method)
+gf_status run_conv(const PassArgs& a, const Plan& pl, void* ws, size_t spec_off, cudaStream_t s)
 {
     ProfScope ps(PROF_CONV, s);
-    if (method == GF_CONV_DIRECT) {
+    if (pl.method == GF_CONV_DIRECT) {
         GF_CUDA(launch_conv_direct(a, s));
         return GF_OK;
     }
-    return fail(GF_EINVAL, "FFT convolution is not available in this build");
+    if ((long long)a.count * a.nchan > 65535)
+        return fail(GF_EINVAL, "FFT convolution: stamps x channels per call must be <= 65535");
+    GF_CUDA(launch_conv_fft(a, fft_args(ws, pl), at<float2>(ws, spec_off), s));
+    return GF_OK;
 }
 
-gf_status jac_pass(const PassArgs& a, int method, const double* params, double* A, double* g,
-                   double* x2, cudaStream_t s)
+gf_status jac_pass(const PassArgs& a, const Plan& pl, void* ws, const double* params, double* A,
+                   double* g, double* x2, cudaStream_t s)
 {
     {
         ProfScope ps(PROF_LM, s);
@@ -468,25 +583,65 @@ gf_status jac_pass(const PassArgs& a, int method, const double* params, double* 
         ProfScope ps(PROF_MODEL, s);
         GF_CUDA(launch_model(a, s));
     }
-    gf_status r = run_conv(a, method, s);
+    gf_status r = run_conv(a, pl, ws, pl.L.spec_jac, s);
     if (r != GF_OK) return r;
     ProfScope ps(PROF_REDUCE, s);
     GF_CUDA(launch_reduce_jac(a, s));
-    GF_CUDA(launch_final_jac(a, A, g, x2, s));
+    // the LM body folds the final reduction into k_final_solve
+    if (!a.lm) GF_CUDA(launch_final_jac(a, A, g, x2, s));
     return GF_OK;
 }
 
-gf_status trial_pass(const PassArgs& a, int method, cudaStream_t s, double* x2)
+gf_status trial_pass(const PassArgs& a, const Plan& pl, void* ws, cudaStream_t s, double* x2)
 {
     {
         ProfScope ps(PROF_MODEL, s);
         GF_CUDA(launch_model(a, s));
     }
-    gf_status r = run_conv(a, method, s);
+    gf_status r = run_conv(a, pl, ws, pl.L.spec_trial, s);
     if (r != GF_OK) return r;
     ProfScope ps(PROF_REDUCE, s);
     GF_CUDA(launch_reduce_chi2(a, s));
-    GF_CUDA(launch_final_chi2(a, x2, s));
+    // the LM body folds the final reduction into k_final_update
+    if (!a.lm) GF_CUDA(launch_final_chi2(a, x2, s));
+    return GF_OK;
+}
+
+// Make every per-kernel attribute call (shared-memory opt-in) before a stream
+// capture begins.
+gf_status prepare_conv(const Plan& pl)
+{
+    if (pl.method == GF_CONV_DIRECT) {
+        static int optin[64];
+        GF_CUDA(ensure_smem_optin_conv_direct(pl.st[0].P, optin));
+    }
+    return GF_OK;
+}
+
+// A graph executable per host thread, updated in place when the next call
+// captures the same topology (only kernel arguments differ), else rebuilt.
+thread_local cudaGraphExec_t t_exec = nullptr;
+thread_local int t_exec_dev = -1;
+
+gf_status instantiate_cached(cudaGraph_t graph, cudaGraphExec_t* out)
+{
+    int dev = 0;
+    GF_CUDA(cudaGetDevice(&dev));
+    if (t_exec && t_exec_dev == dev) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(t_exec, graph, &info) == cudaSuccess) {
+            *out = t_exec;
+            return GF_OK;
+        }
+        cudaGetLastError();
+    }
+    if (t_exec) {
+        cudaGraphExecDestroy(t_exec);
+        t_exec = nullptr;
+    }
+    GF_CUDA(cudaGraphInstantiate(&t_exec, graph, 0));
+    t_exec_dev = dev;
+    *out = t_exec;
     return GF_OK;
 }
 
@@ -622,7 +777,8 @@ gf_status gf_convolve(const gf_desc* d, const float* ext, const float* psf, floa
     a.chan_stride = 1;
     a.ext = const_cast<float*>(ext);
     a.y = out;
-    return run_conv(a, resolve_method(d), s);
+    if ((r = setup_conv(ws, pl, psf, s)) != GF_OK) return r;
+    return run_conv(a, pl, ws, pl.L.spec_trial, s);
 }
 
 gf_status gf_chi2(const gf_desc* d, const float* model, const float* img, const float* sig,
@@ -676,8 +832,9 @@ gf_status gf_eval(const gf_desc* d, const double* params, const float* img, cons
     if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
     PassArgs a = trial_args(ws, pl.L, base_args(ws, pl.L, psf, img, sig, d->psf_size));
     a.m_out = model_out;
+    if ((r = setup_conv(ws, pl, psf, s)) != GF_OK) return r;
     GF_CUDA(launch_prep_sum(a, at<double>(ws, pl.L.params), 0, s));
-    return trial_pass(a, resolve_method(d), s, chi2);
+    return trial_pass(a, pl, ws, s, chi2);
 }
 
 gf_status gf_jacobian(const gf_desc* d, const double* params, const uint8_t* fixed, double fd_rel,
@@ -704,7 +861,8 @@ gf_status gf_jacobian(const gf_desc* d, const double* params, const uint8_t* fix
     PassArgs a = jac_args(ws, pl.L, base_args(ws, pl.L, psf, img, sig, d->psf_size));
     a.J_out = J_out;
     GF_CUDA(launch_psf_sum(1, a.st, psf, const_cast<float*>(a.psf_sum), s));
-    return jac_pass(a, resolve_method(d), at<double>(ws, pl.L.params), A, g, chi2, s);
+    if ((r = setup_conv(ws, pl, psf, s)) != GF_OK) return r;
+    return jac_pass(a, pl, ws, at<double>(ws, pl.L.params), A, g, chi2, s);
 }
 
 static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params,
@@ -725,13 +883,14 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     Structure S;
     if ((r = make_structure(d, fixed, lo, hi, opts, &S)) != GF_OK) return r;
     if (S.nfree < 1) return fail(GF_EINVAL, "no free slots");
+    if ((r = check_fft(d, b->count, b->H, b->W)) != GF_OK) return r;
     Plan pl;
     plan_batch(d, S, b->count, b->H, b->W, b->pix_off, b->psf_off, NEED_LM, &pl);
     if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
     const Layout& L = pl.L;
     if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
-    const int method = resolve_method(d);
+    if ((r = setup_conv(ws, pl, psf, s)) != GF_OK) return r;
     PassArgs base = base_args(ws, L, psf, img, sig, d->psf_size);
     LMState* lm = at<LMState>(ws, L.lm);
     PassArgs aj = jac_args(ws, L, base);
@@ -743,21 +902,49 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     int* active = at<int>(ws, L.active);
     GF_CUDA(launch_psf_sum(L.count, base.st, psf, const_cast<float*>(base.psf_sum), s));
     GF_CUDA(launch_lm_init(L.count, base.S, lm, at<double>(ws, L.params), s));
+    // One LM "body": the Jacobian pass (stamps that need it), the damped solve,
+    // the trial pass, accept/reject and the count of stamps still active.
+    auto body = [&]() -> gf_status {
+        gf_status rr = jac_pass(aj, pl, ws, nullptr, nullptr, nullptr, nullptr, s);
+        if (rr != GF_OK) return rr;
+        {
+            ProfScope ps(PROF_LM, s);
+            GF_CUDA(launch_final_solve(aj, at<Channel>(ws, L.chan_trial), active, s));
+        }
+        if ((rr = trial_pass(at_, pl, ws, s, nullptr)) != GF_OK) return rr;
+        ProfScope ps(PROF_LM, s);
+        GF_CUDA(launch_final_update(at_, active, s));
+        return GF_OK;
+    };
+    // With a capturable stream and no profiling, the body's ~20 launches are
+    // captured once into a CUDA graph and replayed; the host reads one integer
+    // (active stamps) every few bodies.
+    cudaGraphExec_t exec = nullptr;
+    if (s != nullptr && !prof::work_dev) {
+        if ((r = prepare_conv(pl)) != GF_OK) return r;
+        cudaGraph_t graph = nullptr;
+        GF_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        gf_status rb = body();
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (rb != GF_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rb;
+        }
+        GF_CUDA(ce);
+        r = instantiate_cached(graph, &exec);
+        cudaGraphDestroy(graph);
+        if (r != GF_OK) return r;
+    }
     const int max_bodies = S.opts.max_iter + 2;
     int bodies = 0;
     for (;;) {
         const int K = bodies < 8 ? 2 : 4;
         for (int k = 0; k < K && bodies < max_bodies; ++k, ++bodies) {
-            if ((r = jac_pass(aj, method, nullptr, nullptr, nullptr, nullptr, s)) != GF_OK)
+            if (exec) {
+                GF_CUDA(cudaGraphLaunch(exec, s));
+            } else if ((r = body()) != GF_OK) {
                 return r;
-            {
-                ProfScope ps(PROF_LM, s);
-                GF_CUDA(launch_lm_solve(aj, at<Channel>(ws, L.chan_trial), s));
             }
-            if ((r = trial_pass(at_, method, s, nullptr)) != GF_OK) return r;
-            ProfScope ps(PROF_LM, s);
-            GF_CUDA(cudaMemsetAsync(active, 0, sizeof(int), s));
-            GF_CUDA(launch_lm_update(at_, active, s));
         }
         int h_active = 0;
         GF_CUDA(cudaMemcpyAsync(&h_active, active, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -887,6 +1074,7 @@ extern "C" gf_status gf_eval_static(const gf_desc* d, const double* params, cons
     GF_CUDA(cudaGetLastError());
     PassArgs a = trial_args(ws, pl.L, base_args(ws, pl.L, psf, img, sig, d->psf_size));
     a.m_out = model_out;
+    if ((r = setup_conv(ws, pl, psf, s)) != GF_OK) return r;
     GF_CUDA(launch_prep_sum(a, at<double>(ws, pl.L.params), 0, s));
-    return trial_pass(a, resolve_method(d), s, chi2);
+    return trial_pass(a, pl, ws, s, chi2);
 }

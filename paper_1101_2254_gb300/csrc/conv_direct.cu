@@ -108,6 +108,8 @@ __global__ void __launch_bounds__(NT) k_conv_direct(PassArgs a)
 
 }  // namespace
 
+cudaError_t ensure_smem_optin_conv_direct(int P, int* cache);
+
 size_t conv_direct_smem(int P)
 {
     const int P4 = (P + 3) & ~3;
@@ -117,11 +119,20 @@ size_t conv_direct_smem(int P)
 cudaError_t launch_conv_direct(const PassArgs& a, cudaStream_t s)
 {
     if (a.tot_conv <= 0) return cudaSuccess;
-    static int optin[64];
     const size_t sm = conv_direct_smem(a.P);
-    cudaError_t e = ensure_smem_optin((const void*)k_conv_direct, (int)sm, optin);
+    cudaError_t e = ensure_smem_optin_conv_direct(a.P, nullptr);
     if (e != cudaSuccess) return e;
     k_conv_direct<<<dim3(a.tot_conv, a.nchan), NT, sm, s>>>(a);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
+}
+
+// one cache per device for every caller, so that a call made before a stream
+// capture leaves nothing to set inside it
+static int g_conv_direct_optin[64];
+
+cudaError_t ensure_smem_optin_conv_direct(int P, int*)
+{
+    return ensure_smem_optin((const void*)k_conv_direct, (int)conv_direct_smem(P),
+                             g_conv_direct_optin);
 }

@@ -1,0 +1,293 @@
+// conv_fft.cu -- step 2 of the fitting loop in Fourier space (Sec. 3 item 2
+// places the PSF convolution there: forward FFTs, a pointwise product, an
+// inverse FFT).
+//
+// The halo-extended grid (He x We) is convolved circularly at a padded size
+// Ny x Nx (smallest 2^a 3^b 5^c >= He, and the smallest even one >= We); with
+// the PSF wrapped so that its centre sits at (0, 0), the circular result equals
+// the direct sum on the valid region, because every output pixel reads only
+// grid pixels inside the extended grid.  Three passes per channel, all through
+// shared-memory Stockham FFTs (fft.cuh):
+//   rows    two real grid rows packed as one complex row, forward FFT, unpacked
+//           into the two half spectra (Nx/2 + 1 bins each);
+//   columns CPC adjacent spectrum columns per CTA (coalesced), forward FFT along
+//           y, product with the PSF spectrum, inverse FFT; only the rows the
+//           output needs are written back;
+//   rows    inverse of the packing: two half spectra form one complex row, one
+//           inverse FFT gives both output rows; only the valid region is kept.
+// The PSF spectrum, scaled by 1/(Ny Nx), is computed once per call by the same
+// kernels.  Grid rows beyond He are zeros and are never read or written.
+#include <math.h>
+
+#include "fft.cuh"
+#include "gf_internal.cuh"
+#include "conv_fft.cuh"
+
+namespace {
+
+constexpr int ROW_THREADS = 128;
+constexpr int COL_THREADS = 256;
+
+__global__ void k_twiddles(int n, float2* tw)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)k / (double)n, &s, &c);
+        tw[k] = make_float2((float)c, (float)-s);
+    }
+}
+
+__device__ __forceinline__ void load_tw(float2* dst, const float2* src, int n)
+{
+    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+}
+
+// The wrapped, normalised PSF on the Ny x Nx grid: psf[v][u] / (Ny Nx) at
+// ((v - c) mod Ny, (u - c) mod Nx); the grid was zeroed by the caller.
+__global__ void k_psf_wrap(FFTArgs f, int count, const StampInfo* st, const float* psf)
+{
+    const int b = blockIdx.y;
+    if (b >= count) return;
+    const int P = st[b].P, c = st[b].c;
+    const float scale = (float)(1.0 / ((double)f.Ny * (double)f.Nx));
+    float* g = f.psfgrid + (long long)b * f.Ny * f.Nx;
+    const float* p = psf + st[b].psf_off;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < P * P; t += gridDim.x * blockDim.x) {
+        const int v = t / P, u = t - v * P;
+        const int y = ((v - c) % f.Ny + f.Ny) % f.Ny, x = ((u - c) % f.Nx + f.Nx) % f.Nx;
+        g[(long long)y * f.Nx + x] = p[t] * scale;
+    }
+}
+
+// Forward row pass.  Problem p = blockIdx.y covers one real grid (rows `rows`
+// valid of row stride `ld`, `width` valid columns) and one half-spectrum array
+// (Kx = Nx/2 + 1 bins per row).  Block x handles rows 2x and 2x + 1.
+__global__ void __launch_bounds__(ROW_THREADS) k_fft_rows_fwd(FFTArgs f, RowIO io, PassArgs a)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    const int p = blockIdx.y;
+    if (a.lm && a.lm[p / io.nchan].phase != a.phase) return;
+    const int Nx = f.Nx, Kx = Nx / 2 + 1;
+    float2* bufA = sm;
+    float2* bufB = sm + Nx;
+    float2* tw = sm + 2 * Nx;
+    load_tw(tw, f.tw_x, Nx);
+    const int y0 = 2 * blockIdx.x, y1 = y0 + 1;
+    const float* in = io.in + (long long)p * io.in_stride;
+    for (int x = threadIdx.x; x < Nx; x += blockDim.x) {
+        const bool cx = x < io.width;
+        const float va = (cx && y0 < io.rows) ? in[(long long)y0 * io.ld + x] : 0.0f;
+        const float vb = (cx && y1 < io.rows) ? in[(long long)y1 * io.ld + x] : 0.0f;
+        bufA[x] = make_float2(va, vb);
+    }
+    __syncthreads();
+    const float2* Z = fft_smem(f.px, bufA, bufB, 1, tw, -1.0f);
+    float2* out = io.spec + (long long)p * io.spec_stride;
+    for (int k = threadIdx.x; k < Kx; k += blockDim.x) {
+        const float2 zk = Z[k], zm = cconj(Z[(Nx - k) % Nx]);
+        const float2 s = cadd(zk, zm), d = csub(zk, zm);
+        // A = (Z[k] + conj Z[N-k]) / 2,  B = (Z[k] - conj Z[N-k]) / (2i)
+        if (y0 < io.out_rows) out[(long long)y0 * Kx + k] = make_float2(0.5f * s.x, 0.5f * s.y);
+        if (y1 < io.out_rows) out[(long long)y1 * Kx + k] = make_float2(0.5f * d.y, -0.5f * d.x);
+    }
+    if (a.work && threadIdx.x == 0) atomicAdd(&a.work[PROF_CONV], (unsigned long long)f.flops_row);
+}
+
+// Column pass.  mode 0: forward only, all Ny rows written (the PSF spectrum);
+// mode 1: forward, product with the PSF spectrum, inverse, rows [c, c + H)
+// written back in place.
+__global__ void __launch_bounds__(COL_THREADS) k_fft_cols(FFTArgs f, ColIO io, PassArgs a, int mode)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    const int p = blockIdx.y;
+    const int b = p / io.nchan;
+    if (a.lm && a.lm[b].phase != a.phase) return;
+    const int Ny = f.Ny, Kx = f.Nx / 2 + 1, B = f.cpc;
+    float2* bufA = sm;
+    float2* bufB = sm + Ny * B;
+    float2* tw = sm + 2 * Ny * B;
+    load_tw(tw, f.tw_y, Ny);
+    const int kx0 = blockIdx.x * B;
+    float2* spec = io.spec + (long long)p * io.spec_stride;
+    for (int t = threadIdx.x; t < Ny * B; t += blockDim.x) {
+        const int y = t / B, kx = kx0 + (t - y * B);
+        bufA[t] = (y < io.rows_in && kx < Kx) ? spec[(long long)y * Kx + kx] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* X = fft_smem(f.py, bufA, bufB, B, tw, -1.0f);
+    if (a.work && threadIdx.x == 0) atomicAdd(&a.work[PROF_CONV], (unsigned long long)f.flops_col);
+    if (mode == 0) {
+        for (int t = threadIdx.x; t < Ny * B; t += blockDim.x) {
+            const int y = t / B, kx = kx0 + (t - y * B);
+            if (kx < Kx) spec[(long long)y * Kx + kx] = X[t];
+        }
+        return;
+    }
+    const float2* H = f.hhat + (long long)b * Ny * Kx;
+    for (int t = threadIdx.x; t < Ny * B; t += blockDim.x) {
+        const int y = t / B, kx = kx0 + (t - y * B);
+        if (kx < Kx) X[t] = cmul(X[t], H[(long long)y * Kx + kx]);
+    }
+    __syncthreads();
+    float2* other = (X == bufA) ? bufB : bufA;
+    const float2* Yv = fft_smem(f.py, X, other, B, tw, 1.0f);
+    const int r0 = io.row0, r1 = io.row0 + io.nrows_out;
+    for (int t = threadIdx.x; t < Ny * B; t += blockDim.x) {
+        const int y = t / B, kx = kx0 + (t - y * B);
+        if (kx < Kx && y >= r0 && y < r1) spec[(long long)y * Kx + kx] = Yv[t];
+    }
+}
+
+// Inverse row pass: output rows 2x, 2x + 1 of an H x W result from spectrum
+// rows row0 + 2x, row0 + 2x + 1; grid columns [col0, col0 + W) are kept.
+__global__ void __launch_bounds__(ROW_THREADS) k_fft_rows_inv(FFTArgs f, RowInvIO io, PassArgs a)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    const int p = blockIdx.y;
+    if (a.lm && a.lm[p / io.nchan].phase != a.phase) return;
+    const int Nx = f.Nx, Kx = Nx / 2 + 1;
+    float2* bufA = sm;
+    float2* bufB = sm + Nx;
+    float2* tw = sm + 2 * Nx;
+    load_tw(tw, f.tw_x, Nx);
+    const int i0 = 2 * blockIdx.x, i1 = i0 + 1;
+    const bool has1 = i1 < io.H;
+    const float2* spec = io.spec + (long long)p * io.spec_stride;
+    const float2* sa = spec + (long long)(io.row0 + i0) * Kx;
+    const float2* sb = spec + (long long)(io.row0 + i1) * Kx;
+    for (int k = threadIdx.x; k < Nx; k += blockDim.x) {
+        float2 A, Bv;
+        if (k < Kx) {
+            A = sa[k];
+            Bv = has1 ? sb[k] : make_float2(0.f, 0.f);
+        } else {
+            A = cconj(sa[Nx - k]);
+            Bv = has1 ? cconj(sb[Nx - k]) : make_float2(0.f, 0.f);
+        }
+        bufA[k] = make_float2(A.x - Bv.y, A.y + Bv.x);  // A + i B
+    }
+    __syncthreads();
+    const float2* z = fft_smem(f.px, bufA, bufB, 1, tw, 1.0f);
+    float* out = io.out + (long long)p * io.out_stride;
+    for (int j = threadIdx.x; j < io.W; j += blockDim.x) {
+        const float2 v = z[io.col0 + j];
+        out[(long long)i0 * io.W + j] = v.x;
+        if (has1) out[(long long)i1 * io.W + j] = v.y;
+    }
+    if (a.work && threadIdx.x == 0) atomicAdd(&a.work[PROF_CONV], (unsigned long long)f.flops_row);
+}
+
+}  // namespace
+
+size_t fft_row_smem(int Nx) { return sizeof(float2) * 3 * (size_t)Nx; }
+size_t fft_col_smem(int Ny, int cpc) { return sizeof(float2) * ((size_t)2 * Ny * cpc + Ny); }
+
+cudaError_t launch_fft_twiddles(const FFTArgs& f, cudaStream_t s)
+{
+    k_twiddles<<<(f.Nx + 255) / 256, 256, 0, s>>>(f.Nx, f.tw_x);
+    GF_COUNT_LAUNCH();
+    k_twiddles<<<(f.Ny + 255) / 256, 256, 0, s>>>(f.Ny, f.tw_y);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+static cudaError_t optin_all(const FFTArgs& f)
+{
+    static int o1[64], o2[64], o3[64];
+    cudaError_t e = ensure_smem_optin((const void*)k_fft_rows_fwd, (int)fft_row_smem(f.Nx), o1);
+    if (e == cudaSuccess)
+        e = ensure_smem_optin((const void*)k_fft_rows_inv, (int)fft_row_smem(f.Nx), o2);
+    if (e == cudaSuccess)
+        e = ensure_smem_optin((const void*)k_fft_cols, (int)fft_col_smem(f.Ny, f.cpc), o3);
+    return e;
+}
+
+// PSF spectra of all stamps of a call (uniform size): wrap, row pass over all
+// Ny rows, forward column pass.
+cudaError_t launch_fft_psf(const FFTArgs& f, int count, const StampInfo* st, const float* psf,
+                           cudaStream_t s)
+{
+    cudaError_t e = optin_all(f);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(f.psfgrid, 0, sizeof(float) * (size_t)count * f.Ny * f.Nx, s);
+    if (e != cudaSuccess) return e;
+    k_psf_wrap<<<dim3(8, count), 256, 0, s>>>(f, count, st, psf);
+    GF_COUNT_LAUNCH();
+    PassArgs none;
+    memset(&none, 0, sizeof(none));
+    const int Kx = f.Nx / 2 + 1;
+    RowIO r;
+    r.in = f.psfgrid;
+    r.in_stride = (long long)f.Ny * f.Nx;
+    r.ld = f.Nx;
+    r.width = f.Nx;
+    r.rows = f.Ny;
+    r.spec = f.hhat;
+    r.spec_stride = (long long)f.Ny * Kx;
+    r.out_rows = f.Ny;
+    r.nchan = 1;
+    k_fft_rows_fwd<<<dim3((f.Ny + 1) / 2, count), ROW_THREADS, fft_row_smem(f.Nx), s>>>(f, r, none);
+    GF_COUNT_LAUNCH();
+    ColIO c;
+    c.spec = f.hhat;
+    c.spec_stride = (long long)f.Ny * Kx;
+    c.rows_in = f.Ny;
+    c.row0 = 0;
+    c.nrows_out = f.Ny;
+    c.nchan = 1;
+    k_fft_cols<<<dim3((Kx + f.cpc - 1) / f.cpc, count), COL_THREADS, fft_col_smem(f.Ny, f.cpc), s>>>(
+        f, c, none, 0);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+// Convolve the pass's channel grids (a.ext) into a.y through the spectrum
+// scratch `spec` (count * nchan * He * Kx complex values).
+cudaError_t launch_conv_fft(const PassArgs& a, const FFTArgs& f, float2* spec, cudaStream_t s)
+{
+    cudaError_t e = optin_all(f);
+    if (e != cudaSuccess) return e;
+    const StampInfo& s0 = f.st0;  // uniform stamp geometry (host copy)
+    const int Kx = f.Nx / 2 + 1;
+    const int nprob = a.count * a.nchan;
+    RowIO r;
+    r.in = a.ext;
+    r.in_stride = (long long)s0.He * s0.We;
+    r.ld = s0.We;
+    r.width = s0.We;
+    r.rows = s0.He;
+    r.spec = spec;
+    r.spec_stride = (long long)s0.He * Kx;
+    r.out_rows = s0.He;
+    r.nchan = a.nchan;
+    k_fft_rows_fwd<<<dim3((s0.He + 1) / 2, nprob), ROW_THREADS, fft_row_smem(f.Nx), s>>>(f, r, a);
+    GF_COUNT_LAUNCH();
+    ColIO c;
+    c.spec = spec;
+    c.spec_stride = (long long)s0.He * Kx;
+    c.rows_in = s0.He;
+    c.row0 = s0.c;
+    c.nrows_out = s0.H;
+    c.nchan = a.nchan;
+    // fewer columns per CTA when the pass has few problems (a one-channel trial
+    // pass), so that the column pass still spreads over the SMs
+    FFTArgs fc = f;
+    while (fc.cpc > 2 && (long long)nprob * ((Kx + fc.cpc - 1) / fc.cpc) < 2 * 152) fc.cpc /= 2;
+    fc.flops_col = f.flops_col * (float)fc.cpc / (float)f.cpc;
+    k_fft_cols<<<dim3((Kx + fc.cpc - 1) / fc.cpc, nprob), COL_THREADS, fft_col_smem(fc.Ny, fc.cpc),
+                 s>>>(fc, c, a, 1);
+    GF_COUNT_LAUNCH();
+    RowInvIO v;
+    v.spec = spec;
+    v.spec_stride = (long long)s0.He * Kx;
+    v.row0 = s0.c;
+    v.col0 = s0.c;
+    v.H = s0.H;
+    v.W = s0.W;
+    v.out = a.y;
+    v.out_stride = (long long)s0.H * s0.W;
+    v.nchan = a.nchan;
+    k_fft_rows_inv<<<dim3((s0.H + 1) / 2, nprob), ROW_THREADS, fft_row_smem(f.Nx), s>>>(f, v, a);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}

@@ -102,7 +102,8 @@ struct LMState {
     double pt[GF_MAX_SLOTS];
     double A[GF_MAX_FREE * GF_MAX_FREE];
     double g[GF_MAX_FREE];
-    double chi2, chi2t, lambda, psum;
+    double chi2, chi2t, lambda, pred;  // pred: chi^2 fall the linearised model predicts for pt
+    double bn_n[GF_MAX_COMP], bn_b[GF_MAX_COMP];  // last (n, b_n) per component: Newton start
     int iters, accepted, status, phase;
 };
 
@@ -171,6 +172,29 @@ __device__ __forceinline__ CSum csum_merge(CSum a, CSum b)
     return r;
 }
 
+// decode accumulator index t into (kind, i, j): 0 = A_ij (i <= j), 1 = g_i, 2 = chi^2
+__host__ __device__ __forceinline__ int decode_acc(int t, int nf, int& i, int& j)
+{
+    const int npair = nf * (nf + 1) / 2;
+    if (t < npair) {
+        int row = 0, rem = t;
+        while (rem >= nf - row) {
+            rem -= nf - row;
+            ++row;
+        }
+        i = row;
+        j = row + rem;
+        return 0;
+    }
+    if (t < npair + nf) {
+        i = t - npair;
+        j = 0;
+        return 1;
+    }
+    i = j = 0;
+    return 2;
+}
+
 // stamp index of a block from an exclusive prefix table (upper_bound - 1)
 __device__ __forceinline__ int find_stamp(const int* prefix, int count, int blk)
 {
@@ -221,6 +245,7 @@ enum { PROF_MODEL = 0, PROF_CONV = 1, PROF_REDUCE = 2, PROF_LM = 3, PROF_CLASSES
 
 // per-device one-time opt-in to large dynamic shared memory for a kernel
 cudaError_t ensure_smem_optin(const void* func, int bytes, int* cache_per_device);
+cudaError_t ensure_smem_optin_conv_direct(int P, int* cache_per_device);
 
 // every kernel launch of the library increments this counter
 extern std::atomic<long long> g_launch_count;
@@ -243,8 +268,9 @@ cudaError_t launch_prep_sum(const PassArgs& a, const double* params, int use_tri
 cudaError_t launch_prep_jac(const PassArgs& a, const double* params, cudaStream_t s);
 cudaError_t launch_lm_init(int count, const Structure* S, LMState* lm, const double* p0,
                            cudaStream_t s);
-cudaError_t launch_lm_solve(const PassArgs& a, Channel* trial_chan, cudaStream_t s);
-cudaError_t launch_lm_update(const PassArgs& a, int* active_count, cudaStream_t s);
+cudaError_t launch_final_solve(const PassArgs& a, Channel* trial_chan, int* active,
+                               cudaStream_t s);
+cudaError_t launch_final_update(const PassArgs& a, int* active_count, cudaStream_t s);
 cudaError_t launch_lm_export(int count, const Structure* S, const LMState* lm, double* out,
                              cudaStream_t s);
 
@@ -257,3 +283,4 @@ cudaError_t launch_lm_export(int count, const Structure* S, const LMState* lm, d
 #define RED_PIX (RED_THREADS * RED_CHUNKS)
 #define MODEL_THREADS 256
 #define OS_WARPS 8
+#define FINAL_THREADS 128

@@ -5,6 +5,17 @@
 // from P(2n, b_n) = 1/2, the rotation terms, finite-difference steps) and in the
 // damped normal-equation solve.  The pixel path receives float32 constants.
 //
+// Every kernel here runs one warp per stamp.  GB300's FP64 units are few and
+// their latency long, so a single thread walking a chain of dependent FP64
+// divisions (the incomplete-gamma series, a Cholesky factorisation) costs
+// hundreds of microseconds; spread over 32 lanes the same work is short:
+//   - the series terms x^k / ((a+1)...(a+k)) come from one division per term,
+//     done in parallel, and a warp prefix product;
+//   - Newton on P(2n, b) - 1/2 starts from the stamp's previous b_n (db_n/dn is
+//     close to 2), so it usually needs two or three series evaluations;
+//   - channel constants are built one channel per lane;
+//   - the Cholesky factorisation updates each column across the lanes.
+//
 // LM per stamp, driven by a phase word so that one launch sequence serves a
 // whole batch of stamps in different states:
 //   PH_NEED_JAC  the Jacobian pass (model/convolution/reduction) runs, -> PH_SOLVE
@@ -12,8 +23,9 @@
 //                step ends the fit; else project p + delta into the box and
 //                build the trial model channel, -> PH_TRIAL
 //   PH_TRIAL     the trial pass computes chi^2 at the trial point; accept if it
-//                fell (lambda shrinks, -> PH_NEED_JAC; a relative fall below ftol
-//                ends the fit), else reject (lambda grows, -> PH_SOLVE)
+//                fell (lambda shrinks, -> PH_NEED_JAC; when both the actual and
+//                the predicted relative falls are below ftol the fit ends), else
+//                reject (lambda grows, -> PH_SOLVE)
 //   PH_DONE      converged, lambda past lambda_max, max_iter trials, or
 //                non-finite chi^2 / normal equations
 #include <math.h>
@@ -23,34 +35,50 @@
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarpsPerBlock = 4;
 
 // Regularised lower incomplete gamma P(a, x) by its power series
-// P(a, x) = x^a e^{-x} / Gamma(a+1) * sum_{k>=0} x^k / ((a+1)...(a+k)).
-// lg1 = ln Gamma(a + 1).
-__device__ double gamma_p(double a, double x, double lg1)
+//   P(a, x) = x^a e^{-x} / Gamma(a+1) * sum_{k>=0} x^k / ((a+1)...(a+k)),
+// evaluated by the whole warp: lane l forms the ratios x/(a+k) for
+// k = 3l+1 .. 3l+3, a warp scan multiplies them into the terms, a butterfly sums
+// them.  96 terms: for the b_n root x < a <= 20, term 96 is below 1e-40.
+// Every lane returns the same value.  lg1 = ln Gamma(a + 1).
+__device__ double gamma_p_warp(double a, double x, double lg1)
 {
     if (x <= 0.0) return 0.0;
-    double sum = 1.0, term = 1.0;
-    for (int k = 1; k < 1000; ++k) {
-        term *= x / (a + k);
-        sum += term;
-        if (term < 1e-17 * sum) break;
+    const int lane = threadIdx.x & 31;
+    const double k0 = 1.0 + 3.0 * lane;
+    const double r0 = x / (a + k0), r1 = x / (a + k0 + 1.0), r2 = x / (a + k0 + 2.0);
+    const double p0 = r0, p1 = p0 * r1, p2 = p1 * r2;
+    double incl = p2;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl *= v;
     }
-    return exp(a * log(x) - x - lg1) * sum;
+    double excl = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) excl = 1.0;
+    double s = excl * (p0 + p1 + p2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    return exp(a * log(x) - x - lg1) * (1.0 + s);
 }
 
-// b_n: root of P(2n, b) = 1/2, by Newton steps safeguarded with a bisection
-// bracket (the median of a Gamma(a) variate lies in (0, a)).  The start is the
-// asymptotic expansion of Ciotti & Bertin (1999).
-__device__ double sersic_bn(double n)
+// b_n: root of P(2n, b) = 1/2 by Newton steps safeguarded with a bisection
+// bracket (the median of a Gamma(a) variate lies in (0, a)).  The start is
+// `guess` when it lies in the bracket, else the asymptotic expansion of
+// Ciotti & Bertin (1999).  Called by all lanes of a warp with equal arguments.
+__device__ double sersic_bn_warp(double n, double guess)
 {
     const double a = 2.0 * n;
     double lo = 0.0, hi = a;
-    double b = a - 1.0 / 3.0 + 4.0 / (405.0 * n) + 46.0 / (25515.0 * n * n);
+    double b = guess;
+    if (!(b > lo && b < hi)) b = a - 1.0 / 3.0 + 4.0 / (405.0 * n) + 46.0 / (25515.0 * n * n);
     if (!(b > lo && b < hi)) b = 0.5 * a;
     const double lg1 = lgamma(a + 1.0), lga = lg1 - log(a);
-    for (int it = 0; it < 200; ++it) {
-        const double f = gamma_p(a, b, lg1) - 0.5;
+    for (int it = 0; it < 100; ++it) {
+        const double f = gamma_p_warp(a, b, lg1) - 0.5;
         if (f == 0.0) break;
         if (f < 0.0)
             lo = b;
@@ -59,9 +87,9 @@ __device__ double sersic_bn(double n)
         const double dens = exp((a - 1.0) * log(b) - b - lga);
         double nb = b - f / dens;
         if (!(nb > lo && nb < hi)) nb = 0.5 * (lo + hi);
-        const bool done = fabs(nb - b) <= 1e-14 * b;
+        const bool done = fabs(nb - b) <= 1e-13 * b;
         b = nb;
-        if (done || hi - lo <= 1e-15 * b) break;
+        if (done || hi - lo <= 1e-14 * b) break;
     }
     return b;
 }
@@ -125,104 +153,15 @@ __device__ __forceinline__ double amp_of(const Structure& S, const double* p, in
     return S.kinds[k] == GF_SKY ? p[S.slot0[k]] : p[S.slot0[k] + 2];
 }
 
-__device__ double sky_of(const Structure& S, const double* p)
+__device__ __forceinline__ double sky_of(const Structure& S, const double* p)
 {
     return S.sky_slot >= 0 ? p[S.sky_slot] : 0.0;
-}
-
-// the model channel (sky and all components) at p
-__device__ void build_sum(const Structure& S, const double* p, Channel& ch)
-{
-    ch.type = CH_SUM;
-    ch.comp = 0;
-    ch.jcol = -1;
-    ch.mweight = 1.0f;
-    ch.scale = 0.0f;
-    ch.sky = (float)sky_of(S, p);
-    ch.ncomp = S.ncomp;
-    ch.msky = 0.0f;
-    for (int k = 0; k < S.ncomp; ++k) {
-        const double bn = S.kinds[k] == GF_SERSIC ? sersic_bn(p[S.slot0[k] + 4]) : 0.0;
-        ch.cc[k] = make_cc(S.kinds[k], p + S.slot0[k], false, bn);
-    }
-    ch.pert = ch.cc[0];
 }
 
 // FD step of slot s at value v: positions fd_rel pixels, others fd_rel*max(|v|,1)
 __device__ __forceinline__ double fd_step(int role, double v, double fd_rel)
 {
     return role == R_POS ? fd_rel : fd_rel * fmax(fabs(v), 1.0);
-}
-
-// Jacobian-pass channels at p: one unit-amplitude shape per profile component
-// (its convolution is the exact amplitude column and, weighted by the
-// amplitude, its share of the model), then one FD channel per free nonlinear
-// slot.  Returns the channel count.
-__device__ int build_jac(const Structure& S, const double* p, double fd_rel, float psum,
-                         Channel* out)
-{
-    CompConst unit[GF_MAX_COMP];
-    double bnk[GF_MAX_COMP];
-    for (int k = 0; k < S.ncomp; ++k) {
-        bnk[k] = S.kinds[k] == GF_SERSIC ? sersic_bn(p[S.slot0[k] + 4]) : 0.0;
-        unit[k] = make_cc(S.kinds[k], p + S.slot0[k], true, bnk[k]);
-    }
-    int nc = 0;
-    const double sky = sky_of(S, p);
-    for (int k = 0; k < S.ncomp; ++k) {
-        if (S.kinds[k] == GF_SKY) continue;
-        Channel& ch = out[nc++];
-        ch.type = CH_SHAPE;
-        ch.comp = k;
-        ch.jcol = -1;
-        for (int f = 0; f < S.nfree; ++f)
-            if (S.freeslot[f] == S.slot0[k] + 2) ch.jcol = f;
-        ch.mweight = (float)amp_of(S, p, k);
-        ch.scale = 0.0f;
-        ch.sky = 0.0f;
-        ch.ncomp = S.ncomp;
-        ch.msky = 0.0f;
-        for (int kk = 0; kk < S.ncomp; ++kk) ch.cc[kk] = unit[kk];
-        ch.pert = unit[k];
-    }
-    double pp[GF_MAX_SLOTS];
-    for (int s = 0; s < S.nslots; ++s) pp[s] = p[s];
-    for (int f = 0; f < S.nfree; ++f) {
-        const int s = S.freeslot[f], role = S.role[s], k = S.owner[s];
-        if (role == R_AMP || role == R_SKY) continue;
-        const double h = fd_step(role, p[s], fd_rel);
-        Channel& ch = out[nc++];
-        ch.type = CH_FD;
-        ch.comp = k;
-        ch.jcol = f;
-        ch.mweight = 0.0f;
-        ch.scale = (float)(amp_of(S, p, k) / h);
-        ch.sky = 0.0f;
-        ch.ncomp = S.ncomp;
-        ch.msky = 0.0f;
-        for (int kk = 0; kk < S.ncomp; ++kk) ch.cc[kk] = unit[kk];
-        pp[s] = p[s] + h;
-        const double bn = role == R_N ? sersic_bn(pp[s]) : bnk[k];
-        ch.pert = make_cc(S.kinds[k], pp + S.slot0[k], true, bn);
-        pp[s] = p[s];
-    }
-    out[0].msky = (float)(sky * (double)psum);
-    return nc;
-}
-
-__device__ void project(const Structure& S, double* p)
-{
-    for (int s = 0; s < S.nslots; ++s) {
-        if (S.role[s] == R_PA) {
-            double a = fmod(p[s], 180.0);
-            if (a < 0.0) a += 180.0;
-            if (a >= 180.0) a -= 180.0;
-            p[s] = a;
-            continue;
-        }
-        if (p[s] < S.lo[s]) p[s] = S.lo[s];
-        if (p[s] > S.hi[s]) p[s] = S.hi[s];
-    }
 }
 
 __device__ __forceinline__ double xtol_scale(int role)
@@ -232,77 +171,185 @@ __device__ __forceinline__ double xtol_scale(int role)
     return 1.0;
 }
 
-// ---------------------------------------------------------------- kernels
-
-__global__ void k_prep_sum(PassArgs a, const double* params, int use_trial)
+__device__ void project_slot(const Structure& S, double* p, int s)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= a.count) return;
-    if (a.lm && a.lm[b].phase != a.phase) return;
-    const Structure& S = *a.S;
-    const double* p = params ? params + (long long)b * S.nslots
-                             : (use_trial ? a.lm[b].pt : a.lm[b].p);
-    Channel* ch = const_cast<Channel*>(a.chan) + (long long)b * a.chan_stride;
-    build_sum(S, p, ch[0]);
+    if (S.role[s] == R_PA) {
+        double a = fmod(p[s], 180.0);
+        if (a < 0.0) a += 180.0;
+        if (a >= 180.0) a -= 180.0;
+        p[s] = a;
+        return;
+    }
+    if (p[s] < S.lo[s]) p[s] = S.lo[s];
+    if (p[s] > S.hi[s]) p[s] = S.hi[s];
 }
 
-// one thread per stamp
-__global__ void k_prep_jac(PassArgs a, const double* params)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= a.count) return;
-    if (a.lm && a.lm[b].phase != a.phase) return;
-    const Structure& S = *a.S;
-    const double* p = params ? params + (long long)b * S.nslots : a.lm[b].p;
-    Channel* ch = const_cast<Channel*>(a.chan) + (long long)b * a.chan_stride;
-    build_jac(S, p, S.opts.fd_rel, a.psf_sum[b], ch);
-}
+// per-warp scratch in shared memory
+struct WarpScratch {
+    double M[GF_MAX_FREE * GF_MAX_FREE];
+    double r[GF_MAX_FREE];
+    double p[GF_MAX_SLOTS];
+    double bn[GF_MAX_COMP];
+    double bnp[GF_MAX_COMP];  // b_n at n + h (FD channel of a free n)
+    CompConst cc[GF_MAX_COMP];
+    int ok;
+};
 
-__global__ void k_lm_init(int count, const Structure* Sp, LMState* lm, const double* p0)
+// b_n of every Sersic component at W.p (warm start from the stamp's cache when
+// one is given), and at n + h when want_pert and the n slot is free
+__device__ void warp_bn(const Structure& S, WarpScratch& W, LMState* L, bool want_pert)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= count) return;
-    const Structure& S = *Sp;
-    LMState& L = lm[b];
-    for (int s = 0; s < S.nslots; ++s) L.p[s] = L.pt[s] = p0[(long long)b * S.nslots + s];
-    project(S, L.p);
-    L.chi2 = INFINITY;
-    L.chi2t = INFINITY;
-    L.lambda = S.opts.lambda0;
-    L.iters = 0;
-    L.accepted = 0;
-    L.status = GF_EMAXITER;
-    L.phase = PH_NEED_JAC;
-}
-
-// Cholesky solve of the SPD system M x = r in place (n <= GF_MAX_FREE)
-__device__ bool cholesky_solve(int n, double* M, double* r)
-{
-    for (int j = 0; j < n; ++j) {
-        double d = M[j * n + j];
-        for (int k = 0; k < j; ++k) d -= M[j * n + k] * M[j * n + k];
-        if (!(d > 0.0) || !isfinite(d)) return false;
-        d = sqrt(d);
-        M[j * n + j] = d;
-        for (int i = j + 1; i < n; ++i) {
-            double s = M[i * n + j];
-            for (int k = 0; k < j; ++k) s -= M[i * n + k] * M[j * n + k];
-            M[i * n + j] = s / d;
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < S.ncomp; ++k) {
+        if (S.kinds[k] != GF_SERSIC) continue;
+        const int sn = S.slot0[k] + 4;
+        const double n = W.p[sn];
+        double guess = -1.0;
+        if (L && L->bn_n[k] > 0.0) guess = L->bn_b[k] + 2.0 * (n - L->bn_n[k]);
+        const double b = sersic_bn_warp(n, guess);
+        __syncwarp();
+        if (lane == 0) {
+            W.bn[k] = b;
+            if (L) {
+                L->bn_n[k] = n;
+                L->bn_b[k] = b;
+            }
+        }
+        if (want_pert) {
+            bool free_n = false;
+            for (int f = 0; f < S.nfree; ++f) free_n |= (S.freeslot[f] == sn);
+            if (free_n) {
+                const double h = fd_step(R_N, n, S.opts.fd_rel);
+                const double bp = sersic_bn_warp(n + h, b + 2.0 * h);
+                if (lane == 0) W.bnp[k] = bp;
+            }
         }
     }
-    for (int i = 0; i < n; ++i) {
-        double s = r[i];
-        for (int k = 0; k < i; ++k) s -= M[i * n + k] * r[k];
-        r[i] = s / M[i * n + i];
+    __syncwarp();
+}
+
+// the model channel (sky and all components) at W.p; lanes build components
+__device__ void warp_build_sum(const Structure& S, WarpScratch& W, Channel* out)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < S.ncomp) {
+        const int k = lane;
+        out->cc[k] = make_cc(S.kinds[k], W.p + S.slot0[k], false, W.bn[k]);
+        if (k == 0) out->pert = out->cc[0];
     }
-    for (int i = n - 1; i >= 0; --i) {
-        double s = r[i];
-        for (int k = i + 1; k < n; ++k) s -= M[k * n + i] * r[k];
-        r[i] = s / M[i * n + i];
+    if (lane == 0) {
+        out->type = CH_SUM;
+        out->comp = 0;
+        out->jcol = -1;
+        out->mweight = 1.0f;
+        out->scale = 0.0f;
+        out->sky = (float)sky_of(S, W.p);
+        out->ncomp = S.ncomp;
+        out->msky = 0.0f;
     }
-    for (int i = 0; i < n; ++i)
-        if (!isfinite(r[i])) return false;
-    return true;
+}
+
+// Jacobian-pass channels at W.p: one unit-amplitude shape per profile component
+// (its convolution is the exact amplitude column and, weighted by the
+// amplitude, its share of the model), then one FD channel per free nonlinear
+// slot.  Lane c builds channel c.
+__device__ void warp_build_jac(const Structure& S, WarpScratch& W, float psum, Channel* out)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < S.ncomp) W.cc[lane] = make_cc(S.kinds[lane], W.p + S.slot0[lane], true, W.bn[lane]);
+    __syncwarp();
+    for (int c = lane; c < S.nchan; c += 32) {
+        // identify channel c
+        int type = CH_SHAPE, comp = -1, slot = -1, jcol = -1;
+        int idx = 0;
+        for (int k = 0; k < S.ncomp && comp < 0; ++k) {
+            if (S.kinds[k] == GF_SKY) continue;
+            if (idx == c) comp = k;
+            ++idx;
+        }
+        if (comp >= 0) {
+            for (int f = 0; f < S.nfree; ++f)
+                if (S.freeslot[f] == S.slot0[comp] + 2) jcol = f;
+        } else {
+            type = CH_FD;
+            for (int f = 0; f < S.nfree && slot < 0; ++f) {
+                const int s = S.freeslot[f];
+                if (S.role[s] == R_AMP || S.role[s] == R_SKY) continue;
+                if (idx == c) {
+                    slot = s;
+                    jcol = f;
+                }
+                ++idx;
+            }
+            comp = S.owner[slot];
+        }
+        Channel& ch = out[c];
+        ch.type = type;
+        ch.comp = comp;
+        ch.jcol = jcol;
+        ch.sky = 0.0f;
+        ch.ncomp = S.ncomp;
+        ch.msky = c == 0 ? (float)(sky_of(S, W.p) * (double)psum) : 0.0f;
+        for (int k = 0; k < S.ncomp; ++k) ch.cc[k] = W.cc[k];
+        if (type == CH_SHAPE) {
+            ch.mweight = (float)amp_of(S, W.p, comp);
+            ch.scale = 0.0f;
+            ch.pert = W.cc[comp];
+        } else {
+            const int role = S.role[slot];
+            const double h = fd_step(role, W.p[slot], S.opts.fd_rel);
+            double q[8];
+            const int ns = S.kinds[comp] == GF_SERSIC ? 8 : 7;
+            for (int t = 0; t < ns; ++t) q[t] = W.p[S.slot0[comp] + t];
+            q[slot - S.slot0[comp]] += h;
+            ch.mweight = 0.0f;
+            ch.scale = (float)(amp_of(S, W.p, comp) / h);
+            ch.pert = make_cc(S.kinds[comp], q, true, role == R_N ? W.bnp[comp] : W.bn[comp]);
+        }
+    }
+}
+
+// Warp Cholesky of the SPD n x n matrix W.M (lower factor in place) and the
+// solve of M x = W.r (x in W.r).  Returns false (uniformly) when a pivot is not
+// positive or a result is not finite.
+__device__ bool warp_cholesky_solve(int n, WarpScratch& W)
+{
+    const int lane = threadIdx.x & 31;
+    double* M = W.M;
+    for (int j = 0; j < n; ++j) {
+        __syncwarp();
+        const double djj = M[j * n + j];
+        if (!(djj > 0.0) || !isfinite(djj)) return false;
+        const double d = sqrt(djj);
+        __syncwarp();
+        for (int i = j + 1 + lane; i < n; i += 32) M[i * n + j] /= d;
+        if (lane == 0) M[j * n + j] = d;
+        __syncwarp();
+        const int m = n - j - 1;
+        for (int t = lane; t < m * m; t += 32) {
+            const int i = j + 1 + t / m, k = j + 1 + t % m;
+            if (k <= i) M[i * n + k] -= M[i * n + j] * M[k * n + j];
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        double* r = W.r;
+        bool ok = true;
+        for (int i = 0; i < n; ++i) {
+            double s = r[i];
+            for (int k = 0; k < i; ++k) s -= M[i * n + k] * r[k];
+            r[i] = s / M[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = r[i];
+            for (int k = i + 1; k < n; ++k) s -= M[k * n + i] * r[k];
+            r[i] = s / M[i * n + i];
+        }
+        for (int i = 0; i < n; ++i) ok = ok && isfinite(r[i]);
+        W.ok = ok;
+    }
+    __syncwarp();
+    return W.ok != 0;
 }
 
 __device__ void lm_reject(const Structure& S, LMState& L)
@@ -324,75 +371,224 @@ __device__ void lm_check_iters(const Structure& S, LMState& L)
     }
 }
 
-__global__ void k_lm_solve(PassArgs a, Channel* trial_chan, int trial_stride)
+// ---------------------------------------------------------------- kernels
+
+// the call's Structure, copied into shared memory by the whole block (the
+// per-stamp code walks its tables in dependent chains: slot -> role -> value)
+__device__ __forceinline__ void load_structure(Structure* dst, const Structure* src)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= a.count) return;
-    LMState& L = a.lm[b];
-    if (L.phase != PH_SOLVE) return;
-    const Structure& S = *a.S;
-    const int nf = S.nfree;
-    bool finite = isfinite(L.chi2);
-    for (int i = 0; i < nf && finite; ++i) finite = isfinite(L.g[i]) && isfinite(L.A[i * nf + i]);
-    if (!finite) {
-        L.status = GF_ENONFINITE;
-        L.phase = PH_DONE;
-        return;
-    }
-    double M[GF_MAX_FREE * GF_MAX_FREE], r[GF_MAX_FREE];
-    for (int i = 0; i < nf; ++i) {
-        r[i] = L.g[i];
-        for (int j = 0; j < nf; ++j) M[i * nf + j] = L.A[i * nf + j];
-    }
-    for (int i = 0; i < nf; ++i) {
-        const double d = L.A[i * nf + i];
-        if (d > 0.0) {
-            M[i * nf + i] = d * (1.0 + L.lambda);
-        } else {
-            // a slot with no influence on the model is held this step
-            for (int j = 0; j < nf; ++j) M[i * nf + j] = M[j * nf + i] = 0.0;
-            M[i * nf + i] = 1.0;
-            r[i] = 0.0;
-        }
-    }
-    L.iters++;
-    if (!cholesky_solve(nf, M, r)) {
-        lm_reject(S, L);
-        lm_check_iters(S, L);
-        return;
-    }
-    double step = 0.0;
-    for (int i = 0; i < nf; ++i) {
-        const int s = S.freeslot[i];
-        step = fmax(step, fabs(r[i]) / fmax(fabs(L.p[s]), xtol_scale(S.role[s])));
-    }
-    if (step < S.opts.xtol) {
-        L.status = GF_OK;
-        L.phase = PH_DONE;
-        return;
-    }
-    for (int s = 0; s < S.nslots; ++s) L.pt[s] = L.p[s];
-    for (int i = 0; i < nf; ++i) L.pt[S.freeslot[i]] += r[i];
-    project(S, L.pt);
-    build_sum(S, L.pt, trial_chan[(long long)b * trial_stride]);
-    L.phase = PH_TRIAL;
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(Structure) / sizeof(int)); i += blockDim.x)
+        d[i] = s[i];
 }
 
-__global__ void k_lm_update(PassArgs a, int* active)
+#define WARP_STAMP()                                                          \
+    __shared__ WarpScratch scratch[kWarpsPerBlock];                           \
+    __shared__ Structure S_sh;                                                \
+    load_structure(&S_sh, a.S);                                               \
+    __syncthreads();                                                          \
+    const Structure& S = S_sh;                                                \
+    const int lane = threadIdx.x & 31;                                        \
+    const int b = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);           \
+    if (b >= a.count) return;                                                 \
+    WarpScratch& W = scratch[threadIdx.x >> 5];
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prep_sum(PassArgs a, const double* params,
+                                                                  int use_trial)
+{
+    WARP_STAMP();
+    if (a.lm && a.lm[b].phase != a.phase) return;
+    const double* p = params ? params + (long long)b * S.nslots
+                             : (use_trial ? a.lm[b].pt : a.lm[b].p);
+    for (int s = lane; s < S.nslots; s += 32) W.p[s] = p[s];
+    __syncwarp();
+    warp_bn(S, W, a.lm ? &a.lm[b] : nullptr, false);
+    warp_build_sum(S, W, const_cast<Channel*>(a.chan) + (long long)b * a.chan_stride);
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prep_jac(PassArgs a, const double* params)
+{
+    WARP_STAMP();
+    if (a.lm && a.lm[b].phase != a.phase) return;
+    const double* p = params ? params + (long long)b * S.nslots : a.lm[b].p;
+    for (int s = lane; s < S.nslots; s += 32) W.p[s] = p[s];
+    __syncwarp();
+    warp_bn(S, W, a.lm ? &a.lm[b] : nullptr, true);
+    warp_build_jac(S, W, a.psf_sum[b], const_cast<Channel*>(a.chan) + (long long)b * a.chan_stride);
+}
+
+__global__ void k_lm_init(int count, const Structure* Sp, LMState* lm, const double* p0)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= a.count) return;
+    if (b >= count) return;
+    const Structure& S = *Sp;
+    LMState& L = lm[b];
+    for (int s = 0; s < S.nslots; ++s) L.p[s] = L.pt[s] = p0[(long long)b * S.nslots + s];
+    for (int s = 0; s < S.nslots; ++s) project_slot(S, L.p, s);
+    for (int k = 0; k < GF_MAX_COMP; ++k) L.bn_n[k] = L.bn_b[k] = 0.0;
+    L.chi2 = INFINITY;
+    L.chi2t = INFINITY;
+    L.lambda = S.opts.lambda0;
+    L.iters = 0;
+    L.accepted = 0;
+    L.status = GF_EMAXITER;
+    L.phase = PH_NEED_JAC;
+}
+
+// One block per stamp.  Stamps whose Jacobian pass just ran (PH_NEED_JAC) first
+// sum that pass's reduction partials in block order into A, g and chi^2; then
+// warp 0 of every stamp in PH_SOLVE solves the damped system, applies the
+// finishing tests on the step, and builds the trial model channel.  Block 0
+// also resets the active-stamp counter that k_final_update fills.
+__global__ void __launch_bounds__(FINAL_THREADS) k_final_solve(PassArgs a, Channel* trial_chan,
+                                                                int* active)
+{
+    __shared__ Structure S_sh;
+    __shared__ WarpScratch W;
+    load_structure(&S_sh, a.S);
+    const int b = blockIdx.x;
+    if (b == 0 && threadIdx.x == 0 && active) *active = 0;
     LMState& L = a.lm[b];
+    int phase = L.phase;
+    __syncthreads();
+    const Structure& S = S_sh;
+    const int nf = S.nfree;
+    if (phase == PH_NEED_JAC) {
+        const int b0 = a.pre_red[b], b1 = a.pre_red[b + 1];
+        for (int t = threadIdx.x; t < a.nacc; t += blockDim.x) {
+            CSum acc = {0.0f, 0.0f};
+            for (int k = b0; k < b1; ++k) csum_add(acc, a.partial[(long long)k * a.nacc + t]);
+            const double v = (double)acc.s + (double)acc.c;
+            int i, j;
+            const int kind = decode_acc(t, nf, i, j);
+            if (kind == 0) {
+                L.A[i * nf + j] = v;
+                L.A[j * nf + i] = v;
+            } else if (kind == 1) {
+                L.g[i] = v;
+            } else {
+                L.chi2 = v;
+            }
+        }
+        __syncthreads();
+        phase = PH_SOLVE;
+        if (threadIdx.x == 0) L.phase = PH_SOLVE;
+    }
+    if (phase != PH_SOLVE || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    bool fin = true;
+    for (int i = lane; i < nf; i += 32) fin = fin && isfinite(L.g[i]) && isfinite(L.A[i * nf + i]);
+    const bool finite = __all_sync(kFull, fin) && isfinite(L.chi2);
+    if (!finite) {
+        __syncwarp();
+        if (lane == 0) {
+            L.status = GF_ENONFINITE;
+            L.phase = PH_DONE;
+        }
+        return;
+    }
+    // damped system (A + lambda diag A) delta = g; a slot with A_ii = 0 is held
+    const double lam = L.lambda;
+    for (int t = lane; t < nf * nf; t += 32) {
+        const int i = t / nf, j = t % nf;
+        const double aii = L.A[i * nf + i], ajj = L.A[j * nf + j];
+        double v = L.A[t];
+        if (!(aii > 0.0) || !(ajj > 0.0))
+            v = (i == j) ? 1.0 : 0.0;
+        else if (i == j)
+            v = aii * (1.0 + lam);
+        W.M[t] = v;
+    }
+    for (int i = lane; i < nf; i += 32) W.r[i] = (L.A[i * nf + i] > 0.0) ? L.g[i] : 0.0;
+    const bool ok = warp_cholesky_solve(nf, W);
+    const int iters = L.iters + 1;
+    __syncwarp();
+    if (lane == 0) L.iters = iters;
+    if (!ok) {
+        if (lane == 0) {
+            lm_reject(S, L);
+            lm_check_iters(S, L);
+        }
+        return;
+    }
+    // scaled step and predicted fall of chi^2 for the damped step,
+    // delta^T (g + lambda diag(A) delta), as warp reductions
+    double step = 0.0, pred = 0.0;
+    for (int i = lane; i < nf; i += 32) {
+        const int s = S.freeslot[i];
+        step = fmax(step, fabs(W.r[i]) / fmax(fabs(L.p[s]), xtol_scale(S.role[s])));
+        const double aii = L.A[i * nf + i];
+        if (aii > 0.0) pred += W.r[i] * (L.g[i] + lam * aii * W.r[i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        step = fmax(step, __shfl_xor_sync(kFull, step, o));
+        pred += __shfl_xor_sync(kFull, pred, o);
+    }
+    if (step < S.opts.xtol) {
+        if (lane == 0) {
+            L.status = GF_OK;
+            L.phase = PH_DONE;
+        }
+        return;
+    }
+    for (int s = lane; s < S.nslots; s += 32) W.p[s] = L.p[s];
+    __syncwarp();
+    for (int i = lane; i < nf; i += 32) W.p[S.freeslot[i]] += W.r[i];
+    __syncwarp();
+    for (int s = lane; s < S.nslots; s += 32) {
+        project_slot(S, W.p, s);
+        L.pt[s] = W.p[s];
+    }
+    __syncwarp();
+    warp_bn(S, W, &L, false);
+    warp_build_sum(S, W, trial_chan + b);
+    __syncwarp();
+    if (lane == 0) {
+        L.pred = pred;
+        L.phase = PH_TRIAL;
+    }
+}
+
+// One block per stamp: stamps in PH_TRIAL sum the trial pass's partials into
+// chi^2 at the trial point (deterministic tree) and accept or reject it; every
+// stamp not yet done adds one to the active counter.
+__global__ void __launch_bounds__(RED_THREADS) k_final_update(PassArgs a, int* active)
+{
+    __shared__ CSum wsum[RED_THREADS / 32];
+    const int b = blockIdx.x;
+    LMState& L = a.lm[b];
+    const int phase = L.phase;
+    if (phase == PH_TRIAL) {
+        const int b0 = a.pre_red[b], b1 = a.pre_red[b + 1];
+        CSum acc = {0.0f, 0.0f};
+        for (int k = b0 + threadIdx.x; k < b1; k += RED_THREADS) csum_add(acc, a.partial[k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            CSum other;
+            other.s = __shfl_down_sync(kFull, acc.s, o);
+            other.c = __shfl_down_sync(kFull, acc.c, o);
+            acc = csum_merge(acc, other);
+        }
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
     const Structure& S = *a.S;
-    if (L.phase == PH_TRIAL) {
-        const double xt = L.chi2t;
+    if (phase == PH_TRIAL) {
+        CSum t = wsum[0];
+        for (int w = 1; w < RED_THREADS / 32; ++w) t = csum_merge(t, wsum[w]);
+        const double xt = (double)t.s + (double)t.c;
+        L.chi2t = xt;
         if (isfinite(xt) && xt < L.chi2) {
             const double rel = (L.chi2 - xt) / L.chi2;
+            const double prel = L.pred / L.chi2;
             for (int s = 0; s < S.nslots; ++s) L.p[s] = L.pt[s];
             L.accepted++;
             L.lambda = fmax(L.lambda * S.opts.lambda_down, S.opts.lambda_min);
             L.chi2 = xt;
-            if (rel < S.opts.ftol) {
+            if (rel < S.opts.ftol && prel < S.opts.ftol) {
                 L.status = GF_OK;
                 L.phase = PH_DONE;
             } else {
@@ -406,46 +602,6 @@ __global__ void k_lm_update(PassArgs a, int* active)
     if (active && L.phase != PH_DONE) atomicAdd(active, 1);
 }
 
-}  // namespace
-
-cudaError_t launch_prep_sum(const PassArgs& a, const double* params, int use_trial,
-                            cudaStream_t s)
-{
-    k_prep_sum<<<(a.count + 63) / 64, 64, 0, s>>>(a, params, use_trial);
-    GF_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_prep_jac(const PassArgs& a, const double* params, cudaStream_t s)
-{
-    k_prep_jac<<<(a.count + 63) / 64, 64, 0, s>>>(a, params);
-    GF_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_lm_init(int count, const Structure* S, LMState* lm, const double* p0,
-                           cudaStream_t s)
-{
-    k_lm_init<<<(count + 127) / 128, 128, 0, s>>>(count, S, lm, p0);
-    GF_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_lm_solve(const PassArgs& a, Channel* trial_chan, cudaStream_t s)
-{
-    k_lm_solve<<<(a.count + 63) / 64, 64, 0, s>>>(a, trial_chan, 1);
-    GF_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_lm_update(const PassArgs& a, int* active_count, cudaStream_t s)
-{
-    k_lm_update<<<(a.count + 127) / 128, 128, 0, s>>>(a, active_count);
-    GF_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
-namespace {
 // compact per-stamp results: p[nslots], chi2, lambda, iters, accepted, status
 __global__ void k_lm_export(int count, const Structure* Sp, const LMState* lm, double* out)
 {
@@ -461,7 +617,48 @@ __global__ void k_lm_export(int count, const Structure* Sp, const LMState* lm, d
     o[ns + 3] = L.accepted;
     o[ns + 4] = L.status;
 }
+
+inline int warp_blocks(int count) { return (count + kWarpsPerBlock - 1) / kWarpsPerBlock; }
+
 }  // namespace
+
+cudaError_t launch_prep_sum(const PassArgs& a, const double* params, int use_trial,
+                            cudaStream_t s)
+{
+    k_prep_sum<<<warp_blocks(a.count), kWarpsPerBlock * 32, 0, s>>>(a, params, use_trial);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_jac(const PassArgs& a, const double* params, cudaStream_t s)
+{
+    k_prep_jac<<<warp_blocks(a.count), kWarpsPerBlock * 32, 0, s>>>(a, params);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lm_init(int count, const Structure* S, LMState* lm, const double* p0,
+                           cudaStream_t s)
+{
+    k_lm_init<<<(count + 127) / 128, 128, 0, s>>>(count, S, lm, p0);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_solve(const PassArgs& a, Channel* trial_chan, int* active,
+                               cudaStream_t s)
+{
+    k_final_solve<<<a.count, FINAL_THREADS, 0, s>>>(a, trial_chan, active);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_update(const PassArgs& a, int* active_count, cudaStream_t s)
+{
+    k_final_update<<<a.count, RED_THREADS, 0, s>>>(a, active_count);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_lm_export(int count, const Structure* S, const LMState* lm, double* out,
                              cudaStream_t s)

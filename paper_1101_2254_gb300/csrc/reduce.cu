@@ -34,29 +34,6 @@ __device__ __forceinline__ void load_chan_info(ChanInfo& ci, float& msky, const 
     if (threadIdx.x == 0) msky = c[0].msky;
 }
 
-// decode accumulator index t into (kind, i, j): 0 = A_ij (i <= j), 1 = g_i, 2 = chi^2
-__device__ __forceinline__ int decode_acc(int t, int nf, int& i, int& j)
-{
-    const int npair = nf * (nf + 1) / 2;
-    if (t < npair) {
-        int row = 0, rem = t;
-        while (rem >= nf - row) {
-            rem -= nf - row;
-            ++row;
-        }
-        i = row;
-        j = row + rem;
-        return 0;
-    }
-    if (t < npair + nf) {
-        i = t - npair;
-        j = 0;
-        return 1;
-    }
-    i = j = 0;
-    return 2;
-}
-
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
 {
     __shared__ float Jt[GF_MAX_FREE][RED_THREADS];
@@ -202,13 +179,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_final_jac(PassArgs a, double* A
     }
 }
 
-__global__ void k_final_jac_phase(PassArgs a)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= a.count) return;
-    if (a.lm[b].phase == a.phase) a.lm[b].phase = PH_SOLVE;
-}
-
 __global__ void __launch_bounds__(RED_THREADS) k_final_chi2(PassArgs a, double* chi2_out)
 {
     __shared__ CSum wsum[RED_THREADS / 32];
@@ -291,10 +261,6 @@ cudaError_t launch_final_jac(const PassArgs& a, double* A_out, double* g_out, do
 {
     k_final_jac<<<a.count, RED_THREADS, 0, s>>>(a, A_out, g_out, chi2_out);
     GF_COUNT_LAUNCH();
-    if (a.lm) {
-        k_final_jac_phase<<<(a.count + 255) / 256, 256, 0, s>>>(a);
-        GF_COUNT_LAUNCH();
-    }
     return cudaGetLastError();
 }
 

@@ -7,7 +7,9 @@ generators); never the CUDA path.
 stamp512.json: the oracle's LM fit of the 512x512 bulge + disk + sky stamp
 (Moffat 65x65 PSF, 10x10 oversampling in the central 20x20, 15 free slots),
 started from the 20 %-perturbed guess, with the oracle's FFT convolution, plus
-the per-call CPU times of its Jacobian and of one evaluation.
+the statistical errors of the free parameters at the solution
+(sqrt of the diagonal of the inverse normal matrix), and the per-call CPU
+times of its Jacobian and of one evaluation.
 """
 import json
 import os
@@ -39,10 +41,14 @@ def stamp512():
     p, res = oracle.lm_fit(d, p0, st.fixed, st.psf, img, sig, method=1)
     t_fit = time.perf_counter() - t0
     x_true, _ = oracle.evaluate(d, st.params, st.psf, img, sig, method=1)
+    # statistical errors of the free parameters at the solution: sqrt diag (J^T W J)^-1
+    jac = oracle.jacobian(d, p, st.fixed, st.psf, img, sig, method=1)
+    sigma = np.sqrt(np.diag(np.linalg.inv(jac["A"])))
     out = dict(workload="stamp512", method="fft", params=p.tolist(), guess=p0.tolist(),
                truth=st.params.tolist(), fixed=st.fixed.tolist(), chi2=res["chi2"],
                chi2_truth=x_true, iters=res["iters"], accepted=res["accepted"],
-               status=res["status"], cpu_s_fit=t_fit, cpu_s_jacobian=t_jac, cpu_s_eval=t_eval,
+               status=res["status"], sigma_free=sigma.tolist(), cpu_s_fit=t_fit,
+               cpu_s_jacobian=t_jac, cpu_s_eval=t_eval,
                threads=1, note="oracle LM, default oracle options (ftol=xtol=1e-8)")
     with open(os.path.join(HERE, "stamp512.json"), "w") as fh:
         json.dump(out, fh, indent=1)
