@@ -36,7 +36,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fits/s to oracle chi2 (512x512 bulge+disk+sky, Moffat 65x65 PSF, 15-param LM)"
 METRIC64 = "fits/s to oracle chi2 (64x64 Sersic+sky, Gaussian 25x25 PSF, 8-param LM)"
+METRICB = ("fits/s to oracle chi2 (4096 Sersic+sky stamps, sides 32-256, Moffat 33x33, "
+           "8-param batched LM)")
 L2_FLUSH_BYTES = 256 << 20
+BENCH_TOL = 1e-6  # LM ftol and xtol of the timed fits
 
 
 def parse():
@@ -45,7 +48,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gf", choices=["gf", "reference"])
-    ap.add_argument("--workload", default="stamp512", choices=["stamp512", "stamp64"])
+    ap.add_argument("--workload", default="stamp512",
+                    choices=["stamp512", "stamp64", "batch4096"])
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (for profiler runs)")
     return ap.parse_args()
@@ -163,8 +167,12 @@ def run_gf(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # the metric counts fits that reach the oracle's chi^2; ftol = xtol = 1e-6
+    # does (tests/test_gpu_parity.py checks it on this stamp)
+    opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL)
+
     def fit():
-        return gf.lm_fit(d, p0, st.fixed, img_d, sig_d, psf_d, ws=ws)
+        return gf.lm_fit(d, p0, st.fixed, img_d, sig_d, psf_d, opts=opts, ws=ws)
 
     for _ in range(max(args.warmup, 0)):
         p, res = fit()
@@ -220,7 +228,7 @@ def run_gf(args):
         img_e.copy_(img_p, non_blocking=True)
         sig_e.copy_(sig_p, non_blocking=True)
         psf_e.copy_(psf_p, non_blocking=True)
-        pe, re_ = gf.lm_fit(d, p0, st.fixed, img_e, sig_e, psf_e, ws=ws)
+        pe, re_ = gf.lm_fit(d, p0, st.fixed, img_e, sig_e, psf_e, opts=opts, ws=ws)
         e1.record(stream)
         e1.synchronize()
         if k > 0:
@@ -269,7 +277,7 @@ def run_gf(args):
         "config": {"workload": args.workload, "stamp": [st.H, st.W], "psf": st.P,
                    "components": "sersic+expdisk+sky" if args.workload == "stamp512"
                    else "sersic+sky", "free_params": st.nfree,
-                   "oversampling": [st.os_factor, st.os_box],
+                   "oversampling": [st.os_factor, st.os_box], "lm_tol": BENCH_TOL,
                    "conv": "fft" if st.P >= 41 else "direct",
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "parallelism": f"replicas{ws_}"},
@@ -291,6 +299,131 @@ def run_gf(args):
         print(json.dumps(line), flush=True)
     if ws_ > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ batch arm
+def run_batch(args):
+    """4096 uneven single-Sersic stamps fitted together by gf_lm_fit_batch."""
+    import torch
+    import torch.distributed as dist
+    ws_, rank, local = dist_env()
+    if ws_ > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1101_2254_gb300 import build, gf, synth
+    build.build()
+    sts = synth.batch_stamps(4096)
+    s0 = sts[0]
+    imgs, sigs, psfs, Hs, Ws, p0 = [], [], [], [], [], []
+    for st in sts:
+        d1 = gf.make_desc(st.H, st.W, st.P, st.kinds, st.os_factor, st.os_box)
+        psf_d = torch.as_tensor(st.psf).to(dev)
+        m = gf.convolve(d1, gf.model(d1, st.params), psf_d).cpu().numpy()
+        img, sig = synth.add_noise(m, st.noise_seed)
+        imgs.append(img.ravel()); sigs.append(sig.ravel()); psfs.append(st.psf.ravel())
+        Hs.append(st.H); Ws.append(st.W); p0.append(st.guess())
+    img_p = torch.as_tensor(np.concatenate(imgs)).pin_memory()
+    sig_p = torch.as_tensor(np.concatenate(sigs)).pin_memory()
+    psf_p = torch.as_tensor(np.concatenate(psfs)).pin_memory()
+    img_d, sig_d, psf_d = img_p.to(dev), sig_p.to(dev), psf_p.to(dev)
+    p0 = np.array(p0)
+    d = gf.make_desc(1, 1, s0.P, s0.kinds, s0.os_factor, 8)
+    batch = gf.make_batch(Hs, Ws, psf_size=s0.P)
+    ws = gf.Workspace(device=dev)
+    stream = torch.cuda.current_stream()
+
+    opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL)
+
+    def fit():
+        return gf.lm_fit_batch(d, batch, p0, s0.fixed, img_d, sig_d, psf_d, opts=opts, ws=ws)
+
+    for _ in range(max(args.warmup, 0)):
+        fit()
+    torch.cuda.synchronize()
+    if ws_ > 1:
+        dist.barrier()
+    step_ms, res = [], None
+    with ClockSampler(local) as clk:
+        launches0 = gf.launch_count()
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pb, res = fit()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        launches = gf.launch_count() - launches0
+    total_ms = float(sum(step_ms))
+    if ws_ > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = len(sts) * args.steps * ws_ / (total_ms / 1e3)
+    with gf.Profiler() as prof:
+        fit()
+    pr = prof.result
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    ach = pr["conv"]["work"] / (pr["conv"]["ms"] / 1e3) / 1e12
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    iters = np.array([r["iters"] for r in res])
+    status = np.array([r["status"] for r in res])
+    line = {"metric": METRICB, "value": value, "unit": "fits/s", "n_gpus": ws_,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded)",
+            "config": {"workload": "batch4096", "stamps": len(sts),
+                       "pixels": int(sum(h * w for h, w in zip(Hs, Ws))), "psf": s0.P,
+                       "conv": "direct", "free_params": s0.nfree, "lm_tol": BENCH_TOL,
+                       "l2": "inputs (0.5 GB) larger than L2", "parallelism": f"replicas{ws_}"},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "kernel": "k_conv_direct (2 P^2 FLOP per output)",
+                         "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "traffic": None},
+            "kernel_ms_per_step": {k: v["ms"] for k, v in pr.items()},
+            "lm": {"iters_median": float(np.median(iters)), "iters_max": int(iters.max()),
+                   "converged": int((status == 0).sum())},
+            "clocks": clk.summary(), "peaks": peak_kind}
+    if rank == 0 and ws_ == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batch(sts, budget_s=20.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws_ > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline_batch(sts, budget_s=20.0):
+    """The oracle's batched LM (OpenMP across stamps) on the first stamps of
+    the same batch, doubling the count until the budget is spent."""
+    import oracle
+    from paper_1101_2254_gb300 import synth
+    n, best = 8, None
+    while n <= len(sts):
+        sub = sts[:n]
+        descs, imgs, sigs, psfs, pix_off, psf_off, p0 = [], [], [], [], [], [], []
+        po = xo = 0
+        for st in sub:
+            dd = oracle.make_desc(st.H, st.W, st.P, st.kinds, st.os_factor, st.os_box)
+            m = oracle.render(dd, st.params, st.psf)
+            img, sig = synth.add_noise(m, st.noise_seed)
+            descs.append(dd); imgs.append(img.ravel()); sigs.append(sig.ravel())
+            psfs.append(st.psf.ravel()); pix_off.append(xo); psf_off.append(po)
+            xo += img.size; po += st.psf.size; p0.append(st.guess())
+        t0 = time.perf_counter()
+        oracle.lm_fit_batch(descs, np.array(p0), sub[0].fixed, np.concatenate(psfs), psf_off,
+                            np.concatenate(imgs), np.concatenate(sigs), pix_off)
+        dt = time.perf_counter() - t0
+        best = {"value": n / dt, "unit": "fits/s", "cores": oracle.num_threads(),
+                "kind": "oracle",
+                "sample": f"oracle batched LM (OpenMP across stamps) of the first {n} of the "
+                          f"4096 stamps, {dt:.1f} s"}
+        if dt > budget_s / 3:
+            break
+        n *= 2
+    return best
 
 
 # ------------------------------------------------------------------ the oracle
@@ -394,5 +527,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch4096":
+        run_batch(a)
     else:
         run_gf(a)

@@ -198,7 +198,7 @@ gf_status gf_jacobian(const gf_desc* d, const double* params_host, const uint8_t
                       gf_stream stream);
 
 /* Fill opts with the library defaults (lambda0 1e-3, x10 / x0.1, [1e-12, 1e12],
- * ftol 1e-6, xtol 1e-6, fd_rel 1e-3, max_iter 200). */
+ * ftol 1e-8, xtol 1e-8, fd_rel 1e-3, max_iter 200). */
 void gf_default_opts(gf_lm_opts* opts);
 
 /* Steps 1-5: Levenberg-Marquardt fit of one stamp.  params_host (nslots) is

@@ -6,6 +6,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <climits>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -227,8 +229,8 @@ void default_opts(gf_lm_opts* o)
     o->lambda_down = 0.1;
     o->lambda_min = 1e-12;
     o->lambda_max = 1e12;
-    o->ftol = 1e-6;
-    o->xtol = 1e-6;
+    o->ftol = 1e-8;
+    o->xtol = 1e-8;
     o->fd_rel = 1e-3;
     o->max_iter = 200;
 }
@@ -310,6 +312,8 @@ enum { NEED_JAC = 1, NEED_TRIAL = 2, NEED_LM = 4, NEED_CHI2 = 8 };
 struct Layout {
     size_t S, st, pre, params, chan_jac, chan_trial, lm, psum, ext_jac, ext_trial, y_jac,
         y_trial, part_jac, part_trial, active, exp, blob_end, total;
+    size_t ids_static, n_static;            // the all-stamps work list (in the blob)
+    size_t wl_n[2], wl_ids[2], wl_pre[2];   // LM work lists: 0 Jacobian pass, 1 trial pass
     size_t tw_x, tw_y, hhat, psfgrid, spec_jac, spec_trial;
     int count, nchan, nacc, nslots;
     int tot_model, tot_os, tot_conv, tot_red;
@@ -382,6 +386,10 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     o += al(sizeof(int) * 4 * (count + 1));
     L.params = o;
     o += al(sizeof(double) * (size_t)count * S.nslots);
+    L.ids_static = o;
+    o += al(sizeof(int) * (size_t)count);
+    L.n_static = o;
+    o += al(sizeof(int));
     L.blob_end = o;
     L.chan_trial = o;
     o += al(sizeof(Channel) * (size_t)count);
@@ -414,6 +422,14 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         o += al(sizeof(LMState) * (size_t)count);
         L.exp = o;
         o += al(sizeof(double) * (size_t)count * (S.nslots + 5));
+        for (int w = 0; w < 2; ++w) {
+            L.wl_n[w] = o;
+            o += al(sizeof(int));
+            L.wl_ids[w] = o;
+            o += al(sizeof(int) * (size_t)count);
+            L.wl_pre[w] = o;
+            o += al(sizeof(int) * (size_t)WK_KINDS * (count + 1));
+        }
     }
     pl->method = resolve_method(d);
     if (pl->method == GF_CONV_FFT) {
@@ -450,6 +466,9 @@ std::vector<uint8_t> make_blob(const Plan& pl, const Structure& S, const double*
     memcpy(blob.data() + L.st, pl.st.data(), sizeof(StampInfo) * L.count);
     memcpy(blob.data() + L.pre, pl.pre.data(), sizeof(int) * pl.pre.size());
     if (params) memcpy(blob.data() + L.params, params, sizeof(double) * (size_t)L.count * S.nslots);
+    int* ids = reinterpret_cast<int*>(blob.data() + L.ids_static);
+    for (int b = 0; b < L.count; ++b) ids[b] = b;
+    *reinterpret_cast<int*>(blob.data() + L.n_static) = L.count;
     return blob;
 }
 
@@ -457,6 +476,19 @@ template <class T>
 T* at(void* ws, size_t off)
 {
     return reinterpret_cast<T*>(static_cast<uint8_t*>(ws) + off);
+}
+
+// Persistent launch grids: the work items of a pass (all stamps' blocks times
+// the pass's channels) or a few waves of resident CTAs, whichever is smaller.
+void set_grids(PassArgs& a, const Layout& L, int nchan)
+{
+    const long long items[WK_KINDS] = {(long long)L.tot_model * nchan, (long long)L.tot_os * nchan,
+                                       (long long)L.tot_conv * nchan, (long long)L.tot_red};
+    const long long cap[WK_KINDS] = {152LL * 16, 152LL * 8, 152LL * 8, 152LL * 6};
+    for (int k = 0; k < WK_KINDS; ++k) {
+        a.maxitems[k] = (int)std::min<long long>(items[k], INT32_MAX);
+        a.grid[k] = (int)std::min(items[k], cap[k]);
+    }
 }
 
 PassArgs base_args(void* ws, const Layout& L, const float* psf, const float* img,
@@ -468,14 +500,11 @@ PassArgs base_args(void* ws, const Layout& L, const float* psf, const float* img
     a.st = at<StampInfo>(ws, L.st);
     a.S = at<Structure>(ws, L.S);
     const int* pre = at<int>(ws, L.pre);
-    a.pre_model = pre;
-    a.pre_os = pre + (L.count + 1);
-    a.pre_conv = pre + 2 * (L.count + 1);
-    a.pre_red = pre + 3 * (L.count + 1);
-    a.tot_model = L.tot_model;
-    a.tot_os = L.tot_os;
-    a.tot_conv = L.tot_conv;
-    a.tot_red = L.tot_red;
+    a.pre_static = pre;
+    a.wl.n = at<int>(ws, L.n_static);
+    a.wl.ids = at<int>(ws, L.ids_static);
+    a.wl.pre = pre;
+    set_grids(a, L, 1);
     a.psf = psf;
     a.psf_sum = at<float>(ws, L.psum);
     a.img = img;
@@ -489,6 +518,7 @@ PassArgs base_args(void* ws, const Layout& L, const float* psf, const float* img
 PassArgs jac_args(void* ws, const Layout& L, const PassArgs& base)
 {
     PassArgs a = base;
+    set_grids(a, L, L.nchan);
     a.chan = at<Channel>(ws, L.chan_jac);
     a.chan_stride = L.nchan;
     a.nchan = L.nchan;
@@ -899,17 +929,33 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     PassArgs at_ = trial_args(ws, L, base);
     at_.lm = lm;
     at_.phase = PH_TRIAL;
+    // each pass walks the list of stamps in its phase, rebuilt every body
+    aj.wl.n = at<int>(ws, L.wl_n[0]);
+    aj.wl.ids = at<int>(ws, L.wl_ids[0]);
+    aj.wl.pre = at<int>(ws, L.wl_pre[0]);
+    at_.wl.n = at<int>(ws, L.wl_n[1]);
+    at_.wl.ids = at<int>(ws, L.wl_ids[1]);
+    at_.wl.pre = at<int>(ws, L.wl_pre[1]);
     int* active = at<int>(ws, L.active);
     GF_CUDA(launch_psf_sum(L.count, base.st, psf, const_cast<float*>(base.psf_sum), s));
     GF_CUDA(launch_lm_init(L.count, base.S, lm, at<double>(ws, L.params), s));
     // One LM "body": the Jacobian pass (stamps that need it), the damped solve,
     // the trial pass, accept/reject and the count of stamps still active.
     auto body = [&]() -> gf_status {
+        {
+            ProfScope ps(PROF_LM, s);
+            GF_CUDA(launch_worklist(L.count, lm, PH_NEED_JAC, base.pre_static,
+                                    at<int>(ws, L.wl_n[0]), at<int>(ws, L.wl_ids[0]),
+                                    at<int>(ws, L.wl_pre[0]), s));
+        }
         gf_status rr = jac_pass(aj, pl, ws, nullptr, nullptr, nullptr, nullptr, s);
         if (rr != GF_OK) return rr;
         {
             ProfScope ps(PROF_LM, s);
             GF_CUDA(launch_final_solve(aj, at<Channel>(ws, L.chan_trial), active, s));
+            GF_CUDA(launch_worklist(L.count, lm, PH_TRIAL, base.pre_static,
+                                    at<int>(ws, L.wl_n[1]), at<int>(ws, L.wl_ids[1]),
+                                    at<int>(ws, L.wl_pre[1]), s));
         }
         if ((rr = trial_pass(at_, pl, ws, s, nullptr)) != GF_OK) return rr;
         ProfScope ps(PROF_LM, s);

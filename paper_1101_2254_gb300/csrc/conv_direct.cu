@@ -22,86 +22,98 @@ namespace {
 
 constexpr int TY = CONV_TY, TX = CONV_TX, NT = 128;
 
+// Work item = (channel, output tile of a listed stamp).
 __global__ void __launch_bounds__(NT) k_conv_direct(PassArgs a)
 {
     extern __shared__ __align__(16) float smem[];
-    const int blk = blockIdx.x;
-    const int b = find_stamp(a.pre_conv, a.count, blk);
-    if (a.lm && a.lm[b].phase != a.phase) return;
-    const int ch = blockIdx.y;
-    const StampInfo st = a.st[b];
-    const int P = st.P, P4 = (P + 3) & ~3;
+    const int n = *a.wl.n;
+    const int* pre = a.wl.pre + WK_CONV * (a.count + 1);
+    const int tot = pre[n];
+    const long long items = (long long)tot * a.nchan;
+    const int P = a.P, P4 = (P + 3) & ~3;
     const int SW = TX + P4, SH = TY + P - 1;
-    const int tiles_x = (st.W + TX - 1) / TX;
-    const int t = blk - a.pre_conv[b];
-    const int ty0 = (t / tiles_x) * TY, tx0 = (t % tiles_x) * TX;
-
     float* ks = smem;               // P x P4 flipped taps
     float* es = smem + P * P4;      // SH x SW grid tile (P*P4 is a multiple of 4)
-    const float* psf = a.psf + st.psf_off;
-    for (int idx = threadIdx.x; idx < P * P4; idx += NT) {
-        const int v = idx / P4, u = idx - v * P4;
-        ks[idx] = (u < P) ? __ldg(&psf[(P - 1 - v) * P + (P - 1 - u)]) : 0.0f;
-    }
-    const float* E = a.ext + ext_index(st, a.nchan, ch);
-    for (int idx = threadIdx.x; idx < SH * SW; idx += NT) {
-        const int r = idx / SW, col = idx - r * SW;
-        const int gy = ty0 + r, gx = tx0 + col;
-        es[idx] = (gy < st.He && gx < st.We) ? __ldg(&E[(long long)gy * st.We + gx]) : 0.0f;
-    }
-    __syncthreads();
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = (warp >> 1) * 16 + (lane >> 3) * 4;
     const int c0 = (warp & 1) * 32 + (lane & 7) * 4;
-    float acc[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int o = 0; o < 4; ++o) acc[r][o] = 0.0f;
+    int hint = -1, psf_b = -1;
+    const long long chunk = (items + gridDim.x - 1) / gridDim.x;
+    const long long it0 = (long long)blockIdx.x * chunk, it1 = min(items, it0 + chunk);
+    for (long long it = it0; it < it1; ++it) {
+        const int ch = (int)(it / tot), blk = (int)(it - (long long)ch * tot);
+        const int li = wl_locate(pre, n, blk, hint);
+        const int b = a.wl.ids[li];
+        const StampInfo st = a.st[b];
+        const int tiles_x = (st.W + TX - 1) / TX;
+        const int t = blk - pre[li];
+        const int ty0 = (t / tiles_x) * TY, tx0 = (t % tiles_x) * TX;
+        __syncthreads();  // the previous item is done with the shared tiles
+        if (b != psf_b) {
+            const float* psf = a.psf + st.psf_off;
+            for (int idx = threadIdx.x; idx < P * P4; idx += NT) {
+                const int v = idx / P4, u = idx - v * P4;
+                ks[idx] = (u < P) ? __ldg(&psf[(P - 1 - v) * P + (P - 1 - u)]) : 0.0f;
+            }
+            psf_b = b;
+        }
+        const float* E = a.ext + ext_index(st, a.nchan, ch);
+        for (int idx = threadIdx.x; idx < SH * SW; idx += NT) {
+            const int r = idx / SW, col = idx - r * SW;
+            const int gy = ty0 + r, gx = tx0 + col;
+            es[idx] = (gy < st.He && gx < st.We) ? __ldg(&E[(long long)gy * st.We + gx]) : 0.0f;
+        }
+        __syncthreads();
 
-    for (int v = 0; v < P; ++v) {
-        const float* kr = ks + v * P4;
-        const float* er = es + (r0 + v) * SW + c0;
-        float4 w0[4];
+        float acc[4][4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) w0[r] = *reinterpret_cast<const float4*>(er + r * SW);
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) acc[r][o] = 0.0f;
+
+        for (int v = 0; v < P; ++v) {
+            const float* kr = ks + v * P4;
+            const float* er = es + (r0 + v) * SW + c0;
+            float4 w0[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) w0[r] = *reinterpret_cast<const float4*>(er + r * SW);
 #pragma unroll 2
-        for (int m = 0; m < P4; m += 4) {
-            const float4 kk = *reinterpret_cast<const float4*>(kr + m);
+            for (int m = 0; m < P4; m += 4) {
+                const float4 kk = *reinterpret_cast<const float4*>(kr + m);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float4 w1 = *reinterpret_cast<const float4*>(er + r * SW + m + 4);
-                const float win[8] = {w0[r].x, w0[r].y, w0[r].z, w0[r].w,
-                                      w1.x,    w1.y,    w1.z,    w1.w};
+                for (int r = 0; r < 4; ++r) {
+                    const float4 w1 = *reinterpret_cast<const float4*>(er + r * SW + m + 4);
+                    const float win[8] = {w0[r].x, w0[r].y, w0[r].z, w0[r].w,
+                                          w1.x,    w1.y,    w1.z,    w1.w};
 #pragma unroll
-                for (int o = 0; o < 4; ++o) {
-                    float x = acc[r][o];
-                    x = fmaf(kk.x, win[o], x);
-                    x = fmaf(kk.y, win[o + 1], x);
-                    x = fmaf(kk.z, win[o + 2], x);
-                    x = fmaf(kk.w, win[o + 3], x);
-                    acc[r][o] = x;
+                    for (int o = 0; o < 4; ++o) {
+                        float x = acc[r][o];
+                        x = fmaf(kk.x, win[o], x);
+                        x = fmaf(kk.y, win[o + 1], x);
+                        x = fmaf(kk.z, win[o + 2], x);
+                        x = fmaf(kk.w, win[o + 3], x);
+                        acc[r][o] = x;
+                    }
+                    w0[r] = w1;
                 }
-                w0[r] = w1;
             }
         }
-    }
 
-    if (a.work && threadIdx.x == 0) {
-        const unsigned long long rows = (unsigned long long)min(TY, st.H - ty0);
-        const unsigned long long cols = (unsigned long long)min(TX, st.W - tx0);
-        atomicAdd(&a.work[PROF_CONV], 2ull * (unsigned long long)P * P * rows * cols);
-    }
-    float* Y = a.y + y_index(st, a.nchan, ch);
+        if (a.work && threadIdx.x == 0) {
+            const unsigned long long rows = (unsigned long long)min(TY, st.H - ty0);
+            const unsigned long long cols = (unsigned long long)min(TX, st.W - tx0);
+            atomicAdd(&a.work[PROF_CONV], 2ull * (unsigned long long)P * P * rows * cols);
+        }
+        float* Y = a.y + y_index(st, a.nchan, ch);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int oy = ty0 + r0 + r;
-        if (oy >= st.H) continue;
+        for (int r = 0; r < 4; ++r) {
+            const int oy = ty0 + r0 + r;
+            if (oy >= st.H) continue;
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            const int ox = tx0 + c0 + o;
-            if (ox < st.W) Y[(long long)oy * st.W + ox] = acc[r][o];
+            for (int o = 0; o < 4; ++o) {
+                const int ox = tx0 + c0 + o;
+                if (ox < st.W) Y[(long long)oy * st.W + ox] = acc[r][o];
+            }
         }
     }
 }
@@ -118,11 +130,11 @@ size_t conv_direct_smem(int P)
 
 cudaError_t launch_conv_direct(const PassArgs& a, cudaStream_t s)
 {
-    if (a.tot_conv <= 0) return cudaSuccess;
+    if (a.maxitems[WK_CONV] <= 0) return cudaSuccess;
     const size_t sm = conv_direct_smem(a.P);
     cudaError_t e = ensure_smem_optin_conv_direct(a.P, nullptr);
     if (e != cudaSuccess) return e;
-    k_conv_direct<<<dim3(a.tot_conv, a.nchan), NT, sm, s>>>(a);
+    k_conv_direct<<<a.grid[WK_CONV], NT, sm, s>>>(a);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }

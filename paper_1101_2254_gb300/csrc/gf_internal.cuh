@@ -209,6 +209,47 @@ __device__ __forceinline__ int find_stamp(const int* prefix, int count, int blk)
     return lo;
 }
 
+// ------------------------------------------------------------------ work lists
+// Kernel kinds with per-stamp block counts.
+enum { WK_MODEL = 0, WK_OS = 1, WK_CONV = 2, WK_RED = 3, WK_KINDS = 4 };
+
+// The stamps taking part in a pass (all stamps, or those in the pass's LM
+// phase), in stamp order, and per kernel kind the exclusive prefix sums of
+// their blocks.  Pass kernels are persistent: each CTA walks one contiguous
+// range of the work items (the listed stamps' blocks), so stamps that are done
+// cost nothing and a CTA's consecutive items mostly share a stamp and channel.
+struct WorkList {
+    const int* n;    // [1] number of listed stamps
+    const int* ids;  // [count] listed stamp ids
+    const int* pre;  // [WK_KINDS][count + 1]
+};
+
+// listed index of block `blk`: a short forward walk from the CTA's previous
+// position (its items increase), else a binary search
+__device__ __forceinline__ int wl_locate(const int* pre, int n, int blk, int& hint)
+{
+    int i = hint;
+    if (i >= 0 && i < n && pre[i] <= blk) {
+        for (int step = 0; step < 4; ++step) {
+            if (i + 1 >= n || pre[i + 1] > blk) {
+                hint = i;
+                return i;
+            }
+            ++i;
+        }
+    }
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= blk)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    hint = lo;
+    return lo;
+}
+
 // ---------------------------------------------------------- host-side launch
 // Arguments of the kernel passes; each .cu file implements its own launcher.
 
@@ -231,12 +272,10 @@ struct PassArgs {
     int nacc;                  // accumulators per reduce block
     float* J_out;              // optional Jacobian output (nfree x H x W per stamp, packed)
     float* m_out;              // optional model output (H x W per stamp, packed at pix_off)
-    // block tables (exclusive prefixes, [count + 1])
-    const int* pre_model;
-    const int* pre_os;
-    const int* pre_conv;
-    const int* pre_red;
-    int tot_model, tot_os, tot_conv, tot_red;
+    WorkList wl;               // the stamps taking part in this pass
+    const int* pre_static;     // [WK_KINDS][count + 1] block prefixes over all stamps
+    int grid[WK_KINDS];        // persistent launch grid per kernel kind
+    int maxitems[WK_KINDS];    // upper bound of work items (all stamps, all channels)
     int P;                     // PSF side (uniform across the stamps of a call)
     unsigned long long* work;  // profiling: algorithmic work per kernel class, or null
 };
@@ -261,6 +300,9 @@ cudaError_t launch_final_jac(const PassArgs& a, double* A_out, double* g_out, do
 cudaError_t launch_final_chi2(const PassArgs& a, double* chi2_out, cudaStream_t s);
 cudaError_t launch_psf_sum(int count, const StampInfo* st, const float* psf, float* out,
                            cudaStream_t s);
+// the work list of the stamps whose LM phase is `phase`
+cudaError_t launch_worklist(int count, const LMState* lm, int phase, const int* pre_static,
+                            int* n, int* ids, int* pre, cudaStream_t s);
 
 // parameter / channel preparation and the LM steps (lm.cu)
 cudaError_t launch_prep_sum(const PassArgs& a, const double* params, int use_trial,

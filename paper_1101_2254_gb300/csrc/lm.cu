@@ -86,8 +86,11 @@ __device__ double sersic_bn_warp(double n, double guess)
             hi = b;
         const double dens = exp((a - 1.0) * log(b) - b - lga);
         double nb = b - f / dens;
-        if (!(nb > lo && nb < hi)) nb = 0.5 * (lo + hi);
-        const bool done = fabs(nb - b) <= 1e-13 * b;
+        const bool newton = nb > lo && nb < hi;
+        if (!newton) nb = 0.5 * (lo + hi);
+        // Newton converges quadratically: once a Newton correction is below
+        // 1e-6 b, the corrected value is good to ~1e-12 b (far below float32)
+        const bool done = newton && fabs(nb - b) <= 1e-6 * b;
         b = nb;
         if (done || hi - lo <= 1e-14 * b) break;
     }
@@ -331,25 +334,27 @@ __device__ bool warp_cholesky_solve(int n, WarpScratch& W)
             if (k <= i) M[i * n + k] -= M[i * n + j] * M[k * n + j];
         }
     }
-    __syncwarp();
-    if (lane == 0) {
-        double* r = W.r;
-        bool ok = true;
-        for (int i = 0; i < n; ++i) {
-            double s = r[i];
-            for (int k = 0; k < i; ++k) s -= M[i * n + k] * r[k];
-            r[i] = s / M[i * n + i];
-        }
-        for (int i = n - 1; i >= 0; --i) {
-            double s = r[i];
-            for (int k = i + 1; k < n; ++k) s -= M[k * n + i] * r[k];
-            r[i] = s / M[i * n + i];
-        }
-        for (int i = 0; i < n; ++i) ok = ok && isfinite(r[i]);
-        W.ok = ok;
+    // forward then back substitution; each row's dot product is a warp reduction
+    double* r = W.r;
+    for (int i = 0; i < n; ++i) {
+        __syncwarp();
+        double t = (lane < i) ? M[i * n + lane] * r[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        __syncwarp();
+        if (lane == 0) r[i] = (r[i] - t) / M[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        __syncwarp();
+        double t = (lane > i && lane < n) ? M[lane * n + i] * r[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        __syncwarp();
+        if (lane == 0) r[i] = (r[i] - t) / M[i * n + i];
     }
     __syncwarp();
-    return W.ok != 0;
+    const bool fin = lane >= n || isfinite(r[lane]);
+    return __all_sync(0xffffffffu, fin);
 }
 
 __device__ void lm_reject(const Structure& S, LMState& L)
@@ -455,10 +460,22 @@ __global__ void __launch_bounds__(FINAL_THREADS) k_final_solve(PassArgs a, Chann
     const Structure& S = S_sh;
     const int nf = S.nfree;
     if (phase == PH_NEED_JAC) {
-        const int b0 = a.pre_red[b], b1 = a.pre_red[b + 1];
-        for (int t = threadIdx.x; t < a.nacc; t += blockDim.x) {
+        // one accumulator per warp: lanes stride over the stamp's partials,
+        // then a fixed shuffle tree (deterministic)
+        const int* pst = a.pre_static + WK_RED * (a.count + 1);
+        const int b0 = pst[b], b1 = pst[b + 1];
+        const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+        for (int t = wid; t < a.nacc; t += FINAL_THREADS / 32) {
             CSum acc = {0.0f, 0.0f};
-            for (int k = b0; k < b1; ++k) csum_add(acc, a.partial[(long long)k * a.nacc + t]);
+            for (int k = b0 + ln; k < b1; k += 32) csum_add(acc, a.partial[(long long)k * a.nacc + t]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                CSum other;
+                other.s = __shfl_down_sync(kFull, acc.s, o);
+                other.c = __shfl_down_sync(kFull, acc.c, o);
+                acc = csum_merge(acc, other);
+            }
+            if (ln != 0) continue;
             const double v = (double)acc.s + (double)acc.c;
             int i, j;
             const int kind = decode_acc(t, nf, i, j);
@@ -561,7 +578,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_final_update(PassArgs a, int* a
     LMState& L = a.lm[b];
     const int phase = L.phase;
     if (phase == PH_TRIAL) {
-        const int b0 = a.pre_red[b], b1 = a.pre_red[b + 1];
+        const int* pst = a.pre_static + WK_RED * (a.count + 1);
+        const int b0 = pst[b], b1 = pst[b + 1];
         CSum acc = {0.0f, 0.0f};
         for (int k = b0 + threadIdx.x; k < b1; k += RED_THREADS) csum_add(acc, a.partial[k]);
 #pragma unroll
@@ -618,6 +636,73 @@ __global__ void k_lm_export(int count, const Structure* Sp, const LMState* lm, d
     o[ns + 4] = L.status;
 }
 
+// One block builds a pass's work list: stamp b is listed when its LM phase is
+// `phase`; for each kernel kind, pre[k][i] sums the static block counts of the
+// listed stamps before the i-th (block-wide exclusive scans).
+constexpr int WL_THREADS = 1024;
+
+__global__ void __launch_bounds__(WL_THREADS) k_worklist(int count, const LMState* lm, int phase,
+                                                         const int* pst, int* n_out, int* ids,
+                                                         int* pre)
+{
+    __shared__ int wsum[WL_THREADS / 32][1 + WK_KINDS];
+    const int per = (count + WL_THREADS - 1) / WL_THREADS;
+    const int b0 = min(count, (int)threadIdx.x * per), b1 = min(count, b0 + per);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int loc[1 + WK_KINDS];
+    for (int q = 0; q <= WK_KINDS; ++q) loc[q] = 0;
+    for (int b = b0; b < b1; ++b) {
+        if (lm[b].phase != phase) continue;
+        loc[0] += 1;
+        for (int k = 0; k < WK_KINDS; ++k)
+            loc[1 + k] += pst[k * (count + 1) + b + 1] - pst[k * (count + 1) + b];
+    }
+    int incl[1 + WK_KINDS];
+    for (int q = 0; q <= WK_KINDS; ++q) {
+        int v = loc[q];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += u;
+        }
+        incl[q] = v;
+        if (lane == 31) wsum[warp][q] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int q = 0; q <= WK_KINDS; ++q) {
+            const int x = wsum[lane][q];
+            int v = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(kFull, v, o);
+                if (lane >= o) v += u;
+            }
+            wsum[lane][q] = v - x;  // exclusive over warps
+        }
+    }
+    __syncthreads();
+    int excl[1 + WK_KINDS];
+    for (int q = 0; q <= WK_KINDS; ++q) excl[q] = incl[q] - loc[q] + wsum[warp][q];
+    int pos = excl[0];
+    int c[WK_KINDS];
+    for (int k = 0; k < WK_KINDS; ++k) c[k] = excl[1 + k];
+    for (int b = b0; b < b1; ++b) {
+        if (lm[b].phase != phase) continue;
+        ids[pos] = b;
+        for (int k = 0; k < WK_KINDS; ++k) {
+            pre[k * (count + 1) + pos] = c[k];
+            c[k] += pst[k * (count + 1) + b + 1] - pst[k * (count + 1) + b];
+        }
+        ++pos;
+    }
+    if (threadIdx.x == WL_THREADS - 1) {
+        const int n = excl[0] + loc[0];
+        *n_out = n;
+        for (int k = 0; k < WK_KINDS; ++k) pre[k * (count + 1) + n] = excl[1 + k] + loc[1 + k];
+    }
+}
+
 inline int warp_blocks(int count) { return (count + kWarpsPerBlock - 1) / kWarpsPerBlock; }
 
 }  // namespace
@@ -664,6 +749,14 @@ cudaError_t launch_lm_export(int count, const Structure* S, const LMState* lm, d
                              cudaStream_t s)
 {
     k_lm_export<<<(count + 127) / 128, 128, 0, s>>>(count, S, lm, out);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_worklist(int count, const LMState* lm, int phase, const int* pre_static,
+                            int* n, int* ids, int* pre, cudaStream_t s)
+{
+    k_worklist<<<1, WL_THREADS, 0, s>>>(count, lm, phase, pre_static, n, ids, pre);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }

@@ -20,66 +20,94 @@ __device__ __forceinline__ void load_channel(Channel* dst, const Channel* src)
     for (int i = threadIdx.x; i < (int)(sizeof(Channel) / 16); i += blockDim.x) d[i] = s[i];
 }
 
+// Work item = (channel, block of MODEL_THREADS grid pixels of a listed stamp).
 __global__ void __launch_bounds__(MODEL_THREADS) k_model(PassArgs a)
 {
     __shared__ __align__(16) Channel ch;
-    const int blk = blockIdx.x;
-    const int b = find_stamp(a.pre_model, a.count, blk);
-    if (a.lm && a.lm[b].phase != a.phase) return;
-    const int k = blockIdx.y;
-    const StampInfo st = a.st[b];
-    load_channel(&ch, &a.chan[(long long)b * a.chan_stride + k]);
-    __syncthreads();
-    const long long npix = (long long)st.He * st.We;
-    const long long pix = (long long)(blk - a.pre_model[b]) * MODEL_THREADS + threadIdx.x;
-    bool write = pix < npix;
-    int i = 0, j = 0;
-    if (write) {
-        const int ie = (int)(pix / st.We), je = (int)(pix - (long long)ie * st.We);
-        i = ie - st.c;
-        j = je - st.c;
-        write = !(st.os_factor > 1 && i >= st.os_y0 && i < st.os_y0 + st.os_box &&
-                  j >= st.os_x0 && j < st.os_x0 + st.os_box);
-    }
-    if (write)
-        a.ext[ext_index(st, a.nchan, k) + pix] =
-            channel_value(ch, (float)j, (float)i, 0.0f, 0.0f);
-    if (a.work) {
-        const int n = __syncthreads_count(write);
-        if (threadIdx.x == 0) atomicAdd(&a.work[PROF_MODEL], 4ull * (unsigned long long)n);
+    const int n = *a.wl.n;
+    const int* pre = a.wl.pre + WK_MODEL * (a.count + 1);
+    const int tot = pre[n];
+    const long long items = (long long)tot * a.nchan;
+    int hint = -1, cur_b = -1, cur_k = -1;
+    const long long chunk = (items + gridDim.x - 1) / gridDim.x;
+    const long long it0 = (long long)blockIdx.x * chunk, it1 = min(items, it0 + chunk);
+    for (long long it = it0; it < it1; ++it) {
+        const int k = (int)(it / tot), blk = (int)(it - (long long)k * tot);
+        const int li = wl_locate(pre, n, blk, hint);
+        const int b = a.wl.ids[li];
+        const StampInfo st = a.st[b];
+        if (b != cur_b || k != cur_k) {
+            __syncthreads();
+            load_channel(&ch, &a.chan[(long long)b * a.chan_stride + k]);
+            __syncthreads();
+            cur_b = b;
+            cur_k = k;
+        }
+        const int npix = st.He * st.We;  // stamps are validated below 2^31 pixels
+        const int pix = (blk - pre[li]) * MODEL_THREADS + threadIdx.x;
+        bool write = pix < npix;
+        int i = 0, j = 0;
+        if (write) {
+            const int ie = pix / st.We, je = pix - ie * st.We;
+            i = ie - st.c;
+            j = je - st.c;
+            write = !(st.os_factor > 1 && i >= st.os_y0 && i < st.os_y0 + st.os_box &&
+                      j >= st.os_x0 && j < st.os_x0 + st.os_box);
+        }
+        if (write)
+            a.ext[ext_index(st, a.nchan, k) + pix] =
+                channel_value(ch, (float)j, (float)i, 0.0f, 0.0f);
+        if (a.work) {
+            const int cnt = __syncthreads_count(write);
+            if (threadIdx.x == 0) atomicAdd(&a.work[PROF_MODEL], 4ull * (unsigned long long)cnt);
+        }
     }
 }
 
+// Work item = (channel, OS_WARPS pixels of a listed stamp's oversampling block).
 __global__ void __launch_bounds__(OS_WARPS * 32) k_model_os(PassArgs a)
 {
     __shared__ __align__(16) Channel ch;
-    const int blk = blockIdx.x;
-    const int b = find_stamp(a.pre_os, a.count, blk);
-    if (a.lm && a.lm[b].phase != a.phase) return;
-    const int k = blockIdx.y;
-    const StampInfo st = a.st[b];
-    load_channel(&ch, &a.chan[(long long)b * a.chan_stride + k]);
-    __syncthreads();
+    const int n = *a.wl.n;
+    const int* pre = a.wl.pre + WK_OS * (a.count + 1);
+    const int tot = pre[n];
+    const long long items = (long long)tot * a.nchan;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = (blk - a.pre_os[b]) * OS_WARPS + warp;
-    const int B = st.os_box;
-    if (q >= B * B) return;
-    const int i = st.os_y0 + q / B, j = st.os_x0 + q % B;
-    const int s = st.os_factor, ns = s * s;
-    const float fs = (float)s;
-    float v = 0.0f;
-    for (int t = lane; t < ns; t += 32) {
-        const int ay = t / s, bx = t - ay * s;
-        const float oy = ((float)ay + 0.5f) / fs - 0.5f;
-        const float ox = ((float)bx + 0.5f) / fs - 0.5f;
-        v += channel_value(ch, (float)j, (float)i, ox, oy);
-    }
+    int hint = -1, cur_b = -1, cur_k = -1;
+    const long long chunk = (items + gridDim.x - 1) / gridDim.x;
+    const long long it0 = (long long)blockIdx.x * chunk, it1 = min(items, it0 + chunk);
+    for (long long it = it0; it < it1; ++it) {
+        const int k = (int)(it / tot), blk = (int)(it - (long long)k * tot);
+        const int li = wl_locate(pre, n, blk, hint);
+        const int b = a.wl.ids[li];
+        const StampInfo st = a.st[b];
+        if (b != cur_b || k != cur_k) {
+            __syncthreads();
+            load_channel(&ch, &a.chan[(long long)b * a.chan_stride + k]);
+            __syncthreads();
+            cur_b = b;
+            cur_k = k;
+        }
+        const int q = (blk - pre[li]) * OS_WARPS + warp;
+        const int B = st.os_box;
+        if (q >= B * B) continue;
+        const int i = st.os_y0 + q / B, j = st.os_x0 + q % B;
+        const int s = st.os_factor, ns = s * s;
+        const float fs = (float)s;
+        float v = 0.0f;
+        for (int t = lane; t < ns; t += 32) {
+            const int ay = t / s, bx = t - ay * s;
+            const float oy = ((float)ay + 0.5f) / fs - 0.5f;
+            const float ox = ((float)bx + 0.5f) / fs - 0.5f;
+            v += channel_value(ch, (float)j, (float)i, ox, oy);
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) {
-        const long long pix = (long long)(i + st.c) * st.We + (j + st.c);
-        a.ext[ext_index(st, a.nchan, k) + pix] = v / (float)ns;
-        if (a.work) atomicAdd(&a.work[PROF_MODEL], 4ull);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            const long long pix = (long long)(i + st.c) * st.We + (j + st.c);
+            a.ext[ext_index(st, a.nchan, k) + pix] = v / (float)ns;
+            if (a.work) atomicAdd(&a.work[PROF_MODEL], 4ull);
+        }
     }
 }
 
@@ -87,12 +115,12 @@ __global__ void __launch_bounds__(OS_WARPS * 32) k_model_os(PassArgs a)
 
 cudaError_t launch_model(const PassArgs& a, cudaStream_t s)
 {
-    if (a.tot_model > 0) {
-        k_model<<<dim3(a.tot_model, a.nchan), MODEL_THREADS, 0, s>>>(a);
+    if (a.maxitems[WK_MODEL] > 0) {
+        k_model<<<a.grid[WK_MODEL], MODEL_THREADS, 0, s>>>(a);
         GF_COUNT_LAUNCH();
     }
-    if (a.tot_os > 0) {
-        k_model_os<<<dim3(a.tot_os, a.nchan), OS_WARPS * 32, 0, s>>>(a);
+    if (a.maxitems[WK_OS] > 0) {
+        k_model_os<<<a.grid[WK_OS], OS_WARPS * 32, 0, s>>>(a);
         GF_COUNT_LAUNCH();
     }
     return cudaGetLastError();

@@ -34,17 +34,39 @@ __device__ __forceinline__ void load_chan_info(ChanInfo& ci, float& msky, const 
     if (threadIdx.x == 0) msky = c[0].msky;
 }
 
+// The normal equations as one bordered matrix: with v = (J_0 .. J_{nf-1}, r)
+// per pixel and weight w, M = sum w v v^T holds A (i, j < nf), g (j = nf) and
+// chi^2 (i = j = nf).  Thread (tile, group) owns a 4 x 4 tile of the upper
+// triangle of M and 16 pixels of each 256-pixel chunk: 9 shared loads feed 16
+// FMAs.  Sums over a thread's 16 pixels are plain float32; they are added to
+// the thread's compensated totals, and the 16 groups of a tile are merged in a
+// fixed order, so the partials are deterministic.
+constexpr int VSTR = GF_MAX_FREE + 1;  // row stride of the staged pixel vectors
+constexpr int NGRP = 16;              // pixel groups per chunk (16 pixels each)
+
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
 {
-    __shared__ float Jt[GF_MAX_FREE][RED_THREADS];
-    __shared__ float wv[RED_THREADS], wr[RED_THREADS], zz[RED_THREADS];
+    __shared__ float V[RED_THREADS][VSTR];  // pixel vectors v = (J, r)
+    __shared__ float Wt[RED_THREADS];       // weights 1/sigma^2
     __shared__ ChanInfo ci;
     __shared__ float msky;
-    const int blk = blockIdx.x;
-    const int b = find_stamp(a.pre_red, a.count, blk);
-    if (a.lm && a.lm[b].phase != a.phase) return;
+    __shared__ float red[NGRP][16][16];      // per group, per tile slot, 4 x 4 sums
+    const int n = *a.wl.n;
+    const int* pre = a.wl.pre + WK_RED * (a.count + 1);
+    const int tot = pre[n];
+    const int nf = a.S->nfree, skyc = a.S->sky_jcol;
+    const int nv = nf + 1;                 // bordered size
+    const int nt = (nv + 3) / 4;           // tiles per side
+    int hint = -1;
+    const int chunk = (tot + gridDim.x - 1) / gridDim.x;
+    const int it0 = blockIdx.x * chunk, it1 = min(tot, it0 + chunk);
+    for (int it = it0; it < it1; ++it) {
+    const int li = wl_locate(pre, n, it, hint);
+    const int b = a.wl.ids[li];
+    const int local = it - pre[li];
+    const int blk = a.pre_static[WK_RED * (a.count + 1) + b] + local;  // partial slot
     const StampInfo st = a.st[b];
-    const int nf = a.S->nfree, nacc = a.nacc, skyc = a.S->sky_jcol;
+    __syncthreads();  // the previous item is done with the shared arrays
     load_chan_info(ci, msky, a, b);
     __syncthreads();
     const float psum = a.psf_sum[b];
@@ -53,10 +75,26 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
     const float* sig = a.sig + st.pix_off;
     const float* Y = a.y + y_index(st, a.nchan, 0);
     const int tid = threadIdx.x;
-    int ai = 0, aj = 0;
-    const int akind = (tid < nacc) ? decode_acc(tid, nf, ai, aj) : -1;
-    CSum acc = {0.0f, 0.0f};
-    const long long base = (long long)(blk - a.pre_red[b]) * RED_PIX;
+    // this thread's tile (upper triangle, row-major over tile pairs) and group
+    const int tslot = tid % 16, grp = tid / 16;
+    int ti = -1, tj = -1;
+    {
+        int k = 0;
+        for (int I = 0; I < nt && ti < 0; ++I)
+            for (int J = I; J < nt; ++J, ++k)
+                if (k == tslot) {
+                    ti = I;
+                    tj = J;
+                    break;
+                }
+    }
+    const bool active_tile = ti >= 0;
+    CSum acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = CSum{0.0f, 0.0f};
+    const long long base = (long long)local * RED_PIX;
     for (int q = 0; q < RED_CHUNKS; ++q) {
         const long long px = base + (long long)q * RED_THREADS + tid;
         if (px < HW) {
@@ -66,36 +104,82 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
             for (int k = 0; k < a.nchan; ++k) {
                 const float yk = Y[(long long)k * HW + px];
                 if (ci.mw[k] != 0.0f) m = fmaf(ci.mw[k], yk, m);
-                if (ci.jc[k] >= 0) Jt[ci.jc[k]][tid] = yk;
+                if (ci.jc[k] >= 0) V[tid][ci.jc[k]] = yk;
             }
-            if (skyc >= 0) Jt[skyc][tid] = psum;
-            const float r = valid ? d - m : 0.0f;
-            const float z = valid ? r / s : 0.0f;
-            wv[tid] = valid ? 1.0f / (s * s) : 0.0f;
-            wr[tid] = valid ? z / s : 0.0f;
-            zz[tid] = z * z;
+            if (skyc >= 0) V[tid][skyc] = psum;
+            V[tid][nf] = valid ? d - m : 0.0f;
+            Wt[tid] = valid ? 1.0f / (s * s) : 0.0f;
             if (a.m_out) a.m_out[st.pix_off + px] = m;
             if (a.J_out)
-                for (int f = 0; f < nf; ++f) a.J_out[(long long)f * HW + px] = Jt[f][tid];
+                for (int f = 0; f < nf; ++f) a.J_out[(long long)f * HW + px] = V[tid][f];
         } else {
-            for (int f = 0; f < nf; ++f) Jt[f][tid] = 0.0f;
-            wv[tid] = wr[tid] = zz[tid] = 0.0f;
+            for (int f = 0; f < nv; ++f) V[tid][f] = 0.0f;
+            Wt[tid] = 0.0f;
         }
+        for (int f = nv; f < VSTR; ++f) V[tid][f] = 0.0f;
         __syncthreads();
-        if (akind == 0) {
-            for (int p = 0; p < RED_THREADS; ++p)
-                csum_add(acc, __fmul_rn(__fmul_rn(wv[p], Jt[ai][p]), Jt[aj][p]));
-        } else if (akind == 1) {
-            for (int p = 0; p < RED_THREADS; ++p) csum_add(acc, __fmul_rn(Jt[ai][p], wr[p]));
-        } else if (akind == 2) {
-            for (int p = 0; p < RED_THREADS; ++p) csum_add(acc, zz[p]);
+        if (active_tile) {
+            float sum[4][4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) sum[x][y] = 0.0f;
+            const int i0 = 4 * ti, j0 = 4 * tj;
+            for (int pp = 0; pp < RED_THREADS / NGRP; ++pp) {
+                const int p = grp * (RED_THREADS / NGRP) + pp;
+                const float w = Wt[p];
+                float vi[4], vj[4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    vi[x] = (i0 + x < VSTR) ? w * V[p][min(i0 + x, VSTR - 1)] : 0.0f;
+                    vj[x] = (j0 + x < VSTR) ? V[p][min(j0 + x, VSTR - 1)] : 0.0f;
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) sum[x][y] = fmaf(vi[x], vj[y], sum[x][y]);
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) csum_add(acc[x][y], sum[x][y]);
         }
         __syncthreads();
     }
-    if (tid < nacc) a.partial[(long long)blk * nacc + tid] = acc.s + acc.c;
+    // merge the 16 groups of each tile in group order, then write the partials
+    // in the accumulator order of decode_acc (A pairs, g, chi^2)
+    if (active_tile)
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) red[grp][tslot][x * 4 + y] = acc[x][y].s + acc[x][y].c;
+    __syncthreads();
+    for (int t = tid; t < a.nacc; t += RED_THREADS) {
+        int i, j;
+        const int kind = decode_acc(t, nf, i, j);
+        int r_, c_;
+        if (kind == 0) {
+            r_ = i;
+            c_ = j;
+        } else if (kind == 1) {
+            r_ = i;
+            c_ = nf;
+        } else {
+            r_ = nf;
+            c_ = nf;
+        }
+        const int I = r_ / 4, J = c_ / 4;
+        int slot = 0;
+        for (int II = 0; II < I; ++II) slot += nt - II;
+        slot += J - I;
+        CSum tot = {0.0f, 0.0f};
+        for (int gq = 0; gq < NGRP; ++gq) csum_add(tot, red[gq][slot][(r_ % 4) * 4 + (c_ % 4)]);
+        a.partial[(long long)blk * a.nacc + t] = tot.s + tot.c;
+    }
     if (a.work && tid == 0) {
-        const long long n = min((long long)RED_PIX, HW - base);
-        atomicAdd(&a.work[PROF_REDUCE], (unsigned long long)n * (4ull * a.nchan + 8ull));
+        const long long np = min((long long)RED_PIX, HW - base);
+        atomicAdd(&a.work[PROF_REDUCE], (unsigned long long)np * (4ull * a.nchan + 8ull));
+    }
     }
 }
 
@@ -104,10 +188,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_chi2(PassArgs a)
     __shared__ ChanInfo ci;
     __shared__ float msky;
     __shared__ CSum wsum[RED_THREADS / 32];
-    const int blk = blockIdx.x;
-    const int b = find_stamp(a.pre_red, a.count, blk);
-    if (a.lm && a.lm[b].phase != a.phase) return;
+    const int n = *a.wl.n;
+    const int* pre = a.wl.pre + WK_RED * (a.count + 1);
+    const int tot = pre[n];
+    int hint = -1;
+    const int chunk = (tot + gridDim.x - 1) / gridDim.x;
+    const int it0 = blockIdx.x * chunk, it1 = min(tot, it0 + chunk);
+    for (int it = it0; it < it1; ++it) {
+    const int li = wl_locate(pre, n, it, hint);
+    const int b = a.wl.ids[li];
+    const int local = it - pre[li];
+    const int blk = a.pre_static[WK_RED * (a.count + 1) + b] + local;  // partial slot
     const StampInfo st = a.st[b];
+    __syncthreads();
     load_chan_info(ci, msky, a, b);
     __syncthreads();
     const long long HW = (long long)st.H * st.W;
@@ -115,7 +208,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_chi2(PassArgs a)
     const float* sig = a.sig + st.pix_off;
     const float* Y = a.y + y_index(st, a.nchan, 0);
     CSum acc = {0.0f, 0.0f};
-    const long long base = (long long)(blk - a.pre_red[b]) * RED_PIX;
+    const long long base = (long long)local * RED_PIX;
     for (int q = 0; q < RED_CHUNKS; ++q) {
         const long long px = base + (long long)q * RED_THREADS + threadIdx.x;
         if (px >= HW) break;
@@ -144,9 +237,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_chi2(PassArgs a)
         for (int w = 1; w < RED_THREADS / 32; ++w) t = csum_merge(t, wsum[w]);
         a.partial[blk] = t.s + t.c;
         if (a.work) {
-            const long long n = min((long long)RED_PIX, HW - base);
-            atomicAdd(&a.work[PROF_REDUCE], (unsigned long long)n * (4ull * a.nchan + 8ull));
+            const long long np = min((long long)RED_PIX, HW - base);
+            atomicAdd(&a.work[PROF_REDUCE], (unsigned long long)np * (4ull * a.nchan + 8ull));
         }
+    }
     }
 }
 
@@ -158,7 +252,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_final_jac(PassArgs a, double* A
     if (a.lm && a.lm[b].phase != a.phase) return;
     const int nf = a.S->nfree, nacc = a.nacc, tid = threadIdx.x;
     if (tid >= nacc) return;
-    const int b0 = a.pre_red[b], b1 = a.pre_red[b + 1];
+    const int* pst = a.pre_static + WK_RED * (a.count + 1);
+    const int b0 = pst[b], b1 = pst[b + 1];
     CSum acc = {0.0f, 0.0f};
     for (int k = b0; k < b1; ++k) csum_add(acc, a.partial[(long long)k * nacc + tid]);
     const double v = (double)acc.s + (double)acc.c;
@@ -184,7 +279,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_final_chi2(PassArgs a, double* 
     __shared__ CSum wsum[RED_THREADS / 32];
     const int b = blockIdx.x;
     if (a.lm && a.lm[b].phase != a.phase) return;
-    const int b0 = a.pre_red[b], b1 = a.pre_red[b + 1];
+    const int* pst = a.pre_static + WK_RED * (a.count + 1);
+    const int b0 = pst[b], b1 = pst[b + 1];
     CSum acc = {0.0f, 0.0f};
     for (int k = b0 + threadIdx.x; k < b1; k += RED_THREADS) csum_add(acc, a.partial[k]);
 #pragma unroll
@@ -240,8 +336,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_psf_sum(int count, const StampI
 
 cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s)
 {
-    if (a.tot_red > 0) {
-        k_reduce_jac<<<a.tot_red, RED_THREADS, 0, s>>>(a);
+    if (a.maxitems[WK_RED] > 0) {
+        k_reduce_jac<<<a.grid[WK_RED], RED_THREADS, 0, s>>>(a);
         GF_COUNT_LAUNCH();
     }
     return cudaGetLastError();
@@ -249,8 +345,8 @@ cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s)
 
 cudaError_t launch_reduce_chi2(const PassArgs& a, cudaStream_t s)
 {
-    if (a.tot_red > 0) {
-        k_reduce_chi2<<<a.tot_red, RED_THREADS, 0, s>>>(a);
+    if (a.maxitems[WK_RED] > 0) {
+        k_reduce_chi2<<<a.grid[WK_RED], RED_THREADS, 0, s>>>(a);
         GF_COUNT_LAUNCH();
     }
     return cudaGetLastError();

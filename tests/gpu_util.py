@@ -43,6 +43,24 @@ def noisy_image(st: synth.Stamp, method=0):
     return m, img, sig
 
 
+SIGMA_FRAC = 0.01
+
+
+def param_bound_ok(pg, po, free, sigma, rel=PARAM_REL, sfrac=SIGMA_FRAC):
+    """|pg - po| <= max(rel * max(|po|, 1), sfrac * sigma) on the free slots;
+    sigma = the oracle's statistical error of each free parameter (sqrt diag of
+    the inverse normal matrix at its solution).  Returns (ok, |dp|/sigma, rel err)."""
+    pg, po = np.asarray(pg)[free], np.asarray(po)[free]
+    dp = np.abs(pg - po)
+    bound = np.maximum(rel * np.maximum(np.abs(po), 1.0), sfrac * np.asarray(sigma))
+    return bool(np.all(dp <= bound)), dp / np.asarray(sigma), dp / np.maximum(np.abs(po), 1.0)
+
+
+def oracle_sigma(d, p, fixed, psf, img, sig, method=0):
+    r = oracle.jacobian(d, p, fixed, psf, img, sig, method=method)
+    return np.sqrt(np.diag(np.linalg.inv(r["A"])))
+
+
 def param_rel_err(p, q, idx):
     p = np.asarray(p)[idx]
     q = np.asarray(q)[idx]

@@ -9,7 +9,7 @@ import oracle
 from paper_1101_2254_gb300 import synth
 
 from gpu_util import (CHI2_REL, PARAM_REL, assert_pix_close, gpu_desc, noisy_image, oracle_desc,
-                      param_rel_err)
+                      oracle_sigma, param_bound_ok, param_rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -153,8 +153,11 @@ def test_lm_fit_stamp64_matches_oracle(gf):
     xg, _ = oracle.evaluate(od, pg, st.psf, img, sig)
     assert xg <= ro["chi2"] * (1 + CHI2_REL), (xg, ro["chi2"])
     assert abs(rg["chi2"] - xg) <= CHI2_REL * xg
-    err = param_rel_err(pg, po, _free(st))
-    assert err.max() < PARAM_REL, (err, pg, po)
+    # 1e-3 relative, or 0.01 sigma where the statistical error is large (the
+    # position angle here: sigma ~ 6 deg at q = 0.7 and this noise level)
+    sd = oracle_sigma(od, po, st.fixed, st.psf, img, sig)
+    ok, in_sigma, rel = param_bound_ok(pg, po, _free(st), sd)
+    assert ok, (in_sigma, rel)
 
 
 def test_lm_fit_noiseless_recovers_truth(gf):
@@ -252,22 +255,23 @@ def test_lm_fit_stamp64_fft_matches_oracle(gf):
     assert rg["status"] == gf.OK, rg
     xg, _ = oracle.evaluate(od, pg, st.psf, img, sig)
     assert xg <= ro["chi2"] * (1 + CHI2_REL), (xg, ro["chi2"])
-    err = param_rel_err(pg, po, _free(st))
-    assert err.max() < PARAM_REL, (err, pg, po)
+    sd = oracle_sigma(od, po, st.fixed, st.psf, img, sig)
+    ok, in_sigma, rel = param_bound_ok(pg, po, _free(st), sd)
+    assert ok, (in_sigma, rel)
 
 
-@pytest.mark.parametrize("method", ["fft", "direct"])
-def test_lm_fit_stamp512_reaches_oracle_fit(gf, method):
+@pytest.mark.parametrize("method,tol", [("fft", None), ("direct", None), ("fft", 1e-6)])
+def test_lm_fit_stamp512_reaches_oracle_fit(gf, method, tol):
     """The 512x512 bulge + disk fit (15 free slots) against the oracle's stored
     converged fit on the same seeded image (tests/golden/stamp512.json).
 
     chi^2: the oracle's chi^2 at the GPU's parameters reaches the oracle's
     minimum within CHI2_REL.  Parameters: within PARAM_REL relative, or within
-    a quarter of the parameter's statistical error sigma (from the oracle's
-    normal matrix at its solution) where that is larger: the bulge/disk split
-    of this stamp is nearly degenerate (sigma/|p| up to 0.2), and float32
-    model arithmetic cannot resolve chi^2 finely enough to pin those
-    directions to 1e-3 relative."""
+    0.1 of the parameter's statistical error sigma (0.25 at the benchmark's
+    looser tolerance) where that is larger: the bulge/disk split of this stamp
+    is nearly degenerate (sigma/|p| up to 0.2), and float32 model arithmetic
+    cannot resolve chi^2 finely enough to pin those directions to 1e-3
+    relative."""
     import json
     import os
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "stamp512.json")))
@@ -277,7 +281,9 @@ def test_lm_fit_stamp512_reaches_oracle_fit(gf, method):
     p0 = np.array(gold["guess"])
     assert np.array_equal(p0, st.guess())
     conv = gf.CONV_FFT if method == "fft" else gf.CONV_DIRECT
-    pg, rg = gf.lm_fit(gpu_desc(gf, st, conv), p0, st.fixed, cuda(img), cuda(sig), cuda(st.psf))
+    opts = None if tol is None else gf.default_opts(ftol=tol, xtol=tol)  # tol: the bench's setting
+    pg, rg = gf.lm_fit(gpu_desc(gf, st, conv), p0, st.fixed, cuda(img), cuda(sig), cuda(st.psf),
+                       opts=opts)
     assert rg["status"] == gf.OK, rg
     xg, _ = oracle.evaluate(od, pg, st.psf, img, sig, method=1)
     assert xg <= gold["chi2"] * (1 + CHI2_REL), (xg, gold["chi2"])
@@ -285,6 +291,5 @@ def test_lm_fit_stamp512_reaches_oracle_fit(gf, method):
     free = _free(st)
     po = np.array(gold["params"])
     sd = np.array(gold["sigma_free"])
-    dp = np.abs(pg[free] - po[free])
-    bound = np.maximum(PARAM_REL * np.maximum(np.abs(po[free]), 1.0), 0.25 * sd)
-    assert np.all(dp <= bound), (dp / sd, param_rel_err(pg, po, free))
+    ok, in_sigma, rel = param_bound_ok(pg, po, free, sd, sfrac=0.1 if tol is None else 0.25)
+    assert ok, (in_sigma, rel)
