@@ -81,8 +81,11 @@ typedef enum { GF_SERSIC = 1, GF_EXPDISK = 2, GF_SKY = 3 } gf_comp_kind;
 typedef enum {
     GF_CONV_AUTO = 0,   /* direct for P < GF_AUTO_FFT_PSF, else FFT */
     GF_CONV_DIRECT = 1, /* tiled direct sum, PSF and halo tile in shared memory */
-    GF_CONV_FFT = 2     /* shared-memory mixed-radix FFT, 2^a 3^b 5^c sizes up to 4096;
+    GF_CONV_FFT = 2,    /* shared-memory mixed-radix FFT, 2^a 3^b 5^c sizes up to 4096;
                            the stamps of one call must share H and W */
+    GF_CONV_DFT_TC = 3  /* Fourier transforms as dense DFT contractions on the tensor cores
+                           (split-precision bf16 operands, float32 accumulation); sizes
+                           N = R1 R2 with R1, R2 <= 64; stamps of one call share H and W */
 } gf_conv_method;
 
 #define GF_MAX_COMP 8

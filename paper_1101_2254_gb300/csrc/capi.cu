@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "conv_dft.cuh"
 #include "conv_fft.cuh"
 #include "gf_internal.cuh"
 
@@ -139,7 +140,8 @@ gf_status check_structure(const gf_desc* d)
     if (d->os_factor < 1 || d->os_factor > 64) return fail(GF_EINVAL, "os_factor out of [1, 64]");
     if (d->os_box < 0) return fail(GF_EINVAL, "os_box < 0");
     const int m = resolve_method(d);
-    if (m != GF_CONV_DIRECT && m != GF_CONV_FFT) return fail(GF_EINVAL, "unknown conv_method");
+    if (m != GF_CONV_DIRECT && m != GF_CONV_FFT && m != GF_CONV_DFT_TC)
+        return fail(GF_EINVAL, "unknown conv_method");
     if (m == GF_CONV_DIRECT && P > GF_DIRECT_MAX_PSF)
         return fail(GF_EINVAL, "direct convolution supports psf_size <= " +
                                    std::to_string(GF_DIRECT_MAX_PSF));
@@ -172,6 +174,36 @@ FFTPlan make_fft_plan(int n)
     return p;
 }
 
+// Transform length for the DFT-contraction path: the smallest N >= n that
+// factors as R1 R2 with R1, R2 <= DFT_RMAX, and the factorisation with the
+// least padding work.  `inner_tile` marks the x axis, whose first stage runs
+// over R2 contiguous columns in tiles of 64 (a short R2 wastes tile width).
+struct DftFactor {
+    int N, R1, R2;
+};
+
+DftFactor dft_factor(int n, bool inner_tile)
+{
+    for (int N = n > 1 ? n : 1; N <= DFT_RMAX * DFT_RMAX; ++N) {
+        double best = 1e30;
+        DftFactor f = {0, 0, 0};
+        for (int R2 = 1; R2 <= DFT_RMAX; ++R2) {
+            if (N % R2) continue;
+            const int R1 = N / R2;
+            if (R1 > DFT_RMAX) continue;
+            const double p1 = (double)((R1 + 15) / 16 * 16) / R1, p2 = (double)((R2 + 15) / 16 * 16) / R2;
+            const double tile = inner_tile ? (double)((R2 + 63) / 64 * 64) / R2 : 1.0;
+            const double cost = p1 * tile + p2;
+            if (cost < best) {
+                best = cost;
+                f = {N, R1, R2};
+            }
+        }
+        if (f.N) return f;
+    }
+    return {0, 0, 0};
+}
+
 // columns per CTA of the column pass: the largest power of two <= 16 whose two
 // buffers and twiddles stay within ~100 KB of shared memory
 int choose_cpc(int Ny)
@@ -184,7 +216,14 @@ int choose_cpc(int Ny)
 // the FFT method needs one geometry for the whole call and sizes within limits
 gf_status check_fft(const gf_desc* d, int count, const int* H, const int* W)
 {
-    if (resolve_method(d) != GF_CONV_FFT) return GF_OK;
+    const int m = resolve_method(d);
+    if (m == GF_CONV_DFT_TC) {
+        for (int b = 1; b < count; ++b)
+            if (H[b] != H[0] || W[b] != W[0])
+                return fail(GF_EINVAL, "DFT convolution needs stamps of one size per call");
+        return GF_OK;
+    }
+    if (m != GF_CONV_FFT) return GF_OK;
     const int c = (d->psf_size - 1) / 2;
     for (int b = 1; b < count; ++b)
         if (H[b] != H[0] || W[b] != W[0])
@@ -203,6 +242,11 @@ gf_status check_stamp(const gf_desc* d, int H, int W)
         const int c = (d->psf_size - 1) / 2;
         if (fft_len(H + 2 * c, false) > GF_FFT_MAX || fft_len(W + 2 * c, true) > GF_FFT_MAX)
             return fail(GF_EINVAL, "FFT size exceeds " + std::to_string(GF_FFT_MAX));
+    }
+    if (resolve_method(d) == GF_CONV_DFT_TC) {
+        const int c = (d->psf_size - 1) / 2;
+        if (H + 2 * c > DFT_RMAX * DFT_RMAX || W + 2 * c > DFT_RMAX * DFT_RMAX)
+            return fail(GF_EINVAL, "DFT size exceeds " + std::to_string(DFT_RMAX * DFT_RMAX));
     }
     if ((long long)H * W > (1LL << 31) - 1) return fail(GF_EINVAL, "stamp too large");
     if (d->os_factor > 1 && d->os_box > 0) {
@@ -315,6 +359,7 @@ struct Layout {
     size_t ids_static, n_static;            // the all-stamps work list (in the blob)
     size_t wl_n[2], wl_ids[2], wl_pre[2];   // LM work lists: 0 Jacobian pass, 1 trial pass
     size_t tw_x, tw_y, hhat, psfgrid, spec_jac, spec_trial;
+    size_t dft_buf[2], dft_mat;  // DFT path: ping-pong complex buffers, bf16 DFT matrices
     int count, nchan, nacc, nslots;
     int tot_model, tot_os, tot_conv, tot_red;
 };
@@ -323,8 +368,9 @@ struct Plan {
     Layout L;
     std::vector<StampInfo> st;
     std::vector<int> pre;  // 4 * (count + 1): model, os, conv, red
-    int method;            // GF_CONV_DIRECT or GF_CONV_FFT
+    int method;            // GF_CONV_DIRECT, GF_CONV_FFT or GF_CONV_DFT_TC
     int Nx, Ny, cpc;       // FFT geometry (method FFT)
+    DftFactor fx, fy;      // DFT geometry (method DFT_TC)
 };
 
 // Build the stamp table, the block tables and the workspace layout.
@@ -454,6 +500,29 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         L.spec_trial = o;
         o += al(sizeof(float2) * (size_t)count * s0.He * Kx);
     }
+    if (pl->method == GF_CONV_DFT_TC) {
+        const StampInfo& s0 = pl->st[0];
+        pl->fx = dft_factor(s0.We, true);
+        pl->fy = dft_factor(s0.He, false);
+        pl->Nx = pl->fx.N;
+        pl->Ny = pl->fy.N;
+        const size_t nn = (size_t)pl->Ny * pl->Nx;
+        const int nch = (need & (NEED_JAC | NEED_LM)) ? S.nchan : 1;
+        L.tw_x = o;
+        o += al(sizeof(float2) * pl->Nx);
+        L.tw_y = o;
+        o += al(sizeof(float2) * pl->Ny);
+        L.hhat = o;
+        o += al(sizeof(float2) * (size_t)count * nn);
+        L.psfgrid = o;
+        o += al(sizeof(float) * (size_t)count * nn);
+        for (int w = 0; w < 2; ++w) {
+            L.dft_buf[w] = o;
+            o += al(sizeof(float2) * (size_t)count * nch * nn);
+        }
+        L.dft_mat = o;
+        o += al(sizeof(__nv_bfloat16) * 8 * 4 * DFT_RMAX * DFT_RMAX);
+    }
     L.total = o;
 }
 
@@ -577,9 +646,197 @@ FFTArgs fft_args(void* ws, const Plan& pl)
     return f;
 }
 
+// ------------------------------------------------ DFT-contraction convolution
+int rpad16(int R) { return (R + 15) / 16 * 16; }
+
+// DFT matrix table t (0..7): axis x/y, digit 1/2, forward/inverse
+__nv_bfloat16* dft_matrix(void* ws, const Plan& pl, int axis, int digit, int inverse)
+{
+    const int t = (axis * 2 + digit) * 2 + inverse;
+    return at<__nv_bfloat16>(ws, pl.L.dft_mat) + (size_t)t * 4 * DFT_RMAX * DFT_RMAX;
+}
+
+DftStage dft_base(void* ws, const Plan& pl, const PassArgs& a)
+{
+    DftStage g;
+    memset(&g, 0, sizeof(g));
+    g.lm = a.lm;
+    g.phase = a.phase;
+    g.nchan = a.nchan > 0 ? a.nchan : 1;
+    return g;
+}
+
+void dft_set(DftStage& g, int R, const __nv_bfloat16* F)
+{
+    g.R = R;
+    g.Rp = rpad16(R);
+    g.F = F;
+}
+
+// the four forward stages: real grid(s) -> digit-reversed spectrum in `out`
+gf_status dft_forward(void* ws, const Plan& pl, DftStage g, const float* real, long long real_ps,
+                      int ld, int rows, int cols, float2* out, int nprob, unsigned long long* work,
+                      cudaStream_t s)
+{
+    const int Nx = pl.Nx, Ny = pl.Ny;
+    const long long nn = (long long)Ny * Nx;
+    float2* B0 = at<float2>(ws, pl.L.dft_buf[0]);
+    float2* B1 = at<float2>(ws, pl.L.dft_buf[1]);
+    g.in_pstride = g.out_pstride = nn;
+    // x axis, digit 1 (stride R2x), twiddle W_Nx^{k1 x2}
+    DftStage f1 = g;
+    dft_set(f1, pl.fx.R1, dft_matrix(ws, pl, 0, 0, 0));
+    f1.L = Ny;
+    f1.Q = pl.fx.R2;
+    f1.tw_mode = 1;
+    f1.tw_div = 1;
+    f1.tw_mod = pl.fx.R2;
+    f1.tw_N = Nx;
+    f1.tw = at<float2>(ws, pl.L.tw_x);
+    f1.tw_sign = -1.0f;
+    f1.in_mode = 1;
+    f1.in_real = real;
+    f1.in_real_pstride = real_ps;
+    f1.in_ld = ld;
+    f1.in_rows = rows;
+    f1.in_cols = cols;
+    f1.in_xdigit = pl.fx.R2;
+    f1.out = B0;
+    GF_CUDA(launch_dft_stage_a(f1, nprob, work, s));
+    // x axis, digit 2 (contiguous)
+    DftStage f2 = g;
+    dft_set(f2, pl.fx.R2, dft_matrix(ws, pl, 0, 1, 0));
+    f2.M = Ny * pl.fx.R1;
+    f2.in = B0;
+    f2.out = B1;
+    GF_CUDA(launch_dft_stage_b(f2, nprob, work, s));
+    // y axis, digit 1 (stride R2y * Nx), twiddle W_Ny^{k1 y2}, y2 = (q / Nx) % R2y
+    DftStage f3 = g;
+    dft_set(f3, pl.fy.R1, dft_matrix(ws, pl, 1, 0, 0));
+    f3.L = 1;
+    f3.Q = pl.fy.R2 * Nx;
+    f3.tw_mode = 1;
+    f3.tw_div = Nx;
+    f3.tw_mod = pl.fy.R2;
+    f3.tw_N = Ny;
+    f3.tw = at<float2>(ws, pl.L.tw_y);
+    f3.tw_sign = -1.0f;
+    f3.in = B1;
+    f3.out = B0;
+    GF_CUDA(launch_dft_stage_a(f3, nprob, work, s));
+    // y axis, digit 2 (stride Nx)
+    DftStage f4 = g;
+    dft_set(f4, pl.fy.R2, dft_matrix(ws, pl, 1, 1, 0));
+    f4.L = pl.fy.R1;
+    f4.Q = Nx;
+    f4.in = B0;
+    f4.out = out;
+    GF_CUDA(launch_dft_stage_a(f4, nprob, work, s));
+    return GF_OK;
+}
+
+gf_status run_conv_dft(const PassArgs& a, const Plan& pl, void* ws, cudaStream_t s)
+{
+    const StampInfo& s0 = pl.st[0];
+    const int Nx = pl.Nx, Ny = pl.Ny;
+    const long long nn = (long long)Ny * Nx;
+    const int nprob = a.count * a.nchan;
+    if (nprob > 65535) return fail(GF_EINVAL, "DFT convolution: stamps x channels must be <= 65535");
+    float2* B0 = at<float2>(ws, pl.L.dft_buf[0]);
+    float2* B1 = at<float2>(ws, pl.L.dft_buf[1]);
+    DftStage g = dft_base(ws, pl, a);
+    gf_status r = dft_forward(ws, pl, g, a.ext, (long long)s0.He * s0.We, s0.We, s0.He, s0.We,
+                              B1, nprob, a.work ? &a.work[PROF_CONV] : nullptr, s);
+    if (r != GF_OK) return r;
+    unsigned long long* work = a.work ? &a.work[PROF_CONV] : nullptr;
+    g.in_pstride = g.out_pstride = nn;
+    // inverse y, digit 2, with the PSF spectrum product and twiddle W_Ny^{+k1 y2}
+    DftStage i1 = g;
+    dft_set(i1, pl.fy.R2, dft_matrix(ws, pl, 1, 1, 1));
+    i1.L = pl.fy.R1;
+    i1.Q = Nx;
+    i1.tw_mode = 2;
+    i1.tw_N = Ny;
+    i1.tw = at<float2>(ws, pl.L.tw_y);
+    i1.tw_sign = 1.0f;
+    i1.in_mode = 2;
+    i1.in = B1;
+    i1.hhat = at<float2>(ws, pl.L.hhat);
+    i1.out = B0;
+    GF_CUDA(launch_dft_stage_a(i1, nprob, work, s));
+    // inverse y, digit 1
+    DftStage i2 = g;
+    dft_set(i2, pl.fy.R1, dft_matrix(ws, pl, 1, 0, 1));
+    i2.L = 1;
+    i2.Q = pl.fy.R2 * Nx;
+    i2.in = B0;
+    i2.out = B1;
+    GF_CUDA(launch_dft_stage_a(i2, nprob, work, s));
+    // inverse x, digit 2 (contiguous), twiddle W_Nx^{+k1 x2}, k1 = m mod R1x
+    DftStage i3 = g;
+    dft_set(i3, pl.fx.R2, dft_matrix(ws, pl, 0, 1, 1));
+    i3.M = Ny * pl.fx.R1;
+    i3.tw_mode = 3;
+    i3.tw_mod = pl.fx.R1;
+    i3.tw_N = Nx;
+    i3.tw = at<float2>(ws, pl.L.tw_x);
+    i3.tw_sign = 1.0f;
+    i3.in = B1;
+    i3.out = B0;
+    GF_CUDA(launch_dft_stage_b(i3, nprob, work, s));
+    // inverse x, digit 1, real part of the valid region into the pass output
+    DftStage i4 = g;
+    dft_set(i4, pl.fx.R1, dft_matrix(ws, pl, 0, 0, 1));
+    i4.L = Ny;
+    i4.Q = pl.fx.R2;
+    i4.in = B0;
+    i4.out_mode = 1;
+    i4.out_real = a.y;
+    i4.out_real_pstride = (long long)s0.H * s0.W;
+    i4.out_xdigit = pl.fx.R2;
+    i4.crop_y0 = s0.c;
+    i4.crop_x0 = s0.c;
+    i4.crop_H = s0.H;
+    i4.crop_W = s0.W;
+    GF_CUDA(launch_dft_stage_a(i4, nprob, work, s));
+    return GF_OK;
+}
+
+gf_status setup_conv_dft(void* ws, const Plan& pl, const float* psf, cudaStream_t s)
+{
+    FFTArgs f;
+    memset(&f, 0, sizeof(f));
+    f.Nx = pl.Nx;
+    f.Ny = pl.Ny;
+    f.tw_x = at<float2>(ws, pl.L.tw_x);
+    f.tw_y = at<float2>(ws, pl.L.tw_y);
+    f.psfgrid = at<float>(ws, pl.L.psfgrid);
+    GF_CUDA(launch_fft_twiddles(f, s));
+    const int Rs[4] = {pl.fx.R1, pl.fx.R2, pl.fy.R1, pl.fy.R2};
+    for (int axis = 0; axis < 2; ++axis)
+        for (int digit = 0; digit < 2; ++digit)
+            for (int inv = 0; inv < 2; ++inv) {
+                const int R = Rs[axis * 2 + digit];
+                GF_CUDA(launch_dft_matrix(R, rpad16(R), inv ? 1.0f : -1.0f,
+                                          dft_matrix(ws, pl, axis, digit, inv), s));
+            }
+    GF_CUDA(cudaMemsetAsync(f.psfgrid, 0, sizeof(float) * (size_t)pl.L.count * pl.Ny * pl.Nx, s));
+    GF_CUDA(launch_psf_wrap(f, pl.L.count, at<StampInfo>(ws, pl.L.st), psf, s));
+    PassArgs none;
+    memset(&none, 0, sizeof(none));
+    none.nchan = 1;
+    DftStage g = dft_base(ws, pl, none);
+    return dft_forward(ws, pl, g, f.psfgrid, (long long)pl.Ny * pl.Nx, pl.Nx, pl.Ny, pl.Nx,
+                       at<float2>(ws, pl.L.hhat), pl.L.count, nullptr, s);
+}
+
 // per-call set-up of the convolution: twiddles and PSF spectra (FFT method)
 gf_status setup_conv(void* ws, const Plan& pl, const float* psf, cudaStream_t s)
 {
+    if (pl.method == GF_CONV_DFT_TC) {
+        ProfScope ps(PROF_CONV, s);
+        return setup_conv_dft(ws, pl, psf, s);
+    }
     if (pl.method != GF_CONV_FFT) return GF_OK;
     ProfScope ps(PROF_CONV, s);
     const FFTArgs f = fft_args(ws, pl);
@@ -596,6 +853,7 @@ gf_status run_conv(const PassArgs& a, const Plan& pl, void* ws, size_t spec_off,
         GF_CUDA(launch_conv_direct(a, s));
         return GF_OK;
     }
+    if (pl.method == GF_CONV_DFT_TC) return run_conv_dft(a, pl, ws, s);
     if ((long long)a.count * a.nchan > 65535)
         return fail(GF_EINVAL, "FFT convolution: stamps x channels per call must be <= 65535");
     GF_CUDA(launch_conv_fft(a, fft_args(ws, pl), at<float2>(ws, spec_off), s));

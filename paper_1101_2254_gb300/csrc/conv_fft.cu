@@ -202,6 +202,14 @@ static cudaError_t optin_all(const FFTArgs& f)
     return e;
 }
 
+cudaError_t launch_psf_wrap(const FFTArgs& f, int count, const StampInfo* st, const float* psf,
+                            cudaStream_t s)
+{
+    k_psf_wrap<<<dim3(8, count), 256, 0, s>>>(f, count, st, psf);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
 // PSF spectra of all stamps of a call (uniform size): wrap, row pass over all
 // Ny rows, forward column pass.
 cudaError_t launch_fft_psf(const FFTArgs& f, int count, const StampInfo* st, const float* psf,

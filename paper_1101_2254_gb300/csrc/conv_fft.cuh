@@ -50,3 +50,6 @@ cudaError_t launch_fft_twiddles(const FFTArgs& f, cudaStream_t s);
 cudaError_t launch_fft_psf(const FFTArgs& f, int count, const StampInfo* st, const float* psf,
                            cudaStream_t s);
 cudaError_t launch_conv_fft(const PassArgs& a, const FFTArgs& f, float2* spec, cudaStream_t s);
+// the wrapped, 1/(Ny Nx)-scaled PSF grids (zeroed by the caller)
+cudaError_t launch_psf_wrap(const FFTArgs& f, int count, const StampInfo* st, const float* psf,
+                            cudaStream_t s);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libgf.so")
 
 SERSIC, EXPDISK, SKY = 1, 2, 3
 NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1}
-CONV_AUTO, CONV_DIRECT, CONV_FFT = 0, 1, 2
+CONV_AUTO, CONV_DIRECT, CONV_FFT, CONV_DFT_TC = 0, 1, 2, 3
 CALL_MODEL, CALL_CONVOLVE, CALL_CHI2, CALL_EVAL, CALL_JACOBIAN, CALL_LM_FIT = range(6)
 OK, EINVAL, ECUDA, ENOCONV, ESINGULAR, ENONFINITE, ETIMEOUT, ENOMEM, EMAXITER = range(9)
 MAX_COMP = 8
