@@ -188,6 +188,18 @@ gf_status gf_eval(const gf_desc* d, const double* params_host, const float* imag
                   const float* sigma_dev, const float* psf_dev, float* model_dev,
                   double* chi2_dev, void* ws, size_t ws_bytes, gf_stream stream);
 
+/* Steps 1-3 for many stamps of one structure at once: params_host is
+ * count x nslots, chi2_dev receives count float64 values, model_dev (may be
+ * NULL) the convolved models packed like the images.  Workspace:
+ * gf_workspace_size_eval_batch(). */
+gf_status gf_eval_batch(const gf_desc* d, const gf_batch* b, const double* params_host,
+                        const float* image_dev, const float* sigma_dev, const float* psf_dev,
+                        float* model_dev, double* chi2_dev, void* ws, size_t ws_bytes,
+                        gf_stream stream);
+
+/* Workspace bytes for gf_eval_batch. */
+size_t gf_workspace_size_eval_batch(const gf_desc* d, const gf_batch* b);
+
 /* The input of step 4: Jacobian columns of the convolved model with respect to
  * the free slots, in slot order.  Amplitude and sky slots use the exact column
  * (the convolved unit-amplitude component; sum(psf) for the sky); the others

@@ -1009,6 +1009,20 @@ size_t gf_workspace_size(const gf_desc* d, const uint8_t* fixed, int call)
     return pl.L.total;
 }
 
+size_t gf_workspace_size_eval_batch(const gf_desc* d, const gf_batch* b)
+{
+    if (!b || b->count < 1 || !b->H || !b->W) return 0;
+    if (check_structure(d) != GF_OK) return 0;
+    for (int i = 0; i < b->count; ++i)
+        if (check_stamp(d, b->H[i], b->W[i]) != GF_OK) return 0;
+    if (check_fft(d, b->count, b->H, b->W) != GF_OK) return 0;
+    Structure S;
+    if (make_structure(d, nullptr, nullptr, nullptr, nullptr, &S) != GF_OK) return 0;
+    Plan pl;
+    plan_batch(d, S, b->count, b->H, b->W, b->pix_off, b->psf_off, NEED_TRIAL, &pl);
+    return pl.L.total;
+}
+
 size_t gf_workspace_size_batch(const gf_desc* d, const gf_batch* b, const uint8_t* fixed)
 {
     if (!b || b->count < 1 || !b->H || !b->W) return 0;
@@ -1115,6 +1129,31 @@ gf_status gf_eval(const gf_desc* d, const double* params, const float* img, cons
     if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, &S)) != GF_OK) return r;
     Plan pl;
     plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, NEED_TRIAL, &pl);
+    if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
+    PassArgs a = trial_args(ws, pl.L, base_args(ws, pl.L, psf, img, sig, d->psf_size));
+    a.m_out = model_out;
+    if ((r = setup_conv(ws, pl, psf, s)) != GF_OK) return r;
+    GF_CUDA(launch_prep_sum(a, at<double>(ws, pl.L.params), 0, s));
+    return trial_pass(a, pl, ws, s, chi2);
+}
+
+gf_status gf_eval_batch(const gf_desc* d, const gf_batch* b, const double* params,
+                        const float* img, const float* sig, const float* psf, float* model_out,
+                        double* chi2, void* ws, size_t ws_bytes, gf_stream stream)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    if (!b || b->count < 1 || !b->H || !b->W) return fail(GF_EINVAL, "bad batch");
+    for (int i = 0; i < b->count; ++i)
+        if ((r = check_stamp(d, b->H[i], b->W[i])) != GF_OK) return r;
+    if ((r = check_fft(d, b->count, b->H, b->W)) != GF_OK) return r;
+    if (!params || !img || !sig || !psf || !chi2) return fail(GF_EINVAL, "NULL argument");
+    Structure S;
+    if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, &S)) != GF_OK) return r;
+    Plan pl;
+    plan_batch(d, S, b->count, b->H, b->W, b->pix_off, b->psf_off, NEED_TRIAL, &pl);
     if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
     if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;

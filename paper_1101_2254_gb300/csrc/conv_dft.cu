@@ -117,10 +117,10 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b)
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__device__ __forceinline__ float2 twiddle(const DftStage& s, long long e)
+// e >= 0 and below 64 * 4096 for every stage, so 32-bit arithmetic suffices
+__device__ __forceinline__ float2 twiddle(const DftStage& s, int e)
 {
     e %= s.tw_N;
-    if (e < 0) e += s.tw_N;
     float2 w = s.tw[e];
     if (s.tw_sign > 0.0f) w.y = -w.y;
     return w;
@@ -221,9 +221,9 @@ __global__ void __launch_bounds__(NT) k_dft_a(DftStage s, unsigned long long* wo
                         if (k >= R || q >= s.Q) continue;
                         float2 v = make_float2(acc[mt][nt][0][2 * hf + j], acc[mt][nt][1][2 * hf + j]);
                         if (s.tw_mode == 1)
-                            v = cmulf(v, twiddle(s, (long long)k * ((q / s.tw_div) % s.tw_mod)));
+                            v = cmulf(v, twiddle(s, k * ((q / s.tw_div) % s.tw_mod)));
                         else if (s.tw_mode == 2)
-                            v = cmulf(v, twiddle(s, (long long)l * k));
+                            v = cmulf(v, twiddle(s, l * k));
                         if (s.out_mode == 0) {
                             s.out[(long long)p * s.out_pstride + ((long long)l * R + k) * s.Q + q] = v;
                         } else {
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(NT) k_dft_b(DftStage s, unsigned long long* wo
                     const int k = 8 * nt + 2 * t + j;
                     if (m >= s.M || k >= R) continue;
                     float2 v = make_float2(acc[nt][0][2 * hf + j], acc[nt][1][2 * hf + j]);
-                    if (s.tw_mode == 3) v = cmulf(v, twiddle(s, (long long)(m % s.tw_mod) * k));
+                    if (s.tw_mode == 3) v = cmulf(v, twiddle(s, (m % s.tw_mod) * k));
                     s.out[(long long)p * s.out_pstride + (long long)m * R + k] = v;
                 }
         }

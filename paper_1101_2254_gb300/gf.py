@@ -95,6 +95,11 @@ def lib():
             L.gf_lm_fit_batch.argtypes = [pd, C.POINTER(Batch), dp, C.c_char_p, fp, fp, fp,
                                           C.POINTER(LMOpts), C.POINTER(LMResult), vp,
                                           C.c_size_t, vp]
+            L.gf_eval_batch.restype = C.c_int
+            L.gf_eval_batch.argtypes = [pd, C.POINTER(Batch), dp, fp, fp, fp, fp, vp, vp,
+                                        C.c_size_t, vp]
+            L.gf_workspace_size_eval_batch.restype = C.c_size_t
+            L.gf_workspace_size_eval_batch.argtypes = [pd, C.POINTER(Batch)]
             L.gf_static_scratch_bytes.restype = C.c_size_t
             L.gf_eval_static.restype = C.c_int
             L.gf_eval_static.argtypes = [pd, dp, fp, fp, fp, fp, vp, vp]
@@ -318,6 +323,19 @@ def make_batch(Hs, Ws, pix_off=None, psf_off=None, psf_size=None):
     b.psf_off = psf_off.ctypes.data_as(C.POINTER(C.c_int64))
     b._keep = (Hs, Ws, pix_off, psf_off)
     return b
+
+
+def evaluate_batch(d: Desc, batch: Batch, params, img, sig, psf, want_model=False, ws=None,
+                   stream=None):
+    """Steps 1-3 for a batch: (chi2 [count] float64 device tensor, packed models or None)."""
+    import torch
+    p = np.ascontiguousarray(np.asarray(params, np.float64))
+    x2 = torch.empty(batch.count, dtype=torch.float64, device="cuda")
+    m = torch.empty_like(img) if want_model else None
+    w, n = _ws(ws).get(lib().gf_workspace_size_eval_batch(C.byref(d), C.byref(batch)))
+    _check(lib().gf_eval_batch(C.byref(d), C.byref(batch), _dp(p), _ptr(img), _ptr(sig),
+                               _ptr(psf), _ptr(m), _ptr(x2), w, n, _stream(stream)))
+    return x2, m
 
 
 def lm_fit_batch(d: Desc, batch: Batch, params, fixed, img, sig, psf,
