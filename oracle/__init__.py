@@ -31,6 +31,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
 SRC = os.path.join(HERE, "gfo.c")
+SRC_CNN = os.path.join(HERE, "gfo_cnn.c")
 
 SERSIC, EXPDISK, SKY = 1, 2, 3
 NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1}
@@ -43,12 +44,12 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile gfo.c into liboracle.so with gcc (portable flags, OpenMP)."""
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "gfo.h"))
+        os.path.getmtime(SRC), os.path.getmtime(SRC_CNN), os.path.getmtime(os.path.join(HERE, "gfo.h"))
     ):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
-           "-D_GNU_SOURCE", SRC, "-o", tmp, "-lm"]
+           "-D_GNU_SOURCE", SRC, SRC_CNN, "-o", tmp, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB
@@ -116,6 +117,11 @@ def lib():
                                            C.POINTER(C.c_int64), C.c_int, C.POINTER(Opts),
                                            C.POINTER(Result)]
             L.gfo_num_threads.restype = C.c_int
+            L.gfo_cnn_nparams.restype = C.c_long
+            L.gfo_cnn_forward.argtypes = [dp, dp, C.c_int, dp]
+            L.gfo_cnn_loss_grad.restype = C.c_double
+            L.gfo_cnn_loss_grad.argtypes = [dp, dp, dp, C.c_int, dp]
+            L.gfo_default_guess.argtypes = [dp, C.c_int, C.c_int, dp]
             _lib = L
     return _lib
 
@@ -305,3 +311,33 @@ def lm_fit_batch(descs, params, fixed, psf_flat, psf_off, img_flat, sigma_flat, 
 
 def num_threads() -> int:
     return lib().gfo_num_threads()
+
+
+# ---------------------------------------------------------------- network
+def cnn_nparams() -> int:
+    return int(lib().gfo_cnn_nparams())
+
+
+def cnn_forward(w, x) -> np.ndarray:
+    """Network outputs (nb x 8) for inputs x (nb x 64 x 64)."""
+    w, x = _f64(w), _f64(x)
+    nb = x.shape[0]
+    y = np.empty((nb, 8), np.float64)
+    lib().gfo_cnn_forward(_dp(w), _dp(x), nb, _dp(y))
+    return y
+
+
+def cnn_loss_grad(w, x, t):
+    """(mean squared error, gradient) for inputs x (nb x 64 x 64) and targets t (nb x 8)."""
+    w, x, t = _f64(w), _f64(x), _f64(t)
+    g = np.empty_like(w)
+    loss = lib().gfo_cnn_loss_grad(_dp(w), _dp(x), _dp(t), x.shape[0], _dp(g))
+    return loss, g
+
+
+def default_guess(img) -> np.ndarray:
+    """Moments-based Sersic + sky start (9 slots) for an image."""
+    img = _f64(img)
+    out = np.empty(9, np.float64)
+    lib().gfo_default_guess(_dp(img), img.shape[0], img.shape[1], _dp(out))
+    return out
