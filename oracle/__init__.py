@@ -122,6 +122,9 @@ def lib():
             L.gfo_cnn_loss_grad.restype = C.c_double
             L.gfo_cnn_loss_grad.argtypes = [dp, dp, dp, C.c_int, dp]
             L.gfo_default_guess.argtypes = [dp, C.c_int, C.c_int, dp]
+            L.gfo_cnn_input.argtypes = [dp, dp, C.c_int, C.c_int, dp]
+            L.gfo_cnn_encode.argtypes = [dp, C.c_int, C.c_int, dp]
+            L.gfo_cnn_decode.argtypes = [dp, C.c_int, C.c_int, dp]
             _lib = L
     return _lib
 
@@ -341,3 +344,28 @@ def default_guess(img) -> np.ndarray:
     out = np.empty(9, np.float64)
     lib().gfo_default_guess(_dp(img), img.shape[0], img.shape[1], _dp(out))
     return out
+
+
+def cnn_input(img, sigma) -> np.ndarray:
+    """Network input asinh(img / a), a = median sigma over the outer ring."""
+    img = _f64(img)
+    sigma = _f64(sigma)
+    x = np.empty_like(img)
+    lib().gfo_cnn_input(_dp(img), _dp(sigma), img.shape[0], img.shape[1], _dp(x))
+    return x
+
+
+def cnn_encode(p, H, W) -> np.ndarray:
+    """Eight regression targets of Sersic slots p[0:7] in an H x W stamp."""
+    p = _f64(p)
+    t = np.empty(8)
+    lib().gfo_cnn_encode(_dp(p), H, W, _dp(t))
+    return t
+
+
+def cnn_decode(t, H, W) -> np.ndarray:
+    """Sersic slots (8, c = 0) from eight targets; I_e NaN outside the flux domain."""
+    t = _f64(t)
+    p = np.empty(8)
+    lib().gfo_cnn_decode(_dp(t), H, W, _dp(p))
+    return p

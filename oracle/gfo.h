@@ -147,5 +147,10 @@ void gfo_cnn_forward(const double* w, const double* x, int nb, double* y);
 double gfo_cnn_loss_grad(const double* w, const double* x, const double* t, int nb, double* grad);
 /* moments-based start of a Sersic + sky fit: x0, y0, I_e, r_e, n, q, pa, c, sky */
 void gfo_default_guess(const double* img, int H, int W, double* out);
+/* network input asinh(img / a), a = median sigma over the outer ring */
+void gfo_cnn_input(const double* img, const double* sigma, int H, int W, double* x);
+/* regression targets (8) of Sersic slots p (7 used), and the inverse */
+void gfo_cnn_encode(const double* p, int H, int W, double* t);
+void gfo_cnn_decode(const double* t, int H, int W, double* p);
 
 #endif

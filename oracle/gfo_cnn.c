@@ -201,8 +201,8 @@ static int cmp_double(const void* a, const void* b)
  *   sky   = median of the border pixels (outermost ring);
  *   x0,y0 = first moments of the sky-subtracted positive pixels;
  *   q, pa = from the second moments (eigen-decomposition of the 2x2 matrix);
- *   r_e   = geometric-mean radius (r sqrt(q) scale) of the elliptical aperture,
- *           grown in 0.25 px steps, that first holds half the summed flux;
+ *   r_e   = semi-major axis of the elliptical aperture (axis ratio q, angle
+ *           pa), grown in 0.25 px steps, that first holds half the summed flux;
  *   n     = 2;  I_e from the summed flux by the closed-form Sersic flux.
  * Output slots: x0, y0, I_e, r_e, n, q, pa_deg, c(=0), sky. */
 void gfo_default_guess(const double* img, int H, int W, double* out)
@@ -284,4 +284,68 @@ void gfo_default_guess(const double* img, int H, int W, double* out)
     out[6] = pa;
     out[7] = 0.0;
     out[8] = sky;
+}
+
+/* ------------------------------------------- network input and targets */
+
+/* Input scaling of one H x W stamp: x = asinh(img / a), a = median of sigma
+ * over the outermost ring of pixels (mean of the two middle values when the
+ * ring has an even count). */
+void gfo_cnn_input(const double* img, const double* sigma, int H, int W, double* x)
+{
+    int nb = (H == 1 || W == 1) ? H * W : 2 * W + 2 * (H - 2);
+    double* ring = (double*)malloc(sizeof(double) * nb);
+    int k = 0;
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j)
+            if (i == 0 || j == 0 || i == H - 1 || j == W - 1) ring[k++] = sigma[(long)i * W + j];
+    qsort(ring, k, sizeof(double), cmp_double);
+    double a = (k % 2) ? ring[k / 2] : 0.5 * (ring[k / 2 - 1] + ring[k / 2]);
+    free(ring);
+    if (!(a > 0.0)) a = 1.0;
+    for (long p = 0; p < (long)H * W; ++p) x[p] = asinh(img[p] / a);
+}
+
+/* Targets of one Sersic component in an H x W stamp (slots x0, y0, I_e, r_e,
+ * n, q, pa_deg), each scaled so the training prior spans about [-1, 1]:
+ *   t0, t1 = offsets of the centre from the stamp centre ((W-1)/2, (H-1)/2)
+ *   t2 = (ln F - 3.5 ln 10) / (1.5 ln 10),  F the closed-form total flux
+ *   t3 = (ln r_e - ln 80 / 2) / (ln 20 / 2)
+ *   t4 = (n - 3.25) / 2.75,   t5 = (q - 0.6) / 0.4
+ *   t6, t7 = cos 2 pa, sin 2 pa  (the angle is defined modulo 180 degrees) */
+void gfo_cnn_encode(const double* p, int H, int W, double* t)
+{
+    const double l10 = log(10.0);
+    double F = gfo_sersic_flux(p[2], p[3], p[4], p[5]);
+    double th = 2.0 * p[6] * M_PI / 180.0;
+    t[0] = p[0] - 0.5 * (W - 1);
+    t[1] = p[1] - 0.5 * (H - 1);
+    t[2] = (log(F) - 3.5 * l10) / (1.5 * l10);
+    t[3] = (log(p[3]) - 0.5 * log(80.0)) / (0.5 * log(20.0));
+    t[4] = (p[4] - 3.25) / 2.75;
+    t[5] = (p[5] - 0.6) / 0.4;
+    t[6] = cos(th);
+    t[7] = sin(th);
+}
+
+/* Inverse of gfo_cnn_encode: Sersic slots x0, y0, I_e, r_e, n, q, pa_deg, c
+ * (c = 0).  I_e is NaN where n leaves [0.2, 10] or q leaves (0, 1], the domain
+ * of the closed-form flux. */
+void gfo_cnn_decode(const double* t, int H, int W, double* p)
+{
+    const double l10 = log(10.0);
+    double F = exp(3.5 * l10 + 1.5 * l10 * t[2]);
+    double re = exp(0.5 * log(80.0) + 0.5 * log(20.0) * t[3]);
+    double n = 3.25 + 2.75 * t[4];
+    double q = 0.6 + 0.4 * t[5];
+    double pa = 0.5 * atan2(t[7], t[6]) * 180.0 / M_PI;
+    if (pa < 0.0) pa += 180.0;
+    p[0] = 0.5 * (W - 1) + t[0];
+    p[1] = 0.5 * (H - 1) + t[1];
+    p[2] = (n >= 0.2 && n <= 10.0 && q > 0.0 && q <= 1.0) ? F / gfo_sersic_flux(1.0, re, n, q) : NAN;
+    p[3] = re;
+    p[4] = n;
+    p[5] = q;
+    p[6] = pa;
+    p[7] = 0.0;
 }

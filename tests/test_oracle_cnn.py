@@ -106,3 +106,48 @@ def test_default_guess_on_a_sampled_gaussian():
     # I_e reproduces the summed flux through the closed form
     F = (img - sky)[img - sky > 0].sum()
     assert abs(oracle.sersic_flux(g[2], g[3], 2.0, g[5]) - F) < 1e-9 * F
+
+
+def test_input_scaling_median_ring_and_asinh():
+    # ring sigmas are a permutation of 1..252: the median is (126 + 127) / 2
+    rng = np.random.default_rng(5)
+    H = W = 64
+    sig = rng.uniform(300.0, 400.0, (H, W))
+    ring = np.zeros((H, W), bool)
+    ring[0, :] = ring[-1, :] = ring[:, 0] = ring[:, -1] = True
+    sig[ring] = rng.permutation(np.arange(1.0, 253.0))
+    z = rng.standard_normal((H, W)) * 3.0
+    img = 126.5 * np.sinh(z)
+    x = oracle.cnn_input(img, sig)
+    assert np.abs(x - z).max() < 1e-12 * np.abs(z).max()
+
+
+def test_target_encoding_reference_points_and_round_trip():
+    # the centre of every scaled range encodes to zero
+    n = 3.25
+    q = 0.6
+    re = math.sqrt(80.0)
+    F = 10.0 ** 3.5
+    ie = F / oracle.sersic_flux(1.0, re, n, q)
+    t = oracle.cnn_encode([31.5, 31.5, ie, re, n, q, 45.0], 64, 64)
+    assert np.abs(t[:6]).max() < 1e-12
+    assert abs(t[6]) < 1e-15 and abs(t[7] - 1.0) < 1e-15  # 2 * 45 deg = 90 deg
+    # range ends: r_e = 40 and F = 1e5 map to +1, n = 0.5 and q = 0.2 to -1
+    ie = 1e5 / oracle.sersic_flux(1.0, 40.0, 0.5, 0.2)
+    t = oracle.cnn_encode([30.5, 32.0, ie, 40.0, 0.5, 0.2, 135.0], 64, 64)
+    assert np.allclose(t, [-1.0, 0.5, 1.0, 1.0, -1.0, -1.0, 0.0, -1.0], atol=1e-12)
+    # decode inverts encode over the training prior
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        p = np.array([31.5 + rng.uniform(-1, 1), 31.5 + rng.uniform(-1, 1), 0.0,
+                      math.exp(rng.uniform(math.log(2), math.log(40))), rng.uniform(0.5, 6),
+                      rng.uniform(0.2, 1.0), rng.uniform(0, 180), 0.0])
+        p[2] = math.exp(rng.uniform(math.log(1e2), math.log(1e5))) / oracle.sersic_flux(
+            1.0, p[3], p[4], p[5])
+        back = oracle.cnn_decode(oracle.cnn_encode(p, 64, 64), 64, 64)
+        assert np.abs(back[[0, 1, 4, 5]] - p[[0, 1, 4, 5]]).max() < 1e-12
+        assert abs(back[2] / p[2] - 1) < 1e-12 and abs(back[3] / p[3] - 1) < 1e-12
+        dpa = (back[6] - p[6] + 90.0) % 180.0 - 90.0
+        assert abs(dpa) < 1e-9 and back[7] == 0.0
+    # outside the flux domain the amplitude is not a number
+    assert math.isnan(oracle.cnn_decode([0, 0, 0, 0, 4.0, 0, 1, 0], 64, 64)[2])
