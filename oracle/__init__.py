@@ -118,9 +118,11 @@ def lib():
                                            C.POINTER(Result)]
             L.gfo_num_threads.restype = C.c_int
             L.gfo_cnn_nparams.restype = C.c_long
-            L.gfo_cnn_forward.argtypes = [dp, dp, C.c_int, dp]
+            L.gfo_cnn_forward.argtypes = [dp, dp, C.c_int, dp, C.c_int]
             L.gfo_cnn_loss_grad.restype = C.c_double
-            L.gfo_cnn_loss_grad.argtypes = [dp, dp, dp, C.c_int, dp]
+            L.gfo_cnn_loss_grad.argtypes = [dp, dp, dp, C.c_int, dp, C.c_int]
+            L.gfo_bf16_round.restype = C.c_double
+            L.gfo_bf16_round.argtypes = [C.c_double]
             L.gfo_default_guess.argtypes = [dp, C.c_int, C.c_int, dp]
             L.gfo_cnn_input.argtypes = [dp, dp, C.c_int, C.c_int, dp]
             L.gfo_cnn_encode.argtypes = [dp, C.c_int, C.c_int, dp]
@@ -321,21 +323,27 @@ def cnn_nparams() -> int:
     return int(lib().gfo_cnn_nparams())
 
 
-def cnn_forward(w, x) -> np.ndarray:
-    """Network outputs (nb x 8) for inputs x (nb x 64 x 64)."""
+def cnn_forward(w, x, bf16_act: bool = False) -> np.ndarray:
+    """Network outputs (nb x 8) for inputs x (nb x 64 x 64); bf16_act stores the
+    convolution outputs as bfloat16 (the network's specified precision)."""
     w, x = _f64(w), _f64(x)
     nb = x.shape[0]
     y = np.empty((nb, 8), np.float64)
-    lib().gfo_cnn_forward(_dp(w), _dp(x), nb, _dp(y))
+    lib().gfo_cnn_forward(_dp(w), _dp(x), nb, _dp(y), int(bf16_act))
     return y
 
 
-def cnn_loss_grad(w, x, t):
+def cnn_loss_grad(w, x, t, bf16_act: bool = False):
     """(mean squared error, gradient) for inputs x (nb x 64 x 64) and targets t (nb x 8)."""
     w, x, t = _f64(w), _f64(x), _f64(t)
     g = np.empty_like(w)
-    loss = lib().gfo_cnn_loss_grad(_dp(w), _dp(x), _dp(t), x.shape[0], _dp(g))
+    loss = lib().gfo_cnn_loss_grad(_dp(w), _dp(x), _dp(t), x.shape[0], _dp(g), int(bf16_act))
     return loss, g
+
+
+def bf16_round(v: float) -> float:
+    """Nearest bfloat16 (ties to even) of a float64 value."""
+    return float(lib().gfo_bf16_round(float(v)))
 
 
 def default_guess(img) -> np.ndarray:

@@ -141,10 +141,14 @@ int gfo_num_threads(void);
 
 /* ---- initial-guess network and default guess (gfo_cnn.c) ---- */
 long gfo_cnn_nparams(void);
-/* outputs y (nb x 8) of the network with parameters w for inputs x (nb x 64 x 64) */
-void gfo_cnn_forward(const double* w, const double* x, int nb, double* y);
+/* outputs y (nb x 8) of the network with parameters w for inputs x (nb x 64 x 64);
+ * round_act = 1 stores the convolution outputs as bfloat16 */
+void gfo_cnn_forward(const double* w, const double* x, int nb, double* y, int round_act);
 /* mean squared error against targets t (nb x 8) and its gradient (nparams) */
-double gfo_cnn_loss_grad(const double* w, const double* x, const double* t, int nb, double* grad);
+double gfo_cnn_loss_grad(const double* w, const double* x, const double* t, int nb, double* grad,
+                         int round_act);
+/* nearest bfloat16, ties to even */
+double gfo_bf16_round(double v);
 /* moments-based start of a Sersic + sky fit: x0, y0, I_e, r_e, n, q, pa, c, sky */
 void gfo_default_guess(const double* img, int H, int W, double* out);
 /* network input asinh(img / a), a = median sigma over the outer ring */

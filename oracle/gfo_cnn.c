@@ -15,6 +15,7 @@
  * Loss: mean over the batch and the 8 outputs of (y - t)^2.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -45,9 +46,26 @@ static long layer_size(const layer_t* L, int out)
                    : (out ? L->cout : L->cin);
 }
 
+/* Round to the nearest bfloat16 (8 significant bits), ties to even: first to
+ * the nearest float32, then the low 16 bits of its encoding are dropped with
+ * round-to-nearest-even on them. */
+double gfo_bf16_round(double v)
+{
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, sizeof(u));
+    if ((u & 0x7f800000u) == 0x7f800000u) return (double)f; /* inf, nan */
+    u += 0x7fffu + ((u >> 16) & 1u);
+    u &= 0xffff0000u;
+    memcpy(&f, &u, sizeof(f));
+    return (double)f;
+}
+
 /* one sample's forward; acts[i] = output of layer i after ReLU (pre-ReLU kept
- * in pre[i]); acts[-1] is the input */
-static void forward1(const double* w, const double* x, double** pre, double** act)
+ * in pre[i]); acts[-1] is the input.  round_act = 1 stores the outputs of the
+ * four convolution layers as bfloat16, the precision the network is specified
+ * in; the derivative of that rounding is taken as 1. */
+static void forward1(const double* w, const double* x, double** pre, double** act, int round_act)
 {
     const double* in = x;
     long off = 0;
@@ -72,6 +90,7 @@ static void forward1(const double* w, const double* x, double** pre, double** ac
                         long o = (co * L->hout + oy) * L->hout + ox;
                         pre[li][o] = s;
                         act[li][o] = s > 0.0 ? s : 0.0;
+                        if (round_act) act[li][o] = gfo_bf16_round(act[li][o]);
                     }
         } else {
             for (int co = 0; co < L->cout; ++co) {
@@ -86,7 +105,7 @@ static void forward1(const double* w, const double* x, double** pre, double** ac
 }
 
 /* Forward of nb samples x (nb x 4096), outputs y (nb x 8). */
-void gfo_cnn_forward(const double* w, const double* x, int nb, double* y)
+void gfo_cnn_forward(const double* w, const double* x, int nb, double* y, int round_act)
 {
     double* pre[6];
     double* act[6];
@@ -95,7 +114,7 @@ void gfo_cnn_forward(const double* w, const double* x, int nb, double* y)
         act[i] = (double*)malloc(sizeof(double) * layer_size(&LAYERS[i], 1));
     }
     for (int s = 0; s < nb; ++s) {
-        forward1(w, x + (long)s * 4096, pre, act);
+        forward1(w, x + (long)s * 4096, pre, act, round_act);
         memcpy(y + (long)s * 8, act[5], sizeof(double) * 8);
     }
     for (int i = 0; i < 6; ++i) {
@@ -107,7 +126,8 @@ void gfo_cnn_forward(const double* w, const double* x, int nb, double* y)
 /* Loss (mean squared error over nb x 8) and its gradient with respect to every
  * parameter, by reverse-mode differentiation of forward1 (chain rule through
  * each layer in reverse order). */
-double gfo_cnn_loss_grad(const double* w, const double* x, const double* t, int nb, double* grad)
+double gfo_cnn_loss_grad(const double* w, const double* x, const double* t, int nb, double* grad,
+                         int round_act)
 {
     const long np = gfo_cnn_nparams();
     memset(grad, 0, sizeof(double) * np);
@@ -131,7 +151,7 @@ double gfo_cnn_loss_grad(const double* w, const double* x, const double* t, int 
     const double scale = 1.0 / (8.0 * nb);
     for (int s = 0; s < nb; ++s) {
         const double* xs = x + (long)s * 4096;
-        forward1(w, xs, pre, act);
+        forward1(w, xs, pre, act, round_act);
         for (int j = 0; j < 8; ++j) {
             double e = act[5][j] - t[(long)s * 8 + j];
             loss += e * e * scale;

@@ -151,3 +151,37 @@ def test_target_encoding_reference_points_and_round_trip():
         assert abs(dpa) < 1e-9 and back[7] == 0.0
     # outside the flux domain the amplitude is not a number
     assert math.isnan(oracle.cnn_decode([0, 0, 0, 0, 4.0, 0, 1, 0], 64, 64)[2])
+
+
+def test_bf16_rounding_matches_library_conversion():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    v = np.concatenate([rng.standard_normal(2000) * 10.0 ** rng.integers(-30, 30, 2000),
+                        # ties: exactly half-way between two bfloat16 neighbours
+                        (1.0 + (2 * np.arange(1, 200) + 1) * 2.0 ** -8) * 0.75,
+                        [0.0, -0.0, 1.0, -2.5, 3.0e38, 1e-40]]).astype(np.float32)
+    want = torch.as_tensor(v).bfloat16().float().numpy().astype(np.float64)
+    got = np.array([oracle.bf16_round(float(a)) for a in v])
+    assert np.array_equal(got, want)
+
+
+def test_bf16_activation_mode():
+    w = he_init(12)
+    rng = np.random.default_rng(13)
+    x = rng.standard_normal((2, 64, 64))
+    t = rng.standard_normal((2, 8))
+    y0 = oracle.cnn_forward(w, x)
+    y1 = oracle.cnn_forward(w, x, bf16_act=True)
+    # 8-bit activations perturb the outputs at the 2^-9 level, not more
+    assert not np.array_equal(y0, y1)
+    assert np.abs(y1 - y0).max() <= 2e-2 * np.abs(y0).max()
+    # the rounded conv outputs do not depend on the fully connected layers, so
+    # the gradient there is the exact derivative: central differences agree
+    loss, g = oracle.cnn_loss_grad(w, x, t, bf16_act=True)
+    assert abs(loss - np.mean((y1 - t) ** 2)) < 1e-12 * loss
+    h = 1e-6
+    for i in list(rng.integers(129600, 195432, 12)) + [195424, 195431]:
+        wp = w.copy(); wp[i] += h
+        wm = w.copy(); wm[i] -= h
+        fd = (oracle.cnn_loss_grad(wp, x, t, True)[0] - oracle.cnn_loss_grad(wm, x, t, True)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * np.abs(g).max(), (i, fd, g[i])
