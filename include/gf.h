@@ -197,8 +197,17 @@ gf_status gf_eval_batch(const gf_desc* d, const gf_batch* b, const double* param
                         float* model_dev, double* chi2_dev, void* ws, size_t ws_bytes,
                         gf_stream stream);
 
-/* Workspace bytes for gf_eval_batch. */
+/* Workspace bytes for gf_eval_batch and gf_eval_batch_dev. */
 size_t gf_workspace_size_eval_batch(const gf_desc* d, const gf_batch* b);
+
+/* gf_eval_batch with the parameters already in device memory (params_dev,
+ * count x nslots float64, read on the stream).  With image_dev, sigma_dev and
+ * chi2_dev all NULL the call only renders: model_dev (required) receives the
+ * convolved models and no chi^2 is formed. */
+gf_status gf_eval_batch_dev(const gf_desc* d, const gf_batch* b, const double* params_dev,
+                            const float* image_dev, const float* sigma_dev, const float* psf_dev,
+                            float* model_dev, double* chi2_dev, void* ws, size_t ws_bytes,
+                            gf_stream stream);
 
 /* The input of step 4: Jacobian columns of the convolved model with respect to
  * the free slots, in slot order.  Amplitude and sky slots use the exact column
@@ -269,6 +278,111 @@ size_t gf_static_scratch_bytes(void);
 gf_status gf_eval_static(const gf_desc* d, const double* params_host, const float* image_dev,
                          const float* sigma_dev, const float* psf_dev, float* model_dev,
                          double* chi2_dev, gf_stream stream);
+
+/* ------------------------------------------------- learned initial guess
+ * No counterpart in the paper's text, which needs a starting point for step 4
+ * (Sec. 2 item 4) but does not say where it comes from, and names more robust
+ * fitting as the use of the speed-up (Sec. 5).  A convolutional network maps
+ * a 64x64 stamp to a start for a single Sersic + sky fit (9 slots: x0, y0, I_e,
+ * r_e, n, q, pa_deg, c, sky); a moments-based default guess is the fallback.
+ *
+ * Network: input x = asinh(img / a), a = median sigma over the stamp's outer
+ * ring; conv 3x3 stride 2 padding 1 1->32->64->64->128 (64 -> 4 pixels), fc
+ * 2048->32, fc 32->8, ReLU after all but the last layer.  Parameters: float32
+ * masters, GF_CNN_NPARAM of them, packed per layer as weights [out][in][ky][kx]
+ * (fc [out][in]) then biases.  Arithmetic: bf16 weights and activations, float32
+ * accumulation, fixed-order (deterministic) reductions.
+ * Outputs / targets (8, each scaled to about [-1, 1] over the training prior):
+ *   x0 - 31.5, y0 - 31.5, (ln F - 3.5 ln 10) / (1.5 ln 10),
+ *   (ln r_e - ln 80 / 2) / (ln 20 / 2), (n - 3.25) / 2.75, (q - 0.6) / 0.4,
+ *   cos 2 pa, sin 2 pa;   F = closed-form Sersic flux.
+ * All buffers are device memory owned by the caller; calls are stream-ordered
+ * and do not synchronise. */
+#define GF_CNN_SIDE 64
+#define GF_CNN_NOUT 8
+#define GF_CNN_NPARAM 195432
+
+size_t gf_cnn_nparams(void);
+/* Workspace bytes of gf_cnn_forward / gf_cnn_loss_grad for a batch. */
+size_t gf_cnn_workspace_size(int batch);
+
+/* He-normal weights N(0, 2 / fan_in) from Philox4x32-10 keyed by seed, zero
+ * biases, into w_dev (GF_CNN_NPARAM floats). */
+gf_status gf_cnn_init(float* w_dev, unsigned long long seed, gf_stream stream);
+
+/* Network input of `batch` 64x64 stamps: x_dev = asinh(img / a) per stamp. */
+gf_status gf_cnn_input(const float* image_dev, const float* sigma_dev, int batch, float* x_dev,
+                       gf_stream stream);
+
+/* y_dev (batch x 8) = network(x_dev (batch x 64 x 64, rounded to bf16)). */
+gf_status gf_cnn_forward(const float* w_dev, const float* x_dev, int batch, float* y_dev,
+                         void* ws, size_t ws_bytes, gf_stream stream);
+
+/* Mean squared error over batch x 8 against t_dev, into loss_dev (1 float),
+ * and its gradient with respect to every parameter, into grad_dev. */
+gf_status gf_cnn_loss_grad(const float* w_dev, const float* x_dev, const float* t_dev, int batch,
+                           float* loss_dev, float* grad_dev, void* ws, size_t ws_bytes,
+                           gf_stream stream);
+
+/* One Adam step (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8) on the
+ * masters w_dev with moments m_dev, v_dev (zero before step 1); step >= 1. */
+gf_status gf_cnn_adam(float* w_dev, float* m_dev, float* v_dev, const float* grad_dev, int step,
+                      float lr, gf_stream stream);
+
+/* Targets (count x 8 float) of the Sersic slots 0..6 of count parameter
+ * vectors of nslots float64 each (64x64 stamps). */
+gf_status gf_cnn_encode(const double* params_dev, int nslots, int count, float* t_dev,
+                        gf_stream stream);
+
+/* Inverse of gf_cnn_encode: count x 9 slots, c = 0, sky copied from slot 8 of
+ * dflt_dev (count x 9, e.g. gf_default_guess); I_e is NaN where n leaves
+ * [0.2, 10] or q leaves (0, 1].  flags: 0, or GF_DECODE_MOMENT_CENTRE to take
+ * x0, y0 from dflt_dev instead of the network. */
+#define GF_DECODE_MOMENT_CENTRE 1
+gf_status gf_cnn_decode(const float* y_dev, const double* dflt_dev, int count, int flags,
+                        double* params_dev, gf_stream stream);
+
+/* Training batch keyed by seed: count x 9 parameters drawn from the prior
+ * (centre 31.5 + U[-1, 1], n ~ U[0.5, 6], r_e log-uniform [2, 40],
+ * q ~ U[0.2, 1], pa ~ U[0, 180), flux log-uniform [1e2, 1e5], c = 0,
+ * sky 0.05) and count Moffat PSFs (beta 3, FWHM ~ U[2, 5], sum 1) of
+ * psf_size^2 floats.  Deterministic in (seed, stamp index). */
+gf_status gf_train_sample(unsigned long long seed, int count, int psf_size, double* params_dev,
+                          float* psf_dev, gf_stream stream);
+
+/* Noise on n model pixels: sigma = sqrt(sigma_read^2 + max(m, 0) / gain),
+ * image = m + sigma z, z standard normal by Box-Muller from Philox4x32-10
+ * (counter = pixel index, key = seed). */
+gf_status gf_noise(const float* model_dev, int64_t n, unsigned long long seed, float sigma_read,
+                   float gain, float* image_dev, float* sigma_dev, gf_stream stream);
+
+/* Philox4x32-10 (Salmon et al., SC 2011) of n blocks: in_dev holds per block
+ * the counter (4 words) then the key (2 words); out_dev 4 words per block.
+ * Exposed so the generator can be checked against its published vectors. */
+gf_status gf_philox4x32_10(const uint32_t* in_dev, uint32_t* out_dev, int n, gf_stream stream);
+
+/* Workspace bytes of gf_default_guess / gf_guess_select for count stamps. */
+size_t gf_workspace_size_guess(int count);
+
+/* Moments-based start of a single Sersic + sky fit for every stamp of a batch
+ * (any sizes; stamp ring at most 8192 pixels), params_dev count x 9:
+ *   sky = median of the outer ring of pixels;
+ *   x0, y0 = first moments of the sky-subtracted positive pixels;
+ *   q, pa = from their second moments;
+ *   r_e = semi-major axis of the smallest elliptical aperture (0.25 px steps)
+ *         holding half their summed flux;  n = 2;  c = 0;
+ *   I_e = summed flux / closed-form flux of unit I_e. */
+gf_status gf_default_guess(const gf_batch* b, const float* image_dev, double* params_dev,
+                           void* ws, size_t ws_bytes, gf_stream stream);
+
+/* Per stamp, out_dev = cand_dev where every slot is finite and inside the
+ * bounds (lo_host / hi_host, 9 each, NULL = the defaults of gf_lm_fit) and
+ * chi2_cand is finite and no larger than chi2_dflt; else dflt_dev.  choice_dev
+ * (may be NULL) receives 1 where the candidate was taken. */
+gf_status gf_guess_select(int count, const double* cand_dev, const double* chi2_cand_dev,
+                          const double* dflt_dev, const double* chi2_dflt_dev,
+                          const double* lo_host, const double* hi_host, double* out_dev,
+                          int* choice_dev, void* ws, size_t ws_bytes, gf_stream stream);
 
 /* ------------------------------------------------------------ diagnostics
  * Not part of the method; used to measure the library (no counterpart in the

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "cnn.cuh"
 #include "conv_dft.cuh"
 #include "conv_fft.cuh"
 #include "gf_internal.cuh"
@@ -890,8 +891,9 @@ gf_status trial_pass(const PassArgs& a, const Plan& pl, void* ws, cudaStream_t s
     if (r != GF_OK) return r;
     ProfScope ps(PROF_REDUCE, s);
     GF_CUDA(launch_reduce_chi2(a, s));
-    // the LM body folds the final reduction into k_final_update
-    if (!a.lm) GF_CUDA(launch_final_chi2(a, x2, s));
+    // the LM body folds the final reduction into k_final_update; a render
+    // (no image) has no chi^2
+    if (!a.lm && x2) GF_CUDA(launch_final_chi2(a, x2, s));
     return GF_OK;
 }
 
@@ -1139,9 +1141,10 @@ gf_status gf_eval(const gf_desc* d, const double* params, const float* img, cons
     return trial_pass(a, pl, ws, s, chi2);
 }
 
-gf_status gf_eval_batch(const gf_desc* d, const gf_batch* b, const double* params,
-                        const float* img, const float* sig, const float* psf, float* model_out,
-                        double* chi2, void* ws, size_t ws_bytes, gf_stream stream)
+static gf_status eval_batch_impl(const gf_desc* d, const gf_batch* b, const double* params,
+                                 bool params_on_device, const float* img, const float* sig,
+                                 const float* psf, float* model_out, double* chi2, void* ws,
+                                 size_t ws_bytes, gf_stream stream)
 {
     gf_status r = check_structure(d);
     if (r != GF_OK) return r;
@@ -1149,19 +1152,42 @@ gf_status gf_eval_batch(const gf_desc* d, const gf_batch* b, const double* param
     for (int i = 0; i < b->count; ++i)
         if ((r = check_stamp(d, b->H[i], b->W[i])) != GF_OK) return r;
     if ((r = check_fft(d, b->count, b->H, b->W)) != GF_OK) return r;
-    if (!params || !img || !sig || !psf || !chi2) return fail(GF_EINVAL, "NULL argument");
+    const bool render = params_on_device && !img && !sig && !chi2;
+    if (!params || !psf || (!render && (!img || !sig || !chi2)) || (render && !model_out))
+        return fail(GF_EINVAL, "NULL argument");
     Structure S;
     if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, &S)) != GF_OK) return r;
     Plan pl;
     plan_batch(d, S, b->count, b->H, b->W, b->pix_off, b->psf_off, NEED_TRIAL, &pl);
     if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
+    if ((r = upload(ws, make_blob(pl, S, params_on_device ? nullptr : params), s)) != GF_OK) return r;
+    if (params_on_device)
+        GF_CUDA(cudaMemcpyAsync(at<double>(ws, pl.L.params), params,
+                                sizeof(double) * (size_t)b->count * S.nslots,
+                                cudaMemcpyDeviceToDevice, s));
     PassArgs a = trial_args(ws, pl.L, base_args(ws, pl.L, psf, img, sig, d->psf_size));
     a.m_out = model_out;
     if ((r = setup_conv(ws, pl, psf, s)) != GF_OK) return r;
     GF_CUDA(launch_prep_sum(a, at<double>(ws, pl.L.params), 0, s));
     return trial_pass(a, pl, ws, s, chi2);
+}
+
+gf_status gf_eval_batch(const gf_desc* d, const gf_batch* b, const double* params,
+                        const float* img, const float* sig, const float* psf, float* model_out,
+                        double* chi2, void* ws, size_t ws_bytes, gf_stream stream)
+{
+    return eval_batch_impl(d, b, params, false, img, sig, psf, model_out, chi2, ws, ws_bytes,
+                           stream);
+}
+
+gf_status gf_eval_batch_dev(const gf_desc* d, const gf_batch* b, const double* params_dev,
+                            const float* img, const float* sig, const float* psf,
+                            float* model_out, double* chi2, void* ws, size_t ws_bytes,
+                            gf_stream stream)
+{
+    return eval_batch_impl(d, b, params_dev, true, img, sig, psf, model_out, chi2, ws, ws_bytes,
+                           stream);
 }
 
 gf_status gf_jacobian(const gf_desc* d, const double* params, const uint8_t* fixed, double fd_rel,
@@ -1421,3 +1447,232 @@ extern "C" gf_status gf_eval_static(const gf_desc* d, const double* params, cons
     GF_CUDA(launch_prep_sum(a, at<double>(ws, pl.L.params), 0, s));
     return trial_pass(a, pl, ws, s, chi2);
 }
+
+// ==================================================== learned initial guess
+
+namespace {
+
+// the start of a single-Sersic + sky fit: 9 slots
+constexpr int kGuessSlots = 9;
+
+gf_status check_cnn_batch(int batch)
+{
+    if (batch < 1 || batch > (1 << 20)) return fail(GF_EINVAL, "batch out of range [1, 2^20]");
+    return GF_OK;
+}
+
+// a guess call's tables in its workspace: H, W (int), offsets (int64), lo, hi
+struct GuessLayout {
+    size_t H, W, off, lo, hi, total;
+};
+
+GuessLayout guess_layout(int count)
+{
+    GuessLayout g;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += (bytes + 255) & ~(size_t)255;
+        return at;
+    };
+    g.H = take(sizeof(int) * (size_t)count);
+    g.W = take(sizeof(int) * (size_t)count);
+    g.off = take(sizeof(long long) * (size_t)count);
+    g.lo = take(sizeof(double) * kGuessSlots);
+    g.hi = take(sizeof(double) * kGuessSlots);
+    g.total = o;
+    return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gf_cnn_nparams(void) { return CNN_NPARAM; }
+
+size_t gf_cnn_workspace_size(int batch)
+{
+    if (batch < 1) return 0;
+    return cnn_buffers(nullptr, batch, nullptr);
+}
+
+gf_status gf_cnn_init(float* w, unsigned long long seed, gf_stream stream)
+{
+    if (!w) return fail(GF_EINVAL, "NULL argument");
+    GF_CUDA(cnn_init(w, seed, (cudaStream_t)stream));
+    return GF_OK;
+}
+
+gf_status gf_cnn_input(const float* img, const float* sig, int batch, float* x, gf_stream stream)
+{
+    gf_status r = check_cnn_batch(batch);
+    if (r != GF_OK) return r;
+    if (!img || !sig || !x) return fail(GF_EINVAL, "NULL argument");
+    GF_CUDA(cnn_input(img, sig, batch, x, (cudaStream_t)stream));
+    return GF_OK;
+}
+
+gf_status gf_cnn_forward(const float* w, const float* x, int batch, float* y, void* ws,
+                         size_t ws_bytes, gf_stream stream)
+{
+    gf_status r = check_cnn_batch(batch);
+    if (r != GF_OK) return r;
+    if (!w || !x || !y) return fail(GF_EINVAL, "NULL argument");
+    if ((r = check_ws(ws, ws_bytes, cnn_buffers(nullptr, batch, nullptr))) != GF_OK) return r;
+    CnnBuffers cb;
+    cnn_buffers(ws, batch, &cb);
+    cudaStream_t s = (cudaStream_t)stream;
+    GF_CUDA(cnn_prepare(w, x, batch, cb, s));
+    GF_CUDA(cnn_forward(w, batch, cb, y, s));
+    return GF_OK;
+}
+
+gf_status gf_cnn_loss_grad(const float* w, const float* x, const float* t, int batch, float* loss,
+                           float* grad, void* ws, size_t ws_bytes, gf_stream stream)
+{
+    gf_status r = check_cnn_batch(batch);
+    if (r != GF_OK) return r;
+    if (!w || !x || !t || !loss || !grad) return fail(GF_EINVAL, "NULL argument");
+    if ((r = check_ws(ws, ws_bytes, cnn_buffers(nullptr, batch, nullptr))) != GF_OK) return r;
+    CnnBuffers cb;
+    cnn_buffers(ws, batch, &cb);
+    cudaStream_t s = (cudaStream_t)stream;
+    GF_CUDA(cnn_prepare(w, x, batch, cb, s));
+    GF_CUDA(cnn_forward(w, batch, cb, nullptr, s));
+    GF_CUDA(cnn_backward(t, batch, loss, grad, cb, s));
+    return GF_OK;
+}
+
+gf_status gf_cnn_adam(float* w, float* m, float* v, const float* grad, int step, float lr,
+                      gf_stream stream)
+{
+    if (!w || !m || !v || !grad) return fail(GF_EINVAL, "NULL argument");
+    if (step < 1 || !(lr > 0.0f)) return fail(GF_EINVAL, "Adam step must be >= 1 and lr > 0");
+    GF_CUDA(cnn_adam(w, m, v, grad, step, lr, (cudaStream_t)stream));
+    return GF_OK;
+}
+
+gf_status gf_cnn_encode(const double* params, int nslots, int count, float* t, gf_stream stream)
+{
+    gf_status r = check_cnn_batch(count);
+    if (r != GF_OK) return r;
+    if (!params || !t) return fail(GF_EINVAL, "NULL argument");
+    if (nslots < 7) return fail(GF_EINVAL, "a Sersic component needs slots 0..6");
+    GF_CUDA(cnn_encode(params, nslots, count, CNN_SIDE, CNN_SIDE, t, (cudaStream_t)stream));
+    return GF_OK;
+}
+
+gf_status gf_cnn_decode(const float* y, const double* dflt, int count, int flags, double* params,
+                        gf_stream stream)
+{
+    gf_status r = check_cnn_batch(count);
+    if (r != GF_OK) return r;
+    if (!y || !dflt || !params) return fail(GF_EINVAL, "NULL argument");
+    if (flags & ~GF_DECODE_MOMENT_CENTRE) return fail(GF_EINVAL, "unknown decode flags");
+    GF_CUDA(cnn_decode(y, dflt, count, CNN_SIDE, CNN_SIDE, flags, params, (cudaStream_t)stream));
+    return GF_OK;
+}
+
+gf_status gf_train_sample(unsigned long long seed, int count, int psf_size, double* params,
+                          float* psf, gf_stream stream)
+{
+    gf_status r = check_cnn_batch(count);
+    if (r != GF_OK) return r;
+    if (!params || !psf) return fail(GF_EINVAL, "NULL argument");
+    if (psf_size < 1 || psf_size % 2 == 0 || psf_size > GF_MAX_PSF)
+        return fail(GF_EINVAL, "PSF side must be odd and <= GF_MAX_PSF");
+    GF_CUDA(train_sample(seed, count, params, psf, psf_size, (cudaStream_t)stream));
+    return GF_OK;
+}
+
+gf_status gf_noise(const float* model, int64_t n, unsigned long long seed, float sigma_read,
+                   float gain, float* img, float* sig, gf_stream stream)
+{
+    if (!model || !img || !sig) return fail(GF_EINVAL, "NULL argument");
+    if (n < 0 || !(gain > 0.0f) || !(sigma_read >= 0.0f))
+        return fail(GF_EINVAL, "need n >= 0, gain > 0, sigma_read >= 0");
+    if (n == 0) return GF_OK;
+    GF_CUDA(noise_fill(model, n, seed, sigma_read, gain, img, sig, (cudaStream_t)stream));
+    return GF_OK;
+}
+
+gf_status gf_philox4x32_10(const uint32_t* in, uint32_t* out, int n, gf_stream stream)
+{
+    if (!in || !out || n < 0) return fail(GF_EINVAL, "bad argument");
+    if (n == 0) return GF_OK;
+    GF_CUDA(philox_blocks(in, out, n, (cudaStream_t)stream));
+    return GF_OK;
+}
+
+size_t gf_workspace_size_guess(int count)
+{
+    if (count < 1) return 0;
+    return guess_layout(count).total;
+}
+
+gf_status gf_default_guess(const gf_batch* b, const float* img, double* params, void* ws,
+                           size_t ws_bytes, gf_stream stream)
+{
+    if (!b || b->count < 1 || !b->H || !b->W) return fail(GF_EINVAL, "bad batch");
+    if (!img || !params) return fail(GF_EINVAL, "NULL argument");
+    const int count = b->count;
+    std::vector<int> H(b->H, b->H + count), W(b->W, b->W + count);
+    std::vector<long long> off(count);
+    size_t smem = 0;
+    long long run = 0;
+    for (int i = 0; i < count; ++i) {
+        if (H[i] < 1 || W[i] < 1 || (long long)H[i] * W[i] > (1LL << 30))
+            return fail(GF_EINVAL, "stamp size out of range");
+        smem = std::max(smem, default_guess_smem(H[i], W[i]));
+        off[i] = b->pix_off ? (long long)b->pix_off[i] : run;
+        run += (long long)H[i] * W[i];
+    }
+    if (smem > 64 * 1024) return fail(GF_EINVAL, "default guess: stamp ring longer than 8192 pixels");
+    const GuessLayout g = guess_layout(count);
+    gf_status r = check_ws(ws, ws_bytes, g.total);
+    if (r != GF_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<uint8_t> blob(g.lo, 0);
+    memcpy(blob.data() + g.H, H.data(), sizeof(int) * count);
+    memcpy(blob.data() + g.W, W.data(), sizeof(int) * count);
+    memcpy(blob.data() + g.off, off.data(), sizeof(long long) * count);
+    if ((r = upload(ws, blob, s)) != GF_OK) return r;
+    GF_CUDA(default_guess(count, at<int>(ws, g.H), at<int>(ws, g.W), at<long long>(ws, g.off), img,
+                          params, kGuessSlots, smem, s));
+    return GF_OK;
+}
+
+gf_status gf_guess_select(int count, const double* cand, const double* chi2_cand,
+                          const double* dflt, const double* chi2_dflt, const double* lo,
+                          const double* hi, double* out, int* choice, void* ws, size_t ws_bytes,
+                          gf_stream stream)
+{
+    gf_status r = check_cnn_batch(count);
+    if (r != GF_OK) return r;
+    if (!cand || !chi2_cand || !dflt || !chi2_dflt || !out) return fail(GF_EINVAL, "NULL argument");
+    const GuessLayout g = guess_layout(1);
+    if ((r = check_ws(ws, ws_bytes, g.total)) != GF_OK) return r;
+    std::vector<uint8_t> blob(g.total, 0);
+    double* blo = reinterpret_cast<double*>(blob.data() + g.lo);
+    double* bhi = reinterpret_cast<double*>(blob.data() + g.hi);
+    gf_desc d;
+    memset(&d, 0, sizeof(d));
+    d.H = d.W = CNN_SIDE;
+    d.psf_size = 1;
+    d.ncomp = 2;
+    d.kinds[0] = GF_SERSIC;
+    d.kinds[1] = GF_SKY;
+    Structure S;
+    if ((r = make_structure(&d, nullptr, lo, hi, nullptr, &S)) != GF_OK) return r;
+    for (int k = 0; k < kGuessSlots; ++k) {
+        blo[k] = S.lo[k];
+        bhi[k] = S.hi[k];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = upload(ws, blob, s)) != GF_OK) return r;
+    GF_CUDA(guess_select(count, kGuessSlots, cand, chi2_cand, dflt, chi2_dflt, at<double>(ws, g.lo),
+                         at<double>(ws, g.hi), out, choice, s));
+    return GF_OK;
+}
+
+}  // extern "C"

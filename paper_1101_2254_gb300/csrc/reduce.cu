@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_chi2(PassArgs a)
         float m = msky;
         for (int k = 0; k < a.nchan; ++k) m = fmaf(ci.mw[k], Y[(long long)k * HW + px], m);
         if (a.m_out) a.m_out[st.pix_off + px] = m;
+        if (!a.img) continue;  // model only
         const float d = img[px], s = sig[px];
         if (isfinite(d) && isfinite(s) && s > 0.0f) {
             const float z = (d - m) / s;

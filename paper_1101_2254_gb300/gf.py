@@ -103,6 +103,39 @@ def lib():
             L.gf_static_scratch_bytes.restype = C.c_size_t
             L.gf_eval_static.restype = C.c_int
             L.gf_eval_static.argtypes = [pd, dp, fp, fp, fp, fp, vp, vp]
+            L.gf_eval_batch_dev.restype = C.c_int
+            L.gf_eval_batch_dev.argtypes = [pd, C.POINTER(Batch), vp, fp, fp, fp, fp, vp, vp,
+                                            C.c_size_t, vp]
+            L.gf_cnn_nparams.restype = C.c_size_t
+            L.gf_cnn_workspace_size.restype = C.c_size_t
+            L.gf_cnn_workspace_size.argtypes = [C.c_int]
+            L.gf_cnn_init.restype = C.c_int
+            L.gf_cnn_init.argtypes = [vp, C.c_ulonglong, vp]
+            L.gf_cnn_input.restype = C.c_int
+            L.gf_cnn_input.argtypes = [vp, vp, C.c_int, vp, vp]
+            L.gf_cnn_forward.restype = C.c_int
+            L.gf_cnn_forward.argtypes = [vp, vp, C.c_int, vp, vp, C.c_size_t, vp]
+            L.gf_cnn_loss_grad.restype = C.c_int
+            L.gf_cnn_loss_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, C.c_size_t, vp]
+            L.gf_cnn_adam.restype = C.c_int
+            L.gf_cnn_adam.argtypes = [vp, vp, vp, vp, C.c_int, C.c_float, vp]
+            L.gf_cnn_encode.restype = C.c_int
+            L.gf_cnn_encode.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+            L.gf_cnn_decode.restype = C.c_int
+            L.gf_cnn_decode.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp]
+            L.gf_train_sample.restype = C.c_int
+            L.gf_train_sample.argtypes = [C.c_ulonglong, C.c_int, C.c_int, vp, vp, vp]
+            L.gf_noise.restype = C.c_int
+            L.gf_noise.argtypes = [vp, C.c_int64, C.c_ulonglong, C.c_float, C.c_float, vp, vp, vp]
+            L.gf_philox4x32_10.restype = C.c_int
+            L.gf_philox4x32_10.argtypes = [vp, vp, C.c_int, vp]
+            L.gf_workspace_size_guess.restype = C.c_size_t
+            L.gf_workspace_size_guess.argtypes = [C.c_int]
+            L.gf_default_guess.restype = C.c_int
+            L.gf_default_guess.argtypes = [C.POINTER(Batch), vp, vp, vp, C.c_size_t, vp]
+            L.gf_guess_select.restype = C.c_int
+            L.gf_guess_select.argtypes = [C.c_int, vp, vp, vp, vp, dp, dp, vp, vp, vp,
+                                          C.c_size_t, vp]
             L.gf_launch_count.restype = C.c_longlong
             L.gf_prof_enable.argtypes = [vp]
             L.gf_prof_times.restype = C.c_int
@@ -349,6 +382,154 @@ def lm_fit_batch(d: Desc, batch: Batch, params, fixed, img, sig, psf,
                                  _ptr(psf), C.byref(opts) if opts is not None else None, res,
                                  w, n, _stream(stream)))
     return p, [_res(r) for r in res]
+
+
+def evaluate_batch_dev(d: Desc, batch: Batch, params_dev, img, sig, psf, want_model=False,
+                       ws=None, stream=None):
+    """evaluate_batch with the parameters in a device float64 tensor (count x nslots).
+    img = sig = None renders only: returns (None, packed convolved models)."""
+    import torch
+    assert params_dev.dtype == torch.float64 and params_dev.is_cuda
+    p = params_dev.contiguous()
+    render = img is None and sig is None
+    x2 = None if render else torch.empty(batch.count, dtype=torch.float64, device=p.device)
+    m = None
+    if render or want_model:
+        npix = int(sum(int(h) * int(w) for h, w in zip(batch._keep[0], batch._keep[1])))
+        m = torch.empty(npix if img is None else img.numel(), dtype=torch.float32, device=p.device)
+    w, n = _ws(ws).get(lib().gf_workspace_size_eval_batch(C.byref(d), C.byref(batch)))
+    _check(lib().gf_eval_batch_dev(C.byref(d), C.byref(batch), _ptr(p), _ptr(img), _ptr(sig),
+                                   _ptr(psf), _ptr(m), _ptr(x2), w, n, _stream(stream)))
+    return x2, m
+
+
+# ------------------------------------------------------ learned initial guess
+CNN_SIDE, CNN_NOUT = 64, 8
+GUESS_SLOTS = 9  # Sersic (8) + sky
+
+
+def cnn_nparams() -> int:
+    return int(lib().gf_cnn_nparams())
+
+
+def cnn_init(seed: int, stream=None):
+    """He-normal initial network parameters (float32 device tensor)."""
+    import torch
+    w = torch.empty(cnn_nparams(), dtype=torch.float32, device="cuda")
+    _check(lib().gf_cnn_init(_ptr(w), seed, _stream(stream)))
+    return w
+
+
+def cnn_input(img, sig, stream=None):
+    """asinh(img / a) per 64x64 stamp (a = median ring sigma): float32 [B, 64, 64]."""
+    import torch
+    B = img.numel() // (CNN_SIDE * CNN_SIDE)
+    x = torch.empty(B, CNN_SIDE, CNN_SIDE, dtype=torch.float32, device=img.device)
+    _check(lib().gf_cnn_input(_ptr(img), _ptr(sig), B, _ptr(x), _stream(stream)))
+    return x
+
+
+def cnn_forward(w, x, ws=None, stream=None):
+    """Network outputs [B, 8] (float32) for scaled inputs x [B, 64, 64]."""
+    import torch
+    B = x.numel() // (CNN_SIDE * CNN_SIDE)
+    y = torch.empty(B, CNN_NOUT, dtype=torch.float32, device=x.device)
+    wk, n = _ws(ws).get(lib().gf_cnn_workspace_size(B))
+    _check(lib().gf_cnn_forward(_ptr(w), _ptr(x), B, _ptr(y), wk, n, _stream(stream)))
+    return y
+
+
+def cnn_loss_grad(w, x, t, ws=None, grad=None, loss=None, stream=None):
+    """(loss [1], grad [nparams]) device tensors of the mean squared error."""
+    import torch
+    B = x.numel() // (CNN_SIDE * CNN_SIDE)
+    if grad is None:
+        grad = torch.empty_like(w)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    wk, n = _ws(ws).get(lib().gf_cnn_workspace_size(B))
+    _check(lib().gf_cnn_loss_grad(_ptr(w), _ptr(x), _ptr(t), B, _ptr(loss), _ptr(grad), wk, n,
+                                  _stream(stream)))
+    return loss, grad
+
+
+def cnn_adam(w, m, v, grad, step: int, lr: float, stream=None):
+    _check(lib().gf_cnn_adam(_ptr(w), _ptr(m), _ptr(v), _ptr(grad), step, lr, _stream(stream)))
+
+
+def cnn_encode(params_dev, stream=None):
+    """Targets [count, 8] of device parameters [count, nslots] (64x64 stamps)."""
+    import torch
+    p = params_dev.contiguous()
+    t = torch.empty(p.shape[0], CNN_NOUT, dtype=torch.float32, device=p.device)
+    _check(lib().gf_cnn_encode(_ptr(p), p.shape[1], p.shape[0], _ptr(t), _stream(stream)))
+    return t
+
+
+DECODE_MOMENT_CENTRE = 1
+
+
+def cnn_decode(y, dflt, moment_centre=False, stream=None):
+    """Parameters [count, 9] from network outputs; sky (and with moment_centre
+    the centre) from the default starts dflt [count, 9]."""
+    import torch
+    out = torch.empty(y.shape[0], GUESS_SLOTS, dtype=torch.float64, device=y.device)
+    flags = DECODE_MOMENT_CENTRE if moment_centre else 0
+    _check(lib().gf_cnn_decode(_ptr(y.contiguous()), _ptr(dflt.contiguous()), y.shape[0], flags,
+                               _ptr(out), _stream(stream)))
+    return out
+
+
+def train_sample(seed: int, count: int, psf_size: int = 33, stream=None):
+    """(params [count, 9] float64, psfs [count, P, P] float32) of a training batch."""
+    import torch
+    p = torch.empty(count, GUESS_SLOTS, dtype=torch.float64, device="cuda")
+    psf = torch.empty(count, psf_size, psf_size, dtype=torch.float32, device="cuda")
+    _check(lib().gf_train_sample(seed, count, psf_size, _ptr(p), _ptr(psf), _stream(stream)))
+    return p, psf
+
+
+def noise(model_t, seed: int, sigma_read: float = 0.01, gain: float = 1.0, stream=None):
+    """(image, sigma) = model + sigma * N(0, 1), sigma^2 = sigma_read^2 + max(m, 0) / gain."""
+    import torch
+    img = torch.empty_like(model_t)
+    sig = torch.empty_like(model_t)
+    _check(lib().gf_noise(_ptr(model_t), model_t.numel(), seed, sigma_read, gain, _ptr(img),
+                          _ptr(sig), _stream(stream)))
+    return img, sig
+
+
+def philox4x32_10(blocks_in, stream=None):
+    """Philox4x32-10 of int64 tensor [n, 6] (counter 4 words, key 2 words) -> [n, 4]."""
+    import torch
+    a = torch.as_tensor(np.asarray(blocks_in, np.uint32).view(np.int32)).cuda()
+    out = torch.empty(a.shape[0], 4, dtype=torch.int32, device="cuda")
+    _check(lib().gf_philox4x32_10(_ptr(a), _ptr(out), a.shape[0], _stream(stream)))
+    return out.cpu().numpy().view(np.uint32)
+
+
+def default_guess(batch: Batch, img, ws=None, stream=None):
+    """Moments-based single-Sersic + sky starts [count, 9] (float64 device tensor)."""
+    import torch
+    out = torch.empty(batch.count, GUESS_SLOTS, dtype=torch.float64, device=img.device)
+    wk, n = _ws(ws).get(lib().gf_workspace_size_guess(batch.count))
+    _check(lib().gf_default_guess(C.byref(batch), _ptr(img), _ptr(out), wk, n, _stream(stream)))
+    return out
+
+
+def guess_select(cand, x2_cand, dflt, x2_dflt, lo=None, hi=None, ws=None, stream=None):
+    """(starts [count, 9], choice [count] int32: 1 where the candidate was kept)."""
+    import torch
+    count = cand.shape[0]
+    out = torch.empty_like(dflt)
+    choice = torch.empty(count, dtype=torch.int32, device=cand.device)
+    wk, n = _ws(ws).get(lib().gf_workspace_size_guess(count))
+    lo_a = _f64(lo) if lo is not None else None
+    hi_a = _f64(hi) if hi is not None else None
+    _check(lib().gf_guess_select(count, _ptr(cand.contiguous()), _ptr(x2_cand),
+                                 _ptr(dflt.contiguous()), _ptr(x2_dflt), _dp(lo_a), _dp(hi_a),
+                                 _ptr(out), _ptr(choice), wk, n, _stream(stream)))
+    return out, choice
 
 
 PROF_CLASSES = ("model", "conv", "reduce", "lm")

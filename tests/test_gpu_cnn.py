@@ -1,0 +1,364 @@
+"""GPU parity of the learned initial guess: the network's forward pass and
+gradient against the FP64 oracle, input scaling, target encoding, the default
+guess, the start selection, the counter-based generator against its published
+vectors, the on-device training sampler, and the gain of the learned start."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1101_2254_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gf():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1101_2254_gb300 import build, gf as gf_
+    build.build()
+    return gf_
+
+
+def bf16_round(a):
+    return torch.as_tensor(np.asarray(a, np.float32)).bfloat16().float().numpy().astype(np.float64)
+
+
+# layer blocks of the packed parameter vector: (name, start, end)
+BLOCKS = [("conv1.w", 0, 288), ("conv1.b", 288, 320), ("conv2.w", 320, 18752),
+          ("conv2.b", 18752, 18816), ("conv3.w", 18816, 55680), ("conv3.b", 55680, 55744),
+          ("conv4.w", 55744, 129472), ("conv4.b", 129472, 129600), ("fc1.w", 129600, 195136),
+          ("fc1.b", 195136, 195168), ("fc2.w", 195168, 195424), ("fc2.b", 195424, 195432)]
+
+
+def network_case(gf, nb=6, seed=3):
+    """bf16-exact weights (He init on the GPU, random biases) and bf16-exact inputs."""
+    w = gf.cnn_init(seed).cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(seed)
+    for name, a, b in BLOCKS:
+        if name.endswith(".b"):
+            w[a:b] = rng.uniform(-0.1, 0.1, b - a)
+    w = bf16_round(w)
+    x = bf16_round(rng.standard_normal((nb, 64, 64)))
+    t = rng.standard_normal((nb, 8))
+    return w, x, t
+
+
+def test_parameter_count_matches_oracle(gf):
+    assert gf.cnn_nparams() == oracle.cnn_nparams() == 195432
+
+
+def test_forward_matches_oracle(gf):
+    w, x, _ = network_case(gf)
+    y = gf.cnn_forward(torch.as_tensor(w, dtype=torch.float32).cuda(),
+                       torch.as_tensor(x, dtype=torch.float32).cuda()).cpu().numpy()
+    # the specified arithmetic (bf16 conv outputs): float32 accumulation order only
+    yq = oracle.cnn_forward(w, x, bf16_act=True)
+    scale = np.sqrt(np.mean(yq ** 2))
+    assert np.abs(y - yq).max() <= 1e-3 * scale, (np.abs(y - yq).max(), scale)
+    # against exact arithmetic: the bf16 activations' 2^-9 steps through four layers
+    yo = oracle.cnn_forward(w, x)
+    assert np.abs(y - yo).max() <= 3e-2 * scale
+
+
+@pytest.mark.parametrize("nb,seed", [(6, 5), (40, 6)])
+def test_gradient_matches_oracle(gf, nb, seed):
+    w, x, t = network_case(gf, nb=nb, seed=seed)
+    loss, g = gf.cnn_loss_grad(torch.as_tensor(w, dtype=torch.float32).cuda(),
+                               torch.as_tensor(x, dtype=torch.float32).cuda(),
+                               torch.as_tensor(t, dtype=torch.float32).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    lq, gq = oracle.cnn_loss_grad(w, x, t, bf16_act=True)
+    lo, go = oracle.cnn_loss_grad(w, x, t)
+    assert abs(float(loss.item()) - lq) <= 1e-4 * lq
+    for name, a, b in BLOCKS:
+        den = np.linalg.norm(gq[a:b])
+        # same arithmetic as the bf16-activation oracle up to float32 sums
+        assert np.linalg.norm(g[a:b] - gq[a:b]) <= 1e-3 * den, name
+        # exact arithmetic: rounding the activations moves gradients by several
+        # per cent at a random initialisation (cancelling sums over positions)
+        assert np.linalg.norm(g[a:b] - go[a:b]) <= 1.5e-1 * np.linalg.norm(go[a:b]), name
+
+
+def test_gradient_is_deterministic(gf):
+    w, x, t = network_case(gf, nb=32, seed=7)
+    args = [torch.as_tensor(a, dtype=torch.float32).cuda() for a in (w, x, t)]
+    g1 = gf.cnn_loss_grad(*args)[1].clone()
+    g2 = gf.cnn_loss_grad(*args)[1]
+    assert torch.equal(g1, g2)
+
+
+def test_adam_first_step_is_sign_step(gf):
+    # with zero moments, bias-corrected Adam moves every weight by lr * g / (|g| + eps)
+    w, x, t = network_case(gf, nb=4, seed=9)
+    wd = torch.as_tensor(w, dtype=torch.float32).cuda()
+    _, g = gf.cnn_loss_grad(wd, torch.as_tensor(x, dtype=torch.float32).cuda(),
+                            torch.as_tensor(t, dtype=torch.float32).cuda())
+    w0 = wd.clone()
+    m = torch.zeros_like(wd)
+    v = torch.zeros_like(wd)
+    lr = 1e-3
+    gf.cnn_adam(wd, m, v, g, 1, lr)
+    gn = g.cpu().numpy().astype(np.float64)
+    step = (wd - w0).cpu().numpy().astype(np.float64)
+    want = -lr * gn / (np.abs(gn) + 1e-8)
+    big = np.abs(gn) > 1e-4
+    assert big.sum() > 1000
+    assert np.abs(step - want)[big].max() <= 1e-6 * lr + 6e-8 * np.abs(w)[big].max()
+
+
+def test_input_scaling_matches_oracle(gf):
+    rng = np.random.default_rng(11)
+    img = rng.standard_normal((5, 64, 64)).astype(np.float32) * 3
+    sig = rng.uniform(0.005, 0.5, (5, 64, 64)).astype(np.float32)
+    x = gf.cnn_input(torch.as_tensor(img).cuda(), torch.as_tensor(sig).cuda()).cpu().numpy()
+    for b in range(5):
+        xo = oracle.cnn_input(img[b], sig[b])
+        assert np.abs(x[b] - xo).max() <= 4e-7 * np.abs(xo).max() + 1e-7
+
+
+def prior_params(n, seed):
+    rng = np.random.default_rng(seed)
+    p = np.zeros((n, 9))
+    for i in range(n):
+        re = math.exp(rng.uniform(math.log(2), math.log(40)))
+        nn = rng.uniform(0.5, 6)
+        q = rng.uniform(0.2, 1)
+        F = math.exp(rng.uniform(math.log(1e2), math.log(1e5)))
+        p[i] = [31.5 + rng.uniform(-1, 1), 31.5 + rng.uniform(-1, 1),
+                F / oracle.sersic_flux(1.0, re, nn, q), re, nn, q, rng.uniform(0, 180), 0.0, 0.05]
+    return p
+
+
+def test_encode_decode_match_oracle(gf):
+    p = prior_params(64, 13)
+    t = gf.cnn_encode(torch.as_tensor(p).cuda()).cpu().numpy()
+    to = np.array([oracle.cnn_encode(pi, 64, 64) for pi in p])
+    assert np.abs(t - to).max() <= 1e-6
+    # decode the float targets on both sides (sky from a default-guess array)
+    dflt = np.zeros((64, 9))
+    dflt[:, 8] = np.linspace(0.0, 1.0, 64)
+    pd = gf.cnn_decode(torch.as_tensor(t).cuda(), torch.as_tensor(dflt).cuda()).cpu().numpy()
+    for i in range(64):
+        po = oracle.cnn_decode(t[i].astype(np.float64), 64, 64)
+        assert np.allclose(pd[i, :8], po, rtol=1e-12, atol=1e-12), (i, pd[i], po)
+        assert pd[i, 8] == dflt[i, 8]
+    # out of the flux domain: NaN amplitude on both sides
+    y = np.zeros((2, 8), np.float32)
+    y[0, 4] = 4.0  # n = 14.25
+    y[1, 5] = 2.0  # q = 1.4
+    pd = gf.cnn_decode(torch.as_tensor(y).cuda(), torch.zeros(2, 9, dtype=torch.float64).cuda())
+    assert torch.isnan(pd[:, 2]).all()
+
+
+def guess_stamps():
+    """Stamps of assorted sizes rendered by the oracle, with seeded noise."""
+    out = []
+    rng = np.random.default_rng(17)
+    for k, (H, W) in enumerate([(64, 64), (48, 80), (97, 61), (33, 33), (128, 96), (2, 9)]):
+        if H < 8:
+            img = rng.uniform(0, 1, (H, W))
+        else:
+            re = rng.uniform(2, 0.2 * min(H, W))
+            p = [W / 2 + rng.uniform(-2, 2), H / 2 + rng.uniform(-2, 2), rng.uniform(0.5, 5), re,
+                 rng.uniform(0.7, 4), rng.uniform(0.3, 1), rng.uniform(0, 180), 0.0, 0.05]
+            d = oracle.make_desc(H, W, 9, [oracle.SERSIC, oracle.SKY])
+            m = oracle.render(d, p, synth.moffat_psf(9, 3.0))
+            img, _ = synth.add_noise(m, 100 + k)
+        out.append(np.asarray(img, np.float32))
+    out.append(np.zeros((40, 40), np.float32))  # flat: no positive pixels
+    return out
+
+
+def enclosed(img, g, a):
+    sky, x0, y0, q, pa = g[8], g[0], g[1], g[5], g[6]
+    th = pa * math.pi / 180
+    yy, xx = np.mgrid[0:img.shape[0], 0:img.shape[1]].astype(np.float64)
+    dx, dy = xx - x0, yy - y0
+    xp = dx * math.cos(th) + dy * math.sin(th)
+    yp = (-dx * math.sin(th) + dy * math.cos(th)) / q
+    v = img.astype(np.float64) - sky
+    return v[(v > 0) & (xp * xp + yp * yp <= a * a)].sum(), v[v > 0].sum()
+
+
+def test_default_guess_matches_oracle(gf):
+    imgs = guess_stamps()
+    Hs = [im.shape[0] for im in imgs]
+    Ws = [im.shape[1] for im in imgs]
+    flat = torch.as_tensor(np.concatenate([im.ravel() for im in imgs])).cuda()
+    b = gf.make_batch(Hs, Ws, psf_size=1)
+    g = gf.default_guess(b, flat).cpu().numpy()
+    for i, im in enumerate(imgs):
+        go = oracle.default_guess(im.astype(np.float64))
+        assert g[i, 8] == go[8], i  # the median of the same float values
+        assert np.allclose(g[i, [0, 1, 5]], go[[0, 1, 5]], rtol=1e-10, atol=1e-10), (i, g[i], go)
+        dpa = (g[i, 6] - go[6] + 90.0) % 180.0 - 90.0
+        assert abs(dpa) < 1e-7, (i, g[i, 6], go[6])
+        assert g[i, 4] == 2.0 and g[i, 7] == 0.0
+        if g[i, 3] != go[3]:
+            # a tie: both radii must be valid ends of the curve of growth
+            assert abs(g[i, 3] - go[3]) == 0.25, (i, g[i, 3], go[3])
+            a = max(g[i, 3], go[3])
+            e_in, tot = enclosed(im, go, a - 0.25)
+            assert abs(e_in - 0.5 * tot) <= 1e-9 * tot, (i, e_in, tot)
+        else:
+            assert abs(g[i, 2] / go[2] - 1.0) <= 1e-10, (i, g[i, 2], go[2])
+
+
+def test_guess_select_rules(gf):
+    n = 6
+    dflt = np.tile(np.array([32.0, 32.0, 1.0, 4.0, 2.0, 0.8, 10.0, 0.0, 0.05]), (n, 1))
+    cand = dflt.copy()
+    cand[:, 3] = 5.0
+    x2c = np.array([1.0, 1.0, 1.0, 3.0, np.nan, 1.0])
+    x2d = np.full(n, 2.0)
+    cand[1, 2] = np.nan  # non-finite slot
+    cand[2, 5] = 1.5     # q out of bounds
+    x2d[5] = np.inf      # default unusable: a finite candidate wins
+    T = lambda a: torch.as_tensor(a).cuda()
+    out, ch = gf.guess_select(T(cand), T(x2c), T(dflt), T(x2d))
+    out, ch = out.cpu().numpy(), ch.cpu().numpy()
+    assert ch.tolist() == [1, 0, 0, 0, 0, 1]
+    for i in range(n):
+        assert np.array_equal(out[i], cand[i] if ch[i] else dflt[i])
+
+
+# Published known-answer vectors of Philox4x32-10 (Salmon et al., SC 2011,
+# distributed with their Random123 library): counter (4 words), key (2), result.
+PHILOX_KAT = [
+    ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+    ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+]
+
+
+def test_philox_known_answers(gf):
+    blocks = np.array([list(c) + list(k) for c, k, _ in PHILOX_KAT], np.uint32)
+    out = gf.philox4x32_10(blocks)
+    for i, (_, _, want) in enumerate(PHILOX_KAT):
+        assert tuple(int(v) for v in out[i]) == want, [hex(int(v)) for v in out[i]]
+
+
+def test_noise_model(gf):
+    m = torch.full((1 << 20,), 4.0, dtype=torch.float32).cuda()
+    m[: 1 << 19] = 0.0
+    img, sig = gf.noise(m, 123, 0.01, 1.0)
+    s_want = np.where(np.arange(1 << 20) < (1 << 19), 0.01, math.sqrt(1e-4 + 4.0))
+    assert np.allclose(sig.cpu().numpy(), s_want, rtol=1e-6)
+    z = ((img - m) / sig).cpu().numpy().astype(np.float64)
+    n = z.size
+    assert abs(z.mean()) < 5.0 / math.sqrt(n)
+    assert abs(z.var() - 1.0) < 5.0 * math.sqrt(2.0 / n)
+    # deterministic in the seed, different across seeds
+    img2, _ = gf.noise(m, 123, 0.01, 1.0)
+    img3, _ = gf.noise(m, 124, 0.01, 1.0)
+    assert torch.equal(img, img2) and not torch.equal(img, img3)
+
+
+def test_train_sample_prior_and_psf(gf):
+    count = 4096
+    p, psf = gf.train_sample(77, count, 33)
+    p = p.cpu().numpy()
+    psf = psf.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(p[:, 0:2] - 31.5) <= 1.0)
+    assert np.all((p[:, 4] >= 0.5) & (p[:, 4] <= 6.0))
+    assert np.all((p[:, 3] >= 2.0) & (p[:, 3] <= 40.0))
+    assert np.all((p[:, 5] >= 0.2) & (p[:, 5] <= 1.0))
+    assert np.all((p[:, 6] >= 0.0) & (p[:, 6] < 180.0))
+    assert np.all(p[:, 7] == 0.0) and np.all(p[:, 8] == 0.05)
+    # uniform and log-uniform draws: means within 5 standard errors
+    se = 5.0 / math.sqrt(count)
+    assert abs(p[:, 4].mean() - 3.25) < 5.5 / math.sqrt(12) * se
+    lr = (np.log(p[:, 3]) - math.log(2)) / (math.log(40) - math.log(2))
+    assert abs(lr.mean() - 0.5) < 5.0 / math.sqrt(12 * count)
+    F = np.array([oracle.sersic_flux(*p[i, [2, 3, 4, 5]]) for i in range(256)])
+    assert np.all((F >= 1e2 * (1 - 1e-9)) & (F <= 1e5 * (1 + 1e-9)))
+    # each PSF is a Moffat(beta = 3) of FWHM in [2, 5]: recover alpha from the
+    # centre-to-neighbour ratio, then compare with the host builder
+    for i in range(0, count, 512):
+        k = psf[i]
+        ratio = k[16, 17] / k[16, 16]
+        alpha = 1.0 / math.sqrt(ratio ** (-1.0 / 3.0) - 1.0)
+        fwhm = 2.0 * alpha * math.sqrt(2.0 ** (1.0 / 3.0) - 1.0)
+        assert 2.0 - 1e-3 <= fwhm <= 5.0 + 1e-3
+        ref = synth.moffat_psf(33, fwhm, 3.0).astype(np.float64)
+        assert np.abs(k - ref).max() <= 1e-5 * ref.max()
+        assert abs(k.sum() - 1.0) < 1e-5
+
+
+def test_eval_batch_dev_matches_host_params(gf):
+    from paper_1101_2254_gb300 import learned
+    count = 8
+    p, psf = gf.train_sample(5, count, 33)
+    d = learned.stamp_desc()
+    b = learned.uniform_batch(count)
+    _, m = gf.evaluate_batch_dev(d, b, p, None, None, psf.reshape(-1))
+    img, sig = gf.noise(m, 9)
+    x2h, mh = gf.evaluate_batch(d, b, p.cpu().numpy(), img, sig, psf.reshape(-1), want_model=True)
+    x2d, md = gf.evaluate_batch_dev(d, b, p, img, sig, psf.reshape(-1), want_model=True)
+    assert torch.equal(x2h, x2d) and torch.equal(mh, md) and torch.equal(m, md)
+
+
+def test_learned_start_gain(gf):
+    """Train on the fly (768k stamps), then fit held-out stamps rendered by the
+    oracle from the default start and from the selected start: the learned
+    start must need fewer LM iterations, converge at least as often, and reach
+    the oracle's chi^2 at least as often."""
+    from paper_1101_2254_gb300 import learned
+    tr = learned.Trainer(seed=40, batch=512, lr=2e-4).train(1500)
+    first = np.mean(tr.losses[:20])
+    last = np.mean(tr.losses[-20:])
+    assert last < 0.25 * first, (first, last)
+    # held-out stamps from the same prior, rendered and noised on the host
+    count = 128
+    p = prior_params(count, 7)
+    rng = np.random.default_rng(8)
+    fwhm = rng.uniform(2, 5, count)
+    psfs = np.stack([synth.moffat_psf(33, f, 3.0) for f in fwhm])
+    od = oracle.make_desc(64, 64, 33, [oracle.SERSIC, oracle.SKY], 5, 8)
+    imgs, sigs = [], []
+    for i in range(count):
+        m = oracle.render(od, p[i], psfs[i], method=1)
+        im, sg = synth.add_noise(m, 1000 + i)
+        imgs.append(im)
+        sigs.append(sg)
+    img = torch.as_tensor(np.stack(imgs)).cuda().reshape(-1)
+    sig = torch.as_tensor(np.stack(sigs)).cuda().reshape(-1)
+    psf = torch.as_tensor(psfs).cuda().reshape(-1)
+    b = learned.uniform_batch(count)
+    d = learned.stamp_desc()
+    st, choice, dflt = learned.starts(tr.w, b, img, sig, psf)
+    fixed = np.zeros(9, np.uint8)
+    fixed[7] = 1
+    opts = gf.default_opts(ftol=1e-6, xtol=1e-6)
+    pl, rl = gf.lm_fit_batch(d, b, st.cpu().numpy(), fixed, img, sig, psf, opts=opts)
+    pdf, rdf = gf.lm_fit_batch(d, b, dflt.cpu().numpy(), fixed, img, sig, psf, opts=opts)
+    it_l = np.array([r["iters"] for r in rl])
+    it_d = np.array([r["iters"] for r in rdf])
+    ok_l = sum(r["status"] == 0 for r in rl)
+    ok_d = sum(r["status"] == 0 for r in rdf)
+    assert choice.sum().item() > count // 4
+    assert np.median(it_l) < np.median(it_d), (np.median(it_l), np.median(it_d))
+    assert ok_l >= ok_d, (ok_l, ok_d)
+    # fits reaching the oracle chi^2 (oracle fits from the true parameters)
+    sub = list(range(0, count, 4))
+    _, ro = oracle.lm_fit_batch([od] * len(sub), p[sub], fixed, psfs[sub].ravel(),
+                                np.arange(len(sub)) * 33 * 33,
+                                np.stack([imgs[i] for i in sub]).ravel(),
+                                np.stack([sigs[i] for i in sub]).ravel(),
+                                np.arange(len(sub)) * 64 * 64, method=1)
+    reach_l = reach_d = 0
+    for k, i in enumerate(sub):
+        x2o = ro[k]["chi2"]
+        x2l = oracle.evaluate(od, pl[i], psfs[i], imgs[i], sigs[i], method=1)[0]
+        x2d = oracle.evaluate(od, pdf[i], psfs[i], imgs[i], sigs[i], method=1)[0]
+        reach_l += x2l <= x2o * (1 + 1e-4)
+        reach_d += x2d <= x2o * (1 + 1e-4)
+    print(f"median iters learned {np.median(it_l)} default {np.median(it_d)}; converged "
+          f"{ok_l}/{ok_d}; oracle chi2 reached {reach_l}/{reach_d} of {len(sub)}")
+    assert reach_l >= reach_d, (reach_l, reach_d)
