@@ -40,6 +40,8 @@ METRICP = ("model+PSF+chi2 evals/s (64 stamps 1024x1024 bulge+disk, Moffat 255x2
            "split-precision bf16 DFT contractions on tensor cores)")
 METRICB = ("fits/s to oracle chi2 (4096 Sersic+sky stamps, sides 32-256, Moffat 33x33, "
            "8-param batched LM)")
+METRICL = ("fits/s to oracle chi2 (65536 64x64 Sersic+sky stamps, Moffat 33x33, learned CNN "
+           "start with default-guess fallback, 8-param batched LM)")
 L2_FLUSH_BYTES = 256 << 20
 BENCH_TOL = 1e-6  # LM ftol and xtol of the timed fits
 
@@ -51,7 +53,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gf", choices=["gf", "reference"])
     ap.add_argument("--workload", default="stamp512",
-                    choices=["stamp512", "stamp64", "batch4096", "precision64x1024"])
+                    choices=["stamp512", "stamp64", "batch4096", "precision64x1024",
+                             "learned65536"])
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (for profiler runs)")
     return ap.parse_args()
@@ -543,6 +546,177 @@ def cpu_baseline_batch(sts, budget_s=20.0):
     return best
 
 
+def run_learned(args):
+    """65536 fresh 64x64 single-Sersic stamps fitted by the batched LM from the
+    learned start (network + default guess + chi^2 check); the network is first
+    trained on about a million stamps rendered on the fly (untimed setup)."""
+    import torch
+    import torch.distributed as dist
+    ws_, rank, local = dist_env()
+    if ws_ > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1101_2254_gb300 import build, gf, learned
+    build.build()
+    stream = torch.cuda.current_stream()
+    # training: 2000 Adam steps of 512 stamps, each batch drawn and rendered on the GPU
+    train_steps, train_batch = 2000, 512
+    tr = learned.Trainer(seed=40, batch=train_batch, lr=2e-4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tr.train(train_steps)
+    e1.record(stream)
+    e1.synchronize()
+    train_s = e0.elapsed_time(e1) / 1e3
+    # evaluation stamps (prior of the training set, their own seeds)
+    count = 65536
+    p_true, psf = gf.train_sample(7 + 1000 * rank, count, learned.PSF_SIZE)
+    img, sig = learned.render(p_true, psf, 8 + 1000 * rank)
+    img, sig, psf = img.reshape(-1), sig.reshape(-1), psf.reshape(-1)
+    b = learned.uniform_batch(count)
+    d = learned.stamp_desc()
+    fixed = np.zeros(9, np.uint8)
+    fixed[7] = 1
+    opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL)
+    ws = gf.Workspace(device=dev)
+    ws_lm = gf.Workspace(device=dev)
+
+    def fit(learned_start=True):
+        if learned_start:
+            st, choice, _ = learned.starts(tr.w, b, img, sig, psf, ws=ws)
+        else:
+            st, choice = gf.default_guess(b, img, ws=ws), None
+        pb, res = gf.lm_fit_batch(d, b, st.cpu().numpy(), fixed, img, sig, psf, opts=opts,
+                                  ws=ws_lm)
+        return pb, res, choice
+
+    for _ in range(max(args.warmup, 0)):
+        fit()
+    torch.cuda.synchronize()
+    if ws_ > 1:
+        dist.barrier()
+    step_ms = []
+    with ClockSampler(local) as clk:
+        launches0 = gf.launch_count()
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pb, res, choice = fit()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        launches = gf.launch_count() - launches0
+    total_ms = float(sum(step_ms))
+    if ws_ > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = count * args.steps * ws_ / (total_ms / 1e3)
+    # the same fits from the default start alone, for comparison
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pdf, rdf, _ = fit(learned_start=False)
+    e1.record(stream)
+    e1.synchronize()
+    dflt_ms = e0.elapsed_time(e1)
+    # end to end through the public calls: host (pinned) inputs in, parameters out
+    img_h, sig_h, psf_h = img.cpu().pin_memory(), sig.cpu().pin_memory(), psf.cpu().pin_memory()
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 2))):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        i_d = img_h.to(dev, non_blocking=True)
+        s_d = sig_h.to(dev, non_blocking=True)
+        p_d = psf_h.to(dev, non_blocking=True)
+        st, _, _ = learned.starts(tr.w, b, i_d, s_d, p_d, ws=ws)
+        pe, _ = gf.lm_fit_batch(d, b, st.cpu().numpy(), fixed, i_d, s_d, p_d, opts=opts, ws=ws_lm)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    with gf.Profiler() as prof:
+        fit()
+    pr = prof.result
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    ach = pr["conv"]["work"] / (pr["conv"]["ms"] / 1e3) / 1e12
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    it_l = np.array([r["iters"] for r in res])
+    it_d = np.array([r["iters"] for r in rdf])
+    st_l = np.array([r["status"] for r in res])
+    st_d = np.array([r["status"] for r in rdf])
+    L = np.array(tr.losses)
+    line = {"metric": METRICL, "value": value, "unit": "fits/s", "n_gpus": ws_,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded; stamps drawn and rendered on the device)",
+            "config": {"workload": "learned65536", "stamps": count, "side": 64,
+                       "psf": learned.PSF_SIZE, "free_params": 8, "lm_tol": BENCH_TOL,
+                       "start": "CNN (bf16) with default-guess fallback by chi2",
+                       "l2": "inputs (2.4 GB) larger than L2", "parallelism": f"replicas{ws_}"},
+            "e2e": {"value": count / (float(np.mean(e2e_ms)) / 1e3), "unit": "fits/s",
+                    "h2d_bytes_per_step": int(img.numel() * 4 * 2 + psf.numel() * 4),
+                    "d2h_bytes_per_step": int(count * 9 * 8 * 2)},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "kernel": "k_conv_direct (2 P^2 FLOP per output)",
+                         "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "traffic": None},
+            "kernel_ms_per_step": {k: v["ms"] for k, v in pr.items()},
+            "lm": {"iters_median": float(np.median(it_l)), "iters_mean": float(it_l.mean()),
+                   "converged": int((st_l == 0).sum()),
+                   "start_network_kept": int(choice.sum().item())},
+            "default_start": {"value": count / (dflt_ms / 1e3), "unit": "fits/s",
+                              "iters_median": float(np.median(it_d)),
+                              "iters_mean": float(it_d.mean()), "converged": int((st_d == 0).sum())},
+            "training": {"stamps": train_steps * train_batch, "seconds": train_s,
+                         "stamps_per_s": train_steps * train_batch / train_s,
+                         "loss_first": float(L[:20].mean()), "loss_last": float(L[-20:].mean())},
+            "clocks": clk.summary(), "peaks": peak_kind}
+    if rank == 0 and ws_ == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"], line["reach_oracle_chi2"] = cpu_baseline_learned(
+            p_true, img, sig, psf, pb, pdf)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws_ > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline_learned(p_true, img, sig, psf, p_learned, p_default, n=128):
+    """The oracle's batched LM (OpenMP across stamps) from its own default guess
+    on the first n stamps (timed), and from the true parameters (the reference
+    chi^2 that the GPU fits are checked against)."""
+    import oracle
+    img = img.cpu().numpy().reshape(-1, 64, 64)[:n].astype(np.float64)
+    sig = sig.cpu().numpy().reshape(-1, 64, 64)[:n].astype(np.float64)
+    psf = psf.cpu().numpy().reshape(-1, 33, 33)[:n].astype(np.float64)
+    pt = p_true[:n].cpu().numpy()
+    od = oracle.make_desc(64, 64, 33, [oracle.SERSIC, oracle.SKY], 5, 8)
+    fixed = np.zeros(9, np.uint8)
+    fixed[7] = 1
+    p0 = np.stack([oracle.default_guess(im) for im in img])
+    args = ([od] * n, None, fixed, psf.ravel(), np.arange(n) * 33 * 33, img.ravel(), sig.ravel(),
+            np.arange(n) * 64 * 64)
+    t0 = time.perf_counter()
+    oracle.lm_fit_batch(args[0], p0, *args[2:], method=1)
+    dt = time.perf_counter() - t0
+    _, ro = oracle.lm_fit_batch(args[0], pt, *args[2:], method=1)
+    reach_l = reach_d = 0
+    for i in range(n):
+        x2o = ro[i]["chi2"]
+        reach_l += oracle.evaluate(od, p_learned[i], psf[i], img[i], sig[i], 1)[0] <= x2o * (1 + 1e-4)
+        reach_d += oracle.evaluate(od, p_default[i], psf[i], img[i], sig[i], 1)[0] <= x2o * (1 + 1e-4)
+    base = {"value": n / dt, "unit": "fits/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"oracle batched LM (OpenMP across stamps, FFT convolution) of the first {n} "
+                      f"of the 65536 stamps from the oracle's default guess, {dt:.1f} s"}
+    reach = {"stamps": n, "learned": int(reach_l), "default": int(reach_d),
+             "rule": "oracle chi2 at the GPU fit <= (1 + 1e-4) x the oracle's own fit from the "
+                     "true parameters"}
+    return base, reach
+
+
 # ------------------------------------------------------------------ the oracle
 def _oracle_setup(name):
     import oracle
@@ -648,5 +822,7 @@ if __name__ == "__main__":
         run_batch(a)
     elif a.workload == "precision64x1024":
         run_precision(a)
+    elif a.workload == "learned65536":
+        run_learned(a)
     else:
         run_gf(a)

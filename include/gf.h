@@ -303,8 +303,9 @@ gf_status gf_eval_static(const gf_desc* d, const double* params_host, const floa
 #define GF_CNN_NPARAM 195432
 
 size_t gf_cnn_nparams(void);
-/* Workspace bytes of gf_cnn_forward / gf_cnn_loss_grad for a batch. */
-size_t gf_cnn_workspace_size(int batch);
+/* Workspace bytes of gf_cnn_forward (training = 0) or gf_cnn_loss_grad
+ * (training = 1) for a batch. */
+size_t gf_cnn_workspace_size(int batch, int training);
 
 /* He-normal weights N(0, 2 / fan_in) from Philox4x32-10 keyed by seed, zero
  * biases, into w_dev (GF_CNN_NPARAM floats). */

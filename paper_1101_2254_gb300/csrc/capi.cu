@@ -1490,10 +1490,10 @@ extern "C" {
 
 size_t gf_cnn_nparams(void) { return CNN_NPARAM; }
 
-size_t gf_cnn_workspace_size(int batch)
+size_t gf_cnn_workspace_size(int batch, int training)
 {
     if (batch < 1) return 0;
-    return cnn_buffers(nullptr, batch, nullptr);
+    return cnn_buffers(nullptr, batch, training != 0, nullptr);
 }
 
 gf_status gf_cnn_init(float* w, unsigned long long seed, gf_stream stream)
@@ -1518,9 +1518,9 @@ gf_status gf_cnn_forward(const float* w, const float* x, int batch, float* y, vo
     gf_status r = check_cnn_batch(batch);
     if (r != GF_OK) return r;
     if (!w || !x || !y) return fail(GF_EINVAL, "NULL argument");
-    if ((r = check_ws(ws, ws_bytes, cnn_buffers(nullptr, batch, nullptr))) != GF_OK) return r;
+    if ((r = check_ws(ws, ws_bytes, cnn_buffers(nullptr, batch, false, nullptr))) != GF_OK) return r;
     CnnBuffers cb;
-    cnn_buffers(ws, batch, &cb);
+    cnn_buffers(ws, batch, false, &cb);
     cudaStream_t s = (cudaStream_t)stream;
     GF_CUDA(cnn_prepare(w, x, batch, cb, s));
     GF_CUDA(cnn_forward(w, batch, cb, y, s));
@@ -1533,9 +1533,9 @@ gf_status gf_cnn_loss_grad(const float* w, const float* x, const float* t, int b
     gf_status r = check_cnn_batch(batch);
     if (r != GF_OK) return r;
     if (!w || !x || !t || !loss || !grad) return fail(GF_EINVAL, "NULL argument");
-    if ((r = check_ws(ws, ws_bytes, cnn_buffers(nullptr, batch, nullptr))) != GF_OK) return r;
+    if ((r = check_ws(ws, ws_bytes, cnn_buffers(nullptr, batch, true, nullptr))) != GF_OK) return r;
     CnnBuffers cb;
-    cnn_buffers(ws, batch, &cb);
+    cnn_buffers(ws, batch, true, &cb);
     cudaStream_t s = (cudaStream_t)stream;
     GF_CUDA(cnn_prepare(w, x, batch, cb, s));
     GF_CUDA(cnn_forward(w, batch, cb, nullptr, s));

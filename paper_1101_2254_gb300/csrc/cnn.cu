@@ -815,7 +815,7 @@ __global__ void k_select(int count, int nslots, const double* __restrict__ cand,
 
 // ================================================================ launchers
 
-size_t cnn_buffers(void* ws, int B, CnnBuffers* cb)
+size_t cnn_buffers(void* ws, int B, bool training, CnnBuffers* cb)
 {
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -831,13 +831,16 @@ size_t cnn_buffers(void* ws, int B, CnnBuffers* cb)
             std::min<long long>(std::max<long long>(1, 2048 / (L.cout * L.cin)), total);
         part = std::max(part, (size_t)(nchunk * L.cout * L.cin * 10));
     }
+    // the gradient buffers exist only when the call trains
+    const size_t T = training ? 1 : 0;
     const size_t wp = take(2ull * NPARAM), wf = take(2ull * CONV_W_END), wb = take(2ull * CONV_W_END),
                  x = take(2ull * B * NPIX), a0 = take(2ull * B * 32 * 32 * 32),
                  a1 = take(2ull * B * 64 * 16 * 16), a2 = take(2ull * B * 64 * 8 * 8),
                  a3 = take(2ull * B * 2048), h = take(4ull * B * 32), y = take(4ull * B * NOUT),
-                 gy = take(4ull * B * NOUT), gh = take(4ull * B * 32), g3 = take(4ull * B * 2048),
-                 g2 = take(4ull * B * 64 * 8 * 8), g1 = take(4ull * B * 64 * 16 * 16),
-                 g0 = take(4ull * B * 32 * 32 * 32), pt = take(4ull * part);
+                 gy = take(T * 4ull * B * NOUT), gh = take(T * 4ull * B * 32),
+                 g3 = take(T * 4ull * B * 2048), g2 = take(T * 4ull * B * 64 * 8 * 8),
+                 g1 = take(T * 4ull * B * 64 * 16 * 16), g0 = take(T * 4ull * B * 32 * 32 * 32),
+                 pt = take(T * 4ull * part);
     if (cb && ws) {
         char* p = static_cast<char*>(ws);
         cb->wp = (__nv_bfloat16*)(p + wp);

@@ -22,8 +22,9 @@ struct CnnBuffers {
     float* part;                   // first-stage weight-gradient partials
 };
 
-// bytes of the buffers for batch B; fills cb when ws and cb are given
-size_t cnn_buffers(void* ws, int B, CnnBuffers* cb);
+// bytes of the buffers for batch B (with the gradient buffers when training);
+// fills cb when ws and cb are given
+size_t cnn_buffers(void* ws, int B, bool training, CnnBuffers* cb);
 cudaError_t cnn_prepare(const float* w, const float* x, int B, const CnnBuffers& cb, cudaStream_t s);
 cudaError_t cnn_forward(const float* w, int B, const CnnBuffers& cb, float* y, cudaStream_t s);
 cudaError_t cnn_backward(const float* t, int B, float* loss, float* grad, const CnnBuffers& cb,

@@ -108,7 +108,7 @@ def lib():
                                             C.c_size_t, vp]
             L.gf_cnn_nparams.restype = C.c_size_t
             L.gf_cnn_workspace_size.restype = C.c_size_t
-            L.gf_cnn_workspace_size.argtypes = [C.c_int]
+            L.gf_cnn_workspace_size.argtypes = [C.c_int, C.c_int]
             L.gf_cnn_init.restype = C.c_int
             L.gf_cnn_init.argtypes = [vp, C.c_ulonglong, vp]
             L.gf_cnn_input.restype = C.c_int
@@ -434,7 +434,7 @@ def cnn_forward(w, x, ws=None, stream=None):
     import torch
     B = x.numel() // (CNN_SIDE * CNN_SIDE)
     y = torch.empty(B, CNN_NOUT, dtype=torch.float32, device=x.device)
-    wk, n = _ws(ws).get(lib().gf_cnn_workspace_size(B))
+    wk, n = _ws(ws).get(lib().gf_cnn_workspace_size(B, 0))
     _check(lib().gf_cnn_forward(_ptr(w), _ptr(x), B, _ptr(y), wk, n, _stream(stream)))
     return y
 
@@ -447,7 +447,7 @@ def cnn_loss_grad(w, x, t, ws=None, grad=None, loss=None, stream=None):
         grad = torch.empty_like(w)
     if loss is None:
         loss = torch.empty(1, dtype=torch.float32, device=x.device)
-    wk, n = _ws(ws).get(lib().gf_cnn_workspace_size(B))
+    wk, n = _ws(ws).get(lib().gf_cnn_workspace_size(B, 1))
     _check(lib().gf_cnn_loss_grad(_ptr(w), _ptr(x), _ptr(t), B, _ptr(loss), _ptr(grad), wk, n,
                                   _stream(stream)))
     return loss, grad
