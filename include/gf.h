@@ -264,8 +264,10 @@ gf_status gf_lm_fit_batch(const gf_desc* d, const gf_batch* b, double* params_ho
  *     before any launch.  A 1024x1024 stamp with a 65x65 PSF fits; 2048x2048
  *     does not.
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current, and (like the first
+ *     model-evaluating call of any kind) fills the library's static b_n table
+ *     with one kernel and a synchronisation of the stream; make that first
+ *     call before any stream capture.
  *   - All calls share the one array and it keeps the last call's contents.
  *     Every byte a call reads is written earlier by the same call, so nothing
  *     needs clearing, but calls whose work overlaps on the GPU (different

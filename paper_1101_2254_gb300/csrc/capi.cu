@@ -363,6 +363,7 @@ struct Layout {
     size_t dft_buf[2], dft_mat;  // DFT path: ping-pong complex buffers, bf16 DFT matrices
     int count, nchan, nacc, nslots;
     int tot_model, tot_os, tot_conv, tot_red;
+    int max_red;  // most reduction blocks of one stamp
 };
 
 struct Plan {
@@ -385,6 +386,7 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     int* po = pm + (count + 1);
     int* pc = po + (count + 1);
     int* pr = pc + (count + 1);
+    int max_red = 0;
     long long e1 = 0, y1 = 0;
     for (int b = 0; b < count; ++b) {
         StampInfo& s = pl->st[b];
@@ -413,9 +415,11 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         po[b + 1] = po[b] + (nb2 + OS_WARPS - 1) / OS_WARPS;
         pc[b + 1] = pc[b] + ((s.H + CONV_TY - 1) / CONV_TY) * ((s.W + CONV_TX - 1) / CONV_TX);
         pr[b + 1] = pr[b] + (int)(((long long)s.H * s.W + RED_PIX - 1) / RED_PIX);
+        max_red = std::max(max_red, pr[b + 1] - pr[b]);
     }
     Layout& L = pl->L;
     memset(&L, 0, sizeof(L));
+    L.max_red = max_red;
     L.count = count;
     L.nchan = S.nchan;
     L.nacc = S.nacc;
@@ -571,6 +575,7 @@ PassArgs base_args(void* ws, const Layout& L, const float* psf, const float* img
     a.S = at<Structure>(ws, L.S);
     const int* pre = at<int>(ws, L.pre);
     a.pre_static = pre;
+    a.max_red = L.max_red;
     a.wl.n = at<int>(ws, L.n_static);
     a.wl.ids = at<int>(ws, L.ids_static);
     a.wl.pre = pre;
@@ -876,8 +881,7 @@ gf_status jac_pass(const PassArgs& a, const Plan& pl, void* ws, const double* pa
     if (r != GF_OK) return r;
     ProfScope ps(PROF_REDUCE, s);
     GF_CUDA(launch_reduce_jac(a, s));
-    // the LM body folds the final reduction into k_final_solve
-    if (!a.lm) GF_CUDA(launch_final_jac(a, A, g, x2, s));
+    GF_CUDA(launch_final_jac(a, A, g, x2, s));
     return GF_OK;
 }
 
@@ -894,6 +898,29 @@ gf_status trial_pass(const PassArgs& a, const Plan& pl, void* ws, cudaStream_t s
     // the LM body folds the final reduction into k_final_update; a render
     // (no image) has no chi^2
     if (!a.lm && x2) GF_CUDA(launch_final_chi2(a, x2, s));
+    return GF_OK;
+}
+
+// The b_n table of the LM kernels, built once per device on the first call
+// that evaluates a model (a one-time synchronisation of that call's stream).
+// Under stream capture it is left for a later call: until it exists the
+// kernels solve for b_n directly.
+std::mutex g_bn_mu;
+bool g_bn_built[64];
+
+gf_status ensure_bn_table(cudaStream_t s)
+{
+    int dev = 0;
+    GF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GF_OK;
+    std::lock_guard<std::mutex> g(g_bn_mu);
+    if (g_bn_built[dev]) return GF_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    GF_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return GF_OK;
+    GF_CUDA(launch_bn_table(s));
+    GF_CUDA(cudaStreamSynchronize(s));
+    g_bn_built[dev] = true;
     return GF_OK;
 }
 
@@ -1051,6 +1078,7 @@ gf_status gf_model(const gf_desc* d, const double* params, float* out, void* ws,
     plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, 0, &pl);
     if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
+    if ((r = ensure_bn_table(s)) != GF_OK) return r;
     if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
     PassArgs a = base_args(ws, pl.L, nullptr, nullptr, nullptr, d->psf_size);
     a.chan = at<Channel>(ws, pl.L.chan_trial);
@@ -1133,6 +1161,7 @@ gf_status gf_eval(const gf_desc* d, const double* params, const float* img, cons
     plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, NEED_TRIAL, &pl);
     if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
+    if ((r = ensure_bn_table(s)) != GF_OK) return r;
     if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
     PassArgs a = trial_args(ws, pl.L, base_args(ws, pl.L, psf, img, sig, d->psf_size));
     a.m_out = model_out;
@@ -1161,6 +1190,7 @@ static gf_status eval_batch_impl(const gf_desc* d, const gf_batch* b, const doub
     plan_batch(d, S, b->count, b->H, b->W, b->pix_off, b->psf_off, NEED_TRIAL, &pl);
     if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
+    if ((r = ensure_bn_table(s)) != GF_OK) return r;
     if ((r = upload(ws, make_blob(pl, S, params_on_device ? nullptr : params), s)) != GF_OK) return r;
     if (params_on_device)
         GF_CUDA(cudaMemcpyAsync(at<double>(ws, pl.L.params), params,
@@ -1210,6 +1240,7 @@ gf_status gf_jacobian(const gf_desc* d, const double* params, const uint8_t* fix
     plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, NEED_JAC, &pl);
     if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
+    if ((r = ensure_bn_table(s)) != GF_OK) return r;
     if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
     PassArgs a = jac_args(ws, pl.L, base_args(ws, pl.L, psf, img, sig, d->psf_size));
     a.J_out = J_out;
@@ -1241,6 +1272,7 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     plan_batch(d, S, b->count, b->H, b->W, b->pix_off, b->psf_off, NEED_LM, &pl);
     if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
+    if ((r = ensure_bn_table(s)) != GF_OK) return r;
     const Layout& L = pl.L;
     if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
     if ((r = setup_conv(ws, pl, psf, s)) != GF_OK) return r;
@@ -1435,6 +1467,7 @@ extern "C" gf_status gf_eval_static(const gf_desc* d, const double* params, cons
     void* ws = nullptr;
     if ((r = static_scratch_address(&ws)) != GF_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
+    if ((r = ensure_bn_table(s)) != GF_OK) return r;
     const std::vector<uint8_t> blob = make_blob(pl, S, params);
     StaticBlob sb;
     memcpy(sb.bytes, blob.data(), blob.size());

@@ -274,6 +274,7 @@ struct PassArgs {
     float* m_out;              // optional model output (H x W per stamp, packed at pix_off)
     WorkList wl;               // the stamps taking part in this pass
     const int* pre_static;     // [WK_KINDS][count + 1] block prefixes over all stamps
+    int max_red;               // most reduction blocks of one stamp
     int grid[WK_KINDS];        // persistent launch grid per kernel kind
     int maxitems[WK_KINDS];    // upper bound of work items (all stamps, all channels)
     int P;                     // PSF side (uniform across the stamps of a call)
@@ -297,6 +298,7 @@ cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_chi2(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_final_jac(const PassArgs& a, double* A_out, double* g_out, double* chi2_out,
                              cudaStream_t s);
+cudaError_t launch_bn_table(cudaStream_t s);
 cudaError_t launch_final_chi2(const PassArgs& a, double* chi2_out, cudaStream_t s);
 cudaError_t launch_psf_sum(int count, const StampInfo* st, const float* psf, float* out,
                            cudaStream_t s);

@@ -246,20 +246,55 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_chi2(PassArgs a)
 }
 
 // one block per stamp: sum the stamp's partials in block order
-__global__ void __launch_bounds__(RED_THREADS) k_final_jac(PassArgs a, double* A_out,
-                                                           double* g_out, double* chi2_out)
+// Final sums of the Jacobian pass.  Block (stamp b, group y) owns accumulators
+// 32y .. 32y + 31, one per lane, so each warp reads whole 128-byte rows of the
+// partials; the warps split the stamp's partials into nseg interleaved
+// segments (nseg from the stamp's own partial count, so a stamp is summed in
+// the same order in any batch), merged in segment order.  Writes A, g and chi^2
+// into the stamp's LM state, or into A_out, g_out, chi2_out.
+constexpr int FINAL_SEG_MAX = 16;
+
+__host__ __device__ __forceinline__ int final_nseg(int nred)
 {
+    return nred / 4 < 1 ? 1 : (nred / 4 > FINAL_SEG_MAX ? FINAL_SEG_MAX : nred / 4);
+}
+
+__global__ void __launch_bounds__(32 * FINAL_SEG_MAX) k_final_jac(PassArgs a, double* A_out,
+                                                                  double* g_out, double* chi2_out)
+{
+    __shared__ CSum part[FINAL_SEG_MAX][32];
     const int b = blockIdx.x;
     if (a.lm && a.lm[b].phase != a.phase) return;
-    const int nf = a.S->nfree, nacc = a.nacc, tid = threadIdx.x;
-    if (tid >= nacc) return;
+    const int nacc = a.nacc, lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const int t = blockIdx.y * 32 + lane;
     const int* pst = a.pre_static + WK_RED * (a.count + 1);
     const int b0 = pst[b], b1 = pst[b + 1];
+    const int nseg = final_nseg(b1 - b0);
     CSum acc = {0.0f, 0.0f};
-    for (int k = b0; k < b1; ++k) csum_add(acc, a.partial[(long long)k * nacc + tid]);
-    const double v = (double)acc.s + (double)acc.c;
+    if (t < nacc && seg < nseg) {
+        const float* src = a.partial + t;
+        int k = b0 + seg;
+        for (; k + 3 * nseg < b1; k += 4 * nseg) {
+            const float v0 = src[(long long)k * nacc];
+            const float v1 = src[(long long)(k + nseg) * nacc];
+            const float v2 = src[(long long)(k + 2 * nseg) * nacc];
+            const float v3 = src[(long long)(k + 3 * nseg) * nacc];
+            csum_add(acc, v0);
+            csum_add(acc, v1);
+            csum_add(acc, v2);
+            csum_add(acc, v3);
+        }
+        for (; k < b1; k += nseg) csum_add(acc, src[(long long)k * nacc]);
+    }
+    part[seg][lane] = acc;
+    __syncthreads();
+    if (seg != 0 || t >= nacc) return;
+    CSum tot = part[0][lane];
+    for (int q = 1; q < nseg; ++q) tot = csum_merge(tot, part[q][lane]);
+    const double v = (double)tot.s + (double)tot.c;
+    const int nf = a.S->nfree;
     int i, j;
-    const int kind = decode_acc(tid, nf, i, j);
+    const int kind = decode_acc(t, nf, i, j);
     double* A = a.lm ? a.lm[b].A : A_out + (long long)b * nf * nf;
     double* g = a.lm ? a.lm[b].g : g_out + (long long)b * nf;
     if (kind == 0) {
@@ -356,7 +391,8 @@ cudaError_t launch_reduce_chi2(const PassArgs& a, cudaStream_t s)
 cudaError_t launch_final_jac(const PassArgs& a, double* A_out, double* g_out, double* chi2_out,
                              cudaStream_t s)
 {
-    k_final_jac<<<a.count, RED_THREADS, 0, s>>>(a, A_out, g_out, chi2_out);
+    const dim3 grid(a.count, (a.nacc + 31) / 32);
+    k_final_jac<<<grid, 32 * final_nseg(a.max_red), 0, s>>>(a, A_out, g_out, chi2_out);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
