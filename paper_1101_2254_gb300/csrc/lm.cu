@@ -209,7 +209,8 @@ __device__ __forceinline__ double xtol_scale(int role)
 __device__ void project_slot(const Structure& S, double* p, int s)
 {
     if (S.role[s] == R_PA) {
-        double a = fmod(p[s], 180.0);
+        // p - 180 k with k = floor(p / 180): exact for the angles a fit meets
+        double a = p[s] - 180.0 * floor(p[s] * (1.0 / 180.0));
         if (a < 0.0) a += 180.0;
         if (a >= 180.0) a -= 180.0;
         p[s] = a;
@@ -348,49 +349,53 @@ __device__ void warp_build_jac(const Structure& S, WarpScratch& W, float psum, C
     }
 }
 
-// Warp Cholesky of the SPD n x n matrix W.M (lower factor in place) and the
-// solve of M x = W.r (x in W.r).  Returns false (uniformly) when a pivot is not
-// positive or a result is not finite.
+// Warp Cholesky factorisation M = L L^T of the SPD n x n matrix W.M (n <= 16;
+// lower factor in place) and the solve M x = W.r (x in W.r).  Lane i owns row
+// i: each column step scales the entries below the pivot by 1/sqrt(pivot) and
+// updates the trailing part of the lane's own row, reading the other rows'
+// pivot-column entries from shared memory; both substitutions go column by
+// column with one shuffle per step.  Returns false (uniformly) when a pivot is
+// not positive or a result is not finite.
 __device__ bool warp_cholesky_solve(int n, WarpScratch& W)
 {
     const int lane = threadIdx.x & 31;
     double* M = W.M;
+    double* mine = M + lane * n;  // dereferenced only for lane < n
+    double invd_mine = 0.0;
     for (int j = 0; j < n; ++j) {
         __syncwarp();
-        const double djj = M[j * n + j];
-        if (!(djj > 0.0) || !isfinite(djj)) return false;
-        const double d = sqrt(djj);
+        const double piv = __shfl_sync(kFull, lane == j ? mine[j] : 0.0, j);
+        if (!(piv > 0.0) || !isfinite(piv)) return false;
+        const double d = sqrt(piv);
+        const double invd = 1.0 / d;
+        if (lane == j) {
+            mine[j] = d;
+            invd_mine = invd;
+        } else if (lane > j && lane < n) {
+            mine[j] *= invd;
+        }
         __syncwarp();
-        for (int i = j + 1 + lane; i < n; i += 32) M[i * n + j] /= d;
-        if (lane == 0) M[j * n + j] = d;
-        __syncwarp();
-        const int m = n - j - 1;
-        for (int t = lane; t < m * m; t += 32) {
-            const int i = j + 1 + t / m, k = j + 1 + t % m;
-            if (k <= i) M[i * n + k] -= M[i * n + j] * M[k * n + j];
+        if (lane > j && lane < n) {
+            const double lij = mine[j];
+            for (int k = j + 1; k <= lane; ++k) mine[k] -= lij * M[k * n + j];
         }
     }
-    // forward then back substitution; each row's dot product is a warp reduction
-    double* r = W.r;
-    for (int i = 0; i < n; ++i) {
-        __syncwarp();
-        double t = (lane < i) ? M[i * n + lane] * r[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        __syncwarp();
-        if (lane == 0) r[i] = (r[i] - t) / M[i * n + i];
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        __syncwarp();
-        double t = (lane > i && lane < n) ? M[lane * n + i] * r[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        __syncwarp();
-        if (lane == 0) r[i] = (r[i] - t) / M[i * n + i];
-    }
     __syncwarp();
-    const bool fin = lane >= n || isfinite(r[lane]);
-    return __all_sync(0xffffffffu, fin);
+    // forward substitution L y = r, then back substitution L^T x = y
+    double ri = lane < n ? W.r[lane] : 0.0;
+    for (int k = 0; k < n; ++k) {
+        const double yk = __shfl_sync(kFull, ri * invd_mine, k);
+        if (lane == k) ri = yk;
+        else if (lane > k && lane < n) ri -= mine[k] * yk;
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        const double xk = __shfl_sync(kFull, ri * invd_mine, k);
+        if (lane == k) ri = xk;
+        else if (lane < k) ri -= M[k * n + lane] * xk;
+    }
+    if (lane < n) W.r[lane] = ri;
+    __syncwarp();
+    return __all_sync(kFull, lane >= n || isfinite(ri));
 }
 
 __device__ void lm_reject(const Structure& S, LMState& L)
@@ -513,17 +518,20 @@ __global__ void __launch_bounds__(32) k_final_solve(PassArgs a, Channel* trial_c
     }
     // damped system (A + lambda diag A) delta = g; a slot with A_ii = 0 is held
     const double lam = L.lambda;
-    for (int t = lane; t < nf * nf; t += 32) {
-        const int i = t / nf, j = t % nf;
-        const double aii = L.A[i * nf + i], ajj = L.A[j * nf + j];
-        double v = L.A[t];
-        if (!(aii > 0.0) || !(ajj > 0.0))
-            v = (i == j) ? 1.0 : 0.0;
-        else if (i == j)
-            v = aii * (1.0 + lam);
-        W.M[t] = v;
+    if (lane < nf) {  // lane i builds row i
+        const int i = lane;
+        const double aii = L.A[i * nf + i];
+        for (int j = 0; j < nf; ++j) {
+            const double ajj = L.A[j * nf + j];
+            double v = L.A[i * nf + j];
+            if (!(aii > 0.0) || !(ajj > 0.0))
+                v = (i == j) ? 1.0 : 0.0;
+            else if (i == j)
+                v = aii * (1.0 + lam);
+            W.M[i * nf + j] = v;
+        }
+        W.r[i] = aii > 0.0 ? L.g[i] : 0.0;
     }
-    for (int i = lane; i < nf; i += 32) W.r[i] = (L.A[i * nf + i] > 0.0) ? L.g[i] : 0.0;
     const bool ok = warp_cholesky_solve(nf, W);
     const int iters = L.iters + 1;
     __syncwarp();
