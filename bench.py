@@ -454,6 +454,10 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
 
     opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL)
+    # untimed setup: the direct convolution's tile width per width class
+    d_direct = gf.make_desc(1, 1, s0.P, s0.kinds, s0.os_factor, 8, conv_method=gf.CONV_DIRECT)
+    gf.autotune(d_direct, batch, psf_d, ws=ws)
+    tiles = {int(c): gf.conv_tile_width(s0.P, 32 * int(c)) for c in sorted({(w + 31) // 32 for w in Ws})}
 
     def fit():
         return gf.lm_fit_batch(d, batch, p0, s0.fixed, img_d, sig_d, psf_d, opts=opts, ws=ws)
@@ -498,6 +502,7 @@ def run_batch(args):
             "config": {"workload": "batch4096", "stamps": len(sts),
                        "pixels": int(sum(h * w for h, w in zip(Hs, Ws))), "psf": s0.P,
                        "conv": "direct", "free_params": s0.nfree, "lm_tol": BENCH_TOL,
+                       "tile_width_by_class": tiles,
                        "l2": "inputs (0.5 GB) larger than L2", "parallelism": f"replicas{ws_}"},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "kernel": "k_conv_direct (2 P^2 FLOP per output)",

@@ -245,6 +245,26 @@ gf_status gf_lm_fit_batch(const gf_desc* d, const gf_batch* b, double* params_ho
                           const gf_lm_opts* opts, gf_lm_result* result_host, void* ws,
                           size_t ws_bytes, gf_stream stream);
 
+/* ------------------------------------------------------------ tile tuning
+ * No counterpart in the paper.  The direct convolution covers each stamp with
+ * 32 x 64 or 32 x 32 output tiles.  The two differ only for stamp widths W with
+ * ceil(W / 32) odd: there the narrow tile saves a 32-column strip per tile row
+ * but stages more halo per output.  The choice is kept per device, per PSF side
+ * P and per class ceil(W / 32); untuned classes use the narrow tile.  Results
+ * do not depend on it (every output is summed in the same order).
+ *
+ * gf_autotune times both widths on the stamps of each such class in the batch
+ * (the Jacobian pass's channels, the caller's PSFs) and keeps the faster.  It
+ * synchronises the stream, must not run under stream capture, and needs a
+ * workspace of gf_workspace_size_batch() bytes.  It does nothing for Fourier-
+ * space convolution. */
+gf_status gf_autotune(const gf_desc* d, const gf_batch* b, const float* psf_dev, void* ws,
+                      size_t ws_bytes, gf_stream stream);
+/* The tile width (64 or 32) the current device uses for PSF side P and width W. */
+int gf_conv_tile_width(int psf_size, int width);
+/* Set it for the class of W (a class with ceil(W / 32) even accepts only 64). */
+gf_status gf_set_conv_tile_width(int psf_size, int width, int tile_w);
+
 /* ------------------------------------------------- allocation-free evaluation
  * No counterpart in the paper: an interface for callers that cannot allocate
  * device memory at all -- for example a plugin whose host application owns

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -354,6 +355,29 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 enum { NEED_JAC = 1, NEED_TRIAL = 2, NEED_LM = 4, NEED_CHI2 = 8 };
 
+// ------------------------------------------------------ tile-width choice
+// Direct-convolution tile width per stamp: 64 (4 warps) or 32 (2 warps).  The
+// two cover a stamp's columns in the same number of 64-wide steps unless
+// ceil(W / 32) is odd, when the 32-wide tile saves a 32-column strip per tile
+// row but stages more halo per output.  Which wins for a given PSF side and
+// width class is measured by gf_autotune and kept per device; until then the
+// smaller padded width wins.
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tune[64];  // (P, ceil(W / 32)) -> tile width
+
+int conv_tile_width(int P, int W)
+{
+    const int cls = (W + 31) / 32;
+    if ((cls & 1) == 0) return 64;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        const auto it = g_tune[dev].find({P, cls});
+        if (it != g_tune[dev].end()) return it->second;
+    }
+    return 32;
+}
+
 struct Layout {
     size_t S, st, pre, params, chan_jac, chan_trial, lm, psum, ext_jac, ext_trial, y_jac,
         y_trial, part_jac, part_trial, active, exp, blob_end, total;
@@ -362,7 +386,7 @@ struct Layout {
     size_t tw_x, tw_y, hhat, psfgrid, spec_jac, spec_trial;
     size_t dft_buf[2], dft_mat;  // DFT path: ping-pong complex buffers, bf16 DFT matrices
     int count, nchan, nacc, nslots;
-    int tot_model, tot_os, tot_conv, tot_red;
+    int tot_model, tot_os, tot_conv, tot_red, tot_conv32;
     int max_red;  // most reduction blocks of one stamp
 };
 
@@ -381,11 +405,12 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
 {
     const int P = d->psf_size, c = (P - 1) / 2;
     pl->st.resize(count);
-    pl->pre.assign(4 * (count + 1), 0);
-    int* pm = pl->pre.data();
-    int* po = pm + (count + 1);
-    int* pc = po + (count + 1);
-    int* pr = pc + (count + 1);
+    pl->pre.assign(WK_KINDS * (count + 1), 0);
+    int* pm = pl->pre.data() + WK_MODEL * (count + 1);
+    int* po = pl->pre.data() + WK_OS * (count + 1);
+    int* pc = pl->pre.data() + WK_CONV * (count + 1);
+    int* pr = pl->pre.data() + WK_RED * (count + 1);
+    int* pc32 = pl->pre.data() + WK_CONV32 * (count + 1);
     int max_red = 0;
     long long e1 = 0, y1 = 0;
     for (int b = 0; b < count; ++b) {
@@ -413,7 +438,10 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         pm[b + 1] = pm[b] + (int)((ne + MODEL_THREADS - 1) / MODEL_THREADS);
         const int nb2 = s.os_factor > 1 ? s.os_box * s.os_box : 0;
         po[b + 1] = po[b] + (nb2 + OS_WARPS - 1) / OS_WARPS;
-        pc[b + 1] = pc[b] + ((s.H + CONV_TY - 1) / CONV_TY) * ((s.W + CONV_TX - 1) / CONV_TX);
+        s.conv_tw = conv_tile_width(P, s.W);
+        const int conv_tiles = ((s.H + CONV_TY - 1) / CONV_TY) * ((s.W + s.conv_tw - 1) / s.conv_tw);
+        pc[b + 1] = pc[b] + (s.conv_tw == 64 ? conv_tiles : 0);
+        pc32[b + 1] = pc32[b] + (s.conv_tw == 32 ? conv_tiles : 0);
         pr[b + 1] = pr[b] + (int)(((long long)s.H * s.W + RED_PIX - 1) / RED_PIX);
         max_red = std::max(max_red, pr[b + 1] - pr[b]);
     }
@@ -427,6 +455,7 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     L.tot_model = pm[count];
     L.tot_os = po[count];
     L.tot_conv = pc[count];
+    L.tot_conv32 = pc32[count];
     L.tot_red = pr[count];
     size_t o = 0;
     L.S = o;
@@ -434,7 +463,7 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     L.st = o;
     o += al(sizeof(StampInfo) * count);
     L.pre = o;
-    o += al(sizeof(int) * 4 * (count + 1));
+    o += al(sizeof(int) * WK_KINDS * (count + 1));
     L.params = o;
     o += al(sizeof(double) * (size_t)count * S.nslots);
     L.ids_static = o;
@@ -557,8 +586,9 @@ T* at(void* ws, size_t off)
 void set_grids(PassArgs& a, const Layout& L, int nchan)
 {
     const long long items[WK_KINDS] = {(long long)L.tot_model * nchan, (long long)L.tot_os * nchan,
-                                       (long long)L.tot_conv * nchan, (long long)L.tot_red};
-    const long long cap[WK_KINDS] = {152LL * 16, 152LL * 8, 152LL * 8, 152LL * 6};
+                                       (long long)L.tot_conv * nchan, (long long)L.tot_red,
+                                       (long long)L.tot_conv32 * nchan};
+    const long long cap[WK_KINDS] = {152LL * 16, 152LL * 8, 152LL * 8, 152LL * 6, 152LL * 16};
     for (int k = 0; k < WK_KINDS; ++k) {
         a.maxitems[k] = (int)std::min<long long>(items[k], INT32_MAX);
         a.grid[k] = (int)std::min(items[k], cap[k]);
@@ -1367,6 +1397,103 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
         res[i].accepted = (int)o[S.nslots + 3];
         res[i].status = (int)o[S.nslots + 4];
     }
+    return GF_OK;
+}
+
+// Time the two direct-convolution tile widths on the stamps of each width
+// class with ceil(W / 32) odd (the classes where they differ), over the
+// Jacobian pass's channels, and keep the faster per (P, class) on this device.
+gf_status gf_autotune(const gf_desc* d, const gf_batch* b, const float* psf, void* ws,
+                      size_t ws_bytes, gf_stream stream)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    if (!b || b->count < 1 || !b->H || !b->W || !psf) return fail(GF_EINVAL, "bad batch or PSF");
+    for (int i = 0; i < b->count; ++i)
+        if ((r = check_stamp(d, b->H[i], b->W[i])) != GF_OK) return r;
+    if (resolve_method(d) != GF_CONV_DIRECT) return GF_OK;  // nothing to choose
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    GF_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return fail(GF_EINVAL, "gf_autotune cannot run under capture");
+    int dev = 0;
+    GF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(GF_ECUDA, "device ordinal out of range");
+    Structure S;
+    if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, &S)) != GF_OK) return r;
+    const int P = d->psf_size;
+    std::map<int, std::vector<int>> classes;  // odd class -> stamps
+    for (int i = 0; i < b->count; ++i) {
+        const int cls = (b->W[i] + 31) / 32;
+        if (cls & 1) classes[cls].push_back(i);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GF_CUDA(cudaEventCreate(&e0));
+    GF_CUDA(cudaEventCreate(&e1));
+    gf_status out = GF_OK;
+    for (const auto& kv : classes) {
+        const int cls = kv.first;
+        std::vector<int> H, W;
+        std::vector<int64_t> psf_off;
+        for (int i : kv.second) {
+            H.push_back(b->H[i]);
+            W.push_back(b->W[i]);
+            psf_off.push_back(b->psf_off ? b->psf_off[i] : (int64_t)i * P * P);
+        }
+        float best_ms[2] = {INFINITY, INFINITY};
+        const int widths[2] = {64, 32};
+        for (int v = 0; v < 2 && out == GF_OK; ++v) {
+            {
+                std::lock_guard<std::mutex> g(g_tune_mu);
+                g_tune[dev][{P, cls}] = widths[v];
+            }
+            Plan pl;
+            plan_batch(d, S, (int)H.size(), H.data(), W.data(), nullptr, psf_off.data(), NEED_JAC, &pl);
+            if ((out = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) break;
+            if ((out = upload(ws, make_blob(pl, S, nullptr), s)) != GF_OK) break;
+            PassArgs a = jac_args(ws, pl.L, base_args(ws, pl.L, psf, nullptr, nullptr, P));
+            if (cudaMemsetAsync(a.ext, 0, sizeof(float) * (size_t)pl.L.nchan *
+                                              (pl.st.back().ext1_off +
+                                               (long long)pl.st.back().He * pl.st.back().We),
+                                s) != cudaSuccess ||
+                launch_conv_direct_width(a, widths[v], s) != cudaSuccess) {
+                out = fail(GF_ECUDA, "autotune launch failed");
+                break;
+            }
+            for (int rep = 0; rep < 3; ++rep) {
+                float ms = 0.0f;
+                if (cudaEventRecord(e0, s) != cudaSuccess ||
+                    launch_conv_direct_width(a, widths[v], s) != cudaSuccess ||
+                    cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    out = fail(GF_ECUDA, "autotune timing failed");
+                    break;
+                }
+                best_ms[v] = std::min(best_ms[v], ms);
+            }
+        }
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune[dev][{P, cls}] = best_ms[1] < best_ms[0] ? 32 : 64;
+        if (out != GF_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return out;
+}
+
+int gf_conv_tile_width(int psf_size, int width) { return conv_tile_width(psf_size, width); }
+
+gf_status gf_set_conv_tile_width(int psf_size, int width, int tile_w)
+{
+    if (tile_w != 32 && tile_w != 64) return fail(GF_EINVAL, "tile width must be 32 or 64");
+    if (psf_size < 1 || width < 1) return fail(GF_EINVAL, "bad PSF side or width");
+    const int cls = (width + 31) / 32;
+    if ((cls & 1) == 0) return tile_w == 64 ? GF_OK : fail(GF_EINVAL, "even width classes use 64");
+    int dev = 0;
+    GF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(GF_ECUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[dev][{psf_size, cls}] = tile_w;
     return GF_OK;
 }
 

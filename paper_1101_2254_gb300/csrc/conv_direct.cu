@@ -4,11 +4,13 @@
 //   out(i, j) = sum_{v,u} psf[v][u] * E[i+2c-v][j+2c-u]
 //             = sum_{v,u} k[v][u]   * E[i+v][j+u],   k[v][u] = psf[P-1-v][P-1-u]
 //
-// One CTA (4 warps) computes a 32 x 64 output tile of one channel.  The flipped
-// PSF (rows padded with zeros to a multiple of 4 taps) and the (32+P-1) x
-// (64+P4) halo tile of the channel grid are staged in shared memory.  A warp
-// covers 16 x 32 outputs with lanes arranged 4 (rows) x 8 (columns); a thread
-// owns a 4 x 4 block.  For each tap row v and each group of 4 taps, a thread
+// One CTA computes a 32 x TX output tile of one channel: TX = 64 (4 warps) or
+// TX = 32 (2 warps), chosen per stamp (the two kinds of work item).  The
+// flipped PSF (rows padded with zeros to a multiple of 4 taps) and the
+// (32+P-1) x (TX+P4) halo tile of the channel grid are staged in shared memory.
+// A warp covers 16 x 32 outputs with lanes arranged 4 (rows) x 8 (columns); a
+// thread owns a 4 x 4 block.  A warp whose 16 x 32 quadrant lies wholly outside
+// the stamp skips the taps (its issue slots go to the SM's other CTAs).  For each tap row v and each group of 4 taps, a thread
 // issues one broadcast 16-byte load of the taps and one 16-byte load of the
 // next 4 grid values per output row, then 64 FMAs: 5 shared loads per 64 FMAs.
 // Eight lanes of a quarter-warp read 128 contiguous bytes, so the grid loads
@@ -20,14 +22,16 @@
 
 namespace {
 
-constexpr int TY = CONV_TY, TX = CONV_TX, NT = 128;
+constexpr int TY = CONV_TY;
 
-// Work item = (channel, output tile of a listed stamp).
-__global__ void __launch_bounds__(NT) k_conv_direct(PassArgs a)
+// Work item = (channel, output tile of a listed stamp of this tile width).
+template <int TX>
+__global__ void __launch_bounds__(TX * 2) k_conv_direct(PassArgs a)
 {
+    constexpr int NT = TX * 2, WX = TX / 32;  // threads, warps across
     extern __shared__ __align__(16) float smem[];
     const int n = *a.wl.n;
-    const int* pre = a.wl.pre + WK_CONV * (a.count + 1);
+    const int* pre = a.wl.pre + (TX == 64 ? WK_CONV : WK_CONV32) * (a.count + 1);
     const int tot = pre[n];
     const long long items = (long long)tot * a.nchan;
     const int P = a.P, P4 = (P + 3) & ~3;
@@ -35,8 +39,9 @@ __global__ void __launch_bounds__(NT) k_conv_direct(PassArgs a)
     float* ks = smem;               // P x P4 flipped taps
     float* es = smem + P * P4;      // SH x SW grid tile (P*P4 is a multiple of 4)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = (warp >> 1) * 16 + (lane >> 3) * 4;
-    const int c0 = (warp & 1) * 32 + (lane & 7) * 4;
+    const int wr0 = (warp / WX) * 16, wc0 = (warp % WX) * 32;
+    const int r0 = wr0 + (lane >> 3) * 4;
+    const int c0 = wc0 + (lane & 7) * 4;
     int hint = -1, psf_b = -1;
     const long long chunk = (items + gridDim.x - 1) / gridDim.x;
     const long long it0 = (long long)blockIdx.x * chunk, it1 = min(items, it0 + chunk);
@@ -65,6 +70,7 @@ __global__ void __launch_bounds__(NT) k_conv_direct(PassArgs a)
         }
         __syncthreads();
 
+        if (ty0 + wr0 >= st.H || tx0 + wc0 >= st.W) continue;  // quadrant outside the stamp
         float acc[4][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -99,9 +105,9 @@ __global__ void __launch_bounds__(NT) k_conv_direct(PassArgs a)
             }
         }
 
-        if (a.work && threadIdx.x == 0) {
+        if (a.work && (lane | (warp / WX)) == 0) {  // lane 0 of the first warp of each column
             const unsigned long long rows = (unsigned long long)min(TY, st.H - ty0);
-            const unsigned long long cols = (unsigned long long)min(TX, st.W - tx0);
+            const unsigned long long cols = (unsigned long long)min(32, st.W - tx0 - wc0);
             atomicAdd(&a.work[PROF_CONV], 2ull * (unsigned long long)P * P * rows * cols);
         }
         float* Y = a.y + y_index(st, a.nchan, ch);
@@ -122,29 +128,48 @@ __global__ void __launch_bounds__(NT) k_conv_direct(PassArgs a)
 
 cudaError_t ensure_smem_optin_conv_direct(int P, int* cache);
 
-size_t conv_direct_smem(int P)
+template <int TX>
+size_t conv_smem(int P)
 {
     const int P4 = (P + 3) & ~3;
     return sizeof(float) * ((size_t)P * P4 + (size_t)(TY + P - 1) * (TX + P4));
 }
 
-cudaError_t launch_conv_direct(const PassArgs& a, cudaStream_t s)
+size_t conv_direct_smem(int P) { return conv_smem<64>(P); }
+
+template <int TX>
+cudaError_t launch_tile(const PassArgs& a, int kind, cudaStream_t s)
 {
-    if (a.maxitems[WK_CONV] <= 0) return cudaSuccess;
-    const size_t sm = conv_direct_smem(a.P);
-    cudaError_t e = ensure_smem_optin_conv_direct(a.P, nullptr);
-    if (e != cudaSuccess) return e;
-    k_conv_direct<<<a.grid[WK_CONV], NT, sm, s>>>(a);
+    if (a.maxitems[kind] <= 0) return cudaSuccess;
+    k_conv_direct<TX><<<a.grid[kind], TX * 2, conv_smem<TX>(a.P), s>>>(a);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
-// one cache per device for every caller, so that a call made before a stream
-// capture leaves nothing to set inside it
-static int g_conv_direct_optin[64];
+cudaError_t launch_conv_direct(const PassArgs& a, cudaStream_t s)
+{
+    cudaError_t e = ensure_smem_optin_conv_direct(a.P, nullptr);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_tile<64>(a, WK_CONV, s)) != cudaSuccess) return e;
+    return launch_tile<32>(a, WK_CONV32, s);
+}
+
+// launch one tile width alone (the tuner times the two against each other)
+cudaError_t launch_conv_direct_width(const PassArgs& a, int tile_w, cudaStream_t s)
+{
+    cudaError_t e = ensure_smem_optin_conv_direct(a.P, nullptr);
+    if (e != cudaSuccess) return e;
+    return tile_w == 64 ? launch_tile<64>(a, WK_CONV, s) : launch_tile<32>(a, WK_CONV32, s);
+}
+
+// one cache per device and width for every caller, so that a call made before a
+// stream capture leaves nothing to set inside it
+static int g_conv_optin64[64], g_conv_optin32[64];
 
 cudaError_t ensure_smem_optin_conv_direct(int P, int*)
 {
-    return ensure_smem_optin((const void*)k_conv_direct, (int)conv_direct_smem(P),
-                             g_conv_direct_optin);
+    cudaError_t e = ensure_smem_optin((const void*)k_conv_direct<64>, (int)conv_smem<64>(P),
+                                      g_conv_optin64);
+    if (e != cudaSuccess) return e;
+    return ensure_smem_optin((const void*)k_conv_direct<32>, (int)conv_smem<32>(P), g_conv_optin32);
 }

@@ -63,7 +63,7 @@ struct StampInfo {
     int He, We;
     int os_factor, os_box, os_x0, os_y0;  // block origin resolved
     int nchan;                             // channels of the Jacobian pass
-    int pad;
+    int conv_tw;                           // direct-convolution tile width (64 or 32)
     long long pix_off;   // into image / sigma / model (H*W elements)
     long long psf_off;   // into the PSF array (P*P)
     long long ext1_off;  // sum of He*We over the earlier stamps
@@ -211,7 +211,9 @@ __device__ __forceinline__ int find_stamp(const int* prefix, int count, int blk)
 
 // ------------------------------------------------------------------ work lists
 // Kernel kinds with per-stamp block counts.
-enum { WK_MODEL = 0, WK_OS = 1, WK_CONV = 2, WK_RED = 3, WK_KINDS = 4 };
+// work-item kinds; the direct convolution has one kind per tile width
+// (WK_CONV: 32 x 64 tiles, WK_CONV32: 32 x 32 tiles; each stamp uses one)
+enum { WK_MODEL = 0, WK_OS = 1, WK_CONV = 2, WK_RED = 3, WK_CONV32 = 4, WK_KINDS = 5 };
 
 // The stamps taking part in a pass (all stamps, or those in the pass's LM
 // phase), in stamp order, and per kernel kind the exclusive prefix sums of
@@ -294,6 +296,7 @@ extern std::atomic<long long> g_launch_count;
 // kernel launchers (return cudaGetLastError())
 cudaError_t launch_model(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_conv_direct(const PassArgs& a, cudaStream_t s);
+cudaError_t launch_conv_direct_width(const PassArgs& a, int tile_w, cudaStream_t s);
 cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_chi2(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_final_jac(const PassArgs& a, double* A_out, double* g_out, double* chi2_out,

@@ -136,6 +136,12 @@ def lib():
             L.gf_guess_select.restype = C.c_int
             L.gf_guess_select.argtypes = [C.c_int, vp, vp, vp, vp, dp, dp, vp, vp, vp,
                                           C.c_size_t, vp]
+            L.gf_autotune.restype = C.c_int
+            L.gf_autotune.argtypes = [pd, C.POINTER(Batch), vp, vp, C.c_size_t, vp]
+            L.gf_conv_tile_width.restype = C.c_int
+            L.gf_conv_tile_width.argtypes = [C.c_int, C.c_int]
+            L.gf_set_conv_tile_width.restype = C.c_int
+            L.gf_set_conv_tile_width.argtypes = [C.c_int, C.c_int, C.c_int]
             L.gf_launch_count.restype = C.c_longlong
             L.gf_prof_enable.argtypes = [vp]
             L.gf_prof_times.restype = C.c_int
@@ -530,6 +536,21 @@ def guess_select(cand, x2_cand, dflt, x2_dflt, lo=None, hi=None, ws=None, stream
                                  _ptr(dflt.contiguous()), _ptr(x2_dflt), _dp(lo_a), _dp(hi_a),
                                  _ptr(out), _ptr(choice), wk, n, _stream(stream)))
     return out, choice
+
+
+def autotune(d: Desc, batch: Batch, psf, ws=None, stream=None):
+    """Time both direct-convolution tile widths per width class of the batch and
+    keep the faster on this device (a no-op for Fourier-space convolution)."""
+    w, n = _ws(ws).get(lib().gf_workspace_size_batch(C.byref(d), C.byref(batch), None))
+    _check(lib().gf_autotune(C.byref(d), C.byref(batch), _ptr(psf), w, n, _stream(stream)))
+
+
+def conv_tile_width(psf_size: int, width: int) -> int:
+    return int(lib().gf_conv_tile_width(psf_size, width))
+
+
+def set_conv_tile_width(psf_size: int, width: int, tile_w: int):
+    _check(lib().gf_set_conv_tile_width(psf_size, width, tile_w))
 
 
 PROF_CLASSES = ("model", "conv", "reduce", "lm")

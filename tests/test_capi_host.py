@@ -91,3 +91,11 @@ def test_workspace_sizes_scale(gf):
     assert 0 < a < b
     # the 512x512 Jacobian pass holds 14 channel grids of 576^2 floats and 14 outputs of 512^2
     assert b > 14 * 4 * (576 * 576 + 512 * 512)
+
+
+def test_tile_width_setter_validates_before_touching_the_device():
+    from paper_1101_2254_gb300 import gf
+    L = gf.lib()
+    assert L.gf_set_conv_tile_width(33, 64, 32) == gf.EINVAL  # even class: 64 only
+    assert L.gf_set_conv_tile_width(33, 70, 48) == gf.EINVAL  # no such width
+    assert L.gf_set_conv_tile_width(0, 70, 32) == gf.EINVAL
