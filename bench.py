@@ -408,7 +408,7 @@ def run_precision(args):
                        "psf": P, "transform": [Ny, Nx], "l2": "inputs (0.5 GB) larger than L2"},
             "paths_evals_per_s": {k: n / (v["ms"] / 1e3) for k, v in res.items()},
             "errors_vs_fp64_oracle_stamp0": errs,
-            "roofline": {"bound": "hbm", "kernel": "k_dft_a + k_dft_b (8 stages x 16 B/elem)",
+            "roofline": {"bound": "hbm", "kernel": "k_dft_tc<A|B> (tcgen05; 8 stages x 16 B/elem)",
                          "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": ach / peaks["hbm_gbs"], "traffic": None,
                          "tensor_tflops": pr["conv"]["work"] / (conv_ms / 1e3) / 1e12},

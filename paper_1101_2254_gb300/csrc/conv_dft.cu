@@ -16,20 +16,34 @@
 //
 // Precision: float32 data and DFT matrices are split x = hi + lo into bf16
 // pairs; each real product uses hi*hi + hi*lo + lo*hi (the lo*lo term is ~2^-16
-// of the result) with float32 accumulation, and a complex product is four real
-// ones with the sign of Im(F) folded into the bf16 sign bits: 12
-// mma.m16n8k16 per complex 16 x 8 x 16 block.
+// of the result) with float32 accumulation.
+//
+// Tensor cores (tcgen05, accumulators in tensor memory).  A stage is a batch
+// of rows (orientation A: the (l, q) pairs; B: the m rows), each contracted
+// with the R x R DFT matrix along r.  A CTA takes 128 rows at a time as the M
+// side of one accumulator of 128 lanes x 2 Rp columns: columns k hold Re and
+// Rp + k hold Im of output k, because the B operand stacks the DFT matrix as
+//   B1 = [Fr; Fi] (against the real part of the rows) and
+//   B2 = [-Fi; Fr] (against the imaginary part),
+// so that Re = Xr Fr^T - Xi Fi^T and Im = Xr Fi^T + Xi Fr^T fall out of one
+// accumulator: 6 MMAs (M 128, N 2Rp, K 16) per 16 values of r.  Operands sit in
+// shared memory in the canonical K-major layout without swizzle (8 x 8 bf16
+// core matrices, 128 B each; consecutive along K 128 B apart, consecutive
+// 8-row groups Kp * 16 B apart).  One thread issues the MMAs and commits them
+// to an mbarrier; every wait on it is bounded and a timeout turns the tile's
+// outputs into NaN and raises the stage's error word.
 #include <math.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "conv_dft.cuh"
 
 namespace {
 
-constexpr int NT = 128;   // 4 warps
-constexpr int QT = 64;    // orientation A: q columns per CTA tile (16 per warp)
-constexpr int MTILE = 64; // orientation B: rows per CTA tile (16 per warp)
-constexpr int LPB = 8;    // tiles per CTA (the DFT matrix is staged once for them)
+constexpr int NT = 256;    // 8 warps: staging 2 threads per row, epilogue 2 warps per lane quarter
+constexpr int TM = 128;    // rows per tile (the MMA's M)
+constexpr unsigned kWaitLimit = 1u << 24;
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& h, __nv_bfloat16& l)
 {
@@ -37,79 +51,62 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& h, __nv_bfloa
     l = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-__device__ __forceinline__ void mma16816(float* c, const uint32_t* a, const uint32_t* b)
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle
+__device__ __forceinline__ uint64_t mdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: bf16 x bf16 -> f32, both K-major, M x N
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, int acc)
 {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
-// A fragment (16 x 16, element (m, k) at P[m * ld + k]) at origin (m0, k0)
-__device__ __forceinline__ void frag_a(uint32_t* a, const __nv_bfloat16* P, int ld, int m0, int k0)
+// element offset of (row, k) in a canonical K-major plane with Kp columns
+__device__ __forceinline__ int cofs(int row, int k, int Kp)
 {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    a[0] = *reinterpret_cast<const uint32_t*>(P + (m0 + g) * ld + k0 + 2 * t);
-    a[1] = *reinterpret_cast<const uint32_t*>(P + (m0 + g + 8) * ld + k0 + 2 * t);
-    a[2] = *reinterpret_cast<const uint32_t*>(P + (m0 + g) * ld + k0 + 2 * t + 8);
-    a[3] = *reinterpret_cast<const uint32_t*>(P + (m0 + g + 8) * ld + k0 + 2 * t + 8);
+    return ((row >> 3) * (Kp >> 3) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
 }
 
-// B fragment (16 x 8, element (k, n) at P[n * ld + k]) at origin (n0, k0)
-__device__ __forceinline__ void frag_b(uint32_t* b, const __nv_bfloat16* P, int ld, int n0, int k0)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    b[0] = *reinterpret_cast<const uint32_t*>(P + (n0 + g) * ld + k0 + 2 * t);
-    b[1] = *reinterpret_cast<const uint32_t*>(P + (n0 + g) * ld + k0 + 2 * t + 8);
+    uint32_t done = 0;
+    for (unsigned it = 0; it < kWaitLimit && !done; ++it)
+        asm volatile(
+            "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, q;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity));
+    return done != 0;
 }
 
-__device__ __forceinline__ void neg2(uint32_t* d, const uint32_t* s, int n)
+// 8 consecutive fp32 columns of the calling warp's lane quarter
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float* v)
 {
-    for (int i = 0; i < n; ++i) d[i] = s[i] ^ 0x80008000u;
-}
-
-// (re, im) += F * X for one 16 x 8 x 16 block; F planes f[0..3] = re hi, re lo,
-// im hi, im lo (A or B role per `f_is_a`), X planes x[0..3] likewise.
-__device__ __forceinline__ void cmma_fa(float* cre, float* cim, const uint32_t (*f)[4],
-                                        const uint32_t (*x)[2])
-{
-    uint32_t nh[4], nl[4];
-    neg2(nh, f[2], 4);
-    neg2(nl, f[3], 4);
-    mma16816(cre, f[0], x[0]);
-    mma16816(cre, f[0], x[1]);
-    mma16816(cre, f[1], x[0]);
-    mma16816(cre, nh, x[2]);
-    mma16816(cre, nh, x[3]);
-    mma16816(cre, nl, x[2]);
-    mma16816(cim, f[0], x[2]);
-    mma16816(cim, f[0], x[3]);
-    mma16816(cim, f[1], x[2]);
-    mma16816(cim, f[2], x[0]);
-    mma16816(cim, f[2], x[1]);
-    mma16816(cim, f[3], x[0]);
-}
-
-// same with the data as the A operand and F as B: (re, im) += X * F^T
-__device__ __forceinline__ void cmma_fb(float* cre, float* cim, const uint32_t (*x)[4],
-                                        const uint32_t (*f)[2])
-{
-    uint32_t nh[2], nl[2];
-    neg2(nh, f[2], 2);
-    neg2(nl, f[3], 2);
-    mma16816(cre, x[0], f[0]);
-    mma16816(cre, x[1], f[0]);
-    mma16816(cre, x[0], f[1]);
-    mma16816(cre, x[2], nh);
-    mma16816(cre, x[3], nh);
-    mma16816(cre, x[2], nl);
-    mma16816(cim, x[2], f[0]);
-    mma16816(cim, x[3], f[0]);
-    mma16816(cim, x[2], f[1]);
-    mma16816(cim, x[0], f[2]);
-    mma16816(cim, x[1], f[2]);
-    mma16816(cim, x[0], f[3]);
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b)
@@ -126,16 +123,6 @@ __device__ __forceinline__ float2 twiddle(const DftStage& s, int e)
     return w;
 }
 
-// stage the 4 F planes (Rp x Rp) into shared memory with row stride LD
-__device__ __forceinline__ void stage_f(__nv_bfloat16* Fs, const DftStage& s, int LD)
-{
-    const int Rp = s.Rp, n = 4 * Rp * Rp;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int pl = i / (Rp * Rp), rem = i - pl * Rp * Rp, k = rem / Rp, r = rem - k * Rp;
-        Fs[(pl * Rp + k) * LD + r] = s.F[i];
-    }
-}
-
 __device__ __forceinline__ float2 in_a(const DftStage& s, int p, int l, int r, int q)
 {
     if (s.in_mode == 1) {
@@ -150,76 +137,166 @@ __device__ __forceinline__ float2 in_a(const DftStage& s, int p, int l, int r, i
     return v;
 }
 
-// Orientation A: OUT[p][l][k][q] = tw * sum_r F[k][r] IN[p][l][r][q].  A CTA holds
-// the whole k range for QT columns q of LPB consecutive l.
-__global__ void __launch_bounds__(NT) k_dft_a(DftStage s, unsigned long long* work)
+// One contraction stage on the tensor cores (see the top of the file).
+// ORIENT_A: rows are g = l * Q + q, input IN[p][l][r][q], output OUT[p][l][k][q];
+// otherwise rows are m, input IN[p][m][r], output OUT[p][m][k].  A CTA runs
+// `tpc` consecutive 128-row tiles of problem blockIdx.z.
+template <bool ORIENT_A>
+__global__ void __launch_bounds__(NT) k_dft_tc(DftStage s, int tpc, unsigned long long* work)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Rp = s.Rp, R = s.R, LD = Rp + 8;
-    __nv_bfloat16* Fs = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // 4 x Rp x LD
-    __nv_bfloat16* Xs = Fs + 4 * Rp * LD;                             // 4 x QT x LD, [q][r]
-    const int p = blockIdx.z, q0 = blockIdx.x * QT;
-    if (s.lm && s.lm[p / s.nchan].phase != s.phase) return;
-    stage_f(Fs, s, LD);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int nmt = Rp / 16, nkt = Rp / 16;
-    for (int li = 0; li < LPB; ++li) {
-        const int l = blockIdx.y * LPB + li;
-        if (l >= s.L) break;
-        if (s.out_mode == 1 && (l < s.crop_y0 || l >= s.crop_y0 + s.crop_H)) continue;
-        __syncthreads();  // Fs staged / previous tile's Xs consumed
-        for (int i = threadIdx.x; i < Rp * QT; i += NT) {
-            const int r = i / QT, qq = i - r * QT, q = q0 + qq;
-            const float2 v = (r < R && q < s.Q) ? in_a(s, p, l, r, q) : make_float2(0.f, 0.f);
-            __nv_bfloat16 h, lo;
-            split_bf16(v.x, h, lo);
-            Xs[(0 * QT + qq) * LD + r] = h;
-            Xs[(1 * QT + qq) * LD + r] = lo;
-            split_bf16(v.y, h, lo);
-            Xs[(2 * QT + qq) * LD + r] = h;
-            Xs[(3 * QT + qq) * LD + r] = lo;
-        }
-        __syncthreads();
-        float acc[4][2][2][4];  // [mtile][ntile][re/im][c]
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int p = blockIdx.z;
+    if (s.lm && s.lm[p / s.nchan].phase != s.phase) return;  // whole CTA
+    const int R = s.R, Rp = s.Rp, Kp = Rp, NB = 2 * Rp;
+    const long long rows = ORIENT_A ? (long long)s.L * s.Q : (long long)s.M;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // operand planes: B1 hi, B1 lo, B2 hi, B2 lo (NB x Kp); Xr hi, Xr lo, Xi hi, Xi lo (TM x Kp)
+    __nv_bfloat16* Bp = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+    __nv_bfloat16* Ap = Bp + 4 * NB * Kp;
+    const int ncols = NB <= 32 ? 32 : (NB <= 64 ? 64 : 128);  // TMEM columns (power of two)
+
+    // stacked DFT matrix: B1 rows n < Rp = Fr[n], n >= Rp = Fi[n - Rp];
+    //                     B2 rows n < Rp = -Fi[n], n >= Rp = Fr[n - Rp]
+    for (int i = tid; i < NB * Kp; i += NT) {
+        const int n = i / Kp, r = i - n * Kp;
+        const int k = n < Rp ? n : n - Rp;
+        const __nv_bfloat16* F = s.F + k * Rp + r;
+        const int RR = Rp * Rp;
+        const __nv_bfloat16 frh = F[0], frl = F[RR], fih = F[2 * RR], fil = F[3 * RR];
+        const int o = cofs(n, r, Kp);
+        Bp[0 * NB * Kp + o] = n < Rp ? frh : fih;
+        Bp[1 * NB * Kp + o] = n < Rp ? frl : fil;
+        Bp[2 * NB * Kp + o] = n < Rp ? __hneg(fih) : frh;
+        Bp[3 * NB * Kp + o] = n < Rp ? __hneg(fil) : frl;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tmem_base)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)));
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const uint32_t bar_a = smem_addr(&bar);
+    const uint32_t idesc = idesc_bf16(TM, NB);
+    const uint32_t lbo = 128, sbo = (uint32_t)Kp * 16;
+    uint32_t parity = 0;
+
+    for (int ti = 0; ti < tpc; ++ti) {
+        const long long g0 = ((long long)blockIdx.x * tpc + ti) * TM;
+        if (g0 >= rows) break;
+        // ---- stage the rows: thread (row, half) splits its half of the r range
+        {
+            const int row = tid & (TM - 1), half = tid >> 7;
+            const long long g = g0 + row;
+            const int rbeg = half * (Kp / 2), rend = rbeg + Kp / 2;
+            int l = 0, q = 0;
+            if (ORIENT_A && g < rows) {
+                l = (int)(g / s.Q);
+                q = (int)(g - (long long)l * s.Q);
+            }
+            for (int r8 = rbeg; r8 < rend; r8 += 8) {
+                __align__(16) __nv_bfloat16 h[4][8];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int c = 0; c < 2; ++c)
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) acc[a][b][c][d] = 0.0f;
-        for (int kt = 0; kt < nkt; ++kt) {
-            uint32_t xb[2][4][2];
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
+                for (int j = 0; j < 8; ++j) {
+                    const int r = r8 + j;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (g < rows && r < R) {
+                        if (ORIENT_A)
+                            v = in_a(s, p, l, r, q);
+                        else
+                            v = s.in[(long long)p * s.in_pstride + g * R + r];
+                    }
+                    split_bf16(v.x, h[0][j], h[1][j]);
+                    split_bf16(v.y, h[2][j], h[3][j]);
+                }
+                const int o = cofs(row, r8, Kp);
 #pragma unroll
                 for (int pl = 0; pl < 4; ++pl)
-                    frag_b(xb[nt][pl], Xs + pl * QT * LD, LD, 16 * warp + 8 * nt, 16 * kt);
-#pragma unroll
-            for (int mt = 0; mt < 4; ++mt) {
-                if (mt >= nmt) break;
-                uint32_t fa[4][4];
-#pragma unroll
-                for (int pl = 0; pl < 4; ++pl) frag_a(fa[pl], Fs + pl * Rp * LD, LD, 16 * mt, 16 * kt);
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) cmma_fa(acc[mt][nt][0], acc[mt][nt][1], fa, xb[nt]);
+                    *reinterpret_cast<uint4*>(Ap + pl * TM * Kp + o) = *reinterpret_cast<const uint4*>(h[pl]);
             }
         }
-        // epilogue: twiddle and store
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // ---- one thread issues the MMAs: acc = Xr B1^T + Xi B2^T, split precision
+        if (tid == 0) {
+            const uint32_t a0 = smem_addr(Ap), b0 = smem_addr(Bp);
+            const uint32_t aps = TM * Kp * 2, bps = NB * Kp * 2;  // plane bytes
+            int acc = 0;
+            for (int ks = 0; ks < Kp / 16; ++ks) {
+                const uint32_t ko = ks * 256;
+                // (A plane, B plane): Xr_h B1_h, Xr_h B1_l, Xr_l B1_h, Xi_h B2_h, Xi_h B2_l, Xi_l B2_h
+                const int ap[6] = {0, 0, 1, 2, 2, 3}, bp[6] = {0, 1, 0, 2, 3, 2};
 #pragma unroll
-        for (int mt = 0; mt < 4; ++mt) {
-            if (mt >= nmt) break;
+                for (int t = 0; t < 6; ++t) {
+                    umma(tmem, mdesc(a0 + ap[t] * aps + ko, lbo, sbo), mdesc(b0 + bp[t] * bps + ko, lbo, sbo),
+                         idesc, acc);
+                    acc = 1;
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a));
+        }
+        const bool done = mbar_wait(bar_a, parity);
+        parity ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!__syncthreads_and(done ? 1 : 0)) {
+            // give up: raise the error word, wait once more (bounded) for the
+            // MMAs in flight, mark this tile's outputs NaN, free TMEM, return
+            if (tid == 0 && s.err) atomicExch(s.err, 1);
+            mbar_wait(bar_a, parity ^ 1u);
+            for (int i = tid; i < TM * R; i += NT) {
+                const long long g = g0 + i / R;
+                const int k = i % R;
+                if (g >= rows) continue;
+                const float2 nan2 = make_float2(NAN, NAN);
+                if (ORIENT_A) {
+                    const int l = (int)(g / s.Q), q = (int)(g - (long long)l * s.Q);
+                    if (s.out_mode == 0) {
+                        s.out[(long long)p * s.out_pstride + ((long long)l * R + k) * s.Q + q] = nan2;
+                    } else {
+                        const int y = l - s.crop_y0, x = k * s.out_xdigit + q - s.crop_x0;
+                        if (y >= 0 && y < s.crop_H && x >= 0 && x < s.crop_W)
+                            s.out_real[(long long)p * s.out_real_pstride + (long long)y * s.crop_W + x] = NAN;
+                    }
+                } else {
+                    s.out[(long long)p * s.out_pstride + g * R + k] = nan2;
+                }
+            }
+            __syncthreads();
+            if (warp == 0)
+                asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+            return;
+        }
+        // ---- epilogue: warp w reads lane quarter w % 4, output half w / 4
+        {
+            const int quarter = warp & 3, khalf = warp >> 2;
+            const int row = quarter * 32 + lane;
+            const long long g = g0 + row;
+            int l = 0, q = 0;
+            if (ORIENT_A) {
+                l = (int)(g / s.Q);
+                q = (int)(g - (long long)l * s.Q);
+            }
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+            for (int k0 = khalf * (Rp / 2); k0 < (khalf + 1) * (Rp / 2); k0 += 8) {
+                float re[8], im[8];
+                tmem_ld8(taddr + k0, re);
+                tmem_ld8(taddr + Rp + k0, im);
+                if (g >= rows) continue;
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                for (int hf = 0; hf < 2; ++hf)
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int k = 16 * mt + g + 8 * hf;
-                        const int q = q0 + 16 * warp + 8 * nt + 2 * t + j;
-                        if (k >= R || q >= s.Q) continue;
-                        float2 v = make_float2(acc[mt][nt][0][2 * hf + j], acc[mt][nt][1][2 * hf + j]);
+                for (int j = 0; j < 8; ++j) {
+                    const int k = k0 + j;
+                    if (k >= R) continue;
+                    float2 v = make_float2(re[j], im[j]);
+                    if (ORIENT_A) {
                         if (s.tw_mode == 1)
                             v = cmulf(v, twiddle(s, k * ((q / s.tw_div) % s.tw_mod)));
                         else if (s.tw_mode == 2)
@@ -231,85 +308,24 @@ __global__ void __launch_bounds__(NT) k_dft_a(DftStage s, unsigned long long* wo
                             if (y >= 0 && y < s.crop_H && x >= 0 && x < s.crop_W)
                                 s.out_real[(long long)p * s.out_real_pstride + (long long)y * s.crop_W + x] = v.x;
                         }
+                    } else {
+                        if (s.tw_mode == 3) v = cmulf(v, twiddle(s, (int)(g % s.tw_mod) * k));
+                        s.out[(long long)p * s.out_pstride + g * R + k] = v;
                     }
-        }
-        if (work && threadIdx.x == 0) {
-            const int qv = min(QT, s.Q - q0);
-            atomicAdd(work, (unsigned long long)(8ull * R * R * qv));  // complex MACs x 8 FLOP
-        }
-    }
-}
-
-// Orientation B: OUT[p][m][k] = tw * sum_r IN[p][m][r] F[k][r].  A CTA holds the
-// whole k range for MTILE rows of LPB consecutive row tiles.
-__global__ void __launch_bounds__(NT) k_dft_b(DftStage s, unsigned long long* work)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Rp = s.Rp, R = s.R, LD = Rp + 8;
-    __nv_bfloat16* Fs = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // 4 x Rp x LD, [k][r]
-    __nv_bfloat16* Xs = Fs + 4 * Rp * LD;                             // 4 x MTILE x LD, [m][r]
-    const int p = blockIdx.z;
-    if (s.lm && s.lm[p / s.nchan].phase != s.phase) return;
-    stage_f(Fs, s, LD);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int nnt = Rp / 8, nkt = Rp / 16;
-    for (int ti = 0; ti < LPB; ++ti) {
-        const int m0 = (blockIdx.x * LPB + ti) * MTILE;
-        if (m0 >= s.M) break;
-        __syncthreads();
-        for (int i = threadIdx.x; i < MTILE * Rp; i += NT) {
-            const int mm = i / Rp, r = i - mm * Rp, m = m0 + mm;
-            float2 v = make_float2(0.f, 0.f);
-            if (r < R && m < s.M) v = s.in[(long long)p * s.in_pstride + (long long)m * R + r];
-            __nv_bfloat16 h, lo;
-            split_bf16(v.x, h, lo);
-            Xs[(0 * MTILE + mm) * LD + r] = h;
-            Xs[(1 * MTILE + mm) * LD + r] = lo;
-            split_bf16(v.y, h, lo);
-            Xs[(2 * MTILE + mm) * LD + r] = h;
-            Xs[(3 * MTILE + mm) * LD + r] = lo;
-        }
-        __syncthreads();
-        float acc[8][2][4];  // [ntile][re/im][c]
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-#pragma unroll
-                for (int d = 0; d < 4; ++d) acc[a][c][d] = 0.0f;
-        for (int kt = 0; kt < nkt; ++kt) {
-            uint32_t xa[4][4];
-#pragma unroll
-            for (int pl = 0; pl < 4; ++pl) frag_a(xa[pl], Xs + pl * MTILE * LD, LD, 16 * warp, 16 * kt);
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                if (nt >= nnt) break;
-                uint32_t fb[4][2];
-#pragma unroll
-                for (int pl = 0; pl < 4; ++pl) frag_b(fb[pl], Fs + pl * Rp * LD, LD, 8 * nt, 16 * kt);
-                cmma_fb(acc[nt][0], acc[nt][1], xa, fb);
+                }
             }
         }
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            if (nt >= nnt) break;
-#pragma unroll
-            for (int hf = 0; hf < 2; ++hf)
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int m = m0 + 16 * warp + g + 8 * hf;
-                    const int k = 8 * nt + 2 * t + j;
-                    if (m >= s.M || k >= R) continue;
-                    float2 v = make_float2(acc[nt][0][2 * hf + j], acc[nt][1][2 * hf + j]);
-                    if (s.tw_mode == 3) v = cmulf(v, twiddle(s, (m % s.tw_mod) * k));
-                    s.out[(long long)p * s.out_pstride + (long long)m * R + k] = v;
-                }
-        }
-        if (work && threadIdx.x == 0) {
-            const int mv = min(MTILE, s.M - m0);
-            atomicAdd(work, (unsigned long long)(8ull * R * R * mv));
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();  // TMEM read and the row planes free for the next tile
+        if (work && tid == 0) {
+            const long long rv = min((long long)TM, rows - g0);
+            atomicAdd(work, (unsigned long long)(8ull * R * R * rv));  // complex MACs x 8 FLOP
         }
     }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
 // F[k][r] = exp(sign 2 pi i k r / R), zero-padded to Rp x Rp, as 4 bf16 planes
@@ -336,8 +352,35 @@ __global__ void k_dft_matrix(int R, int Rp, float sign, __nv_bfloat16* F)
     }
 }
 
-size_t smem_a(int Rp) { return sizeof(__nv_bfloat16) * 4 * (size_t)(Rp + QT) * (Rp + 8); }
-size_t smem_b(int Rp) { return sizeof(__nv_bfloat16) * 4 * (size_t)(Rp + MTILE) * (Rp + 8); }
+size_t smem_tc(int Rp)
+{
+    const size_t Kp = Rp, NB = 2 * (size_t)Rp;
+    return sizeof(__nv_bfloat16) * 4 * (NB * Kp + (size_t)TM * Kp);
+}
+
+// tiles per CTA: enough CTAs for every SM (the CTA stages its DFT matrix once)
+int tiles_per_cta(long long rows, int nprob)
+{
+    const long long tiles = (rows + TM - 1) / TM;
+    long long tpc = tiles * nprob / (2 * 152);
+    return (int)std::max(1LL, std::min(tpc, 8LL));
+}
+
+template <bool A>
+cudaError_t launch_tc(const DftStage& s, int nprob, unsigned long long* work, cudaStream_t st)
+{
+    static int optin[64];
+    const size_t sm = smem_tc(s.Rp);
+    cudaError_t e = ensure_smem_optin((const void*)k_dft_tc<A>, (int)sm, optin);
+    if (e != cudaSuccess) return e;
+    const long long rows = A ? (long long)s.L * s.Q : (long long)s.M;
+    const int tpc = tiles_per_cta(rows, nprob);
+    const long long ctas = (rows + (long long)TM * tpc - 1) / ((long long)TM * tpc);
+    dim3 grid((unsigned)ctas, 1, nprob);
+    k_dft_tc<A><<<grid, NT, sm, st>>>(s, tpc, work);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -351,26 +394,11 @@ cudaError_t launch_dft_matrix(int R, int Rp, float sign, __nv_bfloat16* F, cudaS
 cudaError_t launch_dft_stage_a(const DftStage& s, int nprob, unsigned long long* work,
                                cudaStream_t st)
 {
-    static int optin[64];
-    const size_t sm = smem_a(s.Rp);
-    cudaError_t e = ensure_smem_optin((const void*)k_dft_a, (int)sm, optin);
-    if (e != cudaSuccess) return e;
-    dim3 grid((s.Q + QT - 1) / QT, (s.L + LPB - 1) / LPB, nprob);
-    k_dft_a<<<grid, NT, sm, st>>>(s, work);
-    GF_COUNT_LAUNCH();
-    return cudaGetLastError();
+    return launch_tc<true>(s, nprob, work, st);
 }
 
 cudaError_t launch_dft_stage_b(const DftStage& s, int nprob, unsigned long long* work,
                                cudaStream_t st)
 {
-    static int optin[64];
-    const size_t sm = smem_b(s.Rp);
-    cudaError_t e = ensure_smem_optin((const void*)k_dft_b, (int)sm, optin);
-    if (e != cudaSuccess) return e;
-    const int tiles = (s.M + MTILE - 1) / MTILE;
-    dim3 grid((tiles + LPB - 1) / LPB, 1, nprob);
-    k_dft_b<<<grid, NT, sm, st>>>(s, work);
-    GF_COUNT_LAUNCH();
-    return cudaGetLastError();
+    return launch_tc<false>(s, nprob, work, st);
 }

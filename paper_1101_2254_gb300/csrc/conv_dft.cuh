@@ -44,6 +44,8 @@ struct DftStage {
     // LM phase filter: problems of stamps whose phase differs are skipped
     const LMState* lm;
     int phase;
+    // set to 1 when a tensor-core wait gives up (that tile's outputs are NaN)
+    int* err;
 };
 
 cudaError_t launch_dft_stage_a(const DftStage& s, int nprob, unsigned long long* work,
