@@ -8,6 +8,14 @@
 //               over the lanes and averaged by a shuffle tree.
 // Splitting the block off keeps every warp of k_model uniform (a block pixel
 // costs os_factor^2 evaluations, 100x a plain one for 10x10 sampling).
+//
+// A Jacobian pass (unit-amplitude shape channels and finite-difference channels
+// that all share the same components) uses k_model_jac / k_model_os_jac: a
+// thread (or warp) covers every channel of its pixel and evaluates each
+// component at p once, so an FD channel costs one evaluation (at p + h) instead
+// of two.  The values written are the same floats as channel_value gives.
+#include <algorithm>
+
 #include "gf_internal.cuh"
 
 namespace {
@@ -111,10 +119,157 @@ __global__ void __launch_bounds__(OS_WARPS * 32) k_model_os(PassArgs a)
     }
 }
 
+// Jacobian-pass value of channel c given the components at p (base)
+__device__ __forceinline__ float jac_channel(const Channel& ch, const float* base, float xi, float yi,
+                                             float ox, float oy)
+{
+    float b = 0.0f;
+#pragma unroll
+    for (int k = 0; k < GF_MAX_COMP; ++k)
+        if (k == ch.comp) b = base[k];
+    if (ch.type == CH_SHAPE) return b;
+    return (comp_eval(ch.pert, xi, yi, ox, oy) - b) * ch.scale;
+}
+
+__device__ __forceinline__ void comp_base(const Channel& c0, float* base, float xi, float yi,
+                                          float ox, float oy)
+{
+#pragma unroll
+    for (int k = 0; k < GF_MAX_COMP; ++k)
+        base[k] = (k < c0.ncomp && c0.cc[k].kind != GF_SKY) ? comp_eval(c0.cc[k], xi, yi, ox, oy)
+                                                            : 0.0f;
+}
+
+// Work item = block of MODEL_THREADS grid pixels of a listed stamp (all channels).
+__global__ void __launch_bounds__(MODEL_THREADS) k_model_jac(PassArgs a)
+{
+    __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
+    const int n = *a.wl.n;
+    const int* pre = a.wl.pre + WK_MODEL * (a.count + 1);
+    const int tot = pre[n];
+    const int nch = a.nchan;
+    int hint = -1, cur_b = -1;
+    const int chunk = (tot + gridDim.x - 1) / gridDim.x;
+    const int it0 = blockIdx.x * chunk, it1 = min(tot, it0 + chunk);
+    for (int blk = it0; blk < it1; ++blk) {
+        const int li = wl_locate(pre, n, blk, hint);
+        const int b = a.wl.ids[li];
+        const StampInfo st = a.st[b];
+        if (b != cur_b) {
+            __syncthreads();
+            for (int c = 0; c < nch; ++c) load_channel(&chs[c], &a.chan[(long long)b * a.chan_stride + c]);
+            __syncthreads();
+            cur_b = b;
+        }
+        const int npix = st.He * st.We;
+        const int pix = (blk - pre[li]) * MODEL_THREADS + threadIdx.x;
+        bool write = pix < npix;
+        int i = 0, j = 0;
+        if (write) {
+            const int ie = pix / st.We, je = pix - ie * st.We;
+            i = ie - st.c;
+            j = je - st.c;
+            write = !(st.os_factor > 1 && i >= st.os_y0 && i < st.os_y0 + st.os_box &&
+                      j >= st.os_x0 && j < st.os_x0 + st.os_box);
+        }
+        if (write) {
+            float base[GF_MAX_COMP];
+            comp_base(chs[0], base, (float)j, (float)i, 0.0f, 0.0f);
+            float* E = a.ext + ext_index(st, nch, 0) + pix;
+            const long long cs = (long long)st.He * st.We;
+            for (int c = 0; c < nch; ++c)
+                E[c * cs] = jac_channel(chs[c], base, (float)j, (float)i, 0.0f, 0.0f);
+        }
+        if (a.work) {
+            const int cnt = __syncthreads_count(write);
+            if (threadIdx.x == 0)
+                atomicAdd(&a.work[PROF_MODEL], 4ull * (unsigned long long)cnt * (unsigned long long)nch);
+        }
+    }
+}
+
+// Work item = OS_WARPS pixels of a listed stamp's oversampling block (all
+// channels); lanes take sub-samples, each lane keeps every channel's sum.
+__global__ void __launch_bounds__(OS_WARPS * 32) k_model_os_jac(PassArgs a)
+{
+    __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
+    const int n = *a.wl.n;
+    const int* pre = a.wl.pre + WK_OS * (a.count + 1);
+    const int tot = pre[n];
+    const int nch = a.nchan;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int hint = -1, cur_b = -1;
+    const int chunk = (tot + gridDim.x - 1) / gridDim.x;
+    const int it0 = blockIdx.x * chunk, it1 = min(tot, it0 + chunk);
+    for (int blk = it0; blk < it1; ++blk) {
+        const int li = wl_locate(pre, n, blk, hint);
+        const int b = a.wl.ids[li];
+        const StampInfo st = a.st[b];
+        if (b != cur_b) {
+            __syncthreads();
+            for (int c = 0; c < nch; ++c) load_channel(&chs[c], &a.chan[(long long)b * a.chan_stride + c]);
+            __syncthreads();
+            cur_b = b;
+        }
+        const int q = (blk - pre[li]) * OS_WARPS + warp;
+        const int B = st.os_box;
+        if (q >= B * B) continue;
+        const int i = st.os_y0 + q / B, j = st.os_x0 + q % B;
+        const int s = st.os_factor, ns = s * s;
+        const float fs = (float)s;
+        float acc[GF_MAX_CHAN];
+#pragma unroll
+        for (int c = 0; c < GF_MAX_CHAN; ++c) acc[c] = 0.0f;
+        for (int t = lane; t < ns; t += 32) {
+            const int ay = t / s, bx = t - ay * s;
+            const float oy = ((float)ay + 0.5f) / fs - 0.5f;
+            const float ox = ((float)bx + 0.5f) / fs - 0.5f;
+            float base[GF_MAX_COMP];
+            comp_base(chs[0], base, (float)j, (float)i, ox, oy);
+#pragma unroll
+            for (int c = 0; c < GF_MAX_CHAN; ++c)
+                if (c < nch) acc[c] += jac_channel(chs[c], base, (float)j, (float)i, ox, oy);
+        }
+        const long long pix = (long long)(i + st.c) * st.We + (j + st.c);
+        const long long cs = (long long)st.He * st.We;
+        float* E = a.ext + ext_index(st, nch, 0) + pix;
+#pragma unroll
+        for (int c = 0; c < GF_MAX_CHAN; ++c) {
+            if (c >= nch) break;
+            float v = acc[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) E[c * cs] = v / (float)ns;
+        }
+        if (a.work && lane == 0) atomicAdd(&a.work[PROF_MODEL], 4ull * (unsigned long long)nch);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_model(const PassArgs& a, cudaStream_t s)
 {
+    if (a.nchan > 1) {  // a Jacobian pass: all channels of a pixel together
+        const int cap[2] = {152 * 16, 152 * 8};
+        if (a.maxitems[WK_MODEL] > 0) {
+            const int g = (int)std::min<long long>(a.maxitems[WK_MODEL] / a.nchan, cap[0]);
+            k_model_jac<<<std::max(g, 1), MODEL_THREADS, 0, s>>>(a);
+            GF_COUNT_LAUNCH();
+        }
+        // the oversampled blocks: all channels per warp when there are enough
+        // block pixels to fill the GPU (many stamps), else a warp per channel
+        // and pixel (one large stamp)
+        const long long os_groups = a.maxitems[WK_OS] / a.nchan;
+        if (os_groups * OS_WARPS >= 152LL * 32) {
+            const int g = (int)std::min<long long>(os_groups, cap[1]);
+            k_model_os_jac<<<std::max(g, 1), OS_WARPS * 32, 0, s>>>(a);
+            GF_COUNT_LAUNCH();
+        } else if (a.maxitems[WK_OS] > 0) {
+            k_model_os<<<a.grid[WK_OS], OS_WARPS * 32, 0, s>>>(a);
+            GF_COUNT_LAUNCH();
+        }
+        return cudaGetLastError();
+    }
     if (a.maxitems[WK_MODEL] > 0) {
         k_model<<<a.grid[WK_MODEL], MODEL_THREADS, 0, s>>>(a);
         GF_COUNT_LAUNCH();

