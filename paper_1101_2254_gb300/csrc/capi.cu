@@ -169,10 +169,18 @@ FFTPlan make_fft_plan(int n)
     memset(&p, 0, sizeof(p));
     p.n = n;
     int m = n;
+    while (m % 8 == 0 && p.nst < FFT_MAX_STAGES) p.radix[p.nst++] = 8, m /= 8;
     while (m % 4 == 0 && p.nst < FFT_MAX_STAGES) p.radix[p.nst++] = 4, m /= 4;
     while (m % 2 == 0 && p.nst < FFT_MAX_STAGES) p.radix[p.nst++] = 2, m /= 2;
     while (m % 3 == 0 && p.nst < FFT_MAX_STAGES) p.radix[p.nst++] = 3, m /= 3;
     while (m % 5 == 0 && p.nst < FFT_MAX_STAGES) p.radix[p.nst++] = 5, m /= 5;
+    int ns = 1;
+    for (int t = 0; t < p.nst; ++t) {
+        p.ns[t] = ns;
+        p.mag[t] = ns > 1 ? (unsigned)((((unsigned long long)1 << 32) + ns - 1) / ns) : 0u;
+        p.twstep[t] = n / (ns * p.radix[t]);
+        ns *= p.radix[t];
+    }
     return p;
 }
 

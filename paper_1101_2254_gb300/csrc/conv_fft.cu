@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_fft_rows_fwd(FFTArgs f, RowIO i
         bufA[x] = make_float2(va, vb);
     }
     __syncthreads();
-    const float2* Z = fft_smem(f.px, bufA, bufB, 1, tw, -1.0f);
+    const float2* Z = fft_smem(f.px, bufA, bufB, 0, tw, -1.0f);
     float2* out = io.spec + (long long)p * io.spec_stride;
     for (int k = threadIdx.x; k < Kx; k += blockDim.x) {
         const float2 zk = Z[k], zm = cconj(Z[(Nx - k) % Nx]);
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(COL_THREADS) k_fft_cols(FFTArgs f, ColIO io, P
     const int p = blockIdx.y;
     const int b = p / io.nchan;
     if (a.lm && a.lm[b].phase != a.phase) return;
-    const int Ny = f.Ny, Kx = f.Nx / 2 + 1, B = f.cpc;
+    const int Ny = f.Ny, Kx = f.Nx / 2 + 1, B = f.cpc, logB = __ffs(B) - 1;  // B a power of two
     float2* bufA = sm;
     float2* bufB = sm + Ny * B;
     float2* tw = sm + 2 * Ny * B;
@@ -110,30 +110,30 @@ __global__ void __launch_bounds__(COL_THREADS) k_fft_cols(FFTArgs f, ColIO io, P
     const int kx0 = blockIdx.x * B;
     float2* spec = io.spec + (long long)p * io.spec_stride;
     for (int t = threadIdx.x; t < Ny * B; t += blockDim.x) {
-        const int y = t / B, kx = kx0 + (t - y * B);
+        const int y = t >> logB, kx = kx0 + (t & (B - 1));
         bufA[t] = (y < io.rows_in && kx < Kx) ? spec[(long long)y * Kx + kx] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2* X = fft_smem(f.py, bufA, bufB, B, tw, -1.0f);
+    float2* X = fft_smem(f.py, bufA, bufB, logB, tw, -1.0f);
     if (a.work && threadIdx.x == 0) atomicAdd(&a.work[PROF_CONV], (unsigned long long)f.flops_col);
     if (mode == 0) {
         for (int t = threadIdx.x; t < Ny * B; t += blockDim.x) {
-            const int y = t / B, kx = kx0 + (t - y * B);
+            const int y = t >> logB, kx = kx0 + (t & (B - 1));
             if (kx < Kx) spec[(long long)y * Kx + kx] = X[t];
         }
         return;
     }
     const float2* H = f.hhat + (long long)b * Ny * Kx;
     for (int t = threadIdx.x; t < Ny * B; t += blockDim.x) {
-        const int y = t / B, kx = kx0 + (t - y * B);
+        const int y = t >> logB, kx = kx0 + (t & (B - 1));
         if (kx < Kx) X[t] = cmul(X[t], H[(long long)y * Kx + kx]);
     }
     __syncthreads();
     float2* other = (X == bufA) ? bufB : bufA;
-    const float2* Yv = fft_smem(f.py, X, other, B, tw, 1.0f);
+    const float2* Yv = fft_smem(f.py, X, other, logB, tw, 1.0f);
     const int r0 = io.row0, r1 = io.row0 + io.nrows_out;
     for (int t = threadIdx.x; t < Ny * B; t += blockDim.x) {
-        const int y = t / B, kx = kx0 + (t - y * B);
+        const int y = t >> logB, kx = kx0 + (t & (B - 1));
         if (kx < Kx && y >= r0 && y < r1) spec[(long long)y * Kx + kx] = Yv[t];
     }
 }
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_fft_rows_inv(FFTArgs f, RowInvI
         bufA[k] = make_float2(A.x - Bv.y, A.y + Bv.x);  // A + i B
     }
     __syncthreads();
-    const float2* z = fft_smem(f.px, bufA, bufB, 1, tw, 1.0f);
+    const float2* z = fft_smem(f.px, bufA, bufB, 0, tw, 1.0f);
     float* out = io.out + (long long)p * io.out_stride;
     for (int j = threadIdx.x; j < io.W; j += blockDim.x) {
         const float2 v = z[io.col0 + j];

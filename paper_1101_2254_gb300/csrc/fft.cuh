@@ -8,8 +8,11 @@
 // comes out in natural order, so no bit reversal is needed; stages alternate
 // between two shared buffers.
 //
-// B independent sequences are transformed at once with element (y, b) at
-// index y * B + b, so that consecutive threads touch consecutive addresses.
+// B independent sequences (B a power of two) are transformed at once with
+// element (y, b) at index y * B + b, so that consecutive threads touch
+// consecutive addresses.  No stage divides at run time: the sequence index is a
+// shift, and j / Ns is a multiply-high by a precomputed reciprocal (exact for
+// j, Ns < 2^16).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,9 +20,12 @@
 #define FFT_MAX_STAGES 24
 
 struct FFTPlan {
-    int n;                       // length
-    int nst;                     // stages
-    int radix[FFT_MAX_STAGES];   // radix of each stage (2, 3, 4 or 5)
+    int n;                        // length
+    int nst;                      // stages
+    int radix[FFT_MAX_STAGES];    // radix of each stage (2, 3, 4, 5 or 8)
+    int ns[FFT_MAX_STAGES];       // span Ns before the stage (product of earlier radices)
+    unsigned mag[FFT_MAX_STAGES]; // ceil(2^32 / Ns) for Ns > 1
+    int twstep[FFT_MAX_STAGES];   // n / (Ns R): twiddle w_{Ns R}^e = tw[e * twstep]
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
@@ -83,29 +89,56 @@ __device__ __forceinline__ void dft5(float2* v, float s)
     v[3] = csub(r2, q2);
 }
 
+// 8-point DFT as two 4-point DFTs: split m = m1 + 4 m2; even outputs are the
+// DFT4 of v[m1] + v[m1+4], odd outputs the DFT4 of w^m1 (v[m1] - v[m1+4]),
+// w = exp(s 2 pi i / 8)
+__device__ __forceinline__ void dft8(float2* v, float s)
+{
+    const float h = 0.70710678118654752440f;
+    float2 a[4], b[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        a[m] = cadd(v[m], v[m + 4]);
+        b[m] = csub(v[m], v[m + 4]);
+    }
+    b[1] = make_float2(h * (b[1].x - s * b[1].y), h * (b[1].y + s * b[1].x));
+    b[2] = cmul_si(b[2], s);
+    b[3] = make_float2(h * (-b[3].x - s * b[3].y), h * (-b[3].y + s * b[3].x));
+    dft4(a, s);
+    dft4(b, s);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        v[2 * m] = a[m];
+        v[2 * m + 1] = b[m];
+    }
+}
+
 template <int R>
 __device__ __forceinline__ void dft_r(float2* v, float s)
 {
     if (R == 2) dft2(v);
     else if (R == 3) dft3(v, s);
     else if (R == 4) dft4(v, s);
-    else dft5(v, s);
+    else if (R == 5) dft5(v, s);
+    else dft8(v, s);
 }
 
-// one Stockham stage of radix R over B interleaved sequences of length n
+// one Stockham stage of radix R over B = 2^logB interleaved sequences of length n
 template <int R>
-__device__ __forceinline__ void fft_stage(int n, int Ns, const float2* __restrict__ src,
-                                          float2* __restrict__ dst, int B, const float2* tw,
+__device__ __forceinline__ void fft_stage(int n, int Ns, unsigned mag, int twstep,
+                                          const float2* __restrict__ src,
+                                          float2* __restrict__ dst, int logB, const float2* tw,
                                           float sign)
 {
-    const int nb = n / R;             // butterflies per sequence
-    const int twstep = n / (Ns * R);  // w_{Ns R}^e = tw[e * twstep]
-    for (int t = threadIdx.x; t < nb * B; t += blockDim.x) {
-        const int j = t / B, q = t - j * B;
-        const int k = j % Ns;
+    const int nb = n / R;  // butterflies per sequence
+    const int B = 1 << logB, total = nb << logB;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int j = t >> logB, q = t & (B - 1);
+        const int jd = Ns > 1 ? (int)__umulhi((unsigned)j, mag) : j;  // j / Ns
+        const int k = j - jd * Ns;                                    // j mod Ns
         float2 v[R];
 #pragma unroll
-        for (int m = 0; m < R; ++m) v[m] = src[(j + m * nb) * B + q];
+        for (int m = 0; m < R; ++m) v[m] = src[((j + m * nb) << logB) + q];
         if (Ns > 1) {
 #pragma unroll
             for (int m = 1; m < R; ++m) {
@@ -115,37 +148,38 @@ __device__ __forceinline__ void fft_stage(int n, int Ns, const float2* __restric
             }
         }
         dft_r<R>(v, sign);
-        const int base = (j / Ns) * Ns * R + k;
+        const int base = jd * Ns * R + k;
 #pragma unroll
-        for (int m = 0; m < R; ++m) dst[(base + m * Ns) * B + q] = v[m];
+        for (int m = 0; m < R; ++m) dst[((base + m * Ns) << logB) + q] = v[m];
     }
 }
 
-// One FFT of each of B interleaved sequences held in `a` (shared memory),
+// One FFT of each of 2^logB interleaved sequences held in `a` (shared memory),
 // using `b` as the second buffer.  tw[k] = exp(-2 pi i k / n) for k < n
 // (shared or global).  sign = -1 forward, +1 inverse (unnormalised).  All
 // threads of the block call it; it ends with a barrier.  Returns the buffer
 // that holds the result.
-static __device__ float2* fft_smem(const FFTPlan& pl, float2* a, float2* b, int B,
+static __device__ float2* fft_smem(const FFTPlan& pl, float2* a, float2* b, int logB,
                                    const float2* tw, float sign)
 {
     const int n = pl.n;
     float2* src = a;
     float2* dst = b;
-    int Ns = 1;
     for (int st = 0; st < pl.nst; ++st) {
-        const int R = pl.radix[st];
-        switch (R) {
-        case 2: fft_stage<2>(n, Ns, src, dst, B, tw, sign); break;
-        case 3: fft_stage<3>(n, Ns, src, dst, B, tw, sign); break;
-        case 4: fft_stage<4>(n, Ns, src, dst, B, tw, sign); break;
-        default: fft_stage<5>(n, Ns, src, dst, B, tw, sign); break;
+        const int Ns = pl.ns[st];
+        const unsigned mag = pl.mag[st];
+        const int tws = pl.twstep[st];
+        switch (pl.radix[st]) {
+        case 2: fft_stage<2>(n, Ns, mag, tws, src, dst, logB, tw, sign); break;
+        case 3: fft_stage<3>(n, Ns, mag, tws, src, dst, logB, tw, sign); break;
+        case 4: fft_stage<4>(n, Ns, mag, tws, src, dst, logB, tw, sign); break;
+        case 5: fft_stage<5>(n, Ns, mag, tws, src, dst, logB, tw, sign); break;
+        default: fft_stage<8>(n, Ns, mag, tws, src, dst, logB, tw, sign); break;
         }
         __syncthreads();
         float2* t = src;
         src = dst;
         dst = t;
-        Ns *= R;
     }
     return src;
 }
