@@ -61,10 +61,8 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1101_2254_gb300 import dist as gd
+    return gd.env()
 
 
 def workload(name):
@@ -148,10 +146,9 @@ def fp32_peak_tflops(sm_count, mhz):
 # ------------------------------------------------------------------ the GPU arm
 def run_gf(args):
     import torch
-    import torch.distributed as dist
     ws_, rank, local = dist_env()
-    if ws_ > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_1101_2254_gb300 import dist as gd
+    gd.init(ws_)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1101_2254_gb300 import build, gf, synth
@@ -182,8 +179,7 @@ def run_gf(args):
     for _ in range(max(args.warmup, 0)):
         p, res = fit()
     torch.cuda.synchronize()
-    if ws_ > 1:
-        dist.barrier()
+    gd.barrier(ws_)
     torch.cuda.synchronize()
     results = []
     step_ms = []
@@ -210,11 +206,8 @@ def run_gf(args):
             fit()
     torch.cuda.synchronize()
     total_ms = float(sum(step_ms))
-    if ws_ > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        total_ms = float(t.item())
+    total_ms = gd.max_over_ranks(total_ms, ws_)
+    gd.barrier(ws_)
     fits = args.steps * ws_
     value = fits / (total_ms / 1e3)
 
@@ -239,10 +232,7 @@ def run_gf(args):
         if k > 0:
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_total = float(sum(e2e_ms))
-    if ws_ > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = gd.max_over_ranks(e2e_total, ws_)
     e2e_value = args.steps * ws_ / (e2e_total / 1e3)
     h2d = img_p.numel() * 4 + sig_p.numel() * 4 + psf_p.numel() * 4
     d2h = 8 * len(p0) + 32
@@ -302,8 +292,7 @@ def run_gf(args):
         line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=20.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if ws_ > 1:
-        dist.destroy_process_group()
+    gd.finalize(ws_)
 
 
 # ------------------------------------------------------------------ precision arm
@@ -425,10 +414,9 @@ def run_precision(args):
 def run_batch(args):
     """4096 uneven single-Sersic stamps fitted together by gf_lm_fit_batch."""
     import torch
-    import torch.distributed as dist
     ws_, rank, local = dist_env()
-    if ws_ > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_1101_2254_gb300 import dist as gd
+    gd.init(ws_)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1101_2254_gb300 import build, gf, synth
@@ -465,8 +453,7 @@ def run_batch(args):
     for _ in range(max(args.warmup, 0)):
         fit()
     torch.cuda.synchronize()
-    if ws_ > 1:
-        dist.barrier()
+    gd.barrier(ws_)
     step_ms, res = [], None
     with ClockSampler(local) as clk:
         launches0 = gf.launch_count()
@@ -480,10 +467,7 @@ def run_batch(args):
             step_ms.append(e0.elapsed_time(e1))
         launches = gf.launch_count() - launches0
     total_ms = float(sum(step_ms))
-    if ws_ > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = gd.max_over_ranks(total_ms, ws_)
     value = len(sts) * args.steps * ws_ / (total_ms / 1e3)
     with gf.Profiler() as prof:
         fit()
@@ -516,8 +500,7 @@ def run_batch(args):
         line["cpu_baseline"] = cpu_baseline_batch(sts, budget_s=20.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if ws_ > 1:
-        dist.destroy_process_group()
+    gd.finalize(ws_)
 
 
 def cpu_baseline_batch(sts, budget_s=20.0):
@@ -556,10 +539,9 @@ def run_learned(args):
     learned start (network + default guess + chi^2 check); the network is first
     trained on about a million stamps rendered on the fly (untimed setup)."""
     import torch
-    import torch.distributed as dist
     ws_, rank, local = dist_env()
-    if ws_ > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_1101_2254_gb300 import dist as gd
+    gd.init(ws_)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1101_2254_gb300 import build, gf, learned
@@ -599,8 +581,7 @@ def run_learned(args):
     for _ in range(max(args.warmup, 0)):
         fit()
     torch.cuda.synchronize()
-    if ws_ > 1:
-        dist.barrier()
+    gd.barrier(ws_)
     step_ms = []
     with ClockSampler(local) as clk:
         launches0 = gf.launch_count()
@@ -614,10 +595,7 @@ def run_learned(args):
             step_ms.append(e0.elapsed_time(e1))
         launches = gf.launch_count() - launches0
     total_ms = float(sum(step_ms))
-    if ws_ > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = gd.max_over_ranks(total_ms, ws_)
     value = count * args.steps * ws_ / (total_ms / 1e3)
     # the same fits from the default start alone, for comparison
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -685,8 +663,7 @@ def run_learned(args):
             p_true, img, sig, psf, pb, pdf)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if ws_ > 1:
-        dist.destroy_process_group()
+    gd.finalize(ws_)
 
 
 def cpu_baseline_learned(p_true, img, sig, psf, p_learned, p_default, n=128):
