@@ -57,6 +57,10 @@ def parse():
                              "learned65536"])
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (for profiler runs)")
+    ap.add_argument("--stamps", type=int, default=None,
+                    help="learned65536: number of stamps (default 65536; smaller for profiler runs)")
+    ap.add_argument("--train-steps", type=int, default=2000,
+                    help="learned65536: Adam steps of 512 stamps before the timed fits")
     return ap.parse_args()
 
 
@@ -548,7 +552,7 @@ def run_learned(args):
     build.build()
     stream = torch.cuda.current_stream()
     # training: 2000 Adam steps of 512 stamps, each batch drawn and rendered on the GPU
-    train_steps, train_batch = 2000, 512
+    train_steps, train_batch = args.train_steps, 512
     tr = learned.Trainer(seed=40, batch=train_batch, lr=2e-4)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -557,7 +561,7 @@ def run_learned(args):
     e1.synchronize()
     train_s = e0.elapsed_time(e1) / 1e3
     # evaluation stamps (prior of the training set, their own seeds)
-    count = 65536
+    count = args.stamps or 65536
     p_true, psf = gf.train_sample(7 + 1000 * rank, count, learned.PSF_SIZE)
     img, sig = learned.render(p_true, psf, 8 + 1000 * rank)
     img, sig, psf = img.reshape(-1), sig.reshape(-1), psf.reshape(-1)
@@ -636,7 +640,8 @@ def run_learned(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded; stamps drawn and rendered on the device)",
-            "config": {"workload": "learned65536", "stamps": count, "side": 64,
+            "config": {"workload": "learned65536" if count == 65536 else f"learned{count}",
+                       "stamps": count, "side": 64, "train_stamps": train_steps * train_batch,
                        "psf": learned.PSF_SIZE, "free_params": 8, "lm_tol": BENCH_TOL,
                        "start": "CNN (bf16) with default-guess fallback by chi2",
                        "l2": "inputs (2.4 GB) larger than L2", "parallelism": f"replicas{ws_}"},

@@ -24,8 +24,43 @@ namespace {
 
 constexpr int TY = CONV_TY;
 
+// One tap row v: acc += sum_u k[v][u] E[r0 + v + r][c0 + o + u].  With the tap
+// count P4K known at compile time (PSFs up to 33 pixels) the loop over tap
+// groups unrolls completely and the sliding 8-value window costs no register
+// moves; otherwise (P4K = 0) it runs over the runtime P4.
+template <int P4K>
+__device__ __forceinline__ void tap_row(float (&acc)[4][4], const float* kr, const float* er, int SW,
+                                        int P4)
+{
+    float4 w0[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) w0[r] = *reinterpret_cast<const float4*>(er + r * SW);
+    constexpr int PU = P4K > 0 ? P4K : 4;
+    const int pend = P4K > 0 ? P4K : P4;
+#pragma unroll(P4K > 0 ? P4K / 4 : 2)
+    for (int m = 0; m < pend; m += 4) {
+        const float4 kk = *reinterpret_cast<const float4*>(kr + m);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float4 w1 = *reinterpret_cast<const float4*>(er + r * SW + m + 4);
+            const float win[8] = {w0[r].x, w0[r].y, w0[r].z, w0[r].w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                float x = acc[r][o];
+                x = fmaf(kk.x, win[o], x);
+                x = fmaf(kk.y, win[o + 1], x);
+                x = fmaf(kk.z, win[o + 2], x);
+                x = fmaf(kk.w, win[o + 3], x);
+                acc[r][o] = x;
+            }
+            w0[r] = w1;
+        }
+    }
+    (void)PU;
+}
+
 // Work item = (channel, output tile of a listed stamp of this tile width).
-template <int TX>
+template <int TX, int P4K>
 __global__ void __launch_bounds__(TX * 2) k_conv_direct(PassArgs a)
 {
     constexpr int NT = TX * 2, WX = TX / 32;  // threads, warps across
@@ -77,33 +112,8 @@ __global__ void __launch_bounds__(TX * 2) k_conv_direct(PassArgs a)
 #pragma unroll
             for (int o = 0; o < 4; ++o) acc[r][o] = 0.0f;
 
-        for (int v = 0; v < P; ++v) {
-            const float* kr = ks + v * P4;
-            const float* er = es + (r0 + v) * SW + c0;
-            float4 w0[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) w0[r] = *reinterpret_cast<const float4*>(er + r * SW);
-#pragma unroll 2
-            for (int m = 0; m < P4; m += 4) {
-                const float4 kk = *reinterpret_cast<const float4*>(kr + m);
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const float4 w1 = *reinterpret_cast<const float4*>(er + r * SW + m + 4);
-                    const float win[8] = {w0[r].x, w0[r].y, w0[r].z, w0[r].w,
-                                          w1.x,    w1.y,    w1.z,    w1.w};
-#pragma unroll
-                    for (int o = 0; o < 4; ++o) {
-                        float x = acc[r][o];
-                        x = fmaf(kk.x, win[o], x);
-                        x = fmaf(kk.y, win[o + 1], x);
-                        x = fmaf(kk.z, win[o + 2], x);
-                        x = fmaf(kk.w, win[o + 3], x);
-                        acc[r][o] = x;
-                    }
-                    w0[r] = w1;
-                }
-            }
-        }
+        for (int v = 0; v < P; ++v)
+            tap_row<P4K>(acc, ks + v * P4, es + (r0 + v) * SW + c0, SW, P4);
 
         if (a.work && (lane | (warp / WX)) == 0) {  // lane 0 of the first warp of each column
             const unsigned long long rows = (unsigned long long)min(TY, st.H - ty0);
@@ -137,13 +147,30 @@ size_t conv_smem(int P)
 
 size_t conv_direct_smem(int P) { return conv_smem<64>(P); }
 
+template <int TX, int P4K>
+cudaError_t launch_p4(const PassArgs& a, int kind, cudaStream_t s)
+{
+    k_conv_direct<TX, P4K><<<a.grid[kind], TX * 2, conv_smem<TX>(a.P), s>>>(a);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
 template <int TX>
 cudaError_t launch_tile(const PassArgs& a, int kind, cudaStream_t s)
 {
     if (a.maxitems[kind] <= 0) return cudaSuccess;
-    k_conv_direct<TX><<<a.grid[kind], TX * 2, conv_smem<TX>(a.P), s>>>(a);
-    GF_COUNT_LAUNCH();
-    return cudaGetLastError();
+    switch ((a.P + 3) & ~3) {
+    case 4: return launch_p4<TX, 4>(a, kind, s);
+    case 8: return launch_p4<TX, 8>(a, kind, s);
+    case 12: return launch_p4<TX, 12>(a, kind, s);
+    case 16: return launch_p4<TX, 16>(a, kind, s);
+    case 20: return launch_p4<TX, 20>(a, kind, s);
+    case 24: return launch_p4<TX, 24>(a, kind, s);
+    case 28: return launch_p4<TX, 28>(a, kind, s);
+    case 32: return launch_p4<TX, 32>(a, kind, s);
+    case 36: return launch_p4<TX, 36>(a, kind, s);
+    default: return launch_p4<TX, 0>(a, kind, s);
+    }
 }
 
 cudaError_t launch_conv_direct(const PassArgs& a, cudaStream_t s)
@@ -166,10 +193,13 @@ cudaError_t launch_conv_direct_width(const PassArgs& a, int tile_w, cudaStream_t
 // stream capture leaves nothing to set inside it
 static int g_conv_optin64[64], g_conv_optin32[64];
 
+// (the specialised kernels serve PSFs up to 33 pixels, whose tiles stay below the
+// default 48 KB of shared memory; only the generic ones need the opt-in)
 cudaError_t ensure_smem_optin_conv_direct(int P, int*)
 {
-    cudaError_t e = ensure_smem_optin((const void*)k_conv_direct<64>, (int)conv_smem<64>(P),
+    cudaError_t e = ensure_smem_optin((const void*)k_conv_direct<64, 0>, (int)conv_smem<64>(P),
                                       g_conv_optin64);
     if (e != cudaSuccess) return e;
-    return ensure_smem_optin((const void*)k_conv_direct<32>, (int)conv_smem<32>(P), g_conv_optin32);
+    return ensure_smem_optin((const void*)k_conv_direct<32, 0>, (int)conv_smem<32>(P),
+                             g_conv_optin32);
 }

@@ -421,12 +421,27 @@ __device__ void lm_check_iters(const Structure& S, LMState& L)
 
 // the call's Structure, copied into shared memory by the whole block (the
 // per-stamp code walks its tables in dependent chains: slot -> role -> value)
+// (8-byte words, four loads in flight per thread before the stores: a 32-thread
+// block copies it in two rounds of L2 latency instead of eighteen)
 __device__ __forceinline__ void load_structure(Structure* dst, const Structure* src)
 {
-    const int* s = reinterpret_cast<const int*>(src);
-    int* d = reinterpret_cast<int*>(dst);
-    for (int i = threadIdx.x; i < (int)(sizeof(Structure) / sizeof(int)); i += blockDim.x)
-        d[i] = s[i];
+    static_assert(sizeof(Structure) % 8 == 0, "Structure must be a multiple of 8 bytes");
+    constexpr int N = (int)(sizeof(Structure) / 8);
+    const uint2* s = reinterpret_cast<const uint2*>(src);
+    uint2* d = reinterpret_cast<uint2*>(dst);
+    for (int i0 = threadIdx.x; i0 < N; i0 += 4 * blockDim.x) {
+        uint2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < N) v[u] = __ldcg(s + i);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < N) d[i] = v[u];
+        }
+    }
 }
 
 #define WARP_STAMP()                                                          \
@@ -491,11 +506,13 @@ __global__ void __launch_bounds__(32) k_final_solve(PassArgs a, Channel* trial_c
 {
     __shared__ Structure S_sh;
     __shared__ WarpScratch W;
-    load_structure(&S_sh, a.S);
+    __shared__ double As[GF_MAX_FREE * GF_MAX_FREE], gs[GF_MAX_FREE];
     const int b = blockIdx.x;
     if (b == 0 && threadIdx.x == 0 && active) *active = 0;
     LMState& L = a.lm[b];
     int phase = L.phase;
+    if (phase != PH_NEED_JAC && phase != PH_SOLVE) return;  // the whole (one-warp) block
+    load_structure(&S_sh, a.S);
     __syncwarp();
     const Structure& S = S_sh;
     const int nf = S.nfree;
@@ -503,10 +520,27 @@ __global__ void __launch_bounds__(32) k_final_solve(PassArgs a, Channel* trial_c
         phase = PH_SOLVE;
         if (threadIdx.x == 0) L.phase = PH_SOLVE;
     }
-    if (phase != PH_SOLVE || threadIdx.x >= 32) return;
+    // A and g into shared memory in one round of loads
+    {
+        double v[8];
+        const int nA = nf * nf;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = threadIdx.x + 32 * u;
+            v[u] = i < nA ? __ldcg(&L.A[i]) : 0.0;
+        }
+        const double gv = threadIdx.x < nf ? __ldcg(&L.g[threadIdx.x]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = threadIdx.x + 32 * u;
+            if (i < nA) As[i] = v[u];
+        }
+        if (threadIdx.x < nf) gs[threadIdx.x] = gv;
+        __syncwarp();
+    }
     const int lane = threadIdx.x;
     bool fin = true;
-    for (int i = lane; i < nf; i += 32) fin = fin && isfinite(L.g[i]) && isfinite(L.A[i * nf + i]);
+    for (int i = lane; i < nf; i += 32) fin = fin && isfinite(gs[i]) && isfinite(As[i * nf + i]);
     const bool finite = __all_sync(kFull, fin) && isfinite(L.chi2);
     if (!finite) {
         __syncwarp();
@@ -520,17 +554,17 @@ __global__ void __launch_bounds__(32) k_final_solve(PassArgs a, Channel* trial_c
     const double lam = L.lambda;
     if (lane < nf) {  // lane i builds row i
         const int i = lane;
-        const double aii = L.A[i * nf + i];
+        const double aii = As[i * nf + i];
         for (int j = 0; j < nf; ++j) {
-            const double ajj = L.A[j * nf + j];
-            double v = L.A[i * nf + j];
+            const double ajj = As[j * nf + j];
+            double v = As[i * nf + j];
             if (!(aii > 0.0) || !(ajj > 0.0))
                 v = (i == j) ? 1.0 : 0.0;
             else if (i == j)
                 v = aii * (1.0 + lam);
             W.M[i * nf + j] = v;
         }
-        W.r[i] = aii > 0.0 ? L.g[i] : 0.0;
+        W.r[i] = aii > 0.0 ? gs[i] : 0.0;
     }
     const bool ok = warp_cholesky_solve(nf, W);
     const int iters = L.iters + 1;
@@ -549,8 +583,8 @@ __global__ void __launch_bounds__(32) k_final_solve(PassArgs a, Channel* trial_c
     for (int i = lane; i < nf; i += 32) {
         const int s = S.freeslot[i];
         step = fmax(step, fabs(W.r[i]) / fmax(fabs(L.p[s]), xtol_scale(S.role[s])));
-        const double aii = L.A[i * nf + i];
-        if (aii > 0.0) pred += W.r[i] * (L.g[i] + lam * aii * W.r[i]);
+        const double aii = As[i * nf + i];
+        if (aii > 0.0) pred += W.r[i] * (gs[i] + lam * aii * W.r[i]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
