@@ -297,11 +297,18 @@ def lm_fit(desc: Desc, params, fixed, psf, img, sigma, method=0, opts: Opts | No
 
 def lm_fit_batch(descs, params, fixed, psf_flat, psf_off, img_flat, sigma_flat, pix_off,
                  method=0, opts: Opts | None = None):
-    """Independent fits, OpenMP across stamps.  params: [nb, nslots] (copied)."""
+    """Independent fits, OpenMP across stamps.  params: [nb, nslots] (copied).
+    fixed: None, one mask of nslots bytes shared by every stamp, or [nb, nslots]."""
     nb = len(descs)
     arr = (Desc * nb)(*descs)
     p = np.array(params, np.float64, copy=True)
     ns = p.shape[1]
+    if fixed is not None:
+        fixed = np.asarray(fixed, np.uint8).reshape(-1)
+        if fixed.size == ns:
+            fixed = np.tile(fixed, nb)
+        if fixed.size != nb * ns:
+            raise ValueError(f"fixed has {fixed.size} bytes; want {ns} or {nb * ns}")
     res = (Result * nb)()
     po = np.ascontiguousarray(psf_off, np.int64)
     xo = np.ascontiguousarray(pix_off, np.int64)

@@ -131,7 +131,8 @@ int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
                const gfo_lm_opts* opts, gfo_lm_result* res);
 
 /* independent stamps, OpenMP across stamps.  Stamp b uses desc ds[b],
- * params + b*nslots, psf + psf_off[b], img/sigma + pix_off[b]. */
+ * params + b*nslots, fixed + b*nslots (NULL = all free), psf + psf_off[b],
+ * img/sigma + pix_off[b]. */
 int gfo_lm_fit_batch(int nb, const gfo_desc* ds, double* params, const uint8_t* fixed,
                      const double* psf, const int64_t* psf_off, const double* img,
                      const double* sigma, const int64_t* pix_off, int method,

@@ -147,3 +147,31 @@ def test_lm_bad_input():
     img = np.zeros((64, 64), np.float32)
     p, res = oracle.lm_fit(d, st.params, fixed, st.psf, img, img + 1)
     assert res["status"] == oracle.BADINPUT
+
+
+def test_lm_batch_equals_single_fits():
+    # the batched oracle fits each stamp on its own: a shared fixed mask (one
+    # row for every stamp) and a per-stamp mask give the single-stamp fits
+    sts = [synth.stamp64(), synth.stamp64()]
+    sts[1].params[6] = 75.0
+    descs, imgs, sigs = [], [], []
+    for st in sts:
+        d = _desc(st)
+        img, sig = synth.add_noise(oracle.render(d, st.params, st.psf), st.noise_seed)
+        descs.append(d); imgs.append(img); sigs.append(sig)
+    fixed = sts[0].fixed.copy()
+    fixed[6] = 1  # hold PA: a mask that differs from the all-free default
+    p0 = np.array([st.guess() for st in sts])
+    singles = [oracle.lm_fit(descs[k], p0[k], fixed, sts[k].psf, imgs[k], sigs[k])
+               for k in range(2)]
+    args = (np.concatenate([st.psf.ravel() for st in sts]), [0, sts[0].psf.size],
+            np.concatenate([i.ravel() for i in imgs]), np.concatenate([s.ravel() for s in sigs]),
+            [0, imgs[0].size])
+    for mask in (fixed, np.tile(fixed, (2, 1))):
+        pb, rb = oracle.lm_fit_batch(descs, p0, mask, *args)
+        for k in range(2):
+            assert np.array_equal(pb[k], singles[k][0])
+            assert rb[k]["chi2"] == singles[k][1]["chi2"]
+            assert pb[k][6] == p0[k][6]
+    with pytest.raises(ValueError):
+        oracle.lm_fit_batch(descs, p0, fixed[:-1], *args)
