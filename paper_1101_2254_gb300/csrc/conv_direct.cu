@@ -63,6 +63,7 @@ __device__ __forceinline__ void tap_row(float (&acc)[4][4], const float* kr, con
 template <int TX, int P4K>
 __global__ void __launch_bounds__(TX * 2) k_conv_direct(PassArgs a)
 {
+    pdl_entry();
     constexpr int NT = TX * 2, WX = TX / 32;  // threads, warps across
     extern __shared__ __align__(16) float smem[];
     const int n = *a.wl.n;
@@ -150,7 +151,7 @@ size_t conv_direct_smem(int P) { return conv_smem<64>(P); }
 template <int TX, int P4K>
 cudaError_t launch_p4(const PassArgs& a, int kind, cudaStream_t s)
 {
-    k_conv_direct<TX, P4K><<<a.grid[kind], TX * 2, conv_smem<TX>(a.P), s>>>(a);
+    GF_LAUNCH_PDL(k_conv_direct<TX, P4K>, dim3(a.grid[kind]), dim3(TX * 2), conv_smem<TX>(a.P), s, a);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }

@@ -64,6 +64,7 @@ __global__ void k_psf_wrap(FFTArgs f, int count, const StampInfo* st, const floa
 // (Kx = Nx/2 + 1 bins per row).  Block x handles rows 2x and 2x + 1.
 __global__ void __launch_bounds__(ROW_THREADS) k_fft_rows_fwd(FFTArgs f, RowIO io, PassArgs a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) float2 sm[];
     const int p = blockIdx.y;
     if (a.lm && a.lm[p / io.nchan].phase != a.phase) return;
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_fft_rows_fwd(FFTArgs f, RowIO i
 // written back in place.
 __global__ void __launch_bounds__(COL_THREADS) k_fft_cols(FFTArgs f, ColIO io, PassArgs a, int mode)
 {
+    pdl_entry();
     extern __shared__ __align__(16) float2 sm[];
     const int p = blockIdx.y;
     const int b = p / io.nchan;
@@ -142,6 +144,7 @@ __global__ void __launch_bounds__(COL_THREADS) k_fft_cols(FFTArgs f, ColIO io, P
 // rows row0 + 2x, row0 + 2x + 1; grid columns [col0, col0 + W) are kept.
 __global__ void __launch_bounds__(ROW_THREADS) k_fft_rows_inv(FFTArgs f, RowInvIO io, PassArgs a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) float2 sm[];
     const int p = blockIdx.y;
     if (a.lm && a.lm[p / io.nchan].phase != a.phase) return;
@@ -234,7 +237,7 @@ cudaError_t launch_fft_psf(const FFTArgs& f, int count, const StampInfo* st, con
     r.spec_stride = (long long)f.Ny * Kx;
     r.out_rows = f.Ny;
     r.nchan = 1;
-    k_fft_rows_fwd<<<dim3((f.Ny + 1) / 2, count), ROW_THREADS, fft_row_smem(f.Nx), s>>>(f, r, none);
+    GF_LAUNCH_PDL(k_fft_rows_fwd, dim3(dim3((f.Ny + 1) / 2, count)), dim3(ROW_THREADS), fft_row_smem(f.Nx), s, f, r, none);
     GF_COUNT_LAUNCH();
     ColIO c;
     c.spec = f.hhat;
@@ -243,8 +246,7 @@ cudaError_t launch_fft_psf(const FFTArgs& f, int count, const StampInfo* st, con
     c.row0 = 0;
     c.nrows_out = f.Ny;
     c.nchan = 1;
-    k_fft_cols<<<dim3((Kx + f.cpc - 1) / f.cpc, count), COL_THREADS, fft_col_smem(f.Ny, f.cpc), s>>>(
-        f, c, none, 0);
+    GF_LAUNCH_PDL(k_fft_cols, dim3(dim3((Kx + f.cpc - 1) / f.cpc, count)), dim3(COL_THREADS), fft_col_smem(f.Ny, f.cpc), s, f, c, none, 0);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -268,7 +270,7 @@ cudaError_t launch_conv_fft(const PassArgs& a, const FFTArgs& f, float2* spec, c
     r.spec_stride = (long long)s0.He * Kx;
     r.out_rows = s0.He;
     r.nchan = a.nchan;
-    k_fft_rows_fwd<<<dim3((s0.He + 1) / 2, nprob), ROW_THREADS, fft_row_smem(f.Nx), s>>>(f, r, a);
+    GF_LAUNCH_PDL(k_fft_rows_fwd, dim3(dim3((s0.He + 1) / 2, nprob)), dim3(ROW_THREADS), fft_row_smem(f.Nx), s, f, r, a);
     GF_COUNT_LAUNCH();
     ColIO c;
     c.spec = spec;
@@ -282,8 +284,7 @@ cudaError_t launch_conv_fft(const PassArgs& a, const FFTArgs& f, float2* spec, c
     FFTArgs fc = f;
     while (fc.cpc > 2 && (long long)nprob * ((Kx + fc.cpc - 1) / fc.cpc) < 2 * 152) fc.cpc /= 2;
     fc.flops_col = f.flops_col * (float)fc.cpc / (float)f.cpc;
-    k_fft_cols<<<dim3((Kx + fc.cpc - 1) / fc.cpc, nprob), COL_THREADS, fft_col_smem(fc.Ny, fc.cpc),
-                 s>>>(fc, c, a, 1);
+    GF_LAUNCH_PDL(k_fft_cols, dim3(dim3((Kx + fc.cpc - 1) / fc.cpc, nprob)), dim3(COL_THREADS), fft_col_smem(fc.Ny, fc.cpc), s, fc, c, a, 1);
     GF_COUNT_LAUNCH();
     RowInvIO v;
     v.spec = spec;
@@ -295,7 +296,7 @@ cudaError_t launch_conv_fft(const PassArgs& a, const FFTArgs& f, float2* spec, c
     v.out = a.y;
     v.out_stride = (long long)s0.H * s0.W;
     v.nchan = a.nchan;
-    k_fft_rows_inv<<<dim3((s0.H + 1) / 2, nprob), ROW_THREADS, fft_row_smem(f.Nx), s>>>(f, v, a);
+    GF_LAUNCH_PDL(k_fft_rows_inv, dim3(dim3((s0.H + 1) / 2, nprob)), dim3(ROW_THREADS), fft_row_smem(f.Nx), s, f, v, a);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }

@@ -289,6 +289,44 @@ enum { PROF_MODEL = 0, PROF_CONV = 1, PROF_REDUCE = 2, PROF_LM = 3, PROF_CLASSES
 cudaError_t ensure_smem_optin(const void* func, int bytes, int* cache_per_device);
 cudaError_t ensure_smem_optin_conv_direct(int P, int* cache_per_device);
 
+// ------------------------------------------------ programmatic dependent launch
+// The kernels of a pass are launched with programmatic stream serialization:
+// a kernel's CTAs may be scheduled while the previous kernel of the stream is
+// still finishing, which hides the launch latency between the short kernels of
+// an LM body.  Every such kernel starts with pdl_entry(): it waits until the
+// previous grid has completed and its memory is visible (so nothing is read or
+// overwritten early), then lets the next kernel begin its own launch.  Kernels
+// launched without the attribute pass through pdl_entry() at once.
+__device__ __forceinline__ void pdl_entry()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Params>(args)...);
+}
+
+// launch through launch_pdl, returning the launch error from the caller
+#define GF_LAUNCH_PDL(...)                                   \
+    do {                                                     \
+        const cudaError_t e_pdl_ = launch_pdl(__VA_ARGS__);  \
+        if (e_pdl_ != cudaSuccess) return e_pdl_;            \
+    } while (0)
+
 // every kernel launch of the library increments this counter
 extern std::atomic<long long> g_launch_count;
 #define GF_COUNT_LAUNCH() g_launch_count.fetch_add(1, std::memory_order_relaxed)

@@ -165,18 +165,26 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
         pa = q[5];
         c = q[6];
     }
+    // The pixel path takes float32 constants, so they are formed in float32
+    // (FP64 transcendentals and divisions are long chains on GB300): the angle
+    // is split th = th_h + th_l with th_h a float, and
+    // cos th = cos th_h - th_l sin th_h, sin th = sin th_h + th_l cos th_h to
+    // first order (|th_l| < 2^-24 |th|: the next term is below 1e-15).
     const double th = pa * (kPi / 180.0);
-    k.cs = (float)cos(th);
-    k.sn = (float)sin(th);
-    k.invq = (float)(1.0 / ax);
+    const float th_h = (float)th, th_l = (float)(th - (double)th_h);
+    float sh, ch;
+    sincosf(th_h, &sh, &ch);
+    k.cs = fmaf(-th_l, sh, ch);
+    k.sn = fmaf(th_l, ch, sh);
+    k.invq = 1.0f / (float)ax;
     k.C = (float)(c + 2.0);
-    k.invC = (float)(1.0 / (c + 2.0));
+    k.invC = 1.0f / k.C;
     k.ellipse = (c == 0.0);
     k.amp = (float)amp;
-    k.invr = (float)(1.0 / r);
+    k.invr = 1.0f / (float)r;
     if (kind == GF_SERSIC) {
         const double n = q[4];
-        k.invn = (float)(1.0 / n);
+        k.invn = 1.0f / (float)n;
         k.b0 = (float)bn;
         k.b = (float)bn;
     }
@@ -349,6 +357,27 @@ __device__ void warp_build_jac(const Structure& S, WarpScratch& W, float psum, C
     }
 }
 
+// sqrt(x) and 1/sqrt(x) of a positive finite x.  A float32 seed refined by two
+// Newton-Raphson steps for the reciprocal square root, y <- y (3 - x y^2) / 2
+// (each step squares the relative error: ~1e-7 -> ~1e-14 -> rounding level),
+// then sqrt(x) = x y: about ten dependent FP64 operations instead of a square
+// root and a division, which GB300's few FP64 units run as long chains.  Values
+// outside the float32 exponent range take the library square root.
+__device__ __forceinline__ void sqrt_and_rsqrt(double x, double& sq, double& rs)
+{
+    if (x > 1e-30 && x < 1e30) {
+        const double h = 0.5 * x;
+        double y = (double)rsqrtf((float)x);
+        y = y * fma(-h, y * y, 1.5);
+        y = y * fma(-h, y * y, 1.5);
+        rs = y;
+        sq = x * y;
+    } else {
+        sq = sqrt(x);
+        rs = 1.0 / sq;
+    }
+}
+
 // Warp Cholesky factorisation M = L L^T of the SPD n x n matrix W.M (n <= 16;
 // lower factor in place) and the solve M x = W.r (x in W.r).  Lane i owns row
 // i: each column step scales the entries below the pivot by 1/sqrt(pivot) and
@@ -366,8 +395,8 @@ __device__ bool warp_cholesky_solve(int n, WarpScratch& W)
         __syncwarp();
         const double piv = __shfl_sync(kFull, lane == j ? mine[j] : 0.0, j);
         if (!(piv > 0.0) || !isfinite(piv)) return false;
-        const double d = sqrt(piv);
-        const double invd = 1.0 / d;
+        double d, invd;
+        sqrt_and_rsqrt(piv, d, invd);
         if (lane == j) {
             mine[j] = d;
             invd_mine = invd;
@@ -458,6 +487,7 @@ __device__ __forceinline__ void load_structure(Structure* dst, const Structure* 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prep_sum(PassArgs a, const double* params,
                                                                   int use_trial)
 {
+    pdl_entry();
     WARP_STAMP();
     if (a.lm && a.lm[b].phase != a.phase) return;
     const double* p = params ? params + (long long)b * S.nslots
@@ -470,6 +500,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prep_sum(PassArgs a, co
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prep_jac(PassArgs a, const double* params)
 {
+    pdl_entry();
     WARP_STAMP();
     if (a.lm && a.lm[b].phase != a.phase) return;
     const double* p = params ? params + (long long)b * S.nslots : a.lm[b].p;
@@ -504,6 +535,7 @@ __global__ void k_lm_init(int count, const Structure* Sp, LMState* lm, const dou
 // active-stamp counter that k_final_update fills.
 __global__ void __launch_bounds__(32) k_final_solve(PassArgs a, Channel* trial_chan, int* active)
 {
+    pdl_entry();
     __shared__ Structure S_sh;
     __shared__ WarpScratch W;
     __shared__ double As[GF_MAX_FREE * GF_MAX_FREE], gs[GF_MAX_FREE];
@@ -552,19 +584,21 @@ __global__ void __launch_bounds__(32) k_final_solve(PassArgs a, Channel* trial_c
     }
     // damped system (A + lambda diag A) delta = g; a slot with A_ii = 0 is held
     const double lam = L.lambda;
+    // bit i: A_ii > 0 (one FP64 comparison per lane instead of one per entry)
+    const unsigned pos = __ballot_sync(kFull, lane < nf && As[lane * nf + lane] > 0.0);
     if (lane < nf) {  // lane i builds row i
         const int i = lane;
         const double aii = As[i * nf + i];
+        const bool pi = (pos >> i) & 1u;
         for (int j = 0; j < nf; ++j) {
-            const double ajj = As[j * nf + j];
             double v = As[i * nf + j];
-            if (!(aii > 0.0) || !(ajj > 0.0))
+            if (!pi || !((pos >> j) & 1u))
                 v = (i == j) ? 1.0 : 0.0;
             else if (i == j)
                 v = aii * (1.0 + lam);
             W.M[i * nf + j] = v;
         }
-        W.r[i] = aii > 0.0 ? gs[i] : 0.0;
+        W.r[i] = pi ? gs[i] : 0.0;
     }
     const bool ok = warp_cholesky_solve(nf, W);
     const int iters = L.iters + 1;
@@ -579,19 +613,18 @@ __global__ void __launch_bounds__(32) k_final_solve(PassArgs a, Channel* trial_c
     }
     // scaled step and predicted fall of chi^2 for the damped step,
     // delta^T (g + lambda diag(A) delta), as warp reductions
-    double step = 0.0, pred = 0.0;
+    // (the scaled-step test max_i |delta_i| / s_i < xtol is taken as
+    // |delta_i| < xtol s_i for every i: no FP64 division per lane)
+    bool small = true;
+    double pred = 0.0;
     for (int i = lane; i < nf; i += 32) {
         const int s = S.freeslot[i];
-        step = fmax(step, fabs(W.r[i]) / fmax(fabs(L.p[s]), xtol_scale(S.role[s])));
-        const double aii = As[i * nf + i];
-        if (aii > 0.0) pred += W.r[i] * (gs[i] + lam * aii * W.r[i]);
+        small = small && fabs(W.r[i]) < S.opts.xtol * fmax(fabs(L.p[s]), xtol_scale(S.role[s]));
+        if ((pos >> i) & 1u) pred += W.r[i] * (gs[i] + lam * As[i * nf + i] * W.r[i]);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        step = fmax(step, __shfl_xor_sync(kFull, step, o));
-        pred += __shfl_xor_sync(kFull, pred, o);
-    }
-    if (step < S.opts.xtol) {
+    for (int o = 16; o > 0; o >>= 1) pred += __shfl_xor_sync(kFull, pred, o);
+    if (__all_sync(kFull, small)) {
         if (lane == 0) {
             L.status = GF_OK;
             L.phase = PH_DONE;
@@ -621,6 +654,7 @@ __global__ void __launch_bounds__(32) k_final_solve(PassArgs a, Channel* trial_c
 // stamp not yet done adds one to the active counter.
 __global__ void __launch_bounds__(RED_THREADS) k_final_update(PassArgs a, int* active)
 {
+    pdl_entry();
     __shared__ CSum wsum[RED_THREADS / 32];
     const int b = blockIdx.x;
     LMState& L = a.lm[b];
@@ -693,6 +727,7 @@ __global__ void __launch_bounds__(WL_THREADS) k_worklist(int count, const LMStat
                                                          const int* pst, int* n_out, int* ids,
                                                          int* pre)
 {
+    pdl_entry();
     __shared__ int wsum[WL_THREADS / 32][1 + WK_KINDS];
     const int per = (count + WL_THREADS - 1) / WL_THREADS;
     const int b0 = min(count, (int)threadIdx.x * per), b1 = min(count, b0 + per);
@@ -758,14 +793,14 @@ inline int warp_blocks(int count) { return (count + kWarpsPerBlock - 1) / kWarps
 cudaError_t launch_prep_sum(const PassArgs& a, const double* params, int use_trial,
                             cudaStream_t s)
 {
-    k_prep_sum<<<warp_blocks(a.count), kWarpsPerBlock * 32, 0, s>>>(a, params, use_trial);
+    GF_LAUNCH_PDL(k_prep_sum, dim3(warp_blocks(a.count)), dim3(kWarpsPerBlock * 32), 0, s, a, params, use_trial);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
 cudaError_t launch_prep_jac(const PassArgs& a, const double* params, cudaStream_t s)
 {
-    k_prep_jac<<<warp_blocks(a.count), kWarpsPerBlock * 32, 0, s>>>(a, params);
+    GF_LAUNCH_PDL(k_prep_jac, dim3(warp_blocks(a.count)), dim3(kWarpsPerBlock * 32), 0, s, a, params);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -781,14 +816,14 @@ cudaError_t launch_lm_init(int count, const Structure* S, LMState* lm, const dou
 cudaError_t launch_final_solve(const PassArgs& a, Channel* trial_chan, int* active,
                                cudaStream_t s)
 {
-    k_final_solve<<<a.count, 32, 0, s>>>(a, trial_chan, active);
+    GF_LAUNCH_PDL(k_final_solve, dim3(a.count), dim3(32), 0, s, a, trial_chan, active);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
 cudaError_t launch_final_update(const PassArgs& a, int* active_count, cudaStream_t s)
 {
-    k_final_update<<<a.count, RED_THREADS, 0, s>>>(a, active_count);
+    GF_LAUNCH_PDL(k_final_update, dim3(a.count), dim3(RED_THREADS), 0, s, a, active_count);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -804,7 +839,7 @@ cudaError_t launch_lm_export(int count, const Structure* S, const LMState* lm, d
 cudaError_t launch_worklist(int count, const LMState* lm, int phase, const int* pre_static,
                             int* n, int* ids, int* pre, cudaStream_t s)
 {
-    k_worklist<<<1, WL_THREADS, 0, s>>>(count, lm, phase, pre_static, n, ids, pre);
+    GF_LAUNCH_PDL(k_worklist, dim3(1), dim3(WL_THREADS), 0, s, count, lm, phase, pre_static, n, ids, pre);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }

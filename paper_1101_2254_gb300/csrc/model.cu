@@ -28,9 +28,33 @@ __device__ __forceinline__ void load_channel(Channel* dst, const Channel* src)
     for (int i = threadIdx.x; i < (int)(sizeof(Channel) / 16); i += blockDim.x) d[i] = s[i];
 }
 
+// channels [0, nch) of a stamp (contiguous) into shared memory: four 16-byte
+// loads per thread in flight before their stores, so the copy takes a couple of
+// L2 round trips instead of one per channel
+__device__ __forceinline__ void load_channels(Channel* dst, const Channel* src, int nch)
+{
+    const int n = nch * (int)(sizeof(Channel) / 16);
+    const int4* s = reinterpret_cast<const int4*>(src);
+    int4* d = reinterpret_cast<int4*>(dst);
+    for (int i0 = threadIdx.x; i0 < n; i0 += 4 * blockDim.x) {
+        int4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < n) v[u] = s[i];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < n) d[i] = v[u];
+        }
+    }
+}
+
 // Work item = (channel, block of MODEL_THREADS grid pixels of a listed stamp).
 __global__ void __launch_bounds__(MODEL_THREADS) k_model(PassArgs a)
 {
+    pdl_entry();
     __shared__ __align__(16) Channel ch;
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_MODEL * (a.count + 1);
@@ -75,6 +99,7 @@ __global__ void __launch_bounds__(MODEL_THREADS) k_model(PassArgs a)
 // Work item = (channel, OS_WARPS pixels of a listed stamp's oversampling block).
 __global__ void __launch_bounds__(OS_WARPS * 32) k_model_os(PassArgs a)
 {
+    pdl_entry();
     __shared__ __align__(16) Channel ch;
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_OS * (a.count + 1);
@@ -143,6 +168,7 @@ __device__ __forceinline__ void comp_base(const Channel& c0, float* base, float 
 // Work item = block of MODEL_THREADS grid pixels of a listed stamp (all channels).
 __global__ void __launch_bounds__(MODEL_THREADS) k_model_jac(PassArgs a)
 {
+    pdl_entry();
     __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_MODEL * (a.count + 1);
@@ -157,7 +183,7 @@ __global__ void __launch_bounds__(MODEL_THREADS) k_model_jac(PassArgs a)
         const StampInfo st = a.st[b];
         if (b != cur_b) {
             __syncthreads();
-            for (int c = 0; c < nch; ++c) load_channel(&chs[c], &a.chan[(long long)b * a.chan_stride + c]);
+            load_channels(chs, &a.chan[(long long)b * a.chan_stride], nch);
             __syncthreads();
             cur_b = b;
         }
@@ -192,6 +218,7 @@ __global__ void __launch_bounds__(MODEL_THREADS) k_model_jac(PassArgs a)
 // channels); lanes take sub-samples, each lane keeps every channel's sum.
 __global__ void __launch_bounds__(OS_WARPS * 32) k_model_os_jac(PassArgs a)
 {
+    pdl_entry();
     __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_OS * (a.count + 1);
@@ -207,7 +234,7 @@ __global__ void __launch_bounds__(OS_WARPS * 32) k_model_os_jac(PassArgs a)
         const StampInfo st = a.st[b];
         if (b != cur_b) {
             __syncthreads();
-            for (int c = 0; c < nch; ++c) load_channel(&chs[c], &a.chan[(long long)b * a.chan_stride + c]);
+            load_channels(chs, &a.chan[(long long)b * a.chan_stride], nch);
             __syncthreads();
             cur_b = b;
         }
@@ -253,7 +280,7 @@ cudaError_t launch_model(const PassArgs& a, cudaStream_t s)
         const int cap[2] = {152 * 16, 152 * 8};
         if (a.maxitems[WK_MODEL] > 0) {
             const int g = (int)std::min<long long>(a.maxitems[WK_MODEL] / a.nchan, cap[0]);
-            k_model_jac<<<std::max(g, 1), MODEL_THREADS, 0, s>>>(a);
+            GF_LAUNCH_PDL(k_model_jac, dim3(std::max(g, 1)), dim3(MODEL_THREADS), 0, s, a);
             GF_COUNT_LAUNCH();
         }
         // the oversampled blocks: all channels per warp when there are enough
@@ -262,20 +289,20 @@ cudaError_t launch_model(const PassArgs& a, cudaStream_t s)
         const long long os_groups = a.maxitems[WK_OS] / a.nchan;
         if (os_groups * OS_WARPS >= 152LL * 32) {
             const int g = (int)std::min<long long>(os_groups, cap[1]);
-            k_model_os_jac<<<std::max(g, 1), OS_WARPS * 32, 0, s>>>(a);
+            GF_LAUNCH_PDL(k_model_os_jac, dim3(std::max(g, 1)), dim3(OS_WARPS * 32), 0, s, a);
             GF_COUNT_LAUNCH();
         } else if (a.maxitems[WK_OS] > 0) {
-            k_model_os<<<a.grid[WK_OS], OS_WARPS * 32, 0, s>>>(a);
+            GF_LAUNCH_PDL(k_model_os, dim3(a.grid[WK_OS]), dim3(OS_WARPS * 32), 0, s, a);
             GF_COUNT_LAUNCH();
         }
         return cudaGetLastError();
     }
     if (a.maxitems[WK_MODEL] > 0) {
-        k_model<<<a.grid[WK_MODEL], MODEL_THREADS, 0, s>>>(a);
+        GF_LAUNCH_PDL(k_model, dim3(a.grid[WK_MODEL]), dim3(MODEL_THREADS), 0, s, a);
         GF_COUNT_LAUNCH();
     }
     if (a.maxitems[WK_OS] > 0) {
-        k_model_os<<<a.grid[WK_OS], OS_WARPS * 32, 0, s>>>(a);
+        GF_LAUNCH_PDL(k_model_os, dim3(a.grid[WK_OS]), dim3(OS_WARPS * 32), 0, s, a);
         GF_COUNT_LAUNCH();
     }
     return cudaGetLastError();

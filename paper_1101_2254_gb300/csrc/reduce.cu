@@ -46,6 +46,7 @@ constexpr int NGRP = 16;              // pixel groups per chunk (16 pixels each)
 
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
 {
+    pdl_entry();
     __shared__ float V[RED_THREADS][VSTR];  // pixel vectors v = (J, r)
     __shared__ float Wt[RED_THREADS];       // weights 1/sigma^2
     __shared__ ChanInfo ci;
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
 
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_chi2(PassArgs a)
 {
+    pdl_entry();
     __shared__ ChanInfo ci;
     __shared__ float msky;
     __shared__ CSum wsum[RED_THREADS / 32];
@@ -209,16 +211,35 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_chi2(PassArgs a)
     const float* Y = a.y + y_index(st, a.nchan, 0);
     CSum acc = {0.0f, 0.0f};
     const long long base = (long long)local * RED_PIX;
+    // every load of the item is issued before the first use (3 x RED_CHUNKS
+    // independent loads per thread in flight), then the pixels are summed in
+    // chunk order as before
+    float m[RED_CHUNKS], dv[RED_CHUNKS], sv[RED_CHUNKS];
+    const bool has_img = a.img != nullptr;
+#pragma unroll
+    for (int q = 0; q < RED_CHUNKS; ++q) {
+        const long long px = base + (long long)q * RED_THREADS + threadIdx.x;
+        const bool in = px < HW;
+        m[q] = in ? __ldg(&Y[px]) : 0.0f;
+        dv[q] = (in && has_img) ? __ldg(&img[px]) : 0.0f;
+        sv[q] = (in && has_img) ? __ldg(&sig[px]) : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < RED_CHUNKS; ++q) {
+        const long long px = base + (long long)q * RED_THREADS + threadIdx.x;
+        m[q] = fmaf(ci.mw[0], m[q], msky);
+        for (int k = 1; k < a.nchan; ++k)
+            if (px < HW) m[q] = fmaf(ci.mw[k], Y[(long long)k * HW + px], m[q]);
+    }
+#pragma unroll
     for (int q = 0; q < RED_CHUNKS; ++q) {
         const long long px = base + (long long)q * RED_THREADS + threadIdx.x;
         if (px >= HW) break;
-        float m = msky;
-        for (int k = 0; k < a.nchan; ++k) m = fmaf(ci.mw[k], Y[(long long)k * HW + px], m);
-        if (a.m_out) a.m_out[st.pix_off + px] = m;
-        if (!a.img) continue;  // model only
-        const float d = img[px], s = sig[px];
+        if (a.m_out) a.m_out[st.pix_off + px] = m[q];
+        if (!has_img) continue;  // model only
+        const float d = dv[q], s = sv[q];
         if (isfinite(d) && isfinite(s) && s > 0.0f) {
-            const float z = (d - m) / s;
+            const float z = (d - m[q]) / s;
             csum_add(acc, z * z);
         }
     }
@@ -262,6 +283,7 @@ __host__ __device__ __forceinline__ int final_nseg(int nred)
 __global__ void __launch_bounds__(32 * FINAL_SEG_MAX) k_final_jac(PassArgs a, double* A_out,
                                                                   double* g_out, double* chi2_out)
 {
+    pdl_entry();
     __shared__ CSum part[FINAL_SEG_MAX][32];
     const int b = blockIdx.x;
     if (a.lm && a.lm[b].phase != a.phase) return;
@@ -312,6 +334,7 @@ __global__ void __launch_bounds__(32 * FINAL_SEG_MAX) k_final_jac(PassArgs a, do
 
 __global__ void __launch_bounds__(RED_THREADS) k_final_chi2(PassArgs a, double* chi2_out)
 {
+    pdl_entry();
     __shared__ CSum wsum[RED_THREADS / 32];
     const int b = blockIdx.x;
     if (a.lm && a.lm[b].phase != a.phase) return;
@@ -373,7 +396,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_psf_sum(int count, const StampI
 cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s)
 {
     if (a.maxitems[WK_RED] > 0) {
-        k_reduce_jac<<<a.grid[WK_RED], RED_THREADS, 0, s>>>(a);
+        GF_LAUNCH_PDL(k_reduce_jac, dim3(a.grid[WK_RED]), dim3(RED_THREADS), 0, s, a);
         GF_COUNT_LAUNCH();
     }
     return cudaGetLastError();
@@ -382,7 +405,7 @@ cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s)
 cudaError_t launch_reduce_chi2(const PassArgs& a, cudaStream_t s)
 {
     if (a.maxitems[WK_RED] > 0) {
-        k_reduce_chi2<<<a.grid[WK_RED], RED_THREADS, 0, s>>>(a);
+        GF_LAUNCH_PDL(k_reduce_chi2, dim3(a.grid[WK_RED]), dim3(RED_THREADS), 0, s, a);
         GF_COUNT_LAUNCH();
     }
     return cudaGetLastError();
@@ -392,14 +415,14 @@ cudaError_t launch_final_jac(const PassArgs& a, double* A_out, double* g_out, do
                              cudaStream_t s)
 {
     const dim3 grid(a.count, (a.nacc + 31) / 32);
-    k_final_jac<<<grid, 32 * final_nseg(a.max_red), 0, s>>>(a, A_out, g_out, chi2_out);
+    GF_LAUNCH_PDL(k_final_jac, dim3(grid), dim3(32 * final_nseg(a.max_red)), 0, s, a, A_out, g_out, chi2_out);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
 cudaError_t launch_final_chi2(const PassArgs& a, double* chi2_out, cudaStream_t s)
 {
-    k_final_chi2<<<a.count, RED_THREADS, 0, s>>>(a, chi2_out);
+    GF_LAUNCH_PDL(k_final_chi2, dim3(a.count), dim3(RED_THREADS), 0, s, a, chi2_out);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
