@@ -94,6 +94,7 @@ typedef enum {
 #define GF_DIRECT_MAX_PSF 127
 #define GF_AUTO_FFT_PSF 41
 #define GF_MAX_PSF 1023
+#define GF_MAX_LADDER 4
 
 /* Model structure of one stamp (or of every stamp of a batch). */
 typedef struct {
@@ -118,6 +119,11 @@ typedef struct {
     double xtol;         /* converged when max |delta_i| / max(|p_i|, scale_i) < xtol */
     double fd_rel;       /* FD step: fd_rel px for positions, fd_rel*max(|p|,1) otherwise */
     int max_iter;        /* cap on trials (accepted + rejected) */
+    int ladder;          /* trials evaluated together in one pass: the steps for lambda,
+                            lambda*up, ... (1 .. GF_MAX_LADDER; 0 = 2).  The fit takes
+                            exactly the steps of the one-trial-at-a-time rule: the trials
+                            after the first are the ones that rule would try next after
+                            rejections, and only those it reaches are used. */
 } gf_lm_opts;
 
 typedef struct {
@@ -159,10 +165,13 @@ int gf_nslots(const gf_desc* d);
 
 /* Workspace bytes needed by `call` for one stamp of structure d; `fixed_host`
  * (one byte per slot, nonzero = held) matters for GF_CALL_JACOBIAN and
- * GF_CALL_LM_FIT and may be NULL (all free). */
+ * GF_CALL_LM_FIT and may be NULL (all free).  The GF_CALL_LM_FIT size holds for
+ * any gf_lm_opts.ladder (it provides GF_MAX_LADDER trial channels); a smaller
+ * workspace is accepted when it covers the ladder of the call (GF_ENOMEM
+ * otherwise). */
 size_t gf_workspace_size(const gf_desc* d, const uint8_t* fixed_host, int call);
 
-/* Workspace bytes for gf_lm_fit_batch. */
+/* Workspace bytes for gf_lm_fit_batch (for any ladder, as gf_workspace_size). */
 size_t gf_workspace_size_batch(const gf_desc* d, const gf_batch* b, const uint8_t* fixed_host);
 
 /* Step 1 (Sec. 2 item 1; Sec. 3 item 1, a transform): write the model
@@ -222,7 +231,7 @@ gf_status gf_jacobian(const gf_desc* d, const double* params_host, const uint8_t
                       gf_stream stream);
 
 /* Fill opts with the library defaults (lambda0 1e-3, x10 / x0.1, [1e-12, 1e12],
- * ftol 1e-8, xtol 1e-8, fd_rel 1e-3, max_iter 200). */
+ * ftol 1e-8, xtol 1e-8, fd_rel 1e-3, max_iter 200, ladder 2). */
 void gf_default_opts(gf_lm_opts* opts);
 
 /* Steps 1-5: Levenberg-Marquardt fit of one stamp.  params_host (nslots) is

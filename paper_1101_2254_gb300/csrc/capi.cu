@@ -287,6 +287,7 @@ void default_opts(gf_lm_opts* o)
     o->xtol = 1e-8;
     o->fd_rel = 1e-3;
     o->max_iter = 200;
+    o->ladder = 2;
 }
 
 gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* lo,
@@ -356,6 +357,9 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
     else
         default_opts(&S->opts);
     if (!(S->opts.fd_rel > 0.0)) S->opts.fd_rel = 1e-3;
+    if (S->opts.ladder == 0) S->opts.ladder = 2;
+    if (S->opts.ladder < 1 || S->opts.ladder > GF_MAX_LADDER)
+        return fail(GF_EINVAL, "LM ladder must be 1 .. " + std::to_string(GF_MAX_LADDER));
     return GF_OK;
 }
 
@@ -394,6 +398,7 @@ struct Layout {
     size_t tw_x, tw_y, hhat, psfgrid, spec_jac, spec_trial;
     size_t dft_buf[2], dft_mat;  // DFT path: ping-pong complex buffers, bf16 DFT matrices
     int count, nchan, nacc, nslots;
+    int rungs;  // channels of the trial pass: 1, or the LM ladder's rungs
     int tot_model, tot_os, tot_conv, tot_red, tot_conv32;
     int max_red;  // most reduction blocks of one stamp
 };
@@ -479,8 +484,11 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     L.n_static = o;
     o += al(sizeof(int));
     L.blob_end = o;
+    // the trial pass: one channel per stamp, or one per rung of the LM ladder
+    const int R = (need & NEED_LM) ? S.opts.ladder : 1;
+    L.rungs = R;
     L.chan_trial = o;
-    o += al(sizeof(Channel) * (size_t)count);
+    o += al(sizeof(Channel) * (size_t)count * R);
     L.psum = o;
     o += al(sizeof(float) * (size_t)count);
     L.active = o;
@@ -497,13 +505,13 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     }
     if (need & (NEED_TRIAL | NEED_LM)) {
         L.ext_trial = o;
-        o += al(sizeof(float) * (size_t)e1);
+        o += al(sizeof(float) * (size_t)R * e1);
         L.y_trial = o;
-        o += al(sizeof(float) * (size_t)y1);
+        o += al(sizeof(float) * (size_t)R * y1);
     }
     if (need & (NEED_TRIAL | NEED_LM | NEED_CHI2)) {
         L.part_trial = o;
-        o += al(sizeof(float) * (size_t)L.tot_red);
+        o += al(sizeof(float) * (size_t)R * L.tot_red);
     }
     if (need & NEED_LM) {
         L.lm = o;
@@ -538,9 +546,10 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
             L.spec_jac = o;
             o += al(sizeof(float2) * (size_t)count * S.nchan * s0.He * Kx);
         }
-        // the trial pass, gf_eval and gf_convolve use one channel per stamp
+        // gf_eval and gf_convolve use one channel per stamp, the LM trial pass
+        // one per rung
         L.spec_trial = o;
-        o += al(sizeof(float2) * (size_t)count * s0.He * Kx);
+        o += al(sizeof(float2) * (size_t)count * R * s0.He * Kx);
     }
     if (pl->method == GF_CONV_DFT_TC) {
         const StampInfo& s0 = pl->st[0];
@@ -549,7 +558,7 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         pl->Nx = pl->fx.N;
         pl->Ny = pl->fy.N;
         const size_t nn = (size_t)pl->Ny * pl->Nx;
-        const int nch = (need & (NEED_JAC | NEED_LM)) ? S.nchan : 1;
+        const int nch = (need & (NEED_JAC | NEED_LM)) ? std::max(S.nchan, R) : 1;
         L.tw_x = o;
         o += al(sizeof(float2) * pl->Nx);
         L.tw_y = o;
@@ -635,6 +644,7 @@ PassArgs jac_args(void* ws, const Layout& L, const PassArgs& base)
     a.chan = at<Channel>(ws, L.chan_jac);
     a.chan_stride = L.nchan;
     a.nchan = L.nchan;
+    a.jac_pass = 1;
     a.ext = at<float>(ws, L.ext_jac);
     a.y = at<float>(ws, L.y_jac);
     a.partial = at<float>(ws, L.part_jac);
@@ -932,10 +942,15 @@ gf_status trial_pass(const PassArgs& a, const Plan& pl, void* ws, cudaStream_t s
     gf_status r = run_conv(a, pl, ws, pl.L.spec_trial, s);
     if (r != GF_OK) return r;
     ProfScope ps(PROF_REDUCE, s);
+    if (a.lm) {
+        // the LM body: one chi^2 per rung of the trial ladder, summed by
+        // k_final_update
+        GF_CUDA(launch_reduce_rungs(a, s));
+        return GF_OK;
+    }
     GF_CUDA(launch_reduce_chi2(a, s));
-    // the LM body folds the final reduction into k_final_update; a render
-    // (no image) has no chi^2
-    if (!a.lm && x2) GF_CUDA(launch_final_chi2(a, x2, s));
+    // a render (no image) has no chi^2
+    if (x2) GF_CUDA(launch_final_chi2(a, x2, s));
     return GF_OK;
 }
 
@@ -1071,6 +1086,7 @@ size_t gf_workspace_size(const gf_desc* d, const uint8_t* fixed, int call)
     if (check_structure(d) != GF_OK || check_stamp(d, d->H, d->W) != GF_OK) return 0;
     Structure S;
     if (make_structure(d, fixed, nullptr, nullptr, nullptr, &S) != GF_OK) return 0;
+    S.opts.ladder = GF_MAX_LADDER;  // an LM fit's size holds for any ladder
     Plan pl;
     plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, need_of(call), &pl);
     return pl.L.total;
@@ -1098,6 +1114,7 @@ size_t gf_workspace_size_batch(const gf_desc* d, const gf_batch* b, const uint8_
         if (check_stamp(d, b->H[i], b->W[i]) != GF_OK) return 0;
     Structure S;
     if (make_structure(d, fixed, nullptr, nullptr, nullptr, &S) != GF_OK) return 0;
+    S.opts.ladder = GF_MAX_LADDER;  // an LM fit's size holds for any ladder
     Plan pl;
     plan_batch(d, S, b->count, b->H, b->W, b->pix_off, b->psf_off, NEED_LM, &pl);
     return pl.L.total;
@@ -1322,6 +1339,8 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     PassArgs at_ = trial_args(ws, L, base);
     at_.lm = lm;
     at_.phase = PH_TRIAL;
+    at_.nchan = at_.chan_stride = L.rungs;  // one trial channel per rung of the ladder
+    set_grids(at_, L, L.rungs);
     // each pass walks the list of stamps in its phase, rebuilt every body
     aj.wl.n = at<int>(ws, L.wl_n[0]);
     aj.wl.ids = at<int>(ws, L.wl_ids[0]);
@@ -1345,7 +1364,7 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
         if (rr != GF_OK) return rr;
         {
             ProfScope ps(PROF_LM, s);
-            GF_CUDA(launch_final_solve(aj, at<Channel>(ws, L.chan_trial), active, s));
+            GF_CUDA(launch_final_solve(aj, at<Channel>(ws, L.chan_trial), active, L.rungs, s));
             GF_CUDA(launch_worklist(L.count, lm, PH_TRIAL, base.pre_static,
                                     at<int>(ws, L.wl_n[1]), at<int>(ws, L.wl_ids[1]),
                                     at<int>(ws, L.wl_pre[1]), s));

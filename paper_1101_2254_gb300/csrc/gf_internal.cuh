@@ -96,14 +96,22 @@ struct Structure {
     gf_lm_opts opts;
 };
 
-// Per-stamp LM state, resident on the device for the whole fit.
+// Outcome of the damped solve of one rung of the trial ladder (see lm.cu)
+enum { RUNG_FAIL = 0, RUNG_SMALL = 1, RUNG_TRIAL = 2 };
+
+// Per-stamp LM state, resident on the device for the whole fit.  Rung r of the
+// trial ladder is the step for lambda * up^r: its trial parameters pt[r], the
+// chi^2 fall its linearised model predicts, and the outcome of its solve.
 struct LMState {
     double p[GF_MAX_SLOTS];
-    double pt[GF_MAX_SLOTS];
+    double pt[GF_MAX_LADDER][GF_MAX_SLOTS];
     double A[GF_MAX_FREE * GF_MAX_FREE];
     double g[GF_MAX_FREE];
-    double chi2, chi2t, lambda, pred;  // pred: chi^2 fall the linearised model predicts for pt
+    double chi2, chi2t, lambda;
+    double pred[GF_MAX_LADDER];
     double bn_n[GF_MAX_COMP], bn_b[GF_MAX_COMP];  // last (n, b_n) per component: Newton start
+    int rung[GF_MAX_LADDER];  // RUNG_* per rung
+    int rung0;                // first rung the trial pass decides (earlier ones were settled)
     int iters, accepted, status, phase;
 };
 
@@ -264,6 +272,8 @@ struct PassArgs {
     const Channel* chan;       // [count * chan_stride]
     int chan_stride;           // channels reserved per stamp
     int nchan;                 // channels processed per stamp in this pass
+    int jac_pass;              // the channels are a Jacobian pass's (shapes, then FD channels
+                               // of the same components); else independent models
     float* ext;                // channel grids: ext + ext_index(st[b], nchan, k)
     float* y;                  // convolved channels: y + y_index(st[b], nchan, k)
     const float* psf;
@@ -337,6 +347,8 @@ cudaError_t launch_conv_direct(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_conv_direct_width(const PassArgs& a, int tile_w, cudaStream_t s);
 cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_chi2(const PassArgs& a, cudaStream_t s);
+// chi^2 partials of each channel as its own model (the rungs of a trial pass)
+cudaError_t launch_reduce_rungs(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_final_jac(const PassArgs& a, double* A_out, double* g_out, double* chi2_out,
                              cudaStream_t s);
 cudaError_t launch_bn_table(cudaStream_t s);
@@ -353,7 +365,8 @@ cudaError_t launch_prep_sum(const PassArgs& a, const double* params, int use_tri
 cudaError_t launch_prep_jac(const PassArgs& a, const double* params, cudaStream_t s);
 cudaError_t launch_lm_init(int count, const Structure* S, LMState* lm, const double* p0,
                            cudaStream_t s);
-cudaError_t launch_final_solve(const PassArgs& a, Channel* trial_chan, int* active,
+// one block per stamp, one warp per rung of the trial ladder (nr rungs)
+cudaError_t launch_final_solve(const PassArgs& a, Channel* trial_chan, int* active, int nr,
                                cudaStream_t s);
 cudaError_t launch_final_update(const PassArgs& a, int* active_count, cudaStream_t s);
 cudaError_t launch_lm_export(int count, const Structure* S, const LMState* lm, double* out,

@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prep_sum(PassArgs a, co
     WARP_STAMP();
     if (a.lm && a.lm[b].phase != a.phase) return;
     const double* p = params ? params + (long long)b * S.nslots
-                             : (use_trial ? a.lm[b].pt : a.lm[b].p);
+                             : (use_trial ? a.lm[b].pt[0] : a.lm[b].p);
     for (int s = lane; s < S.nslots; s += 32) W.p[s] = p[s];
     __syncwarp();
     warp_bn(S, W, a.lm ? &a.lm[b] : nullptr, false);
@@ -516,74 +516,79 @@ __global__ void k_lm_init(int count, const Structure* Sp, LMState* lm, const dou
     if (b >= count) return;
     const Structure& S = *Sp;
     LMState& L = lm[b];
-    for (int s = 0; s < S.nslots; ++s) L.p[s] = L.pt[s] = p0[(long long)b * S.nslots + s];
+    for (int s = 0; s < S.nslots; ++s) L.p[s] = L.pt[0][s] = p0[(long long)b * S.nslots + s];
     for (int s = 0; s < S.nslots; ++s) project_slot(S, L.p, s);
     for (int k = 0; k < GF_MAX_COMP; ++k) L.bn_n[k] = L.bn_b[k] = 0.0;
     L.chi2 = INFINITY;
     L.chi2t = INFINITY;
     L.lambda = S.opts.lambda0;
+    for (int r = 0; r < GF_MAX_LADDER; ++r) {
+        L.pred[r] = 0.0;
+        L.rung[r] = RUNG_FAIL;
+    }
+    L.rung0 = 0;
     L.iters = 0;
     L.accepted = 0;
     L.status = GF_EMAXITER;
     L.phase = PH_NEED_JAC;
 }
 
-// One warp per stamp.  Stamps whose Jacobian pass just ran (PH_NEED_JAC; its
-// sums already in A, g and chi^2 from k_final_acc) and stamps retrying after a
-// rejection (PH_SOLVE) solve the damped system, apply the finishing tests on
-// the step, and build the trial model channel.  Block 0 also resets the
-// active-stamp counter that k_final_update fills.
-__global__ void __launch_bounds__(32) k_final_solve(PassArgs a, Channel* trial_chan, int* active)
+// The trial ladder.  Marquardt's rule tries one step at a time: solve with
+// lambda, evaluate the trial, and after a rejection solve again with
+// lambda*up.  With a ladder of R rungs the damped systems for lambda,
+// lambda*up, ..., lambda*up^(R-1) (the damping of each repeated by the same
+// multiplications the rule makes) are solved side by side, one warp per rung,
+// and their trials are evaluated in one pass.  k_final_update then walks the
+// rungs in order, applying the rule to each, and stops where the rule stops (an
+// accepted trial, a finishing criterion); the rungs it does not reach are
+// discarded.  The fit therefore takes exactly the steps of the one-at-a-time
+// rule, in fewer passes when trials are rejected.
+
+// One block per stamp, one warp per rung.  Stamps whose Jacobian pass just ran
+// (PH_NEED_JAC; its sums already in A, g and chi^2) and stamps retrying after
+// rejections (PH_SOLVE) solve the damped systems, apply the scaled-step test,
+// and build one trial model channel per rung.  Rungs before the first one that
+// needs a trial (failed solves, a finishing step) are settled here.  Block 0
+// also resets the active-stamp counter that k_final_update fills.
+__global__ void __launch_bounds__(32 * GF_MAX_LADDER) k_final_solve(PassArgs a, Channel* trial_chan,
+                                                                    int* active)
 {
     pdl_entry();
     __shared__ Structure S_sh;
-    __shared__ WarpScratch W;
+    __shared__ WarpScratch Ws[GF_MAX_LADDER];
     __shared__ double As[GF_MAX_FREE * GF_MAX_FREE], gs[GF_MAX_FREE];
+    __shared__ int rung_state[GF_MAX_LADDER];
     const int b = blockIdx.x;
+    const int nr = blockDim.x >> 5;  // rungs
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (b == 0 && threadIdx.x == 0 && active) *active = 0;
     LMState& L = a.lm[b];
-    int phase = L.phase;
-    if (phase != PH_NEED_JAC && phase != PH_SOLVE) return;  // the whole (one-warp) block
+    const int phase = L.phase;
+    if (phase != PH_NEED_JAC && phase != PH_SOLVE) return;  // the whole block
     load_structure(&S_sh, a.S);
-    __syncwarp();
     const Structure& S = S_sh;
-    const int nf = S.nfree;
-    if (phase == PH_NEED_JAC) {
-        phase = PH_SOLVE;
-        if (threadIdx.x == 0) L.phase = PH_SOLVE;
-    }
-    // A and g into shared memory in one round of loads
+    const int nf = a.S->nfree;
     {
-        double v[8];
         const int nA = nf * nf;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = threadIdx.x + 32 * u;
-            v[u] = i < nA ? __ldcg(&L.A[i]) : 0.0;
-        }
-        const double gv = threadIdx.x < nf ? __ldcg(&L.g[threadIdx.x]) : 0.0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = threadIdx.x + 32 * u;
-            if (i < nA) As[i] = v[u];
-        }
-        if (threadIdx.x < nf) gs[threadIdx.x] = gv;
-        __syncwarp();
+        for (int i = threadIdx.x; i < nA; i += blockDim.x) As[i] = __ldcg(&L.A[i]);
+        if (threadIdx.x < nf) gs[threadIdx.x] = __ldcg(&L.g[threadIdx.x]);
     }
-    const int lane = threadIdx.x;
+    __syncthreads();
     bool fin = true;
     for (int i = lane; i < nf; i += 32) fin = fin && isfinite(gs[i]) && isfinite(As[i * nf + i]);
-    const bool finite = __all_sync(kFull, fin) && isfinite(L.chi2);
+    const bool finite = __all_sync(kFull, fin) && isfinite(L.chi2);  // the same in every warp
     if (!finite) {
-        __syncwarp();
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             L.status = GF_ENONFINITE;
             L.phase = PH_DONE;
         }
         return;
     }
+    WarpScratch& W = Ws[w];
+    // damping of rung w: lambda times up, w times over (the rule's own sequence)
+    double lam = L.lambda;
+    for (int r = 0; r < w; ++r) lam *= S.opts.lambda_up;
     // damped system (A + lambda diag A) delta = g; a slot with A_ii = 0 is held
-    const double lam = L.lambda;
     // bit i: A_ii > 0 (one FP64 comparison per lane instead of one per entry)
     const unsigned pos = __ballot_sync(kFull, lane < nf && As[lane * nf + lane] > 0.0);
     if (lane < nf) {  // lane i builds row i
@@ -601,103 +606,140 @@ __global__ void __launch_bounds__(32) k_final_solve(PassArgs a, Channel* trial_c
         W.r[i] = pi ? gs[i] : 0.0;
     }
     const bool ok = warp_cholesky_solve(nf, W);
-    const int iters = L.iters + 1;
-    __syncwarp();
-    if (lane == 0) L.iters = iters;
-    if (!ok) {
-        if (lane == 0) {
-            lm_reject(S, L);
-            lm_check_iters(S, L);
-        }
-        return;
-    }
-    // scaled step and predicted fall of chi^2 for the damped step,
-    // delta^T (g + lambda diag(A) delta), as warp reductions
-    // (the scaled-step test max_i |delta_i| / s_i < xtol is taken as
-    // |delta_i| < xtol s_i for every i: no FP64 division per lane)
-    bool small = true;
+    int state = RUNG_FAIL;
     double pred = 0.0;
-    for (int i = lane; i < nf; i += 32) {
-        const int s = S.freeslot[i];
-        small = small && fabs(W.r[i]) < S.opts.xtol * fmax(fabs(L.p[s]), xtol_scale(S.role[s]));
-        if ((pos >> i) & 1u) pred += W.r[i] * (gs[i] + lam * As[i * nf + i] * W.r[i]);
-    }
+    if (ok) {
+        // scaled step and predicted fall of chi^2 for the damped step,
+        // delta^T (g + lambda diag(A) delta), as warp reductions (the test
+        // max_i |delta_i| / s_i < xtol is taken as |delta_i| < xtol s_i for
+        // every i: no FP64 division per lane)
+        bool small = true;
+        for (int i = lane; i < nf; i += 32) {
+            const int sl = S.freeslot[i];
+            small = small && fabs(W.r[i]) < S.opts.xtol * fmax(fabs(L.p[sl]), xtol_scale(S.role[sl]));
+            if ((pos >> i) & 1u) pred += W.r[i] * (gs[i] + lam * As[i * nf + i] * W.r[i]);
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) pred += __shfl_xor_sync(kFull, pred, o);
-    if (__all_sync(kFull, small)) {
-        if (lane == 0) {
+        for (int o = 16; o > 0; o >>= 1) pred += __shfl_xor_sync(kFull, pred, o);
+        state = __all_sync(kFull, small) ? RUNG_SMALL : RUNG_TRIAL;
+    }
+    // trial parameters p + delta projected into the box (a rung without a
+    // trial keeps p, so that its channel is still a valid model)
+    for (int sl = lane; sl < S.nslots; sl += 32) W.p[sl] = L.p[sl];
+    __syncwarp();
+    if (state == RUNG_TRIAL)
+        for (int i = lane; i < nf; i += 32) W.p[S.freeslot[i]] += W.r[i];
+    __syncwarp();
+    for (int sl = lane; sl < S.nslots; sl += 32) {
+        project_slot(S, W.p, sl);
+        L.pt[w][sl] = W.p[sl];
+    }
+    __syncwarp();
+    warp_bn(S, W, w == 0 ? &L : nullptr, false);
+    warp_build_sum(S, W, trial_chan + (long long)b * nr + w);
+    if (lane == 0) {
+        L.pred[w] = pred;
+        L.rung[w] = state;
+        rung_state[w] = state;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    // settle the rungs before the first trial, as the rule would, one by one
+    int r = 0;
+    for (; r < nr; ++r) {
+        const int st = rung_state[r];
+        if (st == RUNG_TRIAL) break;
+        L.iters += 1;
+        if (st == RUNG_SMALL) {
             L.status = GF_OK;
             L.phase = PH_DONE;
+            return;
         }
-        return;
+        lm_reject(S, L);
+        lm_check_iters(S, L);
+        if (L.phase == PH_DONE) return;
     }
-    for (int s = lane; s < S.nslots; s += 32) W.p[s] = L.p[s];
-    __syncwarp();
-    for (int i = lane; i < nf; i += 32) W.p[S.freeslot[i]] += W.r[i];
-    __syncwarp();
-    for (int s = lane; s < S.nslots; s += 32) {
-        project_slot(S, W.p, s);
-        L.pt[s] = W.p[s];
-    }
-    __syncwarp();
-    warp_bn(S, W, &L, false);
-    warp_build_sum(S, W, trial_chan + b);
-    __syncwarp();
-    if (lane == 0) {
-        L.pred = pred;
+    if (r < nr) {
+        L.rung0 = r;
         L.phase = PH_TRIAL;
+    } else {
+        L.phase = PH_SOLVE;  // every rung's solve failed: solve again at the grown damping
     }
 }
 
 // One block per stamp: stamps in PH_TRIAL sum the trial pass's partials into
-// chi^2 at the trial point (deterministic tree) and accept or reject it; every
-// stamp not yet done adds one to the active counter.
+// the chi^2 of each rung from rung0 on (deterministic tree, the same for every
+// rung), then apply the rule rung by rung: a rejected trial grows lambda and
+// passes to the next rung, an accepted one (or a finishing criterion) ends the
+// walk.  Every stamp not yet done adds one to the active counter.
 __global__ void __launch_bounds__(RED_THREADS) k_final_update(PassArgs a, int* active)
 {
     pdl_entry();
     __shared__ CSum wsum[RED_THREADS / 32];
+    __shared__ double x2r[GF_MAX_LADDER];
     const int b = blockIdx.x;
     LMState& L = a.lm[b];
     const int phase = L.phase;
+    const int nr = a.nchan;  // rungs of the trial pass
     if (phase == PH_TRIAL) {
         const int* pst = a.pre_static + WK_RED * (a.count + 1);
         const int b0 = pst[b], b1 = pst[b + 1];
-        CSum acc = {0.0f, 0.0f};
-        for (int k = b0 + threadIdx.x; k < b1; k += RED_THREADS) csum_add(acc, a.partial[k]);
+        for (int r = L.rung0; r < nr; ++r) {
+            CSum acc = {0.0f, 0.0f};
+            for (int k = b0 + threadIdx.x; k < b1; k += RED_THREADS)
+                csum_add(acc, a.partial[(long long)k * nr + r]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            CSum other;
-            other.s = __shfl_down_sync(kFull, acc.s, o);
-            other.c = __shfl_down_sync(kFull, acc.c, o);
-            acc = csum_merge(acc, other);
+            for (int o = 16; o > 0; o >>= 1) {
+                CSum other;
+                other.s = __shfl_down_sync(kFull, acc.s, o);
+                other.c = __shfl_down_sync(kFull, acc.c, o);
+                acc = csum_merge(acc, other);
+            }
+            if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                CSum t = wsum[0];
+                for (int w = 1; w < RED_THREADS / 32; ++w) t = csum_merge(t, wsum[w]);
+                x2r[r] = (double)t.s + (double)t.c;
+            }
+            __syncthreads();
         }
-        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
-        __syncthreads();
     }
     if (threadIdx.x != 0) return;
     const Structure& S = *a.S;
     if (phase == PH_TRIAL) {
-        CSum t = wsum[0];
-        for (int w = 1; w < RED_THREADS / 32; ++w) t = csum_merge(t, wsum[w]);
-        const double xt = (double)t.s + (double)t.c;
-        L.chi2t = xt;
-        if (isfinite(xt) && xt < L.chi2) {
-            const double rel = (L.chi2 - xt) / L.chi2;
-            const double prel = L.pred / L.chi2;
-            for (int s = 0; s < S.nslots; ++s) L.p[s] = L.pt[s];
-            L.accepted++;
-            L.lambda = fmax(L.lambda * S.opts.lambda_down, S.opts.lambda_min);
-            L.chi2 = xt;
-            if (rel < S.opts.ftol && prel < S.opts.ftol) {
+        for (int r = L.rung0; r < nr; ++r) {
+            L.iters += 1;
+            const int st = L.rung[r];
+            if (st == RUNG_SMALL) {
                 L.status = GF_OK;
                 L.phase = PH_DONE;
-            } else {
-                L.phase = PH_NEED_JAC;
+                break;
             }
-        } else {
+            if (st == RUNG_TRIAL) {
+                const double xt = x2r[r];
+                L.chi2t = xt;
+                if (isfinite(xt) && xt < L.chi2) {
+                    const double rel = (L.chi2 - xt) / L.chi2;
+                    const double prel = L.pred[r] / L.chi2;
+                    for (int sl = 0; sl < S.nslots; ++sl) L.p[sl] = L.pt[r][sl];
+                    L.accepted++;
+                    L.lambda = fmax(L.lambda * S.opts.lambda_down, S.opts.lambda_min);
+                    L.chi2 = xt;
+                    if (rel < S.opts.ftol && prel < S.opts.ftol) {
+                        L.status = GF_OK;
+                        L.phase = PH_DONE;
+                    } else {
+                        L.phase = PH_NEED_JAC;
+                    }
+                    lm_check_iters(S, L);
+                    break;
+                }
+            }
             lm_reject(S, L);
+            lm_check_iters(S, L);
+            if (L.phase == PH_DONE) break;
         }
-        lm_check_iters(S, L);
     }
     if (active && L.phase != PH_DONE) atomicAdd(active, 1);
 }
@@ -813,10 +855,11 @@ cudaError_t launch_lm_init(int count, const Structure* S, LMState* lm, const dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_final_solve(const PassArgs& a, Channel* trial_chan, int* active,
+cudaError_t launch_final_solve(const PassArgs& a, Channel* trial_chan, int* active, int nr,
                                cudaStream_t s)
 {
-    GF_LAUNCH_PDL(k_final_solve, dim3(a.count), dim3(32), 0, s, a, trial_chan, active);
+    if (nr < 1 || nr > GF_MAX_LADDER) return cudaErrorInvalidValue;
+    GF_LAUNCH_PDL(k_final_solve, dim3(a.count), dim3(32 * nr), 0, s, a, trial_chan, active);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }

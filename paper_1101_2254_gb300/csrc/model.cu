@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(OS_WARPS * 32) k_model_os_jac(PassArgs a)
 
 cudaError_t launch_model(const PassArgs& a, cudaStream_t s)
 {
-    if (a.nchan > 1) {  // a Jacobian pass: all channels of a pixel together
+    if (a.jac_pass && a.nchan > 1) {  // a Jacobian pass: all channels of a pixel together
         const int cap[2] = {152 * 16, 152 * 8};
         if (a.maxitems[WK_MODEL] > 0) {
             const int g = (int)std::min<long long>(a.maxitems[WK_MODEL] / a.nchan, cap[0]);

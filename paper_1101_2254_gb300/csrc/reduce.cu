@@ -266,6 +266,95 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_chi2(PassArgs a)
     }
 }
 
+// The trial pass of an LM body evaluates the rungs of the trial ladder (one
+// channel each, each its own model): per work item and channel k, the chi^2
+// partial of channel k goes to partial[item * nchan + k].  Each channel is
+// summed exactly as k_reduce_chi2 sums a one-channel pass (same per-thread
+// order, same tree), so a rung's chi^2 does not depend on the other rungs.
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_rungs(PassArgs a)
+{
+    pdl_entry();
+    __shared__ ChanInfo ci;
+    __shared__ float mskys[GF_MAX_LADDER];
+    __shared__ CSum wsum[GF_MAX_LADDER][RED_THREADS / 32];
+    const int n = *a.wl.n;
+    const int* pre = a.wl.pre + WK_RED * (a.count + 1);
+    const int tot = pre[n];
+    const int nch = a.nchan;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int hint = -1;
+    const int chunk = (tot + gridDim.x - 1) / gridDim.x;
+    const int it0 = blockIdx.x * chunk, it1 = min(tot, it0 + chunk);
+    for (int it = it0; it < it1; ++it) {
+        const int li = wl_locate(pre, n, it, hint);
+        const int b = a.wl.ids[li];
+        const int local = it - pre[li];
+        const int blk = a.pre_static[WK_RED * (a.count + 1) + b] + local;  // partial slot
+        const StampInfo st = a.st[b];
+        __syncthreads();
+        {
+            const Channel* c = a.chan + (long long)b * a.chan_stride;
+            if (threadIdx.x < nch) {
+                ci.mw[threadIdx.x] = c[threadIdx.x].mweight;
+                mskys[threadIdx.x] = c[threadIdx.x].msky;
+            }
+        }
+        __syncthreads();
+        const long long HW = (long long)st.H * st.W;
+        const float* img = a.img + st.pix_off;
+        const float* sig = a.sig + st.pix_off;
+        const long long base = (long long)local * RED_PIX;
+        float dv[RED_CHUNKS], sv[RED_CHUNKS];
+#pragma unroll
+        for (int q = 0; q < RED_CHUNKS; ++q) {
+            const long long px = base + (long long)q * RED_THREADS + threadIdx.x;
+            const bool in = px < HW;
+            dv[q] = in ? __ldg(&img[px]) : 0.0f;
+            sv[q] = in ? __ldg(&sig[px]) : 0.0f;
+        }
+        for (int k = 0; k < nch; ++k) {
+            const float* Y = a.y + y_index(st, nch, k);
+            float m[RED_CHUNKS];
+#pragma unroll
+            for (int q = 0; q < RED_CHUNKS; ++q) {
+                const long long px = base + (long long)q * RED_THREADS + threadIdx.x;
+                m[q] = px < HW ? __ldg(&Y[px]) : 0.0f;
+            }
+            CSum acc = {0.0f, 0.0f};
+#pragma unroll
+            for (int q = 0; q < RED_CHUNKS; ++q) {
+                const long long px = base + (long long)q * RED_THREADS + threadIdx.x;
+                if (px >= HW) break;
+                const float mq = fmaf(ci.mw[k], m[q], mskys[k]);
+                const float d = dv[q], s = sv[q];
+                if (isfinite(d) && isfinite(s) && s > 0.0f) {
+                    const float z = (d - mq) / s;
+                    csum_add(acc, z * z);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                CSum other;
+                other.s = __shfl_down_sync(0xffffffffu, acc.s, o);
+                other.c = __shfl_down_sync(0xffffffffu, acc.c, o);
+                acc = csum_merge(acc, other);
+            }
+            if (lane == 0) wsum[k][warp] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x < nch) {
+            const int k = threadIdx.x;
+            CSum t = wsum[k][0];
+            for (int w = 1; w < RED_THREADS / 32; ++w) t = csum_merge(t, wsum[k][w]);
+            a.partial[(long long)blk * nch + k] = t.s + t.c;
+        }
+        if (a.work && threadIdx.x == 0) {
+            const long long np = min((long long)RED_PIX, HW - base);
+            atomicAdd(&a.work[PROF_REDUCE], (unsigned long long)np * (4ull * nch + 8ull));
+        }
+    }
+}
+
 // one block per stamp: sum the stamp's partials in block order
 // Final sums of the Jacobian pass.  Block (stamp b, group y) owns accumulators
 // 32y .. 32y + 31, one per lane, so each warp reads whole 128-byte rows of the
@@ -406,6 +495,16 @@ cudaError_t launch_reduce_chi2(const PassArgs& a, cudaStream_t s)
 {
     if (a.maxitems[WK_RED] > 0) {
         GF_LAUNCH_PDL(k_reduce_chi2, dim3(a.grid[WK_RED]), dim3(RED_THREADS), 0, s, a);
+        GF_COUNT_LAUNCH();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_rungs(const PassArgs& a, cudaStream_t s)
+{
+    if (a.nchan > GF_MAX_LADDER) return cudaErrorInvalidValue;
+    if (a.maxitems[WK_RED] > 0) {
+        GF_LAUNCH_PDL(k_reduce_rungs, dim3(a.grid[WK_RED]), dim3(RED_THREADS), 0, s, a);
         GF_COUNT_LAUNCH();
     }
     return cudaGetLastError();

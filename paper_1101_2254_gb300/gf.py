@@ -40,7 +40,7 @@ class LMOpts(C.Structure):
     _fields_ = [("lambda0", C.c_double), ("lambda_up", C.c_double),
                 ("lambda_down", C.c_double), ("lambda_min", C.c_double),
                 ("lambda_max", C.c_double), ("ftol", C.c_double), ("xtol", C.c_double),
-                ("fd_rel", C.c_double), ("max_iter", C.c_int)]
+                ("fd_rel", C.c_double), ("max_iter", C.c_int), ("ladder", C.c_int)]
 
 
 class LMResult(C.Structure):

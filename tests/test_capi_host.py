@@ -99,3 +99,23 @@ def test_tile_width_setter_validates_before_touching_the_device():
     assert L.gf_set_conv_tile_width(33, 64, 32) == gf.EINVAL  # even class: 64 only
     assert L.gf_set_conv_tile_width(33, 70, 48) == gf.EINVAL  # no such width
     assert L.gf_set_conv_tile_width(0, 70, 32) == gf.EINVAL
+
+
+def test_lm_ladder_option_validated_before_launch(gf):
+    L = gf.lib()
+    o = gf.default_opts()
+    assert o.ladder == 2
+    d = gf.make_desc(64, 64, 25, [1, 3])
+    p = np.zeros(9)
+    r = gf.LMResult()
+    fake = C.c_void_p(256)
+    for bad in (-1, 5):
+        o.ladder = bad
+        st = L.gf_lm_fit(C.byref(d), p.ctypes.data_as(C.POINTER(C.c_double)), None, None, None,
+                         fake, fake, fake, C.byref(o), C.byref(r), fake, 1 << 30, None)
+        assert st == gf.EINVAL, bad
+        assert b"ladder" in L.gf_last_error()
+    # the LM workspace size covers the largest ladder: GF_MAX_LADDER trial channels
+    one = gf.make_desc(64, 64, 25, [1, 3])
+    assert L.gf_workspace_size(C.byref(one), None, gf.CALL_LM_FIT) > \
+        L.gf_workspace_size(C.byref(one), None, gf.CALL_JACOBIAN) + 4 * 4 * (88 * 88 + 64 * 64)

@@ -338,3 +338,51 @@ def test_eval_dft_tc_1024_sampled(gf):
     got = gm[idx[:, 0], idx[:, 1]]
     err = np.abs(got - want)
     assert np.all(err <= 1e-5 * np.abs(want) + DFT_FLOOR * gm.max()), err.max() / gm.max()
+
+
+# ------------------------------------------------------------ trial ladder
+# Evaluating the trials for lambda, lambda*up, ... in one pass must take exactly
+# the steps of Marquardt's one-trial-at-a-time rule: every ladder size gives the
+# same fit, bit for bit (parameters, chi^2, trial and acceptance counts, status).
+@pytest.mark.parametrize("conv", ["direct", "fft"])
+def test_lm_ladder_takes_the_rules_steps(gf, conv):
+    st = synth.stamp64()
+    _, img, sig = noisy_image(st)
+    method = gf.CONV_FFT if conv == "fft" else gf.CONV_DIRECT
+    d = gf.make_desc(st.H, st.W, st.P, st.kinds, st.os_factor, st.os_box, conv_method=method)
+    runs = []
+    for ladder in (1, 2, 3, 4):
+        # a large starting damping forces runs of rejections at the start
+        for lam0 in (1e-3, 1e2):
+            opts = gf.default_opts(ladder=ladder, lambda0=lam0)
+            runs.append(((ladder, lam0),) + gf.lm_fit(d, st.guess(), st.fixed, cuda(img),
+                                                      cuda(sig), cuda(st.psf), opts=opts))
+    for lam0 in (1e-3, 1e2):
+        ref = [r for r in runs if r[0] == (1, lam0)][0]
+        assert ref[2]["iters"] > ref[2]["accepted"]  # the fit has rejections
+        for key, p, res in runs:
+            if key[1] != lam0:
+                continue
+            assert np.array_equal(p, ref[1]), key
+            for f in ("chi2", "iters", "accepted", "status", "lam"):
+                assert res[f] == ref[2][f], (key, f, res[f], ref[2][f])
+
+
+def test_lm_ladder_batch_equals_single_rung(gf):
+    sts = small_batch(7, seed=5)
+    d0 = sts[0]
+    imgs, sigs, psfs, Hs, Ws, p0 = [], [], [], [], [], []
+    for st in sts:
+        m, img, sig = noisy_image(st)
+        imgs.append(img.ravel()); sigs.append(sig.ravel()); psfs.append(st.psf.ravel())
+        Hs.append(st.H); Ws.append(st.W); p0.append(st.guess())
+    d = gf.make_desc(1, 1, d0.P, d0.kinds, d0.os_factor, 8)
+    b = gf.make_batch(Hs, Ws, psf_size=d0.P)
+    args = (cuda(np.concatenate(imgs)), cuda(np.concatenate(sigs)), cuda(np.concatenate(psfs)))
+    p1, r1 = gf.lm_fit_batch(d, b, np.array(p0), d0.fixed, *args, opts=gf.default_opts(ladder=1))
+    for ladder in (2, 4):
+        pk, rk = gf.lm_fit_batch(d, b, np.array(p0), d0.fixed, *args,
+                                 opts=gf.default_opts(ladder=ladder))
+        assert np.array_equal(pk, p1), ladder
+        assert [(r["chi2"], r["iters"], r["accepted"], r["status"]) for r in rk] == \
+            [(r["chi2"], r["iters"], r["accepted"], r["status"]) for r in r1]
