@@ -148,6 +148,82 @@ def fp32_peak_tflops(sm_count, mhz):
 
 
 # ------------------------------------------------------------------ the GPU arm
+def _smooth_len(n):
+    """The smallest 2^a 3^b 5^c >= n that is even (a cuFFT-friendly size)."""
+    m = max(n, 2)
+    while True:
+        k = m
+        for f in (2, 3, 5):
+            while k % f == 0:
+                k //= f
+        if k == 1 and m % 2 == 0:
+            return m
+        m += 1
+
+
+def eval_paths(gf, torch, st, d, img_d, sig_d, psf_d, ws, stream, args, n=32):
+    """Steps 1-3 (model, PSF convolution, chi^2) of n copies of the stamp per call:
+    the library's path (gf_eval_batch: model grids, shared-memory FFT
+    convolution, chi^2 reduction, the PSF spectrum made by the same kernels)
+    against a plain unfused chain (the library's model kernel per
+    stamp, cuFFT R2C/C2R through torch.fft with a separate pointwise product,
+    a separate chi^2 pass).  Inputs resident, L2 flushed before each timed call."""
+    H, W, P = st.H, st.W, st.P
+    c = (P - 1) // 2
+    params = np.tile(st.params, (n, 1))
+    img = img_d.reshape(-1).repeat(n)
+    sig = sig_d.reshape(-1).repeat(n)
+    psf = psf_d.reshape(-1).repeat(n)
+    batch = gf.make_batch([H] * n, [W] * n, psf_size=P)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=img.device)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        ms = []
+        for _ in range(max(args.steps, 1)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms)), out
+
+    ms_f, (x2f, _) = timed(lambda: gf.evaluate_batch(d, batch, params, img, sig, psf, ws=ws))
+    Ny, Nx = _smooth_len(H + 2 * c), _smooth_len(W + 2 * c)
+    ext = torch.empty((n, H + 2 * c, W + 2 * c), dtype=torch.float32, device=img.device)
+    pw = torch.zeros((n, Ny, Nx), dtype=torch.float32, device=img.device)
+    yy = (torch.arange(P, device=img.device) - c) % Ny
+    xx = (torch.arange(P, device=img.device) - c) % Nx
+    d_m = gf.make_desc(H, W, P, st.kinds, st.os_factor, st.os_box)
+
+    def plain():
+        for i in range(n):
+            gf.model(d_m, params[i], out=ext[i], ws=ws)
+        pw.zero_()
+        pw[:, yy[:, None], xx[None, :]] = psf.view(n, P, P)
+        spec = torch.fft.rfft2(ext, s=(Ny, Nx)) * torch.fft.rfft2(pw)
+        conv = torch.fft.irfft2(spec, s=(Ny, Nx))[:, c:c + H, c:c + W]
+        z = (img.view(n, H, W) - conv) / sig.view(n, H, W)
+        return (z.double() ** 2).sum(dim=(1, 2))
+
+    ms_p, x2p = timed(plain)
+    rel = float((x2f.cpu() - x2p.cpu()).abs().max() / x2p.cpu().abs().max())
+    px = n * H * W
+    return {"stamps_per_call": n, "alg_bytes_per_eval": 8 * H * W + 4 * P * P,
+            "fused": {"evals_per_s": n / (ms_f / 1e3),
+                      "alg_hbm_gbs": n * (8 * H * W + 4 * P * P) / (ms_f / 1e3) / 1e9},
+            "plain_cufft": {"evals_per_s": n / (ms_p / 1e3),
+                            "min_bytes_per_eval": 24 * H * W,
+                            "alg_hbm_gbs": px * 24 / (ms_p / 1e3) / 1e9},
+            "chi2_rel_diff": rel,
+            "note": "fused reads image and sigma once per evaluation (8 B/px); the plain chain "
+                    "writes the model grid, passes it through cuFFT and reads image, sigma "
+                    "and model again (>= 24 B/px)"}
+
+
 def run_gf(args):
     import torch
     ws_, rank, local = dist_env()
@@ -241,6 +317,9 @@ def run_gf(args):
     h2d = img_p.numel() * 4 + sig_p.numel() * 4 + psf_p.numel() * 4
     d2h = 8 * len(p0) + 32
 
+    evals = eval_paths(gf, torch, st, d, img_d, sig_d, psf_d, ws, stream, args) \
+        if args.workload == "stamp512" else None
+
     peaks, peak_kind = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
@@ -285,6 +364,7 @@ def run_gf(args):
         "gpu_launches": launches,
         "roofline": roof,
         "evals_per_s": (chan_evals * ws_ / (total_ms / 1e3)) if chan_evals else None,
+        "evals": evals,
         "alg_hbm_gbs": alg_bytes / (total_ms / 1e3) / 1e9,
         "kernel_ms_per_fit": {k: v["ms"] / args.steps for k, v in pr.items()},
         "lm": {"iters": results[-1]["iters"], "accepted": results[-1]["accepted"],

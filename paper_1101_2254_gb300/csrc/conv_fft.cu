@@ -27,6 +27,8 @@ namespace {
 
 constexpr int ROW_THREADS = 128;
 constexpr int COL_THREADS = 256;
+constexpr int COL_UNROLL = 8;   // column-block loads in flight per thread
+constexpr int COL_HPRE = 12;    // PSF-spectrum values a thread may hold in registers
 
 __global__ void k_twiddles(int n, float2* tw)
 {
@@ -111,9 +113,35 @@ __global__ void __launch_bounds__(COL_THREADS) k_fft_cols(FFTArgs f, ColIO io, P
     load_tw(tw, f.tw_y, Ny);
     const int kx0 = blockIdx.x * B;
     float2* spec = io.spec + (long long)p * io.spec_stride;
-    for (int t = threadIdx.x; t < Ny * B; t += blockDim.x) {
-        const int y = t >> logB, kx = kx0 + (t & (B - 1));
-        bufA[t] = (y < io.rows_in && kx < Kx) ? spec[(long long)y * Kx + kx] : make_float2(0.f, 0.f);
+    const int total = Ny * B;
+    // the column block: eight loads per thread in flight before their stores
+    for (int t0 = threadIdx.x; t0 < total; t0 += COL_UNROLL * COL_THREADS) {
+        float2 v[COL_UNROLL];
+#pragma unroll
+        for (int u = 0; u < COL_UNROLL; ++u) {
+            const int t = t0 + u * COL_THREADS;
+            const int y = t >> logB, kx = kx0 + (t & (B - 1));
+            v[u] = (t < total && y < io.rows_in && kx < Kx) ? spec[(long long)y * Kx + kx]
+                                                            : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < COL_UNROLL; ++u) {
+            const int t = t0 + u * COL_THREADS;
+            if (t < total) bufA[t] = v[u];
+        }
+    }
+    // the PSF spectrum this thread multiplies, fetched now so that its latency
+    // hides behind the forward transform (when it fits the registers)
+    const float2* Hs = f.hhat + (long long)b * Ny * Kx;
+    float2 hv[COL_HPRE];
+    const bool hpre = mode == 1 && total <= COL_HPRE * COL_THREADS;
+    if (hpre) {
+#pragma unroll
+        for (int u = 0; u < COL_HPRE; ++u) {
+            const int t = threadIdx.x + u * COL_THREADS;
+            const int y = t >> logB, kx = kx0 + (t & (B - 1));
+            hv[u] = (t < total && kx < Kx) ? Hs[(long long)y * Kx + kx] : make_float2(0.f, 0.f);
+        }
     }
     __syncthreads();
     float2* X = fft_smem(f.py, bufA, bufB, logB, tw, -1.0f);
@@ -125,10 +153,18 @@ __global__ void __launch_bounds__(COL_THREADS) k_fft_cols(FFTArgs f, ColIO io, P
         }
         return;
     }
-    const float2* H = f.hhat + (long long)b * Ny * Kx;
-    for (int t = threadIdx.x; t < Ny * B; t += blockDim.x) {
-        const int y = t >> logB, kx = kx0 + (t & (B - 1));
-        if (kx < Kx) X[t] = cmul(X[t], H[(long long)y * Kx + kx]);
+    if (hpre) {
+#pragma unroll
+        for (int u = 0; u < COL_HPRE; ++u) {
+            const int t = threadIdx.x + u * COL_THREADS;
+            const int kx = kx0 + (t & (B - 1));
+            if (t < total && kx < Kx) X[t] = cmul(X[t], hv[u]);
+        }
+    } else {
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int y = t >> logB, kx = kx0 + (t & (B - 1));
+            if (kx < Kx) X[t] = cmul(X[t], Hs[(long long)y * Kx + kx]);
+        }
     }
     __syncthreads();
     float2* other = (X == bufA) ? bufB : bufA;
@@ -279,10 +315,10 @@ cudaError_t launch_conv_fft(const PassArgs& a, const FFTArgs& f, float2* spec, c
     c.row0 = s0.c;
     c.nrows_out = s0.H;
     c.nchan = a.nchan;
-    // fewer columns per CTA when the pass has few problems (a one-channel trial
-    // pass), so that the column pass still spreads over the SMs
+    // fewer columns per CTA until the pass has four CTAs per SM (the column
+    // pass waits on L2 loads: more, smaller CTAs keep more of them in flight)
     FFTArgs fc = f;
-    while (fc.cpc > 2 && (long long)nprob * ((Kx + fc.cpc - 1) / fc.cpc) < 2 * 152) fc.cpc /= 2;
+    while (fc.cpc > 2 && (long long)nprob * ((Kx + fc.cpc - 1) / fc.cpc) < 4 * 152) fc.cpc /= 2;
     fc.flops_col = f.flops_col * (float)fc.cpc / (float)f.cpc;
     GF_LAUNCH_PDL(k_fft_cols, dim3(dim3((Kx + fc.cpc - 1) / fc.cpc, nprob)), dim3(COL_THREADS), fft_col_smem(fc.Ny, fc.cpc), s, fc, c, a, 1);
     GF_COUNT_LAUNCH();

@@ -378,49 +378,68 @@ __device__ __forceinline__ void sqrt_and_rsqrt(double x, double& sq, double& rs)
     }
 }
 
-// Warp Cholesky factorisation M = L L^T of the SPD n x n matrix W.M (n <= 16;
-// lower factor in place) and the solve M x = W.r (x in W.r).  Lane i owns row
-// i: each column step scales the entries below the pivot by 1/sqrt(pivot) and
-// updates the trailing part of the lane's own row, reading the other rows'
-// pivot-column entries from shared memory; both substitutions go column by
-// column with one shuffle per step.  Returns false (uniformly) when a pivot is
-// not positive or a result is not finite.
+// Warp Cholesky factorisation M = L L^T of the SPD n x n matrix W.M (n <= 16)
+// and the solve M x = W.r (x in W.r).  Lane i holds row i of M in registers
+// (the loops over columns are unrolled to GF_MAX_FREE, so the row stays in
+// registers): each column step j broadcasts the pivot from lane j, scales the
+// entries below it by 1/sqrt(pivot), and every lane updates its row with
+// L_ij L_kj, reading L_kj from lane k by a shuffle -- independent FMAs with no
+// memory round trips between them.  The forward substitution runs on the
+// register rows; the factor is then written to W.M for the back substitution,
+// which needs it by columns.  Returns false (uniformly) when a pivot is not
+// positive or a result is not finite.
 __device__ bool warp_cholesky_solve(int n, WarpScratch& W)
 {
     const int lane = threadIdx.x & 31;
     double* M = W.M;
-    double* mine = M + lane * n;  // dereferenced only for lane < n
+    double row[GF_MAX_FREE];
+#pragma unroll
+    for (int k = 0; k < GF_MAX_FREE; ++k)
+        row[k] = (lane < n && k < n && k <= lane) ? M[lane * n + k] : 0.0;
     double invd_mine = 0.0;
-    for (int j = 0; j < n; ++j) {
-        __syncwarp();
-        const double piv = __shfl_sync(kFull, lane == j ? mine[j] : 0.0, j);
+#pragma unroll
+    for (int j = 0; j < GF_MAX_FREE; ++j) {
+        if (j >= n) break;
+        const double piv = __shfl_sync(kFull, row[j], j);
         if (!(piv > 0.0) || !isfinite(piv)) return false;
         double d, invd;
         sqrt_and_rsqrt(piv, d, invd);
         if (lane == j) {
-            mine[j] = d;
+            row[j] = d;
             invd_mine = invd;
-        } else if (lane > j && lane < n) {
-            mine[j] *= invd;
+        } else if (lane > j) {
+            row[j] *= invd;
         }
-        __syncwarp();
-        if (lane > j && lane < n) {
-            const double lij = mine[j];
-            for (int k = j + 1; k <= lane; ++k) mine[k] -= lij * M[k * n + j];
+#pragma unroll
+        for (int k = j + 1; k < GF_MAX_FREE; ++k) {
+            if (k >= n) break;
+            const double lkj = __shfl_sync(kFull, row[j], k);
+            if (lane >= k && lane < n) row[k] = fma(-row[j], lkj, row[k]);
         }
     }
-    __syncwarp();
-    // forward substitution L y = r, then back substitution L^T x = y
+    // forward substitution L y = r
     double ri = lane < n ? W.r[lane] : 0.0;
-    for (int k = 0; k < n; ++k) {
+#pragma unroll
+    for (int k = 0; k < GF_MAX_FREE; ++k) {
+        if (k >= n) break;
         const double yk = __shfl_sync(kFull, ri * invd_mine, k);
-        if (lane == k) ri = yk;
-        else if (lane > k && lane < n) ri -= mine[k] * yk;
+        if (lane == k)
+            ri = yk;
+        else if (lane > k && lane < n)
+            ri = fma(-row[k], yk, ri);
     }
+    // the factor by rows into shared memory, then back substitution L^T x = y
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < GF_MAX_FREE; ++k)
+        if (lane < n && k < n && k <= lane) M[lane * n + k] = row[k];
+    __syncwarp();
     for (int k = n - 1; k >= 0; --k) {
         const double xk = __shfl_sync(kFull, ri * invd_mine, k);
-        if (lane == k) ri = xk;
-        else if (lane < k) ri -= M[k * n + lane] * xk;
+        if (lane == k)
+            ri = xk;
+        else if (lane < k)
+            ri = fma(-M[k * n + lane], xk, ri);
     }
     if (lane < n) W.r[lane] = ri;
     __syncwarp();
