@@ -22,6 +22,7 @@
 #include "fft.cuh"
 #include "gf_internal.cuh"
 #include "conv_fft.cuh"
+#include "warp_fft.cuh"
 
 namespace {
 
@@ -216,6 +217,120 @@ __global__ void __launch_bounds__(ROW_THREADS) k_fft_rows_inv(FFTArgs f, RowInvI
     if (a.work && threadIdx.x == 0) atomicAdd(&a.work[PROF_CONV], (unsigned long long)f.flops_row);
 }
 
+// ---------------------------------------------------------- warp row passes
+// For Nx = 32 M with M in the WarpFFTFactor list the row passes use one warp
+// per pair of rows and the register FFT of warp_fft.cuh: no block barrier
+// between stages, every input load of a lane issued before the first
+// butterfly.  The CTA's four warps share the padded twiddle table; each warp
+// has an Nx-element buffer to bring its result into natural order (and, in the
+// forward pass, to pair Z[k] with Z[Nx - k] for the unpacking).
+constexpr int WROW_WARPS = 4;
+
+template <int M>
+__global__ void __launch_bounds__(WROW_WARPS * 32) k_fft_rows_fwd_w(FFTArgs f, RowIO io, PassArgs a)
+{
+    pdl_entry();
+    constexpr int N = 32 * M, Kx = N / 2 + 1;
+    extern __shared__ __align__(16) float2 sm[];
+    const int p = blockIdx.y;
+    if (a.lm && a.lm[p / io.nchan].phase != a.phase) return;
+    float2* tws = sm;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) tws[warp_fft_pad(t)] = f.tw_x[t];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int y0 = 2 * (blockIdx.x * WROW_WARPS + warp), y1 = y0 + 1;
+    if (y0 >= io.out_rows) return;
+    const float* in = io.in + (long long)p * io.in_stride;
+    float2 v[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const int x = l + 32 * j;
+        const bool cx = x < io.width;
+        const float va = (cx && y0 < io.rows) ? in[(long long)y0 * io.ld + x] : 0.0f;
+        const float vb = (cx && y1 < io.rows) ? in[(long long)y1 * io.ld + x] : 0.0f;
+        v[j] = make_float2(va, vb);
+    }
+    warp_fft<M, false>(v, tws);
+    float2* z = sm + warp_fft_table_len(N) + warp * N;
+    const int br = bitrev5(l);
+#pragma unroll
+    for (int k2 = 0; k2 < M; ++k2) z[k2 + M * br] = v[k2];
+    __syncwarp();
+    float2* out = io.spec + (long long)p * io.spec_stride;
+    for (int k = l; k < Kx; k += 32) {
+        const float2 zk = z[k], zm = cconj(z[(N - k) % N]);
+        const float2 s = cadd(zk, zm), d = csub(zk, zm);
+        // A = (Z[k] + conj Z[N-k]) / 2,  B = (Z[k] - conj Z[N-k]) / (2i)
+        out[(long long)y0 * Kx + k] = make_float2(0.5f * s.x, 0.5f * s.y);
+        if (y1 < io.out_rows) out[(long long)y1 * Kx + k] = make_float2(0.5f * d.y, -0.5f * d.x);
+    }
+    if (a.work && l == 0) atomicAdd(&a.work[PROF_CONV], (unsigned long long)f.flops_row);
+}
+
+template <int M>
+__global__ void __launch_bounds__(WROW_WARPS * 32) k_fft_rows_inv_w(FFTArgs f, RowInvIO io, PassArgs a)
+{
+    pdl_entry();
+    constexpr int N = 32 * M, Kx = N / 2 + 1;
+    extern __shared__ __align__(16) float2 sm[];
+    const int p = blockIdx.y;
+    if (a.lm && a.lm[p / io.nchan].phase != a.phase) return;
+    float2* tws = sm;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) tws[warp_fft_pad(t)] = f.tw_x[t];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int i0 = 2 * (blockIdx.x * WROW_WARPS + warp), i1 = i0 + 1;
+    if (i0 >= io.H) return;
+    const bool has1 = i1 < io.H;
+    const float2* spec = io.spec + (long long)p * io.spec_stride;
+    const float2* sa = spec + (long long)(io.row0 + i0) * Kx;
+    const float2* sb = spec + (long long)(io.row0 + i1) * Kx;
+    float2 v[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const int k = l + 32 * j;
+        float2 A, Bv;
+        if (k < Kx) {
+            A = sa[k];
+            Bv = has1 ? sb[k] : make_float2(0.f, 0.f);
+        } else {
+            A = cconj(sa[N - k]);
+            Bv = has1 ? cconj(sb[N - k]) : make_float2(0.f, 0.f);
+        }
+        v[j] = make_float2(A.x - Bv.y, A.y + Bv.x);  // A + i B
+    }
+    warp_fft<M, true>(v, tws);
+    float2* z = sm + warp_fft_table_len(N) + warp * N;
+    const int br = bitrev5(l);
+#pragma unroll
+    for (int k2 = 0; k2 < M; ++k2) z[k2 + M * br] = v[k2];
+    __syncwarp();
+    float* out = io.out + (long long)p * io.out_stride;
+    for (int j = l; j < io.W; j += 32) {
+        const float2 w = z[io.col0 + j];
+        out[(long long)i0 * io.W + j] = w.x;
+        if (has1) out[(long long)i1 * io.W + j] = w.y;
+    }
+    if (a.work && l == 0) atomicAdd(&a.work[PROF_CONV], (unsigned long long)f.flops_row);
+}
+
+size_t warp_row_smem(int N) { return sizeof(float2) * ((size_t)warp_fft_table_len(N) + (size_t)WROW_WARPS * N); }
+
+// the warp row kernels exist for these Nx
+#define WARP_FFT_CASES(X) X(3) X(4) X(5) X(6) X(8) X(9) X(10) X(12) X(15) X(16) X(18) X(20)
+
+bool warp_rows_ok(int Nx)
+{
+    if (Nx % 32 != 0) return false;
+    switch (Nx / 32) {
+#define WF_CASE(M_) case M_:
+        WARP_FFT_CASES(WF_CASE)
+#undef WF_CASE
+        return true;
+    default: return false;
+    }
+}
+
 }  // namespace
 
 size_t fft_row_smem(int Nx) { return sizeof(float2) * 3 * (size_t)Nx; }
@@ -239,6 +354,54 @@ static cudaError_t optin_all(const FFTArgs& f)
     if (e == cudaSuccess)
         e = ensure_smem_optin((const void*)k_fft_cols, (int)fft_col_smem(f.Ny, f.cpc), o3);
     return e;
+}
+
+// forward / inverse row pass over `pairs` row pairs of each of nprob problems:
+// the warp kernels where Nx allows, else the shared-memory Stockham kernels
+static cudaError_t rows_fwd(const FFTArgs& f, const RowIO& r, const PassArgs& a, int pairs,
+                            int nprob, cudaStream_t s)
+{
+    if (warp_rows_ok(f.Nx)) {
+        const dim3 grid((pairs + WROW_WARPS - 1) / WROW_WARPS, nprob);
+        switch (f.Nx / 32) {
+#define WF_CASE(M_)                                                                          \
+    case M_:                                                                                 \
+        GF_LAUNCH_PDL(k_fft_rows_fwd_w<M_>, grid, dim3(WROW_WARPS * 32), warp_row_smem(f.Nx), \
+                      s, f, r, a);                                                           \
+        break;
+            WARP_FFT_CASES(WF_CASE)
+#undef WF_CASE
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        GF_LAUNCH_PDL(k_fft_rows_fwd, dim3(pairs, nprob), dim3(ROW_THREADS), fft_row_smem(f.Nx), s,
+                      f, r, a);
+    }
+    GF_COUNT_LAUNCH();
+    return cudaSuccess;
+}
+
+static cudaError_t rows_inv(const FFTArgs& f, const RowInvIO& v, const PassArgs& a, int pairs,
+                            int nprob, cudaStream_t s)
+{
+    if (warp_rows_ok(f.Nx)) {
+        const dim3 grid((pairs + WROW_WARPS - 1) / WROW_WARPS, nprob);
+        switch (f.Nx / 32) {
+#define WF_CASE(M_)                                                                          \
+    case M_:                                                                                 \
+        GF_LAUNCH_PDL(k_fft_rows_inv_w<M_>, grid, dim3(WROW_WARPS * 32), warp_row_smem(f.Nx), \
+                      s, f, v, a);                                                           \
+        break;
+            WARP_FFT_CASES(WF_CASE)
+#undef WF_CASE
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        GF_LAUNCH_PDL(k_fft_rows_inv, dim3(pairs, nprob), dim3(ROW_THREADS), fft_row_smem(f.Nx), s,
+                      f, v, a);
+    }
+    GF_COUNT_LAUNCH();
+    return cudaSuccess;
 }
 
 cudaError_t launch_psf_wrap(const FFTArgs& f, int count, const StampInfo* st, const float* psf,
@@ -273,8 +436,8 @@ cudaError_t launch_fft_psf(const FFTArgs& f, int count, const StampInfo* st, con
     r.spec_stride = (long long)f.Ny * Kx;
     r.out_rows = f.Ny;
     r.nchan = 1;
-    GF_LAUNCH_PDL(k_fft_rows_fwd, dim3(dim3((f.Ny + 1) / 2, count)), dim3(ROW_THREADS), fft_row_smem(f.Nx), s, f, r, none);
-    GF_COUNT_LAUNCH();
+    e = rows_fwd(f, r, none, (f.Ny + 1) / 2, count, s);
+    if (e != cudaSuccess) return e;
     ColIO c;
     c.spec = f.hhat;
     c.spec_stride = (long long)f.Ny * Kx;
@@ -306,8 +469,8 @@ cudaError_t launch_conv_fft(const PassArgs& a, const FFTArgs& f, float2* spec, c
     r.spec_stride = (long long)s0.He * Kx;
     r.out_rows = s0.He;
     r.nchan = a.nchan;
-    GF_LAUNCH_PDL(k_fft_rows_fwd, dim3(dim3((s0.He + 1) / 2, nprob)), dim3(ROW_THREADS), fft_row_smem(f.Nx), s, f, r, a);
-    GF_COUNT_LAUNCH();
+    e = rows_fwd(f, r, a, (s0.He + 1) / 2, nprob, s);
+    if (e != cudaSuccess) return e;
     ColIO c;
     c.spec = spec;
     c.spec_stride = (long long)s0.He * Kx;
@@ -332,7 +495,7 @@ cudaError_t launch_conv_fft(const PassArgs& a, const FFTArgs& f, float2* spec, c
     v.out = a.y;
     v.out_stride = (long long)s0.H * s0.W;
     v.nchan = a.nchan;
-    GF_LAUNCH_PDL(k_fft_rows_inv, dim3(dim3((s0.H + 1) / 2, nprob)), dim3(ROW_THREADS), fft_row_smem(f.Nx), s, f, v, a);
-    GF_COUNT_LAUNCH();
+    e = rows_inv(f, v, a, (s0.H + 1) / 2, nprob, s);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -386,3 +386,21 @@ def test_lm_ladder_batch_equals_single_rung(gf):
         assert np.array_equal(pk, p1), ladder
         assert [(r["chi2"], r["iters"], r["accepted"], r["status"]) for r in rk] == \
             [(r["chi2"], r["iters"], r["accepted"], r["status"]) for r in r1]
+
+
+# Row lengths Nx = 32 M take the warp-register row FFT (one warp per pair of
+# rows); every supported M, with an odd number of grid and output rows so that
+# the last pair has one row.
+@pytest.mark.parametrize("M", [3, 4, 5, 6, 8, 9, 10, 12, 15, 16, 18, 20])
+def test_convolve_fft_warp_rows(gf, M):
+    P = 9
+    c = (P - 1) // 2
+    W = 32 * M - 2 * c          # extended width exactly 32 M
+    H = 23                      # extended height 31: odd
+    rng = np.random.default_rng(M)
+    ext = rng.uniform(0.0, 2.0, (H + 2 * c, W + 2 * c)).astype(np.float32)
+    psf = synth.random_psf(P, M)
+    d = gf.make_desc(H, W, P, [synth.SERSIC], conv_method=gf.CONV_FFT)
+    g = gf.convolve(d, cuda(ext), cuda(psf)).cpu().numpy()
+    o = oracle.convolve_direct(ext.astype(np.float64), psf.astype(np.float64))
+    assert_pix_close(g, o, rel=1e-5, floor=FFT_FLOOR, what=f"fft conv 32x{M} rows")
