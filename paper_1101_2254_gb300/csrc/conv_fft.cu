@@ -381,6 +381,23 @@ static cudaError_t rows_fwd(const FFTArgs& f, const RowIO& r, const PassArgs& a,
     return cudaSuccess;
 }
 
+// column pass (mode 1: transform, PSF product, inverse; mode 0: forward only)
+static cudaError_t cols_pass(const FFTArgs& f, const ColIO& c, const PassArgs& a, int nprob,
+                             int mode, cudaStream_t s)
+{
+    const int Kx = f.Nx / 2 + 1;
+    // fewer columns per CTA until the pass has four CTAs per SM (the column
+    // pass waits on L2 loads: more, smaller CTAs keep more of them in flight)
+    FFTArgs fc = f;
+    if (mode == 1)
+        while (fc.cpc > 2 && (long long)nprob * ((Kx + fc.cpc - 1) / fc.cpc) < 4 * 152) fc.cpc /= 2;
+    fc.flops_col = f.flops_col * (float)fc.cpc / (float)f.cpc;
+    GF_LAUNCH_PDL(k_fft_cols, dim3((Kx + fc.cpc - 1) / fc.cpc, nprob), dim3(COL_THREADS),
+                  fft_col_smem(fc.Ny, fc.cpc), s, fc, c, a, mode);
+    GF_COUNT_LAUNCH();
+    return cudaSuccess;
+}
+
 static cudaError_t rows_inv(const FFTArgs& f, const RowInvIO& v, const PassArgs& a, int pairs,
                             int nprob, cudaStream_t s)
 {
@@ -445,8 +462,8 @@ cudaError_t launch_fft_psf(const FFTArgs& f, int count, const StampInfo* st, con
     c.row0 = 0;
     c.nrows_out = f.Ny;
     c.nchan = 1;
-    GF_LAUNCH_PDL(k_fft_cols, dim3(dim3((Kx + f.cpc - 1) / f.cpc, count)), dim3(COL_THREADS), fft_col_smem(f.Ny, f.cpc), s, f, c, none, 0);
-    GF_COUNT_LAUNCH();
+    e = cols_pass(f, c, none, count, 0, s);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -478,13 +495,8 @@ cudaError_t launch_conv_fft(const PassArgs& a, const FFTArgs& f, float2* spec, c
     c.row0 = s0.c;
     c.nrows_out = s0.H;
     c.nchan = a.nchan;
-    // fewer columns per CTA until the pass has four CTAs per SM (the column
-    // pass waits on L2 loads: more, smaller CTAs keep more of them in flight)
-    FFTArgs fc = f;
-    while (fc.cpc > 2 && (long long)nprob * ((Kx + fc.cpc - 1) / fc.cpc) < 4 * 152) fc.cpc /= 2;
-    fc.flops_col = f.flops_col * (float)fc.cpc / (float)f.cpc;
-    GF_LAUNCH_PDL(k_fft_cols, dim3(dim3((Kx + fc.cpc - 1) / fc.cpc, nprob)), dim3(COL_THREADS), fft_col_smem(fc.Ny, fc.cpc), s, fc, c, a, 1);
-    GF_COUNT_LAUNCH();
+    e = cols_pass(f, c, a, nprob, 1, s);
+    if (e != cudaSuccess) return e;
     RowInvIO v;
     v.spec = spec;
     v.spec_stride = (long long)s0.He * Kx;

@@ -52,23 +52,23 @@ __device__ __forceinline__ void load_channels(Channel* dst, const Channel* src, 
 }
 
 // Work item = (channel, block of MODEL_THREADS grid pixels of a listed stamp).
-__global__ void __launch_bounds__(MODEL_THREADS) k_model(PassArgs a)
+__device__ __forceinline__ void body_model(const PassArgs& a, int vb, int vg)
 {
-    pdl_entry();
     __shared__ __align__(16) Channel ch;
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_MODEL * (a.count + 1);
     const int tot = pre[n];
     const long long items = (long long)tot * a.nchan;
     int hint = -1, cur_b = -1, cur_k = -1;
-    const long long chunk = (items + gridDim.x - 1) / gridDim.x;
-    const long long it0 = (long long)blockIdx.x * chunk, it1 = min(items, it0 + chunk);
+    StampInfo st;
+    const long long chunk = (items + vg - 1) / vg;
+    const long long it0 = (long long)vb * chunk, it1 = min(items, it0 + chunk);
     for (long long it = it0; it < it1; ++it) {
         const int k = (int)(it / tot), blk = (int)(it - (long long)k * tot);
         const int li = wl_locate(pre, n, blk, hint);
         const int b = a.wl.ids[li];
-        const StampInfo st = a.st[b];
         if (b != cur_b || k != cur_k) {
+            if (b != cur_b) st = a.st[b];  // the stamp's geometry, kept while it lasts
             __syncthreads();
             load_channel(&ch, &a.chan[(long long)b * a.chan_stride + k]);
             __syncthreads();
@@ -97,9 +97,8 @@ __global__ void __launch_bounds__(MODEL_THREADS) k_model(PassArgs a)
 }
 
 // Work item = (channel, OS_WARPS pixels of a listed stamp's oversampling block).
-__global__ void __launch_bounds__(OS_WARPS * 32) k_model_os(PassArgs a)
+__device__ __forceinline__ void body_model_os(const PassArgs& a, int vb, int vg)
 {
-    pdl_entry();
     __shared__ __align__(16) Channel ch;
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_OS * (a.count + 1);
@@ -107,8 +106,8 @@ __global__ void __launch_bounds__(OS_WARPS * 32) k_model_os(PassArgs a)
     const long long items = (long long)tot * a.nchan;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int hint = -1, cur_b = -1, cur_k = -1;
-    const long long chunk = (items + gridDim.x - 1) / gridDim.x;
-    const long long it0 = (long long)blockIdx.x * chunk, it1 = min(items, it0 + chunk);
+    const long long chunk = (items + vg - 1) / vg;
+    const long long it0 = (long long)vb * chunk, it1 = min(items, it0 + chunk);
     for (long long it = it0; it < it1; ++it) {
         const int k = (int)(it / tot), blk = (int)(it - (long long)k * tot);
         const int li = wl_locate(pre, n, blk, hint);
@@ -166,17 +165,16 @@ __device__ __forceinline__ void comp_base(const Channel& c0, float* base, float 
 }
 
 // Work item = block of MODEL_THREADS grid pixels of a listed stamp (all channels).
-__global__ void __launch_bounds__(MODEL_THREADS) k_model_jac(PassArgs a)
+__device__ __forceinline__ void body_model_jac(const PassArgs& a, int vb, int vg)
 {
-    pdl_entry();
     __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_MODEL * (a.count + 1);
     const int tot = pre[n];
     const int nch = a.nchan;
     int hint = -1, cur_b = -1;
-    const int chunk = (tot + gridDim.x - 1) / gridDim.x;
-    const int it0 = blockIdx.x * chunk, it1 = min(tot, it0 + chunk);
+    const int chunk = (tot + vg - 1) / vg;
+    const int it0 = vb * chunk, it1 = min(tot, it0 + chunk);
     for (int blk = it0; blk < it1; ++blk) {
         const int li = wl_locate(pre, n, blk, hint);
         const int b = a.wl.ids[li];
@@ -216,9 +214,8 @@ __global__ void __launch_bounds__(MODEL_THREADS) k_model_jac(PassArgs a)
 
 // Work item = OS_WARPS pixels of a listed stamp's oversampling block (all
 // channels); lanes take sub-samples, each lane keeps every channel's sum.
-__global__ void __launch_bounds__(OS_WARPS * 32) k_model_os_jac(PassArgs a)
+__device__ __forceinline__ void body_model_os_jac(const PassArgs& a, int vb, int vg)
 {
-    pdl_entry();
     __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_OS * (a.count + 1);
@@ -226,8 +223,8 @@ __global__ void __launch_bounds__(OS_WARPS * 32) k_model_os_jac(PassArgs a)
     const int nch = a.nchan;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int hint = -1, cur_b = -1;
-    const int chunk = (tot + gridDim.x - 1) / gridDim.x;
-    const int it0 = blockIdx.x * chunk, it1 = min(tot, it0 + chunk);
+    const int chunk = (tot + vg - 1) / vg;
+    const int it0 = vb * chunk, it1 = min(tot, it0 + chunk);
     for (int blk = it0; blk < it1; ++blk) {
         const int li = wl_locate(pre, n, blk, hint);
         const int b = a.wl.ids[li];
@@ -272,38 +269,71 @@ __global__ void __launch_bounds__(OS_WARPS * 32) k_model_os_jac(PassArgs a)
     }
 }
 
+// One launch per pass for all of step 1: blocks [0, g_os) evaluate the
+// oversampled blocks (the heavy items, scheduled first), the others the plain
+// grid pixels, so that the two kinds of work overlap instead of running as two
+// dependent launches.  PIX: 0 one channel per item, 1 every channel of a
+// Jacobian pass per pixel.  OS: 0 none, 1 a warp per (channel, block pixel),
+// 2 a warp per block pixel with every channel.
+template <int PIX, int OS>
+__global__ void __launch_bounds__(MODEL_THREADS) k_model_pass(PassArgs a, int g_os)
+{
+    static_assert(MODEL_THREADS == OS_WARPS * 32, "one block size for both kinds of item");
+    pdl_entry();
+    if (OS != 0 && (int)blockIdx.x < g_os) {
+        if (OS == 1)
+            body_model_os(a, blockIdx.x, g_os);
+        else
+            body_model_os_jac(a, blockIdx.x, g_os);
+        return;
+    }
+    const int vb = blockIdx.x - (OS != 0 ? g_os : 0), vg = gridDim.x - (OS != 0 ? g_os : 0);
+    if (PIX == 0)
+        body_model(a, vb, vg);
+    else
+        body_model_jac(a, vb, vg);
+}
+
+template <int PIX, int OS>
+cudaError_t launch_pass(const PassArgs& a, int g_pix, int g_os, cudaStream_t s)
+{
+    GF_LAUNCH_PDL((k_model_pass<PIX, OS>), dim3(g_pix + g_os), dim3(MODEL_THREADS), 0, s, a, g_os);
+    GF_COUNT_LAUNCH();
+    return cudaSuccess;
+}
+
 }  // namespace
+
+// The oversampled blocks share the plain pixels' launch when they are few (one
+// large stamp: the two kinds of work then overlap); many of them (batches of
+// stamps) take a launch of their own, so that the plain pixels keep the lower
+// register count and full occupancy.
+constexpr long long MERGE_OS_MAX = 152LL * 8;
 
 cudaError_t launch_model(const PassArgs& a, cudaStream_t s)
 {
+    cudaError_t e;
     if (a.jac_pass && a.nchan > 1) {  // a Jacobian pass: all channels of a pixel together
         const int cap[2] = {152 * 16, 152 * 8};
-        if (a.maxitems[WK_MODEL] > 0) {
-            const int g = (int)std::min<long long>(a.maxitems[WK_MODEL] / a.nchan, cap[0]);
-            GF_LAUNCH_PDL(k_model_jac, dim3(std::max(g, 1)), dim3(MODEL_THREADS), 0, s, a);
-            GF_COUNT_LAUNCH();
-        }
+        const int g_pix = a.maxitems[WK_MODEL] > 0
+                              ? std::max(1, (int)std::min<long long>(a.maxitems[WK_MODEL] / a.nchan, cap[0]))
+                              : 0;
         // the oversampled blocks: all channels per warp when there are enough
         // block pixels to fill the GPU (many stamps), else a warp per channel
         // and pixel (one large stamp)
         const long long os_groups = a.maxitems[WK_OS] / a.nchan;
         if (os_groups * OS_WARPS >= 152LL * 32) {
-            const int g = (int)std::min<long long>(os_groups, cap[1]);
-            GF_LAUNCH_PDL(k_model_os_jac, dim3(std::max(g, 1)), dim3(OS_WARPS * 32), 0, s, a);
-            GF_COUNT_LAUNCH();
-        } else if (a.maxitems[WK_OS] > 0) {
-            GF_LAUNCH_PDL(k_model_os, dim3(a.grid[WK_OS]), dim3(OS_WARPS * 32), 0, s, a);
-            GF_COUNT_LAUNCH();
+            if (g_pix > 0 && (e = launch_pass<1, 0>(a, g_pix, 0, s)) != cudaSuccess) return e;
+            return launch_pass<1, 2>(a, 0, std::max(1, (int)std::min<long long>(os_groups, cap[1])), s);
         }
-        return cudaGetLastError();
+        if (a.maxitems[WK_OS] == 0) return g_pix > 0 ? launch_pass<1, 0>(a, g_pix, 0, s) : cudaSuccess;
+        if (a.grid[WK_OS] <= MERGE_OS_MAX) return launch_pass<1, 1>(a, g_pix, a.grid[WK_OS], s);
+        if (g_pix > 0 && (e = launch_pass<1, 0>(a, g_pix, 0, s)) != cudaSuccess) return e;
+        return launch_pass<0, 1>(a, 0, a.grid[WK_OS], s);
     }
-    if (a.maxitems[WK_MODEL] > 0) {
-        GF_LAUNCH_PDL(k_model, dim3(a.grid[WK_MODEL]), dim3(MODEL_THREADS), 0, s, a);
-        GF_COUNT_LAUNCH();
-    }
-    if (a.maxitems[WK_OS] > 0) {
-        GF_LAUNCH_PDL(k_model_os, dim3(a.grid[WK_OS]), dim3(OS_WARPS * 32), 0, s, a);
-        GF_COUNT_LAUNCH();
-    }
-    return cudaGetLastError();
+    const int g_pix = a.maxitems[WK_MODEL] > 0 ? a.grid[WK_MODEL] : 0;
+    if (a.maxitems[WK_OS] == 0) return g_pix > 0 ? launch_pass<0, 0>(a, g_pix, 0, s) : cudaSuccess;
+    if (a.grid[WK_OS] <= MERGE_OS_MAX) return launch_pass<0, 1>(a, g_pix, a.grid[WK_OS], s);
+    if (g_pix > 0 && (e = launch_pass<0, 0>(a, g_pix, 0, s)) != cudaSuccess) return e;
+    return launch_pass<0, 1>(a, 0, a.grid[WK_OS], s);
 }

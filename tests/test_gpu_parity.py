@@ -404,3 +404,19 @@ def test_convolve_fft_warp_rows(gf, M):
     g = gf.convolve(d, cuda(ext), cuda(psf)).cpu().numpy()
     o = oracle.convolve_direct(ext.astype(np.float64), psf.astype(np.float64))
     assert_pix_close(g, o, rel=1e-5, floor=FFT_FLOOR, what=f"fft conv 32x{M} rows")
+
+
+# Column lengths Ny = 32 M with the Stockham column pass (widths give a ragged
+# last group of spectrum columns).
+@pytest.mark.parametrize("M,W", [(3, 20), (5, 41), (9, 7), (12, 64), (18, 33), (20, 90)])
+def test_convolve_fft_warp_cols(gf, M, W):
+    P = 11
+    c = (P - 1) // 2
+    H = 32 * M - 2 * c          # extended height exactly 32 M
+    rng = np.random.default_rng(100 + M)
+    ext = rng.uniform(0.0, 2.0, (H + 2 * c, W + 2 * c)).astype(np.float32)
+    psf = synth.random_psf(P, 7 * M)
+    d = gf.make_desc(H, W, P, [synth.SERSIC], conv_method=gf.CONV_FFT)
+    g = gf.convolve(d, cuda(ext), cuda(psf)).cpu().numpy()
+    o = oracle.convolve_direct(ext.astype(np.float64), psf.astype(np.float64))
+    assert_pix_close(g, o, rel=1e-5, floor=FFT_FLOOR, what=f"fft conv 32x{M} columns")
