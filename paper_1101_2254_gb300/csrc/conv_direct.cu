@@ -6,16 +6,21 @@
 //
 // One CTA computes a 32 x TX output tile of one channel: TX = 64 (4 warps) or
 // TX = 32 (2 warps), chosen per stamp (the two kinds of work item).  The
-// flipped PSF (rows padded with zeros to a multiple of 4 taps) and the
-// (32+P-1) x (TX+P4) halo tile of the channel grid are staged in shared memory.
-// A warp covers 16 x 32 outputs with lanes arranged 4 (rows) x 8 (columns); a
-// thread owns a 4 x 4 block.  A warp whose 16 x 32 quadrant lies wholly outside
-// the stamp skips the taps (its issue slots go to the SM's other CTAs).  For each tap row v and each group of 4 taps, a thread
-// issues one broadcast 16-byte load of the taps and one 16-byte load of the
-// next 4 grid values per output row, then 64 FMAs: 5 shared loads per 64 FMAs.
-// Eight lanes of a quarter-warp read 128 contiguous bytes, so the grid loads
-// are free of bank conflicts; the tap loads are broadcasts.
+// flipped PSF (rows padded with zeros to P4, a multiple of 4 taps) and the
+// (32+P-1) x SW halo tile of the channel grid are staged in shared memory.
+// A warp covers 16 x 32 outputs: lane 8 cg + rl owns the 8 contiguous columns
+// 8 cg .. 8 cg + 7 of rows rl and rl + 8.  For each tap row and group of 4
+// taps a thread holds, per row, a sliding window of 12 grid values (one new
+// 16-byte load per group) and the 4 taps (one broadcast 16-byte load), and
+// issues 2 x 8 x 4 = 64 FMAs: 3 shared loads per 64 FMAs.
+// The eight lanes of a quarter-warp read the same columns of eight
+// consecutive rows; with the tile's row stride SW = 4 (mod 8) floats their
+// 16-byte reads fall in distinct bank groups, so a load takes the minimum four
+// wavefronts per warp and shared-memory traffic stays at half the FMA rate.
+// The outputs go back through shared memory (row stride TX + 1, conflict-free)
+// so that the global stores are coalesced rows.
 //
+// Each output accumulates its taps in the order v, then u, as a chain of FMAs.
 // The work is bound by the FP32 FMA pipe (2 P^2 flop per output pixel against
 // 8 bytes of HBM traffic), not by HBM.
 #include "gf_internal.cuh"
@@ -24,39 +29,69 @@ namespace {
 
 constexpr int TY = CONV_TY;
 
-// One tap row v: acc += sum_u k[v][u] E[r0 + v + r][c0 + o + u].  With the tap
-// count P4K known at compile time (PSFs up to 33 pixels) the loop over tap
-// groups unrolls completely and the sliding 8-value window costs no register
-// moves; otherwise (P4K = 0) it runs over the runtime P4.
-template <int P4K>
-__device__ __forceinline__ void tap_row(float (&acc)[4][4], const float* kr, const float* er, int SW,
-                                        int P4)
+// row stride of the staged grid tile: >= TX + P4 and 4 (mod 8)
+__host__ __device__ __forceinline__ int conv_sw(int TX, int P4)
 {
-    float4 w0[4];
+    const int w = TX + P4;  // a multiple of 4
+    return (w % 8 == 0) ? w + 4 : w;
+}
+
+constexpr int RPT = 2;  // rows per thread (rows rl + 8 i)
+
+// acc[o] += sum_t kk[t] win[o + t] for the 8 outputs of one row
+__device__ __forceinline__ void fma_row(float (&acc)[8], const float4 kk, const float (&win)[12])
+{
 #pragma unroll
-    for (int r = 0; r < 4; ++r) w0[r] = *reinterpret_cast<const float4*>(er + r * SW);
-    constexpr int PU = P4K > 0 ? P4K : 4;
+    for (int o = 0; o < 8; ++o) {
+        float x = acc[o];
+        x = fmaf(kk.x, win[o], x);
+        x = fmaf(kk.y, win[o + 1], x);
+        x = fmaf(kk.z, win[o + 2], x);
+        x = fmaf(kk.w, win[o + 3], x);
+        acc[o] = x;
+    }
+}
+
+// One tap row v for the thread's RPT rows: er0 points at the first row's first
+// window column.  With the tap count P4K known at compile time (PSFs up to
+// 35 pixels) the loop over tap groups unrolls completely and the sliding
+// window costs no register moves; otherwise (P4K = 0) it runs over P4.
+template <int P4K>
+__device__ __forceinline__ void tap_row(float (&acc)[RPT][8], const float* kr, const float* er0,
+                                        int SW, int P4)
+{
+    float win[RPT][12];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const float* er = er0 + i * 8 * SW;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float4 t = *reinterpret_cast<const float4*>(er + 4 * q);
+            win[i][4 * q] = t.x;
+            win[i][4 * q + 1] = t.y;
+            win[i][4 * q + 2] = t.z;
+            win[i][4 * q + 3] = t.w;
+        }
+    }
     const int pend = P4K > 0 ? P4K : P4;
-#pragma unroll(P4K > 0 ? P4K / 4 : 2)
+#pragma unroll(P4K > 0 ? P4K / 4 : 1)
     for (int m = 0; m < pend; m += 4) {
         const float4 kk = *reinterpret_cast<const float4*>(kr + m);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float4 w1 = *reinterpret_cast<const float4*>(er + r * SW + m + 4);
-            const float win[8] = {w0[r].x, w0[r].y, w0[r].z, w0[r].w, w1.x, w1.y, w1.z, w1.w};
+        for (int i = 0; i < RPT; ++i) fma_row(acc[i], kk, win[i]);
+        if (m + 4 < pend) {
 #pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                float x = acc[r][o];
-                x = fmaf(kk.x, win[o], x);
-                x = fmaf(kk.y, win[o + 1], x);
-                x = fmaf(kk.z, win[o + 2], x);
-                x = fmaf(kk.w, win[o + 3], x);
-                acc[r][o] = x;
+            for (int i = 0; i < RPT; ++i) {
+                const float4 t = *reinterpret_cast<const float4*>(er0 + i * 8 * SW + m + 12);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) win[i][q] = win[i][q + 4];
+                win[i][8] = t.x;
+                win[i][9] = t.y;
+                win[i][10] = t.z;
+                win[i][11] = t.w;
             }
-            w0[r] = w1;
         }
     }
-    (void)PU;
 }
 
 // Work item = (channel, output tile of a listed stamp of this tile width).
@@ -71,13 +106,14 @@ __global__ void __launch_bounds__(TX * 2) k_conv_direct(PassArgs a)
     const int tot = pre[n];
     const long long items = (long long)tot * a.nchan;
     const int P = a.P, P4 = (P + 3) & ~3;
-    const int SW = TX + P4, SH = TY + P - 1;
+    const int SW = conv_sw(TX, P4), SH = TY + P - 1;
     float* ks = smem;               // P x P4 flipped taps
     float* es = smem + P * P4;      // SH x SW grid tile (P*P4 is a multiple of 4)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rl = lane & 7, cg = lane >> 3;
     const int wr0 = (warp / WX) * 16, wc0 = (warp % WX) * 32;
-    const int r0 = wr0 + (lane >> 3) * 4;
-    const int c0 = wc0 + (lane & 7) * 4;
+    const int r0 = wr0 + rl;       // the thread's first row in the tile
+    const int c0 = wc0 + 8 * cg;   // the thread's first column in the tile
     int hint = -1, psf_b = -1;
     const long long chunk = (items + gridDim.x - 1) / gridDim.x;
     const long long it0 = (long long)blockIdx.x * chunk, it1 = min(items, it0 + chunk);
@@ -98,39 +134,57 @@ __global__ void __launch_bounds__(TX * 2) k_conv_direct(PassArgs a)
             }
             psf_b = b;
         }
+        // the halo tile, a warp per row (coalesced, no index division), four
+        // loads per lane in flight
         const float* E = a.ext + ext_index(st, a.nchan, ch);
-        for (int idx = threadIdx.x; idx < SH * SW; idx += NT) {
-            const int r = idx / SW, col = idx - r * SW;
-            const int gy = ty0 + r, gx = tx0 + col;
-            es[idx] = (gy < st.He && gx < st.We) ? __ldg(&E[(long long)gy * st.We + gx]) : 0.0f;
+        for (int r = warp; r < SH; r += NT / 32) {
+            const int gy = ty0 + r;
+            const bool row_in = gy < st.He;
+            const float* Er = E + (long long)gy * st.We;
+            float* er = es + r * SW;
+            for (int c0_ = lane; c0_ < SW; c0_ += 128) {
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int col = c0_ + 32 * u, gx = tx0 + col;
+                    v[u] = (row_in && col < SW && gx < st.We) ? __ldg(&Er[gx]) : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (c0_ + 32 * u < SW) er[c0_ + 32 * u] = v[u];
+            }
         }
         __syncthreads();
 
-        if (ty0 + wr0 >= st.H || tx0 + wc0 >= st.W) continue;  // quadrant outside the stamp
-        float acc[4][4];
+        // the warp's block meets the stamp
+        const bool active = ty0 + wr0 < st.H && tx0 + wc0 < st.W;
+        float acc[RPT][8];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int i = 0; i < RPT; ++i)
 #pragma unroll
-            for (int o = 0; o < 4; ++o) acc[r][o] = 0.0f;
+            for (int o = 0; o < 8; ++o) acc[i][o] = 0.0f;
+        if (active)
+            for (int v = 0; v < P; ++v)
+                tap_row<P4K>(acc, ks + v * P4, es + (r0 + v) * SW + c0, SW, P4);
 
-        for (int v = 0; v < P; ++v)
-            tap_row<P4K>(acc, ks + v * P4, es + (r0 + v) * SW + c0, SW, P4);
-
-        if (a.work && (lane | (warp / WX)) == 0) {  // lane 0 of the first warp of each column
-            const unsigned long long rows = (unsigned long long)min(TY, st.H - ty0);
+        if (active && a.work && lane == 0) {
+            const unsigned long long rows = (unsigned long long)min(16, st.H - ty0 - wr0);
             const unsigned long long cols = (unsigned long long)min(32, st.W - tx0 - wc0);
             atomicAdd(&a.work[PROF_CONV], 2ull * (unsigned long long)P * P * rows * cols);
         }
+        // the tile through shared memory (row stride TX + 1), then coalesced rows
+        __syncthreads();
+        constexpr int OS = TX + 1;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+#pragma unroll
+            for (int o = 0; o < 8; ++o) es[(r0 + 8 * i) * OS + c0 + o] = acc[i][o];
+        __syncthreads();
         float* Y = a.y + y_index(st, a.nchan, ch);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int oy = ty0 + r0 + r;
-            if (oy >= st.H) continue;
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                const int ox = tx0 + c0 + o;
-                if (ox < st.W) Y[(long long)oy * st.W + ox] = acc[r][o];
-            }
+        const int rows = min(TY, st.H - ty0), cols = min(TX, st.W - tx0);
+        for (int idx = threadIdx.x; idx < TY * TX; idx += NT) {
+            const int r = idx / TX, c = idx - r * TX;
+            if (r < rows && c < cols) Y[(long long)(ty0 + r) * st.W + tx0 + c] = es[r * OS + c];
         }
     }
 }
@@ -143,7 +197,7 @@ template <int TX>
 size_t conv_smem(int P)
 {
     const int P4 = (P + 3) & ~3;
-    return sizeof(float) * ((size_t)P * P4 + (size_t)(TY + P - 1) * (TX + P4));
+    return sizeof(float) * ((size_t)P * P4 + (size_t)(TY + P - 1) * conv_sw(TX, P4));
 }
 
 size_t conv_direct_smem(int P) { return conv_smem<64>(P); }
