@@ -14,6 +14,8 @@
 // partials of the stamp in block order.
 #include <math.h>
 
+#include <algorithm>
+
 #include "gf_internal.cuh"
 
 namespace {
@@ -211,35 +213,55 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_chi2(PassArgs a)
     const float* Y = a.y + y_index(st, a.nchan, 0);
     CSum acc = {0.0f, 0.0f};
     const long long base = (long long)local * RED_PIX;
-    // every load of the item is issued before the first use (3 x RED_CHUNKS
-    // independent loads per thread in flight), then the pixels are summed in
-    // chunk order as before
-    float m[RED_CHUNKS], dv[RED_CHUNKS], sv[RED_CHUNKS];
+    // Thread t takes the RED_CHUNKS consecutive pixels base + RED_CHUNKS t + e
+    // and sums them in order e.  Where the stamp's arrays are 16-byte aligned
+    // and its pixel count a multiple of 4, the image, sigma and model values
+    // come in one 16-byte load each; otherwise by single loads.  The order of
+    // the sums is the same either way, so chi^2 does not depend on where a
+    // stamp sits in a batch.
+    static_assert(RED_CHUNKS == 4, "one float4 per thread and array");
+    const long long p0 = base + (long long)RED_CHUNKS * threadIdx.x;
     const bool has_img = a.img != nullptr;
+    float m[RED_CHUNKS], dv[RED_CHUNKS], sv[RED_CHUNKS];
+    const bool vec = ((st.pix_off | HW | y_index(st, a.nchan, 0)) & 3) == 0 && p0 < HW;
+    if (vec) {
+        const float4 y4 = __ldg(reinterpret_cast<const float4*>(Y + p0));
+        m[0] = y4.x; m[1] = y4.y; m[2] = y4.z; m[3] = y4.w;
+        if (has_img) {
+            const float4 d4 = __ldg(reinterpret_cast<const float4*>(img + p0));
+            const float4 s4 = __ldg(reinterpret_cast<const float4*>(sig + p0));
+            dv[0] = d4.x; dv[1] = d4.y; dv[2] = d4.z; dv[3] = d4.w;
+            sv[0] = s4.x; sv[1] = s4.y; sv[2] = s4.z; sv[3] = s4.w;
+        } else {
 #pragma unroll
-    for (int q = 0; q < RED_CHUNKS; ++q) {
-        const long long px = base + (long long)q * RED_THREADS + threadIdx.x;
-        const bool in = px < HW;
-        m[q] = in ? __ldg(&Y[px]) : 0.0f;
-        dv[q] = (in && has_img) ? __ldg(&img[px]) : 0.0f;
-        sv[q] = (in && has_img) ? __ldg(&sig[px]) : 0.0f;
+            for (int e = 0; e < RED_CHUNKS; ++e) dv[e] = sv[e] = 0.0f;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < RED_CHUNKS; ++e) {
+            const long long px = p0 + e;
+            const bool in = px < HW;
+            m[e] = in ? __ldg(&Y[px]) : 0.0f;
+            dv[e] = (in && has_img) ? __ldg(&img[px]) : 0.0f;
+            sv[e] = (in && has_img) ? __ldg(&sig[px]) : 0.0f;
+        }
     }
 #pragma unroll
-    for (int q = 0; q < RED_CHUNKS; ++q) {
-        const long long px = base + (long long)q * RED_THREADS + threadIdx.x;
-        m[q] = fmaf(ci.mw[0], m[q], msky);
+    for (int e = 0; e < RED_CHUNKS; ++e) {
+        const long long px = p0 + e;
+        m[e] = fmaf(ci.mw[0], m[e], msky);
         for (int k = 1; k < a.nchan; ++k)
-            if (px < HW) m[q] = fmaf(ci.mw[k], Y[(long long)k * HW + px], m[q]);
+            if (px < HW) m[e] = fmaf(ci.mw[k], Y[(long long)k * HW + px], m[e]);
     }
 #pragma unroll
-    for (int q = 0; q < RED_CHUNKS; ++q) {
-        const long long px = base + (long long)q * RED_THREADS + threadIdx.x;
+    for (int e = 0; e < RED_CHUNKS; ++e) {
+        const long long px = p0 + e;
         if (px >= HW) break;
-        if (a.m_out) a.m_out[st.pix_off + px] = m[q];
+        if (a.m_out) a.m_out[st.pix_off + px] = m[e];
         if (!has_img) continue;  // model only
-        const float d = dv[q], s = sv[q];
+        const float d = dv[e], s = sv[e];
         if (isfinite(d) && isfinite(s) && s > 0.0f) {
-            const float z = (d - m[q]) / s;
+            const float z = (d - m[e]) / s;
             csum_add(acc, z * z);
         }
     }
@@ -494,7 +516,10 @@ cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s)
 cudaError_t launch_reduce_chi2(const PassArgs& a, cudaStream_t s)
 {
     if (a.maxitems[WK_RED] > 0) {
-        GF_LAUNCH_PDL(k_reduce_chi2, dim3(a.grid[WK_RED]), dim3(RED_THREADS), 0, s, a);
+        // light CTAs: eight per SM are resident, and every one keeps its loads
+        // in flight
+        const int g = (int)std::min<long long>(a.maxitems[WK_RED], 152LL * 8);
+        GF_LAUNCH_PDL(k_reduce_chi2, dim3(g), dim3(RED_THREADS), 0, s, a);
         GF_COUNT_LAUNCH();
     }
     return cudaGetLastError();
