@@ -17,7 +17,10 @@ Parity status: every function here is pinned by the tests in
 ``tests/test_oracle_*.py`` against closed forms, library special functions,
 brute force or invariants -- except the generalised-radius boxiness term
 (c != 0), whose flux factor has no closed form in the paper: parity unpinned
-beyond self-consistency (two-resolution grid integration).
+beyond self-consistency (two-resolution grid integration).  The analytic
+derivatives (``comp_grad``, ``model_ext_grad``, ``jacobian(analytic=True)``)
+are pinned by central differences of the definitions, and db_n/dn by scipy's
+inverse of the incomplete gamma and the Ciotti-Bertin expansion.
 """
 from __future__ import annotations
 
@@ -65,7 +68,10 @@ class Opts(C.Structure):
     _fields_ = [("lambda0", C.c_double), ("lambda_up", C.c_double),
                 ("lambda_down", C.c_double), ("lambda_min", C.c_double),
                 ("lambda_max", C.c_double), ("ftol", C.c_double), ("xtol", C.c_double),
-                ("fd_rel", C.c_double), ("max_iter", C.c_int)]
+                ("fd_rel", C.c_double), ("max_iter", C.c_int), ("jac_mode", C.c_int)]
+
+
+JAC_FORWARD, JAC_CENTRAL, JAC_ANALYTIC = 0, 1, 2
 
 
 class Result(C.Structure):
@@ -82,6 +88,13 @@ def lib():
             dp = C.POINTER(C.c_double)
             L.gfo_bn.restype = C.c_double
             L.gfo_bn.argtypes = [C.c_double]
+            L.gfo_bn_deriv.restype = C.c_double
+            L.gfo_bn_deriv.argtypes = [C.c_double]
+            L.gfo_comp_grad.restype = C.c_double
+            L.gfo_comp_grad.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, dp]
+            L.gfo_model_ext_grad.restype = C.c_int
+            L.gfo_model_ext_grad.argtypes = [C.POINTER(Desc), dp, C.c_int, dp]
             L.gfo_gammainc_lower.restype = C.c_double
             L.gfo_gammainc_lower.argtypes = [C.c_double, C.c_double]
             L.gfo_sersic_flux.restype = C.c_double
@@ -154,6 +167,27 @@ def nslots(kinds) -> int:
 
 def bn(n: float) -> float:
     return lib().gfo_bn(float(n))
+
+
+def bn_deriv(n: float) -> float:
+    return lib().gfo_bn_deriv(float(n))
+
+
+def comp_grad(kind, p, x, y):
+    """(value, gradient over the component's slots) at (x, y)."""
+    p = _f64(p)
+    bn_ = bn(p[4]) if kind == SERSIC else 0.0
+    db = bn_deriv(p[4]) if kind == SERSIC else 0.0
+    g = np.zeros(8)
+    v = lib().gfo_comp_grad(int(kind), _dp(p), float(x), float(y), bn_, db, _dp(g))
+    return v, g[:len(p)]
+
+
+def model_ext_grad(desc: Desc, params, slot: int) -> np.ndarray:
+    c = (desc.P - 1) // 2
+    out = np.empty((desc.H + 2 * c, desc.W + 2 * c), np.float64)
+    assert lib().gfo_model_ext_grad(C.byref(desc), _dp(_f64(params)), int(slot), _dp(out)) == 0
+    return out
 
 
 def gammainc_lower(a: float, x: float) -> float:
@@ -241,7 +275,7 @@ def _fixed_bytes(fixed, ns):
 
 
 def jacobian(desc: Desc, params, fixed, psf, img, sigma, method=0, fd_rel=1e-3,
-             central=False):
+             central=False, analytic=False):
     """Returns dict(J [nfree,H,W], A, g, chi2, model)."""
     ns = nslots([desc.kinds[i] for i in range(desc.ncomp)])
     fb = _fixed_bytes(fixed, ns)
@@ -252,7 +286,9 @@ def jacobian(desc: Desc, params, fixed, psf, img, sigma, method=0, fd_rel=1e-3,
     m = np.empty((desc.H, desc.W), np.float64)
     p, psf, img, sigma = _f64(params), _f64(psf), _f64(img), _f64(sigma)
     x2 = lib().gfo_jacobian(C.byref(desc), _dp(p), fb, _dp(psf), _dp(img), _dp(sigma),
-                            int(method), float(fd_rel), int(central), _dp(J), _dp(A), _dp(g),
+                            int(method), float(fd_rel),
+                            JAC_ANALYTIC if analytic else (JAC_CENTRAL if central else JAC_FORWARD),
+                            _dp(J), _dp(A), _dp(g),
                             _dp(m))
     return dict(J=J, A=A, g=g, chi2=x2, model=m)
 

@@ -167,6 +167,99 @@ double gfo_comp_value(int kind, const double* p, double x, double y, double bn)
     return amp * exp(-r / rs);
 }
 
+/* db_n/dn by central differences of the b_n solver (FP64; the solver is
+ * accurate to ~1e-14, so the difference quotient carries ~1e-10 relative). */
+double gfo_bn_deriv(double n)
+{
+    double e = 1e-4 * fmax(n, 1.0);
+    return (gfo_bn(n + e) - gfo_bn(n - e)) / (2.0 * e);
+}
+
+/* The component's value at (x, y) and its partial derivatives with respect to
+ * each of its slots, by the chain rule through the definitions above
+ * (analytic Jacobian columns, the "next" step after finite differences).
+ *   r^C = |x'|^C + |Y|^C with Y = y'/q:
+ *     dr/dx' = sgn(x') (|x'|/r)^(C-1),  dr/dY = sgn(Y) (|Y|/r)^(C-1),
+ *     dr/dC  = r [ (|x'|^C ln|x'| + |Y|^C ln|Y|) / (C r^C) - ln(r^C) / C^2 ];
+ *   x' = dx cos t + dy sin t, y' = -dx sin t + dy cos t, dx = x - x0, dy = y - y0:
+ *     dx'/dx0 = -cos t, dx'/dy0 = -sin t, dy'/dx0 = sin t, dy'/dy0 = -cos t,
+ *     dx'/dt = y', dy'/dt = -x', dt/dpa = pi/180, dY/dq = -Y/q;
+ *   Sersic, u = (r/r_e)^(1/n), I = I_e exp(-b_n (u - 1)):
+ *     dI/dr = -b_n I u / (n r),  dI/dr_e = b_n I u / (n r_e),
+ *     dI/dn = I [ (1 - u) db_n/dn + b_n u ln(r/r_e) / n^2 ];
+ *   disk, I = I_0 exp(-r/r_s): dI/dr = -I/r_s, dI/dr_s = I r / r_s^2;
+ *   amplitude: dI/dA = I/A (the profile at unit amplitude); sky: 1.
+ * At r = 0 (a sample exactly on the centre) the geometric derivatives are
+ * set to 0.  grad has one entry per slot of the component. */
+double gfo_comp_grad(int kind, const double* p, double x, double y, double bn, double dbdn,
+                     double* grad)
+{
+    if (kind == GFO_SKY) {
+        grad[0] = 1.0;
+        return p[0];
+    }
+    double x0 = p[0], y0 = p[1], amp = p[2], rs = p[3];
+    double n = 1.0, q, pa, c;
+    int iq, ipa, ic, in = -1;
+    if (kind == GFO_SERSIC) {
+        n = p[4];
+        q = p[5];
+        pa = p[6];
+        c = p[7];
+        in = 4;
+        iq = 5;
+        ipa = 6;
+        ic = 7;
+    } else {
+        q = p[4];
+        pa = p[5];
+        c = p[6];
+        iq = 4;
+        ipa = 5;
+        ic = 6;
+    }
+    double th = pa * M_PI / 180.0, cs = cos(th), sn = sin(th);
+    double dx = x - x0, dy = y - y0;
+    double xp = dx * cs + dy * sn;
+    double yp = -dx * sn + dy * cs;
+    double Y = yp / q;
+    double C = c + 2.0;
+    double ax = pow(fabs(xp), C), ay = pow(fabs(Y), C);
+    double S = ax + ay;
+    double r = pow(S, 1.0 / C);
+    double unit, dIdr, dIdrs, dIdn = 0.0;
+    if (kind == GFO_SERSIC) {
+        double t = r / rs, u = pow(t, 1.0 / n);
+        unit = exp(-bn * (u - 1.0));
+        double I = amp * unit;
+        dIdr = r > 0.0 ? -bn * I * u / (n * r) : 0.0;
+        dIdrs = bn * I * u / (n * rs);
+        dIdn = r > 0.0 ? I * ((1.0 - u) * dbdn + bn * u * log(t) / (n * n)) : I * dbdn;
+    } else {
+        unit = exp(-r / rs);
+        double I = amp * unit;
+        dIdr = -I / rs;
+        dIdrs = I * r / (rs * rs);
+    }
+    double drdxp = 0.0, drdY = 0.0, drdC = 0.0;
+    if (r > 0.0) {
+        drdxp = (xp > 0.0 ? 1.0 : (xp < 0.0 ? -1.0 : 0.0)) * pow(fabs(xp) / r, C - 1.0);
+        drdY = (Y > 0.0 ? 1.0 : (Y < 0.0 ? -1.0 : 0.0)) * pow(fabs(Y) / r, C - 1.0);
+        double lx = ax > 0.0 ? ax * log(fabs(xp)) : 0.0;
+        double ly = ay > 0.0 ? ay * log(fabs(Y)) : 0.0;
+        drdC = r * ((lx + ly) / (C * S) - log(S) / (C * C));
+    }
+    grad[0] = dIdr * (drdxp * (-cs) + drdY * (sn / q));
+    grad[1] = dIdr * (drdxp * (-sn) + drdY * (-cs / q));
+    grad[2] = unit;
+    grad[3] = dIdrs;
+    if (in >= 0) grad[in] = dIdn;
+    grad[iq] = dIdr * drdY * (-Y / q);
+    grad[ipa] = dIdr * (drdxp * yp + drdY * (-xp / q)) * (M_PI / 180.0);
+    grad[ic] = dIdr * drdC;
+    return amp * unit;
+}
+
 static void os_block(const gfo_desc* d, int* bx0, int* by0)
 {
     *bx0 = d->os_x0 >= 0 ? d->os_x0 : (d->W - d->os_box) / 2;
@@ -195,6 +288,51 @@ static double comp_pixel_bn(const gfo_desc* d, int kind, const double* p, int i,
         }
     }
     return gfo_comp_value(kind, p, (double)j, (double)i, bn);
+}
+
+/* d(pixel value)/d(slot `local` of the component): the derivative of the
+ * pixel-centre value, or the mean of the sub-sample derivatives inside the
+ * oversampling block. */
+static double comp_pixel_grad(const gfo_desc* d, int kind, const double* p, int i, int j,
+                              double bn, double dbdn, int local)
+{
+    double gr[8];
+    int s = d->os_factor, B = d->os_box;
+    if (kind != GFO_SKY && s > 1 && B > 0) {
+        int bx0, by0;
+        os_block(d, &bx0, &by0);
+        if (i >= by0 && i < by0 + B && j >= bx0 && j < bx0 + B) {
+            double acc = 0.0;
+            for (int a = 0; a < s; ++a)
+                for (int b = 0; b < s; ++b) {
+                    double y = i - 0.5 + (a + 0.5) / s;
+                    double x = j - 0.5 + (b + 0.5) / s;
+                    gfo_comp_grad(kind, p, x, y, bn, dbdn, gr);
+                    acc += gr[local];
+                }
+            return acc / ((double)s * s);
+        }
+    }
+    gfo_comp_grad(kind, p, (double)j, (double)i, bn, dbdn, gr);
+    return gr[local];
+}
+
+/* The derivative of the extended-grid model with respect to slot `slot`. */
+int gfo_model_ext_grad(const gfo_desc* d, const double* params, int slot, double* out)
+{
+    int c = (d->P - 1) / 2;
+    int He = d->H + 2 * c, We = d->W + 2 * c;
+    int k, l, b;
+    slot_owner(d, slot, &k, &l, &b);
+    if (k < 0) return -1;
+    int kind = d->kinds[k];
+    const double* p = params + b;
+    double bn = kind == GFO_SERSIC ? gfo_bn(p[4]) : 0.0;
+    double dbdn = kind == GFO_SERSIC ? gfo_bn_deriv(p[4]) : 0.0;
+    for (int ie = 0; ie < He; ++ie)
+        for (int je = 0; je < We; ++je)
+            out[(size_t)ie * We + je] = comp_pixel_grad(d, kind, p, ie - c, je - c, bn, dbdn, l);
+    return 0;
 }
 
 double gfo_comp_pixel(const gfo_desc* d, int kind, const double* p, int i, int j)
@@ -452,12 +590,13 @@ double gfo_fd_step(const gfo_desc* d, int slot, double v, double fd_rel)
 
 /* Jacobian of the convolved model with respect to the free slots:
  * linear slots (amplitudes, sky) by the exact column, the convolution of the
- * component with unit amplitude; nonlinear slots by forward (or central)
- * differences of the full convolved model.  A = J^T W J, g = J^T W r with
+ * component with unit amplitude; nonlinear slots by forward (mode 0) or
+ * central (mode 1) differences of the full convolved model, or (mode 2) by the
+ * convolution of the analytic derivative of the extended-grid model.  A = J^T W J, g = J^T W r with
  * W = diag(1/sigma^2) on valid pixels and r = d - m. */
 double gfo_jacobian(const gfo_desc* d, const double* params, const uint8_t* fixed,
                     const double* psf, const double* img, const double* sigma,
-                    int method, double fd_rel, int central, double* J, double* A,
+                    int method, double fd_rel, int mode, double* J, double* A,
                     double* g, double* model_out)
 {
     int c = (d->P - 1) / 2, ns = gfo_nslots(d);
@@ -484,12 +623,17 @@ double gfo_jacobian(const gfo_desc* d, const double* params, const uint8_t* fixe
             convolve(method, d->H, d->W, d->P, ext, psf, col);
             continue;
         }
+        if (mode == GFO_JAC_ANALYTIC) {
+            gfo_model_ext_grad(d, params, s, ext);
+            convolve(method, d->H, d->W, d->P, ext, psf, col);
+            continue;
+        }
         double h = gfo_fd_step(d, s, params[s], fd_rel);
         memcpy(pp, params, sizeof(double) * ns);
         pp[s] = params[s] + h;
         gfo_model_ext(d, pp, -1, 0, ext);
         convolve(method, d->H, d->W, d->P, ext, psf, mp);
-        if (central) {
+        if (mode == GFO_JAC_CENTRAL) {
             pp[s] = params[s] - h;
             gfo_model_ext(d, pp, -1, 0, ext);
             convolve(method, d->H, d->W, d->P, ext, psf, mm);
@@ -543,6 +687,7 @@ void gfo_default_opts(gfo_lm_opts* o)
     o->xtol = 1e-8;
     o->fd_rel = 1e-3;
     o->max_iter = 200;
+    o->jac_mode = GFO_JAC_FORWARD;
 }
 
 /* Default box: I >= 0, radii >= 0.1, n in [0.2, 10], q in [0.05, 1],
@@ -661,8 +806,8 @@ int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
     double A[GFO_MAX_FREE * GFO_MAX_FREE], g[GFO_MAX_FREE], M[GFO_MAX_FREE * GFO_MAX_FREE];
     double rhs[GFO_MAX_FREE], delta[GFO_MAX_FREE];
     double lambda = o.lambda0;
-    double chi2 = gfo_jacobian(d, p, fixed, psf, img, sigma, method, o.fd_rel, 0, NULL, A, g,
-                               NULL);
+    double chi2 = gfo_jacobian(d, p, fixed, psf, img, sigma, method, o.fd_rel, o.jac_mode, NULL,
+                               A, g, NULL);
     while (r.iters < o.max_iter) {
         for (int i = 0; i < nfree; ++i) {
             rhs[i] = g[i];
@@ -709,8 +854,8 @@ int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
                     r.status = GFO_CONVERGED;
                     break;
                 }
-                chi2 = gfo_jacobian(d, p, fixed, psf, img, sigma, method, o.fd_rel, 0, NULL, A,
-                                    g, NULL);
+                chi2 = gfo_jacobian(d, p, fixed, psf, img, sigma, method, o.fd_rel, o.jac_mode,
+                                    NULL, A, g, NULL);
                 continue;
             }
         }

@@ -52,10 +52,16 @@ typedef struct {
     int os_x0, os_y0;/* block origin in stamp pixels; -1 = centred on the stamp */
 } gfo_desc;
 
+/* Jacobian columns of the nonlinear slots */
+#define GFO_JAC_FORWARD 0   /* forward differences (the LM default) */
+#define GFO_JAC_CENTRAL 1   /* central differences */
+#define GFO_JAC_ANALYTIC 2  /* convolved analytic derivatives of the model */
+
 typedef struct {
     double lambda0, lambda_up, lambda_down, lambda_min, lambda_max;
     double ftol, xtol, fd_rel;
     int max_iter;
+    int jac_mode;    /* GFO_JAC_FORWARD or GFO_JAC_ANALYTIC */
 } gfo_lm_opts;
 
 typedef struct {
@@ -82,6 +88,15 @@ double gfo_comp_value(int kind, const double* p, double x, double y, double bn);
 /* value of one component averaged over stamp pixel (i, j) with the desc's
  * oversampling rule; i, j may lie in the halo. */
 double gfo_comp_pixel(const gfo_desc* d, int kind, const double* p, int i, int j);
+
+/* db_n/dn (central differences of gfo_bn) */
+double gfo_bn_deriv(double n);
+/* value of a component at (x, y) and its derivative with respect to each of
+ * its slots (grad: one entry per slot) */
+double gfo_comp_grad(int kind, const double* p, double x, double y, double bn, double dbdn,
+                     double* grad);
+/* derivative of the extended-grid model with respect to slot `slot` */
+int gfo_model_ext_grad(const gfo_desc* d, const double* params, int slot, double* out);
 
 /* Step 1: the model on the extended grid; out has (H+2c)*(W+2c) entries.
  * comp = -1: all components summed; comp = k >= 0: component k only.
@@ -111,10 +126,11 @@ double gfo_eval(const gfo_desc* d, const double* params, const double* psf,
 
 /* Step 4 input: Jacobian columns for the free slots (fixed[s] == 0).
  * J: nfree x H*W (may be NULL), A: nfree^2, g: nfree, returns chi^2 at params.
- * central = 1 uses central differences for the nonlinear slots. */
+ * mode: GFO_JAC_FORWARD / GFO_JAC_CENTRAL differences, or GFO_JAC_ANALYTIC
+ * (the convolution of the analytic derivative grid) for the nonlinear slots. */
 double gfo_jacobian(const gfo_desc* d, const double* params, const uint8_t* fixed,
                     const double* psf, const double* img, const double* sigma,
-                    int method, double fd_rel, int central, double* J, double* A,
+                    int method, double fd_rel, int mode, double* J, double* A,
                     double* g, double* model_out);
 
 /* default bounds for every slot */
