@@ -96,6 +96,10 @@ typedef enum {
 #define GF_MAX_PSF 1023
 #define GF_MAX_LADDER 4
 
+/* How the Jacobian columns of the nonlinear slots are formed. */
+#define GF_JAC_FD 0        /* forward differences of the model (step fd_rel) */
+#define GF_JAC_ANALYTIC 1  /* the convolved analytic derivative of the model grid */
+
 /* Model structure of one stamp (or of every stamp of a batch). */
 typedef struct {
     int H, W;            /* stamp rows and columns (>= 1) */
@@ -119,6 +123,8 @@ typedef struct {
     double xtol;         /* converged when max |delta_i| / max(|p_i|, scale_i) < xtol */
     double fd_rel;       /* FD step: fd_rel px for positions, fd_rel*max(|p|,1) otherwise */
     int max_iter;        /* cap on trials (accepted + rejected) */
+    int jac_mode;        /* GF_JAC_FD: forward-difference columns for the nonlinear slots
+                            (the default); GF_JAC_ANALYTIC: their analytic derivatives */
     int ladder;          /* trials evaluated together in one pass: the steps for lambda,
                             lambda*up, ... (1 .. GF_MAX_LADDER; 0 = 2).  The fit takes
                             exactly the steps of the one-trial-at-a-time rule: the trials
@@ -230,8 +236,23 @@ gf_status gf_jacobian(const gf_desc* d, const double* params_host, const uint8_t
                       double* JtWr_dev, double* chi2_dev, void* ws, size_t ws_bytes,
                       gf_stream stream);
 
+/* As gf_jacobian, with the nonlinear columns formed from the analytic
+ * derivatives of the model (the chain rule through the generalised radius, the
+ * rotation and the Sersic index; db_n/dn from the b_n table) instead of finite
+ * differences.  The paper names the finite-difference Jacobian as the routine's
+ * own (Sec. 2 item 4: "routine-specific"); this is the next step after it:
+ * no step-size noise, one evaluation of each component per sample instead of
+ * one per finite-difference channel.  Arguments as gf_jacobian without fd_rel;
+ * the workspace is gf_workspace_size(d, fixed_host, GF_CALL_JACOBIAN). */
+gf_status gf_jacobian_analytic(const gf_desc* d, const double* params_host,
+                               const uint8_t* fixed_host, const float* image_dev,
+                               const float* sigma_dev, const float* psf_dev, float* J_dev,
+                               double* JtWJ_dev, double* JtWr_dev, double* chi2_dev, void* ws,
+                               size_t ws_bytes, gf_stream stream);
+
 /* Fill opts with the library defaults (lambda0 1e-3, x10 / x0.1, [1e-12, 1e12],
- * ftol 1e-8, xtol 1e-8, fd_rel 1e-3, max_iter 200, ladder 2). */
+ * ftol 1e-8, xtol 1e-8, fd_rel 1e-3, max_iter 200, jac_mode GF_JAC_FD,
+ * ladder 2). */
 void gf_default_opts(gf_lm_opts* opts);
 
 /* Steps 1-5: Levenberg-Marquardt fit of one stamp.  params_host (nslots) is

@@ -287,6 +287,7 @@ void default_opts(gf_lm_opts* o)
     o->xtol = 1e-8;
     o->fd_rel = 1e-3;
     o->max_iter = 200;
+    o->jac_mode = GF_JAC_FD;
     o->ladder = 2;
 }
 
@@ -357,6 +358,8 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
     else
         default_opts(&S->opts);
     if (!(S->opts.fd_rel > 0.0)) S->opts.fd_rel = 1e-3;
+    if (S->opts.jac_mode != GF_JAC_FD && S->opts.jac_mode != GF_JAC_ANALYTIC)
+        return fail(GF_EINVAL, "jac_mode must be GF_JAC_FD or GF_JAC_ANALYTIC");
     if (S->opts.ladder == 0) S->opts.ladder = 2;
     if (S->opts.ladder < 1 || S->opts.ladder > GF_MAX_LADDER)
         return fail(GF_EINVAL, "LM ladder must be 1 .. " + std::to_string(GF_MAX_LADDER));
@@ -1275,10 +1278,33 @@ gf_status gf_eval_batch_dev(const gf_desc* d, const gf_batch* b, const double* p
                            stream);
 }
 
+static gf_status jacobian_impl(const gf_desc* d, const double* params, const uint8_t* fixed,
+                               double fd_rel, int jac_mode, const float* img, const float* sig,
+                               const float* psf, float* J_out, double* A, double* g,
+                               double* chi2, void* ws, size_t ws_bytes, gf_stream stream);
+
 gf_status gf_jacobian(const gf_desc* d, const double* params, const uint8_t* fixed, double fd_rel,
                       const float* img, const float* sig, const float* psf, float* J_out,
                       double* A, double* g, double* chi2, void* ws, size_t ws_bytes,
                       gf_stream stream)
+{
+    return jacobian_impl(d, params, fixed, fd_rel, GF_JAC_FD, img, sig, psf, J_out, A, g, chi2,
+                         ws, ws_bytes, stream);
+}
+
+gf_status gf_jacobian_analytic(const gf_desc* d, const double* params, const uint8_t* fixed,
+                               const float* img, const float* sig, const float* psf,
+                               float* J_out, double* A, double* g, double* chi2, void* ws,
+                               size_t ws_bytes, gf_stream stream)
+{
+    return jacobian_impl(d, params, fixed, 0.0, GF_JAC_ANALYTIC, img, sig, psf, J_out, A, g, chi2,
+                         ws, ws_bytes, stream);
+}
+
+static gf_status jacobian_impl(const gf_desc* d, const double* params, const uint8_t* fixed,
+                               double fd_rel, int jac_mode, const float* img, const float* sig,
+                               const float* psf, float* J_out, double* A, double* g,
+                               double* chi2, void* ws, size_t ws_bytes, gf_stream stream)
 {
     gf_status r = check_structure(d);
     if (r != GF_OK) return r;
@@ -1288,6 +1314,7 @@ gf_status gf_jacobian(const gf_desc* d, const double* params, const uint8_t* fix
     gf_lm_opts o;
     default_opts(&o);
     if (fd_rel > 0.0) o.fd_rel = fd_rel;
+    o.jac_mode = jac_mode;
     Structure S;
     if ((r = make_structure(d, fixed, nullptr, nullptr, &o, &S)) != GF_OK) return r;
     if (S.nfree < 1) return fail(GF_EINVAL, "no free slots");
@@ -1298,6 +1325,7 @@ gf_status gf_jacobian(const gf_desc* d, const double* params, const uint8_t* fix
     if ((r = ensure_bn_table(s)) != GF_OK) return r;
     if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
     PassArgs a = jac_args(ws, pl.L, base_args(ws, pl.L, psf, img, sig, d->psf_size));
+    a.jac_analytic = jac_mode == GF_JAC_ANALYTIC;
     a.J_out = J_out;
     GF_CUDA(launch_psf_sum(1, a.st, psf, const_cast<float*>(a.psf_sum), s));
     if ((r = setup_conv(ws, pl, psf, s)) != GF_OK) return r;
@@ -1334,6 +1362,7 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     PassArgs base = base_args(ws, L, psf, img, sig, d->psf_size);
     LMState* lm = at<LMState>(ws, L.lm);
     PassArgs aj = jac_args(ws, L, base);
+    aj.jac_analytic = S.opts.jac_mode == GF_JAC_ANALYTIC;
     aj.lm = lm;
     aj.phase = PH_NEED_JAC;
     PassArgs at_ = trial_args(ws, L, base);

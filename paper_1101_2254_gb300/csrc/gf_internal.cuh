@@ -8,6 +8,7 @@
 //   CH_SUM    sky + all components at one parameter vector (the model, step 1)
 //   CH_SHAPE  component k with unit amplitude (exact amplitude column)
 //   CH_FD     amp_k (S_k(p + h e_s) - S_k(p)) / h for a nonlinear slot s
+//   CH_DERIV  amp_k dS_k/dp_s, the analytic derivative for a nonlinear slot s
 // Convolved channels are combined per pixel into the model
 //   m = sum_ch mweight_ch * Y_ch + sky_const
 // and the Jacobian columns; chi^2 and J^T W J, J^T W r are reduced from there.
@@ -23,7 +24,7 @@
 #define GF_MAX_CHAN 24
 #define GF_NACC_MAX (GF_MAX_FREE * (GF_MAX_FREE + 1) / 2 + GF_MAX_FREE + 1)
 
-enum { CH_SUM = 0, CH_SHAPE = 1, CH_FD = 2 };
+enum { CH_SUM = 0, CH_SHAPE = 1, CH_FD = 2, CH_DERIV = 3 };
 
 // LM phases of a stamp
 enum { PH_NEED_JAC = 0, PH_SOLVE = 1, PH_TRIAL = 2, PH_DONE = 3, PH_NONE = 99 };
@@ -53,6 +54,9 @@ struct Channel {
     float sky;      // CH_SUM: sky level added on the grid
     int ncomp;
     float msky;     // channel 0 of a pass: constant added to the convolved model
+    int dslot;      // CH_DERIV: the slot's index inside its component
+    float dbdn;     // CH_DERIV of a Sersic component: db_n/dn at its n
+    int pad_[2];
     CompConst cc[GF_MAX_COMP];  // all components at the channel's parameter vector
     CompConst pert;             // CH_FD: component `comp` at p + h e_s (unit amplitude)
 };
@@ -139,10 +143,97 @@ __device__ __forceinline__ float comp_eval(const CompConst& k, float xi, float y
     return k.amp * expf(fmaf(-k.b, u, k.b0));
 }
 
+// The unit-amplitude profile of component k at grid point (xi + ox, yi + oy)
+// and its derivatives with respect to the component's slots, in slot order
+// (Sersic: x0, y0, amplitude, r_e, n, q, pa, c; disk: x0, y0, amplitude, r_s, q,
+// pa, c), by the chain rule through the generalised radius:
+//   r^C = |x'|^C + |Y|^C, Y = y'/q:  dr/dx' = sgn(x') (|x'|/r)^(C-1), likewise Y,
+//     dr/dC = r [ (|x'|^C ln|x'| + |Y|^C ln|Y|) / (C r^C) - ln(r^C) / C^2 ];
+//   dx'/dx0 = -cos, dx'/dy0 = -sin, dy'/dx0 = sin, dy'/dy0 = -cos,
+//   dx'/dth = y', dy'/dth = -x', dY/dq = -Y/q;
+//   S = exp(b0 - b u), u = (r/r_e)^(1/n):  dS/dr = -b S u / (n r),
+//     dS/dr_e = b S u / (n r_e), dS/dn = S ((1 - u) db/dn + b u ln(r/r_e) / n^2)
+// (the disk is the case b = 1, b0 = 0, n = 1).  Float32 throughout, like the
+// pixel path; the derivative channels carry no finite-difference step noise.
+// At r = 0 (a sample exactly on the centre) the geometric derivatives are 0.
+__device__ __forceinline__ float comp_grad(const CompConst& k, float xi, float yi, float ox,
+                                           float oy, float dbdn, float (&g)[8])
+{
+    const float dx = (xi - k.x0h) + (ox - k.x0l);
+    const float dy = (yi - k.y0h) + (oy - k.y0l);
+    const float xp = fmaf(dx, k.cs, dy * k.sn);
+    const float yp = fmaf(dy, k.cs, -dx * k.sn);
+    const float Y = yp * k.invq;
+    float r, drdx, drdY, drdC;
+    if (k.ellipse) {
+        const float S2 = fmaf(xp, xp, Y * Y);
+        r = sqrtf(S2);
+        const float ir = r > 0.0f ? 1.0f / r : 0.0f;
+        drdx = xp * ir;
+        drdY = Y * ir;
+        // C = 2: r [ (x'^2 ln|x'| + Y^2 ln|Y|) / (2 r^2) - ln(r^2) / 4 ]
+        const float lx = xp != 0.0f ? xp * xp * logf(fabsf(xp)) : 0.0f;
+        const float ly = Y != 0.0f ? Y * Y * logf(fabsf(Y)) : 0.0f;
+        drdC = r > 0.0f ? r * ((lx + ly) * (0.5f * ir * ir) - 0.5f * logf(r)) : 0.0f;
+    } else {
+        const float l2x = log2f(fabsf(xp)), l2y = log2f(fabsf(Y));
+        const float ax = exp2f(k.C * l2x), ay = exp2f(k.C * l2y);
+        const float S = ax + ay;
+        const float l2S = log2f(S);
+        const float l2r = k.invC * l2S;
+        r = exp2f(l2r);
+        const float cm1 = k.C - 1.0f;
+        drdx = xp != 0.0f ? copysignf(exp2f(cm1 * (l2x - l2r)), xp) : 0.0f;
+        drdY = Y != 0.0f ? copysignf(exp2f(cm1 * (l2y - l2r)), Y) : 0.0f;
+        const float ln2 = 0.69314718055994531f;
+        const float lx = ax > 0.0f ? ax * l2x : 0.0f, ly = ay > 0.0f ? ay * l2y : 0.0f;
+        drdC = r > 0.0f ? r * ln2 * ((lx + ly) / (k.C * S) - l2S * k.invC * k.invC) : 0.0f;
+    }
+    const float t = r * k.invr;
+    const float u = (k.invn == 1.0f) ? t : exp2f(k.invn * log2f(t));
+    const float Sv = expf(fmaf(-k.b, u, k.b0));
+    // dS/dr and the radius-independent factors
+    const float dSdr = r > 0.0f ? -k.b * Sv * u * k.invn / r : 0.0f;
+    g[0] = dSdr * fmaf(drdx, -k.cs, drdY * (k.sn * k.invq));
+    g[1] = dSdr * fmaf(drdx, -k.sn, drdY * (-k.cs * k.invq));
+    g[2] = Sv;
+    g[3] = k.b * Sv * u * k.invn * k.invr;
+    const float dq = dSdr * drdY * (-Y * k.invq);
+    const float dpa = dSdr * fmaf(drdx, yp, drdY * (-xp * k.invq)) * 0.017453292519943295f;
+    const float dc = dSdr * drdC;
+    if (k.kind == GF_SERSIC) {
+        const float lt = r > 0.0f ? logf(t) : 0.0f;
+        g[4] = Sv * fmaf(1.0f - u, dbdn, k.b * u * lt * k.invn * k.invn);
+        g[5] = dq;
+        g[6] = dpa;
+        g[7] = dc;
+    } else {
+        g[4] = dq;
+        g[5] = dpa;
+        g[6] = dc;
+        g[7] = 0.0f;
+    }
+    return Sv;
+}
+
+// g[i] for a runtime i, by selects (the array stays in registers)
+__device__ __forceinline__ float grad_pick(const float (&g)[8], int i)
+{
+    float v = g[0];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) v = (i == q) ? g[q] : v;
+    return v;
+}
+
 // value of a channel at grid point (xi + ox, yi + oy)
 __device__ __forceinline__ float channel_value(const Channel& ch, float xi, float yi, float ox,
                                                float oy)
 {
+    if (ch.type == CH_DERIV) {
+        float g[8];
+        comp_grad(ch.cc[ch.comp], xi, yi, ox, oy, ch.dbdn, g);
+        return grad_pick(g, ch.dslot) * ch.scale;
+    }
     if (ch.type == CH_SUM) {
         float v = ch.sky;
         for (int k = 0; k < ch.ncomp; ++k)
@@ -274,6 +365,7 @@ struct PassArgs {
     int nchan;                 // channels processed per stamp in this pass
     int jac_pass;              // the channels are a Jacobian pass's (shapes, then FD channels
                                // of the same components); else independent models
+    int jac_analytic;          // the Jacobian pass's nonlinear columns are CH_DERIV channels
     float* ext;                // channel grids: ext + ext_index(st[b], nchan, k)
     float* y;                  // convolved channels: y + y_index(st[b], nchan, k)
     const float* psf;

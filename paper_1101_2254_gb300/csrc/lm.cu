@@ -129,6 +129,22 @@ __device__ double bn_lookup(double n)
            tp1 * t * tm2 * 0.5 * f2 + tp1 * t * tm1 * (1.0 / 6.0) * f3;
 }
 
+// db_n/dn from the table: the derivative of the same 4-point Lagrange
+// interpolant (NaN where bn_lookup is NaN)
+__device__ double bn_deriv_lookup(double n)
+{
+    if (*(volatile int*)&g_bn_ready != 1) return NAN;
+    const double u = (n - BN_N0) * (1.0 / BN_DN);
+    if (!(u >= 1.0) || !(u < (double)(BN_TAB - 2))) return NAN;
+    const int k = (int)floor(u) - 1;
+    const double t = u - (double)(k + 1);
+    const double f0 = g_bn_tab[k], f1 = g_bn_tab[k + 1], f2 = g_bn_tab[k + 2], f3 = g_bn_tab[k + 3];
+    const double t2 = 3.0 * t * t;
+    const double d = -(t2 - 6.0 * t + 2.0) * (1.0 / 6.0) * f0 + (t2 - 4.0 * t - 1.0) * 0.5 * f1 -
+                     (t2 - 2.0 * t - 2.0) * 0.5 * f2 + (t2 - 1.0) * (1.0 / 6.0) * f3;
+    return d * (1.0 / BN_DN);
+}
+
 // float32 constants of one component from its float64 slots q; bn is b_n for
 // a Sersic component (ignored otherwise)
 __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn)
@@ -235,6 +251,7 @@ struct WarpScratch {
     double p[GF_MAX_SLOTS];
     double bn[GF_MAX_COMP];
     double bnp[GF_MAX_COMP];  // b_n at n + h (FD channel of a free n)
+    double dbdn[GF_MAX_COMP]; // db_n/dn (analytic channel of a free n)
     CompConst cc[GF_MAX_COMP];
     int ok;
 };
@@ -265,7 +282,15 @@ __device__ void warp_bn(const Structure& S, WarpScratch& W, LMState* L, bool wan
         if (want_pert) {
             bool free_n = false;
             for (int f = 0; f < S.nfree; ++f) free_n |= (S.freeslot[f] == sn);
-            if (free_n) {
+            if (S.opts.jac_mode == GF_JAC_ANALYTIC) {
+                double db = bn_deriv_lookup(n);
+                if (isnan(db)) {  // outside the table: central differences of the solver
+                    const double e = 1e-4 * fmax(n, 1.0);
+                    db = (sersic_bn_warp(n + e, b + 2.0 * e) - sersic_bn_warp(n - e, b - 2.0 * e)) /
+                         (2.0 * e);
+                }
+                if (lane == 0) W.dbdn[k] = db;
+            } else if (free_n) {
                 const double h = fd_step(R_N, n, S.opts.fd_rel);
                 double bp = bn_lookup(n + h);
                 if (isnan(bp)) bp = sersic_bn_warp(n + h, b + 2.0 * h);
@@ -333,6 +358,8 @@ __device__ void warp_build_jac(const Structure& S, WarpScratch& W, float psum, C
         }
         Channel& ch = out[c];
         ch.type = type;
+        ch.dslot = 0;
+        ch.dbdn = 0.0f;
         ch.comp = comp;
         ch.jcol = jcol;
         ch.sky = 0.0f;
@@ -342,6 +369,13 @@ __device__ void warp_build_jac(const Structure& S, WarpScratch& W, float psum, C
         if (type == CH_SHAPE) {
             ch.mweight = (float)amp_of(S, W.p, comp);
             ch.scale = 0.0f;
+            ch.pert = W.cc[comp];
+        } else if (S.opts.jac_mode == GF_JAC_ANALYTIC) {
+            ch.type = CH_DERIV;
+            ch.mweight = 0.0f;
+            ch.scale = (float)amp_of(S, W.p, comp);
+            ch.dslot = slot - S.slot0[comp];
+            ch.dbdn = S.kinds[comp] == GF_SERSIC ? (float)W.dbdn[comp] : 0.0f;
             ch.pert = W.cc[comp];
         } else {
             const int role = S.role[slot];

@@ -152,6 +152,11 @@ __device__ __forceinline__ float jac_channel(const Channel& ch, const float* bas
     for (int k = 0; k < GF_MAX_COMP; ++k)
         if (k == ch.comp) b = base[k];
     if (ch.type == CH_SHAPE) return b;
+    if (ch.type == CH_DERIV) {
+        float g[8];
+        comp_grad(ch.cc[ch.comp], xi, yi, ox, oy, ch.dbdn, g);
+        return grad_pick(g, ch.dslot) * ch.scale;
+    }
     return (comp_eval(ch.pert, xi, yi, ox, oy) - b) * ch.scale;
 }
 
@@ -203,6 +208,82 @@ __device__ __forceinline__ void body_model_jac(const PassArgs& a, int vb, int vg
             const long long cs = (long long)st.He * st.We;
             for (int c = 0; c < nch; ++c)
                 E[c * cs] = jac_channel(chs[c], base, (float)j, (float)i, 0.0f, 0.0f);
+        }
+        if (a.work) {
+            const int cnt = __syncthreads_count(write);
+            if (threadIdx.x == 0)
+                atomicAdd(&a.work[PROF_MODEL], 4ull * (unsigned long long)cnt * (unsigned long long)nch);
+        }
+    }
+}
+
+// Work item = block of MODEL_THREADS grid pixels of a listed stamp (all
+// channels) of an analytic Jacobian pass: each component's value and gradient
+// once per pixel (comp_grad), its shape channel and every derivative channel
+// of it written from them.
+__device__ __forceinline__ void body_model_jac_an(const PassArgs& a, int vb, int vg)
+{
+    __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
+    __shared__ int shape_c[GF_MAX_COMP], d0[GF_MAX_COMP], d1[GF_MAX_COMP];
+    __shared__ float dbdn_c[GF_MAX_COMP];
+    const int n = *a.wl.n;
+    const int* pre = a.wl.pre + WK_MODEL * (a.count + 1);
+    const int tot = pre[n];
+    const int nch = a.nchan;
+    int hint = -1, cur_b = -1;
+    StampInfo st;
+    const int chunk = (tot + vg - 1) / vg;
+    const int it0 = vb * chunk, it1 = min(tot, it0 + chunk);
+    for (int blk = it0; blk < it1; ++blk) {
+        const int li = wl_locate(pre, n, blk, hint);
+        const int b = a.wl.ids[li];
+        if (b != cur_b) {
+            st = a.st[b];
+            __syncthreads();
+            load_channels(chs, &a.chan[(long long)b * a.chan_stride], nch);
+            __syncthreads();
+            if (threadIdx.x == 0) {  // the channel ranges of each component
+                for (int k = 0; k < GF_MAX_COMP; ++k) {
+                    shape_c[k] = -1;
+                    d0[k] = d1[k] = 0;
+                    dbdn_c[k] = 0.0f;
+                }
+                for (int c = nch - 1; c >= 0; --c) {
+                    const int k = chs[c].comp;
+                    if (chs[c].type == CH_SHAPE) shape_c[k] = c;
+                    if (chs[c].type == CH_DERIV) {
+                        if (d1[k] == 0) d1[k] = c + 1;
+                        d0[k] = c;
+                        dbdn_c[k] = chs[c].dbdn;
+                    }
+                }
+            }
+            __syncthreads();
+            cur_b = b;
+        }
+        const int npix = st.He * st.We;
+        const int pix = (blk - pre[li]) * MODEL_THREADS + threadIdx.x;
+        bool write = pix < npix;
+        int i = 0, j = 0;
+        if (write) {
+            const int ie = pix / st.We, je = pix - ie * st.We;
+            i = ie - st.c;
+            j = je - st.c;
+            write = !(st.os_factor > 1 && i >= st.os_y0 && i < st.os_y0 + st.os_box &&
+                      j >= st.os_x0 && j < st.os_x0 + st.os_box);
+        }
+        if (write) {
+            float* E = a.ext + ext_index(st, nch, 0) + pix;
+            const long long cs = (long long)st.He * st.We;
+            const Channel& c0 = chs[0];
+            for (int k = 0; k < c0.ncomp; ++k) {
+                if (c0.cc[k].kind == GF_SKY) continue;
+                float g[8];
+                const float v = comp_grad(c0.cc[k], (float)j, (float)i, 0.0f, 0.0f, dbdn_c[k], g);
+                if (shape_c[k] >= 0) E[shape_c[k] * cs] = v;
+                for (int c = d0[k]; c < d1[k]; ++c)
+                    E[c * cs] = grad_pick(g, chs[c].dslot) * chs[c].scale;
+            }
         }
         if (a.work) {
             const int cnt = __syncthreads_count(write);
@@ -273,7 +354,7 @@ __device__ __forceinline__ void body_model_os_jac(const PassArgs& a, int vb, int
 // oversampled blocks (the heavy items, scheduled first), the others the plain
 // grid pixels, so that the two kinds of work overlap instead of running as two
 // dependent launches.  PIX: 0 one channel per item, 1 every channel of a
-// Jacobian pass per pixel.  OS: 0 none, 1 a warp per (channel, block pixel),
+// Jacobian pass per pixel, 2 the same with analytic derivative channels.  OS: 0 none, 1 a warp per (channel, block pixel),
 // 2 a warp per block pixel with every channel.
 template <int PIX, int OS>
 __global__ void __launch_bounds__(MODEL_THREADS) k_model_pass(PassArgs a, int g_os)
@@ -290,8 +371,10 @@ __global__ void __launch_bounds__(MODEL_THREADS) k_model_pass(PassArgs a, int g_
     const int vb = blockIdx.x - (OS != 0 ? g_os : 0), vg = gridDim.x - (OS != 0 ? g_os : 0);
     if (PIX == 0)
         body_model(a, vb, vg);
-    else
+    else if (PIX == 1)
         body_model_jac(a, vb, vg);
+    else
+        body_model_jac_an(a, vb, vg);
 }
 
 template <int PIX, int OS>
@@ -322,9 +405,20 @@ cudaError_t launch_model(const PassArgs& a, cudaStream_t s)
         // block pixels to fill the GPU (many stamps), else a warp per channel
         // and pixel (one large stamp)
         const long long os_groups = a.maxitems[WK_OS] / a.nchan;
+        const int g_os2 = std::max(1, (int)std::min<long long>(os_groups, cap[1]));
+        if (a.jac_analytic) {
+            if (os_groups * OS_WARPS >= 152LL * 32) {
+                if (g_pix > 0 && (e = launch_pass<2, 0>(a, g_pix, 0, s)) != cudaSuccess) return e;
+                return launch_pass<1, 2>(a, 0, g_os2, s);
+            }
+            if (a.maxitems[WK_OS] == 0) return g_pix > 0 ? launch_pass<2, 0>(a, g_pix, 0, s) : cudaSuccess;
+            if (a.grid[WK_OS] <= MERGE_OS_MAX) return launch_pass<2, 1>(a, g_pix, a.grid[WK_OS], s);
+            if (g_pix > 0 && (e = launch_pass<2, 0>(a, g_pix, 0, s)) != cudaSuccess) return e;
+            return launch_pass<0, 1>(a, 0, a.grid[WK_OS], s);
+        }
         if (os_groups * OS_WARPS >= 152LL * 32) {
             if (g_pix > 0 && (e = launch_pass<1, 0>(a, g_pix, 0, s)) != cudaSuccess) return e;
-            return launch_pass<1, 2>(a, 0, std::max(1, (int)std::min<long long>(os_groups, cap[1])), s);
+            return launch_pass<1, 2>(a, 0, g_os2, s);
         }
         if (a.maxitems[WK_OS] == 0) return g_pix > 0 ? launch_pass<1, 0>(a, g_pix, 0, s) : cudaSuccess;
         if (a.grid[WK_OS] <= MERGE_OS_MAX) return launch_pass<1, 1>(a, g_pix, a.grid[WK_OS], s);

@@ -40,7 +40,11 @@ class LMOpts(C.Structure):
     _fields_ = [("lambda0", C.c_double), ("lambda_up", C.c_double),
                 ("lambda_down", C.c_double), ("lambda_min", C.c_double),
                 ("lambda_max", C.c_double), ("ftol", C.c_double), ("xtol", C.c_double),
-                ("fd_rel", C.c_double), ("max_iter", C.c_int), ("ladder", C.c_int)]
+                ("fd_rel", C.c_double), ("max_iter", C.c_int), ("jac_mode", C.c_int),
+                ("ladder", C.c_int)]
+
+
+JAC_FD, JAC_ANALYTIC = 0, 1
 
 
 class LMResult(C.Structure):
@@ -88,6 +92,9 @@ def lib():
             L.gf_jacobian.restype = C.c_int
             L.gf_jacobian.argtypes = [pd, dp, C.c_char_p, C.c_double, fp, fp, fp, fp, vp, vp,
                                       vp, vp, C.c_size_t, vp]
+            L.gf_jacobian_analytic.restype = C.c_int
+            L.gf_jacobian_analytic.argtypes = [pd, dp, C.c_char_p, fp, fp, fp, fp, vp, vp, vp, vp,
+                                               C.c_size_t, vp]
             L.gf_lm_fit.restype = C.c_int
             L.gf_lm_fit.argtypes = [pd, dp, C.c_char_p, dp, dp, fp, fp, fp,
                                     C.POINTER(LMOpts), C.POINTER(LMResult), vp, C.c_size_t, vp]
@@ -301,8 +308,10 @@ def evaluate(d: Desc, params, img, sig, psf, want_model=True, ws=None, stream=No
 
 
 def jacobian(d: Desc, params, fixed, img, sig, psf, fd_rel=1e-3, want_J=True, ws=None,
-             stream=None):
-    """Jacobian columns and normal equations: dict(J, A, g, chi2) of device tensors."""
+             stream=None, analytic=False):
+    """Jacobian columns and normal equations: dict(J, A, g, chi2) of device tensors.
+    analytic=True: the nonlinear columns from the analytic derivatives
+    (gf_jacobian_analytic) instead of forward differences."""
     import torch
     for t in (img, sig):
         _cuda_f32(t, (d.H, d.W))
@@ -317,9 +326,14 @@ def jacobian(d: Desc, params, fixed, img, sig, psf, fd_rel=1e-3, want_J=True, ws
     p = _f64(params)
     fb = _fixed(fx)
     w, n = _ws(ws).get(lib().gf_workspace_size(C.byref(d), fb, CALL_JACOBIAN))
-    _check(lib().gf_jacobian(C.byref(d), _dp(p), fb, float(fd_rel), _ptr(img), _ptr(sig),
-                             _ptr(psf), _ptr(J), _ptr(A), _ptr(g), _ptr(x2), w, n,
-                             _stream(stream)))
+    if analytic:
+        _check(lib().gf_jacobian_analytic(C.byref(d), _dp(p), fb, _ptr(img), _ptr(sig),
+                                          _ptr(psf), _ptr(J), _ptr(A), _ptr(g), _ptr(x2), w, n,
+                                          _stream(stream)))
+    else:
+        _check(lib().gf_jacobian(C.byref(d), _dp(p), fb, float(fd_rel), _ptr(img), _ptr(sig),
+                                 _ptr(psf), _ptr(J), _ptr(A), _ptr(g), _ptr(x2), w, n,
+                                 _stream(stream)))
     return dict(J=J, A=A, g=g, chi2=x2)
 
 

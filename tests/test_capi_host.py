@@ -119,3 +119,21 @@ def test_lm_ladder_option_validated_before_launch(gf):
     one = gf.make_desc(64, 64, 25, [1, 3])
     assert L.gf_workspace_size(C.byref(one), None, gf.CALL_LM_FIT) > \
         L.gf_workspace_size(C.byref(one), None, gf.CALL_JACOBIAN) + 4 * 4 * (88 * 88 + 64 * 64)
+
+
+def test_jac_mode_validated_before_launch(gf):
+    L = gf.lib()
+    o = gf.default_opts()
+    assert o.jac_mode == gf.JAC_FD
+    d = gf.make_desc(64, 64, 25, [1, 3])
+    p = np.zeros(9)
+    r = gf.LMResult()
+    fake = C.c_void_p(256)
+    o.jac_mode = 7
+    st = L.gf_lm_fit(C.byref(d), p.ctypes.data_as(C.POINTER(C.c_double)), None, None, None,
+                     fake, fake, fake, C.byref(o), C.byref(r), fake, 1 << 30, None)
+    assert st == gf.EINVAL and b"jac_mode" in L.gf_last_error()
+    # the analytic Jacobian rejects bad arguments before any launch too
+    dp = p.ctypes.data_as(C.POINTER(C.c_double))
+    assert L.gf_jacobian_analytic(C.byref(d), dp, None, None, fake, fake, None, fake, fake, fake,
+                                  fake, 1 << 30, None) == gf.EINVAL

@@ -420,3 +420,119 @@ def test_convolve_fft_warp_cols(gf, M, W):
     g = gf.convolve(d, cuda(ext), cuda(psf)).cpu().numpy()
     o = oracle.convolve_direct(ext.astype(np.float64), psf.astype(np.float64))
     assert_pix_close(g, o, rel=1e-5, floor=FFT_FLOOR, what=f"fft conv 32x{M} columns")
+
+
+# ------------------------------------------------------ analytic Jacobian
+# The analytic columns carry no finite-difference step noise: float32 model
+# and convolution round-off only, so their bound is far tighter than the FD
+# columns' 2e-3 of the column scale.
+JAC_AN_REL = 5e-5
+
+
+@pytest.mark.parametrize("case", stamp_cases()[:3], ids=lambda s: s.name)
+def test_jacobian_analytic_parity(gf, case):
+    m_true, img, sig = noisy_image(case)
+    p = case.guess()
+    d = gpu_desc(gf, case)
+    r = gf.jacobian(d, p, case.fixed, cuda(img), cuda(sig), cuda(case.psf), analytic=True)
+    o = oracle.jacobian(oracle_desc(case), p, case.fixed, case.psf, img, sig, analytic=True)
+    J, Jo = r["J"].cpu().numpy(), o["J"]
+    assert J.shape == Jo.shape
+    for f in range(J.shape[0]):
+        scale = np.abs(Jo[f]).max()
+        err = np.abs(J[f] - Jo[f]).max()
+        assert err <= JAC_AN_REL * scale, (case.name, f, err, scale)
+    A, Ao = r["A"].cpu().numpy(), o["A"]
+    dA = np.abs(A - Ao) / np.sqrt(np.outer(np.diag(Ao), np.diag(Ao)))
+    assert dA.max() < 1e-4, dA.max()
+    g, go = r["g"].cpu().numpy(), o["g"]
+    gscale = np.sqrt(np.diag(Ao) * o["chi2"])
+    assert np.all(np.abs(g - go) <= 1e-4 * gscale), (g, go)
+
+
+def test_jacobian_analytic_fft_path(gf):
+    # the same columns through the Fourier-space convolution
+    case = stamp_cases()[0]
+    m_true, img, sig = noisy_image(case)
+    p = case.guess()
+    r = gf.jacobian(gpu_desc(gf, case, gf.CONV_FFT), p, case.fixed, cuda(img), cuda(sig),
+                    cuda(case.psf), analytic=True)
+    o = oracle.jacobian(oracle_desc(case), p, case.fixed, case.psf, img, sig, analytic=True)
+    J, Jo = r["J"].cpu().numpy(), o["J"]
+    for f in range(J.shape[0]):
+        scale = np.abs(Jo[f]).max()
+        assert np.abs(J[f] - Jo[f]).max() <= JAC_AN_REL * scale + FFT_FLOOR * np.abs(m_true).max(), f
+
+
+@pytest.mark.parametrize("conv", ["direct", "fft"])
+def test_lm_fit_analytic_matches_oracle(gf, conv):
+    st = synth.stamp64()
+    m_true, img, sig = noisy_image(st)
+    od = oracle_desc(st)
+    po, ro = oracle.lm_fit(od, st.guess(), st.fixed, st.psf, img, sig,
+                           opts=oracle.default_opts(jac_mode=oracle.JAC_ANALYTIC))
+    assert ro["status"] == oracle.CONVERGED
+    method = gf.CONV_FFT if conv == "fft" else gf.CONV_DIRECT
+    pg, rg = gf.lm_fit(gpu_desc(gf, st, method), st.guess(), st.fixed, cuda(img), cuda(sig),
+                       cuda(st.psf), opts=gf.default_opts(jac_mode=gf.JAC_ANALYTIC))
+    assert rg["status"] == gf.OK, rg
+    xg, _ = oracle.evaluate(od, pg, st.psf, img, sig)
+    assert xg <= ro["chi2"] * (1 + CHI2_REL), (xg, ro["chi2"])
+    sd = oracle_sigma(od, po, st.fixed, st.psf, img, sig)
+    ok, in_sigma, rel = param_bound_ok(pg, po, _free(st), sd)
+    assert ok, (in_sigma, rel)
+
+
+def test_lm_fit_analytic_noiseless_recovers_truth(gf):
+    st = synth.stamp64()
+    m_true, _, sig = noisy_image(st)
+    pg, rg = gf.lm_fit(gpu_desc(gf, st), st.guess(), st.fixed, cuda(m_true), cuda(sig),
+                       cuda(st.psf), opts=gf.default_opts(jac_mode=gf.JAC_ANALYTIC))
+    assert rg["status"] == gf.OK, rg
+    assert rg["chi2"] <= 1e-4 * m_true.size
+    err = param_rel_err(pg, st.params, _free(st))
+    assert err.max() < PARAM_REL, err
+
+
+def test_lm_fit_stamp512_analytic_reaches_oracle_fit(gf):
+    """The 512x512 fit with analytic columns reaches the oracle's stored minimum
+    in chi^2 (the benchmark's criterion).  On this stamp Marquardt's rule can
+    crawl along the nearly degenerate bulge/disk valley (lambda alternating
+    between accepted and rejected trials) up to the trial cap with either kind
+    of column: the oracle itself, in FP64, ends at the cap with forward
+    differences on a 128x128 version of the stamp and with analytic columns on
+    a 192x192 one.  So the status may be the cap; the chi^2 reached is what is
+    checked."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "stamp512.json")))
+    st = synth.stamp512()
+    m_true, img, sig = noisy_image(st, method=1)
+    od = oracle_desc(st)
+    pg, rg = gf.lm_fit(gpu_desc(gf, st, gf.CONV_FFT), np.array(gold["guess"]), st.fixed, cuda(img),
+                       cuda(sig), cuda(st.psf), opts=gf.default_opts(jac_mode=gf.JAC_ANALYTIC))
+    assert rg["status"] in (gf.OK, gf.EMAXITER), rg
+    xg, _ = oracle.evaluate(od, pg, st.psf, img, sig, method=1)
+    assert xg <= gold["chi2"] * (1 + CHI2_REL), (xg, gold["chi2"])
+    assert abs(rg["chi2"] - xg) <= CHI2_REL * xg
+
+
+def test_lm_analytic_batch_equals_single_stamp_fits(gf):
+    sts = small_batch(5, seed=13)
+    d0 = sts[0]
+    imgs, sigs, psfs, Hs, Ws, p0 = [], [], [], [], [], []
+    for st in sts:
+        m, img, sig = noisy_image(st)
+        imgs.append(img.ravel()); sigs.append(sig.ravel()); psfs.append(st.psf.ravel())
+        Hs.append(st.H); Ws.append(st.W); p0.append(st.guess())
+    opts = gf.default_opts(jac_mode=gf.JAC_ANALYTIC)
+    d = gf.make_desc(1, 1, d0.P, d0.kinds, d0.os_factor, 8)
+    b = gf.make_batch(Hs, Ws, psf_size=d0.P)
+    pb, rb = gf.lm_fit_batch(d, b, np.array(p0), d0.fixed, cuda(np.concatenate(imgs)),
+                             cuda(np.concatenate(sigs)), cuda(np.concatenate(psfs)), opts=opts)
+    for i, st in enumerate(sts):
+        ds = gf.make_desc(st.H, st.W, st.P, st.kinds, st.os_factor, 8)
+        ps, rs = gf.lm_fit(ds, p0[i], st.fixed, cuda(imgs[i]), cuda(sigs[i]), cuda(st.psf),
+                           opts=opts)
+        assert np.array_equal(pb[i], ps), (i, pb[i], ps)
+        assert rb[i]["chi2"] == rs["chi2"] and rb[i]["iters"] == rs["iters"]
