@@ -97,6 +97,9 @@ def parse():
                     help="skip the oracle timing (for profiler runs)")
     ap.add_argument("--stamps", type=int, default=None,
                     help="learned65536: number of stamps (default 65536; smaller for profiler runs)")
+    ap.add_argument("--jac", default="fd", choices=["fd", "analytic"],
+                    help="Jacobian columns of the nonlinear slots: forward differences (the "
+                         "method's own) or analytic derivatives")
     ap.add_argument("--train-steps", type=int, default=2000,
                     help="learned65536: Adam steps of 512 stamps before the timed fits")
     return ap.parse_args()
@@ -172,6 +175,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ peaks
+def jac_mode(gf, args):
+    return gf.JAC_ANALYTIC if args.jac == "analytic" else gf.JAC_FD
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -186,6 +193,37 @@ def fp32_peak_tflops(sm_count, mhz):
 
 
 # ------------------------------------------------------------------ the GPU arm
+def other_jacobian(gf, torch, st, d, p0, img_d, sig_d, psf_d, ws, stream, flush, args):
+    """The same fits with the other kind of Jacobian column (analytic when the
+    line measures forward differences, and the reverse): fits/s over the same
+    number of steps, the fit's counts, and its chi^2 against the oracle's
+    stored minimum for this stamp (tests/golden/stamp512.json)."""
+    other = gf.JAC_FD if args.jac == "analytic" else gf.JAC_ANALYTIC
+    opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL, jac_mode=other)
+    for _ in range(max(args.warmup, 1)):
+        gf.lm_fit(d, p0, st.fixed, img_d, sig_d, psf_d, opts=opts, ws=ws)
+    ms, res = [], None
+    for _ in range(max(args.steps, 1)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, res = gf.lm_fit(d, p0, st.fixed, img_d, sig_d, psf_d, opts=opts, ws=ws)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    out = {"jac": "analytic" if other == gf.JAC_ANALYTIC else "fd",
+           "value": len(ms) / (sum(ms) / 1e3), "unit": "fits/s", "iters": res["iters"],
+           "accepted": res["accepted"], "status": res["status"], "chi2": res["chi2"]}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "stamp512.json")) as fh:
+            gold = json.load(fh)["chi2"]
+        out["oracle_min_chi2"] = gold
+        out["reaches_oracle_chi2"] = bool(res["chi2"] <= gold * (1 + 1e-4))
+    except (OSError, ValueError, KeyError):
+        pass
+    return out
+
+
 def _smooth_len(n):
     """The smallest 2^a 3^b 5^c >= n that is even (a cuFFT-friendly size)."""
     m = max(n, 2)
@@ -289,7 +327,7 @@ def run_gf(args):
 
     # the metric counts fits that reach the oracle's chi^2; ftol = xtol = 1e-6
     # does (tests/test_gpu_parity.py checks it on this stamp)
-    opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL)
+    opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL, jac_mode=jac_mode(gf, args))
 
     def fit():
         return gf.lm_fit(d, p0, st.fixed, img_d, sig_d, psf_d, opts=opts, ws=ws)
@@ -357,6 +395,8 @@ def run_gf(args):
 
     evals = eval_paths(gf, torch, st, d, img_d, sig_d, psf_d, ws, stream, args) \
         if args.workload == "stamp512" else None
+    other = other_jacobian(gf, torch, st, d, p0, img_d, sig_d, psf_d, ws, stream, flush, args) \
+        if args.workload == "stamp512" else None
 
     peaks, peak_kind = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -395,7 +435,7 @@ def run_gf(args):
                    "components": "sersic+expdisk+sky" if args.workload == "stamp512"
                    else "sersic+sky", "free_params": st.nfree,
                    "oversampling": [st.os_factor, st.os_box], "lm_tol": BENCH_TOL,
-                   "conv": "fft" if st.P >= 41 else "direct",
+                   "conv": "fft" if st.P >= 41 else "direct", "jacobian": args.jac,
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "parallelism": f"replicas{ws_}"},
         "e2e": {"value": e2e_value, "unit": "fits/s", "h2d_bytes_per_step": h2d,
@@ -404,6 +444,7 @@ def run_gf(args):
         "roofline": roof,
         "evals_per_s": (chan_evals * ws_ / (total_ms / 1e3)) if chan_evals else None,
         "evals": evals,
+        "other_jacobian": other,
         "alg_hbm_gbs": alg_bytes / (total_ms / 1e3) / 1e9,
         "kernel_ms_per_fit": {k: v["ms"] / args.steps for k, v in pr.items()},
         "lm": {"iters": results[-1]["iters"], "accepted": results[-1]["accepted"],
@@ -564,7 +605,7 @@ def run_batch(args):
     ws = gf.Workspace(device=dev)
     stream = torch.cuda.current_stream()
 
-    opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL)
+    opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL, jac_mode=jac_mode(gf, args))
     # untimed setup: the direct convolution's tile width per width class
     d_direct = gf.make_desc(1, 1, s0.P, s0.kinds, s0.os_factor, 8, conv_method=gf.CONV_DIRECT)
     gf.autotune(d_direct, batch, psf_d, ws=ws)
@@ -609,6 +650,7 @@ def run_batch(args):
             "config": {"workload": "batch4096", "stamps": len(sts),
                        "pixels": int(sum(h * w for h, w in zip(Hs, Ws))), "psf": s0.P,
                        "conv": "direct", "free_params": s0.nfree, "lm_tol": BENCH_TOL,
+                       "jacobian": args.jac,
                        "tile_width_by_class": tiles,
                        "l2": "inputs (0.5 GB) larger than L2", "parallelism": f"replicas{ws_}"},
             "gpu_launches": launches,
@@ -688,7 +730,7 @@ def run_learned(args):
     d = learned.stamp_desc()
     fixed = np.zeros(9, np.uint8)
     fixed[7] = 1
-    opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL)
+    opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL, jac_mode=jac_mode(gf, args))
     ws = gf.Workspace(device=dev)
     ws_lm = gf.Workspace(device=dev)
 
@@ -762,6 +804,7 @@ def run_learned(args):
             "config": {"workload": "learned65536" if count == 65536 else f"learned{count}",
                        "stamps": count, "side": 64, "train_stamps": train_steps * train_batch,
                        "psf": learned.PSF_SIZE, "free_params": 8, "lm_tol": BENCH_TOL,
+                       "jacobian": args.jac,
                        "start": "CNN (bf16) with default-guess fallback by chi2",
                        "l2": "inputs (2.4 GB) larger than L2", "parallelism": f"replicas{ws_}"},
             "e2e": {"value": count / (float(np.mean(e2e_ms)) / 1e3), "unit": "fits/s",

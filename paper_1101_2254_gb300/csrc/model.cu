@@ -350,12 +350,80 @@ __device__ __forceinline__ void body_model_os_jac(const PassArgs& a, int vb, int
     }
 }
 
+// The oversampled blocks of an analytic Jacobian pass, all channels per warp:
+// per sub-sample each component's value and gradient once (comp_grad), then
+// every channel of that component takes its entry.
+__device__ __forceinline__ void body_model_os_jac_an(const PassArgs& a, int vb, int vg)
+{
+    __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
+    const int n = *a.wl.n;
+    const int* pre = a.wl.pre + WK_OS * (a.count + 1);
+    const int tot = pre[n];
+    const int nch = a.nchan;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int hint = -1, cur_b = -1;
+    const int chunk = (tot + vg - 1) / vg;
+    const int it0 = vb * chunk, it1 = min(tot, it0 + chunk);
+    for (int blk = it0; blk < it1; ++blk) {
+        const int li = wl_locate(pre, n, blk, hint);
+        const int b = a.wl.ids[li];
+        const StampInfo st = a.st[b];
+        if (b != cur_b) {
+            __syncthreads();
+            load_channels(chs, &a.chan[(long long)b * a.chan_stride], nch);
+            __syncthreads();
+            cur_b = b;
+        }
+        const int q = (blk - pre[li]) * OS_WARPS + warp;
+        const int B = st.os_box;
+        if (q >= B * B) continue;
+        const int i = st.os_y0 + q / B, j = st.os_x0 + q % B;
+        const int s = st.os_factor, ns = s * s;
+        const float fs = (float)s;
+        float acc[GF_MAX_CHAN];
+#pragma unroll
+        for (int c = 0; c < GF_MAX_CHAN; ++c) acc[c] = 0.0f;
+        const Channel& c0 = chs[0];
+        for (int t = lane; t < ns; t += 32) {
+            const int ay = t / s, bx = t - ay * s;
+            const float oy = ((float)ay + 0.5f) / fs - 0.5f;
+            const float ox = ((float)bx + 0.5f) / fs - 0.5f;
+            for (int k = 0; k < c0.ncomp; ++k) {
+                if (c0.cc[k].kind == GF_SKY) continue;
+                float dbdn = 0.0f;
+                for (int c = 0; c < nch; ++c)
+                    if (chs[c].comp == k && chs[c].type == CH_DERIV) dbdn = chs[c].dbdn;
+                float g[8];
+                const float v = comp_grad(c0.cc[k], (float)j, (float)i, ox, oy, dbdn, g);
+#pragma unroll
+                for (int c = 0; c < GF_MAX_CHAN; ++c) {
+                    if (c < nch && chs[c].comp == k)
+                        acc[c] += chs[c].type == CH_SHAPE ? v
+                                                          : grad_pick(g, chs[c].dslot) * chs[c].scale;
+                }
+            }
+        }
+        const long long pix = (long long)(i + st.c) * st.We + (j + st.c);
+        const long long cs = (long long)st.He * st.We;
+        float* E = a.ext + ext_index(st, nch, 0) + pix;
+#pragma unroll
+        for (int c = 0; c < GF_MAX_CHAN; ++c) {
+            if (c >= nch) break;
+            float v = acc[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) E[c * cs] = v / (float)ns;
+        }
+        if (a.work && lane == 0) atomicAdd(&a.work[PROF_MODEL], 4ull * (unsigned long long)nch);
+    }
+}
+
 // One launch per pass for all of step 1: blocks [0, g_os) evaluate the
 // oversampled blocks (the heavy items, scheduled first), the others the plain
 // grid pixels, so that the two kinds of work overlap instead of running as two
 // dependent launches.  PIX: 0 one channel per item, 1 every channel of a
 // Jacobian pass per pixel, 2 the same with analytic derivative channels.  OS: 0 none, 1 a warp per (channel, block pixel),
-// 2 a warp per block pixel with every channel.
+// 2 a warp per block pixel with every channel, 3 the same with analytic channels.
 template <int PIX, int OS>
 __global__ void __launch_bounds__(MODEL_THREADS) k_model_pass(PassArgs a, int g_os)
 {
@@ -364,8 +432,10 @@ __global__ void __launch_bounds__(MODEL_THREADS) k_model_pass(PassArgs a, int g_
     if (OS != 0 && (int)blockIdx.x < g_os) {
         if (OS == 1)
             body_model_os(a, blockIdx.x, g_os);
-        else
+        else if (OS == 2)
             body_model_os_jac(a, blockIdx.x, g_os);
+        else
+            body_model_os_jac_an(a, blockIdx.x, g_os);
         return;
     }
     const int vb = blockIdx.x - (OS != 0 ? g_os : 0), vg = gridDim.x - (OS != 0 ? g_os : 0);
@@ -409,7 +479,7 @@ cudaError_t launch_model(const PassArgs& a, cudaStream_t s)
         if (a.jac_analytic) {
             if (os_groups * OS_WARPS >= 152LL * 32) {
                 if (g_pix > 0 && (e = launch_pass<2, 0>(a, g_pix, 0, s)) != cudaSuccess) return e;
-                return launch_pass<1, 2>(a, 0, g_os2, s);
+                return launch_pass<2, 3>(a, 0, g_os2, s);
             }
             if (a.maxitems[WK_OS] == 0) return g_pix > 0 ? launch_pass<2, 0>(a, g_pix, 0, s) : cudaSuccess;
             if (a.grid[WK_OS] <= MERGE_OS_MAX) return launch_pass<2, 1>(a, g_pix, a.grid[WK_OS], s);

@@ -517,8 +517,12 @@ def test_lm_fit_stamp512_analytic_reaches_oracle_fit(gf):
     assert abs(rg["chi2"] - xg) <= CHI2_REL * xg
 
 
-def test_lm_analytic_batch_equals_single_stamp_fits(gf):
-    sts = small_batch(5, seed=13)
+@pytest.mark.parametrize("n", [5, 96])
+def test_lm_analytic_batch_equals_single_stamp_fits(gf, n):
+    # 96 stamps: enough oversampled-block pixels that the batch takes the
+    # all-channels-per-warp block kernel, while a single stamp takes the
+    # warp-per-channel one; both give the same floats
+    sts = small_batch(n, seed=13)
     d0 = sts[0]
     imgs, sigs, psfs, Hs, Ws, p0 = [], [], [], [], [], []
     for st in sts:
@@ -530,7 +534,8 @@ def test_lm_analytic_batch_equals_single_stamp_fits(gf):
     b = gf.make_batch(Hs, Ws, psf_size=d0.P)
     pb, rb = gf.lm_fit_batch(d, b, np.array(p0), d0.fixed, cuda(np.concatenate(imgs)),
                              cuda(np.concatenate(sigs)), cuda(np.concatenate(psfs)), opts=opts)
-    for i, st in enumerate(sts):
+    for i in np.linspace(0, n - 1, 5).astype(int):
+        st = sts[i]
         ds = gf.make_desc(st.H, st.W, st.P, st.kinds, st.os_factor, 8)
         ps, rs = gf.lm_fit(ds, p0[i], st.fixed, cuda(imgs[i]), cuda(sigs[i]), cuda(st.psf),
                            opts=opts)
