@@ -177,6 +177,10 @@ int gf_nslots(const gf_desc* d);
  * otherwise). */
 size_t gf_workspace_size(const gf_desc* d, const uint8_t* fixed_host, int call);
 
+/* Workspace bytes for gf_lm_fit_multistart with `starts` starts per stamp. */
+size_t gf_workspace_size_multistart(const gf_desc* d, const gf_batch* b, int starts,
+                                    const uint8_t* fixed_host);
+
 /* Workspace bytes for gf_lm_fit_batch (for any ladder, as gf_workspace_size). */
 size_t gf_workspace_size_batch(const gf_desc* d, const gf_batch* b, const uint8_t* fixed_host);
 
@@ -274,6 +278,27 @@ gf_status gf_lm_fit_batch(const gf_desc* d, const gf_batch* b, double* params_ho
                           const float* sigma_dev, const float* psf_dev,
                           const gf_lm_opts* opts, gf_lm_result* result_host, void* ws,
                           size_t ws_bytes, gf_stream stream);
+
+/* Multi-start fitting: each of the b->count stamps is fitted from `starts`
+ * starting points, and the fit with the lowest finite chi^2 is kept (the
+ * earliest start on ties).  This spends the GPU's speed-up on robustness
+ * against local minima: Sec. 5 names costlier, more robust routines as the use
+ * of the speed-up.  All count x starts fits advance together in one batched
+ * fit; the copies of a stamp share its image, sigma and PSF (nothing is
+ * copied).
+ *   starts_host: count x starts x nslots float64, start k of stamp i at
+ *     (i * starts + k) * nslots;
+ *   params_out: count x nslots, the kept fits;
+ *   result_out: count entries;
+ *   best_out (may be NULL): count ints, the start each stamp kept.
+ * Each fit is the one gf_lm_fit_batch gives for that start.  Workspace:
+ * gf_workspace_size_multistart().  Synchronises `stream` before returning. */
+gf_status gf_lm_fit_multistart(const gf_desc* d, const gf_batch* b, int starts,
+                               const double* starts_host, const uint8_t* fixed_host,
+                               const float* image_dev, const float* sigma_dev,
+                               const float* psf_dev, const gf_lm_opts* opts, double* params_out,
+                               gf_lm_result* result_out, int* best_out, void* ws,
+                               size_t ws_bytes, gf_stream stream);
 
 /* ------------------------------------------------------------ tile tuning
  * No counterpart in the paper.  The direct convolution covers each stamp with

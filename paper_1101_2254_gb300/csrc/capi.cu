@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1560,6 +1561,88 @@ gf_status gf_lm_fit_batch(const gf_desc* d, const gf_batch* b, double* params,
 {
     return lm_fit_impl(d, b, params, fixed, nullptr, nullptr, img, sig, psf, opts, res, ws,
                        ws_bytes, stream);
+}
+
+// The batch of a multi-start fit: stamp i repeated `starts` times (entry
+// i * starts + k), every copy pointing at the stamp's own image, sigma and PSF.
+struct MultiBatch {
+    std::vector<int> H, W;
+    std::vector<int64_t> pix, psf;
+    gf_batch b;
+};
+
+static gf_status make_multi(const gf_batch* b, int starts, MultiBatch* m)
+{
+    if (!b || b->count < 1 || !b->H || !b->W) return fail(GF_EINVAL, "bad batch");
+    if (starts < 1) return fail(GF_EINVAL, "starts must be >= 1");
+    const long long n = (long long)b->count * starts;
+    if (n > INT32_MAX) return fail(GF_EINVAL, "count x starts too large");
+    m->H.resize(n);
+    m->W.resize(n);
+    m->pix.resize(n);
+    m->psf.resize(n);
+    long long packed = 0;
+    for (int i = 0; i < b->count; ++i) {
+        const int64_t po = b->pix_off ? b->pix_off[i] : packed;
+        const int64_t fo = b->psf_off ? b->psf_off[i] : 0;
+        packed += (long long)b->H[i] * b->W[i];
+        for (int k = 0; k < starts; ++k) {
+            const long long e = (long long)i * starts + k;
+            m->H[e] = b->H[i];
+            m->W[e] = b->W[i];
+            m->pix[e] = po;
+            m->psf[e] = fo;
+        }
+    }
+    m->b.count = (int)n;
+    m->b.H = m->H.data();
+    m->b.W = m->W.data();
+    m->b.pix_off = m->pix.data();
+    m->b.psf_off = m->psf.data();
+    return GF_OK;
+}
+
+size_t gf_workspace_size_multistart(const gf_desc* d, const gf_batch* b, int starts,
+                                    const uint8_t* fixed)
+{
+    MultiBatch m;
+    if (make_multi(b, starts, &m) != GF_OK) return 0;
+    return gf_workspace_size_batch(d, &m.b, fixed);
+}
+
+gf_status gf_lm_fit_multistart(const gf_desc* d, const gf_batch* b, int starts,
+                               const double* starts_host, const uint8_t* fixed, const float* img,
+                               const float* sig, const float* psf, const gf_lm_opts* opts,
+                               double* params_out, gf_lm_result* res_out, int* best_out, void* ws,
+                               size_t ws_bytes, gf_stream stream)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    MultiBatch m;
+    if ((r = make_multi(b, starts, &m)) != GF_OK) return r;
+    if (!starts_host || !params_out || !res_out) return fail(GF_EINVAL, "NULL argument");
+    const int ns = nslots_of(d);
+    const long long n = m.b.count;
+    std::vector<double> p(starts_host, starts_host + (size_t)n * ns);
+    std::vector<gf_lm_result> res((size_t)n);
+    if ((r = lm_fit_impl(d, &m.b, p.data(), fixed, nullptr, nullptr, img, sig, psf, opts, res.data(),
+                         ws, ws_bytes, stream)) != GF_OK)
+        return r;
+    // per stamp the fit with the lowest finite chi^2, the earliest start on ties
+    for (int i = 0; i < b->count; ++i) {
+        int best = -1;
+        for (int k = 0; k < starts; ++k) {
+            const gf_lm_result& q = res[(size_t)i * starts + k];
+            if (!std::isfinite(q.chi2)) continue;
+            if (best < 0 || q.chi2 < res[(size_t)i * starts + best].chi2) best = k;
+        }
+        if (best < 0) best = 0;
+        const size_t e = (size_t)i * starts + best;
+        memcpy(params_out + (size_t)i * ns, p.data() + e * ns, sizeof(double) * ns);
+        res_out[i] = res[e];
+        if (best_out) best_out[i] = best;
+    }
+    return GF_OK;
 }
 
 gf_status gf_lm_fit(const gf_desc* d, double* params, const uint8_t* fixed, const double* lo,

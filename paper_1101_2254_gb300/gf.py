@@ -95,6 +95,13 @@ def lib():
             L.gf_jacobian_analytic.restype = C.c_int
             L.gf_jacobian_analytic.argtypes = [pd, dp, C.c_char_p, fp, fp, fp, fp, vp, vp, vp, vp,
                                                C.c_size_t, vp]
+            L.gf_workspace_size_multistart.restype = C.c_size_t
+            L.gf_workspace_size_multistart.argtypes = [pd, C.POINTER(Batch), C.c_int, C.c_char_p]
+            L.gf_lm_fit_multistart.restype = C.c_int
+            L.gf_lm_fit_multistart.argtypes = [pd, C.POINTER(Batch), C.c_int, dp, C.c_char_p, fp,
+                                               fp, fp, C.POINTER(LMOpts), dp,
+                                               C.POINTER(LMResult), C.POINTER(C.c_int), vp,
+                                               C.c_size_t, vp]
             L.gf_lm_fit.restype = C.c_int
             L.gf_lm_fit.argtypes = [pd, dp, C.c_char_p, dp, dp, fp, fp, fp,
                                     C.POINTER(LMOpts), C.POINTER(LMResult), vp, C.c_size_t, vp]
@@ -402,6 +409,26 @@ def lm_fit_batch(d: Desc, batch: Batch, params, fixed, img, sig, psf,
                                  _ptr(psf), C.byref(opts) if opts is not None else None, res,
                                  w, n, _stream(stream)))
     return p, [_res(r) for r in res]
+
+
+def lm_fit_multistart(d: Desc, batch: Batch, starts, fixed, img, sig, psf,
+                      opts: LMOpts | None = None, ws=None, stream=None):
+    """Multi-start fits: starts is count x K x nslots; returns (params [count, nslots],
+    list of result dicts, best start index per stamp)."""
+    st = np.ascontiguousarray(np.asarray(starts, np.float64))
+    assert st.ndim == 3 and st.shape[0] == batch.count
+    K = st.shape[1]
+    fb = _fixed(fixed)
+    p = np.empty((batch.count, st.shape[2]), np.float64)
+    res = (LMResult * batch.count)()
+    best = np.empty(batch.count, np.int32)
+    w, n = _ws(ws).get(lib().gf_workspace_size_multistart(C.byref(d), C.byref(batch), K, fb))
+    _check(lib().gf_lm_fit_multistart(C.byref(d), C.byref(batch), K, _dp(st), fb, _ptr(img),
+                                      _ptr(sig), _ptr(psf),
+                                      C.byref(opts) if opts is not None else None,
+                                      _dp(p), res, best.ctypes.data_as(C.POINTER(C.c_int)),
+                                      w, n, _stream(stream)))
+    return p, [_res(r) for r in res], best
 
 
 def evaluate_batch_dev(d: Desc, batch: Batch, params_dev, img, sig, psf, want_model=False,

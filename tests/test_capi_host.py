@@ -137,3 +137,23 @@ def test_jac_mode_validated_before_launch(gf):
     dp = p.ctypes.data_as(C.POINTER(C.c_double))
     assert L.gf_jacobian_analytic(C.byref(d), dp, None, None, fake, fake, None, fake, fake, fake,
                                   fake, 1 << 30, None) == gf.EINVAL
+
+
+def test_multistart_validated_before_launch(gf):
+    L = gf.lib()
+    d = gf.make_desc(1, 1, 25, [1, 3])
+    b = gf.make_batch([64, 64], [64, 64], psf_size=25)
+    st = np.zeros((2, 3, 9))
+    out = np.zeros((2, 9))
+    res = (gf.LMResult * 2)()
+    fake = C.c_void_p(256)
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))  # noqa: E731
+    for starts in (0, -2):
+        assert L.gf_lm_fit_multistart(C.byref(d), C.byref(b), starts, dp(st), None, fake, fake,
+                                      fake, None, dp(out), res, None, fake, 1 << 30,
+                                      None) == gf.EINVAL
+        assert L.gf_workspace_size_multistart(C.byref(d), C.byref(b), starts, None) == 0
+    # the workspace of K starts is that of the batch with every stamp K times
+    bk = gf.make_batch([64] * 6, [64] * 6, psf_size=25)
+    assert L.gf_workspace_size_multistart(C.byref(d), C.byref(b), 3, None) == \
+        L.gf_workspace_size_batch(C.byref(d), C.byref(bk), None)

@@ -541,3 +541,83 @@ def test_lm_analytic_batch_equals_single_stamp_fits(gf, n):
                            opts=opts)
         assert np.array_equal(pb[i], ps), (i, pb[i], ps)
         assert rb[i]["chi2"] == rs["chi2"] and rb[i]["iters"] == rs["iters"]
+
+
+# ------------------------------------------------------------ multi-start
+def _starts(st, K, rng):
+    """Start 0: the stamp's usual guess; the others perturbed by up to 50 %."""
+    p0 = st.guess()
+    out = [p0]
+    for _ in range(K - 1):
+        p = p0.copy()
+        for s in range(len(p)):
+            if st.fixed[s]:
+                continue
+            p[s] *= 1.0 + 0.5 * rng.uniform(-1.0, 1.0)
+        out.append(p)
+    return np.array(out)
+
+
+def test_multistart_keeps_the_best_of_the_batched_fits(gf):
+    sts = small_batch(6, seed=21)
+    d0 = sts[0]
+    rng = np.random.default_rng(4)
+    K = 3
+    starts = np.stack([_starts(st, K, rng) for st in sts])
+    imgs, sigs, psfs = [], [], []
+    for st in sts:
+        m, img, sig = noisy_image(st)
+        imgs.append(img.ravel()); sigs.append(sig.ravel()); psfs.append(st.psf.ravel())
+    d = gf.make_desc(1, 1, d0.P, d0.kinds, d0.os_factor, 8)
+    b = gf.make_batch([st.H for st in sts], [st.W for st in sts], psf_size=d0.P)
+    args = (cuda(np.concatenate(imgs)), cuda(np.concatenate(sigs)), cuda(np.concatenate(psfs)))
+    pm, rm, best = gf.lm_fit_multistart(d, b, starts, d0.fixed, *args)
+    # each start's fit as a plain batched fit
+    for k in range(K):
+        pk, rk = gf.lm_fit_batch(d, b, starts[:, k], d0.fixed, *args)
+        for i in range(len(sts)):
+            assert rm[i]["chi2"] <= rk[i]["chi2"] or not np.isfinite(rk[i]["chi2"])
+            if best[i] == k:
+                assert np.array_equal(pm[i], pk[i]) and rm[i]["chi2"] == rk[i]["chi2"]
+    # one start: the plain batched fit
+    p1, r1, b1 = gf.lm_fit_multistart(d, b, starts[:, :1], d0.fixed, *args)
+    pb, rb = gf.lm_fit_batch(d, b, starts[:, 0], d0.fixed, *args)
+    assert np.array_equal(p1, pb) and np.all(b1 == 0)
+
+
+def test_multistart_reaches_the_oracle_minimum_at_least_as_often(gf):
+    # stamps fitted from deliberately poor first starts: best-of-4 reaches the
+    # oracle's chi^2 (its fit from the true parameters) at least as often as
+    # the first start alone
+    sts = small_batch(16, seed=33)
+    d0 = sts[0]
+    rng = np.random.default_rng(9)
+    K = 4
+    starts = []
+    for st in sts:
+        s = _starts(st, K, rng)
+        s[0] = _starts(st, 2, rng)[1]  # a poor first start
+        starts.append(s)
+    starts = np.stack(starts)
+    imgs, sigs, psfs, ref = [], [], [], []
+    for st in sts:
+        m, img, sig = noisy_image(st)
+        imgs.append(img); sigs.append(sig); psfs.append(st.psf.ravel())
+        od = oracle.make_desc(st.H, st.W, st.P, st.kinds, st.os_factor, 8)
+        _, ro = oracle.lm_fit(od, st.params, st.fixed, st.psf, img, sig)
+        ref.append((od, ro["chi2"]))
+    d = gf.make_desc(1, 1, d0.P, d0.kinds, d0.os_factor, 8)
+    b = gf.make_batch([st.H for st in sts], [st.W for st in sts], psf_size=d0.P)
+    args = (cuda(np.concatenate([i.ravel() for i in imgs])),
+            cuda(np.concatenate([s.ravel() for s in sigs])), cuda(np.concatenate(psfs)))
+    pm, rm, best = gf.lm_fit_multistart(d, b, starts, d0.fixed, *args)
+    p1, r1 = gf.lm_fit_batch(d, b, starts[:, 0], d0.fixed, *args)
+
+    def reached(p, i):
+        od, x2ref = ref[i]
+        x2, _ = oracle.evaluate(od, p, sts[i].psf, imgs[i], sigs[i])
+        return x2 <= x2ref * (1 + CHI2_REL)
+    n_multi = sum(reached(pm[i], i) for i in range(len(sts)))
+    n_one = sum(reached(p1[i], i) for i in range(len(sts)))
+    assert n_multi >= n_one
+    assert n_multi >= 14, (n_multi, n_one)
