@@ -11,6 +11,7 @@ Every function takes and returns numpy float64 arrays; the parameter layout
 per component is
     Sersic  : x0, y0, I_e, r_e, n, q, pa_deg, c
     ExpDisk : x0, y0, I_0, r_s, q, pa_deg, c
+    Gaussian: x0, y0, I_0, fwhm, q, pa_deg, c
     Sky     : s0
 
 Parity status: every function here is pinned by the tests in
@@ -36,8 +37,8 @@ LIB = os.path.join(HERE, "liboracle.so")
 SRC = os.path.join(HERE, "gfo.c")
 SRC_CNN = os.path.join(HERE, "gfo_cnn.c")
 
-SERSIC, EXPDISK, SKY = 1, 2, 3
-NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1}
+SERSIC, EXPDISK, SKY, GAUSSIAN = 1, 2, 3, 4
+NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7}
 CONVERGED, BADINPUT, NOCONV, MAXITER = 0, 1, 3, 8
 
 _lock = threading.Lock()

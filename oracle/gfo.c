@@ -31,6 +31,7 @@ int gfo_comp_nslots(int kind)
     switch (kind) {
     case GFO_SERSIC: return 8;
     case GFO_EXPDISK: return 7;
+    case GFO_GAUSSIAN: return 7;
     case GFO_SKY: return 1;
     default: return -1;
     }
@@ -137,6 +138,9 @@ double gfo_sersic_flux(double Ie, double re, double n, double q)
 
 /* ------------------------------------------------------------------ model */
 
+/* sigma of a Gaussian of full width at half maximum 1: 1 / (2 sqrt(2 ln 2)) */
+static double gauss_sigma_per_fwhm(void) { return 1.0 / (2.0 * sqrt(2.0 * log(2.0))); }
+
 /* Surface brightness of one component at (x, y).
  * Rotation: theta = pa_deg * pi / 180, counter-clockwise from +x to the major
  * axis; x' = dx cos + dy sin, y' = -dx sin + dy cos.
@@ -164,6 +168,10 @@ double gfo_comp_value(int kind, const double* p, double x, double y, double bn)
     double C = c + 2.0;
     double r = pow(pow(fabs(xp), C) + pow(fabs(yp / q), C), 1.0 / C);
     if (kind == GFO_SERSIC) return amp * exp(-bn * (pow(r / rs, 1.0 / n) - 1.0));
+    if (kind == GFO_GAUSSIAN) {
+        double sig = rs * gauss_sigma_per_fwhm();
+        return amp * exp(-r * r / (2.0 * sig * sig));
+    }
     return amp * exp(-r / rs);
 }
 
@@ -188,6 +196,8 @@ double gfo_bn_deriv(double n)
  *     dI/dr = -b_n I u / (n r),  dI/dr_e = b_n I u / (n r_e),
  *     dI/dn = I [ (1 - u) db_n/dn + b_n u ln(r/r_e) / n^2 ];
  *   disk, I = I_0 exp(-r/r_s): dI/dr = -I/r_s, dI/dr_s = I r / r_s^2;
+ *   Gaussian, I = I_0 exp(-r^2 / (2 s^2)), s = FWHM / (2 sqrt(2 ln 2)):
+ *     dI/dr = -I r / s^2, dI/dFWHM = I r^2 / s^3 * ds/dFWHM;
  *   amplitude: dI/dA = I/A (the profile at unit amplitude); sky: 1.
  * At r = 0 (a sample exactly on the centre) the geometric derivatives are
  * set to 0.  grad has one entry per slot of the component. */
@@ -235,6 +245,14 @@ double gfo_comp_grad(int kind, const double* p, double x, double y, double bn, d
         dIdr = r > 0.0 ? -bn * I * u / (n * r) : 0.0;
         dIdrs = bn * I * u / (n * rs);
         dIdn = r > 0.0 ? I * ((1.0 - u) * dbdn + bn * u * log(t) / (n * n)) : I * dbdn;
+    } else if (kind == GFO_GAUSSIAN) {
+        /* I = A exp(-r^2 / (2 sigma^2)), sigma = k FWHM:
+         * dI/dr = -I r / sigma^2, dI/dFWHM = I r^2 / sigma^3 * k */
+        double k = gauss_sigma_per_fwhm(), sig = rs * k;
+        unit = exp(-r * r / (2.0 * sig * sig));
+        double I = amp * unit;
+        dIdr = -I * r / (sig * sig);
+        dIdrs = I * r * r / (sig * sig * sig) * k;
     } else {
         unit = exp(-r / rs);
         double I = amp * unit;

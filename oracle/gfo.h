@@ -32,6 +32,7 @@
 #define GFO_SERSIC 1
 #define GFO_EXPDISK 2
 #define GFO_SKY 3
+#define GFO_GAUSSIAN 4  /* I_0 exp(-r^2 / (2 sigma^2)), sigma = FWHM / (2 sqrt(2 ln 2)) */
 #define GFO_MAX_COMP 8
 #define GFO_MAX_SLOTS 64
 #define GFO_MAX_FREE 16

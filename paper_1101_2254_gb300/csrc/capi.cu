@@ -111,6 +111,7 @@ int comp_slots(int kind)
     case GF_SERSIC: return 8;
     case GF_EXPDISK: return 7;
     case GF_SKY: return 1;
+    case GF_GAUSSIAN: return 7;
     default: return -1;
     }
 }
@@ -139,7 +140,7 @@ gf_status check_structure(const gf_desc* d)
             ++nprof;
     }
     if (nsky > 1) return fail(GF_EINVAL, "at most one sky component");
-    if (nprof < 1) return fail(GF_EINVAL, "at least one Sersic or exponential-disk component");
+    if (nprof < 1) return fail(GF_EINVAL, "at least one profile component (Sersic, disk, Gaussian)");
     if (d->os_factor < 1 || d->os_factor > 64) return fail(GF_EINVAL, "os_factor out of [1, 64]");
     if (d->os_box < 0) return fail(GF_EINVAL, "os_box < 0");
     const int m = resolve_method(d);

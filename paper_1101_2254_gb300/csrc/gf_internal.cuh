@@ -38,10 +38,10 @@ struct CompConst {
     float cs, sn, invq;        // rotation and axis ratio
     float C, invC;             // generalised-radius exponent C = c + 2
     float amp;                 // amplitude (1 for unit shapes)
-    float invr;                // 1 / r_e or 1 / r_s
+    float invr;                // 1 / r_e, 1 / r_s, or 1 / s for a Gaussian
     float invn;                // 1 / n (1 for the disk)
     float b0, b;               // I = amp * exp(b0 - b * (r invr)^invn)
-    int kind;                  // GF_SERSIC / GF_EXPDISK / GF_SKY
+    int kind;                  // GF_SERSIC / GF_EXPDISK / GF_SKY / GF_GAUSSIAN
     int ellipse;               // C == 2 exactly: r by sqrt
 };
 
@@ -145,15 +145,17 @@ __device__ __forceinline__ float comp_eval(const CompConst& k, float xi, float y
 
 // The unit-amplitude profile of component k at grid point (xi + ox, yi + oy)
 // and its derivatives with respect to the component's slots, in slot order
-// (Sersic: x0, y0, amplitude, r_e, n, q, pa, c; disk: x0, y0, amplitude, r_s, q,
-// pa, c), by the chain rule through the generalised radius:
+// (Sersic: x0, y0, amplitude, r_e, n, q, pa, c; disk and Gaussian: x0, y0,
+// amplitude, r_s or fwhm, q, pa, c), by the chain rule through the generalised
+// radius:
 //   r^C = |x'|^C + |Y|^C, Y = y'/q:  dr/dx' = sgn(x') (|x'|/r)^(C-1), likewise Y,
 //     dr/dC = r [ (|x'|^C ln|x'| + |Y|^C ln|Y|) / (C r^C) - ln(r^C) / C^2 ];
 //   dx'/dx0 = -cos, dx'/dy0 = -sin, dy'/dx0 = sin, dy'/dy0 = -cos,
 //   dx'/dth = y', dy'/dth = -x', dY/dq = -Y/q;
 //   S = exp(b0 - b u), u = (r/r_e)^(1/n):  dS/dr = -b S u / (n r),
 //     dS/dr_e = b S u / (n r_e), dS/dn = S ((1 - u) db/dn + b u ln(r/r_e) / n^2)
-// (the disk is the case b = 1, b0 = 0, n = 1).  Float32 throughout, like the
+// (the disk is the case b = 1, b0 = 0, n = 1; the Gaussian b = 1/2, b0 = 0, n = 1/2
+// with the radius s = fwhm / (2 sqrt(2 ln 2))).  Float32 throughout, like the
 // pixel path; the derivative channels carry no finite-difference step noise.
 // At r = 0 (a sample exactly on the centre) the geometric derivatives are 0.
 __device__ __forceinline__ float comp_grad(const CompConst& k, float xi, float yi, float ox,
@@ -197,7 +199,8 @@ __device__ __forceinline__ float comp_grad(const CompConst& k, float xi, float y
     g[0] = dSdr * fmaf(drdx, -k.cs, drdY * (k.sn * k.invq));
     g[1] = dSdr * fmaf(drdx, -k.sn, drdY * (-k.cs * k.invq));
     g[2] = Sv;
-    g[3] = k.b * Sv * u * k.invn * k.invr;
+    g[3] = k.b * Sv * u * k.invn * k.invr;  // with respect to 1/invr (r_e, r_s, or s)
+    if (k.kind == GF_GAUSSIAN) g[3] *= 0.42466090014400952f;  // s = fwhm / (2 sqrt(2 ln 2))
     const float dq = dSdr * drdY * (-Y * k.invq);
     const float dpa = dSdr * fmaf(drdx, yp, drdY * (-xp * k.invq)) * 0.017453292519943295f;
     const float dc = dSdr * drdC;

@@ -35,6 +35,8 @@
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+// sigma of a Gaussian per unit full width at half maximum, 1 / (2 sqrt(2 ln 2))
+constexpr double kGaussSigmaPerFwhm = 0.42466090014400952136;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerBlock = 4;
 
@@ -181,26 +183,28 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
         pa = q[5];
         c = q[6];
     }
-    // The pixel path takes float32 constants, so they are formed in float32
-    // (FP64 transcendentals and divisions are long chains on GB300): the angle
-    // is split th = th_h + th_l with th_h a float, and
-    // cos th = cos th_h - th_l sin th_h, sin th = sin th_h + th_l cos th_h to
-    // first order (|th_l| < 2^-24 |th|: the next term is below 1e-15).
+    // The constants are formed in FP64 and rounded once to float32: the
+    // finite-difference channels difference two such constant sets, so their
+    // rounding is what the 1/h of a forward difference amplifies.
     const double th = pa * (kPi / 180.0);
-    const float th_h = (float)th, th_l = (float)(th - (double)th_h);
-    float sh, ch;
-    sincosf(th_h, &sh, &ch);
-    k.cs = fmaf(-th_l, sh, ch);
-    k.sn = fmaf(th_l, ch, sh);
-    k.invq = 1.0f / (float)ax;
+    k.cs = (float)cos(th);
+    k.sn = (float)sin(th);
+    k.invq = (float)(1.0 / ax);
     k.C = (float)(c + 2.0);
-    k.invC = 1.0f / k.C;
+    k.invC = (float)(1.0 / (c + 2.0));
     k.ellipse = (c == 0.0);
     k.amp = (float)amp;
-    k.invr = 1.0f / (float)r;
+    k.invr = (float)(1.0 / r);
+    if (kind == GF_GAUSSIAN) {
+        // exp(-(r/s)^2 / 2): the exp(b0 - b u) form with u = (r/s)^2
+        k.invr = (float)(1.0 / (r * kGaussSigmaPerFwhm));
+        k.invn = 2.0f;
+        k.b0 = 0.0f;
+        k.b = 0.5f;
+    }
     if (kind == GF_SERSIC) {
         const double n = q[4];
-        k.invn = 1.0f / (float)n;
+        k.invn = (float)(1.0 / n);
         k.b0 = (float)bn;
         k.b = (float)bn;
     }

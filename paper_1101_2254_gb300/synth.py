@@ -10,6 +10,7 @@ Parameter layout per component (the library's ABI):
     Sersic  (kind 1): x0, y0, I_e, r_e, n, q, pa_deg, c
     ExpDisk (kind 2): x0, y0, I_0, r_s, q, pa_deg, c
     Sky     (kind 3): s0
+    Gaussian(kind 4): x0, y0, I_0, fwhm, q, pa_deg, c
 
 Workloads (sizes and distributions as the galaxy-fitting configurations state
 them; values the statement leaves open are marked "chosen"):
@@ -29,8 +30,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-SERSIC, EXPDISK, SKY = 1, 2, 3
-NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1}
+SERSIC, EXPDISK, SKY, GAUSSIAN = 1, 2, 3, 4
+NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7}
 
 SIGMA_READ = 0.01
 GAIN = 1.0
@@ -92,7 +93,7 @@ def slot_roles(kinds):
     for k in kinds:
         if k == SERSIC:
             roles += ["pos", "pos", "amp", "rad", "n", "q", "pa", "c"]
-        elif k == EXPDISK:
+        elif k in (EXPDISK, GAUSSIAN):
             roles += ["pos", "pos", "amp", "rad", "q", "pa", "c"]
         elif k == SKY:
             roles += ["sky"]

@@ -621,3 +621,50 @@ def test_multistart_reaches_the_oracle_minimum_at_least_as_often(gf):
     n_one = sum(reached(p1[i], i) for i in range(len(sts)))
     assert n_multi >= n_one
     assert n_multi >= 14, (n_multi, n_one)
+
+
+# ---------------------------------------------------------- Gaussian profile
+def gaussian_case():
+    rng = np.random.default_rng(77)
+    kinds = [synth.GAUSSIAN, synth.SERSIC, synth.SKY]
+    # a Sersic index of at most 3: the float32 forward differences of a much
+    # cuspier profile (n ~ 5, a centre 1e4 x above the wings) carry more noise
+    # than the FD bound allows; the analytic columns have no such limit
+    p = synth.random_params(kinds, rng, 45, 61, n_range=(1.0, 3.0), boxy=True)
+    fixed = np.zeros(len(p), np.uint8)
+    return synth.Stamp(45, 61, kinds, p, fixed, synth.moffat_psf(11, 2.5), os_factor=4,
+                       os_box=6, name="gauss45x61")
+
+
+def test_gaussian_model_parity(gf):
+    case = gaussian_case()
+    g = gf.model(gpu_desc(gf, case), case.params).cpu().numpy()
+    o = oracle.model_ext(oracle_desc(case), case.params)
+    assert_pix_close(g, o, what="model gaussian")
+
+
+@pytest.mark.parametrize("analytic", [False, True])
+def test_gaussian_jacobian_parity(gf, analytic):
+    case = gaussian_case()
+    m_true, img, sig = noisy_image(case)
+    p = case.guess()
+    r = gf.jacobian(gpu_desc(gf, case), p, case.fixed, cuda(img), cuda(sig), cuda(case.psf),
+                    analytic=analytic)
+    o = oracle.jacobian(oracle_desc(case), p, case.fixed, case.psf, img, sig, analytic=analytic)
+    J, Jo = r["J"].cpu().numpy(), o["J"]
+    bound = JAC_AN_REL if analytic else 2e-3
+    for f in range(J.shape[0]):
+        scale = np.abs(Jo[f]).max()
+        assert np.abs(J[f] - Jo[f]).max() <= bound * scale, (f, analytic)
+
+
+def test_gaussian_lm_fit_reaches_oracle(gf):
+    case = gaussian_case()
+    m_true, img, sig = noisy_image(case)
+    od = oracle_desc(case)
+    po, ro = oracle.lm_fit(od, case.guess(), case.fixed, case.psf, img, sig)
+    pg, rg = gf.lm_fit(gpu_desc(gf, case), case.guess(), case.fixed, cuda(img), cuda(sig),
+                       cuda(case.psf))
+    assert rg["status"] in (gf.OK, gf.EMAXITER), rg
+    xg, _ = oracle.evaluate(od, pg, case.psf, img, sig)
+    assert xg <= ro["chi2"] * (1 + CHI2_REL), (xg, ro["chi2"])

@@ -188,3 +188,50 @@ def test_stamp64_central_intensity():
     # the 64x64 workload's n = 4 component peaks at I_e e^{b_4} = 2141.47354...
     p = np.array([32.3, 31.7, 1.0, 8.0, 4.0, 0.7, 30.0, 0.0])
     assert abs(oracle.comp_value(S, p, 32.3, 31.7) - 2141.47354) < 1e-4
+
+
+# ---------------------------------------------------------------- Gaussian
+def _gauss_sigma(fwhm):
+    return fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+
+
+def test_gaussian_is_the_sersic_half_profile():
+    # a Sersic n = 1/2 profile is a Gaussian: b_1/2 = ln 2 gives
+    # I_e exp(-ln 2 ((r/r_e)^2 - 1)) = 2 I_e exp(-r^2 / (2 s^2)) with
+    # r_e^2 = 2 ln 2 s^2; the two formulas of the oracle must agree
+    fwhm, amp = 5.3, 1.7
+    s = _gauss_sigma(fwhm)
+    pg = np.array([1.2, -0.7, amp, fwhm, 0.6, 33.0, 0.0])
+    ps = np.array([1.2, -0.7, amp / 2.0, s * math.sqrt(2.0 * math.log(2.0)), 0.5, 0.6, 33.0, 0.0])
+    rng = np.random.default_rng(0)
+    for x, y in rng.uniform(-12.0, 12.0, (50, 2)):
+        vg = oracle.comp_value(oracle.GAUSSIAN, pg, x, y)
+        vs = oracle.comp_value(oracle.SERSIC, ps, x, y)
+        assert abs(vg - vs) <= 1e-13 * max(abs(vs), 1e-300)
+
+
+def test_gaussian_flux_closed_form():
+    # sum of the sampled profile on a fine grid = 2 pi q I_0 s^2
+    fwhm, amp, q = 4.0, 1.3, 0.7
+    s = _gauss_sigma(fwhm)
+    p = np.array([0.0, 0.0, amp, fwhm, q, 25.0, 0.0])
+    h = 0.05
+    xs = np.arange(-30.0, 30.0, h) + h / 2
+    tot = sum(oracle.comp_value(oracle.GAUSSIAN, p, x, y) for x in xs[::8] for y in xs[::8])
+    tot *= (8 * h) ** 2
+    assert abs(tot - 2.0 * math.pi * q * amp * s * s) < 1e-6 * tot
+
+
+def test_gaussian_gradient_matches_central_differences():
+    p = np.array([2.1, -1.3, 0.9, 6.0, 0.55, 110.0, 0.3])
+    rng = np.random.default_rng(1)
+    for x, y in rng.uniform(-10.0, 10.0, (30, 2)):
+        v, g = oracle.comp_grad(oracle.GAUSSIAN, p, x, y)
+        for s in range(len(p)):
+            h = 1e-5 * max(abs(p[s]), 1.0)
+            pp, pm = p.copy(), p.copy()
+            pp[s] += h
+            pm[s] -= h
+            fd = (oracle.comp_value(oracle.GAUSSIAN, pp, x, y) -
+                  oracle.comp_value(oracle.GAUSSIAN, pm, x, y)) / (2.0 * h)
+            assert abs(g[s] - fd) <= 2e-7 * max(abs(fd), 1e-3 * abs(v)) + 1e-11, (s, x, y)
