@@ -26,10 +26,13 @@
  *       GF_EXPDISK x0, y0, I_0, r_s, q, pa_deg, c          (7 slots)
  *       GF_SKY     s0                                      (1 slot)
  *       GF_GAUSSIAN x0, y0, I_0, fwhm, q, pa_deg, c        (7 slots)
+ *       GF_MOFFAT  x0, y0, I_0, fwhm, beta, q, pa_deg, c   (8 slots)
  *     Sersic: I_e exp(-b_n((r/r_e)^{1/n} - 1)), b_n from P(2n, b_n) = 1/2.
  *     Exponential disk: I_0 exp(-r/r_s).
- *     Gaussian: I_0 exp(-r^2 / (2 s^2)), s = fwhm / (2 sqrt(2 ln 2)) (one of the
- *     further profile families after the Sersic and the disk).
+ *     Gaussian: I_0 exp(-r^2 / (2 s^2)), s = fwhm / (2 sqrt(2 ln 2)).
+ *     Moffat: I_0 (1 + (r/alpha)^2)^(-beta), alpha = fwhm / (2 sqrt(2^(1/beta) - 1)),
+ *     beta in [0.5, 20] by default.  (The Gaussian and the Moffat are further
+ *     profile families after the Sersic and the disk.)
  *     r = (|x'|^{c+2} + |y'/q|^{c+2})^{1/(c+2)}, x' = dx cos t + dy sin t,
  *     y' = -dx sin t + dy cos t, t = pa_deg * pi/180 (counter-clockwise from +x).
  *   - Oversampling: inside an os_box x os_box block of stamp pixels (origin
@@ -79,7 +82,13 @@ typedef enum {
     GF_EMAXITER = 8    /* LM: max_iter trials without meeting a criterion */
 } gf_status;
 
-typedef enum { GF_SERSIC = 1, GF_EXPDISK = 2, GF_SKY = 3, GF_GAUSSIAN = 4 } gf_comp_kind;
+typedef enum {
+    GF_SERSIC = 1,
+    GF_EXPDISK = 2,
+    GF_SKY = 3,
+    GF_GAUSSIAN = 4,
+    GF_MOFFAT = 5
+} gf_comp_kind;
 
 typedef enum {
     GF_CONV_AUTO = 0,   /* direct for P < GF_AUTO_FFT_PSF, else FFT */

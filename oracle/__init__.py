@@ -37,8 +37,8 @@ LIB = os.path.join(HERE, "liboracle.so")
 SRC = os.path.join(HERE, "gfo.c")
 SRC_CNN = os.path.join(HERE, "gfo_cnn.c")
 
-SERSIC, EXPDISK, SKY, GAUSSIAN = 1, 2, 3, 4
-NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7}
+SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT = 1, 2, 3, 4, 5
+NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8}
 CONVERGED, BADINPUT, NOCONV, MAXITER = 0, 1, 3, 8
 
 _lock = threading.Lock()
@@ -100,6 +100,8 @@ def lib():
             L.gfo_gammainc_lower.argtypes = [C.c_double, C.c_double]
             L.gfo_sersic_flux.restype = C.c_double
             L.gfo_sersic_flux.argtypes = [C.c_double] * 4
+            L.gfo_moffat_alpha_per_fwhm.restype = C.c_double
+            L.gfo_moffat_alpha_per_fwhm.argtypes = [C.c_double]
             L.gfo_comp_value.restype = C.c_double
             L.gfo_comp_value.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double]
             L.gfo_model_ext.restype = C.c_int
@@ -197,6 +199,10 @@ def gammainc_lower(a: float, x: float) -> float:
 
 def sersic_flux(Ie, re, n, q) -> float:
     return lib().gfo_sersic_flux(float(Ie), float(re), float(n), float(q))
+
+
+def moffat_alpha_per_fwhm(beta) -> float:
+    return lib().gfo_moffat_alpha_per_fwhm(float(beta))
 
 
 def comp_value(kind, p, x, y) -> float:

@@ -32,6 +32,7 @@ int gfo_comp_nslots(int kind)
     case GFO_SERSIC: return 8;
     case GFO_EXPDISK: return 7;
     case GFO_GAUSSIAN: return 7;
+    case GFO_MOFFAT: return 8;
     case GFO_SKY: return 1;
     default: return -1;
     }
@@ -74,7 +75,7 @@ int gfo_slot_is_linear(const gfo_desc* d, int s)
 }
 
 /* slot semantics: 0 = position, 1 = amplitude, 2 = radius, 3 = Sersic n,
- * 4 = axis ratio, 5 = position angle, 6 = boxiness, 7 = sky */
+ * 4 = axis ratio, 5 = position angle, 6 = boxiness, 7 = sky, 8 = Moffat beta */
 static int slot_role(const gfo_desc* d, int s)
 {
     int k, l, b;
@@ -87,6 +88,10 @@ static int slot_role(const gfo_desc* d, int s)
     if (l == 3) return 2;
     if (kind == GFO_SERSIC) {
         static const int r[8] = {0, 0, 1, 2, 3, 4, 5, 6};
+        return r[l];
+    }
+    if (kind == GFO_MOFFAT) {
+        static const int r[8] = {0, 0, 1, 2, 8, 4, 5, 6};
         return r[l];
     }
     {
@@ -141,17 +146,34 @@ double gfo_sersic_flux(double Ie, double re, double n, double q)
 /* sigma of a Gaussian of full width at half maximum 1: 1 / (2 sqrt(2 ln 2)) */
 static double gauss_sigma_per_fwhm(void) { return 1.0 / (2.0 * sqrt(2.0 * log(2.0))); }
 
+/* alpha of a Moffat profile (1 + (r/alpha)^2)^(-beta) of full width at half
+ * maximum 1: the half maximum sits where (1 + (r/alpha)^2)^beta = 2, so
+ * r = alpha sqrt(2^(1/beta) - 1) = 1/2. */
+double gfo_moffat_alpha_per_fwhm(double beta)
+{
+    return 1.0 / (2.0 * sqrt(pow(2.0, 1.0 / beta) - 1.0));
+}
+
+/* d(alpha/FWHM)/d(beta) / (alpha/FWHM) = 2^(1/beta) ln 2 / (2 beta^2 (2^(1/beta) - 1)) */
+static double moffat_dlnalpha_dbeta(double beta)
+{
+    double t = pow(2.0, 1.0 / beta);
+    return t * log(2.0) / (2.0 * beta * beta * (t - 1.0));
+}
+
 /* Surface brightness of one component at (x, y).
  * Rotation: theta = pa_deg * pi / 180, counter-clockwise from +x to the major
  * axis; x' = dx cos + dy sin, y' = -dx sin + dy cos.
  * Generalised radius: r = (|x'|^C + |y'/q|^C)^{1/C}, C = c + 2.
- * Sersic: I_e exp(-b_n ((r/r_e)^{1/n} - 1)); exponential disk: I_0 exp(-r/r_s). */
+ * Sersic: I_e exp(-b_n ((r/r_e)^{1/n} - 1)); exponential disk: I_0 exp(-r/r_s);
+ * Gaussian: I_0 exp(-r^2 / (2 sigma^2)); Moffat: I_0 (1 + (r/alpha)^2)^(-beta).
+ * The Sersic n and the Moffat beta share slot 4. */
 double gfo_comp_value(int kind, const double* p, double x, double y, double bn)
 {
     if (kind == GFO_SKY) return p[0];
     double x0 = p[0], y0 = p[1], amp = p[2], rs = p[3];
     double n = 1.0, q, pa, c;
-    if (kind == GFO_SERSIC) {
+    if (kind == GFO_SERSIC || kind == GFO_MOFFAT) {
         n = p[4];
         q = p[5];
         pa = p[6];
@@ -171,6 +193,10 @@ double gfo_comp_value(int kind, const double* p, double x, double y, double bn)
     if (kind == GFO_GAUSSIAN) {
         double sig = rs * gauss_sigma_per_fwhm();
         return amp * exp(-r * r / (2.0 * sig * sig));
+    }
+    if (kind == GFO_MOFFAT) {
+        double al = rs * gfo_moffat_alpha_per_fwhm(n), t = r / al;
+        return amp * pow(1.0 + t * t, -n);
     }
     return amp * exp(-r / rs);
 }
@@ -198,6 +224,10 @@ double gfo_bn_deriv(double n)
  *   disk, I = I_0 exp(-r/r_s): dI/dr = -I/r_s, dI/dr_s = I r / r_s^2;
  *   Gaussian, I = I_0 exp(-r^2 / (2 s^2)), s = FWHM / (2 sqrt(2 ln 2)):
  *     dI/dr = -I r / s^2, dI/dFWHM = I r^2 / s^3 * ds/dFWHM;
+ *   Moffat, I = I_0 w^(-beta), w = 1 + t^2, t = r/alpha, alpha = FWHM a(beta):
+ *     dI/dr = -2 beta I t / (alpha w),  dI/dalpha = 2 beta I t^2 / (alpha w),
+ *     dI/dFWHM = dI/dalpha * alpha / FWHM,
+ *     dI/dbeta = -I ln w + dI/dalpha * alpha * d ln a / d beta;
  *   amplitude: dI/dA = I/A (the profile at unit amplitude); sky: 1.
  * At r = 0 (a sample exactly on the centre) the geometric derivatives are
  * set to 0.  grad has one entry per slot of the component. */
@@ -211,7 +241,7 @@ double gfo_comp_grad(int kind, const double* p, double x, double y, double bn, d
     double x0 = p[0], y0 = p[1], amp = p[2], rs = p[3];
     double n = 1.0, q, pa, c;
     int iq, ipa, ic, in = -1;
-    if (kind == GFO_SERSIC) {
+    if (kind == GFO_SERSIC || kind == GFO_MOFFAT) {
         n = p[4];
         q = p[5];
         pa = p[6];
@@ -253,6 +283,15 @@ double gfo_comp_grad(int kind, const double* p, double x, double y, double bn, d
         double I = amp * unit;
         dIdr = -I * r / (sig * sig);
         dIdrs = I * r * r / (sig * sig * sig) * k;
+    } else if (kind == GFO_MOFFAT) {
+        double beta = n, al = rs * gfo_moffat_alpha_per_fwhm(beta);
+        double t = r / al, w = 1.0 + t * t;
+        unit = pow(w, -beta);
+        double I = amp * unit;
+        double dIdal = 2.0 * beta * I * t * t / (al * w);
+        dIdr = -2.0 * beta * I * t / (al * w);
+        dIdrs = dIdal * al / rs;
+        dIdn = -I * log(w) + dIdal * al * moffat_dlnalpha_dbeta(beta);
     } else {
         unit = exp(-r / rs);
         double I = amp * unit;
@@ -709,8 +748,8 @@ void gfo_default_opts(gfo_lm_opts* o)
 }
 
 /* Default box: I >= 0, radii >= 0.1, n in [0.2, 10], q in [0.05, 1],
- * boxiness in [-1.9, 2]; positions and sky free; position angles are wrapped
- * into [0, 180) instead of clamped. */
+ * boxiness in [-1.9, 2], Moffat beta in [0.5, 20]; positions and sky free;
+ * position angles are wrapped into [0, 180) instead of clamped. */
 void gfo_default_bounds(const gfo_desc* d, double* lo, double* hi)
 {
     int ns = gfo_nslots(d);
@@ -723,6 +762,7 @@ void gfo_default_bounds(const gfo_desc* d, double* lo, double* hi)
         case 3: lo[s] = 0.2; hi[s] = 10.0; break;
         case 4: lo[s] = 0.05; hi[s] = 1.0; break;
         case 6: lo[s] = -1.9; hi[s] = 2.0; break;
+        case 8: lo[s] = 0.5; hi[s] = 20.0; break;
         default: break;
         }
     }
@@ -786,33 +826,21 @@ static int cholesky_solve(int n, const double* M, const double* b, double* x)
 }
 
 /* Levenberg-Marquardt (Marquardt's diagonal damping), steps 4 and 5 of the
- * loop.  One trial = solve (A + lambda diag A) delta = g, project p + delta
- * into the box, evaluate chi^2 there; accept if chi^2 falls (lambda shrinks,
- * a new Jacobian is taken), otherwise reject (lambda grows).  Finishing
- * criteria: the scaled step falls below xtol, or an accepted step lowers
- * chi^2 by less than ftol relative while the linearised model also predicts
- * a relative fall below ftol (converged; the predicted fall of the damped step
- * is delta^T (g + lambda diag(A) delta)); lambda exceeds lambda_max (no
+ * loop, over any problem that supplies its normal equations, its chi^2, a
+ * projection into its box and the scales of its step test.
+ * One trial = solve (A + lambda diag A) delta = g, project p + delta into the
+ * box, evaluate chi^2 there; accept if chi^2 falls (lambda shrinks, a new
+ * Jacobian is taken), otherwise reject (lambda grows).  Finishing criteria:
+ * the scaled step falls below xtol, or an accepted step lowers chi^2 by less
+ * than ftol relative while the linearised model also predicts a relative fall
+ * below ftol (converged; the predicted fall of the damped step is
+ * delta^T (g + lambda diag(A) delta)); lambda exceeds lambda_max (no
  * convergence); max_iter trials (iteration cap). */
-int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
-               const double* lo_in, const double* hi_in, const double* psf,
-               const double* img, const double* sigma, int method,
-               const gfo_lm_opts* opts_in, gfo_lm_result* res)
+int gfo_lm_core(const gfo_lm_problem* P, double* params, const gfo_lm_opts* o, gfo_lm_result* res)
 {
-    gfo_lm_opts o;
-    if (opts_in)
-        o = *opts_in;
-    else
-        gfo_default_opts(&o);
-    int ns = gfo_nslots(d);
-    double lo[GFO_MAX_SLOTS], hi[GFO_MAX_SLOTS];
-    gfo_default_bounds(d, lo, hi);
-    if (lo_in) memcpy(lo, lo_in, sizeof(double) * ns);
-    if (hi_in) memcpy(hi, hi_in, sizeof(double) * ns);
-    int fs[GFO_MAX_SLOTS], nfree = 0;
-    for (int s = 0; s < ns; ++s)
-        if (!fixed || !fixed[s]) fs[nfree++] = s;
-    gfo_lm_result r = {0.0, o.lambda0, 0, 0, GFO_MAXITER};
+    int ns = P->nslots, nfree = P->nfree;
+    const int* fs = P->free_slots;
+    gfo_lm_result r = {0.0, o->lambda0, 0, 0, GFO_MAXITER};
     if (nfree == 0 || nfree > GFO_MAX_FREE) {
         r.status = GFO_BADINPUT;
         if (res) *res = r;
@@ -820,13 +848,12 @@ int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
     }
     double p[GFO_MAX_SLOTS], pt[GFO_MAX_SLOTS];
     memcpy(p, params, sizeof(double) * ns);
-    project(d, p, lo, hi);
+    P->project(P->ctx, p);
     double A[GFO_MAX_FREE * GFO_MAX_FREE], g[GFO_MAX_FREE], M[GFO_MAX_FREE * GFO_MAX_FREE];
     double rhs[GFO_MAX_FREE], delta[GFO_MAX_FREE];
-    double lambda = o.lambda0;
-    double chi2 = gfo_jacobian(d, p, fixed, psf, img, sigma, method, o.fd_rel, o.jac_mode, NULL,
-                               A, g, NULL);
-    while (r.iters < o.max_iter) {
+    double lambda = o->lambda0;
+    double chi2 = P->normal(P->ctx, p, A, g);
+    while (r.iters < o->max_iter) {
         for (int i = 0; i < nfree; ++i) {
             rhs[i] = g[i];
             for (int j = 0; j < nfree; ++j) M[i * nfree + j] = A[i * nfree + j];
@@ -846,10 +873,10 @@ int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
         if (ok) {
             double step = 0.0;
             for (int i = 0; i < nfree; ++i) {
-                double den = fmax(fabs(p[fs[i]]), xtol_scale(d, fs[i]));
+                double den = fmax(fabs(p[fs[i]]), P->xscale(P->ctx, fs[i]));
                 step = fmax(step, fabs(delta[i]) / den);
             }
-            if (step < o.xtol) {
+            if (step < o->xtol) {
                 r.status = GFO_CONVERGED;
                 break;
             }
@@ -860,25 +887,24 @@ int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
             }
             memcpy(pt, p, sizeof(double) * ns);
             for (int i = 0; i < nfree; ++i) pt[fs[i]] += delta[i];
-            project(d, pt, lo, hi);
-            double chi2t = gfo_eval(d, pt, psf, img, sigma, method, NULL);
+            P->project(P->ctx, pt);
+            double chi2t = P->eval(P->ctx, pt);
             if (isfinite(chi2t) && chi2t < chi2) {
                 double rel = (chi2 - chi2t) / chi2;
                 memcpy(p, pt, sizeof(double) * ns);
                 r.accepted++;
-                lambda = fmax(lambda * o.lambda_down, o.lambda_min);
-                if (rel < o.ftol && pred / chi2 < o.ftol) {
+                lambda = fmax(lambda * o->lambda_down, o->lambda_min);
+                if (rel < o->ftol && pred / chi2 < o->ftol) {
                     chi2 = chi2t;
                     r.status = GFO_CONVERGED;
                     break;
                 }
-                chi2 = gfo_jacobian(d, p, fixed, psf, img, sigma, method, o.fd_rel, o.jac_mode,
-                                    NULL, A, g, NULL);
+                chi2 = P->normal(P->ctx, p, A, g);
                 continue;
             }
         }
-        lambda *= o.lambda_up;
-        if (lambda > o.lambda_max) {
+        lambda *= o->lambda_up;
+        if (lambda > o->lambda_max) {
             r.status = GFO_NOCONV;
             break;
         }
@@ -888,6 +914,62 @@ int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
     memcpy(params, p, sizeof(double) * ns);
     if (res) *res = r;
     return r.status;
+}
+
+/* the stamp problem of gfo_lm_fit for gfo_lm_core */
+typedef struct {
+    const gfo_desc* d;
+    const uint8_t* fixed;
+    const double *lo, *hi, *psf, *img, *sigma;
+    int method;
+    const gfo_lm_opts* o;
+} stamp_problem;
+
+static double stamp_normal(void* ctx, const double* p, double* A, double* g)
+{
+    const stamp_problem* q = (const stamp_problem*)ctx;
+    return gfo_jacobian(q->d, p, q->fixed, q->psf, q->img, q->sigma, q->method, q->o->fd_rel,
+                        q->o->jac_mode, NULL, A, g, NULL);
+}
+
+static double stamp_eval(void* ctx, const double* p)
+{
+    const stamp_problem* q = (const stamp_problem*)ctx;
+    return gfo_eval(q->d, p, q->psf, q->img, q->sigma, q->method, NULL);
+}
+
+static void stamp_project(void* ctx, double* p)
+{
+    const stamp_problem* q = (const stamp_problem*)ctx;
+    project(q->d, p, q->lo, q->hi);
+}
+
+static double stamp_xscale(void* ctx, int s)
+{
+    return xtol_scale(((const stamp_problem*)ctx)->d, s);
+}
+
+int gfo_lm_fit(const gfo_desc* d, double* params, const uint8_t* fixed,
+               const double* lo_in, const double* hi_in, const double* psf,
+               const double* img, const double* sigma, int method,
+               const gfo_lm_opts* opts_in, gfo_lm_result* res)
+{
+    gfo_lm_opts o;
+    if (opts_in)
+        o = *opts_in;
+    else
+        gfo_default_opts(&o);
+    int ns = gfo_nslots(d);
+    double lo[GFO_MAX_SLOTS], hi[GFO_MAX_SLOTS];
+    gfo_default_bounds(d, lo, hi);
+    if (lo_in) memcpy(lo, lo_in, sizeof(double) * ns);
+    if (hi_in) memcpy(hi, hi_in, sizeof(double) * ns);
+    int fs[GFO_MAX_SLOTS], nfree = 0;
+    for (int s = 0; s < ns; ++s)
+        if (!fixed || !fixed[s]) fs[nfree++] = s;
+    stamp_problem q = {d, fixed, lo, hi, psf, img, sigma, method, &o};
+    gfo_lm_problem P = {ns, nfree, fs, stamp_normal, stamp_eval, stamp_project, stamp_xscale, &q};
+    return gfo_lm_core(&P, params, &o, res);
 }
 
 int gfo_lm_fit_batch(int nb, const gfo_desc* ds, double* params, const uint8_t* fixed,

@@ -24,6 +24,8 @@
  *   Sersic  (kind 1): x0, y0, I_e, r_e, n, q, pa_deg, c     (8 slots)
  *   ExpDisk (kind 2): x0, y0, I_0, r_s, q, pa_deg, c         (7 slots)
  *   Sky     (kind 3): s0                                     (1 slot)
+ *   Gaussian(kind 4): x0, y0, I_0, FWHM, q, pa_deg, c        (7 slots)
+ *   Moffat  (kind 5): x0, y0, I_0, FWHM, beta, q, pa_deg, c  (8 slots)
  */
 #ifndef GFO_H
 #define GFO_H
@@ -33,6 +35,7 @@
 #define GFO_EXPDISK 2
 #define GFO_SKY 3
 #define GFO_GAUSSIAN 4  /* I_0 exp(-r^2 / (2 sigma^2)), sigma = FWHM / (2 sqrt(2 ln 2)) */
+#define GFO_MOFFAT 5    /* I_0 (1 + (r/alpha)^2)^(-beta), alpha = FWHM / (2 sqrt(2^(1/beta) - 1)) */
 #define GFO_MAX_COMP 8
 #define GFO_MAX_SLOTS 64
 #define GFO_MAX_FREE 16
@@ -73,6 +76,25 @@ typedef struct {
     int status;
 } gfo_lm_result;
 
+/* A least-squares problem as the LM core sees it: nslots parameters of which
+ * the nfree listed in free_slots move; normal() returns chi^2 at p and fills
+ * A = J^T W J (nfree x nfree) and g = J^T W r; eval() returns chi^2 at p;
+ * project() moves p into the box; xscale(s) is the floor of |p_s| in the
+ * scaled step test. */
+typedef struct {
+    int nslots, nfree;
+    const int* free_slots;
+    double (*normal)(void* ctx, const double* p, double* A, double* g);
+    double (*eval)(void* ctx, const double* p);
+    void (*project)(void* ctx, double* p);
+    double (*xscale)(void* ctx, int slot);
+    void* ctx;
+} gfo_lm_problem;
+
+/* Levenberg-Marquardt over any such problem (the rules of gfo_lm_fit). */
+int gfo_lm_core(const gfo_lm_problem* P, double* params, const gfo_lm_opts* o,
+                gfo_lm_result* res);
+
 int gfo_comp_nslots(int kind);
 int gfo_nslots(const gfo_desc* d);
 
@@ -82,6 +104,8 @@ double gfo_bn(double n);
 double gfo_gammainc_lower(double a, double x);
 /* closed-form total flux of an elliptical (c = 0) Sersic component */
 double gfo_sersic_flux(double Ie, double re, double n, double q);
+/* alpha / FWHM of a Moffat profile of index beta */
+double gfo_moffat_alpha_per_fwhm(double beta);
 
 /* surface brightness of one component at a point (amplitude taken from p) */
 double gfo_comp_value(int kind, const double* p, double x, double y, double bn);

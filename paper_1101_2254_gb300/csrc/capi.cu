@@ -112,6 +112,7 @@ int comp_slots(int kind)
     case GF_EXPDISK: return 7;
     case GF_SKY: return 1;
     case GF_GAUSSIAN: return 7;
+    case GF_MOFFAT: return 8;
     default: return -1;
     }
 }
@@ -321,6 +322,9 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
             } else if (kind == GF_SERSIC) {
                 static const int r[8] = {0, 0, 1, 2, R_N, R_Q, R_PA, R_BOXY};
                 role = r[l];
+            } else if (kind == GF_MOFFAT) {
+                static const int r[8] = {0, 0, 1, 2, R_BETA, R_Q, R_PA, R_BOXY};
+                role = r[l];
             } else {
                 static const int r[7] = {0, 0, 1, 2, R_Q, R_PA, R_BOXY};
                 role = r[l];
@@ -334,6 +338,7 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
             case R_N: l0 = 0.2; h0 = 10.0; break;
             case R_Q: l0 = 0.05; h0 = 1.0; break;
             case R_BOXY: l0 = -1.9; h0 = 2.0; break;
+            case R_BETA: l0 = 0.5; h0 = 20.0; break;
             default: break;
             }
             S->lo[s] = lo ? lo[s] : l0;

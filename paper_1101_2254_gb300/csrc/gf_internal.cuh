@@ -30,7 +30,7 @@ enum { CH_SUM = 0, CH_SHAPE = 1, CH_FD = 2, CH_DERIV = 3 };
 enum { PH_NEED_JAC = 0, PH_SOLVE = 1, PH_TRIAL = 2, PH_DONE = 3, PH_NONE = 99 };
 
 // slot roles
-enum { R_POS = 0, R_AMP = 1, R_RAD = 2, R_N = 3, R_Q = 4, R_PA = 5, R_BOXY = 6, R_SKY = 7 };
+enum { R_POS = 0, R_AMP = 1, R_RAD = 2, R_N = 3, R_Q = 4, R_PA = 5, R_BOXY = 6, R_SKY = 7, R_BETA = 8 };
 
 // Float32 constants of one component at one parameter vector.
 struct CompConst {
@@ -38,10 +38,11 @@ struct CompConst {
     float cs, sn, invq;        // rotation and axis ratio
     float C, invC;             // generalised-radius exponent C = c + 2
     float amp;                 // amplitude (1 for unit shapes)
-    float invr;                // 1 / r_e, 1 / r_s, or 1 / s for a Gaussian
-    float invn;                // 1 / n (1 for the disk)
-    float b0, b;               // I = amp * exp(b0 - b * (r invr)^invn)
-    int kind;                  // GF_SERSIC / GF_EXPDISK / GF_SKY / GF_GAUSSIAN
+    float invr;                // 1 / r_e, 1 / r_s, 1 / s (Gaussian), 1 / alpha (Moffat)
+    float invn;                // 1 / n (1 for the disk); beta for a Moffat
+    float b0, b;               // I = amp * exp(b0 - b * (r invr)^invn); Moffat:
+                               // amp * exp(-b log2(1 + (r invr)^2)), b = beta ln 2
+    int kind;                  // GF_SERSIC / GF_EXPDISK / GF_SKY / GF_GAUSSIAN / GF_MOFFAT
     int ellipse;               // C == 2 exactly: r by sqrt
 };
 
@@ -139,15 +140,20 @@ __device__ __forceinline__ float comp_eval(const CompConst& k, float xi, float y
         r = exp2f(k.invC * log2f(ax + ay));
     }
     float t = r * k.invr;
-    float u = (k.invn == 1.0f) ? t : exp2f(k.invn * log2f(t));
+    // one logarithm for every kind: log2 t (Sersic, Gaussian) or log2(1 + t^2)
+    // (Moffat), chosen by selects so the loop body stays branch-free
+    const bool moffat = k.kind == GF_MOFFAT;
+    const float lt = log2f(moffat ? fmaf(t, t, 1.0f) : t);
+    float u = (k.invn == 1.0f) ? t : exp2f(k.invn * lt);
+    u = moffat ? lt : u;
     return k.amp * expf(fmaf(-k.b, u, k.b0));
 }
 
 // The unit-amplitude profile of component k at grid point (xi + ox, yi + oy)
 // and its derivatives with respect to the component's slots, in slot order
-// (Sersic: x0, y0, amplitude, r_e, n, q, pa, c; disk and Gaussian: x0, y0,
-// amplitude, r_s or fwhm, q, pa, c), by the chain rule through the generalised
-// radius:
+// (Sersic: x0, y0, amplitude, r_e, n, q, pa, c; Moffat: the same with alpha
+// and beta for r_e and n; disk and Gaussian: x0, y0, amplitude, r_s or fwhm, q,
+// pa, c), by the chain rule through the generalised radius:
 //   r^C = |x'|^C + |Y|^C, Y = y'/q:  dr/dx' = sgn(x') (|x'|/r)^(C-1), likewise Y,
 //     dr/dC = r [ (|x'|^C ln|x'| + |Y|^C ln|Y|) / (C r^C) - ln(r^C) / C^2 ];
 //   dx'/dx0 = -cos, dx'/dy0 = -sin, dy'/dx0 = sin, dy'/dy0 = -cos,
@@ -192,21 +198,38 @@ __device__ __forceinline__ float comp_grad(const CompConst& k, float xi, float y
         drdC = r > 0.0f ? r * ln2 * ((lx + ly) / (k.C * S) - l2S * k.invC * k.invC) : 0.0f;
     }
     const float t = r * k.invr;
-    const float u = (k.invn == 1.0f) ? t : exp2f(k.invn * log2f(t));
-    const float Sv = expf(fmaf(-k.b, u, k.b0));
-    // dS/dr and the radius-independent factors
-    const float dSdr = r > 0.0f ? -k.b * Sv * u * k.invn / r : 0.0f;
+    float Sv, dSdr, g3, g4 = 0.0f;
+    if (k.kind == GF_MOFFAT) {
+        // S = w^-beta, w = 1 + t^2:  dS/dr = -2 beta S t / (alpha w),
+        // dS/dalpha = 2 beta S t^2 / (alpha w) (the channel scale carries
+        // alpha / fwhm), dS/dbeta = S (-ln w + 2 beta t^2 / w * dbdn) with dbdn
+        // standing for d ln(alpha / fwhm) / d beta
+        const float beta = k.invn, w = fmaf(t, t, 1.0f), iw = 1.0f / w, l2w = log2f(w);
+        Sv = expf(-k.b * l2w);
+        const float s2 = 2.0f * beta * Sv * t * iw * k.invr;
+        dSdr = -s2;
+        g3 = s2 * t;
+        g4 = Sv * fmaf(2.0f * beta * t * t * iw, dbdn, -0.69314718055994531f * l2w);
+    } else {
+        const float u = (k.invn == 1.0f) ? t : exp2f(k.invn * log2f(t));
+        Sv = expf(fmaf(-k.b, u, k.b0));
+        dSdr = r > 0.0f ? -k.b * Sv * u * k.invn / r : 0.0f;
+        g3 = k.b * Sv * u * k.invn * k.invr;  // with respect to 1/invr (r_e, r_s, or s)
+        if (k.kind == GF_GAUSSIAN) g3 *= 0.42466090014400952f;  // s = fwhm / (2 sqrt(2 ln 2))
+        if (k.kind == GF_SERSIC) {
+            const float lt = r > 0.0f ? logf(t) : 0.0f;
+            g4 = Sv * fmaf(1.0f - u, dbdn, k.b * u * lt * k.invn * k.invn);
+        }
+    }
     g[0] = dSdr * fmaf(drdx, -k.cs, drdY * (k.sn * k.invq));
     g[1] = dSdr * fmaf(drdx, -k.sn, drdY * (-k.cs * k.invq));
     g[2] = Sv;
-    g[3] = k.b * Sv * u * k.invn * k.invr;  // with respect to 1/invr (r_e, r_s, or s)
-    if (k.kind == GF_GAUSSIAN) g[3] *= 0.42466090014400952f;  // s = fwhm / (2 sqrt(2 ln 2))
+    g[3] = g3;
     const float dq = dSdr * drdY * (-Y * k.invq);
     const float dpa = dSdr * fmaf(drdx, yp, drdY * (-xp * k.invq)) * 0.017453292519943295f;
     const float dc = dSdr * drdC;
-    if (k.kind == GF_SERSIC) {
-        const float lt = r > 0.0f ? logf(t) : 0.0f;
-        g[4] = Sv * fmaf(1.0f - u, dbdn, k.b * u * lt * k.invn * k.invn);
+    if (k.kind == GF_SERSIC || k.kind == GF_MOFFAT) {  // slot 4 is n or beta
+        g[4] = g4;
         g[5] = dq;
         g[6] = dpa;
         g[7] = dc;

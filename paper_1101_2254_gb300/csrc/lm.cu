@@ -37,6 +37,19 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 // sigma of a Gaussian per unit full width at half maximum, 1 / (2 sqrt(2 ln 2))
 constexpr double kGaussSigmaPerFwhm = 0.42466090014400952136;
+constexpr double kLn2 = 0.69314718055994530942;
+
+// alpha / fwhm of a Moffat profile of index beta, 1 / (2 sqrt(2^(1/beta) - 1)),
+// and d ln(alpha / fwhm) / d beta = 2^(1/beta) ln 2 / (2 beta^2 (2^(1/beta) - 1))
+__device__ __forceinline__ double moffat_alpha_per_fwhm(double beta)
+{
+    return 0.5 / sqrt(exp2(1.0 / beta) - 1.0);
+}
+__device__ __forceinline__ double moffat_dlnalpha_dbeta(double beta)
+{
+    const double t = exp2(1.0 / beta);
+    return t * kLn2 / (2.0 * beta * beta * (t - 1.0));
+}
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerBlock = 4;
 
@@ -174,7 +187,7 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
     const double amp = unit_amp ? 1.0 : q[2];
     const double r = q[3];
     double ax, pa, c;
-    if (kind == GF_SERSIC) {
+    if (kind == GF_SERSIC || kind == GF_MOFFAT) {  // slot 4 is n or beta
         ax = q[5];
         pa = q[6];
         c = q[7];
@@ -201,6 +214,16 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
         k.invn = 2.0f;
         k.b0 = 0.0f;
         k.b = 0.5f;
+    }
+    if (kind == GF_MOFFAT) {
+        // (1 + t^2)^(-beta) = exp(-b u) with u = log2(1 + t^2), b = beta ln 2,
+        // t = r / alpha, alpha = fwhm / (2 sqrt(2^(1/beta) - 1)); invn carries
+        // beta for the gradient
+        const double beta = q[4];
+        k.invr = (float)(2.0 * sqrt(exp2(1.0 / beta) - 1.0) / r);
+        k.invn = (float)beta;
+        k.b0 = 0.0f;
+        k.b = (float)(beta * kLn2);
     }
     if (kind == GF_SERSIC) {
         const double n = q[4];
@@ -380,12 +403,19 @@ __device__ void warp_build_jac(const Structure& S, WarpScratch& W, float psum, C
             ch.scale = (float)amp_of(S, W.p, comp);
             ch.dslot = slot - S.slot0[comp];
             ch.dbdn = S.kinds[comp] == GF_SERSIC ? (float)W.dbdn[comp] : 0.0f;
+            if (S.kinds[comp] == GF_MOFFAT) {
+                // the gradient's slot 3 is d/d alpha: alpha / fwhm turns it into
+                // d/d fwhm; slot 4 takes d ln(alpha / fwhm) / d beta
+                const double beta = W.p[S.slot0[comp] + 4];
+                if (ch.dslot == 3) ch.scale = (float)(amp_of(S, W.p, comp) * moffat_alpha_per_fwhm(beta));
+                ch.dbdn = (float)moffat_dlnalpha_dbeta(beta);
+            }
             ch.pert = W.cc[comp];
         } else {
             const int role = S.role[slot];
             const double h = fd_step(role, W.p[slot], S.opts.fd_rel);
             double q[8];
-            const int ns = S.kinds[comp] == GF_SERSIC ? 8 : 7;
+            const int ns = (S.kinds[comp] == GF_SERSIC || S.kinds[comp] == GF_MOFFAT) ? 8 : 7;
             for (int t = 0; t < ns; ++t) q[t] = W.p[S.slot0[comp] + t];
             q[slot - S.slot0[comp]] += h;
             ch.mweight = 0.0f;

@@ -186,105 +186,163 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
     }
 }
 
-__global__ void __launch_bounds__(RED_THREADS) k_reduce_chi2(PassArgs a)
+// Where the chi^2 pass's current item sits: its stamp, the stamp's offsets and
+// the end of the stamp's item range, kept in registers so that the next item of
+// the same stamp is found without the dependent loads of the work-list search.
+struct Chi2Loc {
+    int b, end, blk0, local;
+    long long HW, pix_off, yoff;
+};
+
+__device__ __forceinline__ void chi2_locate(Chi2Loc& L, const PassArgs& a, const int* pre, int n,
+                                            int it, int& hint)
+{
+    const int li = wl_locate(pre, n, it, hint);
+    L.b = a.wl.ids[li];
+    L.end = pre[li + 1];
+    L.local = it - pre[li];
+    L.blk0 = a.pre_static[WK_RED * (a.count + 1) + L.b];
+    const StampInfo& st = a.st[L.b];
+    L.HW = (long long)st.H * st.W;
+    L.pix_off = st.pix_off;
+    L.yoff = y_index(st, a.nchan, 0);
+}
+
+// the item after L's, in the work list's order
+__device__ __forceinline__ void chi2_advance(Chi2Loc& L, const PassArgs& a, const int* pre, int n,
+                                             int it, int& hint)
+{
+    if (it < L.end)
+        ++L.local;
+    else
+        chi2_locate(L, a, pre, n, it, hint);
+}
+
+// The values one thread reads for one item: RED_CHUNKS consecutive pixels
+// base + RED_CHUNKS t + e of the image, sigma and model.  Where the stamp's
+// arrays are 16-byte aligned and its pixel count a multiple of 4 they come in
+// one 16-byte load each; otherwise by single loads.  The values are not used
+// here, so the loads stay in flight while the caller finishes the previous
+// item.
+struct Chi2Vals {
+    float m[RED_CHUNKS], dv[RED_CHUNKS], sv[RED_CHUNKS];
+};
+
+__device__ __forceinline__ void chi2_fetch(Chi2Vals& q, const Chi2Loc& L, const PassArgs& a)
+{
+    const long long p0 = (long long)L.local * RED_PIX + (long long)RED_CHUNKS * threadIdx.x;
+    const float* Y = a.y + L.yoff;
+    const float* img = a.img + L.pix_off;
+    const float* sig = a.sig + L.pix_off;
+    const bool has_img = a.img != nullptr;
+    const bool vec = ((L.pix_off | L.HW | L.yoff) & 3) == 0 && p0 < L.HW;
+    if (vec) {
+        const float4 y4 = __ldg(reinterpret_cast<const float4*>(Y + p0));
+        q.m[0] = y4.x; q.m[1] = y4.y; q.m[2] = y4.z; q.m[3] = y4.w;
+        if (has_img) {
+            const float4 d4 = __ldg(reinterpret_cast<const float4*>(img + p0));
+            const float4 s4 = __ldg(reinterpret_cast<const float4*>(sig + p0));
+            q.dv[0] = d4.x; q.dv[1] = d4.y; q.dv[2] = d4.z; q.dv[3] = d4.w;
+            q.sv[0] = s4.x; q.sv[1] = s4.y; q.sv[2] = s4.z; q.sv[3] = s4.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < RED_CHUNKS; ++e) q.dv[e] = q.sv[e] = 0.0f;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < RED_CHUNKS; ++e) {
+            const long long px = p0 + e;
+            const bool in = px < L.HW;
+            q.m[e] = in ? __ldg(&Y[px]) : 0.0f;
+            q.dv[e] = (in && has_img) ? __ldg(&img[px]) : 0.0f;
+            q.sv[e] = (in && has_img) ? __ldg(&sig[px]) : 0.0f;
+        }
+    }
+}
+
+// chi^2 partials, one per work item of RED_PIX pixels.  A block walks its
+// contiguous range of items with the loads of item i + 1 issued before the
+// reduction tree of item i, so the tree, its barrier and the partial's store
+// hide under the next item's memory latency.  Each item is summed in the same
+// per-thread order and the same tree whatever its neighbours, so a stamp's
+// chi^2 does not depend on the batch around it.
+__global__ void __launch_bounds__(RED_THREADS, 4) k_reduce_chi2(PassArgs a)
 {
     pdl_entry();
-    __shared__ ChanInfo ci;
-    __shared__ float msky;
-    __shared__ CSum wsum[RED_THREADS / 32];
+    __shared__ CSum wsum[2][RED_THREADS / 32];  // by item parity: one barrier per item
+    static_assert(RED_CHUNKS == 4, "one float4 per thread and array");
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_RED * (a.count + 1);
     const int tot = pre[n];
     int hint = -1;
     const int chunk = (tot + gridDim.x - 1) / gridDim.x;
     const int it0 = blockIdx.x * chunk, it1 = min(tot, it0 + chunk);
-    for (int it = it0; it < it1; ++it) {
-    const int li = wl_locate(pre, n, it, hint);
-    const int b = a.wl.ids[li];
-    const int local = it - pre[li];
-    const int blk = a.pre_static[WK_RED * (a.count + 1) + b] + local;  // partial slot
-    const StampInfo st = a.st[b];
-    __syncthreads();
-    load_chan_info(ci, msky, a, b);
-    __syncthreads();
-    const long long HW = (long long)st.H * st.W;
-    const float* img = a.img + st.pix_off;
-    const float* sig = a.sig + st.pix_off;
-    const float* Y = a.y + y_index(st, a.nchan, 0);
-    CSum acc = {0.0f, 0.0f};
-    const long long base = (long long)local * RED_PIX;
-    // Thread t takes the RED_CHUNKS consecutive pixels base + RED_CHUNKS t + e
-    // and sums them in order e.  Where the stamp's arrays are 16-byte aligned
-    // and its pixel count a multiple of 4, the image, sigma and model values
-    // come in one 16-byte load each; otherwise by single loads.  The order of
-    // the sums is the same either way, so chi^2 does not depend on where a
-    // stamp sits in a batch.
-    static_assert(RED_CHUNKS == 4, "one float4 per thread and array");
-    const long long p0 = base + (long long)RED_CHUNKS * threadIdx.x;
     const bool has_img = a.img != nullptr;
-    float m[RED_CHUNKS], dv[RED_CHUNKS], sv[RED_CHUNKS];
-    const bool vec = ((st.pix_off | HW | y_index(st, a.nchan, 0)) & 3) == 0 && p0 < HW;
-    if (vec) {
-        const float4 y4 = __ldg(reinterpret_cast<const float4*>(Y + p0));
-        m[0] = y4.x; m[1] = y4.y; m[2] = y4.z; m[3] = y4.w;
-        if (has_img) {
-            const float4 d4 = __ldg(reinterpret_cast<const float4*>(img + p0));
-            const float4 s4 = __ldg(reinterpret_cast<const float4*>(sig + p0));
-            dv[0] = d4.x; dv[1] = d4.y; dv[2] = d4.z; dv[3] = d4.w;
-            sv[0] = s4.x; sv[1] = s4.y; sv[2] = s4.z; sv[3] = s4.w;
-        } else {
-#pragma unroll
-            for (int e = 0; e < RED_CHUNKS; ++e) dv[e] = sv[e] = 0.0f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (it0 >= it1) return;
+    Chi2Loc cl, nl;
+    Chi2Vals cv, nv;
+    chi2_locate(cl, a, pre, n, it0, hint);
+    chi2_fetch(cv, cl, a);
+    for (int it = it0; it < it1; ++it) {
+        nl = cl;
+        if (it + 1 < it1) {
+            chi2_advance(nl, a, pre, n, it + 1, hint);
+            chi2_fetch(nv, nl, a);
         }
-    } else {
+        const long long p0 = (long long)cl.local * RED_PIX + (long long)RED_CHUNKS * threadIdx.x;
+        // the model: channel weights of this stamp (read through the cache;
+        // every thread of the block reads the same words)
+        const Channel* ch = a.chan + (long long)cl.b * a.chan_stride;
+        const float msky = ch[0].msky, mw0 = ch[0].mweight;
+        float m[RED_CHUNKS];
+#pragma unroll
+        for (int e = 0; e < RED_CHUNKS; ++e) m[e] = fmaf(mw0, cv.m[e], msky);
+        if (a.nchan > 1) {
+            const float* Y = a.y + cl.yoff;
+#pragma unroll
+            for (int e = 0; e < RED_CHUNKS; ++e) {
+                const long long px = p0 + e;
+                for (int k = 1; k < a.nchan; ++k)
+                    if (px < cl.HW) m[e] = fmaf(ch[k].mweight, Y[(long long)k * cl.HW + px], m[e]);
+            }
+        }
+        float* m_out = a.m_out ? a.m_out + cl.pix_off : nullptr;
+        CSum acc = {0.0f, 0.0f};
 #pragma unroll
         for (int e = 0; e < RED_CHUNKS; ++e) {
             const long long px = p0 + e;
-            const bool in = px < HW;
-            m[e] = in ? __ldg(&Y[px]) : 0.0f;
-            dv[e] = (in && has_img) ? __ldg(&img[px]) : 0.0f;
-            sv[e] = (in && has_img) ? __ldg(&sig[px]) : 0.0f;
+            if (px >= cl.HW) break;
+            if (m_out) m_out[px] = m[e];
+            if (!has_img) continue;  // model only
+            const float d = cv.dv[e], s = cv.sv[e];
+            if (isfinite(d) && isfinite(s) && s > 0.0f) {
+                const float z = (d - m[e]) / s;
+                csum_add(acc, z * z);
+            }
         }
-    }
+        // deterministic shuffle tree, then across warps
 #pragma unroll
-    for (int e = 0; e < RED_CHUNKS; ++e) {
-        const long long px = p0 + e;
-        m[e] = fmaf(ci.mw[0], m[e], msky);
-        for (int k = 1; k < a.nchan; ++k)
-            if (px < HW) m[e] = fmaf(ci.mw[k], Y[(long long)k * HW + px], m[e]);
-    }
-#pragma unroll
-    for (int e = 0; e < RED_CHUNKS; ++e) {
-        const long long px = p0 + e;
-        if (px >= HW) break;
-        if (a.m_out) a.m_out[st.pix_off + px] = m[e];
-        if (!has_img) continue;  // model only
-        const float d = dv[e], s = sv[e];
-        if (isfinite(d) && isfinite(s) && s > 0.0f) {
-            const float z = (d - m[e]) / s;
-            csum_add(acc, z * z);
+        for (int o = 16; o > 0; o >>= 1) {
+            CSum other;
+            other.s = __shfl_down_sync(0xffffffffu, acc.s, o);
+            other.c = __shfl_down_sync(0xffffffffu, acc.c, o);
+            acc = csum_merge(acc, other);
         }
-    }
-    // deterministic shuffle tree, then across warps
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        CSum other;
-        other.s = __shfl_down_sync(0xffffffffu, acc.s, o);
-        other.c = __shfl_down_sync(0xffffffffu, acc.c, o);
-        acc = csum_merge(acc, other);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) wsum[warp] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        CSum t = wsum[0];
-        for (int w = 1; w < RED_THREADS / 32; ++w) t = csum_merge(t, wsum[w]);
-        a.partial[blk] = t.s + t.c;
-        if (a.work) {
-            const long long np = min((long long)RED_PIX, HW - base);
-            atomicAdd(&a.work[PROF_REDUCE], (unsigned long long)np * (4ull * a.nchan + 8ull));
+        CSum* ws = wsum[it & 1];
+        if (lane == 0) ws[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            CSum t = ws[0];
+            for (int w = 1; w < RED_THREADS / 32; ++w) t = csum_merge(t, ws[w]);
+            a.partial[cl.blk0 + cl.local] = t.s + t.c;
+            if (a.work) {
+                const long long np = min((long long)RED_PIX, cl.HW - (long long)cl.local * RED_PIX);
+                atomicAdd(&a.work[PROF_REDUCE], (unsigned long long)np * (4ull * a.nchan + 8ull));
+            }
         }
-    }
+        cl = nl;
+        cv = nv;
     }
 }
 
@@ -516,9 +574,9 @@ cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s)
 cudaError_t launch_reduce_chi2(const PassArgs& a, cudaStream_t s)
 {
     if (a.maxitems[WK_RED] > 0) {
-        // light CTAs: eight per SM are resident, and every one keeps its loads
-        // in flight
-        const int g = (int)std::min<long long>(a.maxitems[WK_RED], 152LL * 8);
+        // one wave: four CTAs per SM are resident (64 registers a thread), and
+        // each keeps two items' loads in flight
+        const int g = (int)std::min<long long>(a.maxitems[WK_RED], 152LL * 4);
         GF_LAUNCH_PDL(k_reduce_chi2, dim3(g), dim3(RED_THREADS), 0, s, a);
         GF_COUNT_LAUNCH();
     }

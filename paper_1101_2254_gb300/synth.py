@@ -30,8 +30,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-SERSIC, EXPDISK, SKY, GAUSSIAN = 1, 2, 3, 4
-NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7}
+SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT = 1, 2, 3, 4, 5
+NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8}
 
 SIGMA_READ = 0.01
 GAIN = 1.0
@@ -88,11 +88,13 @@ def noise_sigma(m_true: np.ndarray, sigma_read: float = SIGMA_READ, gain: float 
 
 # ------------------------------------------------------------ parameters
 def slot_roles(kinds):
-    """Role name per slot: pos, amp, rad, n, q, pa, c, sky."""
+    """Role name per slot: pos, amp, rad, n, beta, q, pa, c, sky."""
     roles = []
     for k in kinds:
         if k == SERSIC:
             roles += ["pos", "pos", "amp", "rad", "n", "q", "pa", "c"]
+        elif k == MOFFAT:
+            roles += ["pos", "pos", "amp", "rad", "beta", "q", "pa", "c"]
         elif k in (EXPDISK, GAUSSIAN):
             roles += ["pos", "pos", "amp", "rad", "q", "pa", "c"]
         elif k == SKY:
@@ -127,6 +129,8 @@ def perturb_guess(kinds, p_true, fixed, seed: int, frac: float = 0.2):
             p[i] = min(max(p[i], 0.05), 1.0)
         elif r == "n":
             p[i] = min(max(p[i], 0.2), 10.0)
+        elif r == "beta":
+            p[i] = min(max(p[i], 0.5), 20.0)
         elif r == "rad":
             p[i] = max(p[i], 0.1)
         elif r == "pa":
@@ -242,7 +246,7 @@ def batch_stamps(count: int = 4096, seed: int = 21, smin: int = 32, smax: int = 
     return out
 
 
-def random_params(kinds, rng, H, W, n_range=(0.5, 6.0), boxy=False):
+def random_params(kinds, rng, H, W, n_range=(0.5, 6.0), boxy=False, beta_range=(1.5, 6.0)):
     """Random but well-inside-the-stamp parameters for parity tests."""
     p = []
     for k in kinds:
@@ -258,6 +262,8 @@ def random_params(kinds, rng, H, W, n_range=(0.5, 6.0), boxy=False):
         c = rng.uniform(-0.5, 0.5) if boxy else 0.0
         if k == SERSIC:
             p += [x0, y0, amp, r, rng.uniform(*n_range), q, pa, c]
+        elif k == MOFFAT:
+            p += [x0, y0, amp, r, rng.uniform(*beta_range), q, pa, c]
         else:
             p += [x0, y0, amp, r, q, pa, c]
     return np.array(p, np.float64)

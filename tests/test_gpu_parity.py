@@ -636,16 +636,34 @@ def gaussian_case():
                        os_box=6, name="gauss45x61")
 
 
-def test_gaussian_model_parity(gf):
-    case = gaussian_case()
+def moffat_case():
+    # a boxy Moffat source beside a discy exponential disk, apart and bright
+    # (peak S/N ~ 20 under the gain-1 noise), so that the fit is well posed;
+    # odd sizes, the oversampled block between them
+    kinds = [synth.MOFFAT, synth.EXPDISK, synth.SKY]
+    p = np.array([15.3, 17.8, 400.0, 5.5, 2.6, 0.75, 62.0, 0.25,
+                  29.1, 33.4, 90.0, 6.5, 0.55, 128.0, -0.3,
+                  2.0])
+    fixed = np.zeros(len(p), np.uint8)
+    return synth.Stamp(52, 47, kinds, p, fixed, synth.moffat_psf(9, 2.2), os_factor=3,
+                       os_box=8, name="moffat52x47")
+
+
+FAMILY_CASES = {"gaussian": gaussian_case, "moffat": moffat_case}
+
+
+@pytest.mark.parametrize("family", sorted(FAMILY_CASES))
+def test_family_model_parity(gf, family):
+    case = FAMILY_CASES[family]()
     g = gf.model(gpu_desc(gf, case), case.params).cpu().numpy()
     o = oracle.model_ext(oracle_desc(case), case.params)
-    assert_pix_close(g, o, what="model gaussian")
+    assert_pix_close(g, o, what=f"model {family}")
 
 
 @pytest.mark.parametrize("analytic", [False, True])
-def test_gaussian_jacobian_parity(gf, analytic):
-    case = gaussian_case()
+@pytest.mark.parametrize("family", sorted(FAMILY_CASES))
+def test_family_jacobian_parity(gf, family, analytic):
+    case = FAMILY_CASES[family]()
     m_true, img, sig = noisy_image(case)
     p = case.guess()
     r = gf.jacobian(gpu_desc(gf, case), p, case.fixed, cuda(img), cuda(sig), cuda(case.psf),
@@ -655,16 +673,19 @@ def test_gaussian_jacobian_parity(gf, analytic):
     bound = JAC_AN_REL if analytic else 2e-3
     for f in range(J.shape[0]):
         scale = np.abs(Jo[f]).max()
-        assert np.abs(J[f] - Jo[f]).max() <= bound * scale, (f, analytic)
+        assert np.abs(J[f] - Jo[f]).max() <= bound * scale, (family, f, analytic)
 
 
-def test_gaussian_lm_fit_reaches_oracle(gf):
-    case = gaussian_case()
+@pytest.mark.parametrize("analytic", [False, True])
+@pytest.mark.parametrize("family", sorted(FAMILY_CASES))
+def test_family_lm_fit_reaches_oracle(gf, family, analytic):
+    case = FAMILY_CASES[family]()
     m_true, img, sig = noisy_image(case)
     od = oracle_desc(case)
     po, ro = oracle.lm_fit(od, case.guess(), case.fixed, case.psf, img, sig)
+    opts = gf.default_opts(jac_mode=gf.JAC_ANALYTIC if analytic else gf.JAC_FD)
     pg, rg = gf.lm_fit(gpu_desc(gf, case), case.guess(), case.fixed, cuda(img), cuda(sig),
-                       cuda(case.psf))
+                       cuda(case.psf), opts=opts)
     assert rg["status"] in (gf.OK, gf.EMAXITER), rg
     xg, _ = oracle.evaluate(od, pg, case.psf, img, sig)
-    assert xg <= ro["chi2"] * (1 + CHI2_REL), (xg, ro["chi2"])
+    assert xg <= ro["chi2"] * (1 + CHI2_REL), (family, xg, ro["chi2"])

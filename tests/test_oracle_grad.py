@@ -33,6 +33,8 @@ CASES = [
     (oracle.SERSIC, [5.0, 1.0, 1.7, 12.0, 7.0, 0.55, 5.0, 1.2]),
     (oracle.EXPDISK, [3.1, -1.7, 0.9, 8.0, 0.6, 80.0, 0.0]),
     (oracle.EXPDISK, [-4.0, 2.2, 1.4, 5.0, 0.85, 140.0, -0.7]),
+    (oracle.MOFFAT, [2.0, -3.0, 1.1, 4.0, 2.5, 0.6, 20.0, 0.0]),
+    (oracle.MOFFAT, [-1.0, 1.5, 0.7, 7.0, 0.9, 0.8, 95.0, -0.4]),
 ]
 
 
@@ -42,8 +44,9 @@ def test_comp_grad_matches_central_differences(case):
     p = np.array(p, np.float64)
     rng = np.random.default_rng(case)
     pts = rng.uniform(-25.0, 25.0, (40, 2))
-    c = p[7] if kind == oracle.SERSIC else p[6]
-    q, pa = (p[5], p[6]) if kind == oracle.SERSIC else (p[4], p[5])
+    eight = kind in (oracle.SERSIC, oracle.MOFFAT)  # slot 4 is n or beta
+    c = p[7] if eight else p[6]
+    q, pa = (p[5], p[6]) if eight else (p[4], p[5])
     th = math.radians(pa)
     for x, y in pts:
         if math.hypot(x - p[0], y - p[1]) < 0.3:
@@ -86,18 +89,22 @@ def test_bn_derivative_asymptotic_series(n):
     assert abs(oracle.bn_deriv(n) - d) < bound
 
 
-def _small_stamp():
+def _small_stamp(moffat=False):
     kinds = [oracle.SERSIC, oracle.EXPDISK, oracle.SKY]
-    p = np.array([14.6, 12.3, 1.2, 4.0, 2.7, 0.65, 40.0, 0.3,
-                  14.1, 12.9, 0.4, 6.0, 0.8, 120.0, 0.0,
-                  0.05])
+    p = [14.6, 12.3, 1.2, 4.0, 2.7, 0.65, 40.0, 0.3,
+         14.1, 12.9, 0.4, 6.0, 0.8, 120.0, 0.0,
+         0.05]
+    if moffat:
+        kinds = [oracle.MOFFAT] + kinds
+        p = [13.2, 15.1, 0.9, 3.5, 2.2, 0.7, 75.0, -0.3] + p
     d = oracle.make_desc(27, 30, 7, kinds, os_factor=4, os_box=6)
-    return d, p
+    return d, np.array(p)
 
 
-def test_model_grid_gradient_matches_differences():
+@pytest.mark.parametrize("moffat", [False, True])
+def test_model_grid_gradient_matches_differences(moffat):
     # the extended grid with its oversampled block, every nonlinear slot
-    d, p = _small_stamp()
+    d, p = _small_stamp(moffat)
     for s in range(len(p)):
         if oracle.slot_is_linear(d, s):
             continue
@@ -112,8 +119,9 @@ def test_model_grid_gradient_matches_differences():
         assert np.abs(an - fd).max() <= 1e-6 * scale, (s, np.abs(an - fd).max(), scale)
 
 
-def test_analytic_jacobian_columns_match_central_differences():
-    d, p = _small_stamp()
+@pytest.mark.parametrize("moffat", [False, True])
+def test_analytic_jacobian_columns_match_central_differences(moffat):
+    d, p = _small_stamp(moffat)
     st_psf = synth.random_psf(7, 3)
     img = oracle.render(d, p, st_psf) + 0.01
     sig = np.full_like(img, 0.02)

@@ -235,3 +235,83 @@ def test_gaussian_gradient_matches_central_differences():
             fd = (oracle.comp_value(oracle.GAUSSIAN, pp, x, y) -
                   oracle.comp_value(oracle.GAUSSIAN, pm, x, y)) / (2.0 * h)
             assert abs(g[s] - fd) <= 2e-7 * max(abs(fd), 1e-3 * abs(v)) + 1e-11, (s, x, y)
+
+
+# ---------------------------------------------------------------- Moffat
+def test_moffat_half_maximum_at_half_fwhm():
+    # the FWHM slot is what its name says: I = I_0 / 2 at r = FWHM / 2 on the
+    # major axis and at q FWHM / 2 on the minor axis, for any beta
+    for beta in (0.8, 1.0, 2.5, 4.765, 12.0):
+        fwhm, amp, q, pa = 3.7, 2.2, 0.6, 40.0
+        p = np.array([0.5, -1.0, amp, fwhm, beta, q, pa, 0.0])
+        th = math.radians(pa)
+        for rr, ang in ((fwhm / 2, th), (q * fwhm / 2, th + math.pi / 2)):
+            x, y = 0.5 + rr * math.cos(ang), -1.0 + rr * math.sin(ang)
+            assert abs(oracle.comp_value(oracle.MOFFAT, p, x, y) - amp / 2) < 1e-13
+        assert oracle.comp_value(oracle.MOFFAT, p, 0.5, -1.0) == amp
+
+
+def test_moffat_flux_closed_form():
+    # integral over the plane of (1 + r^2/alpha^2)^(-beta) on an ellipse of
+    # axis ratio q: pi q alpha^2 / (beta - 1), beta > 1
+    fwhm, amp, q, beta = 3.0, 0.8, 0.75, 3.5
+    al = fwhm * oracle.moffat_alpha_per_fwhm(beta)
+    p = np.array([0.0, 0.0, amp, fwhm, beta, q, 70.0, 0.0])
+    # polar quadrature in the component's own frame, r up to 4000 alpha
+    # (the tail beyond holds (4000)^(2 - 2 beta) / (beta - 1) of the flux)
+    from scipy.integrate import quad
+    th = math.radians(70.0)
+
+    def ring(r):
+        # the ellipse of radius r: points (r cos t, q r sin t) in the frame
+        v = oracle.comp_value(oracle.MOFFAT, p, r * math.cos(th), r * math.sin(th))
+        return 2.0 * math.pi * q * r * v
+    tot = quad(ring, 0.0, 4000.0 * al, limit=400, epsabs=0.0, epsrel=1e-12)[0]
+    assert abs(tot - math.pi * q * amp * al * al / (beta - 1.0)) < 1e-8 * tot
+
+
+def test_moffat_large_beta_is_the_gaussian():
+    # (1 + r^2/alpha^2)^(-beta) with alpha^2 = FWHM^2 / (4 (2^(1/beta) - 1))
+    # tends to exp(-a), a = 4 ln2 r^2 / FWHM^2, the Gaussian of the same FWHM.
+    # Expanding 2^(1/beta) - 1 and ln(1 + z) to second order in 1/beta:
+    #   ln(I_Moffat / I_Gauss) = (a^2 - a ln 2) / (2 beta) + O(a^3 / beta^2)
+    fwhm = 4.4
+    pg = np.array([0.0, 0.0, 1.0, fwhm, 0.8, 10.0, 0.0])
+    for beta in (1e3, 1e5):
+        pm = np.array([0.0, 0.0, 1.0, fwhm, beta, 0.8, 10.0, 0.0])
+        for x, y in ((0.7, 0.2), (2.0, -1.5), (-3.0, 2.5)):
+            vg = oracle.comp_value(oracle.GAUSSIAN, pg, x, y)
+            vm = oracle.comp_value(oracle.MOFFAT, pm, x, y)
+            a = -math.log(vg)
+            first = (a * a - a * math.log(2.0)) / (2.0 * beta)
+            assert abs(math.log(vm / vg) - first) <= 10.0 * (1.0 + a ** 3) / beta ** 2, \
+                (beta, x, y, math.log(vm / vg), first)
+
+
+def test_moffat_beta_one_closed_form():
+    # beta = 1: alpha = FWHM / 2 and I = I_0 / (1 + (2 r / FWHM)^2)
+    p = np.array([1.0, 2.0, 1.5, 6.0, 1.0, 1.0, 0.0, 0.0])
+    for x, y in ((4.0, 2.0), (1.0, -3.0), (-2.0, 6.0)):
+        r = math.hypot(x - 1.0, y - 2.0)
+        assert abs(oracle.comp_value(oracle.MOFFAT, p, x, y) - 1.5 / (1.0 + (2 * r / 6.0) ** 2)) < 1e-14
+
+
+@pytest.mark.parametrize("c", [0.0, 0.4])
+def test_moffat_gradient_matches_central_differences(c):
+    p = np.array([-1.2, 0.7, 1.4, 5.0, 2.7, 0.65, 128.0, c])
+    rng = np.random.default_rng(2)
+    th = math.radians(p[6])
+    for x, y in rng.uniform(-10.0, 10.0, (30, 2)):
+        xp = (x - p[0]) * math.cos(th) + (y - p[1]) * math.sin(th)
+        yq = (-(x - p[0]) * math.sin(th) + (y - p[1]) * math.cos(th)) / p[5]
+        if c != 0.0 and min(abs(xp), abs(yq)) < 1.0:
+            continue  # as for the Sersic pins: differences lose accuracy on the axes
+        v, g = oracle.comp_grad(oracle.MOFFAT, p, x, y)
+        for s in range(len(p)):
+            h = 1e-5 * max(abs(p[s]), 1.0)
+            pp, pm = p.copy(), p.copy()
+            pp[s] += h
+            pm[s] -= h
+            fd = (oracle.comp_value(oracle.MOFFAT, pp, x, y) -
+                  oracle.comp_value(oracle.MOFFAT, pm, x, y)) / (2.0 * h)
+            assert abs(g[s] - fd) <= 2e-7 * max(abs(fd), 1e-3 * abs(v)) + 1e-11, (s, x, y)
