@@ -36,6 +36,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
 SRC = os.path.join(HERE, "gfo.c")
 SRC_CNN = os.path.join(HERE, "gfo_cnn.c")
+SRC_SPEC = os.path.join(HERE, "gfo_spec.c")
 
 SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT = 1, 2, 3, 4, 5
 NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8}
@@ -46,14 +47,16 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile gfo.c into liboracle.so with gcc (portable flags, OpenMP)."""
+    """Compile gfo.c, gfo_cnn.c and gfo_spec.c into liboracle.so with gcc
+    (portable flags, OpenMP)."""
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
-        os.path.getmtime(SRC), os.path.getmtime(SRC_CNN), os.path.getmtime(os.path.join(HERE, "gfo.h"))
+        os.path.getmtime(SRC), os.path.getmtime(SRC_CNN), os.path.getmtime(SRC_SPEC),
+        os.path.getmtime(os.path.join(HERE, "gfo.h"))
     ):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
-           "-D_GNU_SOURCE", SRC, SRC_CNN, "-o", tmp, "-lm"]
+           "-D_GNU_SOURCE", SRC, SRC_CNN, SRC_SPEC, "-o", tmp, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB
@@ -366,6 +369,128 @@ def lm_fit_batch(descs, params, fixed, psf_flat, psf_off, img_flat, sigma_flat, 
 
 def num_threads() -> int:
     return lib().gfo_num_threads()
+
+
+# ---------------------------------------------------------------- spectral lines
+class SpecDesc(C.Structure):
+    _fields_ = [("n_chan", C.c_int), ("n_lines", C.c_int), ("n_cont", C.c_int),
+                ("lsf_len", C.c_int)]
+
+
+def spec_desc(n_chan, n_lines, n_cont, lsf_len) -> SpecDesc:
+    return SpecDesc(int(n_chan), int(n_lines), int(n_cont), int(lsf_len))
+
+
+def spec_nparams(d: SpecDesc) -> int:
+    return d.n_cont + 3 * d.n_lines
+
+
+def _spec_lib():
+    L = lib()
+    if not getattr(L, "_spec_ready", False):
+        dp, sd = C.POINTER(C.c_double), C.POINTER(SpecDesc)
+        L.gfo_spec_value.restype = C.c_double
+        L.gfo_spec_value.argtypes = [sd, dp, C.c_double]
+        L.gfo_spec_grad.restype = C.c_double
+        L.gfo_spec_grad.argtypes = [sd, dp, C.c_int, C.c_double]
+        L.gfo_spec_model_ext.argtypes = [sd, dp, C.c_int, dp]
+        L.gfo_spec_convolve.argtypes = [sd, dp, dp, dp]
+        L.gfo_spec_eval.restype = C.c_double
+        L.gfo_spec_eval.argtypes = [sd, dp, dp, dp, dp, dp]
+        L.gfo_spec_fd_step.restype = C.c_double
+        L.gfo_spec_fd_step.argtypes = [sd, C.c_int, C.c_double, C.c_double]
+        L.gfo_spec_jacobian.restype = C.c_double
+        L.gfo_spec_jacobian.argtypes = [sd, dp, C.c_char_p, dp, dp, dp, C.c_int, C.c_double,
+                                        dp, dp, dp]
+        L.gfo_spec_default_bounds.argtypes = [sd, dp, dp]
+        L.gfo_spec_fit.restype = C.c_int
+        L.gfo_spec_fit.argtypes = [sd, dp, C.c_char_p, dp, dp, dp, dp, dp, C.POINTER(Opts),
+                                   C.POINTER(Result)]
+        L.gfo_spec_fit_batch.restype = C.c_int
+        L.gfo_spec_fit_batch.argtypes = [C.c_int, sd, dp, C.c_char_p, dp, C.c_int, dp, dp,
+                                         C.POINTER(Opts), C.POINTER(Result)]
+        L._spec_ready = True
+    return L
+
+
+def spec_value(d: SpecDesc, p, x) -> float:
+    return _spec_lib().gfo_spec_value(C.byref(d), _dp(_f64(p)), float(x))
+
+
+def spec_grad(d: SpecDesc, p, s, x) -> float:
+    return _spec_lib().gfo_spec_grad(C.byref(d), _dp(_f64(p)), int(s), float(x))
+
+
+def spec_model_ext(d: SpecDesc, p, slot: int = -1) -> np.ndarray:
+    E = np.zeros(d.n_chan + d.lsf_len - 1)
+    _spec_lib().gfo_spec_model_ext(C.byref(d), _dp(_f64(p)), int(slot), _dp(E))
+    return E
+
+
+def spec_convolve(d: SpecDesc, E, lsf) -> np.ndarray:
+    m = np.zeros(d.n_chan)
+    _spec_lib().gfo_spec_convolve(C.byref(d), _dp(_f64(E)), _dp(_f64(lsf)), _dp(m))
+    return m
+
+
+def spec_eval(d: SpecDesc, p, lsf, spec=None, sig=None):
+    """(chi^2, convolved model); chi^2 is 0 without data."""
+    m = np.zeros(d.n_chan)
+    x2 = _spec_lib().gfo_spec_eval(C.byref(d), _dp(_f64(p)), _dp(_f64(lsf)), _dp(_f64(spec)),
+                                   _dp(_f64(sig)), _dp(m))
+    return x2, m
+
+
+def spec_fd_step(d: SpecDesc, s, v, fd_rel=1e-3) -> float:
+    return _spec_lib().gfo_spec_fd_step(C.byref(d), int(s), float(v), float(fd_rel))
+
+
+def spec_jacobian(d: SpecDesc, p, fixed, lsf, spec, sig, mode=JAC_FORWARD, fd_rel=1e-3):
+    """dict(J [nfree, N], A, g, chi2)."""
+    npar = spec_nparams(d)
+    fx = _fixed_bytes(fixed, npar)
+    nf = npar if fixed is None else int(npar - np.count_nonzero(np.asarray(fixed)))
+    J = np.zeros((max(nf, 1), d.n_chan))
+    A = np.zeros((max(nf, 1), max(nf, 1)))
+    g = np.zeros(max(nf, 1))
+    x2 = _spec_lib().gfo_spec_jacobian(C.byref(d), _dp(_f64(p)), fx, _dp(_f64(lsf)),
+                                       _dp(_f64(spec)), _dp(_f64(sig)), int(mode), float(fd_rel),
+                                       _dp(J), _dp(A), _dp(g))
+    return dict(J=J[:nf], A=A[:nf, :nf], g=g[:nf], chi2=x2)
+
+
+def spec_default_bounds(d: SpecDesc):
+    n = spec_nparams(d)
+    lo, hi = np.zeros(n), np.zeros(n)
+    _spec_lib().gfo_spec_default_bounds(C.byref(d), _dp(lo), _dp(hi))
+    return lo, hi
+
+
+def spec_fit(d: SpecDesc, params, fixed, lsf, spec, sig, opts: Opts | None = None,
+             lo=None, hi=None):
+    """Returns (params, dict(chi2, lam, iters, accepted, status))."""
+    p = np.array(params, np.float64, copy=True)
+    r = Result()
+    _spec_lib().gfo_spec_fit(C.byref(d), _dp(p), _fixed_bytes(fixed, spec_nparams(d)),
+                             _dp(_f64(lo)), _dp(_f64(hi)), _dp(_f64(lsf)), _dp(_f64(spec)),
+                             _dp(_f64(sig)), C.byref(opts) if opts is not None else None,
+                             C.byref(r))
+    return p, dict(chi2=r.chi2, lam=r.lam, iters=r.iters, accepted=r.accepted, status=r.status)
+
+
+def spec_fit_batch(d: SpecDesc, params, fixed, lsf, spec, sig, opts: Opts | None = None):
+    """Independent spectra (count x N), OpenMP across spectra.  lsf: L values
+    shared by all, or count x L."""
+    p = np.array(params, np.float64, copy=True)
+    count = p.shape[0]
+    lsf = _f64(lsf)
+    per = int(lsf.ndim == 2)
+    res = (Result * count)()
+    _spec_lib().gfo_spec_fit_batch(count, C.byref(d), _dp(p), _fixed_bytes(fixed, spec_nparams(d)),
+                                   _dp(lsf), per, _dp(_f64(spec)), _dp(_f64(sig)),
+                                   C.byref(opts) if opts is not None else None, res)
+    return p, [dict(chi2=r.chi2, lam=r.lam, iters=r.iters, accepted=r.accepted, status=r.status)
+               for r in res]
 
 
 # ---------------------------------------------------------------- network

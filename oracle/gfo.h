@@ -199,4 +199,33 @@ void gfo_cnn_input(const double* img, const double* sigma, int H, int W, double*
 void gfo_cnn_encode(const double* p, int H, int W, double* t);
 void gfo_cnn_decode(const double* t, int H, int W, double* p);
 
+/* ------------------------------------------------ spectral lines (gfo_spec.c)
+ * One-dimensional form of the loop: spectra of n_chan channels, a continuum
+ * polynomial of n_cont terms and n_lines Gaussian lines (A, mu, s each),
+ * convolved with an odd line-spread function of lsf_len taps.  Parameters
+ * [a_0 .. a_{n_cont-1}, A_0, mu_0, s_0, A_1, ...]. */
+typedef struct {
+    int n_chan, n_lines, n_cont, lsf_len;
+} gfo_spec_desc;
+
+int gfo_spec_nparams(const gfo_spec_desc* d);
+int gfo_spec_slot_is_linear(const gfo_spec_desc* d, int s);
+double gfo_spec_value(const gfo_spec_desc* d, const double* p, double x);
+double gfo_spec_grad(const gfo_spec_desc* d, const double* p, int s, double x);
+void gfo_spec_model_ext(const gfo_spec_desc* d, const double* p, int slot, double* E);
+void gfo_spec_convolve(const gfo_spec_desc* d, const double* E, const double* lsf, double* m);
+double gfo_spec_eval(const gfo_spec_desc* d, const double* p, const double* lsf,
+                     const double* spec, const double* sig, double* m_out);
+double gfo_spec_fd_step(const gfo_spec_desc* d, int s, double v, double fd_rel);
+double gfo_spec_jacobian(const gfo_spec_desc* d, const double* p, const uint8_t* fixed,
+                         const double* lsf, const double* spec, const double* sig, int mode,
+                         double fd_rel, double* J, double* A, double* g);
+void gfo_spec_default_bounds(const gfo_spec_desc* d, double* lo, double* hi);
+int gfo_spec_fit(const gfo_spec_desc* d, double* params, const uint8_t* fixed,
+                 const double* lo, const double* hi, const double* lsf, const double* spec,
+                 const double* sig, const gfo_lm_opts* opts, gfo_lm_result* res);
+int gfo_spec_fit_batch(int count, const gfo_spec_desc* d, double* params, const uint8_t* fixed,
+                       const double* lsf, int lsf_per_spectrum, const double* spec,
+                       const double* sig, const gfo_lm_opts* opts, gfo_lm_result* res);
+
 #endif
