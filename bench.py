@@ -42,6 +42,8 @@ METRICB = ("fits/s to oracle chi2 (4096 Sersic+sky stamps, sides 32-256, Moffat 
            "8-param batched LM)")
 METRICL = ("fits/s to oracle chi2 (65536 64x64 Sersic+sky stamps, Moffat 33x33, learned CNN "
            "start with default-guess fallback, 8-param batched LM)")
+METRICC = ("spectra fitted/s to oracle chi2 (128x128-spaxel cube, 2048 channels, 3 Gaussian "
+           "lines + linear continuum, Gaussian LSF 25 taps, 11-param batched LM)")
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM traffic per launch of the dominant kernel class, from one ncu capture
@@ -92,11 +94,13 @@ def parse():
     ap.add_argument("--impl", default="gf", choices=["gf", "reference"])
     ap.add_argument("--workload", default="stamp512",
                     choices=["stamp512", "stamp64", "batch4096", "precision64x1024",
-                             "learned65536"])
+                             "learned65536", "cube128x2048"])
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle timing (for profiler runs)")
     ap.add_argument("--stamps", type=int, default=None,
                     help="learned65536: number of stamps (default 65536; smaller for profiler runs)")
+    ap.add_argument("--cube-side", type=int, default=128,
+                    help="cube128x2048: spaxels per side (default 128; smaller for profiler runs)")
     ap.add_argument("--jac", default="fd", choices=["fd", "analytic"],
                     help="Jacobian columns of the nonlinear slots: forward differences (the "
                          "method's own) or analytic derivatives")
@@ -668,6 +672,149 @@ def run_batch(args):
     gd.finalize(ws_)
 
 
+# ------------------------------------------------------------------ cube arm
+def run_cube(args):
+    """An integral-field cube fitted spaxel by spaxel: one batched spectral LM
+    launch over its 16384 spectra (the loop in one dimension)."""
+    import torch
+    ws_, rank, local = dist_env()
+    from paper_1101_2254_gb300 import dist as gd
+    gd.init(ws_)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1101_2254_gb300 import build, gf, synth
+    build.build()
+    cube = synth.spec_cube(args.cube_side, 2048, seed=0)
+    d = gf.make_spec_desc(cube.n_chan, cube.n_lines, cube.n_cont, cube.lsf.size)
+    lsf_d = torch.as_tensor(cube.lsf).to(dev)
+    # untimed setup: the spectra rendered and noised on the device, resident in HBM
+    model = gf.spec_model(d, cube.params, lsf_d)
+    spec_d, sig_d = gf.noise(model, seed=cube.noise_seed, sigma_read=0.01, gain=1.0)
+    del model
+    start = cube.guess()
+    start_d = torch.as_tensor(start).to(dev)
+    out_d = torch.empty_like(start_d)
+    opts = gf.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL, jac_mode=jac_mode(gf, args))
+    stream = torch.cuda.current_stream()
+
+    def fit():
+        return gf.spec_fit(d, start_d, None, spec_d, sig_d, lsf_d, opts=opts, out=out_d)
+
+    for _ in range(max(args.warmup, 0)):
+        fit()
+    torch.cuda.synchronize()
+    gd.barrier(ws_)
+    step_ms, res = [], None
+    with ClockSampler(local) as clk:
+        launches0 = gf.launch_count()
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, res = fit()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        launches = gf.launch_count() - launches0
+    total_ms = gd.max_over_ranks(float(sum(step_ms)), ws_)
+    value = cube.count * args.steps * ws_ / (total_ms / 1e3)
+    with gf.Profiler() as prof:
+        fit()
+    pr = prof.result
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    # one launch per step: the kernel's duration is the step's
+    ach = pr["conv"]["work"] / (pr["conv"]["ms"] / 1e3) / 1e12
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    rr = gf.spec_results(res)
+    iters = np.array([r["iters"] for r in rr])
+    status = np.array([r["status"] for r in rr])
+
+    # end to end through the public calls: spectra, sigma and starts from
+    # pinned host memory each step, fitted parameters and results read back
+    spec_h = spec_d.cpu().pin_memory()
+    sig_h = sig_d.cpu().pin_memory()
+    start_h = torch.as_tensor(start).pin_memory()
+    out_h = torch.empty_like(start_h).pin_memory()
+    res_h = torch.empty((cube.count, res.shape[1]), dtype=torch.uint8).pin_memory()
+
+    def e2e_step():
+        sd = spec_h.to(dev, non_blocking=True)
+        gd_ = sig_h.to(dev, non_blocking=True)
+        pd = start_h.to(dev, non_blocking=True)
+        po, ro = gf.spec_fit(d, pd, None, sd, gd_, lsf_d, opts=opts)
+        out_h.copy_(po, non_blocking=True)
+        res_h.copy_(ro, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = gd.max_over_ranks(e0.elapsed_time(e1), ws_)
+    h2d = spec_h.numel() * 4 * 2 + start_h.numel() * 8
+    d2h = out_h.numel() * 8 + res_h.numel()
+    line = {"metric": METRICC, "value": value, "unit": "fits/s", "n_gpus": ws_,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded)",
+            "config": {"workload": "cube128x2048" if args.cube_side == 128 else
+                       f"cube{args.cube_side}x2048", "spectra": cube.count,
+                       "channels": cube.n_chan, "lines": cube.n_lines,
+                       "continuum_terms": cube.n_cont, "lsf": int(cube.lsf.size),
+                       "free_params": int(cube.params.shape[1]), "lm_tol": BENCH_TOL,
+                       "jacobian": args.jac,
+                       "l2": f"inputs ({cube.count * cube.n_chan * 8 / 1e6:.0f} MB)"
+                             + (" larger than L2" if cube.count * cube.n_chan * 8 > 129e6 else ""),
+                       "parallelism": f"replicas{ws_}"},
+            "gpu_launches": launches,
+            "e2e": {"value": cube.count * args.steps * ws_ / (e2e_ms / 1e3), "unit": "fits/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "roofline": {"bound": "alu",
+                         "kernel": "k_spec (useful FLOPs: LSF sums of the model and Jacobian "
+                                   "columns, the normal-matrix triangle, trial chi^2)",
+                         "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "traffic": None},
+            "kernel_ms_per_step": {k: v["ms"] for k, v in pr.items()},
+            "lm": {"iters_median": float(np.median(iters)), "iters_max": int(iters.max()),
+                   "converged": int((status == 0).sum())},
+            "clocks": clk.summary(), "peaks": peak_kind}
+    if rank == 0 and ws_ == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_cube(cube, spec_d, sig_d, start, opts, budget_s=20.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    gd.finalize(ws_)
+
+
+def cpu_baseline_cube(cube, spec_d, sig_d, start, opts, budget_s=20.0):
+    """The oracle's batched spectral LM (OpenMP across spectra) on the first
+    spaxels of the same cube, doubling the count until the budget is spent."""
+    import oracle
+    od = oracle.spec_desc(cube.n_chan, cube.n_lines, cube.n_cont, cube.lsf.size)
+    oo = oracle.default_opts(ftol=opts.ftol, xtol=opts.xtol, jac_mode=(
+        oracle.JAC_ANALYTIC if opts.jac_mode == 1 else oracle.JAC_FORWARD))
+    n, best = 64, None
+    while n <= cube.count:
+        spec = spec_d[:n].cpu().numpy()
+        sig = sig_d[:n].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.spec_fit_batch(od, start[:n], None, cube.lsf, spec, sig, opts=oo)
+        dt = time.perf_counter() - t0
+        best = {"value": n / dt, "unit": "fits/s", "cores": oracle.num_threads(),
+                "kind": "oracle",
+                "sample": f"oracle batched spectral LM (OpenMP across spectra) of the first {n} "
+                          f"of the {cube.count} spaxels, {dt:.1f} s"}
+        if dt > budget_s / 3:
+            break
+        n *= 2
+    return best
+
+
 def cpu_baseline_batch(sts, budget_s=20.0):
     """The oracle's batched LM (OpenMP across stamps) on the first stamps of
     the same batch, doubling the count until the budget is spent."""
@@ -973,5 +1120,7 @@ if __name__ == "__main__":
         run_precision(a)
     elif a.workload == "learned65536":
         run_learned(a)
+    elif a.workload == "cube128x2048":
+        run_cube(a)
     else:
         run_gf(a)

@@ -474,6 +474,77 @@ gf_status gf_guess_select(int count, const double* cand_dev, const double* chi2_
                           const double* lo_host, const double* hi_host, double* out_dev,
                           int* choice_dev, void* ws, size_t ws_bytes, gf_stream stream);
 
+/* ------------------------------------------------------ spectral lines, cubes
+ * The fitting loop in one dimension (Sec. 5: with a flexible dimensionality
+ * the same procedure fits spectral lines or data cubes; a cube is fitted
+ * spectrum by spectrum, each spaxel's spectrum one entry of a batch).
+ *
+ * A spectrum has n_chan channels; channel i has its centre at x = i.  Its
+ * model on the extended grid x = -c .. n_chan-1+c,
+ *     E(x) = sum_{j < n_cont} a_j t^j + sum_k A_k exp(-(x - mu_k)^2 / (2 s_k^2)),
+ *     t = (x - (n_chan-1)/2) / h,  h = (n_chan-1)/2 (1 when n_chan = 1),
+ * is convolved with an odd line-spread function (LSF) of lsf_len = 2c+1 taps
+ * by the flipped-kernel sum m_i = sum_u lsf[u] E(i + c - u), the stamp
+ * convention in one dimension.  chi^2 as for stamps (finite data, sigma > 0).
+ * Parameters (float64) of a spectrum, in order:
+ *     a_0 .. a_{n_cont-1}, then A_k, mu_k, s_k for each line k
+ * (mu and s in channels).  Default box: s_k >= 0.25, the rest free.
+ * The amplitude and continuum columns of the Jacobian are exact (convolved
+ * basis functions); the centre and width columns are forward differences
+ * (GF_JAC_FD, step fd_rel channels for mu, fd_rel*max(|s|,1) for s) or
+ * analytic derivatives (GF_JAC_ANALYTIC).  The LM rules are those of
+ * gf_lm_fit taken one trial at a time (opts.ladder is not used).
+ * All arrays are device memory unless named *_host; spectra, sigma maps and
+ * models are packed count x n_chan float32, parameters count x nparams
+ * float64.  Nothing is allocated: these calls need no workspace. */
+#define GF_SPEC_MAX_LINES 5
+#define GF_SPEC_MAX_CONT 3
+#define GF_SPEC_MAX_LSF 129
+#define GF_SPEC_MAX_CHAN (1 << 24)
+
+typedef struct {
+    int n_chan;            /* 1 .. GF_SPEC_MAX_CHAN */
+    int n_lines;           /* 0 .. GF_SPEC_MAX_LINES */
+    int n_cont;            /* 0 .. GF_SPEC_MAX_CONT */
+    int lsf_len;           /* odd, 1 .. GF_SPEC_MAX_LSF */
+    int lsf_per_spectrum;  /* 0: one LSF (lsf_len floats) for all; 1: count x lsf_len */
+} gf_spec_desc;
+
+/* n_cont + 3 n_lines, or -1 for an invalid description. */
+int gf_spec_nparams(const gf_spec_desc* d);
+
+/* Convolved models (count x n_chan) at params_dev. */
+gf_status gf_spec_model(const gf_spec_desc* d, int count, const double* params_dev,
+                        const float* lsf_dev, float* model_dev, gf_stream stream);
+
+/* chi^2 of each spectrum (chi2_dev, count float64) and, if model_dev is not
+ * NULL, its convolved model. */
+gf_status gf_spec_eval(const gf_spec_desc* d, int count, const double* params_dev,
+                       const float* spec_dev, const float* sig_dev, const float* lsf_dev,
+                       double* chi2_dev, float* model_dev, gf_stream stream);
+
+/* Normal equations at params_dev over the free slots (fixed_host: nparams
+ * bytes shared by all spectra, nonzero = held; NULL = all free; at most
+ * GF_MAX_FREE free): A_dev count x nf x nf, g_dev count x nf (J^T W r),
+ * chi2_dev count.  jac_mode and fd_rel as in gf_lm_opts. */
+gf_status gf_spec_normal(const gf_spec_desc* d, int count, const double* params_dev,
+                         const uint8_t* fixed_host, const float* spec_dev,
+                         const float* sig_dev, const float* lsf_dev, int jac_mode,
+                         double fd_rel, double* A_dev, double* g_dev, double* chi2_dev,
+                         gf_stream stream);
+
+/* Batched LM: every spectrum fitted independently from its row of params_dev
+ * (projected into the box first) into params_out_dev (may equal params_dev);
+ * result_dev receives count gf_lm_result.  lo_host / hi_host: nparams bounds
+ * or NULL for the defaults.  A spectrum's result does not depend on the
+ * batch around it.  Returns once the launch is queued; the results are ready
+ * when the stream is. */
+gf_status gf_spec_fit(const gf_spec_desc* d, int count, const double* params_dev,
+                      const uint8_t* fixed_host, const double* lo_host, const double* hi_host,
+                      const float* spec_dev, const float* sig_dev, const float* lsf_dev,
+                      const gf_lm_opts* opts, double* params_out_dev, gf_lm_result* result_dev,
+                      gf_stream stream);
+
 /* ------------------------------------------------------------ diagnostics
  * Not part of the method; used to measure the library (no counterpart in the
  * paper).  Kernel classes: 0 model evaluation, 1 convolution, 2 reductions,

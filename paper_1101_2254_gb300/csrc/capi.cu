@@ -18,6 +18,7 @@
 #include "conv_dft.cuh"
 #include "conv_fft.cuh"
 #include "gf_internal.cuh"
+#include "spec.cuh"
 
 std::atomic<long long> g_launch_count{0};
 
@@ -1981,3 +1982,168 @@ gf_status gf_guess_select(int count, const double* cand, const double* chi2_cand
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ spectral lines, cubes
+
+namespace {
+
+gf_status check_spec(const gf_spec_desc* d, int count)
+{
+    if (!d) return fail(GF_EINVAL, "NULL spectral description");
+    if (d->n_chan < 1 || d->n_chan > GF_SPEC_MAX_CHAN)
+        return fail(GF_EINVAL, "n_chan must be 1 .. " + std::to_string(GF_SPEC_MAX_CHAN));
+    if (d->n_lines < 0 || d->n_lines > GF_SPEC_MAX_LINES)
+        return fail(GF_EINVAL, "n_lines must be 0 .. " + std::to_string(GF_SPEC_MAX_LINES));
+    if (d->n_cont < 0 || d->n_cont > GF_SPEC_MAX_CONT)
+        return fail(GF_EINVAL, "n_cont must be 0 .. " + std::to_string(GF_SPEC_MAX_CONT));
+    if (d->n_cont + d->n_lines < 1) return fail(GF_EINVAL, "a spectrum needs a continuum or a line");
+    if (d->lsf_len < 1 || d->lsf_len > GF_SPEC_MAX_LSF || (d->lsf_len & 1) == 0)
+        return fail(GF_EINVAL, "lsf_len must be odd, 1 .. " + std::to_string(GF_SPEC_MAX_LSF));
+    if (d->lsf_per_spectrum != 0 && d->lsf_per_spectrum != 1)
+        return fail(GF_EINVAL, "lsf_per_spectrum must be 0 or 1");
+    if (count < 0) return fail(GF_EINVAL, "count must be >= 0");
+    return GF_OK;
+}
+
+SpecArgs spec_args(const gf_spec_desc* d, int count, int mode)
+{
+    SpecArgs a;
+    memset(&a, 0, sizeof(a));
+    a.mode = mode;
+    a.N = d->n_chan;
+    a.K = d->n_lines;
+    a.nc = d->n_cont;
+    a.L = d->lsf_len;
+    a.lsf_stride = d->lsf_per_spectrum ? d->lsf_len : 0;
+    a.count = count;
+    a.np = d->n_cont + 3 * d->n_lines;
+    default_opts(&a.opts);
+    for (int s = 0; s < a.np; ++s) {
+        const bool width = s >= a.nc && (s - a.nc) % 3 == 2;
+        a.lo[s] = width ? 0.25 : -INFINITY;
+        a.hi[s] = INFINITY;
+    }
+    return a;
+}
+
+gf_status spec_free(SpecArgs& a, const uint8_t* fixed)
+{
+    a.nf = 0;
+    for (int s = 0; s < a.np; ++s) {
+        if (fixed && fixed[s]) continue;
+        if (a.nf >= GF_MAX_FREE)
+            return fail(GF_EINVAL, "more than " + std::to_string(GF_MAX_FREE) + " free slots");
+        a.fs[a.nf++] = s;
+    }
+    if (a.nf < 1) return fail(GF_EINVAL, "no free slots");
+    return GF_OK;
+}
+
+gf_status spec_launch(SpecArgs a, gf_stream stream)
+{
+    // profiled as the convolution class: the LSF sums are most of its work
+    ProfScope ps(PROF_CONV, (cudaStream_t)stream);
+    a.work = prof::work_dev ? prof::work_dev + PROF_CONV : nullptr;
+    GF_CUDA(launch_spec(a, (cudaStream_t)stream));
+    return GF_OK;
+}
+
+}  // namespace
+
+int gf_spec_nparams(const gf_spec_desc* d)
+{
+    if (check_spec(d, 0) != GF_OK) return -1;
+    return d->n_cont + 3 * d->n_lines;
+}
+
+gf_status gf_spec_model(const gf_spec_desc* d, int count, const double* params_dev,
+                        const float* lsf_dev, float* model_dev, gf_stream stream)
+{
+    gf_status r = check_spec(d, count);
+    if (r != GF_OK) return r;
+    if (count == 0) return GF_OK;
+    if (!params_dev || !lsf_dev || !model_dev) return fail(GF_EINVAL, "NULL argument");
+    SpecArgs a = spec_args(d, count, SPEC_MODEL);
+    a.p_in = params_dev;
+    a.lsf = lsf_dev;
+    a.model = model_dev;
+    return spec_launch(a, stream);
+}
+
+gf_status gf_spec_eval(const gf_spec_desc* d, int count, const double* params_dev,
+                       const float* spec_dev, const float* sig_dev, const float* lsf_dev,
+                       double* chi2_dev, float* model_dev, gf_stream stream)
+{
+    gf_status r = check_spec(d, count);
+    if (r != GF_OK) return r;
+    if (count == 0) return GF_OK;
+    if (!params_dev || !spec_dev || !sig_dev || !lsf_dev || !chi2_dev)
+        return fail(GF_EINVAL, "NULL argument");
+    SpecArgs a = spec_args(d, count, SPEC_EVAL);
+    a.p_in = params_dev;
+    a.spec = spec_dev;
+    a.sig = sig_dev;
+    a.lsf = lsf_dev;
+    a.chi2 = chi2_dev;
+    a.model = model_dev;
+    return spec_launch(a, stream);
+}
+
+gf_status gf_spec_normal(const gf_spec_desc* d, int count, const double* params_dev,
+                         const uint8_t* fixed_host, const float* spec_dev,
+                         const float* sig_dev, const float* lsf_dev, int jac_mode,
+                         double fd_rel, double* A_dev, double* g_dev, double* chi2_dev,
+                         gf_stream stream)
+{
+    gf_status r = check_spec(d, count);
+    if (r != GF_OK) return r;
+    if (jac_mode != GF_JAC_FD && jac_mode != GF_JAC_ANALYTIC)
+        return fail(GF_EINVAL, "jac_mode must be GF_JAC_FD or GF_JAC_ANALYTIC");
+    SpecArgs a = spec_args(d, count, SPEC_NORMAL);
+    if ((r = spec_free(a, fixed_host)) != GF_OK) return r;
+    if (count == 0) return GF_OK;
+    if (!params_dev || !spec_dev || !sig_dev || !lsf_dev || !A_dev || !g_dev || !chi2_dev)
+        return fail(GF_EINVAL, "NULL argument");
+    a.opts.jac_mode = jac_mode;
+    if (fd_rel > 0.0) a.opts.fd_rel = fd_rel;
+    a.p_in = params_dev;
+    a.spec = spec_dev;
+    a.sig = sig_dev;
+    a.lsf = lsf_dev;
+    a.A = A_dev;
+    a.g = g_dev;
+    a.chi2 = chi2_dev;
+    return spec_launch(a, stream);
+}
+
+gf_status gf_spec_fit(const gf_spec_desc* d, int count, const double* params_dev,
+                      const uint8_t* fixed_host, const double* lo_host, const double* hi_host,
+                      const float* spec_dev, const float* sig_dev, const float* lsf_dev,
+                      const gf_lm_opts* opts, double* params_out_dev, gf_lm_result* result_dev,
+                      gf_stream stream)
+{
+    gf_status r = check_spec(d, count);
+    if (r != GF_OK) return r;
+    SpecArgs a = spec_args(d, count, SPEC_FIT);
+    if ((r = spec_free(a, fixed_host)) != GF_OK) return r;
+    if (opts) a.opts = *opts;
+    if (!(a.opts.fd_rel > 0.0)) a.opts.fd_rel = 1e-3;
+    if (a.opts.jac_mode != GF_JAC_FD && a.opts.jac_mode != GF_JAC_ANALYTIC)
+        return fail(GF_EINVAL, "jac_mode must be GF_JAC_FD or GF_JAC_ANALYTIC");
+    if (a.opts.max_iter < 0) return fail(GF_EINVAL, "max_iter must be >= 0");
+    for (int s = 0; s < a.np; ++s) {
+        if (lo_host) a.lo[s] = lo_host[s];
+        if (hi_host) a.hi[s] = hi_host[s];
+        if (!(a.lo[s] <= a.hi[s])) return fail(GF_EINVAL, "bounds: lo > hi");
+    }
+    if (count == 0) return GF_OK;
+    if (!params_dev || !spec_dev || !sig_dev || !lsf_dev || !params_out_dev || !result_dev)
+        return fail(GF_EINVAL, "NULL argument");
+    a.p_in = params_dev;
+    a.p_out = params_out_dev;
+    a.res = result_dev;
+    a.spec = spec_dev;
+    a.sig = sig_dev;
+    a.lsf = lsf_dev;
+    return spec_launch(a, stream);
+}

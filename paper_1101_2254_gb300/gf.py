@@ -52,6 +52,11 @@ class LMResult(C.Structure):
                 ("accepted", C.c_int), ("status", C.c_int)]
 
 
+class SpecDesc(C.Structure):
+    _fields_ = [("n_chan", C.c_int), ("n_lines", C.c_int), ("n_cont", C.c_int),
+                ("lsf_len", C.c_int), ("lsf_per_spectrum", C.c_int)]
+
+
 class Batch(C.Structure):
     _fields_ = [("count", C.c_int), ("H", C.POINTER(C.c_int)), ("W", C.POINTER(C.c_int)),
                 ("pix_off", C.POINTER(C.c_int64)), ("psf_off", C.POINTER(C.c_int64))]
@@ -157,6 +162,15 @@ def lib():
             L.gf_set_conv_tile_width.restype = C.c_int
             L.gf_set_conv_tile_width.argtypes = [C.c_int, C.c_int, C.c_int]
             L.gf_launch_count.restype = C.c_longlong
+            ps = C.POINTER(SpecDesc)
+            L.gf_spec_nparams.restype = C.c_int
+            L.gf_spec_nparams.argtypes = [ps]
+            L.gf_spec_model.argtypes = [ps, C.c_int, vp, vp, vp, vp]
+            L.gf_spec_eval.argtypes = [ps, C.c_int, vp, vp, vp, vp, vp, vp, vp]
+            L.gf_spec_normal.argtypes = [ps, C.c_int, vp, C.c_char_p, vp, vp, vp, C.c_int,
+                                         C.c_double, vp, vp, vp, vp]
+            L.gf_spec_fit.argtypes = [ps, C.c_int, vp, C.c_char_p, dp, dp, vp, vp, vp,
+                                      C.POINTER(LMOpts), vp, vp, vp]
             L.gf_prof_enable.argtypes = [vp]
             L.gf_prof_times.restype = C.c_int
             L.gf_prof_times.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
@@ -627,3 +641,107 @@ class Profiler:
         self.result = {k: dict(ms=ms[i], launches=n[i], work=w[i])
                        for i, k in enumerate(PROF_CLASSES)}
         return False
+
+
+# ------------------------------------------------------ spectral lines, cubes
+def make_spec_desc(n_chan, n_lines, n_cont, lsf_len, lsf_per_spectrum=False) -> SpecDesc:
+    return SpecDesc(int(n_chan), int(n_lines), int(n_cont), int(lsf_len), int(bool(lsf_per_spectrum)))
+
+
+def spec_nparams(d: SpecDesc) -> int:
+    n = lib().gf_spec_nparams(C.byref(d))
+    if n < 0:
+        _check(EINVAL)
+    return n
+
+
+def _cuda_f64(t, shape):
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda, "expected a CUDA tensor"
+    assert t.dtype == torch.float64 and t.is_contiguous(), "expected contiguous float64"
+    assert t.numel() == int(np.prod(shape)), f"expected {shape} elements, got {t.shape}"
+    return t
+
+
+def _spec_params(d: SpecDesc, params):
+    """params as a contiguous float64 CUDA tensor of count x nparams."""
+    import torch
+    npar = spec_nparams(d)
+    if not isinstance(params, torch.Tensor):
+        params = torch.as_tensor(np.asarray(params, np.float64).reshape(-1, npar), device="cuda")
+    params = params.reshape(-1, npar)
+    return _cuda_f64(params.contiguous(), (params.shape[0], npar)), params.shape[0]
+
+
+def _spec_lsf(d: SpecDesc, lsf, count):
+    return _cuda_f32(lsf, (count if d.lsf_per_spectrum else 1, d.lsf_len))
+
+
+def spec_model(d: SpecDesc, params, lsf, stream=None):
+    """Convolved models (count x n_chan float32) of the spectra in params."""
+    import torch
+    p, count = _spec_params(d, params)
+    _spec_lsf(d, lsf, count)
+    out = torch.empty((count, d.n_chan), dtype=torch.float32, device=p.device)
+    _check(lib().gf_spec_model(C.byref(d), count, _ptr(p), _ptr(lsf), _ptr(out), _stream(stream)))
+    return out
+
+
+def spec_eval(d: SpecDesc, params, spec, sig, lsf, want_model=False, stream=None):
+    """(chi^2 per spectrum, model or None)."""
+    import torch
+    p, count = _spec_params(d, params)
+    for t in (spec, sig):
+        _cuda_f32(t, (count, d.n_chan))
+    _spec_lsf(d, lsf, count)
+    x2 = torch.empty(count, dtype=torch.float64, device=p.device)
+    m = torch.empty((count, d.n_chan), dtype=torch.float32, device=p.device) if want_model else None
+    _check(lib().gf_spec_eval(C.byref(d), count, _ptr(p), _ptr(spec), _ptr(sig), _ptr(lsf),
+                              _ptr(x2), _ptr(m), _stream(stream)))
+    return x2, m
+
+
+def spec_normal(d: SpecDesc, params, fixed, spec, sig, lsf, analytic=False, fd_rel=1e-3,
+                stream=None):
+    """Normal equations over the free slots: dict(A [count, nf, nf], g, chi2)."""
+    import torch
+    p, count = _spec_params(d, params)
+    for t in (spec, sig):
+        _cuda_f32(t, (count, d.n_chan))
+    _spec_lsf(d, lsf, count)
+    npar = spec_nparams(d)
+    nf = npar if fixed is None else int(npar - np.count_nonzero(np.asarray(fixed)))
+    A = torch.empty((count, nf, nf), dtype=torch.float64, device=p.device)
+    g = torch.empty((count, nf), dtype=torch.float64, device=p.device)
+    x2 = torch.empty(count, dtype=torch.float64, device=p.device)
+    _check(lib().gf_spec_normal(C.byref(d), count, _ptr(p), _fixed(fixed), _ptr(spec), _ptr(sig),
+                                _ptr(lsf), JAC_ANALYTIC if analytic else JAC_FD, float(fd_rel),
+                                _ptr(A), _ptr(g), _ptr(x2), _stream(stream)))
+    return dict(A=A, g=g, chi2=x2)
+
+
+def spec_fit(d: SpecDesc, params, fixed, spec, sig, lsf, opts: LMOpts | None = None, lo=None,
+             hi=None, out=None, stream=None):
+    """Batched LM over the spectra (each fitted independently): returns
+    (params tensor count x nparams, result tensor) on the device; see
+    spec_results for the per-spectrum dicts."""
+    import torch
+    p, count = _spec_params(d, params)
+    for t in (spec, sig):
+        _cuda_f32(t, (count, d.n_chan))
+    _spec_lsf(d, lsf, count)
+    out = torch.empty_like(p) if out is None else _cuda_f64(out, tuple(p.shape))
+    res = torch.empty((count, C.sizeof(LMResult)), dtype=torch.uint8, device=p.device)
+    _check(lib().gf_spec_fit(C.byref(d), count, _ptr(p), _fixed(fixed),
+                             _dp(_f64(lo) if lo is not None else None),
+                             _dp(_f64(hi) if hi is not None else None), _ptr(spec), _ptr(sig),
+                             _ptr(lsf), C.byref(opts) if opts is not None else None, _ptr(out),
+                             _ptr(res), _stream(stream)))
+    return out, res
+
+
+def spec_results(res) -> list:
+    """Per-spectrum result dicts from spec_fit's result tensor (copies to the host)."""
+    raw = res.cpu().numpy().tobytes()
+    n = C.sizeof(LMResult)
+    return [_res(LMResult.from_buffer_copy(raw[i * n:(i + 1) * n])) for i in range(len(raw) // n)]

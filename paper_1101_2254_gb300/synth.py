@@ -267,3 +267,117 @@ def random_params(kinds, rng, H, W, n_range=(0.5, 6.0), boxy=False, beta_range=(
         else:
             p += [x0, y0, amp, r, q, pa, c]
     return np.array(p, np.float64)
+
+
+# ------------------------------------------------------ spectral lines, cubes
+def gaussian_lsf(size: int, fwhm: float) -> np.ndarray:
+    """Gaussian line-spread function sampled at channel offsets -c .. c, sum 1
+    (FP64) -> FP32."""
+    assert size % 2 == 1
+    c = (size - 1) // 2
+    s = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    u = np.arange(-c, c + 1, dtype=np.float64)
+    return _normalised_f32(np.exp(-u * u / (2.0 * s * s)))
+
+
+def random_lsf(size: int, seed: int) -> np.ndarray:
+    """Asymmetric positive random LSF (pins the flip of the convolution)."""
+    return _normalised_f32(np.random.default_rng(seed).uniform(0.05, 1.0, size))
+
+
+@dataclass
+class SpecCube:
+    """Spectra of a cube (one per spaxel) or any batch of spectra: everything
+    but the rendered data.  params: count x (n_cont + 3 n_lines)."""
+    n_chan: int
+    n_lines: int
+    n_cont: int
+    params: np.ndarray
+    lsf: np.ndarray              # float32 L (shared) or count x L
+    noise_seed: int = 0
+    guess_seed: int = 1
+    name: str = ""
+
+    @property
+    def count(self) -> int:
+        return self.params.shape[0]
+
+    def guess(self, frac: float = 0.2) -> np.ndarray:
+        """Each amplitude and width p <- p (1 + frac u), each centre moves by
+        frac * width * u, the continuum a_j <- a_j (1 + frac u), u ~ U[-1, 1]
+        from guess_seed; widths are kept at >= 0.25."""
+        rng = np.random.default_rng(self.guess_seed)
+        p = self.params.copy()
+        u = rng.uniform(-1.0, 1.0, p.shape)
+        nc = self.n_cont
+        p[:, :nc] *= 1.0 + frac * u[:, :nc]
+        for k in range(self.n_lines):
+            a, m, s = nc + 3 * k, nc + 3 * k + 1, nc + 3 * k + 2
+            p[:, a] *= 1.0 + frac * u[:, a]
+            p[:, m] += frac * self.params[:, s] * u[:, m]
+            p[:, s] = np.maximum(p[:, s] * (1.0 + frac * u[:, s]), 0.25)
+        return p
+
+
+def spec_batch(count: int, n_chan: int, n_lines: int, n_cont: int, lsf_size: int,
+               seed: int, lsf_fwhm: float = 3.0, per_spectrum_lsf: bool = False,
+               name: str = "") -> SpecCube:
+    """Random spectra: a continuum of level U[20, 80] with a gentle slope and
+    curvature, and lines of amplitude U[30, 300] (one in four absorbing, 0.4 to
+    0.8 of the continuum deep), width U[1.5, 6] channels, centres spread over the
+    middle 80 % of the band at least 4 widths apart."""
+    rng = np.random.default_rng(seed)
+    npar = n_cont + 3 * n_lines
+    p = np.zeros((count, npar))
+    cont = [lambda: rng.uniform(20.0, 80.0), lambda: rng.uniform(-5.0, 5.0),
+            lambda: rng.uniform(-3.0, 3.0)]
+    for b in range(count):
+        for j in range(n_cont):
+            p[b, j] = cont[j]()
+        lo, hi = 0.1 * n_chan, 0.9 * n_chan
+        slots = np.sort(rng.uniform(lo, hi, n_lines))
+        for k in range(n_lines):
+            s = rng.uniform(1.5, 6.0)
+            A = rng.uniform(30.0, 300.0)
+            if rng.uniform() < 0.25:
+                A = -rng.uniform(0.4, 0.8) * (p[b, 0] if n_cont else 50.0)
+            p[b, n_cont + 3 * k:n_cont + 3 * k + 3] = [A, slots[k], s]
+        # separate the lines by at least 4 widths (shift the later ones)
+        for k in range(1, n_lines):
+            prev = p[b, n_cont + 3 * (k - 1) + 1] + 4.0 * max(p[b, n_cont + 3 * (k - 1) + 2],
+                                                            p[b, n_cont + 3 * k + 2])
+            p[b, n_cont + 3 * k + 1] = max(p[b, n_cont + 3 * k + 1], prev)
+    if per_spectrum_lsf:
+        lsf = np.stack([gaussian_lsf(lsf_size, rng.uniform(0.7, 1.3) * lsf_fwhm)
+                        for _ in range(count)])
+    else:
+        lsf = gaussian_lsf(lsf_size, lsf_fwhm)
+    return SpecCube(n_chan, n_lines, n_cont, p, lsf, noise_seed=seed * 7 + 1,
+                    guess_seed=seed * 7 + 2, name=name or f"spec{count}x{n_chan}")
+
+
+def spec_cube(side: int, n_chan: int, lsf_size: int = 25, seed: int = 0) -> SpecCube:
+    """An integral-field cube of side x side spaxels (row-major), each spectrum
+    an emission-line triplet like H-alpha with the [N II] doublet on a sloped
+    continuum: fixed line spacing, a rotation-curve velocity field (centres
+    shift by up to 6 % of the band across the disc), amplitudes falling off
+    with radius, widths 2-4 channels."""
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:side, 0:side].astype(np.float64)
+    xc = yc = (side - 1) / 2.0
+    r = np.hypot(x - xc, y - yc) / max(side / 2.0, 1.0)
+    phi = np.arctan2(y - yc, x - xc)
+    v = 0.06 * n_chan * np.tanh(3.0 * r) * np.cos(phi)  # centre shift in channels
+    base = 0.5 * n_chan + v
+    sep = 0.03 * n_chan
+    amp = 250.0 * np.exp(-1.5 * r) + 20.0
+    p = np.zeros((side * side, 2 + 9))
+    p[:, 0] = (40.0 + 10.0 * rng.uniform(-1, 1, side * side))
+    p[:, 1] = rng.uniform(-3.0, 3.0, side * side)
+    w = rng.uniform(2.0, 4.0, side * side)
+    for k, (off, rel) in enumerate(((-sep, 0.35), (0.0, 1.0), (sep, 0.9))):
+        p[:, 2 + 3 * k] = (amp * rel).ravel() * rng.uniform(0.9, 1.1, side * side)
+        p[:, 3 + 3 * k] = (base + off).ravel()
+        p[:, 4 + 3 * k] = w
+    return SpecCube(n_chan, 3, 2, p, gaussian_lsf(lsf_size, 3.0), noise_seed=seed * 7 + 1,
+                    guess_seed=seed * 7 + 2, name=f"cube{side}x{side}x{n_chan}")

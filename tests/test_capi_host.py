@@ -157,3 +157,54 @@ def test_multistart_validated_before_launch(gf):
     bk = gf.make_batch([64] * 6, [64] * 6, psf_size=25)
     assert L.gf_workspace_size_multistart(C.byref(d), C.byref(b), 3, None) == \
         L.gf_workspace_size_batch(C.byref(d), C.byref(bk), None)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n_chan=0), dict(n_lines=6), dict(n_lines=-1), dict(n_cont=4),
+    dict(n_lines=0, n_cont=0), dict(lsf_len=8), dict(lsf_len=131), dict(lsf_len=0),
+])
+def test_spectral_desc_rejected_before_launch(gf, bad):
+    kw = dict(n_chan=100, n_lines=2, n_cont=2, lsf_len=9)
+    kw.update(bad)
+    d = gf.make_spec_desc(**kw)
+    L = gf.lib()
+    assert L.gf_spec_nparams(C.byref(d)) == -1
+    dummy = C.c_void_p(256)  # never dereferenced: validation fails first
+    st = L.gf_spec_fit(C.byref(d), 4, dummy, None, None, None, dummy, dummy, dummy, None,
+                       dummy, dummy, None)
+    assert st == gf.EINVAL
+    assert L.gf_spec_model(C.byref(d), 4, dummy, dummy, dummy, None) == gf.EINVAL
+
+
+def test_spectral_calls_validate_before_launch(gf):
+    L = gf.lib()
+    dummy = C.c_void_p(256)
+    d = gf.make_spec_desc(100, 5, 3, 9)  # 18 parameters: two must be held
+    assert L.gf_spec_nparams(C.byref(d)) == 18
+    st = L.gf_spec_fit(C.byref(d), 4, dummy, None, None, None, dummy, dummy, dummy, None,
+                       dummy, dummy, None)
+    assert st == gf.EINVAL and b"free slots" in L.gf_last_error()
+    fixed = np.zeros(18, np.uint8)
+    fixed[:3] = 1
+    # all held: no free slot
+    st = L.gf_spec_normal(C.byref(d), 4, dummy, np.ones(18, np.uint8).tobytes(), dummy, dummy,
+                          dummy, gf.JAC_FD, 1e-3, dummy, dummy, dummy, None)
+    assert st == gf.EINVAL
+    # a bad Jacobian mode, bounds with lo > hi, a NULL output: each rejected
+    st = L.gf_spec_normal(C.byref(d), 4, dummy, fixed.tobytes(), dummy, dummy, dummy, 7, 1e-3,
+                          dummy, dummy, dummy, None)
+    assert st == gf.EINVAL
+    lo = np.zeros(18)
+    hi = np.full(18, -1.0)
+    st = L.gf_spec_fit(C.byref(d), 4, dummy, fixed.tobytes(),
+                       lo.ctypes.data_as(C.POINTER(C.c_double)),
+                       hi.ctypes.data_as(C.POINTER(C.c_double)), dummy, dummy, dummy, None,
+                       dummy, dummy, None)
+    assert st == gf.EINVAL and b"lo > hi" in L.gf_last_error()
+    st = L.gf_spec_fit(C.byref(d), 4, dummy, fixed.tobytes(), None, None, dummy, dummy, dummy,
+                       None, dummy, None, None)
+    assert st == gf.EINVAL and b"NULL" in L.gf_last_error()
+    # count 0 is a no-op that touches nothing
+    st = L.gf_spec_fit(C.byref(d), 0, None, fixed.tobytes(), None, None, None, None, None, None,
+                       None, None, None)
+    assert st == gf.OK
