@@ -38,8 +38,12 @@
  *   - Oversampling: inside an os_box x os_box block of stamp pixels (origin
  *     os_x0, os_y0; -1 centres it) a pixel is the mean of os_factor^2 samples at
  *     x = j - 1/2 + (b + 1/2)/os_factor (same in y); elsewhere the pixel centre.
- *   - chi^2 = sum over pixels with finite image and sigma > 0 of
+ *   - chi^2 = sum over pixels with finite image and finite sigma > 0 of
  *     ((image - model)/sigma)^2, accumulated in compensated float32.
+ *   - Bad-pixel masks: a pixel whose sigma is 0 (or negative, infinite or NaN)
+ *     or whose image value is not finite has weight 0 in chi^2, J^T W J and
+ *     J^T W r on every path, so a mask is passed by setting sigma to 0 at the
+ *     masked pixels (the same holds for the channels of spectra).
  *
  * Memory and streams
  *   - The caller owns every buffer.  Pointers named *_dev are device memory;

@@ -160,6 +160,49 @@ def test_lm_fit_stamp64_matches_oracle(gf):
     assert ok, (in_sigma, rel)
 
 
+@pytest.mark.parametrize("how", ["sigma0", "nan_image"])
+def test_lm_fit_with_bad_pixel_mask(gf, how):
+    # 60 pixels corrupted by large positive outliers (cosmic-ray hits), masked
+    # by sigma = 0 or by a NaN image value: the GPU fit reaches the oracle's
+    # masked fit; unmasked, the same outliers pull the fit far from it
+    st = synth.stamp64()
+    m_true, img, sig = noisy_image(st)
+    rng = np.random.default_rng(91)
+    idx = rng.choice(img.size, 60, replace=False)
+    bad = img.copy()
+    bad.flat[idx] += rng.uniform(5.0, 50.0, 60).astype(np.float32)
+    img_m, sig_m = bad.copy(), sig.copy()
+    if how == "sigma0":
+        sig_m.flat[idx] = 0.0
+    else:
+        img_m.flat[idx] = np.nan
+    od = oracle_desc(st)
+    po, ro = oracle.lm_fit(od, st.guess(), st.fixed, st.psf, img_m, sig_m)
+    assert ro["status"] == oracle.CONVERGED
+    pg, rg = gf.lm_fit(gpu_desc(gf, st), st.guess(), st.fixed, cuda(img_m), cuda(sig_m),
+                       cuda(st.psf))
+    assert rg["status"] == gf.OK, rg
+    xg, _ = oracle.evaluate(od, pg, st.psf, img_m, sig_m)
+    assert xg <= ro["chi2"] * (1 + CHI2_REL), (xg, ro["chi2"])
+    # Parameters: anywhere inside the chi^2 tolerance.  A point dp from the
+    # minimum has chi^2 higher by (dp/sigma)^2 along a principal direction, so
+    # chi^2 within CHI2_REL chi2 allows sqrt(CHI2_REL chi2) sigma (0.63 sigma
+    # here).  On this low-S/N stamp the float32 LM can stop that far out: once
+    # the damping is large, a step's chi^2 gain falls below the float32 passes'
+    # round-off, trials are rejected and the step test ends the fit.
+    sd = oracle_sigma(od, po, st.fixed, st.psf, img_m, sig_m)
+    free = _free(st)
+    span = math.sqrt(CHI2_REL * ro["chi2"])
+    dpo = np.abs(pg[free] - po[free]) / sd
+    assert dpo.max() <= span, (dpo, span)
+    # the masked fit sits near the fit of the clean image; the unmasked one not
+    pc, _ = oracle.lm_fit(od, st.guess(), st.fixed, st.psf, img, sig)
+    pu, _ = gf.lm_fit(gpu_desc(gf, st), st.guess(), st.fixed, cuda(bad), cuda(sig), cuda(st.psf))
+    dm = np.abs(pg[free] - pc[free]) / sd
+    du = np.abs(pu[free] - pc[free]) / sd
+    assert dm.max() < 1.5 and du.max() > 3.0, (dm, du)
+
+
 def test_lm_fit_noiseless_recovers_truth(gf):
     st = synth.stamp64()
     m_true, _, sig = noisy_image(st)
