@@ -201,8 +201,10 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
     // finite-difference channels difference two such constant sets, so their
     // rounding is what the 1/h of a forward difference amplifies.
     const double th = pa * (kPi / 180.0);
-    k.cs = (float)cos(th);
-    k.sn = (float)sin(th);
+    double sth, cth;
+    sincos(th, &sth, &cth);  // one range reduction for both
+    k.cs = (float)cth;
+    k.sn = (float)sth;
     k.invq = (float)(1.0 / ax);
     k.C = (float)(c + 2.0);
     k.invC = (float)(1.0 / (c + 2.0));
