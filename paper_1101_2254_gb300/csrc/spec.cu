@@ -41,12 +41,24 @@ constexpr unsigned kFull = 0xffffffffu;
 
 static_assert(4 * ((SV + 3) / 4) <= SVP && SVP % 4 == 0, "tiles stay inside a V row");
 static_assert((SV * SSPAN * sizeof(float)) % 16 == 0, "V rows start 16-byte aligned");
+static_assert((ST * SVP * sizeof(float)) % 16 == 0, "the column sums start 16-byte aligned");
+static_assert(sizeof(float) * GF_MAX_FREE * ST >= sizeof(float) * SGRP * STILE * 16, "union");
+// the blocked sums read D up to 4 * 63 + 4 ceil((L + 3) / 4) - 1 < SSPAN
+static_assert(252 + 4 * ((GF_SPEC_MAX_LSF + 6) / 4) <= SSPAN, "blocked window inside D");
+
+// the LSF zero padded for the blocked sums: tap u at index u + 7 + lsf_pad_off(L)
+constexpr int SLSFZ = ((GF_SPEC_MAX_LSF + 17 + 3) / 4) * 4;
+__host__ __device__ constexpr int lsf_pad_off(int L) { return (4 - (L + 3) % 4) % 4; }
 
 struct SpecShared {
     float D[SV][SSPAN];        // extended-grid columns of the chunk
     float V[ST][SVP];          // convolved columns, then (J, r) per channel (zero padded)
+    union {
+        float Vc[GF_MAX_FREE][ST];   // the Jacobian columns' LSF sums, by column
+        float red[SGRP][STILE][16];  // after the chunks: per group and tile, its 4 x 4 sums
+    } u;
+    float lsfz[SLSFZ];         // zero-padded LSF of the blocked sums
     float Wt[ST];              // weights 1/sigma^2 (0 on invalid channels)
-    float red[SGRP][STILE][16];  // per group and tile: its 4 x 4 sums
     float lsf[GF_SPEC_MAX_LSF];
     // float32 constants of the current parameter vector
     float ca[3];                             // continuum coefficients
@@ -118,7 +130,9 @@ __device__ void spec_consts(const SpecArgs& a, SpecShared& S, const double* q, b
 __device__ void spec_columns(const SpecArgs& a, SpecShared& S, int i0, bool cols)
 {
     const int c = (a.L - 1) / 2;
-    const int span = ST + a.L - 1;
+    // a Jacobian pass fills the whole blocked window (up to 3 points past the
+    // extended chunk, whose taps are zero)
+    const int span = cols ? 252 + 4 * ((a.L + 6) / 4) : ST + a.L - 1;
     const int mcol = cols ? a.nf : 0;
     const bool fd = a.opts.jac_mode == GF_JAC_FD;
     for (int e = threadIdx.x; e < span; e += ST) {
@@ -204,20 +218,48 @@ __device__ void spec_pass(const SpecArgs& a, SpecShared& S, const float* spec, c
             s = sig[i];
         }
         const bool valid = in && isfinite(d) && isfinite(s) && s > 0.0f;
-        for (int f = 0; f < ncol; ++f) {
+        if (cols) {
+            // The Jacobian columns by blocks: item (f, q) sums outputs 4q .. 4q+3
+            // of column f from aligned 16-byte windows of D, the taps read as
+            // two broadcast float4 of the padded LSF per window: 16 FMAs per
+            // three shared loads.  Output r takes window value s with tap
+            // u = r + L - 1 - 4b - s, at lsfz[k0 + r - s + 3].
+            const int nb = (a.L + 6) / 4;
+            const int kb = a.L + 3 + lsf_pad_off(a.L);
+            for (int it = tid; it < a.nf * (ST / 4); it += ST) {
+                const int f = it / (ST / 4), q = it % (ST / 4);
+                const float* Dq = &S.D[f][4 * q];
+                float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f, o3 = 0.0f;
+                for (int bb = 0; bb < nb; ++bb) {
+                    const float4 w = *reinterpret_cast<const float4*>(Dq + 4 * bb);
+                    const int k0 = kb - 4 * bb;
+                    const float4 ca = *reinterpret_cast<const float4*>(&S.lsfz[k0]);
+                    const float4 cb = *reinterpret_cast<const float4*>(&S.lsfz[k0 + 4]);
+                    o0 = fmaf(ca.w, w.x, o0); o0 = fmaf(ca.z, w.y, o0);
+                    o0 = fmaf(ca.y, w.z, o0); o0 = fmaf(ca.x, w.w, o0);
+                    o1 = fmaf(cb.x, w.x, o1); o1 = fmaf(ca.w, w.y, o1);
+                    o1 = fmaf(ca.z, w.z, o1); o1 = fmaf(ca.y, w.w, o1);
+                    o2 = fmaf(cb.y, w.x, o2); o2 = fmaf(cb.x, w.y, o2);
+                    o2 = fmaf(ca.w, w.z, o2); o2 = fmaf(ca.z, w.w, o2);
+                    o3 = fmaf(cb.z, w.x, o3); o3 = fmaf(cb.y, w.y, o3);
+                    o3 = fmaf(cb.x, w.z, o3); o3 = fmaf(ca.w, w.w, o3);
+                }
+                *reinterpret_cast<float4*>(&S.u.Vc[f][4 * q]) = make_float4(o0, o1, o2, o3);
+            }
+        }
+        {
+            // the model, one channel per thread in tap order (the trial pass
+            // sums it the same way, so both passes give the same model)
             float v = 0.0f;
-            const float* Df = &S.D[f][tid + a.L - 1];
-            for (int u = 0; u < a.L; ++u) v = fmaf(S.lsf[u], Df[-u], v);
-            if (f == ncol - 1)
-                m = v;
-            else
-                S.V[tid][f] = in ? v : 0.0f;
+            const float* Dm = &S.D[ncol - 1][tid + a.L - 1];
+            for (int u = 0; u < a.L; ++u) v = fmaf(S.lsf[u], Dm[-u], v);
+            m = v;
         }
         if (in && m_out) m_out[i] = m;
         if (cols) {
+            __syncthreads();  // the column sums
+            for (int f = 0; f < a.nf; ++f) S.V[tid][f] = in ? S.u.Vc[f][tid] : 0.0f;
             S.V[tid][a.nf] = valid ? d - m : 0.0f;
-            if (!in)
-                for (int f = 0; f < a.nf; ++f) S.V[tid][f] = 0.0f;
             for (int f = nv; f < SVP; ++f) S.V[tid][f] = 0.0f;
             S.Wt[tid] = valid ? 1.0f / (s * s) : 0.0f;
         } else if (valid) {
@@ -256,7 +298,7 @@ __device__ void spec_pass(const SpecArgs& a, SpecShared& S, const float* spec, c
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int y = 0; y < 4; ++y) S.red[grp][tslot][x * 4 + y] = acc[x][y].s + acc[x][y].c;
+                for (int y = 0; y < 4; ++y) S.u.red[grp][tslot][x * 4 + y] = acc[x][y].s + acc[x][y].c;
         __syncthreads();
         // entry (r_, c_), r_ <= c_ < nv, of the bordered matrix: merge the 16
         // groups in order
@@ -274,7 +316,7 @@ __device__ void spec_pass(const SpecArgs& a, SpecShared& S, const float* spec, c
             for (int II = 0; II < I; ++II) slot += nt - II;
             slot += J - I;
             CSum tot = {0.0f, 0.0f};
-            for (int gq = 0; gq < SGRP; ++gq) csum_add(tot, S.red[gq][slot][(r_ % 4) * 4 + (c_ % 4)]);
+            for (int gq = 0; gq < SGRP; ++gq) csum_add(tot, S.u.red[gq][slot][(r_ % 4) * 4 + (c_ % 4)]);
             const double v = (double)tot.s + (double)tot.c;
             if (c_ < a.nf) {
                 S.A[r_ * a.nf + c_] = v;
@@ -328,6 +370,19 @@ __device__ void spec_eval_at(const SpecArgs& a, SpecShared& S, const double* q, 
     spec_pass(a, S, spec, sig, m_out, cols);
 }
 
+// The LSF into shared memory, plain and zero padded (tap u at lsfz[u + 7 +
+// lsf_pad_off(L)]).  The caller synchronises before use.
+__device__ void spec_load_lsf(const SpecArgs& a, SpecShared& S, const float* lsf)
+{
+    const int off = 7 + lsf_pad_off(a.L);
+    for (int k = threadIdx.x; k < SLSFZ; k += ST) {
+        const int u = k - off;
+        const float v = (u >= 0 && u < a.L) ? lsf[u] : 0.0f;
+        S.lsfz[k] = v;
+        if (u >= 0 && u < a.L) S.lsf[u] = v;
+    }
+}
+
 // Spectrum b: the call's mode (model, chi^2, normal equations or the LM fit).
 // All threads of the block call it.
 __device__ void spec_one(const SpecArgs& a, SpecShared& S, int b)
@@ -336,7 +391,7 @@ __device__ void spec_one(const SpecArgs& a, SpecShared& S, int b)
     const float* spec = a.spec ? a.spec + (long long)b * a.N : nullptr;
     const float* sig = a.sig ? a.sig + (long long)b * a.N : nullptr;
     if (a.lsf_stride) {
-        for (int u = tid; u < a.L; u += ST) S.lsf[u] = a.lsf[(long long)b * a.lsf_stride + u];
+        spec_load_lsf(a, S, a.lsf + (long long)b * a.lsf_stride);
     }
     if (tid < a.np) S.p[tid] = a.p_in[(long long)b * a.np + tid];
     __syncthreads();
@@ -474,7 +529,7 @@ __global__ void __launch_bounds__(ST, 3) k_spec(const __grid_constant__ SpecArgs
         }
     }
     if (a.lsf_stride == 0)
-        for (int u = tid; u < a.L; u += ST) S.lsf[u] = a.lsf[u];
+        spec_load_lsf(a, S, a.lsf);
     __syncthreads();
     for (int b = blockIdx.x; b < a.count; b += gridDim.x) spec_one(a, S, b);
 }
