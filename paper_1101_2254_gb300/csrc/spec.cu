@@ -34,15 +34,16 @@ namespace {
 constexpr int ST = 256;                          // threads, and channels per chunk
 constexpr int SSPAN = ST + GF_SPEC_MAX_LSF - 1;  // extended points of a chunk
 constexpr int SV = GF_MAX_FREE + 1;              // columns: free slots + model/residual
-constexpr int SVP = 20;                          // V row stride: 4 x 4 tiles read as float4
+constexpr int SVP = 20;                          // rows of the column sums (tiles of 4 stay inside)
+constexpr int SVC = ST + 4;                      // their row stride (a 16-byte multiple)
 constexpr int SGRP = 16;                         // pixel groups of a chunk (16 pixels each)
 constexpr int STILE = 15;                        // 4 x 4 tiles of the upper triangle, at most
 constexpr unsigned kFull = 0xffffffffu;
 
-static_assert(4 * ((SV + 3) / 4) <= SVP && SVP % 4 == 0, "tiles stay inside a V row");
-static_assert((SV * SSPAN * sizeof(float)) % 16 == 0, "V rows start 16-byte aligned");
-static_assert((ST * SVP * sizeof(float)) % 16 == 0, "the column sums start 16-byte aligned");
-static_assert(sizeof(float) * GF_MAX_FREE * ST >= sizeof(float) * SGRP * STILE * 16, "union");
+static_assert(4 * ((SV + 3) / 4) <= SVP && SVP % 4 == 0, "tiles stay inside the column sums");
+static_assert((SV * SSPAN * sizeof(float)) % 16 == 0, "the column sums start 16-byte aligned");
+static_assert((SVC * sizeof(float)) % 16 == 0, "column-sum rows 16-byte aligned");
+static_assert(sizeof(float) * SVP * SVC >= sizeof(float) * SGRP * STILE * 16, "union");
 // the blocked sums read D up to 4 * 63 + 4 ceil((L + 3) / 4) - 1 < SSPAN
 static_assert(252 + 4 * ((GF_SPEC_MAX_LSF + 6) / 4) <= SSPAN, "blocked window inside D");
 
@@ -52,9 +53,10 @@ __host__ __device__ constexpr int lsf_pad_off(int L) { return (4 - (L + 3) % 4) 
 
 struct SpecShared {
     float D[SV][SSPAN];        // extended-grid columns of the chunk
-    float V[ST][SVP];          // convolved columns, then (J, r) per channel (zero padded)
     union {
-        float Vc[GF_MAX_FREE][ST];   // the Jacobian columns' LSF sums, by column
+        // the bordered matrix's columns (J_0 .. J_{nf-1}, r, zero rows up to
+        // a multiple of 4) by column, one entry per channel of the chunk
+        float Vc[SVP][SVC];
         float red[SGRP][STILE][16];  // after the chunks: per group and tile, its 4 x 4 sums
     } u;
     float lsfz[SLSFZ];         // zero-padded LSF of the blocked sums
@@ -257,10 +259,10 @@ __device__ void spec_pass(const SpecArgs& a, SpecShared& S, const float* spec, c
         }
         if (in && m_out) m_out[i] = m;
         if (cols) {
-            __syncthreads();  // the column sums
-            for (int f = 0; f < a.nf; ++f) S.V[tid][f] = in ? S.u.Vc[f][tid] : 0.0f;
-            S.V[tid][a.nf] = valid ? d - m : 0.0f;
-            for (int f = nv; f < SVP; ++f) S.V[tid][f] = 0.0f;
+            // the residual row and the zero rows up to a multiple of 4; channels
+            // past the spectrum keep finite column sums but weight 0
+            S.u.Vc[a.nf][tid] = valid ? d - m : 0.0f;
+            for (int f = nv; f < 4 * nt; ++f) S.u.Vc[f][tid] = 0.0f;
             S.Wt[tid] = valid ? 1.0f / (s * s) : 0.0f;
         } else if (valid) {
             const float z = (d - m) / s;
@@ -268,30 +270,44 @@ __device__ void spec_pass(const SpecArgs& a, SpecShared& S, const float* spec, c
         }
         __syncthreads();
         if (active_tile) {
+            // 4 pixels per step: the tile's 4 rows and 4 columns as float4 along
+            // the pixels, the sums taken pixel by pixel in order
             float sum[4][4];
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
                 for (int y = 0; y < 4; ++y) sum[x][y] = 0.0f;
             const int c0 = 4 * ti, r0 = 4 * tj;
-            for (int pp = 0; pp < ST / SGRP; ++pp) {
+            for (int pp = 0; pp < ST / SGRP; pp += 4) {
                 const int p = grp * (ST / SGRP) + pp;
-                const float w = S.Wt[p];
-                const float4 a4 = *reinterpret_cast<const float4*>(&S.V[p][c0]);
-                const float4 b4 = *reinterpret_cast<const float4*>(&S.V[p][r0]);
-                const float vi[4] = {w * a4.x, w * a4.y, w * a4.z, w * a4.w};
-                const float vj[4] = {b4.x, b4.y, b4.z, b4.w};
+                const float4 w4 = *reinterpret_cast<const float4*>(&S.Wt[p]);
+                float4 va[4], vb[4];
 #pragma unroll
-                for (int x = 0; x < 4; ++x)
+                for (int x = 0; x < 4; ++x) {
+                    va[x] = *reinterpret_cast<const float4*>(&S.u.Vc[c0 + x][p]);
+                    vb[x] = *reinterpret_cast<const float4*>(&S.u.Vc[r0 + x][p]);
+                }
+                const float wk[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) sum[x][y] = fmaf(vi[x], vj[y], sum[x][y]);
+                for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        const float ax = k == 0 ? va[x].x : k == 1 ? va[x].y : k == 2 ? va[x].z : va[x].w;
+                        const float vi = wk[k] * ax;
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) {
+                            const float by = k == 0 ? vb[y].x : k == 1 ? vb[y].y : k == 2 ? vb[y].z : vb[y].w;
+                            sum[x][y] = fmaf(vi, by, sum[x][y]);
+                        }
+                    }
+                }
             }
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
                 for (int y = 0; y < 4; ++y) csum_add(acc[x][y], sum[x][y]);
         }
-        __syncthreads();  // D and V are rewritten by the next chunk
+        __syncthreads();  // D and the column sums are rewritten by the next chunk
     }
     if (cols) {
         if (active_tile)
