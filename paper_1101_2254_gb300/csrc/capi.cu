@@ -412,6 +412,7 @@ struct Layout {
     int rungs;  // channels of the trial pass: 1, or the LM ladder's rungs
     int tot_model, tot_os, tot_conv, tot_red, tot_conv32;
     int max_red;  // most reduction blocks of one stamp
+    int has_moffat;  // a component is a Moffat: the model kernels' longer evaluator
 };
 
 struct Plan {
@@ -474,6 +475,8 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     L.max_red = max_red;
     L.count = count;
     L.nchan = S.nchan;
+    L.has_moffat = 0;
+    for (int k = 0; k < S.ncomp; ++k) L.has_moffat |= S.kinds[k] == GF_MOFFAT;
     L.nacc = S.nacc;
     L.nslots = S.nslots;
     L.tot_model = pm[count];
@@ -645,6 +648,7 @@ PassArgs base_args(void* ws, const Layout& L, const float* psf, const float* img
     a.P = P;
     a.phase = PH_NONE;
     a.work = prof::work_dev;
+    a.has_moffat = L.has_moffat;
     return a;
 }
 

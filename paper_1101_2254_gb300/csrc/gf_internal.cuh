@@ -122,6 +122,9 @@ struct LMState {
 
 // ------------------------------------------------------------ device helpers
 
+// MOF: the call has a Moffat component (the kernels are compiled both ways,
+// so that calls without one keep the shorter evaluator)
+template <bool MOF>
 __device__ __forceinline__ float comp_eval(const CompConst& k, float xi, float yi, float ox,
                                            float oy)
 {
@@ -140,12 +143,18 @@ __device__ __forceinline__ float comp_eval(const CompConst& k, float xi, float y
         r = exp2f(k.invC * log2f(ax + ay));
     }
     float t = r * k.invr;
-    // one logarithm for every kind: log2 t (Sersic, Gaussian) or log2(1 + t^2)
-    // (Moffat), chosen by selects so the loop body stays branch-free
-    const bool moffat = k.kind == GF_MOFFAT;
-    const float lt = log2f(moffat ? fmaf(t, t, 1.0f) : t);
-    float u = (k.invn == 1.0f) ? t : exp2f(k.invn * lt);
-    u = moffat ? lt : u;
+    float u;
+    if (MOF) {
+        // one logarithm for every kind: log2 t (Sersic, Gaussian) or
+        // log2(1 + t^2) (Moffat), chosen by selects so the loop body stays
+        // branch-free
+        const bool moffat = k.kind == GF_MOFFAT;
+        const float lt = log2f(moffat ? fmaf(t, t, 1.0f) : t);
+        u = (k.invn == 1.0f) ? t : exp2f(k.invn * lt);
+        u = moffat ? lt : u;
+    } else {
+        u = (k.invn == 1.0f) ? t : exp2f(k.invn * log2f(t));
+    }
     return k.amp * expf(fmaf(-k.b, u, k.b0));
 }
 
@@ -252,6 +261,7 @@ __device__ __forceinline__ float grad_pick(const float (&g)[8], int i)
 }
 
 // value of a channel at grid point (xi + ox, yi + oy)
+template <bool MOF>
 __device__ __forceinline__ float channel_value(const Channel& ch, float xi, float yi, float ox,
                                                float oy)
 {
@@ -263,12 +273,12 @@ __device__ __forceinline__ float channel_value(const Channel& ch, float xi, floa
     if (ch.type == CH_SUM) {
         float v = ch.sky;
         for (int k = 0; k < ch.ncomp; ++k)
-            if (ch.cc[k].kind != GF_SKY) v += comp_eval(ch.cc[k], xi, yi, ox, oy);
+            if (ch.cc[k].kind != GF_SKY) v += comp_eval<MOF>(ch.cc[k], xi, yi, ox, oy);
         return v;
     }
-    if (ch.type == CH_SHAPE) return comp_eval(ch.cc[ch.comp], xi, yi, ox, oy);
-    float a = comp_eval(ch.pert, xi, yi, ox, oy);
-    float b = comp_eval(ch.cc[ch.comp], xi, yi, ox, oy);
+    if (ch.type == CH_SHAPE) return comp_eval<MOF>(ch.cc[ch.comp], xi, yi, ox, oy);
+    float a = comp_eval<MOF>(ch.pert, xi, yi, ox, oy);
+    float b = comp_eval<MOF>(ch.cc[ch.comp], xi, yi, ox, oy);
     return (a - b) * ch.scale;
 }
 
@@ -392,6 +402,7 @@ struct PassArgs {
     int jac_pass;              // the channels are a Jacobian pass's (shapes, then FD channels
                                // of the same components); else independent models
     int jac_analytic;          // the Jacobian pass's nonlinear columns are CH_DERIV channels
+    int has_moffat;            // a component is a Moffat (the evaluator's longer form)
     float* ext;                // channel grids: ext + ext_index(st[b], nchan, k)
     float* y;                  // convolved channels: y + y_index(st[b], nchan, k)
     const float* psf;
