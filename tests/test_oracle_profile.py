@@ -315,3 +315,28 @@ def test_moffat_gradient_matches_central_differences(c):
             fd = (oracle.comp_value(oracle.MOFFAT, pp, x, y) -
                   oracle.comp_value(oracle.MOFFAT, pm, x, y)) / (2.0 * h)
             assert abs(g[s] - fd) <= 2e-7 * max(abs(fd), 1e-3 * abs(v)) + 1e-11, (s, x, y)
+
+
+def test_gaussian_and_moffat_render_conserves_closed_form_flux():
+    # The whole oracle render (pixel grid with an oversampled block, then the
+    # convolution with a normalised PSF) holds each family's total light:
+    # Gaussian 2 pi q I_0 s^2, Moffat pi q I_0 alpha^2 / (beta - 1).  The
+    # stamp is wide enough for the Gaussian's tail; the Moffat (beta = 4.5) has
+    # (r/alpha)^(2 - 2 beta) of its light beyond radius r, below 1e-7 at the
+    # stamp's edge (r ~ 80, alpha ~ 7.5).
+    from paper_1101_2254_gb300 import synth
+    psf = synth.moffat_psf(11, 2.5).astype(np.float64)
+    psf /= psf.sum()
+    q, fwhm = 0.7, 6.0
+    s = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    d = oracle.make_desc(111, 111, 11, [oracle.GAUSSIAN], os_factor=8, os_box=40)
+    img = oracle.render(d, np.array([55.2, 54.7, 2.0, fwhm, q, 35.0, 0.0]), psf)
+    # the render covers the stamp; the PSF spills 5 px of light over the edge
+    # only where the model is ~exp(-50^2/2 s^2), far below the tolerance
+    assert abs(img.sum() - 2.0 * math.pi * q * 2.0 * s * s) < 1e-6 * img.sum()
+    beta = 4.5
+    al = fwhm * oracle.moffat_alpha_per_fwhm(beta)
+    d = oracle.make_desc(161, 161, 11, [oracle.MOFFAT], os_factor=8, os_box=40)
+    img = oracle.render(d, np.array([80.3, 80.6, 3.0, fwhm, beta, q, 110.0, 0.0]), psf)
+    want = math.pi * q * 3.0 * al * al / (beta - 1.0)
+    assert abs(img.sum() - want) < 2e-5 * want, (img.sum(), want)
