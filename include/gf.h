@@ -350,10 +350,20 @@ gf_status gf_set_conv_tile_width(int psf_size, int width, int tile_w);
  * The call allocates nothing and calls no allocating routine; the caller still
  * passes the inputs (image, sigma, PSF) and outputs (model_dev may be NULL,
  * chi2_dev one double) in its own device memory.
- *   - A stamp whose scratch (about 4 bytes per extended-grid pixel plus 4 per
- *     stamp pixel) exceeds the array is rejected with GF_ENOMEM and a message,
- *     before any launch.  A 1024x1024 stamp with a 65x65 PSF fits; 2048x2048
- *     does not.
+ *   - A stamp is accepted exactly when gf_workspace_size(d, NULL,
+ *     GF_CALL_EVAL) <= GF_STATIC_SCRATCH_BYTES; otherwise the call returns
+ *     GF_ENOMEM with a message, before any launch.  The scratch depends on the
+ *     convolution method (He x We = extended grid, Ny x Nx = transform size,
+ *     each array rounded up to 256 bytes, plus a few KB of tables):
+ *       direct:  4 He We + 4 H W
+ *       FFT:     the direct terms + 8 Ny (Nx/2+1) + 4 Ny Nx + 8 He (Nx/2+1)
+ *                + 8 (Nx + Ny)
+ *       DFT_TC:  the direct terms + 8 Ny Nx + 4 Ny Nx + 2 x 8 Ny Nx
+ *                + 8 (Nx + Ny) + 256 KiB of DFT matrices
+ *     With a 65x65 PSF, GF_CONV_AUTO takes the FFT (P >= GF_AUTO_FFT_PSF):
+ *     square stamps up to 836x836 fit and 1024x1024 (24.4 MB) does not; with
+ *     GF_CONV_DIRECT named, 1024x1024 fits (8.9 MB) and 2048x2048 does not.
+ *     A 33x33 PSF (direct under GF_CONV_AUTO) fits up to 1431x1431.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current, and (like the first
  *     model-evaluating call of any kind) fills the library's static b_n table
@@ -569,6 +579,15 @@ void gf_prof_enable(unsigned long long* work_dev);
  * summed device milliseconds since the previous call (then resets).  Either
  * pointer may be NULL. */
 int gf_prof_times(double* ms_out, long long* launches_out);
+
+/* Measured FMA peak of the current device, the denominator of the ALU-bound
+ * kernels' roofline fractions: an FMA loop (8 independent chains per thread,
+ * 8 CTAs of 256 threads per SM) in float32 (fp64 = 0) or float64 (fp64 = 1),
+ * timed by CUDA events on `stream` over `reps` launches after one warm-up
+ * launch.  sink_dev: 8 bytes of device memory the kernel may write (it does
+ * not in practice).  *tflops_out = FLOPs (2 per FMA) / seconds / 1e12.
+ * Synchronises the stream.  Diagnostic only. */
+gf_status gf_fma_peak(int fp64, int reps, void* sink_dev, double* tflops_out, gf_stream stream);
 
 #ifdef __cplusplus
 }

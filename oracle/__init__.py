@@ -371,6 +371,11 @@ def num_threads() -> int:
     return lib().gfo_num_threads()
 
 
+def set_num_threads(n: int) -> None:
+    """Threads of the OpenMP loops across stamps (batched fits) from here on."""
+    lib().gfo_set_num_threads(int(n))
+
+
 # ---------------------------------------------------------------- spectral lines
 class SpecDesc(C.Structure):
     _fields_ = [("n_chan", C.c_int), ("n_lines", C.c_int), ("n_cont", C.c_int),

@@ -7,8 +7,8 @@
  * steps of the loop (Sec. 2) and names the algorithms inside steps 1-3
  * (Sec. 3: transform, FFT + transform, transform + reduce); the profile
  * formulas, the oversampling rule, the chi^2 weights and the LM variant are
- * the standard definitions the paper leaves implicit.  Every such reading is
- * listed in the repository's design doc.
+ * the standard definitions the paper leaves implicit, and each function
+ * names the one it takes.
  */
 #include "gfo.h"
 
@@ -992,5 +992,15 @@ int gfo_num_threads(void)
     return omp_get_max_threads();
 #else
     return 1;
+#endif
+}
+
+/* Threads of the OpenMP loops across stamps from here on (n >= 1). */
+void gfo_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
 #endif
 }

@@ -11,8 +11,7 @@
  * Everything is double precision, plain loops, no blocking or fusion.
  * OpenMP is used only across independent stamps (gfo_lm_fit_batch).
  *
- * Conventions (the paper names the steps only; each reading is listed in
- * the design doc of the repository):
+ * Conventions (the paper names the steps only; these are the readings taken):
  *   - pixel (row i, column j) of an H x W stamp has its centre at (x=j, y=i);
  *   - the model is evaluated on the halo-extended grid E of
  *     (H+2c) x (W+2c) pixels, c = (P-1)/2 for an odd P x P PSF; grid pixel
@@ -180,6 +179,7 @@ int gfo_lm_fit_batch(int nb, const gfo_desc* ds, double* params, const uint8_t* 
                      const gfo_lm_opts* opts, gfo_lm_result* res);
 
 int gfo_num_threads(void);
+void gfo_set_num_threads(int n);
 
 /* ---- initial-guess network and default guess (gfo_cnn.c) ---- */
 long gfo_cnn_nparams(void);

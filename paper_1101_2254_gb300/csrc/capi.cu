@@ -1074,6 +1074,36 @@ int gf_prof_times(double* ms_out, long long* launches_out)
 
 const char* gf_last_error(void) { return g_err.c_str(); }
 
+gf_status gf_fma_peak(int fp64, int reps, void* sink, double* tflops, gf_stream stream)
+{
+    if (!sink || !tflops || reps < 1 || reps > 1000 || (fp64 != 0 && fp64 != 1))
+        return fail(GF_EINVAL, "gf_fma_peak: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    GF_CUDA(cudaGetDevice(&dev));
+    GF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // about 10 ms per float32 launch at full rate; float64 runs far slower, so
+    // it takes fewer iterations
+    const int grid = sms * 8, iters = fp64 ? 64 : 4096;
+    double flops = 0.0;
+    GF_CUDA(launch_fma_peak(fp64, grid, iters, sink, s, &flops));
+    cudaEvent_t e0, e1;
+    GF_CUDA(cudaEventCreate(&e0));
+    GF_CUDA(cudaEventCreate(&e1));
+    cudaError_t err = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && err == cudaSuccess; ++r)
+        err = launch_fma_peak(fp64, grid, iters, sink, s, &flops);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    GF_CUDA(err);
+    *tflops = flops * reps / (ms * 1e-3) / 1e12;
+    return GF_OK;
+}
+
 int gf_nslots(const gf_desc* d)
 {
     if (check_structure(d) != GF_OK) return -1;

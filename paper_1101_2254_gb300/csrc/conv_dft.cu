@@ -249,9 +249,14 @@ __global__ void __launch_bounds__(NT) k_dft_tc(DftStage s, int tpc, unsigned lon
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (!__syncthreads_and(done ? 1 : 0)) {
             // give up: raise the error word, wait once more (bounded) for the
-            // MMAs in flight, mark this tile's outputs NaN, free TMEM, return
+            // MMAs in flight, mark this tile's outputs NaN and return.  The
+            // tensor memory is freed only once that second wait has seen the
+            // MMAs complete: freeing it under an MMA still in flight would let
+            // that MMA write into columns another CTA may have allocated since.
+            // If they never complete the columns stay allocated (the error
+            // word tells the host the context is no longer trustworthy).
             if (tid == 0 && s.err) atomicExch(s.err, 1);
-            mbar_wait(bar_a, parity ^ 1u);
+            const bool drained = __syncthreads_and(mbar_wait(bar_a, parity ^ 1u) ? 1 : 0);
             for (int i = tid; i < TM * R; i += NT) {
                 const long long g = g0 + i / R;
                 const int k = i % R;
@@ -271,7 +276,7 @@ __global__ void __launch_bounds__(NT) k_dft_tc(DftStage s, int tpc, unsigned lon
                 }
             }
             __syncthreads();
-            if (warp == 0)
+            if (drained && warp == 0)
                 asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
             return;
         }

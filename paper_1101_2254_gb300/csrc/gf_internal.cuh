@@ -471,6 +471,8 @@ extern std::atomic<long long> g_launch_count;
 #define GF_COUNT_LAUNCH() g_launch_count.fetch_add(1, std::memory_order_relaxed)
 
 // kernel launchers (return cudaGetLastError())
+cudaError_t launch_fma_peak(int fp64, int grid, int iters, void* sink, cudaStream_t s,
+                            double* flops);
 cudaError_t launch_model(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_conv_direct(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_conv_direct_width(const PassArgs& a, int tile_w, cudaStream_t s);

@@ -172,6 +172,7 @@ def lib():
             L.gf_spec_fit.argtypes = [ps, C.c_int, vp, C.c_char_p, dp, dp, vp, vp, vp,
                                       C.POINTER(LMOpts), vp, vp, vp]
             L.gf_prof_enable.argtypes = [vp]
+            L.gf_fma_peak.argtypes = [C.c_int, C.c_int, vp, C.POINTER(C.c_double), vp]
             L.gf_prof_times.restype = C.c_int
             L.gf_prof_times.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
             _lib = L
@@ -609,6 +610,16 @@ def set_conv_tile_width(psf_size: int, width: int, tile_w: int):
 
 
 PROF_CLASSES = ("model", "conv", "reduce", "lm")
+
+
+def fma_peak(fp64: bool = False, reps: int = 20, stream=None) -> float:
+    """Measured FMA peak of the current device in TFLOP/s (gf_fma_peak)."""
+    import torch
+    sink = torch.empty(1, dtype=torch.float64, device="cuda")
+    out = C.c_double(0.0)
+    _check(lib().gf_fma_peak(1 if fp64 else 0, reps, C.c_void_p(sink.data_ptr()),
+                             C.byref(out), _stream(stream)))
+    return float(out.value)
 
 
 def launch_count() -> int:

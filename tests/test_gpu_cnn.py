@@ -65,7 +65,7 @@ def test_forward_matches_oracle(gf):
     assert np.abs(y - yo).max() <= 3e-2 * scale
 
 
-@pytest.mark.parametrize("nb,seed", [(6, 5), (40, 6)])
+@pytest.mark.parametrize("nb,seed", [(6, 5), (40, 6), (64, 12)])
 def test_gradient_matches_oracle(gf, nb, seed):
     w, x, t = network_case(gf, nb=nb, seed=seed)
     loss, g = gf.cnn_loss_grad(torch.as_tensor(w, dtype=torch.float32).cuda(),
@@ -76,9 +76,16 @@ def test_gradient_matches_oracle(gf, nb, seed):
     lo, go = oracle.cnn_loss_grad(w, x, t)
     assert abs(float(loss.item()) - lq) <= 1e-4 * lq
     for name, a, b in BLOCKS:
-        den = np.linalg.norm(gq[a:b])
-        # same arithmetic as the bf16-activation oracle up to float32 sums
-        assert np.linalg.norm(g[a:b] - gq[a:b]) <= 1e-3 * den, name
+        # same arithmetic as the bf16-activation oracle up to float32 sums,
+        # element by element: where a different float32 summation order puts an
+        # activation on the other side of a bf16 rounding boundary, that
+        # activation moves by one bf16 step (2^-8 relative) and the gradient
+        # elements it feeds move with it.  Measured worst case 3.2e-3 of the
+        # block's RMS over four batches; bound 1e-2 of the RMS per element.
+        rms = np.sqrt(np.mean(gq[a:b] ** 2))
+        err = np.abs(g[a:b] - gq[a:b])
+        k = int(np.argmax(err))
+        assert err[k] <= 1e-2 * rms, (name, a + k, g[a + k], gq[a + k], rms)
         # exact arithmetic: rounding the activations moves gradients by several
         # per cent at a random initialisation (cancelling sums over positions)
         assert np.linalg.norm(g[a:b] - go[a:b]) <= 1.5e-1 * np.linalg.norm(go[a:b]), name
