@@ -146,6 +146,12 @@ typedef struct {
                             exactly the steps of the one-trial-at-a-time rule: the trials
                             after the first are the ones that rule would try next after
                             rejections, and only those it reaches are used. */
+    double time_budget_s; /* wall-clock budget of a stamp fit on the device, measured
+                             by the GPU's global timer from the start of the LM loop;
+                             0 = none.  When it runs out, every stamp still fitting
+                             stops with status GF_ETIMEOUT and keeps its last
+                             accepted parameters.  Used by the stamp fits
+                             (gf_lm_fit, gf_lm_fit_batch, gf_lm_fit_multistart). */
 } gf_lm_opts;
 
 typedef struct {
@@ -153,7 +159,8 @@ typedef struct {
     double lambda;
     int iters;           /* trials taken */
     int accepted;
-    int status;          /* GF_OK (converged), GF_ENOCONV, GF_EMAXITER, GF_ENONFINITE */
+    int status;          /* GF_OK (converged), GF_ENOCONV, GF_EMAXITER, GF_ENONFINITE,
+                            GF_ETIMEOUT (the options' time budget ran out) */
 } gf_lm_result;
 
 /* Stamps of a batch: one structure (gf_desc, H and W ignored), per-stamp sizes
@@ -204,6 +211,14 @@ size_t gf_workspace_size_batch(const gf_desc* d, const gf_batch* b, const uint8_
  * (sky + all components) on the extended grid, (H+2c) x (W+2c) floats. */
 gf_status gf_model(const gf_desc* d, const double* params_host, float* model_ext_dev,
                    void* ws, size_t ws_bytes, gf_stream stream);
+
+/* Step 1 for many stamps of one structure in one launch: params_host is
+ * count x nslots; model_ext_dev receives the extended grids packed stamp after
+ * stamp ((H_b+2c) x (W_b+2c) floats each, in batch order; b->pix_off and
+ * b->psf_off are not used).  Workspace: gf_workspace_size_model_batch(). */
+gf_status gf_model_batch(const gf_desc* d, const gf_batch* b, const double* params_host,
+                         float* model_ext_dev, void* ws, size_t ws_bytes, gf_stream stream);
+size_t gf_workspace_size_model_batch(const gf_desc* d, const gf_batch* b);
 
 /* Step 2 (Sec. 2 item 2; Sec. 3 item 2): convolve an extended grid with the
  * PSF; out_dev receives the H x W valid region.  Method per d->conv_method. */
@@ -272,7 +287,7 @@ gf_status gf_jacobian_analytic(const gf_desc* d, const double* params_host,
 
 /* Fill opts with the library defaults (lambda0 1e-3, x10 / x0.1, [1e-12, 1e12],
  * ftol 1e-8, xtol 1e-8, fd_rel 1e-3, max_iter 200, jac_mode GF_JAC_FD,
- * ladder 2). */
+ * ladder 2, no time budget). */
 void gf_default_opts(gf_lm_opts* opts);
 
 /* Steps 1-5: Levenberg-Marquardt fit of one stamp.  params_host (nslots) is
@@ -288,7 +303,21 @@ gf_status gf_lm_fit(const gf_desc* d, double* params_host, const uint8_t* fixed_
 
 /* Steps 1-5 for many independent stamps of one structure, all resident on the
  * device, advanced together; params_host is count x nslots (in/out),
- * result_host count entries.  Synchronises `stream` before returning. */
+ * result_host count entries.  Synchronises `stream` before returning.
+ *
+ * Residency (Sec. 3): on a capturable stream (not the legacy default stream)
+ * the whole LM loop is one CUDA-graph launch.  The loop body (work lists,
+ * Jacobian pass, damped solves, trial pass, accept/reject) sits inside a
+ * conditional WHILE node, and the body's last kernel decides on the device
+ * whether to run it again: while any stamp is still fitting, fewer than
+ * max_iter + 2 bodies have run and the time budget (opts->time_budget_s) is
+ * not spent.  The host waits once, for the final parameters.  The executable
+ * graph is kept per host thread and updated in place when the next call has
+ * the same shape.  A call on the legacy default stream (NULL), which cannot
+ * be captured, runs on a blocking stream the library keeps per host thread
+ * and device; the legacy stream's implicit synchronisation orders it with
+ * the caller's work.  Profiled calls (gf_prof_enable) launch the same body
+ * directly and the host reads the active-stamp count every few bodies. */
 gf_status gf_lm_fit_batch(const gf_desc* d, const gf_batch* b, double* params_host,
                           const uint8_t* fixed_host, const float* image_dev,
                           const float* sigma_dev, const float* psf_dev,

@@ -293,6 +293,7 @@ void default_opts(gf_lm_opts* o)
     o->max_iter = 200;
     o->jac_mode = GF_JAC_FD;
     o->ladder = 2;
+    o->time_budget_s = 0.0;
 }
 
 gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* lo,
@@ -403,7 +404,7 @@ int conv_tile_width(int P, int W)
 
 struct Layout {
     size_t S, st, pre, params, chan_jac, chan_trial, lm, psum, ext_jac, ext_trial, y_jac,
-        y_trial, part_jac, part_trial, active, exp, blob_end, total;
+        y_trial, part_jac, part_trial, active, exp, ctl, blob_end, total;
     size_t ids_static, n_static;            // the all-stamps work list (in the blob)
     size_t wl_n[2], wl_ids[2], wl_pre[2];   // LM work lists: 0 Jacobian pass, 1 trial pass
     size_t tw_x, tw_y, hhat, psfgrid, spec_jac, spec_trial;
@@ -532,6 +533,8 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         o += al(sizeof(LMState) * (size_t)count);
         L.exp = o;
         o += al(sizeof(double) * (size_t)count * (S.nslots + 5));
+        L.ctl = o;
+        o += al(sizeof(LoopCtl));
         for (int w = 0; w < 2; ++w) {
             L.wl_n[w] = o;
             o += al(sizeof(int));
@@ -1003,30 +1006,99 @@ gf_status prepare_conv(const Plan& pl)
     return GF_OK;
 }
 
-// A graph executable per host thread, updated in place when the next call
-// captures the same topology (only kernel arguments differ), else rebuilt.
-thread_local cudaGraphExec_t t_exec = nullptr;
-thread_local int t_exec_dev = -1;
+// The batched LM loop as one CUDA graph per host thread: a conditional WHILE
+// node whose body graph holds one LM body (captured from the stream), and whose
+// condition the body's last kernel (k_loop_ctl) sets on the device.  The outer
+// graph, its node and the condition handle are made once per thread and
+// device; each call empties the body, captures its own body into it and
+// updates the executable in place (cudaGraphExecUpdate), or instantiates it
+// again when the body's shape changed.
+// A blocking stream per host thread and device (created on first use, kept
+// until exit) for LM fits the caller queues on the legacy default stream.
+thread_local cudaStream_t t_loop_stream[64];
 
-gf_status instantiate_cached(cudaGraph_t graph, cudaGraphExec_t* out)
+gf_status loop_stream(cudaStream_t* out)
 {
     int dev = 0;
     GF_CUDA(cudaGetDevice(&dev));
-    if (t_exec && t_exec_dev == dev) {
-        cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(t_exec, graph, &info) == cudaSuccess) {
-            *out = t_exec;
-            return GF_OK;
+    if (dev < 0 || dev >= 64) return fail(GF_ECUDA, "device ordinal out of range");
+    if (!t_loop_stream[dev]) GF_CUDA(cudaStreamCreateWithFlags(&t_loop_stream[dev], cudaStreamDefault));
+    *out = t_loop_stream[dev];
+    return GF_OK;
+}
+
+struct LoopGraph {
+    cudaGraph_t g = nullptr;
+    cudaGraph_t body = nullptr;
+    cudaGraphNode_t cond = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphExec_t exec = nullptr;
+    int dev = -1;
+};
+thread_local LoopGraph t_loop;
+
+void loop_graph_reset(LoopGraph& G)
+{
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.g) cudaGraphDestroy(G.g);
+    G = LoopGraph();
+}
+
+// capture(h) launches one LM body on the stream (k_loop_ctl given handle h)
+template <typename F>
+gf_status loop_graph(cudaStream_t s, F&& capture, cudaGraphExec_t* out)
+{
+    int dev = 0;
+    GF_CUDA(cudaGetDevice(&dev));
+    LoopGraph& G = t_loop;
+    if (G.g && G.dev != dev) loop_graph_reset(G);
+    if (!G.g) {
+        GF_CUDA(cudaGraphCreate(&G.g, 0));
+        G.dev = dev;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&G.h, G.g, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np = {};
+        if (e == cudaSuccess) {
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = G.h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            e = cudaGraphAddNode(&G.cond, G.g, nullptr, nullptr, 0, &np);
         }
-        cudaGetLastError();
+        if (e != cudaSuccess) {
+            loop_graph_reset(G);
+            return fail(GF_ECUDA, std::string("conditional graph node: ") + cudaGetErrorString(e));
+        }
+        G.body = np.conditional.phGraph_out[0];
+    } else {
+        size_t n = 0;
+        GF_CUDA(cudaGraphGetNodes(G.body, nullptr, &n));
+        std::vector<cudaGraphNode_t> nodes(n);
+        if (n) GF_CUDA(cudaGraphGetNodes(G.body, nodes.data(), &n));
+        for (cudaGraphNode_t nd : nodes) GF_CUDA(cudaGraphDestroyNode(nd));
     }
-    if (t_exec) {
-        cudaGraphExecDestroy(t_exec);
-        t_exec = nullptr;
+    GF_CUDA(cudaStreamBeginCaptureToGraph(s, G.body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    const gf_status rb = capture(G.h);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &captured);
+    if (rb != GF_OK) return rb;
+    GF_CUDA(ce);
+    if (G.exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(G.exec, G.g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(G.exec);
+            G.exec = nullptr;
+        }
     }
-    GF_CUDA(cudaGraphInstantiate(&t_exec, graph, 0));
-    t_exec_dev = dev;
-    *out = t_exec;
+    if (!G.exec) {
+        const cudaError_t e = cudaGraphInstantiate(&G.exec, G.g, 0);
+        if (e != cudaSuccess) {
+            G.exec = nullptr;
+            return fail(GF_ECUDA, std::string("loop graph instantiation: ") + cudaGetErrorString(e));
+        }
+    }
+    *out = G.exec;
     return GF_OK;
 }
 
@@ -1176,6 +1248,48 @@ gf_status gf_model(const gf_desc* d, const double* params, float* out, void* ws,
     if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, &S)) != GF_OK) return r;
     Plan pl;
     plan_batch(d, S, 1, &d->H, &d->W, nullptr, nullptr, 0, &pl);
+    if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = ensure_bn_table(s)) != GF_OK) return r;
+    if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
+    PassArgs a = base_args(ws, pl.L, nullptr, nullptr, nullptr, d->psf_size);
+    a.chan = at<Channel>(ws, pl.L.chan_trial);
+    a.chan_stride = 1;
+    a.nchan = 1;
+    a.ext = out;
+    GF_CUDA(launch_prep_sum(a, at<double>(ws, pl.L.params), 0, s));
+    GF_CUDA(launch_model(a, s));
+    return GF_OK;
+}
+
+static gf_status model_batch_plan(const gf_desc* d, const gf_batch* b, Structure* S, Plan* pl)
+{
+    gf_status r = check_structure(d);
+    if (r != GF_OK) return r;
+    if (!b || b->count < 1 || !b->H || !b->W) return fail(GF_EINVAL, "bad batch");
+    for (int i = 0; i < b->count; ++i)
+        if ((r = check_stamp(d, b->H[i], b->W[i])) != GF_OK) return r;
+    if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, S)) != GF_OK) return r;
+    plan_batch(d, *S, b->count, b->H, b->W, nullptr, nullptr, 0, pl);
+    return GF_OK;
+}
+
+size_t gf_workspace_size_model_batch(const gf_desc* d, const gf_batch* b)
+{
+    Structure S;
+    Plan pl;
+    if (model_batch_plan(d, b, &S, &pl) != GF_OK) return 0;
+    return pl.L.total;
+}
+
+gf_status gf_model_batch(const gf_desc* d, const gf_batch* b, const double* params, float* out,
+                         void* ws, size_t ws_bytes, gf_stream stream)
+{
+    Structure S;
+    Plan pl;
+    gf_status r = model_batch_plan(d, b, &S, &pl);
+    if (r != GF_OK) return r;
+    if (!params || !out) return fail(GF_EINVAL, "params or output is NULL");
     if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
     if ((r = ensure_bn_table(s)) != GF_OK) return r;
@@ -1387,7 +1501,8 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
         if ((r = check_stamp(d, b->H[i], b->W[i])) != GF_OK) return r;
     if (!params || !img || !sig || !psf || !res) return fail(GF_EINVAL, "NULL argument");
     if (opts && !(opts->max_iter >= 1 && opts->lambda_up > 1.0 && opts->lambda_down > 0.0 &&
-                  opts->lambda_down < 1.0 && opts->lambda0 > 0.0))
+                  opts->lambda_down < 1.0 && opts->lambda0 > 0.0 &&
+                  opts->time_budget_s >= 0.0 && opts->time_budget_s < 1e6))
         return fail(GF_EINVAL, "bad LM options");
     Structure S;
     if ((r = make_structure(d, fixed, lo, hi, opts, &S)) != GF_OK) return r;
@@ -1397,6 +1512,10 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     plan_batch(d, S, b->count, b->H, b->W, b->pix_off, b->psf_off, NEED_LM, &pl);
     if ((r = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
+    // the legacy default stream cannot be captured: a call on it runs on the
+    // thread's own blocking stream, which the legacy stream's semantics order
+    // after the legacy stream's earlier work and before its later work
+    if (s == nullptr && !prof::work_dev && (r = loop_stream(&s)) != GF_OK) return r;
     if ((r = ensure_bn_table(s)) != GF_OK) return r;
     const Layout& L = pl.L;
     if ((r = upload(ws, make_blob(pl, S, params), s)) != GF_OK) return r;
@@ -1423,8 +1542,10 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     GF_CUDA(launch_psf_sum(L.count, base.st, psf, const_cast<float*>(base.psf_sum), s));
     GF_CUDA(launch_lm_init(L.count, base.S, lm, at<double>(ws, L.params), s));
     // One LM "body": the Jacobian pass (stamps that need it), the damped solve,
-    // the trial pass, accept/reject and the count of stamps still active.
-    auto body = [&]() -> gf_status {
+    // the trial pass, accept/reject, and the loop's control kernel (stamps
+    // still active, bodies run, time budget).
+    LoopCtl* ctl = at<LoopCtl>(ws, L.ctl);
+    auto body = [&](cudaGraphConditionalHandle h, int use_handle) -> gf_status {
         {
             ProfScope ps(PROF_LM, s);
             GF_CUDA(launch_worklist(L.count, lm, PH_NEED_JAC, base.pre_static,
@@ -1443,49 +1564,49 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
         if ((rr = trial_pass(at_, pl, ws, s, nullptr)) != GF_OK) return rr;
         ProfScope ps(PROF_LM, s);
         GF_CUDA(launch_final_update(at_, active, s));
+        GF_CUDA(launch_loop_ctl(L.count, lm, active, ctl, h, use_handle, s));
         return GF_OK;
     };
-    // With a capturable stream and no profiling, the body's ~20 launches are
-    // captured once into a CUDA graph and replayed; the host reads one integer
-    // (active stamps) every few bodies.
-    cudaGraphExec_t exec = nullptr;
+    const int max_bodies = S.opts.max_iter + 2;
+    const unsigned long long budget_ns =
+        S.opts.time_budget_s > 0.0 ? (unsigned long long)(S.opts.time_budget_s * 1e9) + 1ull : 0ull;
+    GF_CUDA(launch_loop_start(ctl, budget_ns, max_bodies, s));
+    // With a capturable stream and no profiling, the whole loop is one graph
+    // launch: the body inside a conditional WHILE node that k_loop_ctl drives.
+    long long per_body = 0;
     if (s != nullptr && !prof::work_dev) {
         if ((r = prepare_conv(pl)) != GF_OK) return r;
-        cudaGraph_t graph = nullptr;
-        GF_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        gf_status rb = body();
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        if (rb != GF_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return rb;
-        }
-        GF_CUDA(ce);
-        r = instantiate_cached(graph, &exec);
-        cudaGraphDestroy(graph);
+        cudaGraphExec_t exec = nullptr;
+        const long long n0 = g_launch_count.load();
+        r = loop_graph(s, [&](cudaGraphConditionalHandle h) { return body(h, 1); }, &exec);
         if (r != GF_OK) return r;
-    }
-    const int max_bodies = S.opts.max_iter + 2;
-    int bodies = 0;
-    for (;;) {
-        const int K = bodies < 8 ? 2 : 4;
-        for (int k = 0; k < K && bodies < max_bodies; ++k, ++bodies) {
-            if (exec) {
-                GF_CUDA(cudaGraphLaunch(exec, s));
-            } else if ((r = body()) != GF_OK) {
-                return r;
-            }
+        per_body = g_launch_count.load() - n0;
+        GF_CUDA(cudaGraphLaunch(exec, s));
+    } else {
+        // profiled calls need host-recorded events around each kernel class:
+        // the body is launched directly and the host reads the active count
+        // every few bodies
+        int bodies = 0;
+        for (;;) {
+            const int K = bodies < 8 ? 2 : 4;
+            for (int k = 0; k < K && bodies < max_bodies; ++k, ++bodies)
+                if ((r = body(0, 0)) != GF_OK) return r;
+            int h_active = 0;
+            GF_CUDA(cudaMemcpyAsync(&h_active, active, sizeof(int), cudaMemcpyDeviceToHost, s));
+            GF_CUDA(cudaStreamSynchronize(s));
+            if (h_active == 0 || bodies >= max_bodies) break;
         }
-        int h_active = 0;
-        GF_CUDA(cudaMemcpyAsync(&h_active, active, sizeof(int), cudaMemcpyDeviceToHost, s));
-        GF_CUDA(cudaStreamSynchronize(s));
-        if (h_active == 0 || bodies >= max_bodies) break;
     }
     double* ex = at<double>(ws, L.exp);
     GF_CUDA(launch_lm_export(L.count, base.S, lm, ex, s));
     const int stride = S.nslots + 5;
     std::vector<double> hx((size_t)L.count * stride);
+    LoopCtl hc;
     GF_CUDA(cudaMemcpyAsync(hx.data(), ex, sizeof(double) * hx.size(), cudaMemcpyDeviceToHost, s));
+    GF_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
     GF_CUDA(cudaStreamSynchronize(s));
+    // the capture counted one body's launches; the graph ran hc.bodies of them
+    if (per_body > 0 && hc.bodies > 1) g_launch_count.fetch_add(per_body * (hc.bodies - 1));
     for (int i = 0; i < L.count; ++i) {
         const double* o = hx.data() + (size_t)i * stride;
         memcpy(params + (size_t)i * S.nslots, o, sizeof(double) * S.nslots);

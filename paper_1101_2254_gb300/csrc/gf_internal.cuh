@@ -120,6 +120,16 @@ struct LMState {
     int iters, accepted, status, phase;
 };
 
+// Control word of a batched LM loop run on the device (see k_loop_ctl).
+struct LoopCtl {
+    unsigned long long t0;         // global timer at the start of the loop (ns)
+    unsigned long long budget_ns;  // 0 = no time budget
+    int bodies;                    // loop bodies run so far
+    int max_bodies;
+    int cont;                      // the last body's decision: run another body
+    int timed_out;                 // the budget ran out (stamps set to GF_ETIMEOUT)
+};
+
 // ------------------------------------------------------------ device helpers
 
 // MOF: the call has a Moffat component (the kernels are compiled both ways,
@@ -483,6 +493,11 @@ cudaError_t launch_reduce_rungs(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_final_jac(const PassArgs& a, double* A_out, double* g_out, double* chi2_out,
                              cudaStream_t s);
 cudaError_t launch_bn_table(cudaStream_t s);
+// the LM loop's control word: reset before the loop, decided after every body
+cudaError_t launch_loop_start(LoopCtl* c, unsigned long long budget_ns, int max_bodies,
+                              cudaStream_t s);
+cudaError_t launch_loop_ctl(int count, LMState* lm, int* active, LoopCtl* c,
+                            cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
 cudaError_t launch_final_chi2(const PassArgs& a, double* chi2_out, cudaStream_t s);
 cudaError_t launch_psf_sum(int count, const StampInfo* st, const float* psf, float* out,
                            cudaStream_t s);

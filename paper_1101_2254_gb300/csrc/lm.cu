@@ -829,6 +829,69 @@ __global__ void __launch_bounds__(WL_THREADS) k_worklist(int count, const LMStat
     }
 }
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// The loop's control word before the first body: start time, budget, caps.
+__global__ void k_loop_start(LoopCtl* c, unsigned long long budget_ns, int max_bodies)
+{
+    c->t0 = global_ns();
+    c->budget_ns = budget_ns;
+    c->bodies = 0;
+    c->max_bodies = max_bodies;
+    c->cont = 1;
+    c->timed_out = 0;
+}
+
+// The last kernel of an LM body: counts the body and decides whether another
+// one runs -- while k_final_update counted stamps still fitting, fewer than
+// max_bodies bodies have run and the time budget is not spent.  When the
+// budget has run out, every stamp still fitting stops with GF_ETIMEOUT (its
+// last accepted parameters and chi^2 stay) and the active count drops to 0.
+// In a CUDA graph the decision sets the WHILE node's condition; otherwise the
+// host reads the active count.  One block.
+constexpr int CTL_THREADS = 1024;
+
+__global__ void __launch_bounds__(CTL_THREADS) k_loop_ctl(int count, LMState* lm, int* active,
+                                                          LoopCtl* c,
+                                                          cudaGraphConditionalHandle h,
+                                                          int use_handle)
+{
+    pdl_entry();
+    __shared__ int decide;  // 0 stop, 1 run another body, 2 out of time
+    if (threadIdx.x == 0) {
+        const int bodies = c->bodies + 1;
+        c->bodies = bodies;
+        const int n = *active;
+        int d = (n > 0 && bodies < c->max_bodies) ? 1 : 0;
+        if (n > 0 && c->budget_ns != 0ull && global_ns() - c->t0 > c->budget_ns) d = 2;
+        decide = d;
+    }
+    __syncthreads();
+    const int d = decide;
+    if (d == 2) {
+        for (int b = threadIdx.x; b < count; b += CTL_THREADS) {
+            LMState& L = lm[b];
+            if (L.phase != PH_DONE) {
+                L.status = GF_ETIMEOUT;
+                L.phase = PH_DONE;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (d == 2) {
+            c->timed_out = 1;
+            *active = 0;
+        }
+        c->cont = d == 1;
+        if (use_handle) cudaGraphSetConditional(h, d == 1 ? 1u : 0u);
+    }
+}
+
 inline int warp_blocks(int count) { return (count + kWarpsPerBlock - 1) / kWarpsPerBlock; }
 
 }  // namespace
@@ -884,6 +947,23 @@ cudaError_t launch_worklist(int count, const LMState* lm, int phase, const int* 
                             int* n, int* ids, int* pre, cudaStream_t s)
 {
     GF_LAUNCH_PDL(k_worklist, dim3(1), dim3(WL_THREADS), 0, s, count, lm, phase, pre_static, n, ids, pre);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_start(LoopCtl* c, unsigned long long budget_ns, int max_bodies,
+                              cudaStream_t s)
+{
+    k_loop_start<<<1, 1, 0, s>>>(c, budget_ns, max_bodies);
+    GF_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_ctl(int count, LMState* lm, int* active, LoopCtl* c,
+                            cudaGraphConditionalHandle h, int use_handle, cudaStream_t s)
+{
+    GF_LAUNCH_PDL(k_loop_ctl, dim3(1), dim3(CTL_THREADS), 0, s, count, lm, active, c, h,
+                  use_handle);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }

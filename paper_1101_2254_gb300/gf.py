@@ -41,7 +41,7 @@ class LMOpts(C.Structure):
                 ("lambda_down", C.c_double), ("lambda_min", C.c_double),
                 ("lambda_max", C.c_double), ("ftol", C.c_double), ("xtol", C.c_double),
                 ("fd_rel", C.c_double), ("max_iter", C.c_int), ("jac_mode", C.c_int),
-                ("ladder", C.c_int)]
+                ("ladder", C.c_int), ("time_budget_s", C.c_double)]
 
 
 JAC_FD, JAC_ANALYTIC = 0, 1
@@ -173,6 +173,10 @@ def lib():
                                       C.POINTER(LMOpts), vp, vp, vp]
             L.gf_prof_enable.argtypes = [vp]
             L.gf_fma_peak.argtypes = [C.c_int, C.c_int, vp, C.POINTER(C.c_double), vp]
+            L.gf_workspace_size_model_batch.restype = C.c_size_t
+            L.gf_workspace_size_model_batch.argtypes = [C.POINTER(Desc), C.POINTER(Batch)]
+            L.gf_model_batch.argtypes = [C.POINTER(Desc), C.POINTER(Batch), dp, vp, vp,
+                                         C.c_size_t, vp]
             L.gf_prof_times.restype = C.c_int
             L.gf_prof_times.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
             _lib = L
@@ -284,6 +288,20 @@ def model(d: Desc, params, out=None, ws=None, stream=None):
     p = _f64(params)
     w, n = _ws(ws).get(lib().gf_workspace_size(C.byref(d), None, CALL_MODEL))
     _check(lib().gf_model(C.byref(d), _dp(p), _ptr(out), w, n, _stream(stream)))
+    return out
+
+
+def model_batch(d: Desc, batch, params, out=None, ws=None, stream=None):
+    """Step 1 for a batch: the extended grids, packed stamp after stamp (float32)."""
+    import torch
+    p = np.ascontiguousarray(np.asarray(params, np.float64))
+    c = (d.psf_size - 1) // 2
+    n = sum((batch._keep[0][i] + 2 * c) * (batch._keep[1][i] + 2 * c) for i in range(batch.count))
+    if out is None:
+        out = torch.empty(int(n), dtype=torch.float32, device="cuda")
+    w, nb = _ws(ws).get(lib().gf_workspace_size_model_batch(C.byref(d), C.byref(batch)))
+    _check(lib().gf_model_batch(C.byref(d), C.byref(batch), _dp(p), _ptr(out), w, nb,
+                                _stream(stream)))
     return out
 
 
