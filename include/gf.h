@@ -27,12 +27,27 @@
  *       GF_SKY     s0                                      (1 slot)
  *       GF_GAUSSIAN x0, y0, I_0, fwhm, q, pa_deg, c        (7 slots)
  *       GF_MOFFAT  x0, y0, I_0, fwhm, beta, q, pa_deg, c   (8 slots)
+ *       GF_KING    x0, y0, I_0, r_c, r_t, alpha, q, pa_deg, c        (9 slots)
+ *       GF_NUKER   x0, y0, I_b, r_b, alpha, beta, gamma, q, pa_deg, c (10 slots)
+ *       GF_PSF     x0, y0, F                                   (3 slots)
  *     Sersic: I_e exp(-b_n((r/r_e)^{1/n} - 1)), b_n from P(2n, b_n) = 1/2.
  *     Exponential disk: I_0 exp(-r/r_s).
  *     Gaussian: I_0 exp(-r^2 / (2 s^2)), s = fwhm / (2 sqrt(2 ln 2)).
  *     Moffat: I_0 (1 + (r/alpha)^2)^(-beta), alpha = fwhm / (2 sqrt(2^(1/beta) - 1)),
  *     beta in [0.5, 20] by default.  (The Gaussian and the Moffat are further
  *     profile families after the Sersic and the disk.)
+ *     King (modified): I_0 [(w - w_t) / (1 - w_t)]^alpha for r < r_t, 0 beyond,
+ *     w = (1 + (r/r_c)^2)^(-1/alpha), w_t = w(r_t); I(0) = I_0, alpha = 2 is
+ *     King's 1962 law; defaults r_t >= 0.1, alpha in [0.1, 10].
+ *     Nuker: I_b 2^((beta-gamma)/alpha) (r/r_b)^-gamma [1 + (r/r_b)^alpha]^((gamma-beta)/alpha),
+ *     I(r_b) = I_b, radius floored at 1e-6 r_b; defaults alpha in [0.1, 10],
+ *     beta in [0, 10], gamma in [0, 2].
+ *     Point source (GF_PSF): flux F at (x0, y0), placed on the grid by the
+ *     cubic-convolution weights of Keys (1981, a = -1/2), w(x - x0) w(y - y0),
+ *     at the pixel centres (also inside the oversampled block), so that the
+ *     convolved image is the PSF interpolated to the sub-pixel position.
+ *     King, Nuker and point sources have finite-difference Jacobian columns
+ *     only: GF_JAC_ANALYTIC with one of them is rejected (GF_EINVAL).
  *     r = (|x'|^{c+2} + |y'/q|^{c+2})^{1/(c+2)}, x' = dx cos t + dy sin t,
  *     y' = -dx sin t + dy cos t, t = pa_deg * pi/180 (counter-clockwise from +x).
  *   - Oversampling: inside an os_box x os_box block of stamp pixels (origin
@@ -91,7 +106,10 @@ typedef enum {
     GF_EXPDISK = 2,
     GF_SKY = 3,
     GF_GAUSSIAN = 4,
-    GF_MOFFAT = 5
+    GF_MOFFAT = 5,
+    GF_KING = 6,
+    GF_NUKER = 7,
+    GF_PSF = 8
 } gf_comp_kind;
 
 typedef enum {

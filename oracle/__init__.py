@@ -38,8 +38,8 @@ SRC = os.path.join(HERE, "gfo.c")
 SRC_CNN = os.path.join(HERE, "gfo_cnn.c")
 SRC_SPEC = os.path.join(HERE, "gfo_spec.c")
 
-SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT = 1, 2, 3, 4, 5
-NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8}
+SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF = 1, 2, 3, 4, 5, 6, 7, 8
+NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8, KING: 9, NUKER: 10, PSF: 3}
 CONVERGED, BADINPUT, NOCONV, MAXITER = 0, 1, 3, 8
 
 _lock = threading.Lock()
@@ -105,6 +105,8 @@ def lib():
             L.gfo_sersic_flux.argtypes = [C.c_double] * 4
             L.gfo_moffat_alpha_per_fwhm.restype = C.c_double
             L.gfo_moffat_alpha_per_fwhm.argtypes = [C.c_double]
+            L.gfo_keys_weight.restype = C.c_double
+            L.gfo_keys_weight.argtypes = [C.c_double]
             L.gfo_comp_value.restype = C.c_double
             L.gfo_comp_value.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double]
             L.gfo_model_ext.restype = C.c_int
@@ -184,7 +186,7 @@ def comp_grad(kind, p, x, y):
     p = _f64(p)
     bn_ = bn(p[4]) if kind == SERSIC else 0.0
     db = bn_deriv(p[4]) if kind == SERSIC else 0.0
-    g = np.zeros(8)
+    g = np.zeros(10)
     v = lib().gfo_comp_grad(int(kind), _dp(p), float(x), float(y), bn_, db, _dp(g))
     return v, g[:len(p)]
 
@@ -206,6 +208,10 @@ def sersic_flux(Ie, re, n, q) -> float:
 
 def moffat_alpha_per_fwhm(beta) -> float:
     return lib().gfo_moffat_alpha_per_fwhm(float(beta))
+
+
+def keys_weight(x: float) -> float:
+    return lib().gfo_keys_weight(float(x))
 
 
 def comp_value(kind, p, x, y) -> float:

@@ -33,6 +33,9 @@ int gfo_comp_nslots(int kind)
     case GFO_EXPDISK: return 7;
     case GFO_GAUSSIAN: return 7;
     case GFO_MOFFAT: return 8;
+    case GFO_KING: return 9;
+    case GFO_NUKER: return 10;
+    case GFO_PSF: return 3;
     case GFO_SKY: return 1;
     default: return -1;
     }
@@ -75,7 +78,9 @@ int gfo_slot_is_linear(const gfo_desc* d, int s)
 }
 
 /* slot semantics: 0 = position, 1 = amplitude, 2 = radius, 3 = Sersic n,
- * 4 = axis ratio, 5 = position angle, 6 = boxiness, 7 = sky, 8 = Moffat beta */
+ * 4 = axis ratio, 5 = position angle, 6 = boxiness, 7 = sky, 8 = Moffat beta,
+ * 9 = King truncation radius, 10 = King alpha, 11 = Nuker alpha,
+ * 12 = Nuker beta, 13 = Nuker gamma */
 static int slot_role(const gfo_desc* d, int s)
 {
     int k, l, b;
@@ -94,6 +99,15 @@ static int slot_role(const gfo_desc* d, int s)
         static const int r[8] = {0, 0, 1, 2, 8, 4, 5, 6};
         return r[l];
     }
+    if (kind == GFO_KING) {
+        static const int r[9] = {0, 0, 1, 2, 9, 10, 4, 5, 6};
+        return r[l];
+    }
+    if (kind == GFO_NUKER) {
+        static const int r[10] = {0, 0, 1, 2, 11, 12, 13, 4, 5, 6};
+        return r[l];
+    }
+    if (kind == GFO_PSF) return -1; /* unreachable: l <= 2 handled above */
     {
         static const int r[7] = {0, 0, 1, 2, 4, 5, 6};
         return r[l];
@@ -168,9 +182,60 @@ static double moffat_dlnalpha_dbeta(double beta)
  * Sersic: I_e exp(-b_n ((r/r_e)^{1/n} - 1)); exponential disk: I_0 exp(-r/r_s);
  * Gaussian: I_0 exp(-r^2 / (2 sigma^2)); Moffat: I_0 (1 + (r/alpha)^2)^(-beta).
  * The Sersic n and the Moffat beta share slot 4. */
+/* Cubic convolution kernel of Keys (1981), parameter a = -1/2:
+ *   w(x) = 3/2 |x|^3 - 5/2 |x|^2 + 1            for |x| <= 1,
+ *   w(x) = -1/2 |x|^3 + 5/2 |x|^2 - 4 |x| + 2    for 1 < |x| < 2,  0 beyond.
+ * The weights of the four grid points around any offset sum to 1 and
+ * reproduce linear (and quadratic) functions exactly. */
+double gfo_keys_weight(double x)
+{
+    double a = fabs(x);
+    if (a <= 1.0) return (1.5 * a - 2.5) * a * a + 1.0;
+    if (a < 2.0) return ((-0.5 * a + 2.5) * a - 4.0) * a + 2.0;
+    return 0.0;
+}
+
+/* Generalised radius of (x, y) about (x0, y0): rotation by pa (degrees,
+ * counter-clockwise from +x), axis ratio q, boxiness c (C = c + 2). */
+static double gen_radius(double x, double y, double x0, double y0, double q, double pa, double c)
+{
+    double th = pa * M_PI / 180.0;
+    double dx = x - x0, dy = y - y0;
+    double xp = dx * cos(th) + dy * sin(th);
+    double yp = -dx * sin(th) + dy * cos(th);
+    double C = c + 2.0;
+    return pow(pow(fabs(xp), C) + pow(fabs(yp / q), C), 1.0 / C);
+}
+
 double gfo_comp_value(int kind, const double* p, double x, double y, double bn)
 {
     if (kind == GFO_SKY) return p[0];
+    if (kind == GFO_PSF) {
+        /* an unresolved source of flux F at (x0, y0): its value at a grid point
+         * is F times the cubic-convolution weights of the offsets, so that the
+         * convolved image is the PSF interpolated to the sub-pixel position */
+        return p[2] * gfo_keys_weight(x - p[0]) * gfo_keys_weight(y - p[1]);
+    }
+    if (kind == GFO_KING) {
+        /* modified King profile: I_0 [(w - w_t) / (1 - w_t)]^alpha for r < r_t,
+         * 0 beyond; w = (1 + (r/r_c)^2)^(-1/alpha), w_t = w(r_t).  I(0) = I_0;
+         * alpha = 2 is King's (1962) empirical law. */
+        double rc = p[3], rt = p[4], al = p[5];
+        double r = gen_radius(x, y, p[0], p[1], p[6], p[7], p[8]);
+        if (r >= rt) return 0.0;
+        double w = pow(1.0 + (r / rc) * (r / rc), -1.0 / al);
+        double wt = pow(1.0 + (rt / rc) * (rt / rc), -1.0 / al);
+        return p[2] * pow((w - wt) / (1.0 - wt), al);
+    }
+    if (kind == GFO_NUKER) {
+        /* Nuker law (Lauer et al. 1995): inner slope gamma, outer slope beta,
+         * break sharpness alpha, I(r_b) = I_b.  The radius is floored at
+         * 1e-6 r_b, where the inner power law (gamma > 0) would diverge. */
+        double rb = p[3], al = p[4], be = p[5], ga = p[6];
+        double r = gen_radius(x, y, p[0], p[1], p[7], p[8], p[9]);
+        double t = fmax(r / rb, 1e-6);
+        return p[2] * pow(2.0, (be - ga) / al) * pow(t, -ga) * pow(1.0 + pow(t, al), (ga - be) / al);
+    }
     double x0 = p[0], y0 = p[1], amp = p[2], rs = p[3];
     double n = 1.0, q, pa, c;
     if (kind == GFO_SERSIC || kind == GFO_MOFFAT) {
@@ -330,7 +395,9 @@ static double comp_pixel_bn(const gfo_desc* d, int kind, const double* p, int i,
                             double bn)
 {
     int s = d->os_factor, B = d->os_box;
-    if (kind != GFO_SKY && s > 1 && B > 0) {
+    /* a point source is not sampled: it stands for an unresolved source whose
+     * shape is the PSF's, so it keeps its pixel-centre weights everywhere */
+    if (kind != GFO_SKY && kind != GFO_PSF && s > 1 && B > 0) {
         int bx0, by0;
         os_block(d, &bx0, &by0);
         if (i >= by0 && i < by0 + B && j >= bx0 && j < bx0 + B) {
@@ -383,6 +450,11 @@ int gfo_model_ext_grad(const gfo_desc* d, const double* params, int slot, double
     slot_owner(d, slot, &k, &l, &b);
     if (k < 0) return -1;
     int kind = d->kinds[k];
+    if (kind == GFO_KING || kind == GFO_NUKER || kind == GFO_PSF) {
+        /* no analytic gradient for these kinds: the column is undefined */
+        for (size_t t = 0; t < (size_t)He * We; ++t) out[t] = NAN;
+        return -1;
+    }
     const double* p = params + b;
     double bn = kind == GFO_SERSIC ? gfo_bn(p[4]) : 0.0;
     double dbdn = kind == GFO_SERSIC ? gfo_bn_deriv(p[4]) : 0.0;
@@ -410,7 +482,7 @@ int gfo_model_ext(const gfo_desc* d, const double* params, int comp, int unit_am
         int kind = d->kinds[k], ns = gfo_comp_nslots(kind);
         if (ns < 0) return -1;
         if (comp < 0 || comp == k) {
-            double p[8];
+            double p[GFO_COMP_MAXSLOTS];
             memcpy(p, params + off, sizeof(double) * ns);
             if (unit_amp) p[kind == GFO_SKY ? 0 : 2] = 1.0;
             double bn = kind == GFO_SERSIC ? gfo_bn(p[4]) : 0.0;
@@ -748,7 +820,9 @@ void gfo_default_opts(gfo_lm_opts* o)
 }
 
 /* Default box: I >= 0, radii >= 0.1, n in [0.2, 10], q in [0.05, 1],
- * boxiness in [-1.9, 2], Moffat beta in [0.5, 20]; positions and sky free;
+ * boxiness in [-1.9, 2], Moffat beta in [0.5, 20], King r_t >= 0.1 and alpha
+ * in [0.1, 10], Nuker alpha in [0.1, 10], beta in [0, 10], gamma in [0, 2];
+ * positions and sky free;
  * position angles are wrapped into [0, 180) instead of clamped. */
 void gfo_default_bounds(const gfo_desc* d, double* lo, double* hi)
 {
@@ -763,6 +837,11 @@ void gfo_default_bounds(const gfo_desc* d, double* lo, double* hi)
         case 4: lo[s] = 0.05; hi[s] = 1.0; break;
         case 6: lo[s] = -1.9; hi[s] = 2.0; break;
         case 8: lo[s] = 0.5; hi[s] = 20.0; break;
+        case 9: lo[s] = 0.1; break;
+        case 10: lo[s] = 0.1; hi[s] = 10.0; break;
+        case 11: lo[s] = 0.1; hi[s] = 10.0; break;
+        case 12: lo[s] = 0.0; hi[s] = 10.0; break;
+        case 13: lo[s] = 0.0; hi[s] = 2.0; break;
         default: break;
         }
     }

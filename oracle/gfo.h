@@ -25,6 +25,11 @@
  *   Sky     (kind 3): s0                                     (1 slot)
  *   Gaussian(kind 4): x0, y0, I_0, FWHM, q, pa_deg, c        (7 slots)
  *   Moffat  (kind 5): x0, y0, I_0, FWHM, beta, q, pa_deg, c  (8 slots)
+ *   King    (kind 6): x0, y0, I_0, r_c, r_t, alpha, q, pa_deg, c        (9 slots)
+ *   Nuker   (kind 7): x0, y0, I_b, r_b, alpha, beta, gamma, q, pa_deg, c (10 slots)
+ *   Point   (kind 8): x0, y0, F                                (3 slots)
+ * The King, Nuker and point-source kinds have finite-difference Jacobian
+ * columns only (no analytic gradient).
  */
 #ifndef GFO_H
 #define GFO_H
@@ -35,6 +40,10 @@
 #define GFO_SKY 3
 #define GFO_GAUSSIAN 4  /* I_0 exp(-r^2 / (2 sigma^2)), sigma = FWHM / (2 sqrt(2 ln 2)) */
 #define GFO_MOFFAT 5    /* I_0 (1 + (r/alpha)^2)^(-beta), alpha = FWHM / (2 sqrt(2^(1/beta) - 1)) */
+#define GFO_KING 6      /* I_0 [(w - w_t) / (1 - w_t)]^alpha inside r_t, w = (1 + (r/r_c)^2)^(-1/alpha) */
+#define GFO_NUKER 7     /* I_b 2^((beta-gamma)/alpha) (r/r_b)^-gamma [1 + (r/r_b)^alpha]^((gamma-beta)/alpha) */
+#define GFO_PSF 8       /* point source: F, placed by cubic-convolution weights (see gfo.c) */
+#define GFO_COMP_MAXSLOTS 10
 #define GFO_MAX_COMP 8
 #define GFO_MAX_SLOTS 64
 #define GFO_MAX_FREE 16
@@ -180,6 +189,9 @@ int gfo_lm_fit_batch(int nb, const gfo_desc* ds, double* params, const uint8_t* 
 
 int gfo_num_threads(void);
 void gfo_set_num_threads(int n);
+
+/* cubic-convolution interpolation weight (Keys 1981, a = -1/2) of offset x */
+double gfo_keys_weight(double x);
 
 /* ---- initial-guess network and default guess (gfo_cnn.c) ---- */
 long gfo_cnn_nparams(void);

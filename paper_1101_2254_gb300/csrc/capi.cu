@@ -114,6 +114,9 @@ int comp_slots(int kind)
     case GF_SKY: return 1;
     case GF_GAUSSIAN: return 7;
     case GF_MOFFAT: return 8;
+    case GF_KING: return 9;
+    case GF_NUKER: return 10;
+    case GF_PSF: return 3;
     default: return -1;
     }
 }
@@ -327,6 +330,12 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
             } else if (kind == GF_MOFFAT) {
                 static const int r[8] = {0, 0, 1, 2, R_BETA, R_Q, R_PA, R_BOXY};
                 role = r[l];
+            } else if (kind == GF_KING) {
+                static const int r[9] = {0, 0, 1, 2, R_RT, R_KALPHA, R_Q, R_PA, R_BOXY};
+                role = r[l];
+            } else if (kind == GF_NUKER) {
+                static const int r[10] = {0, 0, 1, 2, R_NALPHA, R_NBETA, R_NGAMMA, R_Q, R_PA, R_BOXY};
+                role = r[l];
             } else {
                 static const int r[7] = {0, 0, 1, 2, R_Q, R_PA, R_BOXY};
                 role = r[l];
@@ -341,6 +350,11 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
             case R_Q: l0 = 0.05; h0 = 1.0; break;
             case R_BOXY: l0 = -1.9; h0 = 2.0; break;
             case R_BETA: l0 = 0.5; h0 = 20.0; break;
+            case R_RT: l0 = 0.1; break;
+            case R_KALPHA: l0 = 0.1; h0 = 10.0; break;
+            case R_NALPHA: l0 = 0.1; h0 = 10.0; break;
+            case R_NBETA: l0 = 0.0; h0 = 10.0; break;
+            case R_NGAMMA: l0 = 0.0; h0 = 2.0; break;
             default: break;
             }
             S->lo[s] = lo ? lo[s] : l0;
@@ -369,6 +383,11 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
     if (!(S->opts.fd_rel > 0.0)) S->opts.fd_rel = 1e-3;
     if (S->opts.jac_mode != GF_JAC_FD && S->opts.jac_mode != GF_JAC_ANALYTIC)
         return fail(GF_EINVAL, "jac_mode must be GF_JAC_FD or GF_JAC_ANALYTIC");
+    if (S->opts.jac_mode == GF_JAC_ANALYTIC)
+        for (int k = 0; k < S->ncomp; ++k)
+            if (S->kinds[k] == GF_KING || S->kinds[k] == GF_NUKER || S->kinds[k] == GF_PSF)
+                return fail(GF_EINVAL, "analytic Jacobian columns are not available for King, Nuker "
+                                       "or point-source components (use GF_JAC_FD)");
     if (S->opts.ladder == 0) S->opts.ladder = 2;
     if (S->opts.ladder < 1 || S->opts.ladder > GF_MAX_LADDER)
         return fail(GF_EINVAL, "LM ladder must be 1 .. " + std::to_string(GF_MAX_LADDER));
@@ -413,7 +432,8 @@ struct Layout {
     int rungs;  // channels of the trial pass: 1, or the LM ladder's rungs
     int tot_model, tot_os, tot_conv, tot_red, tot_conv32;
     int max_red;  // most reduction blocks of one stamp
-    int has_moffat;  // a component is a Moffat: the model kernels' longer evaluator
+    int eval_variant;  // the model kernels' evaluator: 0 Sersic / disk / Gaussian,
+                       // 1 with Moffat, 2 with King, Nuker or point sources
 };
 
 struct Plan {
@@ -476,8 +496,12 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     L.max_red = max_red;
     L.count = count;
     L.nchan = S.nchan;
-    L.has_moffat = 0;
-    for (int k = 0; k < S.ncomp; ++k) L.has_moffat |= S.kinds[k] == GF_MOFFAT;
+    L.eval_variant = 0;
+    for (int k = 0; k < S.ncomp; ++k) {
+        const int kd = S.kinds[k];
+        if (kd == GF_MOFFAT) L.eval_variant = std::max(L.eval_variant, 1);
+        if (kd == GF_KING || kd == GF_NUKER || kd == GF_PSF) L.eval_variant = 2;
+    }
     L.nacc = S.nacc;
     L.nslots = S.nslots;
     L.tot_model = pm[count];
@@ -651,7 +675,7 @@ PassArgs base_args(void* ws, const Layout& L, const float* psf, const float* img
     a.P = P;
     a.phase = PH_NONE;
     a.work = prof::work_dev;
-    a.has_moffat = L.has_moffat;
+    a.eval_variant = L.eval_variant;
     return a;
 }
 

@@ -12,7 +12,10 @@
 // 8 cg .. 8 cg + 7 of rows rl and rl + 8.  For each tap row and group of 4
 // taps a thread holds, per row, a sliding window of 12 grid values (one new
 // 16-byte load per group) and the 4 taps (one broadcast 16-byte load), and
-// issues 2 x 8 x 4 = 64 FMAs: 3 shared loads per 64 FMAs.
+// issues 2 x 8 x 4 = 64 FMAs: 3 shared loads per 64 FMAs.  In the kernels
+// specialised on the padded tap count, the last group of a tap row issues only
+// the FMAs of its real taps (P - P4 + 4 of them): for P = 33 that is 33 FMAs
+// per output and tap row instead of 36.
 // The eight lanes of a quarter-warp read the same columns of eight
 // consecutive rows; with the tile's row stride SW = 4 (mod 8) floats their
 // 16-byte reads fall in distinct bank groups, so a load takes the minimum four
@@ -52,13 +55,31 @@ __device__ __forceinline__ void fma_row(float (&acc)[8], const float4 kk, const 
     }
 }
 
+// fma_row for a last tap group with t = 1, 2 or 3 real taps (uniform across
+// the warp: the branch costs no divergence)
+__device__ __forceinline__ void fma_row_tail(float (&acc)[8], const float4 kk, const float (&win)[12],
+                                             int t)
+{
+    if (t == 1) {
+#pragma unroll
+        for (int o = 0; o < 8; ++o) acc[o] = fmaf(kk.x, win[o], acc[o]);
+    } else if (t == 2) {
+#pragma unroll
+        for (int o = 0; o < 8; ++o) acc[o] = fmaf(kk.y, win[o + 1], fmaf(kk.x, win[o], acc[o]));
+    } else {
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+            acc[o] = fmaf(kk.z, win[o + 2], fmaf(kk.y, win[o + 1], fmaf(kk.x, win[o], acc[o])));
+    }
+}
+
 // One tap row v for the thread's RPT rows: er0 points at the first row's first
 // window column.  With the tap count P4K known at compile time (PSFs up to
 // 35 pixels) the loop over tap groups unrolls completely and the sliding
 // window costs no register moves; otherwise (P4K = 0) it runs over P4.
 template <int P4K>
 __device__ __forceinline__ void tap_row(float (&acc)[RPT][8], const float* kr, const float* er0,
-                                        int SW, int P4)
+                                        int SW, int P4, int tail)
 {
     float win[RPT][12];
 #pragma unroll
@@ -77,8 +98,16 @@ __device__ __forceinline__ void tap_row(float (&acc)[RPT][8], const float* kr, c
 #pragma unroll(P4K > 0 ? P4K / 4 : 1)
     for (int m = 0; m < pend; m += 4) {
         const float4 kk = *reinterpret_cast<const float4*>(kr + m);
+        if (P4K > 0 && m + 4 == pend && tail < 4) {
+            // the last group holds only `tail` real taps (the rest are the zero
+            // padding): skip the padded ones.  fmaf(0, x, acc) == acc for finite
+            // x, so the sums are unchanged.
 #pragma unroll
-        for (int i = 0; i < RPT; ++i) fma_row(acc[i], kk, win[i]);
+            for (int i = 0; i < RPT; ++i) fma_row_tail(acc[i], kk, win[i], tail);
+        } else {
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) fma_row(acc[i], kk, win[i]);
+        }
         if (m + 4 < pend) {
 #pragma unroll
             for (int i = 0; i < RPT; ++i) {
@@ -165,7 +194,7 @@ __global__ void __launch_bounds__(TX * 2) k_conv_direct(PassArgs a)
             for (int o = 0; o < 8; ++o) acc[i][o] = 0.0f;
         if (active)
             for (int v = 0; v < P; ++v)
-                tap_row<P4K>(acc, ks + v * P4, es + (r0 + v) * SW + c0, SW, P4);
+                tap_row<P4K>(acc, ks + v * P4, es + (r0 + v) * SW + c0, SW, P4, P - (P4 - 4));
 
         if (active && a.work && lane == 0) {
             const unsigned long long rows = (unsigned long long)min(16, st.H - ty0 - wr0);

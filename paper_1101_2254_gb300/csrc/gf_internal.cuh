@@ -30,7 +30,25 @@ enum { CH_SUM = 0, CH_SHAPE = 1, CH_FD = 2, CH_DERIV = 3 };
 enum { PH_NEED_JAC = 0, PH_SOLVE = 1, PH_TRIAL = 2, PH_DONE = 3, PH_NONE = 99 };
 
 // slot roles
-enum { R_POS = 0, R_AMP = 1, R_RAD = 2, R_N = 3, R_Q = 4, R_PA = 5, R_BOXY = 6, R_SKY = 7, R_BETA = 8 };
+enum { R_POS = 0, R_AMP = 1, R_RAD = 2, R_N = 3, R_Q = 4, R_PA = 5, R_BOXY = 6, R_SKY = 7, R_BETA = 8,
+       R_RT = 9, R_KALPHA = 10, R_NALPHA = 11, R_NBETA = 12, R_NGAMMA = 13 };
+
+// slots of a component of kind `kind` (-1 for an unknown kind)
+__host__ __device__ __forceinline__ int comp_nslots(int kind)
+{
+    switch (kind) {
+    case GF_SERSIC: return 8;
+    case GF_EXPDISK: return 7;
+    case GF_SKY: return 1;
+    case GF_GAUSSIAN: return 7;
+    case GF_MOFFAT: return 8;
+    case GF_KING: return 9;
+    case GF_NUKER: return 10;
+    case GF_PSF: return 3;
+    default: return -1;
+    }
+}
+#define GF_COMP_MAXSLOTS 10
 
 // Float32 constants of one component at one parameter vector.
 struct CompConst {
@@ -42,8 +60,12 @@ struct CompConst {
     float invn;                // 1 / n (1 for the disk); beta for a Moffat
     float b0, b;               // I = amp * exp(b0 - b * (r invr)^invn); Moffat:
                                // amp * exp(-b log2(1 + (r invr)^2)), b = beta ln 2
-    int kind;                  // GF_SERSIC / GF_EXPDISK / GF_SKY / GF_GAUSSIAN / GF_MOFFAT
+    int kind;                  // GF_SERSIC / GF_EXPDISK / GF_SKY / GF_GAUSSIAN / GF_MOFFAT /
+                               // GF_KING / GF_NUKER / GF_PSF
     int ellipse;               // C == 2 exactly: r by sqrt
+    float e0, e1, e2, e3;      // King: 1/alpha, w_t, 1/(1 - w_t) (invn = alpha, invr = 1/r_c);
+                               // Nuker: gamma, (beta-gamma)/alpha, (gamma-beta)/alpha
+                               // (invn = alpha, invr = 1/r_b)
 };
 
 struct Channel {
@@ -132,12 +154,61 @@ struct LoopCtl {
 
 // ------------------------------------------------------------ device helpers
 
-// MOF: the call has a Moffat component (the kernels are compiled both ways,
-// so that calls without one keep the shorter evaluator)
-template <bool MOF>
+// Cubic-convolution weight of Keys (1981), a = -1/2, at offset x
+__device__ __forceinline__ float keys_w(float x)
+{
+    const float a = fabsf(x);
+    if (a <= 1.0f) return fmaf(fmaf(1.5f, a, -2.5f), a * a, 1.0f);
+    if (a < 2.0f) return fmaf(fmaf(fmaf(-0.5f, a, 2.5f), a, -4.0f), a, 2.0f);
+    return 0.0f;
+}
+
+// The further families (King, Nuker, point source) at grid point (xi + ox, yi + oy).
+static __device__ __noinline__ float comp_eval_ext(const CompConst& k, float xi, float yi, float ox,
+                                            float oy)
+{
+    if (k.kind == GF_PSF) {
+        // a point source keeps its pixel-centre weights (it is not sampled)
+        const float dx = (xi - k.x0h) - k.x0l, dy = (yi - k.y0h) - k.y0l;
+        return k.amp * keys_w(dx) * keys_w(dy);
+    }
+    const float dx = (xi - k.x0h) + (ox - k.x0l);
+    const float dy = (yi - k.y0h) + (oy - k.y0l);
+    const float xp = fmaf(dx, k.cs, dy * k.sn);
+    const float yp = fmaf(dy, k.cs, -dx * k.sn) * k.invq;
+    float r;
+    if (k.ellipse) {
+        r = sqrtf(fmaf(xp, xp, yp * yp));
+    } else {
+        const float ax = exp2f(k.C * log2f(fabsf(xp)));
+        const float ay = exp2f(k.C * log2f(fabsf(yp)));
+        r = exp2f(k.invC * log2f(ax + ay));
+    }
+    const float t = r * k.invr;
+    if (k.kind == GF_KING) {
+        // w = (1 + t^2)^(-1/alpha); I = amp ((w - w_t) / (1 - w_t))^alpha, 0 from r_t out
+        const float w = exp2f(-k.e0 * log2f(fmaf(t, t, 1.0f)));
+        const float z = (w - k.e1) * k.e2;
+        return z > 0.0f ? k.amp * exp2f(k.invn * log2f(z)) : 0.0f;
+    }
+    // Nuker: log2(I / amp) = (beta-gamma)/alpha - gamma log2 t
+    //                        + (gamma-beta)/alpha log2(1 + t^alpha)
+    const float lt = log2f(fmaxf(t, 1e-6f));
+    const float at = k.invn * lt;
+    const float l1p = at > 30.0f ? at : log2f(1.0f + exp2f(at));  // log2(1 + 2^at)
+    return k.amp * exp2f(fmaf(k.e2, l1p, fmaf(-k.e0, lt, k.e1)));
+}
+
+// EV, the evaluator variant of the call: 0 Sersic, disk and Gaussian only;
+// 1 with a Moffat (one more log and selects per sample); 2 with King, Nuker or
+// point-source components (those take comp_eval_ext).  The kernels are
+// compiled for each, so that calls without the longer forms keep the shorter
+// evaluator.
+template <int EV>
 __device__ __forceinline__ float comp_eval(const CompConst& k, float xi, float yi, float ox,
                                            float oy)
 {
+    if (EV == 2 && k.kind >= GF_KING) return comp_eval_ext(k, xi, yi, ox, oy);
     // dx = x - x0 with x = xi + ox: the integer part against the hi word is exact
     // near the centre (Sterbenz), the sub-pixel offset absorbs the lo word.
     float dx = (xi - k.x0h) + (ox - k.x0l);
@@ -154,7 +225,7 @@ __device__ __forceinline__ float comp_eval(const CompConst& k, float xi, float y
     }
     float t = r * k.invr;
     float u;
-    if (MOF) {
+    if (EV >= 1) {
         // one logarithm for every kind: log2 t (Sersic, Gaussian) or
         // log2(1 + t^2) (Moffat), chosen by selects so the loop body stays
         // branch-free
@@ -271,7 +342,7 @@ __device__ __forceinline__ float grad_pick(const float (&g)[8], int i)
 }
 
 // value of a channel at grid point (xi + ox, yi + oy)
-template <bool MOF>
+template <int EV>
 __device__ __forceinline__ float channel_value(const Channel& ch, float xi, float yi, float ox,
                                                float oy)
 {
@@ -283,12 +354,12 @@ __device__ __forceinline__ float channel_value(const Channel& ch, float xi, floa
     if (ch.type == CH_SUM) {
         float v = ch.sky;
         for (int k = 0; k < ch.ncomp; ++k)
-            if (ch.cc[k].kind != GF_SKY) v += comp_eval<MOF>(ch.cc[k], xi, yi, ox, oy);
+            if (ch.cc[k].kind != GF_SKY) v += comp_eval<EV>(ch.cc[k], xi, yi, ox, oy);
         return v;
     }
-    if (ch.type == CH_SHAPE) return comp_eval<MOF>(ch.cc[ch.comp], xi, yi, ox, oy);
-    float a = comp_eval<MOF>(ch.pert, xi, yi, ox, oy);
-    float b = comp_eval<MOF>(ch.cc[ch.comp], xi, yi, ox, oy);
+    if (ch.type == CH_SHAPE) return comp_eval<EV>(ch.cc[ch.comp], xi, yi, ox, oy);
+    float a = comp_eval<EV>(ch.pert, xi, yi, ox, oy);
+    float b = comp_eval<EV>(ch.cc[ch.comp], xi, yi, ox, oy);
     return (a - b) * ch.scale;
 }
 
@@ -412,7 +483,7 @@ struct PassArgs {
     int jac_pass;              // the channels are a Jacobian pass's (shapes, then FD channels
                                // of the same components); else independent models
     int jac_analytic;          // the Jacobian pass's nonlinear columns are CH_DERIV channels
-    int has_moffat;            // a component is a Moffat (the evaluator's longer form)
+    int eval_variant;          // 0 Sersic/disk/Gaussian, 1 with Moffat, 2 with King/Nuker/point
     float* ext;                // channel grids: ext + ext_index(st[b], nchan, k)
     float* y;                  // convolved channels: y + y_index(st[b], nchan, k)
     const float* psf;

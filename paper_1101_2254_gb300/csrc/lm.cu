@@ -179,6 +179,7 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
     k.b0 = 0.0f;
     k.b = 1.0f;
     k.ellipse = 1;
+    k.e0 = k.e1 = k.e2 = k.e3 = 0.0f;
     if (kind == GF_SKY) return k;
     const double x0 = q[0], y0 = q[1];
     k.x0h = (float)x0;
@@ -186,17 +187,17 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
     k.y0h = (float)y0;
     k.y0l = (float)(y0 - (double)k.y0h);
     const double amp = unit_amp ? 1.0 : q[2];
-    const double r = q[3];
-    double ax, pa, c;
-    if (kind == GF_SERSIC || kind == GF_MOFFAT) {  // slot 4 is n or beta
-        ax = q[5];
-        pa = q[6];
-        c = q[7];
-    } else {
-        ax = q[4];
-        pa = q[5];
-        c = q[6];
+    if (kind == GF_PSF) {  // a point source: position and flux only
+        k.amp = (float)amp;
+        return k;
     }
+    const double r = q[3];
+    // the axis ratio, position angle and boxiness follow the kind's shape slots
+    const int g = (kind == GF_SERSIC || kind == GF_MOFFAT) ? 5
+                  : kind == GF_KING                        ? 6
+                  : kind == GF_NUKER                       ? 7
+                                                           : 4;
+    const double ax = q[g], pa = q[g + 1], c = q[g + 2];
     // The constants are formed in FP64 and rounded once to float32: the
     // finite-difference channels difference two such constant sets, so their
     // rounding is what the 1/h of a forward difference amplifies.
@@ -233,6 +234,23 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
         k.invn = (float)(1.0 / n);
         k.b0 = (float)bn;
         k.b = (float)bn;
+    }
+    if (kind == GF_KING) {
+        // slots r_c (3), r_t (4), alpha (5): w_t = (1 + (r_t/r_c)^2)^(-1/alpha)
+        const double rt = q[4], al = q[5], x = rt / r;
+        const double wt = pow(1.0 + x * x, -1.0 / al);
+        k.invn = (float)al;
+        k.e0 = (float)(1.0 / al);
+        k.e1 = (float)wt;
+        k.e2 = (float)(1.0 / (1.0 - wt));
+    }
+    if (kind == GF_NUKER) {
+        // slots r_b (3), alpha (4), beta (5), gamma (6)
+        const double al = q[4], be = q[5], ga = q[6];
+        k.invn = (float)al;
+        k.e0 = (float)ga;
+        k.e1 = (float)((be - ga) / al);
+        k.e2 = (float)((ga - be) / al);
     }
     return k;
 }
@@ -417,8 +435,8 @@ __device__ void warp_build_jac(const Structure& S, WarpScratch& W, float psum, C
         } else {
             const int role = S.role[slot];
             const double h = fd_step(role, W.p[slot], S.opts.fd_rel);
-            double q[8];
-            const int ns = (S.kinds[comp] == GF_SERSIC || S.kinds[comp] == GF_MOFFAT) ? 8 : 7;
+            double q[GF_COMP_MAXSLOTS];
+            const int ns = comp_nslots(S.kinds[comp]);
             for (int t = 0; t < ns; ++t) q[t] = W.p[S.slot0[comp] + t];
             q[slot - S.slot0[comp]] += h;
             ch.mweight = 0.0f;

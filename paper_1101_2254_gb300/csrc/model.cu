@@ -52,7 +52,7 @@ __device__ __forceinline__ void load_channels(Channel* dst, const Channel* src, 
 }
 
 // Work item = (channel, block of MODEL_THREADS grid pixels of a listed stamp).
-template <bool MOF>
+template <int EV>
 __device__ __forceinline__ void body_model(const PassArgs& a, int vb, int vg)
 {
     __shared__ __align__(16) Channel ch;
@@ -89,7 +89,7 @@ __device__ __forceinline__ void body_model(const PassArgs& a, int vb, int vg)
         }
         if (write)
             a.ext[ext_index(st, a.nchan, k) + pix] =
-                channel_value<MOF>(ch, (float)j, (float)i, 0.0f, 0.0f);
+                channel_value<EV>(ch, (float)j, (float)i, 0.0f, 0.0f);
         if (a.work) {
             const int cnt = __syncthreads_count(write);
             if (threadIdx.x == 0) atomicAdd(&a.work[PROF_MODEL], 4ull * (unsigned long long)cnt);
@@ -98,7 +98,7 @@ __device__ __forceinline__ void body_model(const PassArgs& a, int vb, int vg)
 }
 
 // Work item = (channel, OS_WARPS pixels of a listed stamp's oversampling block).
-template <bool MOF>
+template <int EV>
 __device__ __forceinline__ void body_model_os(const PassArgs& a, int vb, int vg)
 {
     __shared__ __align__(16) Channel ch;
@@ -133,7 +133,7 @@ __device__ __forceinline__ void body_model_os(const PassArgs& a, int vb, int vg)
             const int ay = t / s, bx = t - ay * s;
             const float oy = ((float)ay + 0.5f) / fs - 0.5f;
             const float ox = ((float)bx + 0.5f) / fs - 0.5f;
-            v += channel_value<MOF>(ch, (float)j, (float)i, ox, oy);
+            v += channel_value<EV>(ch, (float)j, (float)i, ox, oy);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -146,7 +146,7 @@ __device__ __forceinline__ void body_model_os(const PassArgs& a, int vb, int vg)
 }
 
 // Jacobian-pass value of channel c given the components at p (base)
-template <bool MOF>
+template <int EV>
 __device__ __forceinline__ float jac_channel(const Channel& ch, const float* base, float xi, float yi,
                                              float ox, float oy)
 {
@@ -160,21 +160,21 @@ __device__ __forceinline__ float jac_channel(const Channel& ch, const float* bas
         comp_grad(ch.cc[ch.comp], xi, yi, ox, oy, ch.dbdn, g);
         return grad_pick(g, ch.dslot) * ch.scale;
     }
-    return (comp_eval<MOF>(ch.pert, xi, yi, ox, oy) - b) * ch.scale;
+    return (comp_eval<EV>(ch.pert, xi, yi, ox, oy) - b) * ch.scale;
 }
 
-template <bool MOF>
+template <int EV>
 __device__ __forceinline__ void comp_base(const Channel& c0, float* base, float xi, float yi,
                                           float ox, float oy)
 {
 #pragma unroll
     for (int k = 0; k < GF_MAX_COMP; ++k)
-        base[k] = (k < c0.ncomp && c0.cc[k].kind != GF_SKY) ? comp_eval<MOF>(c0.cc[k], xi, yi, ox, oy)
+        base[k] = (k < c0.ncomp && c0.cc[k].kind != GF_SKY) ? comp_eval<EV>(c0.cc[k], xi, yi, ox, oy)
                                                             : 0.0f;
 }
 
 // Work item = block of MODEL_THREADS grid pixels of a listed stamp (all channels).
-template <bool MOF>
+template <int EV>
 __device__ __forceinline__ void body_model_jac(const PassArgs& a, int vb, int vg)
 {
     __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
@@ -208,11 +208,11 @@ __device__ __forceinline__ void body_model_jac(const PassArgs& a, int vb, int vg
         }
         if (write) {
             float base[GF_MAX_COMP];
-            comp_base<MOF>(chs[0], base, (float)j, (float)i, 0.0f, 0.0f);
+            comp_base<EV>(chs[0], base, (float)j, (float)i, 0.0f, 0.0f);
             float* E = a.ext + ext_index(st, nch, 0) + pix;
             const long long cs = (long long)st.He * st.We;
             for (int c = 0; c < nch; ++c)
-                E[c * cs] = jac_channel<MOF>(chs[c], base, (float)j, (float)i, 0.0f, 0.0f);
+                E[c * cs] = jac_channel<EV>(chs[c], base, (float)j, (float)i, 0.0f, 0.0f);
         }
         if (a.work) {
             const int cnt = __syncthreads_count(write);
@@ -226,7 +226,7 @@ __device__ __forceinline__ void body_model_jac(const PassArgs& a, int vb, int vg
 // channels) of an analytic Jacobian pass: each component's value and gradient
 // once per pixel (comp_grad), its shape channel and every derivative channel
 // of it written from them.
-template <bool MOF>
+template <int EV>
 __device__ __forceinline__ void body_model_jac_an(const PassArgs& a, int vb, int vg)
 {
     __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
@@ -301,7 +301,7 @@ __device__ __forceinline__ void body_model_jac_an(const PassArgs& a, int vb, int
 
 // Work item = OS_WARPS pixels of a listed stamp's oversampling block (all
 // channels); lanes take sub-samples, each lane keeps every channel's sum.
-template <bool MOF>
+template <int EV>
 __device__ __forceinline__ void body_model_os_jac(const PassArgs& a, int vb, int vg)
 {
     __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
@@ -337,10 +337,10 @@ __device__ __forceinline__ void body_model_os_jac(const PassArgs& a, int vb, int
             const float oy = ((float)ay + 0.5f) / fs - 0.5f;
             const float ox = ((float)bx + 0.5f) / fs - 0.5f;
             float base[GF_MAX_COMP];
-            comp_base<MOF>(chs[0], base, (float)j, (float)i, ox, oy);
+            comp_base<EV>(chs[0], base, (float)j, (float)i, ox, oy);
 #pragma unroll
             for (int c = 0; c < GF_MAX_CHAN; ++c)
-                if (c < nch) acc[c] += jac_channel<MOF>(chs[c], base, (float)j, (float)i, ox, oy);
+                if (c < nch) acc[c] += jac_channel<EV>(chs[c], base, (float)j, (float)i, ox, oy);
         }
         const long long pix = (long long)(i + st.c) * st.We + (j + st.c);
         const long long cs = (long long)st.He * st.We;
@@ -360,7 +360,7 @@ __device__ __forceinline__ void body_model_os_jac(const PassArgs& a, int vb, int
 // The oversampled blocks of an analytic Jacobian pass, all channels per warp:
 // per sub-sample each component's value and gradient once (comp_grad), then
 // every channel of that component takes its entry.
-template <bool MOF>
+template <int EV>
 __device__ __forceinline__ void body_model_os_jac_an(const PassArgs& a, int vb, int vg)
 {
     __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
@@ -432,37 +432,40 @@ __device__ __forceinline__ void body_model_os_jac_an(const PassArgs& a, int vb, 
 // dependent launches.  PIX: 0 one channel per item, 1 every channel of a
 // Jacobian pass per pixel, 2 the same with analytic derivative channels.  OS: 0 none, 1 a warp per (channel, block pixel),
 // 2 a warp per block pixel with every channel, 3 the same with analytic channels.
-template <int PIX, int OS, bool MOF>
+template <int PIX, int OS, int EV>
 __global__ void __launch_bounds__(MODEL_THREADS) k_model_pass(PassArgs a, int g_os)
 {
     static_assert(MODEL_THREADS == OS_WARPS * 32, "one block size for both kinds of item");
     pdl_entry();
     if (OS != 0 && (int)blockIdx.x < g_os) {
         if (OS == 1)
-            body_model_os<MOF>(a, blockIdx.x, g_os);
+            body_model_os<EV>(a, blockIdx.x, g_os);
         else if (OS == 2)
-            body_model_os_jac<MOF>(a, blockIdx.x, g_os);
+            body_model_os_jac<EV>(a, blockIdx.x, g_os);
         else
-            body_model_os_jac_an<MOF>(a, blockIdx.x, g_os);
+            body_model_os_jac_an<EV>(a, blockIdx.x, g_os);
         return;
     }
     const int vb = blockIdx.x - (OS != 0 ? g_os : 0), vg = gridDim.x - (OS != 0 ? g_os : 0);
     if (PIX == 0)
-        body_model<MOF>(a, vb, vg);
+        body_model<EV>(a, vb, vg);
     else if (PIX == 1)
-        body_model_jac<MOF>(a, vb, vg);
+        body_model_jac<EV>(a, vb, vg);
     else
-        body_model_jac_an<MOF>(a, vb, vg);
+        body_model_jac_an<EV>(a, vb, vg);
 }
 
 template <int PIX, int OS>
 cudaError_t launch_pass(const PassArgs& a, int g_pix, int g_os, cudaStream_t s)
 {
-    if (a.has_moffat)
-        GF_LAUNCH_PDL((k_model_pass<PIX, OS, true>), dim3(g_pix + g_os), dim3(MODEL_THREADS), 0, s,
+    if (a.eval_variant == 2)
+        GF_LAUNCH_PDL((k_model_pass<PIX, OS, 2>), dim3(g_pix + g_os), dim3(MODEL_THREADS), 0, s,
+                      a, g_os);
+    else if (a.eval_variant == 1)
+        GF_LAUNCH_PDL((k_model_pass<PIX, OS, 1>), dim3(g_pix + g_os), dim3(MODEL_THREADS), 0, s,
                       a, g_os);
     else
-        GF_LAUNCH_PDL((k_model_pass<PIX, OS, false>), dim3(g_pix + g_os), dim3(MODEL_THREADS), 0,
+        GF_LAUNCH_PDL((k_model_pass<PIX, OS, 0>), dim3(g_pix + g_os), dim3(MODEL_THREADS), 0,
                       s, a, g_os);
     GF_COUNT_LAUNCH();
     return cudaSuccess;

@@ -30,8 +30,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT = 1, 2, 3, 4, 5
-NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8}
+SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF = 1, 2, 3, 4, 5, 6, 7, 8
+NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8, KING: 9, NUKER: 10, PSF: 3}
 
 SIGMA_READ = 0.01
 GAIN = 1.0
@@ -88,7 +88,8 @@ def noise_sigma(m_true: np.ndarray, sigma_read: float = SIGMA_READ, gain: float 
 
 # ------------------------------------------------------------ parameters
 def slot_roles(kinds):
-    """Role name per slot: pos, amp, rad, n, beta, q, pa, c, sky."""
+    """Role name per slot: pos, amp, rad, n, beta, q, pa, c, sky; King rt,
+    kalpha; Nuker nalpha, nbeta, ngamma."""
     roles = []
     for k in kinds:
         if k == SERSIC:
@@ -97,6 +98,12 @@ def slot_roles(kinds):
             roles += ["pos", "pos", "amp", "rad", "beta", "q", "pa", "c"]
         elif k in (EXPDISK, GAUSSIAN):
             roles += ["pos", "pos", "amp", "rad", "q", "pa", "c"]
+        elif k == KING:
+            roles += ["pos", "pos", "amp", "rad", "rt", "kalpha", "q", "pa", "c"]
+        elif k == NUKER:
+            roles += ["pos", "pos", "amp", "rad", "nalpha", "nbeta", "ngamma", "q", "pa", "c"]
+        elif k == PSF:
+            roles += ["pos", "pos", "amp"]
         elif k == SKY:
             roles += ["sky"]
         else:
@@ -137,6 +144,14 @@ def perturb_guess(kinds, p_true, fixed, seed: int, frac: float = 0.2):
             p[i] = p[i] % 180.0
         elif r == "c":
             p[i] = min(max(p[i], -1.9), 2.0)
+        elif r == "rt":
+            p[i] = max(p[i], 0.1)
+        elif r in ("kalpha", "nalpha"):
+            p[i] = min(max(p[i], 0.1), 10.0)
+        elif r == "nbeta":
+            p[i] = min(max(p[i], 0.0), 10.0)
+        elif r == "ngamma":
+            p[i] = min(max(p[i], 0.0), 2.0)
     return p
 
 
@@ -264,6 +279,14 @@ def random_params(kinds, rng, H, W, n_range=(0.5, 6.0), boxy=False, beta_range=(
             p += [x0, y0, amp, r, rng.uniform(*n_range), q, pa, c]
         elif k == MOFFAT:
             p += [x0, y0, amp, r, rng.uniform(*beta_range), q, pa, c]
+        elif k == KING:
+            rc = rng.uniform(1.5, 0.1 * min(H, W) + 2.0)
+            p += [x0, y0, amp, rc, rc * rng.uniform(4.0, 10.0), rng.uniform(1.5, 3.0), q, pa, c]
+        elif k == NUKER:
+            p += [x0, y0, amp, r, rng.uniform(1.0, 3.0), rng.uniform(2.5, 4.5),
+                  rng.uniform(0.0, 0.8), q, pa, c]
+        elif k == PSF:
+            p += [x0, y0, rng.uniform(20.0, 100.0)]
         else:
             p += [x0, y0, amp, r, q, pa, c]
     return np.array(p, np.float64)

@@ -716,7 +716,73 @@ def moffat_case():
                        os_box=8, name="moffat52x47")
 
 
+def king_case():
+    # a boxy modified King profile (alpha 2.2) on a sky, truncated inside the
+    # stamp's halo; boxiness held in the fit
+    kinds = [synth.KING, synth.SKY]
+    p = np.array([24.6, 21.3, 400.0, 3.0, 22.0, 2.2, 0.7, 35.0, 0.2, 0.3])
+    fixed = np.zeros(len(p), np.uint8)
+    fixed[8] = 1
+    return synth.Stamp(46, 50, kinds, p, fixed, synth.moffat_psf(11, 2.5), os_factor=4,
+                       os_box=8, name="king46x50")
+
+
+def nuker_case():
+    # a Nuker law with a mild inner cusp (gamma 0.5), discy isophotes held
+    kinds = [synth.NUKER, synth.SKY]
+    p = np.array([22.4, 25.1, 300.0, 4.0, 2.0, 3.5, 0.5, 0.8, 110.0, -0.2, 0.3])
+    fixed = np.zeros(len(p), np.uint8)
+    fixed[9] = 1
+    return synth.Stamp(49, 44, kinds, p, fixed, synth.moffat_psf(9, 2.2), os_factor=4,
+                       os_box=8, name="nuker49x44")
+
+
+def point_case():
+    # a bright point source off the centre of a Sersic galaxy (an AGN-like
+    # nucleus), inside the oversampled block, on a sky
+    kinds = [synth.SERSIC, synth.PSF, synth.SKY]
+    p = np.array([25.2, 23.9, 20.0, 6.0, 2.0, 0.7, 60.0, 0.0, 25.6, 23.3, 3000.0, 0.3])
+    fixed = np.zeros(len(p), np.uint8)
+    fixed[7] = 1
+    return synth.Stamp(48, 51, kinds, p, fixed, synth.moffat_psf(11, 2.5), os_factor=4,
+                       os_box=8, name="point48x51")
+
+
 FAMILY_CASES = {"gaussian": gaussian_case, "moffat": moffat_case}
+# families with finite-difference columns only (no analytic gradient)
+FD_FAMILY_CASES = {"king": king_case, "nuker": nuker_case, "point": point_case}
+
+
+@pytest.mark.parametrize("family", sorted(FD_FAMILY_CASES))
+def test_fd_family_model_jacobian_fit(gf, family):
+    """King, Nuker and point sources: the model grid within the pixel bound,
+    the forward-difference columns within 2e-3 of each column's scale, and the
+    LM fit reaching the oracle's chi^2 from the same start; analytic columns
+    are rejected before any launch."""
+    case = FD_FAMILY_CASES[family]()
+    d = gpu_desc(gf, case)
+    g = gf.model(d, case.params).cpu().numpy()
+    o = oracle.model_ext(oracle_desc(case), case.params)
+    assert_pix_close(g, o, what=f"model {family}")
+    m_true, img, sig = noisy_image(case)
+    p = case.guess()
+    r = gf.jacobian(d, p, case.fixed, cuda(img), cuda(sig), cuda(case.psf))
+    ro = oracle.jacobian(oracle_desc(case), p, case.fixed, case.psf, img, sig)
+    J, Jo = r["J"].cpu().numpy(), ro["J"]
+    for f in range(J.shape[0]):
+        scale = np.abs(Jo[f]).max()
+        assert np.abs(J[f] - Jo[f]).max() <= 2e-3 * scale, (family, f)
+    assert abs(r["chi2"].item() - ro["chi2"]) <= CHI2_REL * ro["chi2"]
+    od = oracle_desc(case)
+    po, rof = oracle.lm_fit(od, p, case.fixed, case.psf, img, sig)
+    pg, rg = gf.lm_fit(d, p, case.fixed, cuda(img), cuda(sig), cuda(case.psf))
+    assert rg["status"] in (gf.OK, gf.EMAXITER), rg
+    xg, _ = oracle.evaluate(od, pg, case.psf, img, sig)
+    assert xg <= rof["chi2"] * (1 + CHI2_REL), (family, xg, rof["chi2"])
+    with pytest.raises(gf.GFError) as e:
+        gf.lm_fit(d, p, case.fixed, cuda(img), cuda(sig), cuda(case.psf),
+                  opts=gf.default_opts(jac_mode=gf.JAC_ANALYTIC))
+    assert e.value.status == gf.EINVAL
 
 
 @pytest.mark.parametrize("family", sorted(FAMILY_CASES))
