@@ -70,6 +70,31 @@ TRAFFIC = {
 }
 
 
+# DRAM bytes per output pixel of the direct convolution (k_conv_direct), from
+# the ncu capture of a 7-channel Jacobian-pass launch on 8,192 stamps of the
+# learned workload (read + write = 3.26 GB for 7 x 8192 x 4096 outputs); a
+# launch's traffic grows in proportion to its outputs (each grid value read
+# once), so the bench scales it by the outputs of its average launch.  Null
+# once the kernel source differs from the one captured.
+CONV_DIRECT_TRAFFIC = {
+    "bytes_per_output": 3.263e9 / (7 * 8192 * 4096),
+    "profile": "profiles/k_conv_direct_learned8192.md",
+    "sources": {"paper_1101_2254_gb300/csrc/conv_direct.cu": "3d49e9b32879377aba2bc64a887399496ef5e347ef6203514debad4ba8309c9c"},
+}
+
+
+def conv_direct_traffic(outputs_per_launch):
+    import hashlib
+    for path, digest in CONV_DIRECT_TRAFFIC["sources"].items():
+        try:
+            with open(os.path.join(ROOT, path), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return CONV_DIRECT_TRAFFIC["bytes_per_output"] * outputs_per_launch
+
+
 def traffic_of(workload):
     import hashlib
     t = TRAFFIC.get(workload)
@@ -655,8 +680,10 @@ def run_batch(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_ms = gd.max_over_ranks(float(np.mean(e2e_ms)), ws_)
+    torch.cuda.nvtx.range_push("gf_profiled")
     with gf.Profiler() as prof:
         fit()
+    torch.cuda.nvtx.range_pop()
     pr = prof.result
     peaks, peak_kind = measured_peaks()
     fp32_peak = gf.fma_peak(False)
@@ -999,12 +1026,18 @@ def run_learned(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_ms = gd.max_over_ranks(float(np.mean(e2e_ms)), ws_)
+    # one more step with the library's profiler on (per-class events; the LM
+    # body is launched directly instead of through the graph), inside an NVTX
+    # range "gf_profiled" that a profiler's launch list can keep to
+    torch.cuda.nvtx.range_push("gf_profiled")
     with gf.Profiler() as prof:
         fit()
+    torch.cuda.nvtx.range_pop()
     pr = prof.result
     peaks, peak_kind = measured_peaks()
     fp32_peak, fp64_peak = gf.fma_peak(False), gf.fma_peak(True)
     ach = pr["conv"]["work"] / (pr["conv"]["ms"] / 1e3) / 1e12
+    conv_out = pr["conv"]["work"] / (2.0 * learned.PSF_SIZE ** 2)  # outputs convolved
     it_l = np.array([r["iters"] for r in res])
     it_d = np.array([r["iters"] for r in rdf])
     st_l = np.array([r["status"] for r in res])
@@ -1042,7 +1075,13 @@ def run_learned(args):
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "kernel": "k_conv_direct (2 P^2 FLOP per output)",
                          "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": ach / fp32_peak, "traffic": None,
+                         "frac": ach / fp32_peak,
+                         "traffic": conv_direct_traffic(conv_out / max(pr["conv"]["launches"], 1)),
+                         "traffic_note": "bytes per launch: 13.9 B per output (ncu capture, "
+                                         "profiles/k_conv_direct_learned8192.md) x the outputs "
+                                         "of the average launch",
+                         "alg_bytes_per_launch": 4.0 * (96 * 96 / 4096 + 1) * conv_out
+                                                 / max(pr["conv"]["launches"], 1),
                          "peak_source": "measured FP32 FMA loop (gf_fma_peak) in this run",
                          "launches": pr["conv"]["launches"],
                          "avg_launch_ms": pr["conv"]["ms"] / max(pr["conv"]["launches"], 1),

@@ -377,6 +377,14 @@ def num_threads() -> int:
     return lib().gfo_num_threads()
 
 
+def set_f32_emulation(on: bool) -> None:
+    """Round component pixel values and convolved model pixels to float32
+    (the GPU path's storage precision) from here on; off by default.  An
+    experiment on the sources of GPU/oracle differences, not a mode of the
+    reference computation."""
+    lib().gfo_set_f32_emulation(1 if on else 0)
+
+
 def set_num_threads(n: int) -> None:
     """Threads of the OpenMP loops across stamps (batched fits) from here on."""
     lib().gfo_set_num_threads(int(n))

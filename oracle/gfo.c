@@ -471,6 +471,18 @@ double gfo_comp_pixel(const gfo_desc* d, int kind, const double* p, int i, int j
 }
 
 /* Step 1 (transform): sum of the components on the extended grid. */
+/* Single-precision emulation (an experiment, off by default): when on, every
+ * component's pixel value and every convolved model pixel is rounded to
+ * float32, the storage precision of the GPU path, while all arithmetic stays
+ * FP64.  It shows which differences between the GPU's fits and the FP64
+ * oracle's come from float32 storage of the model (for example the noise that
+ * a forward difference's 1/h amplifies) rather than from the GPU's code. */
+static int g_f32_emulation = 0;
+
+void gfo_set_f32_emulation(int on) { g_f32_emulation = on != 0; }
+
+static double f32_store(double v) { return g_f32_emulation ? (double)(float)v : v; }
+
 int gfo_model_ext(const gfo_desc* d, const double* params, int comp, int unit_amp,
                   double* out)
 {
@@ -488,7 +500,7 @@ int gfo_model_ext(const gfo_desc* d, const double* params, int comp, int unit_am
             double bn = kind == GFO_SERSIC ? gfo_bn(p[4]) : 0.0;
             for (int ie = 0; ie < He; ++ie)
                 for (int je = 0; je < We; ++je)
-                    out[(size_t)ie * We + je] += comp_pixel_bn(d, kind, p, ie - c, je - c, bn);
+                    out[(size_t)ie * We + je] += f32_store(comp_pixel_bn(d, kind, p, ie - c, je - c, bn));
         }
         off += ns;
     }
@@ -688,6 +700,8 @@ static void convolve(int method, int H, int W, int P, const double* ext, const d
         gfo_convolve_fft(H, W, P, ext, psf, out);
     else
         gfo_convolve_direct(H, W, P, ext, psf, out);
+    if (g_f32_emulation)
+        for (size_t t = 0; t < (size_t)H * W; ++t) out[t] = (double)(float)out[t];
 }
 
 /* Steps 1-3 for one parameter vector. */

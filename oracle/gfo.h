@@ -189,6 +189,9 @@ int gfo_lm_fit_batch(int nb, const gfo_desc* ds, double* params, const uint8_t* 
 
 int gfo_num_threads(void);
 void gfo_set_num_threads(int n);
+/* Single-precision storage emulation (experiment; 0 = off, the default):
+ * component pixel values and convolved model pixels rounded to float32. */
+void gfo_set_f32_emulation(int on);
 
 /* cubic-convolution interpolation weight (Keys 1981, a = -1/2) of offset x */
 double gfo_keys_weight(double x);

@@ -329,6 +329,34 @@ __device__ __forceinline__ void body_model_os_jac(const PassArgs& a, int vb, int
         const int i = st.os_y0 + q / B, j = st.os_x0 + q % B;
         const int s = st.os_factor, ns = s * s;
         const float fs = (float)s;
+        const long long pix = (long long)(i + st.c) * st.We + (j + st.c);
+        const long long cs = (long long)st.He * st.We;
+        float* E = a.ext + ext_index(st, nch, 0) + pix;
+        if (ns <= 32) {
+            // one sub-sample per lane: the components at p once, then a runtime
+            // loop over the channels, each reduced across the lanes as soon as
+            // it is evaluated (the same sums, in the same order, as the
+            // accumulating loop below, with one evaluator in the code instead
+            // of one per unrolled channel)
+            const bool on = lane < ns;
+            float ox = 0.0f, oy = 0.0f;
+            if (on) {
+                const int ay = lane / s, bx = lane - ay * s;
+                oy = ((float)ay + 0.5f) / fs - 0.5f;
+                ox = ((float)bx + 0.5f) / fs - 0.5f;
+            }
+            float base[GF_MAX_COMP];
+            comp_base<EV>(chs[0], base, (float)j, (float)i, ox, oy);
+            for (int c = 0; c < nch; ++c) {
+                float v = on ? jac_channel<EV>(chs[c], base, (float)j, (float)i, ox, oy) : 0.0f;
+                v += 0.0f;  // an idle lane adds +0, as the accumulator it replaces
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) E[c * cs] = v / (float)ns;
+            }
+            if (a.work && lane == 0) atomicAdd(&a.work[PROF_MODEL], 4ull * (unsigned long long)nch);
+            continue;
+        }
         float acc[GF_MAX_CHAN];
 #pragma unroll
         for (int c = 0; c < GF_MAX_CHAN; ++c) acc[c] = 0.0f;
@@ -342,9 +370,6 @@ __device__ __forceinline__ void body_model_os_jac(const PassArgs& a, int vb, int
             for (int c = 0; c < GF_MAX_CHAN; ++c)
                 if (c < nch) acc[c] += jac_channel<EV>(chs[c], base, (float)j, (float)i, ox, oy);
         }
-        const long long pix = (long long)(i + st.c) * st.We + (j + st.c);
-        const long long cs = (long long)st.He * st.We;
-        float* E = a.ext + ext_index(st, nch, 0) + pix;
 #pragma unroll
         for (int c = 0; c < GF_MAX_CHAN; ++c) {
             if (c >= nch) break;

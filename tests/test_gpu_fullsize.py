@@ -3,14 +3,15 @@ benchmark times, on sampled outputs the oracle computes one by one, and on
 properties that hold at any size.
 
 - 4096 uneven single-Sersic stamps (sides 32-256, Moffat 33x33) fitted in one
-  batched LM call: sampled stamps reach the oracle's chi^2 from the same start.
+  batched LM call: every sampled stamp reaches the chi^2 of the oracle's fit
+  from the same start under the same LM options (ftol = xtol = 1e-6).
 - 64 stamps of 1024x1024 with a 255x255 PSF evaluated in one call by the
   tensor-core DFT path: sampled pixels against the oracle's direct sum, chi^2
   against the oracle's evaluation.
 - 65536 64x64 stamps fitted from the learned start in one batched LM call: 512
   distinct oracle-rendered stamps, each repeated 128 times; every copy of a
-  stamp must give the same fit bit for bit, and sampled stamps reach the
-  oracle's chi^2 from the same start.
+  stamp must give the same fit bit for bit, and every sampled stamp reaches
+  the chi^2 of the oracle's fit from the same start under the same options.
 Every input is rendered by the oracle or drawn by the seeded generators; none
 comes from the CUDA path."""
 import numpy as np
@@ -81,10 +82,11 @@ def test_batch4096_full_size(gf):
                                 np.cumsum([0] + [sts[i].psf.size for i in sample[:-1]]),
                                 np.concatenate([imgs[i] for i in sample]),
                                 np.concatenate([sigs[i] for i in sample]),
-                                np.cumsum([0] + [imgs[i].size for i in sample[:-1]]), method=1)
+                                np.cumsum([0] + [imgs[i].size for i in sample[:-1]]), method=1,
+                                opts=oracle.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL))
     hits = [reach(descs[i], pg[i], sts[i].psf, imgs[i].reshape(sts[i].H, sts[i].W),
                   sigs[i].reshape(sts[i].H, sts[i].W), ro[k]["chi2"]) for k, i in enumerate(sample)]
-    assert sum(hits) >= 11, hits
+    assert all(hits), hits
 
 
 def test_precision64x1024_full_size(gf):
@@ -153,6 +155,7 @@ def test_learned65536_full_size(gf):
     sample = np.random.default_rng(1).choice(nd, 16, replace=False)
     _, ro = oracle.lm_fit_batch([od] * len(sample), st[sample], fixed, psfs[sample].ravel(),
                                 np.arange(len(sample)) * 33 * 33, imgs[sample].ravel(),
-                                sigs[sample].ravel(), np.arange(len(sample)) * 64 * 64, method=1)
+                                sigs[sample].ravel(), np.arange(len(sample)) * 64 * 64, method=1,
+                                opts=oracle.default_opts(ftol=BENCH_TOL, xtol=BENCH_TOL))
     hits = [reach(od, pg[i], psfs[i], imgs[i], sigs[i], ro[k]["chi2"]) for k, i in enumerate(sample)]
-    assert sum(hits) >= 15, hits
+    assert all(hits), hits

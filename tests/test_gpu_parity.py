@@ -334,12 +334,14 @@ def test_lm_fit_stamp512_reaches_oracle_fit(gf, method, tol):
 
     chi^2: the oracle's chi^2 at the GPU's parameters reaches the oracle's
     minimum within CHI2_REL.  Parameters: within PARAM_REL relative, or within
-    0.25 of the parameter's statistical error sigma where that is larger: the
-    bulge/disk split of this stamp is nearly degenerate (sigma/|p| up to 0.2),
-    and float32 model arithmetic cannot resolve chi^2 finely enough to pin
-    those directions to 1e-3 relative (a one-ulp change of the Jacobian columns
-    moves the endpoint by ~0.15 sigma along the valley).  At the benchmark's
-    ftol = 1e-6 the bound is 0.5 sigma (see below)."""
+    a fraction of the parameter's statistical error sigma where that is larger.
+    The bulge/disk split of this stamp is nearly degenerate (sigma/|p| up to
+    0.2), and how far along that flat valley a fit stops is set by the storage
+    precision of the model: the oracle itself, run with every model pixel
+    rounded to float32 (tests/golden/stamp512_f32.json, written by the oracle
+    alone), stops 0.053 sigma from its FP64 fit at ftol = 1e-8 and 0.245 sigma
+    at the benchmark's ftol = 1e-6.  The bound is 1.4 times that distance, and
+    never looser than 0.1 sigma."""
     import json
     import os
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "stamp512.json")))
@@ -359,11 +361,10 @@ def test_lm_fit_stamp512_reaches_oracle_fit(gf, method, tol):
     free = _free(st)
     po = np.array(gold["params"])
     sd = np.array(gold["sigma_free"])
-    # float32 round-off resolves the flat bulge/disk valley to ~0.25 sigma; at
-    # the benchmark's ftol = 1e-6 the fit may stop where chi^2 still falls by
-    # ftol * chi^2 ~ 0.26 per step, i.e. up to sqrt(0.26) ~ 0.5 sigma along it
-    ok, in_sigma, rel = param_bound_ok(pg, po, free, sd, sfrac=0.25 if tol is None else 0.5)
-    assert ok, (in_sigma, rel)
+    emu = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "stamp512_f32.json")))
+    d_emu = emu["fits"]["1e-08" if tol is None else f"{tol:g}"]["max_sigma_distance"]
+    ok, in_sigma, rel = param_bound_ok(pg, po, free, sd, sfrac=max(0.1, 1.4 * d_emu))
+    assert ok, (in_sigma, rel, d_emu)
 
 
 # ------------------------------------------------- tensor-core DFT contraction path
@@ -761,9 +762,18 @@ def test_fd_family_model_jacobian_fit(gf, family):
     are rejected before any launch."""
     case = FD_FAMILY_CASES[family]()
     d = gpu_desc(gf, case)
-    g = gf.model(d, case.params).cpu().numpy()
-    o = oracle.model_ext(oracle_desc(case), case.params)
-    assert_pix_close(g, o, what=f"model {family}")
+    g = gf.model(d, case.params).cpu().numpy().astype(np.float64)
+    od = oracle_desc(case)
+    o = oracle.model_ext(od, case.params)
+    # the point source's cubic-convolution weights have negative lobes, so its
+    # grid values cancel against the galaxy's near the nucleus: the relative
+    # bound applies to the magnitudes being summed (the sum over components of
+    # |component value|), where float32 rounding lives, not to their difference
+    scale = sum(np.abs(oracle.model_ext(od, case.params, comp=k)) for k in range(len(case.kinds)))
+    err = np.abs(g - o)
+    bound = 1e-5 * scale + 1e-7 * np.abs(o).max()
+    assert np.all(err <= bound), (family, np.unravel_index(np.argmax(err - bound), o.shape),
+                                  (err - bound).max())
     m_true, img, sig = noisy_image(case)
     p = case.guess()
     r = gf.jacobian(d, p, case.fixed, cuda(img), cuda(sig), cuda(case.psf))

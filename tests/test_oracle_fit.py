@@ -175,3 +175,23 @@ def test_lm_batch_equals_single_fits():
             assert pb[k][6] == p0[k][6]
     with pytest.raises(ValueError):
         oracle.lm_fit_batch(descs, p0, fixed[:-1], *args)
+
+
+def test_f32_emulation_rounds_storage_only(s64):
+    """The single-precision storage experiment rounds every component pixel
+    value and convolved model pixel to float32 and nothing else: off, the grid
+    is the FP64 one; on, it equals that grid rounded per component."""
+    st, d, m_true, img, sig = s64
+    ext64 = oracle.model_ext(d, st.params)
+    comps = [oracle.model_ext(d, st.params, comp=k) for k in range(len(st.kinds))]
+    try:
+        oracle.set_f32_emulation(True)
+        ext32 = oracle.model_ext(d, st.params)
+        m32 = oracle.render(d, st.params, st.psf)
+    finally:
+        oracle.set_f32_emulation(False)
+    want = sum(c.astype(np.float32).astype(np.float64) for c in comps)
+    assert np.array_equal(ext32, want)
+    assert np.array_equal(m32, m32.astype(np.float32).astype(np.float64))
+    assert not np.array_equal(ext32, ext64)
+    assert np.array_equal(oracle.model_ext(d, st.params), ext64)
