@@ -641,13 +641,30 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
 
     opts = gf.default_opts(ftol=args.lm_tol, xtol=args.lm_tol, jac_mode=jac_mode(gf, args))
-    # untimed setup: the direct convolution's tile width per width class
-    d_direct = gf.make_desc(1, 1, s0.P, s0.kinds, s0.os_factor, 8, conv_method=gf.CONV_DIRECT)
-    gf.autotune(d_direct, batch, psf_d, ws=ws)
-    tiles = {int(c): gf.conv_tile_width(s0.P, 32 * int(c)) for c in sorted({(w + 31) // 32 for w in Ws})}
 
     def fit(i_d=img_d, s_d=sig_d, p_d=psf_d):
         return gf.lm_fit_batch(d, batch, p0, s0.fixed, i_d, s_d, p_d, opts=opts, ws=ws)
+
+    def quick_rate(n=2):
+        fit()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fit()
+        e1.record(stream)
+        e1.synchronize()
+        return n * len(sts) / (e0.elapsed_time(e1) / 1e3)
+
+    # untimed setup: the direct convolution's launch shape tuned on these stamps
+    # (tile width per width class, tile height and persistent grid), against
+    # the untuned cost model
+    untuned = quick_rate()
+    d_direct = gf.make_desc(1, 1, s0.P, s0.kinds, s0.os_factor, 8, conv_method=gf.CONV_DIRECT)
+    gf.autotune(d_direct, batch, psf_d, ws=ws)
+    tuned = quick_rate()
+    shape = gf.conv_tile_shape(s0.P, 64)
+    tiles = {int(c): gf.conv_tile_width(s0.P, 32 * int(c)) for c in sorted({(w + 31) // 32 for w in Ws})}
 
     for _ in range(max(args.warmup, 0)):
         fit()
@@ -706,6 +723,7 @@ def run_batch(args):
                        "conv": "direct", "free_params": s0.nfree, "lm_tol": args.lm_tol,
                        "jacobian": args.jac,
                        "tile_width_by_class": tiles,
+                       "tile_height": shape[1], "conv_ctas_per_sm": shape[2],
                        "value_counts": "fits reaching the oracle chi2 (fraction from the "
                                        "seeded oracle sample in reach_oracle_chi2)",
                        "l2": "inputs (0.5 GB) larger than L2", "parallelism": f"replicas{ws_}"},
@@ -725,6 +743,11 @@ def run_batch(args):
             "kernel_ms_per_step": {k: v["ms"] for k, v in pr.items()},
             "lm": {"iters_median": float(np.median(iters)), "iters_max": int(iters.max()),
                    "converged": int((status == 0).sum())},
+            "autotune": {"untuned_fits_per_s": untuned, "tuned_fits_per_s": tuned,
+                         "gain": tuned / untuned,
+                         "untuned": "tile width 32 for odd width classes, 64 for even; "
+                                    "tile height 32; 8 CTAs per SM",
+                         "note": "two-step rates from the untimed setup"},
             "clocks": clk.summary(), "peaks": peak_kind}
     if reach is not None:
         line["reach_oracle_chi2"] = reach
@@ -971,6 +994,9 @@ def run_learned(args):
     opts = gf.default_opts(ftol=args.lm_tol, xtol=args.lm_tol, jac_mode=jac_mode(gf, args))
     ws = gf.Workspace(device=dev)
     ws_lm = gf.Workspace(device=dev)
+    # untimed setup: the direct convolution's launch shape tuned on these stamps
+    gf.autotune(d, b, psf, ws=ws_lm)
+    shape = gf.conv_tile_shape(learned.PSF_SIZE, 64)
 
     def fit(learned_start=True, i_d=img, s_d=sig, p_d=psf):
         if learned_start:
@@ -1061,6 +1087,8 @@ def run_learned(args):
                        "psf": learned.PSF_SIZE, "free_params": 8, "lm_tol": args.lm_tol,
                        "jacobian": args.jac,
                        "start": "CNN (bf16) with default-guess fallback by chi2",
+                       "conv_tile": {"width": shape[0], "height": shape[1],
+                                     "ctas_per_sm": shape[2], "tuned": True},
                        "value_counts": "fits reaching the oracle chi2 (fraction from the "
                                        "seeded oracle sample in reach_oracle_chi2)",
                        "l2": "inputs (2.4 GB) larger than L2", "parallelism": f"replicas{ws_}"},

@@ -365,23 +365,34 @@ gf_status gf_lm_fit_multistart(const gf_desc* d, const gf_batch* b, int starts,
 
 /* ------------------------------------------------------------ tile tuning
  * No counterpart in the paper.  The direct convolution covers each stamp with
- * 32 x 64 or 32 x 32 output tiles.  The two differ only for stamp widths W with
- * ceil(W / 32) odd: there the narrow tile saves a 32-column strip per tile row
- * but stages more halo per output.  The choice is kept per device, per PSF side
- * P and per class ceil(W / 32); untuned classes use the narrow tile.  Results
- * do not depend on it (every output is summed in the same order).
+ * TY x TX output tiles on a persistent grid.  The shape is kept per device:
+ *   - the tile width TX (64 or 32) per PSF side P and class ceil(W / 32).  The
+ *     widths differ only for classes with ceil(W / 32) odd: there the narrow
+ *     tile saves a 32-column strip per tile row but stages more halo per
+ *     output.  Untuned odd classes use the narrow tile, even ones the wide;
+ *   - the tile height TY (32 or 16) and the persistent grid (CTAs per SM) per
+ *     P, for every stamp of a call; untuned: 32 and 8.
+ * Results do not depend on the shape (every output sums its taps in the same
+ * order).
  *
- * gf_autotune times both widths on the stamps of each such class in the batch
- * (the Jacobian pass's channels, the caller's PSFs) and keeps the faster.  It
- * synchronises the stream, must not run under stream capture, and needs a
- * workspace of gf_workspace_size_batch() bytes.  It does nothing for Fourier-
- * space convolution. */
+ * gf_autotune times the candidates on the call's stamps over the Jacobian
+ * pass's channels and the caller's PSFs, and keeps the fastest: the two widths
+ * per odd class, then the six (TY, CTAs per SM) pairs in {32, 16} x {4, 8, 16}
+ * on the whole batch, then the widths again under the chosen pair (12 shapes
+ * per odd class, 6 per even one).  It synchronises the stream, must not run
+ * under stream capture, and needs a workspace of gf_workspace_size_batch()
+ * bytes.  It does nothing for Fourier-space convolution. */
 gf_status gf_autotune(const gf_desc* d, const gf_batch* b, const float* psf_dev, void* ws,
                       size_t ws_bytes, gf_stream stream);
 /* The tile width (64 or 32) the current device uses for PSF side P and width W. */
 int gf_conv_tile_width(int psf_size, int width);
 /* Set it for the class of W (a class with ceil(W / 32) even accepts only 64). */
 gf_status gf_set_conv_tile_width(int psf_size, int width, int tile_w);
+/* The whole shape the current device uses for PSF side P and width W (any
+ * pointer may be NULL). */
+gf_status gf_conv_tile_shape(int psf_size, int width, int* tile_w, int* tile_h, int* ctas_per_sm);
+/* Set the tile height (16 or 32) and CTAs per SM (1 .. 32) for PSF side P. */
+gf_status gf_set_conv_tile_shape(int psf_size, int tile_h, int ctas_per_sm);
 
 /* ------------------------------------------------- allocation-free evaluation
  * No counterpart in the paper: an interface for callers that cannot allocate

@@ -407,6 +407,23 @@ enum { NEED_JAC = 1, NEED_TRIAL = 2, NEED_LM = 4, NEED_CHI2 = 8 };
 // smaller padded width wins.
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, int> g_tune[64];  // (P, ceil(W / 32)) -> tile width
+// per PSF side: direct-convolution tile height and persistent CTAs per SM
+struct ConvShape {
+    int ty, ctas_per_sm;
+};
+std::map<int, ConvShape> g_tune_shape[64];
+constexpr ConvShape kConvShapeDefault = {CONV_TY, 8};
+
+ConvShape conv_shape(int P)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        const auto it = g_tune_shape[dev].find(P);
+        if (it != g_tune_shape[dev].end()) return it->second;
+    }
+    return kConvShapeDefault;
+}
 
 int conv_tile_width(int P, int W)
 {
@@ -432,6 +449,7 @@ struct Layout {
     int rungs;  // channels of the trial pass: 1, or the LM ladder's rungs
     int tot_model, tot_os, tot_conv, tot_red, tot_conv32;
     int max_red;  // most reduction blocks of one stamp
+    int conv_ty, conv_cap;  // direct convolution: tile height, persistent CTAs per SM
     int eval_variant;  // the model kernels' evaluator: 0 Sersic / disk / Gaussian,
                        // 1 with Moffat, 2 with King, Nuker or point sources
 };
@@ -459,6 +477,7 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     int* pc32 = pl->pre.data() + WK_CONV32 * (count + 1);
     int max_red = 0;
     long long e1 = 0, y1 = 0;
+    const ConvShape shape = conv_shape(P);
     for (int b = 0; b < count; ++b) {
         StampInfo& s = pl->st[b];
         memset(&s, 0, sizeof(s));
@@ -485,7 +504,7 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         const int nb2 = s.os_factor > 1 ? s.os_box * s.os_box : 0;
         po[b + 1] = po[b] + (nb2 + OS_WARPS - 1) / OS_WARPS;
         s.conv_tw = conv_tile_width(P, s.W);
-        const int conv_tiles = ((s.H + CONV_TY - 1) / CONV_TY) * ((s.W + s.conv_tw - 1) / s.conv_tw);
+        const int conv_tiles = ((s.H + shape.ty - 1) / shape.ty) * ((s.W + s.conv_tw - 1) / s.conv_tw);
         pc[b + 1] = pc[b] + (s.conv_tw == 64 ? conv_tiles : 0);
         pc32[b + 1] = pc32[b] + (s.conv_tw == 32 ? conv_tiles : 0);
         pr[b + 1] = pr[b] + (int)(((long long)s.H * s.W + RED_PIX - 1) / RED_PIX);
@@ -494,6 +513,8 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     Layout& L = pl->L;
     memset(&L, 0, sizeof(L));
     L.max_red = max_red;
+    L.conv_ty = shape.ty;
+    L.conv_cap = shape.ctas_per_sm;
     L.count = count;
     L.nchan = S.nchan;
     L.eval_variant = 0;
@@ -646,7 +667,8 @@ void set_grids(PassArgs& a, const Layout& L, int nchan)
     const long long items[WK_KINDS] = {(long long)L.tot_model * nchan, (long long)L.tot_os * nchan,
                                        (long long)L.tot_conv * nchan, (long long)L.tot_red,
                                        (long long)L.tot_conv32 * nchan};
-    const long long cap[WK_KINDS] = {152LL * 16, 152LL * 8, 152LL * 8, 152LL * 6, 152LL * 16};
+    const long long cc = 152LL * L.conv_cap;  // the direct convolution's persistent grid
+    const long long cap[WK_KINDS] = {152LL * 16, 152LL * 8, cc, 152LL * 6, cc};
     for (int k = 0; k < WK_KINDS; ++k) {
         a.maxitems[k] = (int)std::min<long long>(items[k], INT32_MAX);
         a.grid[k] = (int)std::min(items[k], cap[k]);
@@ -676,6 +698,7 @@ PassArgs base_args(void* ws, const Layout& L, const float* psf, const float* img
     a.phase = PH_NONE;
     a.work = prof::work_dev;
     a.eval_variant = L.eval_variant;
+    a.conv_ty = L.conv_ty;
     return a;
 }
 
@@ -1643,9 +1666,17 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     return GF_OK;
 }
 
-// Time the two direct-convolution tile widths on the stamps of each width
-// class with ceil(W / 32) odd (the classes where they differ), over the
-// Jacobian pass's channels, and keep the faster per (P, class) on this device.
+// The direct convolution's launch shape, tuned on the device per PSF side P:
+//   tile width TX (64 or 32) per width class ceil(W / 32), for the odd
+//   classes (the only ones where the widths differ);
+//   tile height TY (32 or 16) and the persistent grid (4, 8 or 16 CTAs per
+//   SM), for all stamps of side P.
+// Candidates are timed on the call's own stamps over the Jacobian pass's
+// channels (best of three launches after a warm-up), coordinate-wise: widths
+// per class, then the 6 (TY, grid) pairs on the whole batch, then the widths
+// again under the chosen pair.  So each class sees 2 x 2 x 3 = 12 shapes (6
+// for even classes).  Results do not depend on the shape: every output sums
+// its taps in the same order.
 gf_status gf_autotune(const gf_desc* d, const gf_batch* b, const float* psf, void* ws,
                       size_t ws_bytes, gf_stream stream)
 {
@@ -1665,66 +1696,121 @@ gf_status gf_autotune(const gf_desc* d, const gf_batch* b, const float* psf, voi
     Structure S;
     if ((r = make_structure(d, nullptr, nullptr, nullptr, nullptr, &S)) != GF_OK) return r;
     const int P = d->psf_size;
-    std::map<int, std::vector<int>> classes;  // odd class -> stamps
-    for (int i = 0; i < b->count; ++i) {
-        const int cls = (b->W[i] + 31) / 32;
-        if (cls & 1) classes[cls].push_back(i);
-    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     GF_CUDA(cudaEventCreate(&e0));
     GF_CUDA(cudaEventCreate(&e1));
     gf_status out = GF_OK;
-    for (const auto& kv : classes) {
-        const int cls = kv.first;
+    // time the Jacobian-pass convolution of stamps idx under the current table;
+    // tile_w > 0 launches that width's kind alone
+    auto time_conv = [&](const std::vector<int>& idx, int tile_w, float* best) -> gf_status {
         std::vector<int> H, W;
         std::vector<int64_t> psf_off;
-        for (int i : kv.second) {
+        for (int i : idx) {
             H.push_back(b->H[i]);
             W.push_back(b->W[i]);
             psf_off.push_back(b->psf_off ? b->psf_off[i] : (int64_t)i * P * P);
         }
-        float best_ms[2] = {INFINITY, INFINITY};
-        const int widths[2] = {64, 32};
-        for (int v = 0; v < 2 && out == GF_OK; ++v) {
+        Plan pl;
+        plan_batch(d, S, (int)H.size(), H.data(), W.data(), nullptr, psf_off.data(), NEED_JAC, &pl);
+        gf_status rr = check_ws(ws, ws_bytes, pl.L.total);
+        if (rr != GF_OK) return rr;
+        if ((rr = upload(ws, make_blob(pl, S, nullptr), s)) != GF_OK) return rr;
+        PassArgs a = jac_args(ws, pl.L, base_args(ws, pl.L, psf, nullptr, nullptr, P));
+        auto launch = [&]() {
+            return tile_w > 0 ? launch_conv_direct_width(a, tile_w, s) : launch_conv_direct(a, s);
+        };
+        if (cudaMemsetAsync(a.ext, 0, sizeof(float) * (size_t)pl.L.nchan *
+                                          (pl.st.back().ext1_off +
+                                           (long long)pl.st.back().He * pl.st.back().We),
+                            s) != cudaSuccess ||
+            launch() != cudaSuccess)
+            return fail(GF_ECUDA, "autotune launch failed");
+        *best = INFINITY;
+        for (int rep = 0; rep < 3; ++rep) {
+            float ms = 0.0f;
+            if (cudaEventRecord(e0, s) != cudaSuccess || launch() != cudaSuccess ||
+                cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                return fail(GF_ECUDA, "autotune timing failed");
+            *best = std::min(*best, ms);
+        }
+        return GF_OK;
+    };
+    std::map<int, std::vector<int>> classes;  // odd class -> stamps
+    std::vector<int> all(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        all[i] = i;
+        const int cls = (b->W[i] + 31) / 32;
+        if (cls & 1) classes[cls].push_back(i);
+    }
+    auto tune_widths = [&]() -> gf_status {
+        for (const auto& kv : classes) {
+            const int widths[2] = {64, 32};
+            float ms[2] = {INFINITY, INFINITY};
+            for (int v = 0; v < 2; ++v) {
+                {
+                    std::lock_guard<std::mutex> g(g_tune_mu);
+                    g_tune[dev][{P, kv.first}] = widths[v];
+                }
+                gf_status rr = time_conv(kv.second, widths[v], &ms[v]);
+                if (rr != GF_OK) return rr;
+            }
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            g_tune[dev][{P, kv.first}] = ms[1] < ms[0] ? 32 : 64;
+        }
+        return GF_OK;
+    };
+    if ((out = tune_widths()) == GF_OK) {
+        const ConvShape cand[6] = {{32, 8}, {32, 4}, {32, 16}, {16, 8}, {16, 4}, {16, 16}};
+        float best = INFINITY;
+        ConvShape pick = kConvShapeDefault;
+        for (const ConvShape& c : cand) {
             {
                 std::lock_guard<std::mutex> g(g_tune_mu);
-                g_tune[dev][{P, cls}] = widths[v];
+                g_tune_shape[dev][P] = c;
             }
-            Plan pl;
-            plan_batch(d, S, (int)H.size(), H.data(), W.data(), nullptr, psf_off.data(), NEED_JAC, &pl);
-            if ((out = check_ws(ws, ws_bytes, pl.L.total)) != GF_OK) break;
-            if ((out = upload(ws, make_blob(pl, S, nullptr), s)) != GF_OK) break;
-            PassArgs a = jac_args(ws, pl.L, base_args(ws, pl.L, psf, nullptr, nullptr, P));
-            if (cudaMemsetAsync(a.ext, 0, sizeof(float) * (size_t)pl.L.nchan *
-                                              (pl.st.back().ext1_off +
-                                               (long long)pl.st.back().He * pl.st.back().We),
-                                s) != cudaSuccess ||
-                launch_conv_direct_width(a, widths[v], s) != cudaSuccess) {
-                out = fail(GF_ECUDA, "autotune launch failed");
-                break;
-            }
-            for (int rep = 0; rep < 3; ++rep) {
-                float ms = 0.0f;
-                if (cudaEventRecord(e0, s) != cudaSuccess ||
-                    launch_conv_direct_width(a, widths[v], s) != cudaSuccess ||
-                    cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                    out = fail(GF_ECUDA, "autotune timing failed");
-                    break;
-                }
-                best_ms[v] = std::min(best_ms[v], ms);
+            float ms = INFINITY;
+            if ((out = time_conv(all, 0, &ms)) != GF_OK) break;
+            if (ms < best) {
+                best = ms;
+                pick = c;
             }
         }
         std::lock_guard<std::mutex> g(g_tune_mu);
-        g_tune[dev][{P, cls}] = best_ms[1] < best_ms[0] ? 32 : 64;
-        if (out != GF_OK) break;
+        g_tune_shape[dev][P] = pick;
     }
+    if (out == GF_OK) out = tune_widths();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return out;
 }
 
 int gf_conv_tile_width(int psf_size, int width) { return conv_tile_width(psf_size, width); }
+
+gf_status gf_conv_tile_shape(int psf_size, int width, int* tile_w, int* tile_h, int* ctas_per_sm)
+{
+    if (psf_size < 1 || psf_size > GF_DIRECT_MAX_PSF || (psf_size & 1) == 0 || width < 1)
+        return fail(GF_EINVAL, "bad PSF side or width");
+    const ConvShape c = conv_shape(psf_size);
+    if (tile_w) *tile_w = conv_tile_width(psf_size, width);
+    if (tile_h) *tile_h = c.ty;
+    if (ctas_per_sm) *ctas_per_sm = c.ctas_per_sm;
+    return GF_OK;
+}
+
+gf_status gf_set_conv_tile_shape(int psf_size, int tile_h, int ctas_per_sm)
+{
+    if (psf_size < 1 || psf_size > GF_DIRECT_MAX_PSF || (psf_size & 1) == 0)
+        return fail(GF_EINVAL, "bad PSF side");
+    if (tile_h != 16 && tile_h != 32) return fail(GF_EINVAL, "tile height must be 16 or 32");
+    if (ctas_per_sm < 1 || ctas_per_sm > 32) return fail(GF_EINVAL, "CTAs per SM must be 1 .. 32");
+    int dev = 0;
+    GF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(GF_ECUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_shape[dev][psf_size] = ConvShape{tile_h, ctas_per_sm};
+    return GF_OK;
+}
 
 gf_status gf_set_conv_tile_width(int psf_size, int width, int tile_w)
 {

@@ -4,8 +4,10 @@
 //   out(i, j) = sum_{v,u} psf[v][u] * E[i+2c-v][j+2c-u]
 //             = sum_{v,u} k[v][u]   * E[i+v][j+u],   k[v][u] = psf[P-1-v][P-1-u]
 //
-// One CTA computes a 32 x TX output tile of one channel: TX = 64 (4 warps) or
-// TX = 32 (2 warps), chosen per stamp (the two kinds of work item).  The
+// One CTA computes a TY x TX output tile of one channel: TX = 64 or 32,
+// chosen per stamp (the two kinds of work item), and TY = 32 or 16, chosen per
+// call; TX/32 x TY/16 warps.  Both, and the persistent grid, come from the
+// device's tuning table (gf_autotune) or its defaults (TY 32, 8 CTAs per SM).  The
 // flipped PSF (rows padded with zeros to P4, a multiple of 4 taps) and the
 // (32+P-1) x SW halo tile of the channel grid are staged in shared memory.
 // A warp covers 16 x 32 outputs: lane 8 cg + rl owns the 8 contiguous columns
@@ -29,8 +31,6 @@
 #include "gf_internal.cuh"
 
 namespace {
-
-constexpr int TY = CONV_TY;
 
 // row stride of the staged grid tile: >= TX + P4 and 4 (mod 8)
 __host__ __device__ __forceinline__ int conv_sw(int TX, int P4)
@@ -124,11 +124,11 @@ __device__ __forceinline__ void tap_row(float (&acc)[RPT][8], const float* kr, c
 }
 
 // Work item = (channel, output tile of a listed stamp of this tile width).
-template <int TX, int P4K>
-__global__ void __launch_bounds__(TX * 2) k_conv_direct(PassArgs a)
+template <int TX, int TY, int P4K>
+__global__ void __launch_bounds__(TX * TY / 16) k_conv_direct(PassArgs a)
 {
     pdl_entry();
-    constexpr int NT = TX * 2, WX = TX / 32;  // threads, warps across
+    constexpr int NT = TX * TY / 16, WX = TX / 32;  // threads, warps across
     extern __shared__ __align__(16) float smem[];
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + (TX == 64 ? WK_CONV : WK_CONV32) * (a.count + 1);
@@ -222,39 +222,46 @@ __global__ void __launch_bounds__(TX * 2) k_conv_direct(PassArgs a)
 
 cudaError_t ensure_smem_optin_conv_direct(int P, int* cache);
 
-template <int TX>
+template <int TX, int TY>
 size_t conv_smem(int P)
 {
     const int P4 = (P + 3) & ~3;
     return sizeof(float) * ((size_t)P * P4 + (size_t)(TY + P - 1) * conv_sw(TX, P4));
 }
 
-size_t conv_direct_smem(int P) { return conv_smem<64>(P); }
+size_t conv_direct_smem(int P) { return conv_smem<64, 32>(P); }
 
-template <int TX, int P4K>
+template <int TX, int TY, int P4K>
 cudaError_t launch_p4(const PassArgs& a, int kind, cudaStream_t s)
 {
-    GF_LAUNCH_PDL(k_conv_direct<TX, P4K>, dim3(a.grid[kind]), dim3(TX * 2), conv_smem<TX>(a.P), s, a);
+    GF_LAUNCH_PDL((k_conv_direct<TX, TY, P4K>), dim3(a.grid[kind]), dim3(TX * TY / 16),
+                  conv_smem<TX, TY>(a.P), s, a);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
+}
+
+template <int TX, int TY>
+cudaError_t launch_tile_h(const PassArgs& a, int kind, cudaStream_t s)
+{
+    switch ((a.P + 3) & ~3) {
+    case 4: return launch_p4<TX, TY, 4>(a, kind, s);
+    case 8: return launch_p4<TX, TY, 8>(a, kind, s);
+    case 12: return launch_p4<TX, TY, 12>(a, kind, s);
+    case 16: return launch_p4<TX, TY, 16>(a, kind, s);
+    case 20: return launch_p4<TX, TY, 20>(a, kind, s);
+    case 24: return launch_p4<TX, TY, 24>(a, kind, s);
+    case 28: return launch_p4<TX, TY, 28>(a, kind, s);
+    case 32: return launch_p4<TX, TY, 32>(a, kind, s);
+    case 36: return launch_p4<TX, TY, 36>(a, kind, s);
+    default: return launch_p4<TX, TY, 0>(a, kind, s);
+    }
 }
 
 template <int TX>
 cudaError_t launch_tile(const PassArgs& a, int kind, cudaStream_t s)
 {
     if (a.maxitems[kind] <= 0) return cudaSuccess;
-    switch ((a.P + 3) & ~3) {
-    case 4: return launch_p4<TX, 4>(a, kind, s);
-    case 8: return launch_p4<TX, 8>(a, kind, s);
-    case 12: return launch_p4<TX, 12>(a, kind, s);
-    case 16: return launch_p4<TX, 16>(a, kind, s);
-    case 20: return launch_p4<TX, 20>(a, kind, s);
-    case 24: return launch_p4<TX, 24>(a, kind, s);
-    case 28: return launch_p4<TX, 28>(a, kind, s);
-    case 32: return launch_p4<TX, 32>(a, kind, s);
-    case 36: return launch_p4<TX, 36>(a, kind, s);
-    default: return launch_p4<TX, 0>(a, kind, s);
-    }
+    return a.conv_ty == 16 ? launch_tile_h<TX, 16>(a, kind, s) : launch_tile_h<TX, 32>(a, kind, s);
 }
 
 cudaError_t launch_conv_direct(const PassArgs& a, cudaStream_t s)
@@ -275,15 +282,22 @@ cudaError_t launch_conv_direct_width(const PassArgs& a, int tile_w, cudaStream_t
 
 // one cache per device and width for every caller, so that a call made before a
 // stream capture leaves nothing to set inside it
-static int g_conv_optin64[64], g_conv_optin32[64];
+static int g_conv_optin[4][64];
 
-// (the specialised kernels serve PSFs up to 33 pixels, whose tiles stay below the
+// (the specialised kernels serve PSFs up to 35 pixels, whose tiles stay below the
 // default 48 KB of shared memory; only the generic ones need the opt-in)
 cudaError_t ensure_smem_optin_conv_direct(int P, int*)
 {
-    cudaError_t e = ensure_smem_optin((const void*)k_conv_direct<64, 0>, (int)conv_smem<64>(P),
-                                      g_conv_optin64);
-    if (e != cudaSuccess) return e;
-    return ensure_smem_optin((const void*)k_conv_direct<32, 0>, (int)conv_smem<32>(P),
-                             g_conv_optin32);
+    cudaError_t e = ensure_smem_optin((const void*)k_conv_direct<64, 32, 0>,
+                                      (int)conv_smem<64, 32>(P), g_conv_optin[0]);
+    if (e == cudaSuccess)
+        e = ensure_smem_optin((const void*)k_conv_direct<32, 32, 0>, (int)conv_smem<32, 32>(P),
+                              g_conv_optin[1]);
+    if (e == cudaSuccess)
+        e = ensure_smem_optin((const void*)k_conv_direct<64, 16, 0>, (int)conv_smem<64, 16>(P),
+                              g_conv_optin[2]);
+    if (e == cudaSuccess)
+        e = ensure_smem_optin((const void*)k_conv_direct<32, 16, 0>, (int)conv_smem<32, 16>(P),
+                              g_conv_optin[3]);
+    return e;
 }

@@ -484,6 +484,7 @@ struct PassArgs {
                                // of the same components); else independent models
     int jac_analytic;          // the Jacobian pass's nonlinear columns are CH_DERIV channels
     int eval_variant;          // 0 Sersic/disk/Gaussian, 1 with Moffat, 2 with King/Nuker/point
+    int conv_ty;               // direct-convolution tile height (32 or 16)
     float* ext;                // channel grids: ext + ext_index(st[b], nchan, k)
     float* y;                  // convolved channels: y + y_index(st[b], nchan, k)
     const float* psf;
@@ -590,7 +591,7 @@ cudaError_t launch_lm_export(int count, const Structure* S, const LMState* lm, d
                              cudaStream_t s);
 
 // conv tile shape of the direct kernel
-#define CONV_TY 32
+#define CONV_TY 32  // default direct-convolution tile height
 #define CONV_TX 64
 // pixels per block of the reductions
 #define RED_THREADS 256

@@ -161,6 +161,9 @@ def lib():
             L.gf_conv_tile_width.argtypes = [C.c_int, C.c_int]
             L.gf_set_conv_tile_width.restype = C.c_int
             L.gf_set_conv_tile_width.argtypes = [C.c_int, C.c_int, C.c_int]
+            ip = C.POINTER(C.c_int)
+            L.gf_conv_tile_shape.argtypes = [C.c_int, C.c_int, ip, ip, ip]
+            L.gf_set_conv_tile_shape.argtypes = [C.c_int, C.c_int, C.c_int]
             L.gf_launch_count.restype = C.c_longlong
             ps = C.POINTER(SpecDesc)
             L.gf_spec_nparams.restype = C.c_int
@@ -613,8 +616,9 @@ def guess_select(cand, x2_cand, dflt, x2_dflt, lo=None, hi=None, ws=None, stream
 
 
 def autotune(d: Desc, batch: Batch, psf, ws=None, stream=None):
-    """Time both direct-convolution tile widths per width class of the batch and
-    keep the faster on this device (a no-op for Fourier-space convolution)."""
+    """Time the direct convolution's launch shapes on the batch (tile width per
+    odd width class, tile height and persistent grid) and keep the fastest on
+    this device (a no-op for Fourier-space convolution)."""
     w, n = _ws(ws).get(lib().gf_workspace_size_batch(C.byref(d), C.byref(batch), None))
     _check(lib().gf_autotune(C.byref(d), C.byref(batch), _ptr(psf), w, n, _stream(stream)))
 
@@ -625,6 +629,18 @@ def conv_tile_width(psf_size: int, width: int) -> int:
 
 def set_conv_tile_width(psf_size: int, width: int, tile_w: int):
     _check(lib().gf_set_conv_tile_width(psf_size, width, tile_w))
+
+
+def conv_tile_shape(psf_size: int, width: int):
+    """(tile width, tile height, CTAs per SM) of the direct convolution on the
+    current device for PSF side psf_size and stamp width `width`."""
+    tw, th, cap = C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(lib().gf_conv_tile_shape(psf_size, width, C.byref(tw), C.byref(th), C.byref(cap)))
+    return tw.value, th.value, cap.value
+
+
+def set_conv_tile_shape(psf_size: int, tile_h: int, ctas_per_sm: int):
+    _check(lib().gf_set_conv_tile_shape(psf_size, tile_h, ctas_per_sm))
 
 
 PROF_CLASSES = ("model", "conv", "reduce", "lm")

@@ -99,6 +99,10 @@ def test_tile_width_setter_validates_before_touching_the_device():
     assert L.gf_set_conv_tile_width(33, 64, 32) == gf.EINVAL  # even class: 64 only
     assert L.gf_set_conv_tile_width(33, 70, 48) == gf.EINVAL  # no such width
     assert L.gf_set_conv_tile_width(0, 70, 32) == gf.EINVAL
+    assert L.gf_set_conv_tile_shape(33, 24, 8) == gf.EINVAL  # no such height
+    assert L.gf_set_conv_tile_shape(33, 16, 0) == gf.EINVAL
+    assert L.gf_set_conv_tile_shape(33, 16, 33) == gf.EINVAL
+    assert L.gf_set_conv_tile_shape(32, 16, 8) == gf.EINVAL  # even PSF side
 
 
 def test_lm_ladder_option_validated_before_launch(gf):

@@ -1,6 +1,7 @@
-"""The direct-convolution tile width (32 x 64 or 32 x 32) changes the work
-decomposition only: models, chi^2 and Jacobian sums must be bit-identical under
-both, and the tuner must leave a valid choice for every class it times."""
+"""The direct-convolution launch shape -- tile width (64 or 32), tile height
+(32 or 16) and persistent grid (CTAs per SM) -- changes the work decomposition
+only: models, chi^2 and Jacobian sums must be bit-identical under every shape,
+and the tuner must leave a valid choice for every class it times."""
 import numpy as np
 import pytest
 
@@ -59,12 +60,27 @@ def test_tile_widths_give_identical_results(gf):
         assert np.array_equal(np.asarray(a), np.asarray(c))
 
 
+def test_every_tile_height_and_grid_gives_identical_results(gf):
+    d, b, params, img, sig, psf = case(gf)
+    outs = []
+    for th, cap in [(32, 8), (16, 8), (32, 4), (16, 16), (32, 1), (16, 2)]:
+        gf.set_conv_tile_shape(P, th, cap)
+        assert gf.conv_tile_shape(P, 64)[1:] == (th, cap)
+        outs.append(run(gf, d, b, params, img, sig, psf))
+    gf.set_conv_tile_shape(P, 32, 8)
+    for o in outs[1:]:
+        for a, c in zip(outs[0], o):
+            assert np.array_equal(np.asarray(a), np.asarray(c))
+
+
 def test_autotune_sets_a_width_per_odd_class(gf):
     d, b, params, img, sig, psf = case(gf)
     ref = run(gf, d, b, params, img, sig, psf)
     gf.autotune(d, b, psf)
     for _, W in SIZES:
         assert gf.conv_tile_width(P, W) in ((32, 64) if ((W + 31) // 32) % 2 else (64,))
+        tw, th, cap = gf.conv_tile_shape(P, W)
+        assert th in (16, 32) and cap in (4, 8, 16)
     after = run(gf, d, b, params, img, sig, psf)
     for a, c in zip(ref, after):
         assert np.array_equal(np.asarray(a), np.asarray(c))
