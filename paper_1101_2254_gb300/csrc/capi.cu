@@ -2191,10 +2191,12 @@ gf_status gf_default_guess(const gf_batch* b, const float* img, double* params, 
     std::vector<long long> off(count);
     size_t smem = 0;
     long long run = 0;
+    int max_npx = 0;
     for (int i = 0; i < count; ++i) {
         if (H[i] < 1 || W[i] < 1 || (long long)H[i] * W[i] > (1LL << 30))
             return fail(GF_EINVAL, "stamp size out of range");
         smem = std::max(smem, default_guess_smem(H[i], W[i]));
+        max_npx = (int)std::min<long long>(std::max<long long>(max_npx, (long long)H[i] * W[i]), INT_MAX);
         off[i] = b->pix_off ? (long long)b->pix_off[i] : run;
         run += (long long)H[i] * W[i];
     }
@@ -2209,7 +2211,7 @@ gf_status gf_default_guess(const gf_batch* b, const float* img, double* params, 
     memcpy(blob.data() + g.off, off.data(), sizeof(long long) * count);
     if ((r = upload(ws, blob, s)) != GF_OK) return r;
     GF_CUDA(default_guess(count, at<int>(ws, g.H), at<int>(ws, g.W), at<long long>(ws, g.off), img,
-                          params, kGuessSlots, smem, s));
+                          params, kGuessSlots, smem, max_npx, s));
     return GF_OK;
 }
 

@@ -686,9 +686,13 @@ __global__ void __launch_bounds__(DG_THREADS) k_default_guess(const int* __restr
                                                                const int* __restrict__ Ws,
                                                                const long long* __restrict__ off,
                                                                const float* __restrict__ img,
-                                                               double* __restrict__ out, int nslots)
+                                                               double* __restrict__ out, int nslots,
+                                                               int ring_cap, int cache_cap)
 {
-    extern __shared__ double ring[];  // next power of two >= ring length
+    // dynamic shared memory: the ring (ring_cap doubles, a power of two >= the
+    // longest ring) then, for stamps of at most cache_cap pixels, each pixel's
+    // sky-subtracted value and squared elliptical radius
+    extern __shared__ double ring[];
     __shared__ double red[DG_THREADS];
     const int b = blockIdx.x;
     const int H = Hs[b], W = Ws[b];
@@ -755,19 +759,46 @@ __global__ void __launch_bounds__(DG_THREADS) k_default_guess(const int* __restr
     const double th = __ddiv_rn(__dmul_rn(pa, M_PI), 180.0), cs = cos(th), sn = sin(th);
     const double half = 0.5 * s0;
     const int K = 4 * max(H, W);
-    int klo = 0, khi = K + 1;  // enclosed(klo) < half <= enclosed(khi); K + 1 = not reached
-    while (khi - klo > 1) {
-        const int km = (klo + khi) >> 1;
-        const double a = 0.25 * km, a2 = __dmul_rn(a, a);
-        double enc = 0.0;
+    // each pixel's value and squared elliptical radius, formed once (FP64 is
+    // slow on this GPU, a division most of all) instead of once per bisection
+    // step; the same operations in the same order, so the same numbers
+    const bool cached = npx <= cache_cap;
+    double* cv = ring + ring_cap;
+    double* crr = cv + cache_cap;
+    if (cached) {
         for (int k = threadIdx.x; k < npx; k += blockDim.x) {
             const double v = (double)im[k] - sky;
+            cv[k] = v;
             if (v <= 0.0) continue;
             const int i = k / W, j = k - i * W;
             const double dx = j - x0, dy = i - y0;
             const double xp = __dadd_rn(__dmul_rn(dx, cs), __dmul_rn(dy, sn));
             const double yp = __ddiv_rn(__dadd_rn(-__dmul_rn(dx, sn), __dmul_rn(dy, cs)), q);
-            if (__dadd_rn(__dmul_rn(xp, xp), __dmul_rn(yp, yp)) <= a2) enc += v;
+            crr[k] = __dadd_rn(__dmul_rn(xp, xp), __dmul_rn(yp, yp));
+        }
+        __syncthreads();
+    }
+    int klo = 0, khi = K + 1;  // enclosed(klo) < half <= enclosed(khi); K + 1 = not reached
+    while (khi - klo > 1) {
+        const int km = (klo + khi) >> 1;
+        const double a = 0.25 * km, a2 = __dmul_rn(a, a);
+        double enc = 0.0;
+        if (cached) {
+            for (int k = threadIdx.x; k < npx; k += blockDim.x) {
+                const double v = cv[k];
+                if (v <= 0.0) continue;
+                if (crr[k] <= a2) enc += v;
+            }
+        } else {
+            for (int k = threadIdx.x; k < npx; k += blockDim.x) {
+                const double v = (double)im[k] - sky;
+                if (v <= 0.0) continue;
+                const int i = k / W, j = k - i * W;
+                const double dx = j - x0, dy = i - y0;
+                const double xp = __dadd_rn(__dmul_rn(dx, cs), __dmul_rn(dy, sn));
+                const double yp = __ddiv_rn(__dadd_rn(-__dmul_rn(dx, sn), __dmul_rn(dy, cs)), q);
+                if (__dadd_rn(__dmul_rn(xp, xp), __dmul_rn(yp, yp)) <= a2) enc += v;
+            }
         }
         enc = block_sum(enc, red);
         if (enc >= half)
@@ -1001,13 +1032,21 @@ size_t default_guess_smem(int H, int W)
     return sizeof(double) * (size_t)n2;
 }
 
+// pixels per stamp the per-pixel cache of k_default_guess holds at most (96 KB)
+constexpr int DG_CACHE_MAX = 6144;
+
 cudaError_t default_guess(int count, const int* H, const int* W, const long long* off,
-                          const float* img, double* out, int nslots, size_t smem, cudaStream_t s)
+                          const float* img, double* out, int nslots, size_t smem, int max_npx,
+                          cudaStream_t s)
 {
     static int optin[64];
-    cudaError_t e = ensure_smem_optin((const void*)k_default_guess, (int)smem, optin);
+    const int ring_cap = (int)(smem / sizeof(double));
+    const int cache_cap = max_npx <= DG_CACHE_MAX ? max_npx : 0;
+    const size_t bytes = smem + 2 * sizeof(double) * (size_t)cache_cap;
+    cudaError_t e = ensure_smem_optin((const void*)k_default_guess, (int)bytes, optin);
     if (e != cudaSuccess) return e;
-    k_default_guess<<<count, DG_THREADS, smem, s>>>(H, W, off, img, out, nslots);
+    k_default_guess<<<count, DG_THREADS, bytes, s>>>(H, W, off, img, out, nslots, ring_cap,
+                                                     cache_cap);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }

@@ -44,7 +44,8 @@ cudaError_t noise_fill(const float* m, long long n, unsigned long long seed, flo
 cudaError_t philox_blocks(const unsigned* in, unsigned* out, int n, cudaStream_t s);
 size_t default_guess_smem(int H, int W);
 cudaError_t default_guess(int count, const int* H, const int* W, const long long* off,
-                          const float* img, double* out, int nslots, size_t smem, cudaStream_t s);
+                          const float* img, double* out, int nslots, size_t smem, int max_npx,
+                          cudaStream_t s);
 cudaError_t guess_select(int count, int nslots, const double* cand, const double* x2c,
                          const double* dflt, const double* x2d, const double* lo, const double* hi,
                          double* out, int* choice, cudaStream_t s);
