@@ -30,6 +30,7 @@
  *       GF_KING    x0, y0, I_0, r_c, r_t, alpha, q, pa_deg, c        (9 slots)
  *       GF_NUKER   x0, y0, I_b, r_b, alpha, beta, gamma, q, pa_deg, c (10 slots)
  *       GF_PSF     x0, y0, F                                   (3 slots)
+ *       GF_SKY_PLANE s0, gx, gy                                (3 slots)
  *     Sersic: I_e exp(-b_n((r/r_e)^{1/n} - 1)), b_n from P(2n, b_n) = 1/2.
  *     Exponential disk: I_0 exp(-r/r_s).
  *     Gaussian: I_0 exp(-r^2 / (2 s^2)), s = fwhm / (2 sqrt(2 ln 2)).
@@ -48,6 +49,10 @@
  *     convolved image is the PSF interpolated to the sub-pixel position.
  *     King, Nuker and point sources have finite-difference Jacobian columns
  *     only: GF_JAC_ANALYTIC with one of them is rejected (GF_EINVAL).
+ *     Sky plane (GF_SKY_PLANE): s0 + gx (x - x_c) + gy (y - y_c) about each
+ *     stamp's centre (x_c, y_c) = ((W-1)/2, (H-1)/2), on the extended grid
+ *     like the constant sky; all three slots are linear with exact columns.
+ *     A structure has at most one sky component (GF_SKY or GF_SKY_PLANE).
  *     r = (|x'|^{c+2} + |y'/q|^{c+2})^{1/(c+2)}, x' = dx cos t + dy sin t,
  *     y' = -dx sin t + dy cos t, t = pa_deg * pi/180 (counter-clockwise from +x).
  *   - Oversampling: inside an os_box x os_box block of stamp pixels (origin
@@ -109,7 +114,8 @@ typedef enum {
     GF_MOFFAT = 5,
     GF_KING = 6,
     GF_NUKER = 7,
-    GF_PSF = 8
+    GF_PSF = 8,
+    GF_SKY_PLANE = 9
 } gf_comp_kind;
 
 typedef enum {

@@ -38,8 +38,9 @@ SRC = os.path.join(HERE, "gfo.c")
 SRC_CNN = os.path.join(HERE, "gfo_cnn.c")
 SRC_SPEC = os.path.join(HERE, "gfo_spec.c")
 
-SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF = 1, 2, 3, 4, 5, 6, 7, 8
-NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8, KING: 9, NUKER: 10, PSF: 3}
+SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF, SKYPLANE = 1, 2, 3, 4, 5, 6, 7, 8, 9
+NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8, KING: 9, NUKER: 10, PSF: 3,
+          SKYPLANE: 3}
 CONVERGED, BADINPUT, NOCONV, MAXITER = 0, 1, 3, 8
 
 _lock = threading.Lock()

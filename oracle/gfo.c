@@ -36,6 +36,7 @@ int gfo_comp_nslots(int kind)
     case GFO_KING: return 9;
     case GFO_NUKER: return 10;
     case GFO_PSF: return 3;
+    case GFO_SKYPLANE: return 3;
     case GFO_SKY: return 1;
     default: return -1;
     }
@@ -73,14 +74,14 @@ int gfo_slot_is_linear(const gfo_desc* d, int s)
     int k, l, b;
     slot_owner(d, s, &k, &l, &b);
     if (k < 0) return 0;
-    if (d->kinds[k] == GFO_SKY) return 1;
+    if (d->kinds[k] == GFO_SKY || d->kinds[k] == GFO_SKYPLANE) return 1;
     return l == 2;
 }
 
 /* slot semantics: 0 = position, 1 = amplitude, 2 = radius, 3 = Sersic n,
  * 4 = axis ratio, 5 = position angle, 6 = boxiness, 7 = sky, 8 = Moffat beta,
  * 9 = King truncation radius, 10 = King alpha, 11 = Nuker alpha,
- * 12 = Nuker beta, 13 = Nuker gamma */
+ * 12 = Nuker beta, 13 = Nuker gamma, 14 = sky slope in x, 15 = sky slope in y */
 static int slot_role(const gfo_desc* d, int s)
 {
     int k, l, b;
@@ -88,6 +89,7 @@ static int slot_role(const gfo_desc* d, int s)
     if (k < 0) return -1;
     int kind = d->kinds[k];
     if (kind == GFO_SKY) return 7;
+    if (kind == GFO_SKYPLANE) return l == 0 ? 7 : 13 + l;
     if (l <= 1) return 0;
     if (l == 2) return 1;
     if (l == 3) return 2;
@@ -210,6 +212,7 @@ static double gen_radius(double x, double y, double x0, double y0, double q, dou
 double gfo_comp_value(int kind, const double* p, double x, double y, double bn)
 {
     if (kind == GFO_SKY) return p[0];
+    if (kind == GFO_SKYPLANE) return NAN; /* depends on the stamp: see gfo_model_ext */
     if (kind == GFO_PSF) {
         /* an unresolved source of flux F at (x0, y0): its value at a grid point
          * is F times the cubic-convolution weights of the offsets, so that the
@@ -496,6 +499,18 @@ int gfo_model_ext(const gfo_desc* d, const double* params, int comp, int unit_am
         if (comp < 0 || comp == k) {
             double p[GFO_COMP_MAXSLOTS];
             memcpy(p, params + off, sizeof(double) * ns);
+            if (kind == GFO_SKYPLANE) {
+                /* the sky plane at the pixel centres (a linear function: its
+                 * sub-sample mean is the centre value) about the stamp centre */
+                double xc = 0.5 * (d->W - 1), yc = 0.5 * (d->H - 1);
+                if (unit_amp) p[0] = 1.0, p[1] = p[2] = 0.0;
+                for (int ie = 0; ie < He; ++ie)
+                    for (int je = 0; je < We; ++je)
+                        out[(size_t)ie * We + je] +=
+                            f32_store(p[0] + p[1] * ((je - c) - xc) + p[2] * ((ie - c) - yc));
+                off += ns;
+                continue;
+            }
             if (unit_amp) p[kind == GFO_SKY ? 0 : 2] = 1.0;
             double bn = kind == GFO_SERSIC ? gfo_bn(p[4]) : 0.0;
             for (int ie = 0; ie < He; ++ie)
@@ -505,6 +520,23 @@ int gfo_model_ext(const gfo_desc* d, const double* params, int comp, int unit_am
         off += ns;
     }
     return 0;
+}
+
+/* The extended-grid basis function of a linear slot: the model of the slot's
+ * component with that slot set to 1 and the component's other linear slots
+ * to 0 (a profile at unit amplitude, the constant sky, or one of the sky
+ * plane's three terms). */
+int gfo_model_ext_basis(const gfo_desc* d, const double* params, int slot, double* out)
+{
+    int k, l, b;
+    slot_owner(d, slot, &k, &l, &b);
+    if (k < 0 || !gfo_slot_is_linear(d, slot)) return -1;
+    if (d->kinds[k] != GFO_SKYPLANE) return gfo_model_ext(d, params, k, 1, out);
+    double q[GFO_MAX_SLOTS];
+    memcpy(q, params, sizeof(double) * gfo_nslots(d));
+    q[b] = q[b + 1] = q[b + 2] = 0.0;
+    q[slot] = 1.0;
+    return gfo_model_ext(d, q, k, 0, out);
 }
 
 /* ------------------------------------------------------------ convolution */
@@ -762,7 +794,7 @@ double gfo_jacobian(const gfo_desc* d, const double* params, const uint8_t* fixe
         slot_owner(d, s, &k, &l, &b);
         double* col = Jl + (size_t)f * np;
         if (gfo_slot_is_linear(d, s)) {
-            gfo_model_ext(d, params, k, 1, ext);
+            gfo_model_ext_basis(d, params, s, ext);
             convolve(method, d->H, d->W, d->P, ext, psf, col);
             continue;
         }
@@ -883,6 +915,7 @@ static double xtol_scale(const gfo_desc* d, int s)
     int role = slot_role(d, s);
     if (role == 1) return 1e-30;
     if (role == 7) return 1e-3;
+    if (role == 14 || role == 15) return 1e-5; /* sky slopes, per pixel */
     return 1.0;
 }
 

@@ -28,6 +28,7 @@
  *   King    (kind 6): x0, y0, I_0, r_c, r_t, alpha, q, pa_deg, c        (9 slots)
  *   Nuker   (kind 7): x0, y0, I_b, r_b, alpha, beta, gamma, q, pa_deg, c (10 slots)
  *   Point   (kind 8): x0, y0, F                                (3 slots)
+ *   Sky plane (kind 9): s0, gx, gy                             (3 slots)
  * The King, Nuker and point-source kinds have finite-difference Jacobian
  * columns only (no analytic gradient).
  */
@@ -43,6 +44,7 @@
 #define GFO_KING 6      /* I_0 [(w - w_t) / (1 - w_t)]^alpha inside r_t, w = (1 + (r/r_c)^2)^(-1/alpha) */
 #define GFO_NUKER 7     /* I_b 2^((beta-gamma)/alpha) (r/r_b)^-gamma [1 + (r/r_b)^alpha]^((gamma-beta)/alpha) */
 #define GFO_PSF 8       /* point source: F, placed by cubic-convolution weights (see gfo.c) */
+#define GFO_SKYPLANE 9  /* sky s0 + gx (x - x_c) + gy (y - y_c) about the stamp centre */
 #define GFO_COMP_MAXSLOTS 10
 #define GFO_MAX_COMP 8
 #define GFO_MAX_SLOTS 64
@@ -136,6 +138,9 @@ int gfo_model_ext_grad(const gfo_desc* d, const double* params, int slot, double
  * unit_amp = 1: component k with its amplitude slot set to 1. */
 int gfo_model_ext(const gfo_desc* d, const double* params, int comp, int unit_amp,
                   double* out);
+/* The extended-grid basis function of linear slot `slot` (its exact column
+ * before the convolution). */
+int gfo_model_ext_basis(const gfo_desc* d, const double* params, int slot, double* out);
 
 /* Step 2, by the definition: out (H*W) from ext ((H+2c)*(W+2c)) */
 void gfo_convolve_direct(int H, int W, int P, const double* ext, const double* psf,

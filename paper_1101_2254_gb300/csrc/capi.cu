@@ -117,6 +117,7 @@ int comp_slots(int kind)
     case GF_KING: return 9;
     case GF_NUKER: return 10;
     case GF_PSF: return 3;
+    case GF_SKY_PLANE: return 3;
     default: return -1;
     }
 }
@@ -139,7 +140,7 @@ gf_status check_structure(const gf_desc* d)
     int nsky = 0, nprof = 0;
     for (int k = 0; k < d->ncomp; ++k) {
         if (comp_slots(d->kinds[k]) < 0) return fail(GF_EINVAL, "unknown component kind");
-        if (d->kinds[k] == GF_SKY)
+        if (is_sky_kind(d->kinds[k]))
             ++nsky;
         else
             ++nprof;
@@ -306,18 +307,25 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
     S->ncomp = d->ncomp;
     S->sky_slot = -1;
     S->sky_jcol = -1;
+    S->tilt_slot[0] = S->tilt_slot[1] = -1;
+    S->tilt_jcol[0] = S->tilt_jcol[1] = -1;
+    S->nplane = 0;
     int s = 0;
     for (int k = 0; k < d->ncomp; ++k) {
         const int kind = d->kinds[k];
         S->kinds[k] = kind;
         S->slot0[k] = s;
-        if (kind != GF_SKY) S->nprofile++;
+        if (!is_sky_kind(kind)) S->nprofile++;
+        if (kind == GF_SKY_PLANE) S->nplane = 2;
         const int ns = comp_slots(kind);
         for (int l = 0; l < ns; ++l, ++s) {
             int role;
-            if (kind == GF_SKY) {
+            if (kind == GF_SKY || (kind == GF_SKY_PLANE && l == 0)) {
                 role = R_SKY;
                 S->sky_slot = s;
+            } else if (kind == GF_SKY_PLANE) {
+                role = l == 1 ? R_TILTX : R_TILTY;
+                S->tilt_slot[l - 1] = s;
             } else if (l <= 1) {
                 role = R_POS;
             } else if (l == 2) {
@@ -369,11 +377,15 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
         if (nf >= GF_MAX_FREE)
             return fail(GF_EINVAL, "more than " + std::to_string(GF_MAX_FREE) + " free slots");
         if (S->role[t] == R_SKY) S->sky_jcol = nf;
-        if (S->role[t] != R_AMP && S->role[t] != R_SKY) ++nfd;
+        if (S->role[t] == R_TILTX) S->tilt_jcol[0] = nf;
+        if (S->role[t] == R_TILTY) S->tilt_jcol[1] = nf;
+        if (S->role[t] != R_AMP && S->role[t] != R_SKY && S->role[t] != R_TILTX &&
+            S->role[t] != R_TILTY)
+            ++nfd;
         S->freeslot[nf++] = t;
     }
     S->nfree = nf;
-    S->nchan = S->nprofile + nfd;
+    S->nchan = S->nprofile + S->nplane + nfd;
     if (S->nchan > GF_MAX_CHAN) return fail(GF_EINVAL, "too many channels");
     S->nacc = nf * (nf + 1) / 2 + nf + 1;
     if (opts)

@@ -9,6 +9,7 @@
 //   CH_SHAPE  component k with unit amplitude (exact amplitude column)
 //   CH_FD     amp_k (S_k(p + h e_s) - S_k(p)) / h for a nonlinear slot s
 //   CH_DERIV  amp_k dS_k/dp_s, the analytic derivative for a nonlinear slot s
+//   CH_PLANE  x - x_c or y - y_c, a sky plane's slope basis (its exact column)
 // Convolved channels are combined per pixel into the model
 //   m = sum_ch mweight_ch * Y_ch + sky_const
 // and the Jacobian columns; chi^2 and J^T W J, J^T W r are reduced from there.
@@ -24,14 +25,22 @@
 #define GF_MAX_CHAN 24
 #define GF_NACC_MAX (GF_MAX_FREE * (GF_MAX_FREE + 1) / 2 + GF_MAX_FREE + 1)
 
-enum { CH_SUM = 0, CH_SHAPE = 1, CH_FD = 2, CH_DERIV = 3 };
+enum { CH_SUM = 0, CH_SHAPE = 1, CH_FD = 2, CH_DERIV = 3, CH_PLANE = 4 };
 
 // LM phases of a stamp
 enum { PH_NEED_JAC = 0, PH_SOLVE = 1, PH_TRIAL = 2, PH_DONE = 3, PH_NONE = 99 };
 
 // slot roles
 enum { R_POS = 0, R_AMP = 1, R_RAD = 2, R_N = 3, R_Q = 4, R_PA = 5, R_BOXY = 6, R_SKY = 7, R_BETA = 8,
-       R_RT = 9, R_KALPHA = 10, R_NALPHA = 11, R_NBETA = 12, R_NGAMMA = 13 };
+       R_RT = 9, R_KALPHA = 10, R_NALPHA = 11, R_NBETA = 12, R_NGAMMA = 13, R_TILTX = 14,
+       R_TILTY = 15 };
+
+// the constant sky and the sky plane enter the model as a term on the grid,
+// not as a profile
+__host__ __device__ __forceinline__ bool is_sky_kind(int kind)
+{
+    return kind == GF_SKY || kind == GF_SKY_PLANE;
+}
 
 // slots of a component of kind `kind` (-1 for an unknown kind)
 __host__ __device__ __forceinline__ int comp_nslots(int kind)
@@ -45,6 +54,7 @@ __host__ __device__ __forceinline__ int comp_nslots(int kind)
     case GF_KING: return 9;
     case GF_NUKER: return 10;
     case GF_PSF: return 3;
+    case GF_SKY_PLANE: return 3;
     default: return -1;
     }
 }
@@ -77,8 +87,10 @@ struct Channel {
     float sky;      // CH_SUM: sky level added on the grid
     int ncomp;
     float msky;     // channel 0 of a pass: constant added to the convolved model
-    int dslot;      // CH_DERIV: the slot's index inside its component
+    int dslot;      // CH_DERIV: the slot's index inside its component; CH_PLANE: 0 x, 1 y
     float dbdn;     // CH_DERIV of a Sersic component: db_n/dn at its n
+    float pxc, pyc; // the stamp centre, origin of a sky plane (CH_SUM, CH_PLANE)
+    float tgx, tgy; // CH_SUM: the sky plane's slopes (0 without a plane)
     int pad_[2];
     CompConst cc[GF_MAX_COMP];  // all components at the channel's parameter vector
     CompConst pert;             // CH_FD: component `comp` at p + h e_s (unit amplitude)
@@ -117,6 +129,9 @@ struct Structure {
     int owner[GF_MAX_SLOTS];        // component per slot
     int sky_slot;                   // -1 if no sky component
     int sky_jcol;                   // Jacobian column of the sky, -1 if held
+    int tilt_slot[2];               // the sky plane's slope slots (x, y), -1 without a plane
+    int tilt_jcol[2];               // their Jacobian columns, -1 if held
+    int nplane;                     // 2 with a sky plane (its two slope channels), else 0
     int nchan;                      // Jacobian-pass channels per stamp
     int nacc;                       // accumulators of the Jacobian reduction
     double lo[GF_MAX_SLOTS], hi[GF_MAX_SLOTS];
@@ -352,11 +367,13 @@ __device__ __forceinline__ float channel_value(const Channel& ch, float xi, floa
         return grad_pick(g, ch.dslot) * ch.scale;
     }
     if (ch.type == CH_SUM) {
-        float v = ch.sky;
+        // the sky (constant and plane, at the pixel centre), then the profiles
+        float v = fmaf(ch.tgy, yi - ch.pyc, fmaf(ch.tgx, xi - ch.pxc, ch.sky));
         for (int k = 0; k < ch.ncomp; ++k)
-            if (ch.cc[k].kind != GF_SKY) v += comp_eval<EV>(ch.cc[k], xi, yi, ox, oy);
+            if (!is_sky_kind(ch.cc[k].kind)) v += comp_eval<EV>(ch.cc[k], xi, yi, ox, oy);
         return v;
     }
+    if (ch.type == CH_PLANE) return ch.dslot == 0 ? xi - ch.pxc : yi - ch.pyc;
     if (ch.type == CH_SHAPE) return comp_eval<EV>(ch.cc[ch.comp], xi, yi, ox, oy);
     float a = comp_eval<EV>(ch.pert, xi, yi, ox, oy);
     float b = comp_eval<EV>(ch.cc[ch.comp], xi, yi, ox, oy);

@@ -180,7 +180,7 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
     k.b = 1.0f;
     k.ellipse = 1;
     k.e0 = k.e1 = k.e2 = k.e3 = 0.0f;
-    if (kind == GF_SKY) return k;
+    if (is_sky_kind(kind)) return k;
     const double x0 = q[0], y0 = q[1];
     k.x0h = (float)x0;
     k.x0l = (float)(x0 - (double)k.x0h);
@@ -257,7 +257,7 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
 
 __device__ __forceinline__ double amp_of(const Structure& S, const double* p, int k)
 {
-    return S.kinds[k] == GF_SKY ? p[S.slot0[k]] : p[S.slot0[k] + 2];
+    return is_sky_kind(S.kinds[k]) ? p[S.slot0[k]] : p[S.slot0[k] + 2];
 }
 
 __device__ __forceinline__ double sky_of(const Structure& S, const double* p)
@@ -275,7 +275,14 @@ __device__ __forceinline__ double xtol_scale(int role)
 {
     if (role == R_AMP) return 1e-30;
     if (role == R_SKY) return 1e-3;
+    if (role == R_TILTX || role == R_TILTY) return 1e-5;  // sky slopes, per pixel
     return 1.0;
+}
+
+// the sky plane's slope along x (0) or y (1), 0 without a plane
+__device__ __forceinline__ double tilt_of(const Structure& S, const double* p, int a)
+{
+    return S.tilt_slot[a] >= 0 ? p[S.tilt_slot[a]] : 0.0;
 }
 
 __device__ void project_slot(const Structure& S, double* p, int s)
@@ -349,8 +356,9 @@ __device__ void warp_bn(const Structure& S, WarpScratch& W, LMState* L, bool wan
     __syncwarp();
 }
 
-// the model channel (sky and all components) at W.p; lanes build components
-__device__ void warp_build_sum(const Structure& S, WarpScratch& W, Channel* out)
+// the model channel (sky and all components) at W.p; lanes build components;
+// (xc, yc) is the stamp centre, the origin of a sky plane
+__device__ void warp_build_sum(const Structure& S, WarpScratch& W, float xc, float yc, Channel* out)
 {
     const int lane = threadIdx.x & 31;
     if (lane < S.ncomp) {
@@ -367,14 +375,20 @@ __device__ void warp_build_sum(const Structure& S, WarpScratch& W, Channel* out)
         out->sky = (float)sky_of(S, W.p);
         out->ncomp = S.ncomp;
         out->msky = 0.0f;
+        out->pxc = xc;
+        out->pyc = yc;
+        out->tgx = (float)tilt_of(S, W.p, 0);
+        out->tgy = (float)tilt_of(S, W.p, 1);
     }
 }
 
 // Jacobian-pass channels at W.p: one unit-amplitude shape per profile component
 // (its convolution is the exact amplitude column and, weighted by the
-// amplitude, its share of the model), then one FD channel per free nonlinear
-// slot.  Lane c builds channel c.
-__device__ void warp_build_jac(const Structure& S, WarpScratch& W, float psum, Channel* out)
+// amplitude, its share of the model), the two slope bases of a sky plane
+// (exact columns; weighted by the slopes, the plane's share), then one FD
+// channel per free nonlinear slot.  Lane c builds channel c.
+__device__ void warp_build_jac(const Structure& S, WarpScratch& W, float psum, float xc, float yc,
+                               Channel* out)
 {
     const int lane = threadIdx.x & 31;
     if (lane < S.ncomp) W.cc[lane] = make_cc(S.kinds[lane], W.p + S.slot0[lane], true, W.bn[lane]);
@@ -384,18 +398,25 @@ __device__ void warp_build_jac(const Structure& S, WarpScratch& W, float psum, C
         int type = CH_SHAPE, comp = -1, slot = -1, jcol = -1;
         int idx = 0;
         for (int k = 0; k < S.ncomp && comp < 0; ++k) {
-            if (S.kinds[k] == GF_SKY) continue;
+            if (is_sky_kind(S.kinds[k])) continue;
             if (idx == c) comp = k;
             ++idx;
         }
         if (comp >= 0) {
             for (int f = 0; f < S.nfree; ++f)
                 if (S.freeslot[f] == S.slot0[comp] + 2) jcol = f;
+        } else if (c < S.nprofile + S.nplane) {
+            type = CH_PLANE;
+            slot = c - S.nprofile;  // 0: slope along x, 1: along y
+            jcol = S.tilt_jcol[slot];
         } else {
             type = CH_FD;
+            idx += S.nplane;
             for (int f = 0; f < S.nfree && slot < 0; ++f) {
                 const int s = S.freeslot[f];
-                if (S.role[s] == R_AMP || S.role[s] == R_SKY) continue;
+                if (S.role[s] == R_AMP || S.role[s] == R_SKY || S.role[s] == R_TILTX ||
+                    S.role[s] == R_TILTY)
+                    continue;
                 if (idx == c) {
                     slot = s;
                     jcol = f;
@@ -413,8 +434,17 @@ __device__ void warp_build_jac(const Structure& S, WarpScratch& W, float psum, C
         ch.sky = 0.0f;
         ch.ncomp = S.ncomp;
         ch.msky = c == 0 ? (float)(sky_of(S, W.p) * (double)psum) : 0.0f;
+        ch.pxc = xc;
+        ch.pyc = yc;
+        ch.tgx = ch.tgy = 0.0f;
         for (int k = 0; k < S.ncomp; ++k) ch.cc[k] = W.cc[k];
-        if (type == CH_SHAPE) {
+        if (type == CH_PLANE) {
+            ch.dslot = slot;
+            ch.comp = -1;
+            ch.mweight = (float)tilt_of(S, W.p, slot);
+            ch.scale = 0.0f;
+            ch.pert = W.cc[0];
+        } else if (type == CH_SHAPE) {
             ch.mweight = (float)amp_of(S, W.p, comp);
             ch.scale = 0.0f;
             ch.pert = W.cc[comp];
@@ -514,7 +544,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prep_sum(PassArgs a, co
     for (int s = lane; s < S.nslots; s += 32) W.p[s] = p[s];
     __syncwarp();
     warp_bn(S, W, a.lm ? &a.lm[b] : nullptr, false);
-    warp_build_sum(S, W, const_cast<Channel*>(a.chan) + (long long)b * a.chan_stride);
+    warp_build_sum(S, W, 0.5f * (float)(a.st[b].W - 1), 0.5f * (float)(a.st[b].H - 1),
+                   const_cast<Channel*>(a.chan) + (long long)b * a.chan_stride);
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prep_jac(PassArgs a, const double* params)
@@ -526,7 +557,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prep_jac(PassArgs a, co
     for (int s = lane; s < S.nslots; s += 32) W.p[s] = p[s];
     __syncwarp();
     warp_bn(S, W, a.lm ? &a.lm[b] : nullptr, true);
-    warp_build_jac(S, W, a.psf_sum[b], const_cast<Channel*>(a.chan) + (long long)b * a.chan_stride);
+    warp_build_jac(S, W, a.psf_sum[b], 0.5f * (float)(a.st[b].W - 1), 0.5f * (float)(a.st[b].H - 1),
+                   const_cast<Channel*>(a.chan) + (long long)b * a.chan_stride);
 }
 
 __global__ void k_lm_init(int count, const Structure* Sp, LMState* lm, const double* p0)
@@ -655,7 +687,8 @@ __global__ void __launch_bounds__(32 * GF_MAX_LADDER) k_final_solve(PassArgs a, 
     }
     __syncwarp();
     warp_bn(S, W, w == 0 ? &L : nullptr, false);
-    warp_build_sum(S, W, trial_chan + (long long)b * nr + w);
+    warp_build_sum(S, W, 0.5f * (float)(a.st[b].W - 1), 0.5f * (float)(a.st[b].H - 1),
+                   trial_chan + (long long)b * nr + w);
     if (lane == 0) {
         L.pred[w] = pred;
         L.rung[w] = state;

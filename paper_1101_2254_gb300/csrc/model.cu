@@ -155,6 +155,7 @@ __device__ __forceinline__ float jac_channel(const Channel& ch, const float* bas
     for (int k = 0; k < GF_MAX_COMP; ++k)
         if (k == ch.comp) b = base[k];
     if (ch.type == CH_SHAPE) return b;
+    if (ch.type == CH_PLANE) return ch.dslot == 0 ? xi - ch.pxc : yi - ch.pyc;  // pixel centre
     if (ch.type == CH_DERIV) {
         float g[8];
         comp_grad(ch.cc[ch.comp], xi, yi, ox, oy, ch.dbdn, g);
@@ -169,8 +170,8 @@ __device__ __forceinline__ void comp_base(const Channel& c0, float* base, float 
 {
 #pragma unroll
     for (int k = 0; k < GF_MAX_COMP; ++k)
-        base[k] = (k < c0.ncomp && c0.cc[k].kind != GF_SKY) ? comp_eval<EV>(c0.cc[k], xi, yi, ox, oy)
-                                                            : 0.0f;
+        base[k] = (k < c0.ncomp && !is_sky_kind(c0.cc[k].kind)) ? comp_eval<EV>(c0.cc[k], xi, yi, ox, oy)
+                                                                 : 0.0f;
 }
 
 // Work item = block of MODEL_THREADS grid pixels of a listed stamp (all channels).
@@ -283,13 +284,16 @@ __device__ __forceinline__ void body_model_jac_an(const PassArgs& a, int vb, int
             const long long cs = (long long)st.He * st.We;
             const Channel& c0 = chs[0];
             for (int k = 0; k < c0.ncomp; ++k) {
-                if (c0.cc[k].kind == GF_SKY) continue;
+                if (is_sky_kind(c0.cc[k].kind)) continue;
                 float g[8];
                 const float v = comp_grad(c0.cc[k], (float)j, (float)i, 0.0f, 0.0f, dbdn_c[k], g);
                 if (shape_c[k] >= 0) E[shape_c[k] * cs] = v;
                 for (int c = d0[k]; c < d1[k]; ++c)
                     E[c * cs] = grad_pick(g, chs[c].dslot) * chs[c].scale;
             }
+            for (int c = 0; c < nch; ++c)  // a sky plane's slope bases
+                if (chs[c].type == CH_PLANE)
+                    E[c * cs] = chs[c].dslot == 0 ? (float)j - chs[c].pxc : (float)i - chs[c].pyc;
         }
         if (a.work) {
             const int cnt = __syncthreads_count(write);
@@ -422,7 +426,7 @@ __device__ __forceinline__ void body_model_os_jac_an(const PassArgs& a, int vb, 
             const float oy = ((float)ay + 0.5f) / fs - 0.5f;
             const float ox = ((float)bx + 0.5f) / fs - 0.5f;
             for (int k = 0; k < c0.ncomp; ++k) {
-                if (c0.cc[k].kind == GF_SKY) continue;
+                if (is_sky_kind(c0.cc[k].kind)) continue;
                 float dbdn = 0.0f;
                 for (int c = 0; c < nch; ++c)
                     if (chs[c].comp == k && chs[c].type == CH_DERIV) dbdn = chs[c].dbdn;
@@ -435,6 +439,10 @@ __device__ __forceinline__ void body_model_os_jac_an(const PassArgs& a, int vb, 
                                                           : grad_pick(g, chs[c].dslot) * chs[c].scale;
                 }
             }
+#pragma unroll
+            for (int c = 0; c < GF_MAX_CHAN; ++c)  // a sky plane's slope bases (pixel centre)
+                if (c < nch && chs[c].type == CH_PLANE)
+                    acc[c] += chs[c].dslot == 0 ? (float)j - chs[c].pxc : (float)i - chs[c].pyc;
         }
         const long long pix = (long long)(i + st.c) * st.We + (j + st.c);
         const long long cs = (long long)st.He * st.We;

@@ -30,8 +30,9 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF = 1, 2, 3, 4, 5, 6, 7, 8
-NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8, KING: 9, NUKER: 10, PSF: 3}
+SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF, SKYPLANE = 1, 2, 3, 4, 5, 6, 7, 8, 9
+NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8, KING: 9, NUKER: 10, PSF: 3,
+          SKYPLANE: 3}
 
 SIGMA_READ = 0.01
 GAIN = 1.0
@@ -106,6 +107,8 @@ def slot_roles(kinds):
             roles += ["pos", "pos", "amp"]
         elif k == SKY:
             roles += ["sky"]
+        elif k == SKYPLANE:
+            roles += ["sky", "skygx", "skygy"]
         else:
             raise ValueError(k)
     return roles
@@ -124,7 +127,7 @@ def perturb_guess(kinds, p_true, fixed, seed: int, frac: float = 0.2):
     for k in kinds:
         ns = NSLOTS[k]
         for s in range(ns):
-            radius_of[off + s] = p_true[off + 3] if k != SKY else 1.0
+            radius_of[off + s] = p_true[off + 3] if k not in (SKY, SKYPLANE) else 1.0
         off += ns
     for ui, i in zip(u, free):
         if roles[i] == "pos":
@@ -267,6 +270,9 @@ def random_params(kinds, rng, H, W, n_range=(0.5, 6.0), boxy=False, beta_range=(
     for k in kinds:
         if k == SKY:
             p += [rng.uniform(0.0, 0.1)]
+            continue
+        if k == SKYPLANE:
+            p += [rng.uniform(0.0, 0.1), rng.uniform(-2e-3, 2e-3), rng.uniform(-2e-3, 2e-3)]
             continue
         x0 = rng.uniform(0.3 * W, 0.7 * W)
         y0 = rng.uniform(0.3 * H, 0.7 * H)

@@ -189,3 +189,70 @@ def test_noiseless_recovery(kinds, params):
     rel = np.abs(p - p_true)[free] / np.maximum(np.abs(p_true[free]), 1.0)
     assert r["chi2"] < 1e-12 * m.size, r
     assert rel.max() < 1e-6, (rel, r)
+
+
+# -------------------------------------------------------------- sky plane
+SKYPLANE = oracle.SKYPLANE
+
+
+def test_sky_plane_convolves_to_closed_form():
+    # s0 + gx (x - x_c) + gy (y - y_c) through a (deliberately asymmetric) PSF:
+    # sum(psf) (s0 + gx (j - x_c) + gy (i - y_c)) + gx M_x + gy M_y, with the
+    # PSF's first moments M_x = sum psf[v][u] (c - u), M_y = sum psf[v][u] (c - v)
+    H, W, P = 17, 23, 7
+    c = (P - 1) // 2
+    psf = synth.random_psf(P, 3).astype(np.float64)
+    s0, gx, gy = 0.7, 0.013, -0.021
+    d = oracle.make_desc(H, W, P, [SKYPLANE], 3, 4)
+    m = oracle.render(d, np.array([s0, gx, gy]), psf)
+    v, u = np.mgrid[0:P, 0:P]
+    Ps, Mx, My = psf.sum(), (psf * (c - u)).sum(), (psf * (c - v)).sum()
+    assert abs(Mx) > 1e-3 and abs(My) > 1e-3  # the test depends on the moments' sign
+    i, j = np.mgrid[0:H, 0:W]
+    xc, yc = (W - 1) / 2, (H - 1) / 2
+    want = Ps * (s0 + gx * (j - xc) + gy * (i - yc)) + gx * Mx + gy * My
+    assert np.abs(m - want).max() < 1e-13
+
+
+def test_sky_plane_fit_is_linear_least_squares():
+    # only the plane's three slots free: the LM ends at the weighted linear
+    # least-squares solution over its three basis columns
+    H, W, P = 40, 36, 9
+    kinds = [SERSIC, SKYPLANE]
+    p_true = np.array([18.2, 19.7, 3.0, 5.0, 2.0, 0.7, 40.0, 0.0, 0.4, 0.004, -0.003])
+    psf = synth.moffat_psf(P, 3.0)
+    d = oracle.make_desc(H, W, P, kinds, 4, 8)
+    img, sig = synth.add_noise(oracle.render(d, p_true, psf), 5)
+    fixed = np.ones(11, np.uint8)
+    fixed[8:] = 0
+    p0 = p_true.copy()
+    p0[8:] = [0.0, 0.0, 0.0]
+    p, r = oracle.lm_fit(d, p0, fixed, psf, img, sig,
+                         opts=oracle.default_opts(ftol=1e-15, xtol=1e-15))
+    # the closed form: columns = the convolved basis, target = image - galaxy
+    gal = oracle.render(d, np.concatenate([p_true[:8], [0.0, 0.0, 0.0]]), psf)
+    i, j = np.mgrid[0:H, 0:W]
+    cols = [oracle.render(d, np.concatenate([p_true[:8], e]), psf) - gal
+            for e in ([1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0])]
+    A = np.stack([c.ravel() for c in cols], 1) / sig.ravel()[:, None]
+    bvec = (img.astype(np.float64) - gal).ravel() / sig.ravel()
+    want = np.linalg.lstsq(A, bvec, rcond=None)[0]
+    assert np.abs(p[8:] - want).max() < 1e-9 * np.abs(want).max(), (p[8:], want)
+
+
+def test_sky_plane_noiseless_recovery():
+    H = W = 48
+    P = 11
+    kinds = [SERSIC, SKYPLANE]
+    p_true = np.array([24.2, 23.9, 0.8, 5.0, 2.0, 0.7, 60.0, 0.0, 0.3, 0.002, -0.0015])
+    psf = synth.moffat_psf(P, 3.0)
+    d = oracle.make_desc(H, W, P, kinds, 4, 8)
+    m = oracle.render(d, p_true, psf)
+    sig = synth.noise_sigma(m)
+    fixed = np.zeros(11, np.uint8)
+    fixed[7] = 1
+    p0 = synth.perturb_guess(kinds, p_true, fixed, 1, frac=0.05)
+    p, r = oracle.lm_fit(d, p0, fixed, psf, m, sig, opts=oracle.default_opts(ftol=1e-14, xtol=1e-14))
+    free = fixed == 0
+    assert r["chi2"] < 1e-12 * m.size, r
+    assert (np.abs(p - p_true)[free] / np.maximum(np.abs(p_true[free]), 1e-3)).max() < 1e-6
