@@ -31,6 +31,7 @@
  *       GF_NUKER   x0, y0, I_b, r_b, alpha, beta, gamma, q, pa_deg, c (10 slots)
  *       GF_PSF     x0, y0, F                                   (3 slots)
  *       GF_SKY_PLANE s0, gx, gy                                (3 slots)
+ *       GF_SERSIC_F  the Sersic's 8 slots, then a1, phi1, a3, phi3, a4, phi4   (14 slots)
  *     Sersic: I_e exp(-b_n((r/r_e)^{1/n} - 1)), b_n from P(2n, b_n) = 1/2.
  *     Exponential disk: I_0 exp(-r/r_s).
  *     Gaussian: I_0 exp(-r^2 / (2 s^2)), s = fwhm / (2 sqrt(2 ln 2)).
@@ -53,6 +54,11 @@
  *     stamp's centre (x_c, y_c) = ((W-1)/2, (H-1)/2), on the extended grid
  *     like the constant sky; all three slots are linear with exact columns.
  *     A structure has at most one sky component (GF_SKY or GF_SKY_PLANE).
+ *     Sersic with Fourier modes (GF_SERSIC_F): the Sersic profile of the
+ *     distorted radius r (1 + sum_m a_m cos(m (t - phi_m))), m = 1, 3, 4,
+ *     t = atan2(y'/q, x') the angle in the component's circularised frame
+ *     (t = 0 on the major axis), phi_m in degrees; amplitudes in [-0.3, 0.3]
+ *     by default, phases free.  Finite-difference columns only.
  *     r = (|x'|^{c+2} + |y'/q|^{c+2})^{1/(c+2)}, x' = dx cos t + dy sin t,
  *     y' = -dx sin t + dy cos t, t = pa_deg * pi/180 (counter-clockwise from +x).
  *   - Oversampling: inside an os_box x os_box block of stamp pixels (origin
@@ -115,7 +121,8 @@ typedef enum {
     GF_KING = 6,
     GF_NUKER = 7,
     GF_PSF = 8,
-    GF_SKY_PLANE = 9
+    GF_SKY_PLANE = 9,
+    GF_SERSIC_F = 10
 } gf_comp_kind;
 
 typedef enum {

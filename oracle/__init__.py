@@ -38,9 +38,9 @@ SRC = os.path.join(HERE, "gfo.c")
 SRC_CNN = os.path.join(HERE, "gfo_cnn.c")
 SRC_SPEC = os.path.join(HERE, "gfo_spec.c")
 
-SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF, SKYPLANE = 1, 2, 3, 4, 5, 6, 7, 8, 9
+SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF, SKYPLANE, SERSIC_F = range(1, 11)
 NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8, KING: 9, NUKER: 10, PSF: 3,
-          SKYPLANE: 3}
+          SKYPLANE: 3, SERSIC_F: 14}
 CONVERGED, BADINPUT, NOCONV, MAXITER = 0, 1, 3, 8
 
 _lock = threading.Lock()
@@ -217,7 +217,7 @@ def keys_weight(x: float) -> float:
 
 def comp_value(kind, p, x, y) -> float:
     p = _f64(p)
-    b = bn(p[4]) if kind == SERSIC else 0.0
+    b = bn(p[4]) if kind in (SERSIC, SERSIC_F) else 0.0
     return lib().gfo_comp_value(int(kind), _dp(p), float(x), float(y), b)
 
 

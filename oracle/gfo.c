@@ -37,6 +37,7 @@ int gfo_comp_nslots(int kind)
     case GFO_NUKER: return 10;
     case GFO_PSF: return 3;
     case GFO_SKYPLANE: return 3;
+    case GFO_SERSIC_F: return 14;
     case GFO_SKY: return 1;
     default: return -1;
     }
@@ -81,7 +82,8 @@ int gfo_slot_is_linear(const gfo_desc* d, int s)
 /* slot semantics: 0 = position, 1 = amplitude, 2 = radius, 3 = Sersic n,
  * 4 = axis ratio, 5 = position angle, 6 = boxiness, 7 = sky, 8 = Moffat beta,
  * 9 = King truncation radius, 10 = King alpha, 11 = Nuker alpha,
- * 12 = Nuker beta, 13 = Nuker gamma, 14 = sky slope in x, 15 = sky slope in y */
+ * 12 = Nuker beta, 13 = Nuker gamma, 14 = sky slope in x, 15 = sky slope in y,
+ * 16 = Fourier amplitude, 17 = Fourier phase */
 static int slot_role(const gfo_desc* d, int s)
 {
     int k, l, b;
@@ -95,6 +97,10 @@ static int slot_role(const gfo_desc* d, int s)
     if (l == 3) return 2;
     if (kind == GFO_SERSIC) {
         static const int r[8] = {0, 0, 1, 2, 3, 4, 5, 6};
+        return r[l];
+    }
+    if (kind == GFO_SERSIC_F) {
+        static const int r[14] = {0, 0, 1, 2, 3, 4, 5, 6, 16, 17, 16, 17, 16, 17};
         return r[l];
     }
     if (kind == GFO_MOFFAT) {
@@ -238,6 +244,23 @@ double gfo_comp_value(int kind, const double* p, double x, double y, double bn)
         double r = gen_radius(x, y, p[0], p[1], p[7], p[8], p[9]);
         double t = fmax(r / rb, 1e-6);
         return p[2] * pow(2.0, (be - ga) / al) * pow(t, -ga) * pow(1.0 + pow(t, al), (ga - be) / al);
+    }
+    if (kind == GFO_SERSIC_F) {
+        /* the Sersic on a radius distorted by Fourier modes m = 1, 3, 4:
+         * r_F = r (1 + sum_m a_m cos(m (t - phi_m))), t = atan2(y'/q, x') the
+         * angle in the component's circularised frame (t = 0 on the major
+         * axis), phi_m in degrees; a_m = 0 gives the plain Sersic */
+        double th = p[6] * M_PI / 180.0;
+        double dx = x - p[0], dy = y - p[1];
+        double xp = dx * cos(th) + dy * sin(th);
+        double yp = -dx * sin(th) + dy * cos(th);
+        double Y = yp / p[5], C = p[7] + 2.0;
+        double r = pow(pow(fabs(xp), C) + pow(fabs(Y), C), 1.0 / C);
+        double t = atan2(Y, xp);
+        static const int ms[3] = {1, 3, 4};
+        double g = 1.0;
+        for (int k = 0; k < 3; ++k) g += p[8 + 2 * k] * cos(ms[k] * (t - p[9 + 2 * k] * M_PI / 180.0));
+        return p[2] * exp(-bn * (pow(r * g / p[3], 1.0 / p[4]) - 1.0));
     }
     double x0 = p[0], y0 = p[1], amp = p[2], rs = p[3];
     double n = 1.0, q, pa, c;
@@ -453,13 +476,13 @@ int gfo_model_ext_grad(const gfo_desc* d, const double* params, int slot, double
     slot_owner(d, slot, &k, &l, &b);
     if (k < 0) return -1;
     int kind = d->kinds[k];
-    if (kind == GFO_KING || kind == GFO_NUKER || kind == GFO_PSF) {
+    if (kind == GFO_KING || kind == GFO_NUKER || kind == GFO_PSF || kind == GFO_SERSIC_F) {
         /* no analytic gradient for these kinds: the column is undefined */
         for (size_t t = 0; t < (size_t)He * We; ++t) out[t] = NAN;
         return -1;
     }
     const double* p = params + b;
-    double bn = kind == GFO_SERSIC ? gfo_bn(p[4]) : 0.0;
+    double bn = (kind == GFO_SERSIC || kind == GFO_SERSIC_F) ? gfo_bn(p[4]) : 0.0;
     double dbdn = kind == GFO_SERSIC ? gfo_bn_deriv(p[4]) : 0.0;
     for (int ie = 0; ie < He; ++ie)
         for (int je = 0; je < We; ++je)
@@ -469,7 +492,7 @@ int gfo_model_ext_grad(const gfo_desc* d, const double* params, int slot, double
 
 double gfo_comp_pixel(const gfo_desc* d, int kind, const double* p, int i, int j)
 {
-    double bn = kind == GFO_SERSIC ? gfo_bn(p[4]) : 0.0;
+    double bn = (kind == GFO_SERSIC || kind == GFO_SERSIC_F) ? gfo_bn(p[4]) : 0.0;
     return comp_pixel_bn(d, kind, p, i, j, bn);
 }
 
@@ -512,7 +535,7 @@ int gfo_model_ext(const gfo_desc* d, const double* params, int comp, int unit_am
                 continue;
             }
             if (unit_amp) p[kind == GFO_SKY ? 0 : 2] = 1.0;
-            double bn = kind == GFO_SERSIC ? gfo_bn(p[4]) : 0.0;
+            double bn = (kind == GFO_SERSIC || kind == GFO_SERSIC_F) ? gfo_bn(p[4]) : 0.0;
             for (int ie = 0; ie < He; ++ie)
                 for (int je = 0; je < We; ++je)
                     out[(size_t)ie * We + je] += f32_store(comp_pixel_bn(d, kind, p, ie - c, je - c, bn));
@@ -867,8 +890,8 @@ void gfo_default_opts(gfo_lm_opts* o)
 
 /* Default box: I >= 0, radii >= 0.1, n in [0.2, 10], q in [0.05, 1],
  * boxiness in [-1.9, 2], Moffat beta in [0.5, 20], King r_t >= 0.1 and alpha
- * in [0.1, 10], Nuker alpha in [0.1, 10], beta in [0, 10], gamma in [0, 2];
- * positions and sky free;
+ * in [0.1, 10], Nuker alpha in [0.1, 10], beta in [0, 10], gamma in [0, 2],
+ * Fourier amplitudes in [-0.3, 0.3]; positions, sky and phases free;
  * position angles are wrapped into [0, 180) instead of clamped. */
 void gfo_default_bounds(const gfo_desc* d, double* lo, double* hi)
 {
@@ -888,6 +911,7 @@ void gfo_default_bounds(const gfo_desc* d, double* lo, double* hi)
         case 11: lo[s] = 0.1; hi[s] = 10.0; break;
         case 12: lo[s] = 0.0; hi[s] = 10.0; break;
         case 13: lo[s] = 0.0; hi[s] = 2.0; break;
+        case 16: lo[s] = -0.3; hi[s] = 0.3; break;
         default: break;
         }
     }

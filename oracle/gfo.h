@@ -29,6 +29,8 @@
  *   Nuker   (kind 7): x0, y0, I_b, r_b, alpha, beta, gamma, q, pa_deg, c (10 slots)
  *   Point   (kind 8): x0, y0, F                                (3 slots)
  *   Sky plane (kind 9): s0, gx, gy                             (3 slots)
+ *   Sersic + Fourier modes (kind 10): the Sersic's 8 slots, then a1, phi1,
+ *             a3, phi3, a4, phi4 (14 slots; phases in degrees)
  * The King, Nuker and point-source kinds have finite-difference Jacobian
  * columns only (no analytic gradient).
  */
@@ -45,7 +47,8 @@
 #define GFO_NUKER 7     /* I_b 2^((beta-gamma)/alpha) (r/r_b)^-gamma [1 + (r/r_b)^alpha]^((gamma-beta)/alpha) */
 #define GFO_PSF 8       /* point source: F, placed by cubic-convolution weights (see gfo.c) */
 #define GFO_SKYPLANE 9  /* sky s0 + gx (x - x_c) + gy (y - y_c) about the stamp centre */
-#define GFO_COMP_MAXSLOTS 10
+#define GFO_SERSIC_F 10 /* Sersic with Fourier modes m = 1, 3, 4 of its isophotes */
+#define GFO_COMP_MAXSLOTS 14
 #define GFO_MAX_COMP 8
 #define GFO_MAX_SLOTS 64
 #define GFO_MAX_FREE 16

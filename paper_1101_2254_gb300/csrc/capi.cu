@@ -118,6 +118,7 @@ int comp_slots(int kind)
     case GF_NUKER: return 10;
     case GF_PSF: return 3;
     case GF_SKY_PLANE: return 3;
+    case GF_SERSIC_F: return 14;
     default: return -1;
     }
 }
@@ -335,6 +336,10 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
             } else if (kind == GF_SERSIC) {
                 static const int r[8] = {0, 0, 1, 2, R_N, R_Q, R_PA, R_BOXY};
                 role = r[l];
+            } else if (kind == GF_SERSIC_F) {
+                static const int r[14] = {0,      0,      1,      2,      R_N,    R_Q,    R_PA,
+                                          R_BOXY, R_FAMP, R_FPHI, R_FAMP, R_FPHI, R_FAMP, R_FPHI};
+                role = r[l];
             } else if (kind == GF_MOFFAT) {
                 static const int r[8] = {0, 0, 1, 2, R_BETA, R_Q, R_PA, R_BOXY};
                 role = r[l];
@@ -363,6 +368,7 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
             case R_NALPHA: l0 = 0.1; h0 = 10.0; break;
             case R_NBETA: l0 = 0.0; h0 = 10.0; break;
             case R_NGAMMA: l0 = 0.0; h0 = 2.0; break;
+            case R_FAMP: l0 = -0.3; h0 = 0.3; break;
             default: break;
             }
             S->lo[s] = lo ? lo[s] : l0;
@@ -397,9 +403,10 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
         return fail(GF_EINVAL, "jac_mode must be GF_JAC_FD or GF_JAC_ANALYTIC");
     if (S->opts.jac_mode == GF_JAC_ANALYTIC)
         for (int k = 0; k < S->ncomp; ++k)
-            if (S->kinds[k] == GF_KING || S->kinds[k] == GF_NUKER || S->kinds[k] == GF_PSF)
-                return fail(GF_EINVAL, "analytic Jacobian columns are not available for King, Nuker "
-                                       "or point-source components (use GF_JAC_FD)");
+            if (S->kinds[k] == GF_KING || S->kinds[k] == GF_NUKER || S->kinds[k] == GF_PSF ||
+                S->kinds[k] == GF_SERSIC_F)
+                return fail(GF_EINVAL, "analytic Jacobian columns are not available for King, Nuker, "
+                                       "point-source or Fourier-mode components (use GF_JAC_FD)");
     if (S->opts.ladder == 0) S->opts.ladder = 2;
     if (S->opts.ladder < 1 || S->opts.ladder > GF_MAX_LADDER)
         return fail(GF_EINVAL, "LM ladder must be 1 .. " + std::to_string(GF_MAX_LADDER));
@@ -533,7 +540,7 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     for (int k = 0; k < S.ncomp; ++k) {
         const int kd = S.kinds[k];
         if (kd == GF_MOFFAT) L.eval_variant = std::max(L.eval_variant, 1);
-        if (kd == GF_KING || kd == GF_NUKER || kd == GF_PSF) L.eval_variant = 2;
+        if (kd == GF_KING || kd == GF_NUKER || kd == GF_PSF || kd == GF_SERSIC_F) L.eval_variant = 2;
     }
     L.nacc = S.nacc;
     L.nslots = S.nslots;

@@ -33,7 +33,13 @@ enum { PH_NEED_JAC = 0, PH_SOLVE = 1, PH_TRIAL = 2, PH_DONE = 3, PH_NONE = 99 };
 // slot roles
 enum { R_POS = 0, R_AMP = 1, R_RAD = 2, R_N = 3, R_Q = 4, R_PA = 5, R_BOXY = 6, R_SKY = 7, R_BETA = 8,
        R_RT = 9, R_KALPHA = 10, R_NALPHA = 11, R_NBETA = 12, R_NGAMMA = 13, R_TILTX = 14,
-       R_TILTY = 15 };
+       R_TILTY = 15, R_FAMP = 16, R_FPHI = 17 };
+
+// a Sersic profile (plain or with Fourier modes): b_n from slot 4
+__host__ __device__ __forceinline__ bool is_sersic_kind(int kind)
+{
+    return kind == GF_SERSIC || kind == GF_SERSIC_F;
+}
 
 // the constant sky and the sky plane enter the model as a term on the grid,
 // not as a profile
@@ -55,10 +61,11 @@ __host__ __device__ __forceinline__ int comp_nslots(int kind)
     case GF_NUKER: return 10;
     case GF_PSF: return 3;
     case GF_SKY_PLANE: return 3;
+    case GF_SERSIC_F: return 14;
     default: return -1;
     }
 }
-#define GF_COMP_MAXSLOTS 10
+#define GF_COMP_MAXSLOTS 14
 
 // Float32 constants of one component at one parameter vector.
 struct CompConst {
@@ -75,7 +82,11 @@ struct CompConst {
     int ellipse;               // C == 2 exactly: r by sqrt
     float e0, e1, e2, e3;      // King: 1/alpha, w_t, 1/(1 - w_t) (invn = alpha, invr = 1/r_c);
                                // Nuker: gamma, (beta-gamma)/alpha, (gamma-beta)/alpha
-                               // (invn = alpha, invr = 1/r_b)
+                               // (invn = alpha, invr = 1/r_b);
+    float e4, e5, e6, e7, e8;  // Sersic + Fourier modes: a_1, a_3, a_4 in e0..e2, then
+                               // cos phi_1 (e3), sin phi_1, cos 3 phi_3, sin 3 phi_3,
+                               // cos 4 phi_4, sin 4 phi_4 (e4..e8)
+    int pad_c[3];
 };
 
 struct Channel {
@@ -182,6 +193,36 @@ __device__ __forceinline__ float keys_w(float x)
 static __device__ __noinline__ float comp_eval_ext(const CompConst& k, float xi, float yi, float ox,
                                             float oy)
 {
+    if (k.kind == GF_SERSIC_F) {
+        // the Sersic of the distorted radius r g(t), g = 1 + sum_m a_m cos m(t - phi_m),
+        // t the angle of (x', y'/q): cos and sin of t from the coordinates, of
+        // 3t and 4t by the multiple-angle identities
+        const float dx = (xi - k.x0h) + (ox - k.x0l);
+        const float dy = (yi - k.y0h) + (oy - k.y0l);
+        const float xp = fmaf(dx, k.cs, dy * k.sn);
+        const float yp = fmaf(dy, k.cs, -dx * k.sn) * k.invq;
+        float r;
+        if (k.ellipse) {
+            r = sqrtf(fmaf(xp, xp, yp * yp));
+        } else {
+            const float ax = exp2f(k.C * log2f(fabsf(xp)));
+            const float ay = exp2f(k.C * log2f(fabsf(yp)));
+            r = exp2f(k.invC * log2f(ax + ay));
+        }
+        const float rho2 = fmaf(xp, xp, yp * yp);
+        const float ir = rho2 > 0.0f ? rsqrtf(rho2) : 0.0f;
+        const float c = rho2 > 0.0f ? xp * ir : 1.0f, s = yp * ir;
+        const float c2 = c * c, s2 = s * s;
+        const float c3 = c * fmaf(4.0f, c2, -3.0f), s3 = s * fmaf(-4.0f, s2, 3.0f);
+        const float c4 = fmaf(8.0f * c2, c2 - 1.0f, 1.0f), s4 = 4.0f * s * c * fmaf(2.0f, c2, -1.0f);
+        float g = 1.0f;
+        g = fmaf(k.e0, fmaf(c, k.e3, s * k.e4), g);
+        g = fmaf(k.e1, fmaf(c3, k.e5, s3 * k.e6), g);
+        g = fmaf(k.e2, fmaf(c4, k.e7, s4 * k.e8), g);
+        const float t = r * g * k.invr;
+        const float u = exp2f(k.invn * log2f(t));
+        return k.amp * expf(fmaf(-k.b, u, k.b0));
+    }
     if (k.kind == GF_PSF) {
         // a point source keeps its pixel-centre weights (it is not sampled)
         const float dx = (xi - k.x0h) - k.x0l, dy = (yi - k.y0h) - k.y0l;

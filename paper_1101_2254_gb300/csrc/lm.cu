@@ -180,6 +180,8 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
     k.b = 1.0f;
     k.ellipse = 1;
     k.e0 = k.e1 = k.e2 = k.e3 = 0.0f;
+    k.e4 = k.e5 = k.e6 = k.e7 = k.e8 = 0.0f;
+    k.pad_c[0] = k.pad_c[1] = k.pad_c[2] = 0;
     if (is_sky_kind(kind)) return k;
     const double x0 = q[0], y0 = q[1];
     k.x0h = (float)x0;
@@ -193,7 +195,7 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
     }
     const double r = q[3];
     // the axis ratio, position angle and boxiness follow the kind's shape slots
-    const int g = (kind == GF_SERSIC || kind == GF_MOFFAT) ? 5
+    const int g = (kind == GF_SERSIC || kind == GF_MOFFAT || kind == GF_SERSIC_F) ? 5
                   : kind == GF_KING                        ? 6
                   : kind == GF_NUKER                       ? 7
                                                            : 4;
@@ -229,11 +231,28 @@ __device__ CompConst make_cc(int kind, const double* q, bool unit_amp, double bn
         k.b0 = 0.0f;
         k.b = (float)(beta * kLn2);
     }
-    if (kind == GF_SERSIC) {
+    if (is_sersic_kind(kind)) {
         const double n = q[4];
         k.invn = (float)(1.0 / n);
         k.b0 = (float)bn;
         k.b = (float)bn;
+    }
+    if (kind == GF_SERSIC_F) {
+        // Fourier modes m = 1, 3, 4 (slots 8 .. 13): amplitudes, then cos and
+        // sin of m phi_m, formed in FP64
+        k.e0 = (float)q[8];
+        k.e1 = (float)q[10];
+        k.e2 = (float)q[12];
+        double sp, cp;
+        sincos(q[9] * (kPi / 180.0), &sp, &cp);
+        k.e3 = (float)cp;
+        k.e4 = (float)sp;
+        sincos(3.0 * q[11] * (kPi / 180.0), &sp, &cp);
+        k.e5 = (float)cp;
+        k.e6 = (float)sp;
+        sincos(4.0 * q[13] * (kPi / 180.0), &sp, &cp);
+        k.e7 = (float)cp;
+        k.e8 = (float)sp;
     }
     if (kind == GF_KING) {
         // slots r_c (3), r_t (4), alpha (5): w_t = (1 + (r_t/r_c)^2)^(-1/alpha)
@@ -317,7 +336,7 @@ __device__ void warp_bn(const Structure& S, WarpScratch& W, LMState* L, bool wan
 {
     const int lane = threadIdx.x & 31;
     for (int k = 0; k < S.ncomp; ++k) {
-        if (S.kinds[k] != GF_SERSIC) continue;
+        if (!is_sersic_kind(S.kinds[k])) continue;
         const int sn = S.slot0[k] + 4;
         const double n = W.p[sn];
         double b = bn_lookup(n);

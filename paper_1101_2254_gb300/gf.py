@@ -16,9 +16,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgf.so")
 
-SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF, SKYPLANE = 1, 2, 3, 4, 5, 6, 7, 8, 9
+SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF, SKYPLANE, SERSIC_F = range(1, 11)
 NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8, KING: 9, NUKER: 10, PSF: 3,
-          SKYPLANE: 3}
+          SKYPLANE: 3, SERSIC_F: 14}
 CONV_AUTO, CONV_DIRECT, CONV_FFT, CONV_DFT_TC = 0, 1, 2, 3
 CALL_MODEL, CALL_CONVOLVE, CALL_CHI2, CALL_EVAL, CALL_JACOBIAN, CALL_LM_FIT = range(6)
 OK, EINVAL, ECUDA, ENOCONV, ESINGULAR, ENONFINITE, ETIMEOUT, ENOMEM, EMAXITER = range(9)

@@ -30,9 +30,9 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF, SKYPLANE = 1, 2, 3, 4, 5, 6, 7, 8, 9
+SERSIC, EXPDISK, SKY, GAUSSIAN, MOFFAT, KING, NUKER, PSF, SKYPLANE, SERSIC_F = range(1, 11)
 NSLOTS = {SERSIC: 8, EXPDISK: 7, SKY: 1, GAUSSIAN: 7, MOFFAT: 8, KING: 9, NUKER: 10, PSF: 3,
-          SKYPLANE: 3}
+          SKYPLANE: 3, SERSIC_F: 14}
 
 SIGMA_READ = 0.01
 GAIN = 1.0
@@ -109,6 +109,9 @@ def slot_roles(kinds):
             roles += ["sky"]
         elif k == SKYPLANE:
             roles += ["sky", "skygx", "skygy"]
+        elif k == SERSIC_F:
+            roles += ["pos", "pos", "amp", "rad", "n", "q", "pa", "c",
+                      "fa", "fphi", "fa", "fphi", "fa", "fphi"]
         else:
             raise ValueError(k)
     return roles
@@ -155,6 +158,8 @@ def perturb_guess(kinds, p_true, fixed, seed: int, frac: float = 0.2):
             p[i] = min(max(p[i], 0.0), 10.0)
         elif r == "ngamma":
             p[i] = min(max(p[i], 0.0), 2.0)
+        elif r == "fa":
+            p[i] = min(max(p[i], -0.3), 0.3)
     return p
 
 

@@ -756,9 +756,22 @@ def point_case():
                        os_box=8, name="point48x51")
 
 
+def fourier_case():
+    # a Sersic with lopsided (m = 1), triangular (m = 3) and boxy/discy (m = 4)
+    # isophote modes; boxiness held
+    kinds = [synth.SERSIC_F, synth.SKY]
+    p = np.array([24.3, 22.6, 30.0, 6.0, 2.0, 0.75, 60.0, 0.0, 0.08, 30.0, 0.05, 10.0, -0.06,
+                  20.0, 0.3])
+    fixed = np.zeros(len(p), np.uint8)
+    fixed[7] = 1
+    return synth.Stamp(47, 49, kinds, p, fixed, synth.moffat_psf(11, 2.5), os_factor=4,
+                       os_box=8, name="fourier47x49")
+
+
 FAMILY_CASES = {"gaussian": gaussian_case, "moffat": moffat_case}
 # families with finite-difference columns only (no analytic gradient)
-FD_FAMILY_CASES = {"king": king_case, "nuker": nuker_case, "point": point_case}
+FD_FAMILY_CASES = {"king": king_case, "nuker": nuker_case, "point": point_case,
+                   "fourier": fourier_case}
 
 
 @pytest.mark.parametrize("family", sorted(FD_FAMILY_CASES))

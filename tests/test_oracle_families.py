@@ -256,3 +256,79 @@ def test_sky_plane_noiseless_recovery():
     free = fixed == 0
     assert r["chi2"] < 1e-12 * m.size, r
     assert (np.abs(p - p_true)[free] / np.maximum(np.abs(p_true[free]), 1e-3)).max() < 1e-6
+
+
+# ------------------------------------------------------- Fourier modes
+SERSIC_F = oracle.SERSIC_F
+
+
+def sersic_f(a=(0.0, 0.0, 0.0), phi=(0.0, 0.0, 0.0), n=1.0, q=0.7, pa=30.0):
+    return np.array([0.0, 0.0, 1.0, 5.0, n, q, pa, 0.0, a[0], phi[0], a[1], phi[1], a[2], phi[2]])
+
+
+def frame_point(p, rho, t):
+    """(x, y) of circular radius rho and angle t in the component's frame
+    (x' = rho cos t, y'/q = rho sin t)."""
+    th = math.radians(p[6])
+    xp, yp = rho * math.cos(t), p[5] * rho * math.sin(t)
+    return p[0] + xp * math.cos(th) - yp * math.sin(th), p[1] + xp * math.sin(th) + yp * math.cos(th)
+
+
+def test_fourier_zero_amplitudes_is_sersic():
+    p = sersic_f(phi=(20.0, 50.0, 80.0), n=2.7)
+    rng = np.random.default_rng(1)
+    for x, y in rng.uniform(-15, 15, (20, 2)):
+        a = oracle.comp_value(SERSIC_F, p, x, y)
+        b = oracle.comp_value(SERSIC, p[:8], x, y)
+        assert abs(a - b) <= 1e-14 * b
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_fourier_isophote_phase_and_amplitude(mode):
+    # a single mode m of amplitude a and phase phi: along t = phi the radius is
+    # scaled by (1 + a), along t = phi + 180/m degrees by (1 - a), so the
+    # effective isophote (I = I_e) sits at rho = r_e / (1 +- a)
+    m = (1, 3, 4)[mode]
+    a, phi = 0.18, 35.0
+    amps, phis = [0.0] * 3, [0.0] * 3
+    amps[mode], phis[mode] = a, phi
+    p = sersic_f(a=amps, phi=phis, n=2.0)
+    for t_deg, g in [(phi, 1 + a), (phi + 180.0 / m, 1 - a)]:
+        x, y = frame_point(p, p[3] / g, math.radians(t_deg))
+        assert abs(oracle.comp_value(SERSIC_F, p, x, y) - p[2]) < 1e-12
+
+
+@pytest.mark.parametrize("mode,a,phi", [(0, 0.2, 40.0), (1, -0.15, 10.0), (2, 0.25, -70.0)])
+def test_fourier_single_mode_flux(mode, a, phi):
+    # the radius r (1 + a cos m(t - phi)) rescales the light of each direction
+    # by 1 / (1 + a cos ...)^2, whose mean over t is (1 - a^2)^(-3/2)
+    from scipy import integrate
+    amps, phis = [0.0] * 3, [0.0] * 3
+    amps[mode], phis[mode] = a, phi
+    p = sersic_f(a=amps, phi=phis, n=1.0)
+
+    def f(rho, t):
+        return oracle.comp_value(SERSIC_F, p, *frame_point(p, rho, t)) * rho
+
+    v, _ = integrate.dblquad(f, 0.0, 2 * math.pi, 0.0, 150.0, epsabs=0.0, epsrel=1e-9)
+    want = oracle.sersic_flux(1.0, 5.0, 1.0, 0.7) * (1 - a * a) ** -1.5
+    assert abs(p[5] * v - want) < 1e-7 * want
+
+
+def test_fourier_noiseless_recovery():
+    H = W = 48
+    P = 11
+    kinds = [SERSIC_F, SKY]
+    p_true = np.array([24.2, 23.9, 2.0, 6.0, 2.0, 0.75, 60.0, 0.0, 0.08, 30.0, 0.05, 10.0,
+                       -0.06, 20.0, 0.3])
+    psf = synth.moffat_psf(P, 3.0)
+    d = oracle.make_desc(H, W, P, kinds, 4, 8)
+    m = oracle.render(d, p_true, psf)
+    sig = synth.noise_sigma(m)
+    fixed = np.zeros(len(p_true), np.uint8)
+    fixed[7] = 1
+    p0 = synth.perturb_guess(kinds, p_true, fixed, 1, frac=0.03)
+    p, r = oracle.lm_fit(d, p0, fixed, psf, m, sig, opts=oracle.default_opts(ftol=1e-14, xtol=1e-14))
+    free = fixed == 0
+    assert r["chi2"] < 1e-12 * m.size, r
+    assert (np.abs(p - p_true)[free] / np.maximum(np.abs(p_true[free]), 1e-2)).max() < 1e-6
