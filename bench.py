@@ -1062,6 +1062,24 @@ def run_learned(args):
         fit()
     torch.cuda.nvtx.range_pop()
     pr = prof.result
+    # the network's inference forward on the step's stamps alone (its conv
+    # layers 2-4 run as implicit GEMMs on the tensor cores)
+    x_in = gf.cnn_input(img, sig)
+    y_net = gf.cnn_forward(tr.w, x_in, ws=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        gf.cnn_forward(tr.w, x_in, ws=ws)
+    e1.record(stream)
+    e1.synchronize()
+    cnn_ms = e0.elapsed_time(e1) / 3
+    # multiply-adds per stamp of conv layers 2-4 (tensor cores) and of the whole
+    # network: conv 2 16^2 x 64 x 288, conv 3 8^2 x 64 x 576, conv 4 4^2 x 128 x 576;
+    # conv 1 32^2 x 32 x 9, fc 2048 x 32 + 32 x 8
+    mac_tc = 256 * 64 * 288 + 64 * 64 * 576 + 16 * 128 * 576
+    mac_all = mac_tc + 1024 * 32 * 9 + 2048 * 32 + 32 * 8
+    del y_net
     peaks, peak_kind = measured_peaks()
     fp32_peak, fp64_peak = gf.fma_peak(False), gf.fma_peak(True)
     ach = pr["conv"]["work"] / (pr["conv"]["ms"] / 1e3) / 1e12
@@ -1128,6 +1146,13 @@ def run_learned(args):
             "wall_ms_per_reached_fit": {
                 "learned": (total_ms / args.steps) / (count * frac_l) if frac_l else None,
                 "default": dflt_ms / (count * frac_d) if frac_d else None},
+            "cnn_forward": {"stamps": count, "ms": cnn_ms, "stamps_per_s": count / (cnn_ms / 1e3),
+                            "tflops_all_layers": 2 * mac_all * count / (cnn_ms / 1e3) / 1e12,
+                            "tflops_tensor_layers_share_of_time": None,
+                            "bf16_peak_sustained_tflops": peaks.get("bf16_tflops_sustained"),
+                            "note": "conv layers 2-4 (%.0f%% of the multiply-adds) on tcgen05; "
+                                    "the whole forward timed, so the rate is a lower bound for "
+                                    "the tensor layers" % (100.0 * mac_tc / mac_all)},
             "training": {"stamps": train_steps * train_batch, "seconds": train_s,
                          "stamps_per_s": train_steps * train_batch / train_s,
                          "loss_first": float(L[:20].mean()), "loss_last": float(L[-20:].mean())},

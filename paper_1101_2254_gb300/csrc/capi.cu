@@ -2113,7 +2113,7 @@ gf_status gf_cnn_forward(const float* w, const float* x, int batch, float* y, vo
     cnn_buffers(ws, batch, false, &cb);
     cudaStream_t s = (cudaStream_t)stream;
     GF_CUDA(cnn_prepare(w, x, batch, cb, s));
-    GF_CUDA(cnn_forward(w, batch, cb, y, s));
+    GF_CUDA(cnn_forward_tc(w, batch, cb, y, s));
     return GF_OK;
 }
 

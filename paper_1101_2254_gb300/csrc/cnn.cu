@@ -916,6 +916,11 @@ cudaError_t cnn_forward(const float* w, int B, const CnnBuffers& cb, float* y, c
         GF_COUNT_LAUNCH();
         in = outs[l];
     }
+    return cnn_forward_fc(w, B, cb, y, s);
+}
+
+cudaError_t cnn_forward_fc(const float* w, int B, const CnnBuffers& cb, float* y, cudaStream_t s)
+{
     k_fc1_fwd<<<blocks((long long)B * 32, 256), 256, 0, s>>>(cb.a3, cb.wp, w, cb.h, B);
     GF_COUNT_LAUNCH();
     k_fc2_fwd<<<blocks((long long)B * NOUT, 256), 256, 0, s>>>(cb.h, cb.wp, w, y ? y : cb.y, B);

@@ -27,6 +27,11 @@ struct CnnBuffers {
 size_t cnn_buffers(void* ws, int B, bool training, CnnBuffers* cb);
 cudaError_t cnn_prepare(const float* w, const float* x, int B, const CnnBuffers& cb, cudaStream_t s);
 cudaError_t cnn_forward(const float* w, int B, const CnnBuffers& cb, float* y, cudaStream_t s);
+// the inference forward: layers 2-4 as implicit GEMMs on the tensor cores
+// (cnn_tc.cu), channels-last activations; the training forward keeps cnn_forward
+cudaError_t cnn_forward_tc(const float* w, int B, const CnnBuffers& cb, float* y, cudaStream_t s);
+// the two fully connected layers on the conv4 output (cb.a3, NCHW) into y
+cudaError_t cnn_forward_fc(const float* w, int B, const CnnBuffers& cb, float* y, cudaStream_t s);
 cudaError_t cnn_backward(const float* t, int B, float* loss, float* grad, const CnnBuffers& cb,
                          cudaStream_t s);
 cudaError_t cnn_adam(float* w, float* m, float* v, const float* g, int step, float lr,

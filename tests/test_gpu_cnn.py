@@ -65,6 +65,19 @@ def test_forward_matches_oracle(gf):
     assert np.abs(y - yo).max() <= 3e-2 * scale
 
 
+def test_forward_ragged_batch_matches_oracle(gf):
+    # the inference forward's tensor-core layers take 128-row tiles of
+    # (sample, output pixel); 13 samples leave a ragged last tile in every layer
+    # (13 x 64 and 13 x 16 rows) and several full ones before it
+    w, x, _ = network_case(gf, nb=13, seed=21)
+    y = gf.cnn_forward(torch.as_tensor(w, dtype=torch.float32).cuda(),
+                       torch.as_tensor(x, dtype=torch.float32).cuda()).cpu().numpy()
+    yq = oracle.cnn_forward(w, x, bf16_act=True)
+    scale = np.sqrt(np.mean(yq ** 2))
+    assert np.all(np.isfinite(y))
+    assert np.abs(y - yq).max() <= 1e-3 * scale, (np.abs(y - yq).max(), scale)
+
+
 @pytest.mark.parametrize("nb,seed", [(6, 5), (40, 6), (64, 12)])
 def test_gradient_matches_oracle(gf, nb, seed):
     w, x, t = network_case(gf, nb=nb, seed=seed)
