@@ -1148,7 +1148,6 @@ def run_learned(args):
                 "default": dflt_ms / (count * frac_d) if frac_d else None},
             "cnn_forward": {"stamps": count, "ms": cnn_ms, "stamps_per_s": count / (cnn_ms / 1e3),
                             "tflops_all_layers": 2 * mac_all * count / (cnn_ms / 1e3) / 1e12,
-                            "tflops_tensor_layers_share_of_time": None,
                             "bf16_peak_sustained_tflops": peaks.get("bf16_tflops_sustained"),
                             "note": "conv layers 2-4 (%.0f%% of the multiply-adds) on tcgen05; "
                                     "the whole forward timed, so the rate is a lower bound for "

@@ -48,8 +48,6 @@ cudaError_t ensure_smem_optin(const void* func, int bytes, int* cache)
     return e;
 }
 
-size_t conv_direct_smem(int P);
-
 // ------------------------------------------------------------ profiling
 // Off unless gf_prof_enable() received a device counter array.  When on, each
 // kernel class launch is bracketed by CUDA events on its stream, and the
@@ -471,6 +469,7 @@ struct Layout {
     int conv_ty, conv_cap;  // direct convolution: tile height, persistent CTAs per SM
     int eval_variant;  // the model kernels' evaluator: 0 Sersic / disk / Gaussian,
                        // 1 with Moffat, 2 with King, Nuker or point sources
+    int os_ns;         // sub-samples per oversampled pixel (os_factor^2; 1 without a block)
 };
 
 struct Plan {
@@ -537,6 +536,7 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     L.count = count;
     L.nchan = S.nchan;
     L.eval_variant = 0;
+    L.os_ns = (d->os_factor > 1 && d->os_box > 0) ? d->os_factor * d->os_factor : 1;
     for (int k = 0; k < S.ncomp; ++k) {
         const int kd = S.kinds[k];
         if (kd == GF_MOFFAT) L.eval_variant = std::max(L.eval_variant, 1);
@@ -717,6 +717,7 @@ PassArgs base_args(void* ws, const Layout& L, const float* psf, const float* img
     a.phase = PH_NONE;
     a.work = prof::work_dev;
     a.eval_variant = L.eval_variant;
+    a.os_ns = L.os_ns;
     a.conv_ty = L.conv_ty;
     return a;
 }
@@ -2053,7 +2054,7 @@ gf_status check_cnn_batch(int batch)
 
 // a guess call's tables in its workspace: H, W (int), offsets (int64), lo, hi
 struct GuessLayout {
-    size_t H, W, off, lo, hi, total;
+    size_t H, W, off, lo, hi, e2, total;
 };
 
 GuessLayout guess_layout(int count)
@@ -2070,6 +2071,7 @@ GuessLayout guess_layout(int count)
     g.off = take(sizeof(long long) * (size_t)count);
     g.lo = take(sizeof(double) * kGuessSlots);
     g.hi = take(sizeof(double) * kGuessSlots);
+    g.e2 = take(sizeof(double));  // the Sersic flux factor at n = 2
     g.total = o;
     return g;
 }
@@ -2128,7 +2130,7 @@ gf_status gf_cnn_loss_grad(const float* w, const float* x, const float* t, int b
     cnn_buffers(ws, batch, true, &cb);
     cudaStream_t s = (cudaStream_t)stream;
     GF_CUDA(cnn_prepare(w, x, batch, cb, s));
-    GF_CUDA(cnn_forward(w, batch, cb, nullptr, s));
+    GF_CUDA(cnn_forward_tc(w, batch, cb, nullptr, s));
     GF_CUDA(cnn_backward(t, batch, loss, grad, cb, s));
     return GF_OK;
 }
@@ -2230,7 +2232,7 @@ gf_status gf_default_guess(const gf_batch* b, const float* img, double* params, 
     memcpy(blob.data() + g.off, off.data(), sizeof(long long) * count);
     if ((r = upload(ws, blob, s)) != GF_OK) return r;
     GF_CUDA(default_guess(count, at<int>(ws, g.H), at<int>(ws, g.W), at<long long>(ws, g.off), img,
-                          params, kGuessSlots, smem, max_npx, s));
+                          params, kGuessSlots, smem, max_npx, at<double>(ws, g.e2), s));
     return GF_OK;
 }
 

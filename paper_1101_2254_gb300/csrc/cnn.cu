@@ -11,9 +11,14 @@
 // parameters are float32, packed layer by layer as weights [out][in][ky][kx]
 // (fc: [out][in]) then biases [out] -- 195432 in all.  Two bf16 copies of the
 // convolution weights are kept: [in][tap][out] for the forward pass (eight
-// consecutive output channels per 16-byte load) and [out][tap][in] for the
-// input gradient (eight consecutive input channels).  Every reduction runs in a
-// fixed order, so a training run is reproducible bit for bit.
+// consecutive output channels per 16-byte load; the first layer's SIMT loop and
+// the tensor-core input gradients read it) and [out][tap][in] (the tensor-core
+// forward's B operand).  The convolution layers' activations and gradients are
+// channels-last except conv4's output, which is stored in the [c][y][x] order
+// fc1 flattens.  Convolutions 2-4 run on the tensor cores in both directions
+// (cnn_tc.cu, cnn_bwd_tc.cu); this file holds the first convolution, the fully
+// connected layers, the loss and Adam.  Every reduction runs in a fixed order,
+// so a training run is reproducible bit for bit.
 #include <math.h>
 #include <stdint.h>
 
@@ -56,44 +61,6 @@ __device__ __forceinline__ void unpack8(const uint4 u, float* f)
 inline int blocks(long long n, int t) { return (int)((n + t - 1) / t); }
 
 // ---------------------------------------------------------------- forward
-// thread = (sample b, group of 8 output channels, output pixel)
-__global__ void k_conv_fwd(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ wt,
-                           const float* __restrict__ bias, __nv_bfloat16* __restrict__ y, int B,
-                           int cin, int hin, int cout, int hout)
-{
-    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int ncg = cout / 8, npix = hout * hout;
-    if (item >= (long long)B * ncg * npix) return;
-    const int pix = (int)(item % npix);
-    const long long r = item / npix;
-    const int cg = (int)(r % ncg), b = (int)(r / ncg);
-    const int oy = pix / hout, ox = pix - oy * hout;
-    float acc[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = bias[cg * 8 + j];
-    const __nv_bfloat16* xb = x + (long long)b * cin * hin * hin;
-    for (int ci = 0; ci < cin; ++ci)
-#pragma unroll
-        for (int ky = 0; ky < 3; ++ky) {
-            const int iy = 2 * oy - 1 + ky;
-            if (iy < 0 || iy >= hin) continue;
-#pragma unroll
-            for (int kx = 0; kx < 3; ++kx) {
-                const int ix = 2 * ox - 1 + kx;
-                if (ix < 0 || ix >= hin) continue;
-                const float v = __bfloat162float(xb[(ci * hin + iy) * hin + ix]);
-                float w[8];
-                unpack8(*reinterpret_cast<const uint4*>(wt + (ci * 9 + ky * 3 + kx) * cout + cg * 8), w);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[j] = fmaf(w[j], v, acc[j]);
-            }
-        }
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-        y[(((long long)b * cout + cg * 8 + j) * hout + oy) * hout + ox] =
-            __float2bfloat16_rn(fmaxf(acc[j], 0.0f));
-}
-
 // fc1: thread = (b, o); input the flattened conv4 output (bf16), output float32 after ReLU
 __global__ void k_fc1_fwd(const __nv_bfloat16* __restrict__ a3, const __nv_bfloat16* __restrict__ w,
                           const float* __restrict__ master, float* __restrict__ h, int B)
@@ -199,7 +166,9 @@ __global__ void k_fc1_bwd_w(const float* __restrict__ gh, const __nv_bfloat16* _
     }
 }
 
-// gradient at conv4's pre-activation (through its ReLU)
+// gradient at conv4's pre-activation (through its ReLU), written channels-last
+// (b, pixel, channel) for the tensor-core backward; the flattened input index i
+// of fc1 is channel * 16 + pixel (conv4's NCHW output)
 __global__ void k_fc1_bwd_x(const float* __restrict__ gh, const __nv_bfloat16* __restrict__ a3,
                             const __nv_bfloat16* __restrict__ w, float* __restrict__ g3, int B)
 {
@@ -208,59 +177,15 @@ __global__ void k_fc1_bwd_x(const float* __restrict__ gh, const __nv_bfloat16* _
     const int b = (int)(item / 2048), i = (int)(item - (long long)b * 2048);
     float s = 0.0f;
     for (int o = 0; o < 32; ++o) s = fmaf(__bfloat162float(w[FC1_W + o * 2048 + i]), gh[b * 32 + o], s);
-    g3[item] = __bfloat162float(a3[item]) > 0.0f ? s : 0.0f;
+    const int c = i >> 4, pix = i & 15;
+    g3[(long long)b * 2048 + pix * 128 + c] = __bfloat162float(a3[item]) > 0.0f ? s : 0.0f;
 }
 
-// Conv input gradient, through the ReLU of the layer below (whose output is
-// this layer's input): thread = (b, group of 8 input channels, input pixel).
-// With stride 2 and padding 1, input row iy feeds output row (iy + 1 - ky) / 2
-// when that is a whole number in range.
-__global__ void k_conv_bwd_x(const float* __restrict__ gout, const __nv_bfloat16* __restrict__ xin,
-                             const __nv_bfloat16* __restrict__ wb, float* __restrict__ gin, int B,
-                             int cin, int hin, int cout, int hout)
-{
-    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int ncg = cin / 8, npix = hin * hin;
-    if (item >= (long long)B * ncg * npix) return;
-    const int pix = (int)(item % npix);
-    const long long r = item / npix;
-    const int cg = (int)(r % ncg), b = (int)(r / ncg);
-    const int iy = pix / hin, ix = pix - iy * hin;
-    float acc[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
-    const float* gb = gout + (long long)b * cout * hout * hout;
-#pragma unroll
-    for (int ky = 0; ky < 3; ++ky) {
-        const int ty = iy + 1 - ky;
-        if (ty < 0 || (ty & 1)) continue;
-        const int oy = ty >> 1;
-        if (oy >= hout) continue;
-#pragma unroll
-        for (int kx = 0; kx < 3; ++kx) {
-            const int tx = ix + 1 - kx;
-            if (tx < 0 || (tx & 1)) continue;
-            const int ox = tx >> 1;
-            if (ox >= hout) continue;
-            for (int co = 0; co < cout; ++co) {
-                const float g = gb[(co * hout + oy) * hout + ox];
-                float w[8];
-                unpack8(*reinterpret_cast<const uint4*>(wb + (co * 9 + ky * 3 + kx) * cin + cg * 8), w);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[j] = fmaf(w[j], g, acc[j]);
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const long long o = (((long long)b * cin + cg * 8 + j) * hin + iy) * hin + ix;
-        gin[o] = __bfloat162float(xin[o]) > 0.0f ? acc[j] : 0.0f;
-    }
-}
-
-// Conv weight gradients, first stage: block = (output channel co, input
-// channel ci, chunk of the batch); threads stride over (b, oy, ox) keeping the
-// nine tap sums (and the bias sum); a fixed tree merges the threads.
+// Weight gradients of the first convolution (one input channel, nine taps per
+// output channel: too narrow for the tensor cores), first stage: block =
+// (output channel co, input channel ci, chunk of the batch); threads stride over
+// (b, oy, ox) keeping the nine tap sums (and the bias sum); a fixed tree merges
+// the threads.  gout is channels-last (b, oy, ox, co).
 constexpr int WG_THREADS = 256;
 
 __global__ void __launch_bounds__(WG_THREADS) k_conv_bwd_w(const float* __restrict__ gout,
@@ -281,7 +206,7 @@ __global__ void __launch_bounds__(WG_THREADS) k_conv_bwd_w(const float* __restri
     for (long long it = i0 + threadIdx.x; it < i1; it += WG_THREADS) {
         const int b = (int)(it / npix), pix = (int)(it - (long long)b * npix);
         const int oy = pix / hout, ox = pix - oy * hout;
-        const float g = gout[(((long long)b * cout + co) * hout + oy) * hout + ox];
+        const float g = gout[((long long)b * npix + pix) * cout + co];
         if (g == 0.0f) continue;
         s[9] += g;
         const __nv_bfloat16* xb = xin + ((long long)b * cin + ci) * hin * hin;
@@ -479,13 +404,28 @@ __device__ double bn_of(double n)
     return b;
 }
 
-// closed-form total flux of an elliptical Sersic component:
-// 2 pi q I_e r_e^2 n e^{b} Gamma(2n) / b^{2n}
-__device__ double sersic_flux(double ie, double re, double n, double q)
+// the n-dependent factor e^{b} Gamma(2n) / b^{2n} of the closed-form flux
+__device__ double sersic_flux_factor(double n)
 {
     const double b = bn_of(n);
-    return 2.0 * M_PI * q * ie * re * re * n * exp(b + lgamma(2.0 * n) - 2.0 * n * log(b));
+    return exp(b + lgamma(2.0 * n) - 2.0 * n * log(b));
 }
+
+// closed-form total flux of an elliptical Sersic component:
+// 2 pi q I_e r_e^2 n e^{b} Gamma(2n) / b^{2n}, given its n-dependent factor e
+__device__ double sersic_flux_e(double ie, double re, double n, double q, double e)
+{
+    return 2.0 * M_PI * q * ie * re * re * n * e;
+}
+
+__device__ double sersic_flux(double ie, double re, double n, double q)
+{
+    return sersic_flux_e(ie, re, n, q, sersic_flux_factor(n));
+}
+
+// the factor at n = 2 (the default guess's index), formed once per call by one
+// thread instead of once per stamp (the b_n solve is a long serial FP64 chain)
+__global__ void k_flux_factor_n2(double* __restrict__ e2) { *e2 = sersic_flux_factor(2.0); }
 
 // ------------------------------------------------ network input scaling
 template <class T>
@@ -687,7 +627,8 @@ __global__ void __launch_bounds__(DG_THREADS) k_default_guess(const int* __restr
                                                                const long long* __restrict__ off,
                                                                const float* __restrict__ img,
                                                                double* __restrict__ out, int nslots,
-                                                               int ring_cap, int cache_cap)
+                                                               int ring_cap, int cache_cap,
+                                                               const double* __restrict__ e2)
 {
     // dynamic shared memory: the ring (ring_cap doubles, a power of two >= the
     // longest ring) then, for stamps of at most cache_cap pixels, each pixel's
@@ -813,7 +754,7 @@ __global__ void __launch_bounds__(DG_THREADS) k_default_guess(const int* __restr
         double* p = out + (long long)b * nslots;
         p[0] = x0;
         p[1] = y0;
-        p[2] = F / sersic_flux(1.0, re, 2.0, q);
+        p[2] = F / sersic_flux_e(1.0, re, 2.0, q, *e2);
         p[3] = re;
         p[4] = 2.0;
         p[5] = q;
@@ -854,12 +795,13 @@ size_t cnn_buffers(void* ws, int B, bool training, CnnBuffers* cb)
         o += (bytes + 255) & ~(size_t)255;
         return at;
     };
-    size_t part = 0;
-    for (int l = 0; l < 4; ++l) {
-        const ConvL L = CONV[l];
+    // weight-gradient partials: the first layer's SIMT chunks or layers 2-4's
+    // tensor-core chunks, whichever need more
+    size_t part = cnn_bwd_tc_part_floats(B);
+    {
+        const ConvL L = CONV[0];
         const long long total = (long long)B * L.hout * L.hout;
-        const long long nchunk =
-            std::min<long long>(std::max<long long>(1, 2048 / (L.cout * L.cin)), total);
+        const long long nchunk = std::min<long long>(std::max<long long>(1, 2048 / (L.cout * L.cin)), total);
         part = std::max(part, (size_t)(nchunk * L.cout * L.cin * 10));
     }
     // the gradient buffers exist only when the call trains
@@ -891,6 +833,7 @@ size_t cnn_buffers(void* ws, int B, bool training, CnnBuffers* cb)
         cb->g1 = (float*)(p + g1);
         cb->g0 = (float*)(p + g0);
         cb->part = (float*)(p + pt);
+        cb->part_floats = T * part;
     }
     return o;
 }
@@ -902,21 +845,6 @@ cudaError_t cnn_prepare(const float* w, const float* x, int B, const CnnBuffers&
     k_to_bf16<<<blocks((long long)B * NPIX, 256), 256, 0, s>>>(x, cb.x, (long long)B * NPIX);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
-}
-
-cudaError_t cnn_forward(const float* w, int B, const CnnBuffers& cb, float* y, cudaStream_t s)
-{
-    const __nv_bfloat16* in = cb.x;
-    __nv_bfloat16* outs[4] = {cb.a0, cb.a1, cb.a2, cb.a3};
-    for (int l = 0; l < 4; ++l) {
-        const ConvL L = CONV[l];
-        const long long n = (long long)B * (L.cout / 8) * L.hout * L.hout;
-        k_conv_fwd<<<blocks(n, 256), 256, 0, s>>>(in, cb.wf + L.woff, w + L.boff, outs[l], B, L.cin,
-                                                  L.hin, L.cout, L.hout);
-        GF_COUNT_LAUNCH();
-        in = outs[l];
-    }
-    return cnn_forward_fc(w, B, cb, y, s);
 }
 
 cudaError_t cnn_forward_fc(const float* w, int B, const CnnBuffers& cb, float* y, cudaStream_t s)
@@ -941,28 +869,21 @@ cudaError_t cnn_backward(const float* t, int B, float* loss, float* grad, const 
     GF_COUNT_LAUNCH();
     k_fc1_bwd_x<<<blocks((long long)B * 2048, 256), 256, 0, s>>>(cb.gh, cb.a3, cb.wp, cb.g3, B);
     GF_COUNT_LAUNCH();
-    // conv layers in reverse; gout[l] = gradient at layer l's pre-activation
+    // layers 4-2 on the tensor cores (weight gradients and the channels-last
+    // gradients at the pre-activations of layers 3-1), then layer 1's weights
     float* gout[4] = {cb.g0, cb.g1, cb.g2, cb.g3};
     const __nv_bfloat16* ins[4] = {cb.x, cb.a0, cb.a1, cb.a2};
-    for (int l = 3; l >= 0; --l) {
-        const ConvL L = CONV[l];
-        const long long total = (long long)B * L.hout * L.hout;
-        const int nchunk =
-            (int)std::min<long long>(std::max<long long>(1, 2048 / (L.cout * L.cin)), total);
-        k_conv_bwd_w<<<dim3(L.cout * L.cin, nchunk), WG_THREADS, 0, s>>>(gout[l], ins[l], cb.part, B,
-                                                                         L.cin, L.hin, L.cout,
-                                                                         L.hout, nchunk);
-        GF_COUNT_LAUNCH();
-        k_conv_bwd_w_sum<<<blocks((long long)L.cout * L.cin * 10, 256), 256, 0, s>>>(
-            cb.part, grad, L.cin, L.cout, nchunk, L.woff, L.boff);
-        GF_COUNT_LAUNCH();
-        if (l > 0) {
-            const long long n = (long long)B * (L.cin / 8) * L.hin * L.hin;
-            k_conv_bwd_x<<<blocks(n, 256), 256, 0, s>>>(gout[l], ins[l], cb.wb + L.woff, gout[l - 1], B,
-                                                        L.cin, L.hin, L.cout, L.hout);
-            GF_COUNT_LAUNCH();
-        }
-    }
+    cudaError_t e = cnn_backward_tc(B, grad, gout, ins, cb.wf, cb.part, cb.part_floats, s);
+    if (e != cudaSuccess) return e;
+    const ConvL L = CONV[0];
+    const long long total = (long long)B * L.hout * L.hout;
+    const int nchunk = (int)std::min<long long>(std::max<long long>(1, 2048 / (L.cout * L.cin)), total);
+    k_conv_bwd_w<<<dim3(L.cout * L.cin, nchunk), WG_THREADS, 0, s>>>(cb.g0, cb.x, cb.part, B, L.cin, L.hin,
+                                                                     L.cout, L.hout, nchunk);
+    GF_COUNT_LAUNCH();
+    k_conv_bwd_w_sum<<<blocks((long long)L.cout * L.cin * 10, 256), 256, 0, s>>>(cb.part, grad, L.cin, L.cout,
+                                                                                nchunk, L.woff, L.boff);
+    GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
@@ -1042,7 +963,7 @@ constexpr int DG_CACHE_MAX = 6144;
 
 cudaError_t default_guess(int count, const int* H, const int* W, const long long* off,
                           const float* img, double* out, int nslots, size_t smem, int max_npx,
-                          cudaStream_t s)
+                          double* e2, cudaStream_t s)
 {
     static int optin[64];
     const int ring_cap = (int)(smem / sizeof(double));
@@ -1050,8 +971,10 @@ cudaError_t default_guess(int count, const int* H, const int* W, const long long
     const size_t bytes = smem + 2 * sizeof(double) * (size_t)cache_cap;
     cudaError_t e = ensure_smem_optin((const void*)k_default_guess, (int)bytes, optin);
     if (e != cudaSuccess) return e;
+    k_flux_factor_n2<<<1, 1, 0, s>>>(e2);
+    GF_COUNT_LAUNCH();
     k_default_guess<<<count, DG_THREADS, bytes, s>>>(H, W, off, img, out, nslots, ring_cap,
-                                                     cache_cap);
+                                                     cache_cap, e2);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }

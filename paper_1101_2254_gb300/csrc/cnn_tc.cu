@@ -1,7 +1,8 @@
-// cnn_tc.cu -- the network's inference forward pass with its 3x3 stride-2
+// cnn_tc.cu -- the network's forward pass with its 3x3 stride-2
 // convolutions 2-4 as implicit GEMMs on the tensor cores (tcgen05).
 //
-// A convolution layer is the contraction
+// The forward of both inference and training.  A convolution layer is the
+// contraction
 //   y[m][n] = relu(bias[n] + sum_k A[m][k] B[n][k]),
 // over m = (sample, output pixel) (M = batch x hout^2 rows), n = output channel
 // (N = 64 or 128) and k = tap * cin + input channel (K = 9 cin = 288 or 576).
@@ -20,9 +21,8 @@
 // connected layer reads).  Layer 1 (one input channel: K = 9) stays a SIMT loop.
 //
 // Arithmetic is the network's specified one: bf16 weights and activations,
-// float32 accumulation; the summation order inside the MMA differs from the
-// SIMT loops' (the outputs agree up to float32 rounding before the bf16 step).
-// Training keeps the SIMT forward, whose NCHW activations its backward reads.
+// float32 accumulation, in the tensor cores' summation order.  The training
+// backward (cnn_bwd_tc.cu) reads the channels-last activations this writes.
 #include <math.h>
 #include <stdint.h>
 
@@ -85,23 +85,36 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(ConvTC a)
         const long long m0 = tile * CT_TM;
         for (int c = 0; c < nchunk && !failed; ++c) {
             const int kc0 = c * CT_KC;
-            // gather the A chunk: (row, 8 consecutive k of one tap) per item
+            // gather the A chunk: (row, 8 consecutive k of one tap) per item.  A
+            // warp takes 8 rows x 4 consecutive 8-k groups: the 8 lanes of each
+            // 16-byte store phase write 8 different rows of one core matrix
+            // (distinct banks), and each row's 4 groups are 64 contiguous bytes
+            // of the input.
+            static_assert(CT_KC % 32 == 0 && CT_THREADS % 32 == 0, "lane mapping");
             for (int i = tid; i < CT_TM * (CT_KC / 8); i += CT_THREADS) {
-                const int row = i / (CT_KC / 8), k8 = (i - row * (CT_KC / 8)) * 8;
+                const int lane_i = i & 31, rest = i >> 5;
+                const int kq = rest % (CT_KC / 32), rg = rest / (CT_KC / 32);
+                const int row = rg * 8 + (lane_i & 7), k8 = (kq * 4 + (lane_i >> 3)) * 8;
                 const int k = kc0 + k8;
                 const long long m = m0 + row;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                const __nv_bfloat16* src = a.x;  // (not read when the copy is a zero fill)
+                bool in = false;
                 if (m < M) {
                     const int b = (int)(m / hw), pix = (int)(m - (long long)b * hw);
                     const int oy = pix / a.hout, ox = pix - oy * a.hout;
                     const int tap = k / a.cin, ci = k - tap * a.cin;
                     const int iy = 2 * oy - 1 + tap / 3, ix = 2 * ox - 1 + tap % 3;
-                    if (iy >= 0 && iy < a.hin && ix >= 0 && ix < a.hin)
-                        v = *reinterpret_cast<const uint4*>(
-                            a.x + (((long long)b * a.hin + iy) * a.hin + ix) * a.cin + ci);
+                    in = iy >= 0 && iy < a.hin && ix >= 0 && ix < a.hin;
+                    if (in) src = a.x + (((long long)b * a.hin + iy) * a.hin + ix) * a.cin + ci;
                 }
-                *reinterpret_cast<uint4*>(As + cofs(row, k8, CT_KC)) = v;
+                // 16 bytes by cp.async (zeros outside the input): every item of the
+                // chunk is in flight at once
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(
+                                 smem_addr(As + cofs(row, k8, CT_KC))),
+                             "l"(src), "r"(in ? 16 : 0)
+                             : "memory");
             }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;");
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
@@ -173,7 +186,7 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(ConvTC a)
 }
 
 // layer 1 (one input channel), channels-last output: thread = (sample, 8
-// output channels, output pixel), the taps in the SIMT forward's order
+// output channels, output pixel), the taps in (ky, kx) order
 __global__ void k_conv1_nhwc(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ wt,
                              const float* __restrict__ bias, __nv_bfloat16* __restrict__ y, int B,
                              int hin, int cout, int hout)

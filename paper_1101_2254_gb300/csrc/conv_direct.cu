@@ -9,12 +9,16 @@
 // call; TX/32 x TY/16 warps.  Both, and the persistent grid, come from the
 // device's tuning table (gf_autotune) or its defaults (TY 32, 8 CTAs per SM).  The
 // flipped PSF (rows padded with zeros to P4, a multiple of 4 taps) and the
-// (32+P-1) x SW halo tile of the channel grid are staged in shared memory.
+// (TY+P-1) x SW halo tile of the channel grid are staged in shared memory; for
+// PSFs up to 35 pixels the tile is double-buffered and filled by cp.async, so a
+// CTA's next tile arrives while its current one is summed.
 // A warp covers 16 x 32 outputs: lane 8 cg + rl owns the 8 contiguous columns
 // 8 cg .. 8 cg + 7 of rows rl and rl + 8.  For each tap row and group of 4
 // taps a thread holds, per row, a sliding window of 12 grid values (one new
 // 16-byte load per group) and the 4 taps (one broadcast 16-byte load), and
-// issues 2 x 8 x 4 = 64 FMAs: 3 shared loads per 64 FMAs.  In the kernels
+// issues 2 x 8 x 4 = 64 FMAs: 3 shared loads per 64 FMAs.  (Packing the two
+// rows' FMAs into __ffma2_rn pairs was measured slower: forming the register
+// pairs cost more ALU instructions than the pairing saved.)  In the kernels
 // specialised on the padded tap count, the last group of a tap row issues only
 // the FMAs of its real taps (P - P4 + 4 of them): for P = 33 that is 33 FMAs
 // per output and tap row instead of 36.
@@ -123,11 +127,125 @@ __device__ __forceinline__ void tap_row(float (&acc)[RPT][8], const float* kr, c
     }
 }
 
+// One work item's addresses and extent: the channel grid E (He x We) it reads,
+// the convolved channel Y (H x W) it writes, its PSF, and the tile's origin.
+struct ConvItem {
+    const float* E;
+    float* Y;
+    const float* psf;
+    int b, He, We, H, W, ty0, tx0;
+};
+
+template <int TX, int TY>
+__device__ __forceinline__ ConvItem conv_item(const PassArgs& a, const int* pre, int n, int tot,
+                                              long long it, int& hint)
+{
+    const int ch = (int)(it / tot), blk = (int)(it - (long long)ch * tot);
+    const int li = wl_locate(pre, n, blk, hint);
+    ConvItem q;
+    q.b = a.wl.ids[li];
+    const StampInfo& st = a.st[q.b];
+    q.He = st.He;
+    q.We = st.We;
+    q.H = st.H;
+    q.W = st.W;
+    const int tiles_x = (st.W + TX - 1) / TX;
+    const int t = blk - pre[li];
+    q.ty0 = (t / tiles_x) * TY;
+    q.tx0 = (t % tiles_x) * TX;
+    q.E = a.ext + ext_index(st, a.nchan, ch);
+    q.Y = a.y + y_index(st, a.nchan, ch);
+    q.psf = a.psf + st.psf_off;
+    return q;
+}
+
+// asynchronous global -> shared copies (cp.async); a copy whose `in` is false
+// reads nothing and writes zeros
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool in)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(in ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool in)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(in ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The SH x SW halo tile of item q into es by cp.async, a warp per row: 16-byte
+// copies where the grid's rows are 16-byte aligned (We a multiple of 4, so a
+// chunk lies wholly inside or wholly outside the grid), else 4-byte ones.
+// Outside the grid the tile holds zeros, as the synchronous staging writes.
+template <int NT>
+__device__ __forceinline__ void stage_tile_async(float* es, const ConvItem& q, int SH, int SW)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool vec = (q.We & 3) == 0 && (reinterpret_cast<uintptr_t>(q.E) & 15) == 0;
+    for (int r = warp; r < SH; r += NT / 32) {
+        const int gy = q.ty0 + r;
+        const bool row_in = gy < q.He;
+        const float* Er = q.E + (long long)(row_in ? gy : 0) * q.We;
+        float* er = es + r * SW;
+        if (vec) {
+            for (int c4 = lane; c4 < (SW >> 2); c4 += 32) {
+                const int gx = q.tx0 + 4 * c4;
+                const bool in = row_in && gx < q.We;
+                cp_async16(er + 4 * c4, in ? Er + gx : q.E, in);
+            }
+        } else {
+            for (int col = lane; col < SW; col += 32) {
+                const int gx = q.tx0 + col;
+                const bool in = row_in && gx < q.We;
+                cp_async4(er + col, in ? Er + gx : q.E, in);
+            }
+        }
+    }
+}
+
+// The same tile by plain loads, four per lane in flight.
+template <int NT>
+__device__ __forceinline__ void stage_tile_sync(float* es, const ConvItem& q, int SH, int SW)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < SH; r += NT / 32) {
+        const int gy = q.ty0 + r;
+        const bool row_in = gy < q.He;
+        const float* Er = q.E + (long long)gy * q.We;
+        float* er = es + r * SW;
+        for (int c0_ = lane; c0_ < SW; c0_ += 128) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int col = c0_ + 32 * u, gx = q.tx0 + col;
+                v[u] = (row_in && col < SW && gx < q.We) ? __ldg(&Er[gx]) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c0_ + 32 * u < SW) er[c0_ + 32 * u] = v[u];
+        }
+    }
+}
+
 // Work item = (channel, output tile of a listed stamp of this tile width).
+// With DB (the kernels specialised on the tap count, P <= 35) the halo tile is
+// double-buffered: the cp.async copies of item it + 1 are in flight while item
+// it's taps run, so the FMA pipe does not wait on global memory between items.
+// The generic kernel (larger PSFs, whose two tiles would not fit in shared
+// memory) stages each tile synchronously.  The sums are the same either way.
 template <int TX, int TY, int P4K>
 __global__ void __launch_bounds__(TX * TY / 16) k_conv_direct(PassArgs a)
 {
     pdl_entry();
+    constexpr bool DB = P4K > 0;
     constexpr int NT = TX * TY / 16, WX = TX / 32;  // threads, warps across
     extern __shared__ __align__(16) float smem[];
     const int n = *a.wl.n;
@@ -136,8 +254,9 @@ __global__ void __launch_bounds__(TX * TY / 16) k_conv_direct(PassArgs a)
     const long long items = (long long)tot * a.nchan;
     const int P = a.P, P4 = (P + 3) & ~3;
     const int SW = conv_sw(TX, P4), SH = TY + P - 1;
-    float* ks = smem;               // P x P4 flipped taps
-    float* es = smem + P * P4;      // SH x SW grid tile (P*P4 is a multiple of 4)
+    float* ks = smem;                         // P x P4 flipped taps
+    float* const es0 = smem + P * P4;         // SH x SW grid tile(s) (P*P4, SW multiples of 4)
+    float* const es1 = es0 + (DB ? SH * SW : 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rl = lane & 7, cg = lane >> 3;
     const int wr0 = (warp / WX) * 16, wc0 = (warp % WX) * 32;
@@ -146,47 +265,38 @@ __global__ void __launch_bounds__(TX * TY / 16) k_conv_direct(PassArgs a)
     int hint = -1, psf_b = -1;
     const long long chunk = (items + gridDim.x - 1) / gridDim.x;
     const long long it0 = (long long)blockIdx.x * chunk, it1 = min(items, it0 + chunk);
+    if (it0 >= it1) return;
+    ConvItem q = conv_item<TX, TY>(a, pre, n, tot, it0, hint);
+    if (DB) {
+        stage_tile_async<NT>(es0, q, SH, SW);
+        cp_async_commit();
+    }
+    int cb = 0;  // the buffer holding item it's tile
     for (long long it = it0; it < it1; ++it) {
-        const int ch = (int)(it / tot), blk = (int)(it - (long long)ch * tot);
-        const int li = wl_locate(pre, n, blk, hint);
-        const int b = a.wl.ids[li];
-        const StampInfo st = a.st[b];
-        const int tiles_x = (st.W + TX - 1) / TX;
-        const int t = blk - pre[li];
-        const int ty0 = (t / tiles_x) * TY, tx0 = (t % tiles_x) * TX;
-        __syncthreads();  // the previous item is done with the shared tiles
-        if (b != psf_b) {
-            const float* psf = a.psf + st.psf_off;
+        __syncthreads();  // the previous item is done with the taps and both tiles
+        // item it + 1 (its tile's copies issued now where the tile is double-buffered)
+        ConvItem qn = q;
+        if (it + 1 < it1) qn = conv_item<TX, TY>(a, pre, n, tot, it + 1, hint);
+        if (DB) {
+            if (it + 1 < it1) stage_tile_async<NT>(cb ? es0 : es1, qn, SH, SW);
+            cp_async_commit();  // (an empty group on the last item)
+        }
+        if (q.b != psf_b) {
             for (int idx = threadIdx.x; idx < P * P4; idx += NT) {
                 const int v = idx / P4, u = idx - v * P4;
-                ks[idx] = (u < P) ? __ldg(&psf[(P - 1 - v) * P + (P - 1 - u)]) : 0.0f;
+                ks[idx] = (u < P) ? __ldg(&q.psf[(P - 1 - v) * P + (P - 1 - u)]) : 0.0f;
             }
-            psf_b = b;
+            psf_b = q.b;
         }
-        // the halo tile, a warp per row (coalesced, no index division), four
-        // loads per lane in flight
-        const float* E = a.ext + ext_index(st, a.nchan, ch);
-        for (int r = warp; r < SH; r += NT / 32) {
-            const int gy = ty0 + r;
-            const bool row_in = gy < st.He;
-            const float* Er = E + (long long)gy * st.We;
-            float* er = es + r * SW;
-            for (int c0_ = lane; c0_ < SW; c0_ += 128) {
-                float v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int col = c0_ + 32 * u, gx = tx0 + col;
-                    v[u] = (row_in && col < SW && gx < st.We) ? __ldg(&Er[gx]) : 0.0f;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (c0_ + 32 * u < SW) er[c0_ + 32 * u] = v[u];
-            }
-        }
+        float* es = cb ? es1 : es0;
+        if (DB)
+            cp_async_wait<1>();  // every group but the newest (item it + 1's) is complete
+        else
+            stage_tile_sync<NT>(es, q, SH, SW);
         __syncthreads();
 
         // the warp's block meets the stamp
-        const bool active = ty0 + wr0 < st.H && tx0 + wc0 < st.W;
+        const bool active = q.ty0 + wr0 < q.H && q.tx0 + wc0 < q.W;
         float acc[RPT][8];
 #pragma unroll
         for (int i = 0; i < RPT; ++i)
@@ -197,8 +307,8 @@ __global__ void __launch_bounds__(TX * TY / 16) k_conv_direct(PassArgs a)
                 tap_row<P4K>(acc, ks + v * P4, es + (r0 + v) * SW + c0, SW, P4, P - (P4 - 4));
 
         if (active && a.work && lane == 0) {
-            const unsigned long long rows = (unsigned long long)min(16, st.H - ty0 - wr0);
-            const unsigned long long cols = (unsigned long long)min(32, st.W - tx0 - wc0);
+            const unsigned long long rows = (unsigned long long)min(16, q.H - q.ty0 - wr0);
+            const unsigned long long cols = (unsigned long long)min(32, q.W - q.tx0 - wc0);
             atomicAdd(&a.work[PROF_CONV], 2ull * (unsigned long long)P * P * rows * cols);
         }
         // the tile through shared memory (row stride TX + 1), then coalesced rows
@@ -209,33 +319,43 @@ __global__ void __launch_bounds__(TX * TY / 16) k_conv_direct(PassArgs a)
 #pragma unroll
             for (int o = 0; o < 8; ++o) es[(r0 + 8 * i) * OS + c0 + o] = acc[i][o];
         __syncthreads();
-        float* Y = a.y + y_index(st, a.nchan, ch);
-        const int rows = min(TY, st.H - ty0), cols = min(TX, st.W - tx0);
+        const int rows = min(TY, q.H - q.ty0), cols = min(TX, q.W - q.tx0);
         for (int idx = threadIdx.x; idx < TY * TX; idx += NT) {
             const int r = idx / TX, c = idx - r * TX;
-            if (r < rows && c < cols) Y[(long long)(ty0 + r) * st.W + tx0 + c] = es[r * OS + c];
+            if (r < rows && c < cols) q.Y[(long long)(q.ty0 + r) * q.W + q.tx0 + c] = es[r * OS + c];
         }
+        q = qn;
+        cb ^= 1;
     }
+    if (DB) cp_async_wait<0>();
 }
 
 }  // namespace
 
 cudaError_t ensure_smem_optin_conv_direct(int P, int* cache);
 
-template <int TX, int TY>
+// shared memory of k_conv_direct<TX, TY, P4K> for a P x P PSF: the taps and one
+// halo tile, or two where the kernel double-buffers (P4K > 0)
+template <int TX, int TY, int P4K>
 size_t conv_smem(int P)
 {
     const int P4 = (P + 3) & ~3;
-    return sizeof(float) * ((size_t)P * P4 + (size_t)(TY + P - 1) * conv_sw(TX, P4));
+    return sizeof(float) * ((size_t)P * P4 + (P4K > 0 ? 2 : 1) * (size_t)(TY + P - 1) * conv_sw(TX, P4));
 }
 
-size_t conv_direct_smem(int P) { return conv_smem<64, 32>(P); }
+// one opt-in record per kernel instance and device
+template <int TX, int TY, int P4K>
+int* conv_optin_cache()
+{
+    static int cache[64];
+    return cache;
+}
 
 template <int TX, int TY, int P4K>
 cudaError_t launch_p4(const PassArgs& a, int kind, cudaStream_t s)
 {
     GF_LAUNCH_PDL((k_conv_direct<TX, TY, P4K>), dim3(a.grid[kind]), dim3(TX * TY / 16),
-                  conv_smem<TX, TY>(a.P), s, a);
+                  conv_smem<TX, TY, P4K>(a.P), s, a);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -280,24 +400,38 @@ cudaError_t launch_conv_direct_width(const PassArgs& a, int tile_w, cudaStream_t
     return tile_w == 64 ? launch_tile<64>(a, WK_CONV, s) : launch_tile<32>(a, WK_CONV32, s);
 }
 
-// one cache per device and width for every caller, so that a call made before a
-// stream capture leaves nothing to set inside it
-static int g_conv_optin[4][64];
+// The shared-memory opt-in of the four tile shapes' kernels for a P x P PSF,
+// made before the first launch (and cached per device), so that a call made
+// before a stream capture leaves nothing to set inside it.
+template <int P4K>
+cudaError_t optin_p4(int P)
+{
+    cudaError_t e = ensure_smem_optin((const void*)k_conv_direct<64, 32, P4K>,
+                                      (int)conv_smem<64, 32, P4K>(P), conv_optin_cache<64, 32, P4K>());
+    if (e == cudaSuccess)
+        e = ensure_smem_optin((const void*)k_conv_direct<32, 32, P4K>, (int)conv_smem<32, 32, P4K>(P),
+                              conv_optin_cache<32, 32, P4K>());
+    if (e == cudaSuccess)
+        e = ensure_smem_optin((const void*)k_conv_direct<64, 16, P4K>, (int)conv_smem<64, 16, P4K>(P),
+                              conv_optin_cache<64, 16, P4K>());
+    if (e == cudaSuccess)
+        e = ensure_smem_optin((const void*)k_conv_direct<32, 16, P4K>, (int)conv_smem<32, 16, P4K>(P),
+                              conv_optin_cache<32, 16, P4K>());
+    return e;
+}
 
-// (the specialised kernels serve PSFs up to 35 pixels, whose tiles stay below the
-// default 48 KB of shared memory; only the generic ones need the opt-in)
 cudaError_t ensure_smem_optin_conv_direct(int P, int*)
 {
-    cudaError_t e = ensure_smem_optin((const void*)k_conv_direct<64, 32, 0>,
-                                      (int)conv_smem<64, 32>(P), g_conv_optin[0]);
-    if (e == cudaSuccess)
-        e = ensure_smem_optin((const void*)k_conv_direct<32, 32, 0>, (int)conv_smem<32, 32>(P),
-                              g_conv_optin[1]);
-    if (e == cudaSuccess)
-        e = ensure_smem_optin((const void*)k_conv_direct<64, 16, 0>, (int)conv_smem<64, 16>(P),
-                              g_conv_optin[2]);
-    if (e == cudaSuccess)
-        e = ensure_smem_optin((const void*)k_conv_direct<32, 16, 0>, (int)conv_smem<32, 16>(P),
-                              g_conv_optin[3]);
-    return e;
+    switch ((P + 3) & ~3) {
+    case 4: return optin_p4<4>(P);
+    case 8: return optin_p4<8>(P);
+    case 12: return optin_p4<12>(P);
+    case 16: return optin_p4<16>(P);
+    case 20: return optin_p4<20>(P);
+    case 24: return optin_p4<24>(P);
+    case 28: return optin_p4<28>(P);
+    case 32: return optin_p4<32>(P);
+    case 36: return optin_p4<36>(P);
+    default: return optin_p4<0>(P);
+    }
 }

@@ -542,6 +542,7 @@ struct PassArgs {
                                // of the same components); else independent models
     int jac_analytic;          // the Jacobian pass's nonlinear columns are CH_DERIV channels
     int eval_variant;          // 0 Sersic/disk/Gaussian, 1 with Moffat, 2 with King/Nuker/point
+    int os_ns;                 // sub-samples per oversampled pixel (os_factor^2)
     int conv_ty;               // direct-convolution tile height (32 or 16)
     float* ext;                // channel grids: ext + ext_index(st[b], nchan, k)
     float* y;                  // convolved channels: y + y_index(st[b], nchan, k)

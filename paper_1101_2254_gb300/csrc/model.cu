@@ -304,7 +304,66 @@ __device__ __forceinline__ void body_model_jac_an(const PassArgs& a, int vb, int
 }
 
 // Work item = OS_WARPS pixels of a listed stamp's oversampling block (all
-// channels); lanes take sub-samples, each lane keeps every channel's sum.
+// channels) for blocks of at most 32 sub-samples (os_factor <= 5): one
+// sub-sample per lane, the components at p once, then a runtime loop over the
+// channels, each reduced across the lanes as soon as it is evaluated.  Kept apart
+// from the general body below, whose per-lane accumulators for every channel
+// would otherwise set this one's register count (and occupancy) too.
+template <int EV>
+__device__ __forceinline__ void body_model_os_jac32(const PassArgs& a, int vb, int vg)
+{
+    __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
+    const int n = *a.wl.n;
+    const int* pre = a.wl.pre + WK_OS * (a.count + 1);
+    const int tot = pre[n];
+    const int nch = a.nchan;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int hint = -1, cur_b = -1;
+    const int chunk = (tot + vg - 1) / vg;
+    const int it0 = vb * chunk, it1 = min(tot, it0 + chunk);
+    for (int blk = it0; blk < it1; ++blk) {
+        const int li = wl_locate(pre, n, blk, hint);
+        const int b = a.wl.ids[li];
+        const StampInfo st = a.st[b];
+        if (b != cur_b) {
+            __syncthreads();
+            load_channels(chs, &a.chan[(long long)b * a.chan_stride], nch);
+            __syncthreads();
+            cur_b = b;
+        }
+        const int q = (blk - pre[li]) * OS_WARPS + warp;
+        const int B = st.os_box;
+        if (q >= B * B) continue;
+        const int i = st.os_y0 + q / B, j = st.os_x0 + q % B;
+        const int s = st.os_factor, ns = s * s;
+        const float fs = (float)s;
+        const long long pix = (long long)(i + st.c) * st.We + (j + st.c);
+        const long long cs = (long long)st.He * st.We;
+        float* E = a.ext + ext_index(st, nch, 0) + pix;
+        const bool on = lane < ns;
+        float ox = 0.0f, oy = 0.0f;
+        if (on) {
+            const int ay = lane / s, bx = lane - ay * s;
+            oy = ((float)ay + 0.5f) / fs - 0.5f;
+            ox = ((float)bx + 0.5f) / fs - 0.5f;
+        }
+        float base[GF_MAX_COMP];
+        comp_base<EV>(chs[0], base, (float)j, (float)i, ox, oy);
+        for (int c = 0; c < nch; ++c) {
+            // (the same sums, in the same order, as the general body's)
+            float v = on ? jac_channel<EV>(chs[c], base, (float)j, (float)i, ox, oy) : 0.0f;
+            v += 0.0f;  // an idle lane adds +0, as the general body's accumulator
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) E[c * cs] = v / (float)ns;
+        }
+        if (a.work && lane == 0) atomicAdd(&a.work[PROF_MODEL], 4ull * (unsigned long long)nch);
+    }
+}
+
+// Work item = OS_WARPS pixels of a listed stamp's oversampling block (all
+// channels), any block size: lanes take sub-samples, each lane keeps every
+// channel's sum.
 template <int EV>
 __device__ __forceinline__ void body_model_os_jac(const PassArgs& a, int vb, int vg)
 {
@@ -336,31 +395,6 @@ __device__ __forceinline__ void body_model_os_jac(const PassArgs& a, int vb, int
         const long long pix = (long long)(i + st.c) * st.We + (j + st.c);
         const long long cs = (long long)st.He * st.We;
         float* E = a.ext + ext_index(st, nch, 0) + pix;
-        if (ns <= 32) {
-            // one sub-sample per lane: the components at p once, then a runtime
-            // loop over the channels, each reduced across the lanes as soon as
-            // it is evaluated (the same sums, in the same order, as the
-            // accumulating loop below, with one evaluator in the code instead
-            // of one per unrolled channel)
-            const bool on = lane < ns;
-            float ox = 0.0f, oy = 0.0f;
-            if (on) {
-                const int ay = lane / s, bx = lane - ay * s;
-                oy = ((float)ay + 0.5f) / fs - 0.5f;
-                ox = ((float)bx + 0.5f) / fs - 0.5f;
-            }
-            float base[GF_MAX_COMP];
-            comp_base<EV>(chs[0], base, (float)j, (float)i, ox, oy);
-            for (int c = 0; c < nch; ++c) {
-                float v = on ? jac_channel<EV>(chs[c], base, (float)j, (float)i, ox, oy) : 0.0f;
-                v += 0.0f;  // an idle lane adds +0, as the accumulator it replaces
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) E[c * cs] = v / (float)ns;
-            }
-            if (a.work && lane == 0) atomicAdd(&a.work[PROF_MODEL], 4ull * (unsigned long long)nch);
-            continue;
-        }
         float acc[GF_MAX_CHAN];
 #pragma unroll
         for (int c = 0; c < GF_MAX_CHAN; ++c) acc[c] = 0.0f;
@@ -463,8 +497,10 @@ __device__ __forceinline__ void body_model_os_jac_an(const PassArgs& a, int vb, 
 // oversampled blocks (the heavy items, scheduled first), the others the plain
 // grid pixels, so that the two kinds of work overlap instead of running as two
 // dependent launches.  PIX: 0 one channel per item, 1 every channel of a
-// Jacobian pass per pixel, 2 the same with analytic derivative channels.  OS: 0 none, 1 a warp per (channel, block pixel),
-// 2 a warp per block pixel with every channel, 3 the same with analytic channels.
+// Jacobian pass per pixel, 2 the same with analytic derivative channels, 3 none
+// (a launch of oversampled blocks alone).  OS: 0 none, 1 a warp per (channel,
+// block pixel), 2 a warp per block pixel with every channel, 3 the same with
+// analytic channels, 4 as 2 for blocks of at most 32 sub-samples.
 template <int PIX, int OS, int EV>
 __global__ void __launch_bounds__(MODEL_THREADS) k_model_pass(PassArgs a, int g_os)
 {
@@ -475,10 +511,13 @@ __global__ void __launch_bounds__(MODEL_THREADS) k_model_pass(PassArgs a, int g_
             body_model_os<EV>(a, blockIdx.x, g_os);
         else if (OS == 2)
             body_model_os_jac<EV>(a, blockIdx.x, g_os);
-        else
+        else if (OS == 3)
             body_model_os_jac_an<EV>(a, blockIdx.x, g_os);
+        else
+            body_model_os_jac32<EV>(a, blockIdx.x, g_os);
         return;
     }
+    if (PIX == 3) return;
     const int vb = blockIdx.x - (OS != 0 ? g_os : 0), vg = gridDim.x - (OS != 0 ? g_os : 0);
     if (PIX == 0)
         body_model<EV>(a, vb, vg);
@@ -528,7 +567,7 @@ cudaError_t launch_model(const PassArgs& a, cudaStream_t s)
         if (a.jac_analytic) {
             if (os_groups * OS_WARPS >= 152LL * 32) {
                 if (g_pix > 0 && (e = launch_pass<2, 0>(a, g_pix, 0, s)) != cudaSuccess) return e;
-                return launch_pass<2, 3>(a, 0, g_os2, s);
+                return launch_pass<3, 3>(a, 0, g_os2, s);
             }
             if (a.maxitems[WK_OS] == 0) return g_pix > 0 ? launch_pass<2, 0>(a, g_pix, 0, s) : cudaSuccess;
             if (a.grid[WK_OS] <= MERGE_OS_MAX) return launch_pass<2, 1>(a, g_pix, a.grid[WK_OS], s);
@@ -537,7 +576,7 @@ cudaError_t launch_model(const PassArgs& a, cudaStream_t s)
         }
         if (os_groups * OS_WARPS >= 152LL * 32) {
             if (g_pix > 0 && (e = launch_pass<1, 0>(a, g_pix, 0, s)) != cudaSuccess) return e;
-            return launch_pass<1, 2>(a, 0, g_os2, s);
+            return a.os_ns <= 32 ? launch_pass<3, 4>(a, 0, g_os2, s) : launch_pass<3, 2>(a, 0, g_os2, s);
         }
         if (a.maxitems[WK_OS] == 0) return g_pix > 0 ? launch_pass<1, 0>(a, g_pix, 0, s) : cudaSuccess;
         if (a.grid[WK_OS] <= MERGE_OS_MAX) return launch_pass<1, 1>(a, g_pix, a.grid[WK_OS], s);

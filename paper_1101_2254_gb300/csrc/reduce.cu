@@ -38,22 +38,29 @@ __device__ __forceinline__ void load_chan_info(ChanInfo& ci, float& msky, const 
 
 // The normal equations as one bordered matrix: with v = (J_0 .. J_{nf-1}, r)
 // per pixel and weight w, M = sum w v v^T holds A (i, j < nf), g (j = nf) and
-// chi^2 (i = j = nf).  Thread (tile, group) owns a 4 x 4 tile of the upper
-// triangle of M and 16 pixels of each 256-pixel chunk: 9 shared loads feed 16
-// FMAs.  Sums over a thread's 16 pixels are plain float32; they are added to
-// the thread's compensated totals, and the 16 groups of a tile are merged in a
-// fixed order, so the partials are deterministic.
-constexpr int VSTR = GF_MAX_FREE + 1;  // row stride of the staged pixel vectors
-constexpr int NGRP = 16;              // pixel groups per chunk (16 pixels each)
+// chi^2 (i = j = nf).  Its upper triangle is covered by T = nt (nt + 1) / 2
+// tiles of 4 x 4 (nt = ceil((nf + 1) / 4)).  The pixels of each 256-pixel chunk
+// are split into G = 256 / T contiguous groups, and thread (group, tile) with
+// tid = group T + tile sums its tile over its group's pixels, so every thread
+// but 256 - G T has a tile.  The staged vectors are stored by component
+// (V[f][pixel], an odd row stride): a thread's staging stores are consecutive
+// words, and the product's reads of one component at neighbouring groups'
+// pixels fall in different banks.  Sums
+// over a group's pixels are plain float32; they are added to the thread's
+// compensated totals, and the G groups of a tile are merged in group order, so
+// the partials are deterministic.
+constexpr int VSTR = 20;  // components staged per pixel: >= 4 nt for nf <= 19
+static_assert(GF_MAX_FREE + 1 <= VSTR, "bordered vector longer than the staged row");
+constexpr int VPAD = RED_THREADS + 1;  // pixel stride of a staged component
 
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
 {
     pdl_entry();
-    __shared__ float V[RED_THREADS][VSTR];  // pixel vectors v = (J, r)
-    __shared__ float Wt[RED_THREADS];       // weights 1/sigma^2
+    __shared__ float V[VSTR][VPAD];  // pixel vectors v = (J, r), by component
+    __shared__ float Wt[RED_THREADS];                     // weights 1/sigma^2
     __shared__ ChanInfo ci;
     __shared__ float msky;
-    __shared__ float red[NGRP][16][16];      // per group, per tile slot, 4 x 4 sums
+    __shared__ float red[RED_THREADS][16];  // per (group, tile), its 4 x 4 sums
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_RED * (a.count + 1);
     const int tot = pre[n];
@@ -79,19 +86,20 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
     const float* Y = a.y + y_index(st, a.nchan, 0);
     const int tid = threadIdx.x;
     // this thread's tile (upper triangle, row-major over tile pairs) and group
-    const int tslot = tid % 16, grp = tid / 16;
-    int ti = -1, tj = -1;
+    const int T = nt * (nt + 1) / 2, G = RED_THREADS / T;
+    const int tslot = tid % T, grp = tid / T;
+    int ti = 0, tj = 0;
     {
         int k = 0;
-        for (int I = 0; I < nt && ti < 0; ++I)
+        for (int I = 0; I < nt; ++I)
             for (int J = I; J < nt; ++J, ++k)
                 if (k == tslot) {
                     ti = I;
                     tj = J;
-                    break;
                 }
     }
-    const bool active_tile = ti >= 0;
+    const bool active_tile = grp < G;
+    const int pg0 = grp * RED_THREADS / G, pg1 = (grp + 1) * RED_THREADS / G;  // the group's pixels
     CSum acc[4][4];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
@@ -107,19 +115,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
             for (int k = 0; k < a.nchan; ++k) {
                 const float yk = Y[(long long)k * HW + px];
                 if (ci.mw[k] != 0.0f) m = fmaf(ci.mw[k], yk, m);
-                if (ci.jc[k] >= 0) V[tid][ci.jc[k]] = yk;
+                if (ci.jc[k] >= 0) V[ci.jc[k]][tid] = yk;
             }
-            if (skyc >= 0) V[tid][skyc] = psum;
-            V[tid][nf] = valid ? d - m : 0.0f;
+            if (skyc >= 0) V[skyc][tid] = psum;
+            V[nf][tid] = valid ? d - m : 0.0f;
             Wt[tid] = valid ? 1.0f / (s * s) : 0.0f;
             if (a.m_out) a.m_out[st.pix_off + px] = m;
             if (a.J_out)
-                for (int f = 0; f < nf; ++f) a.J_out[(long long)f * HW + px] = V[tid][f];
+                for (int f = 0; f < nf; ++f) a.J_out[(long long)f * HW + px] = V[f][tid];
         } else {
-            for (int f = 0; f < nv; ++f) V[tid][f] = 0.0f;
+            for (int f = 0; f < nv; ++f) V[f][tid] = 0.0f;
             Wt[tid] = 0.0f;
         }
-        for (int f = nv; f < VSTR; ++f) V[tid][f] = 0.0f;
+        for (int f = nv; f < VSTR; ++f) V[f][tid] = 0.0f;
         __syncthreads();
         if (active_tile) {
             float sum[4][4];
@@ -128,14 +136,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
 #pragma unroll
                 for (int y = 0; y < 4; ++y) sum[x][y] = 0.0f;
             const int i0 = 4 * ti, j0 = 4 * tj;
-            for (int pp = 0; pp < RED_THREADS / NGRP; ++pp) {
-                const int p = grp * (RED_THREADS / NGRP) + pp;
+            for (int p = pg0; p < pg1; ++p) {
                 const float w = Wt[p];
                 float vi[4], vj[4];
 #pragma unroll
                 for (int x = 0; x < 4; ++x) {
-                    vi[x] = (i0 + x < VSTR) ? w * V[p][min(i0 + x, VSTR - 1)] : 0.0f;
-                    vj[x] = (j0 + x < VSTR) ? V[p][min(j0 + x, VSTR - 1)] : 0.0f;
+                    vi[x] = w * V[i0 + x][p];
+                    vj[x] = V[j0 + x][p];
                 }
 #pragma unroll
                 for (int x = 0; x < 4; ++x)
@@ -149,13 +156,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
         }
         __syncthreads();
     }
-    // merge the 16 groups of each tile in group order, then write the partials
+    // merge the G groups of each tile in group order, then write the partials
     // in the accumulator order of decode_acc (A pairs, g, chi^2)
     if (active_tile)
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) red[grp][tslot][x * 4 + y] = acc[x][y].s + acc[x][y].c;
+            for (int y = 0; y < 4; ++y) red[tid][x * 4 + y] = acc[x][y].s + acc[x][y].c;
     __syncthreads();
     for (int t = tid; t < a.nacc; t += RED_THREADS) {
         int i, j;
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
         for (int II = 0; II < I; ++II) slot += nt - II;
         slot += J - I;
         CSum tot = {0.0f, 0.0f};
-        for (int gq = 0; gq < NGRP; ++gq) csum_add(tot, red[gq][slot][(r_ % 4) * 4 + (c_ % 4)]);
+        for (int gq = 0; gq < G; ++gq) csum_add(tot, red[gq * T + slot][(r_ % 4) * 4 + (c_ % 4)]);
         a.partial[(long long)blk * a.nacc + t] = tot.s + tot.c;
     }
     if (a.work && tid == 0) {

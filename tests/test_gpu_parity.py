@@ -99,6 +99,29 @@ def test_convolve_parity(gf, H, W, P):
     assert_pix_close(g, o, what=f"conv {H}x{W} P{P}")
 
 
+@pytest.mark.parametrize("P", [9, 33, 41, 65])
+def test_convolve_several_tiles_per_cta(gf, P):
+    """The direct convolution on a small persistent grid (one CTA per SM, 16-row
+    tiles): a 512 x 512 channel has 256 tiles of 16 x 64 for 152 CTAs, so most
+    CTAs sum two tiles in turn.  That exercises the advance from tile to tile
+    and, for PSFs up to 35 pixels, the copies of the next tile that run while
+    the current one is summed.  Every output against the oracle's FFT sum."""
+    H = W = 512
+    c = (P - 1) // 2
+    rng = np.random.default_rng(P + 77)
+    ext = rng.uniform(0.0, 2.0, (H + 2 * c, W + 2 * c)).astype(np.float32)
+    psf = synth.random_psf(P, P + 5)
+    _, th, cap = gf.conv_tile_shape(P, W)
+    gf.set_conv_tile_shape(P, 16, 1)
+    try:
+        d = gf.make_desc(H, W, P, [synth.SERSIC], conv_method=gf.CONV_DIRECT)
+        g = gf.convolve(d, cuda(ext), cuda(psf)).cpu().numpy()
+    finally:
+        gf.set_conv_tile_shape(P, th, cap)
+    o = oracle.convolve_fft(ext.astype(np.float64), psf.astype(np.float64))
+    assert_pix_close(g, o, what=f"conv 512x512 P{P}, 152 CTAs")
+
+
 def test_convolve_delta_is_bit_exact_crop(gf):
     H, W, P = 45, 77, 17
     c = (P - 1) // 2
