@@ -466,6 +466,7 @@ struct Layout {
     int rungs;  // channels of the trial pass: 1, or the LM ladder's rungs
     int tot_model, tot_os, tot_conv, tot_red, tot_conv32;
     int max_red;  // most reduction blocks of one stamp
+    long long tot_wb;  // 16 x 32 output blocks of all stamps (the fused trial chi^2's partials)
     int conv_ty, conv_cap;  // direct convolution: tile height, persistent CTAs per SM
     int eval_variant;  // the model kernels' evaluator: 0 Sersic / disk / Gaussian,
                        // 1 with Moffat, 2 with King, Nuker or point sources
@@ -494,7 +495,7 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     int* pr = pl->pre.data() + WK_RED * (count + 1);
     int* pc32 = pl->pre.data() + WK_CONV32 * (count + 1);
     int max_red = 0;
-    long long e1 = 0, y1 = 0;
+    long long e1 = 0, y1 = 0, wb = 0;
     const ConvShape shape = conv_shape(P);
     for (int b = 0; b < count; ++b) {
         StampInfo& s = pl->st[b];
@@ -526,11 +527,14 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         pc[b + 1] = pc[b] + (s.conv_tw == 64 ? conv_tiles : 0);
         pc32[b + 1] = pc32[b] + (s.conv_tw == 32 ? conv_tiles : 0);
         pr[b + 1] = pr[b] + (int)(((long long)s.H * s.W + RED_PIX - 1) / RED_PIX);
+        s.wb_off = (int)std::min<long long>(wb, INT32_MAX);
+        wb += (long long)((s.H + 15) / 16) * ((s.W + 31) / 32);
         max_red = std::max(max_red, pr[b + 1] - pr[b]);
     }
     Layout& L = pl->L;
     memset(&L, 0, sizeof(L));
     L.max_red = max_red;
+    L.tot_wb = wb;
     L.conv_ty = shape.ty;
     L.conv_cap = shape.ctas_per_sm;
     L.count = count;
@@ -589,8 +593,10 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         o += al(sizeof(float) * (size_t)R * y1);
     }
     if (need & (NEED_TRIAL | NEED_LM | NEED_CHI2)) {
+        // per rung: one partial per reduce block, or (LM on the direct path)
+        // one per 16 x 32 output block
         L.part_trial = o;
-        o += al(sizeof(float) * (size_t)R * L.tot_red);
+        o += al(sizeof(float) * (size_t)R * std::max<long long>(L.tot_red, L.tot_wb));
     }
     if (need & NEED_LM) {
         L.lm = o;
@@ -1029,8 +1035,9 @@ gf_status trial_pass(const PassArgs& a, const Plan& pl, void* ws, cudaStream_t s
     ProfScope ps(PROF_REDUCE, s);
     if (a.lm) {
         // the LM body: one chi^2 per rung of the trial ladder, summed by
-        // k_final_update
-        GF_CUDA(launch_reduce_rungs(a, s));
+        // k_final_update (on the direct path already reduced per tile by the
+        // convolution)
+        if (!a.conv_chi2) GF_CUDA(launch_reduce_rungs(a, s));
         return GF_OK;
     }
     GF_CUDA(launch_reduce_chi2(a, s));
@@ -1598,6 +1605,8 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     at_.phase = PH_TRIAL;
     at_.nchan = at_.chan_stride = L.rungs;  // one trial channel per rung of the ladder
     set_grids(at_, L, L.rungs);
+    // the direct path reduces the trial chi^2 inside the convolution's epilogue
+    at_.conv_chi2 = pl.method == GF_CONV_DIRECT ? 1 : 0;
     // each pass walks the list of stamps in its phase, rebuilt every body
     aj.wl.n = at<int>(ws, L.wl_n[0]);
     aj.wl.ids = at<int>(ws, L.wl_ids[0]);

@@ -133,7 +133,8 @@ struct ConvItem {
     const float* E;
     float* Y;
     const float* psf;
-    int b, He, We, H, W, ty0, tx0;
+    long long pix_off;  // the stamp's image / sigma offset
+    int b, ch, wb_off, He, We, H, W, ty0, tx0;
 };
 
 template <int TX, int TY>
@@ -144,7 +145,10 @@ __device__ __forceinline__ ConvItem conv_item(const PassArgs& a, const int* pre,
     const int li = wl_locate(pre, n, blk, hint);
     ConvItem q;
     q.b = a.wl.ids[li];
+    q.ch = ch;
     const StampInfo& st = a.st[q.b];
+    q.pix_off = st.pix_off;
+    q.wb_off = st.wb_off;
     q.He = st.He;
     q.We = st.We;
     q.H = st.H;
@@ -297,6 +301,30 @@ __global__ void __launch_bounds__(TX * TY / 16) k_conv_direct(PassArgs a)
 
         // the warp's block meets the stamp
         const bool active = q.ty0 + wr0 < q.H && q.tx0 + wc0 < q.W;
+        // an LM trial pass reduces chi^2 here: the thread's 16 image and sigma
+        // values are loaded now, so that their latency hides under the taps
+        // (outside the stamp: sigma = 0, a pixel that counts nothing)
+        float dv[RPT][8], sv[RPT][8];
+        float tmw = 0.0f, tmsky = 0.0f;
+        if (a.conv_chi2) {
+            const Channel& chn = a.chan[(long long)q.b * a.chan_stride + q.ch];
+            tmw = chn.mweight;
+            tmsky = chn.msky;
+            const float* img = a.img + q.pix_off;
+            const float* sig = a.sig + q.pix_off;
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+                const int y = q.ty0 + r0 + 8 * i;
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    const int x = q.tx0 + c0 + o;
+                    const bool in = active && y < q.H && x < q.W;
+                    const long long px = (long long)y * q.W + x;
+                    dv[i][o] = in ? __ldg(&img[px]) : 0.0f;
+                    sv[i][o] = in ? __ldg(&sig[px]) : 0.0f;
+                }
+            }
+        }
         float acc[RPT][8];
 #pragma unroll
         for (int i = 0; i < RPT; ++i)
@@ -310,6 +338,39 @@ __global__ void __launch_bounds__(TX * TY / 16) k_conv_direct(PassArgs a)
             const unsigned long long rows = (unsigned long long)min(16, q.H - q.ty0 - wr0);
             const unsigned long long cols = (unsigned long long)min(32, q.W - q.tx0 - wc0);
             atomicAdd(&a.work[PROF_CONV], 2ull * (unsigned long long)P * P * rows * cols);
+        }
+        if (a.conv_chi2) {
+            // an LM trial pass: this rung's chi^2 over the warp's 16 x 32 block
+            // (each thread its 16 outputs in order, then the warp's shuffle
+            // tree), one partial per block, and no convolved tile written.  The
+            // blocks are the same under every tile shape, so the sums are too.
+            CSum cs = {0.0f, 0.0f};
+            if (active)
+#pragma unroll
+                for (int i = 0; i < RPT; ++i)
+#pragma unroll
+                    for (int o = 0; o < 8; ++o) {
+                        const float d = dv[i][o], sg = sv[i][o];
+                        if (isfinite(d) && isfinite(sg) && sg > 0.0f) {
+                            const float z = (d - fmaf(tmw, acc[i][o], tmsky)) / sg;
+                            csum_add(cs, z * z);
+                        }
+                    }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                CSum other;
+                other.s = __shfl_down_sync(0xffffffffu, cs.s, o);
+                other.c = __shfl_down_sync(0xffffffffu, cs.c, o);
+                cs = csum_merge(cs, other);
+            }
+            if (active && lane == 0) {
+                const int nbx = (q.W + 31) / 32;
+                const long long slot = q.wb_off + (long long)((q.ty0 + wr0) / 16) * nbx + (q.tx0 + wc0) / 32;
+                a.partial[slot * a.nchan + q.ch] = cs.s + cs.c;
+            }
+            q = qn;
+            cb ^= 1;
+            continue;
         }
         // the tile through shared memory (row stride TX + 1), then coalesced rows
         __syncthreads();

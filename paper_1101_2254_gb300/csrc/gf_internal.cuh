@@ -114,6 +114,8 @@ struct StampInfo {
     int os_factor, os_box, os_x0, os_y0;  // block origin resolved
     int nchan;                             // channels of the Jacobian pass
     int conv_tw;                           // direct-convolution tile width (64 or 32)
+    int wb_off;                            // first slot of the stamp's 16 x 32 output blocks
+                                           // (ceil(H/16) x ceil(W/32), row-major) in a call
     long long pix_off;   // into image / sigma / model (H*W elements)
     long long psf_off;   // into the PSF array (P*P)
     long long ext1_off;  // sum of He*We over the earlier stamps
@@ -544,6 +546,9 @@ struct PassArgs {
     int eval_variant;          // 0 Sersic/disk/Gaussian, 1 with Moffat, 2 with King/Nuker/point
     int os_ns;                 // sub-samples per oversampled pixel (os_factor^2)
     int conv_ty;               // direct-convolution tile height (32 or 16)
+    int conv_chi2;             // an LM trial pass on the direct path: the convolution writes the
+                               // chi^2 partial of each 16 x 32 output block per rung (channel),
+                               // slot st.wb_off + block, instead of the convolved tile
     float* ext;                // channel grids: ext + ext_index(st[b], nchan, k)
     float* y;                  // convolved channels: y + y_index(st[b], nchan, k)
     const float* psf;

@@ -753,8 +753,18 @@ __global__ void __launch_bounds__(RED_THREADS) k_final_update(PassArgs a, int* a
     const int phase = L.phase;
     const int nr = a.nchan;  // rungs of the trial pass
     if (phase == PH_TRIAL) {
-        const int* pst = a.pre_static + WK_RED * (a.count + 1);
-        const int b0 = pst[b], b1 = pst[b + 1];
+        // the stamp's partial slots: its reduce blocks, or its 16 x 32 output
+        // blocks when the direct convolution reduced the trial
+        int b0, b1;
+        if (a.conv_chi2) {
+            const StampInfo& st = a.st[b];
+            b0 = st.wb_off;
+            b1 = b0 + ((st.H + 15) / 16) * ((st.W + 31) / 32);
+        } else {
+            const int* pst = a.pre_static + WK_RED * (a.count + 1);
+            b0 = pst[b];
+            b1 = pst[b + 1];
+        }
         for (int r = L.rung0; r < nr; ++r) {
             CSum acc = {0.0f, 0.0f};
             for (int k = b0 + threadIdx.x; k < b1; k += RED_THREADS)

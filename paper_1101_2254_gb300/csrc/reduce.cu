@@ -41,26 +41,24 @@ __device__ __forceinline__ void load_chan_info(ChanInfo& ci, float& msky, const 
 // chi^2 (i = j = nf).  Its upper triangle is covered by T = nt (nt + 1) / 2
 // tiles of 4 x 4 (nt = ceil((nf + 1) / 4)).  The pixels of each 256-pixel chunk
 // are split into G = 256 / T contiguous groups, and thread (group, tile) with
-// tid = group T + tile sums its tile over its group's pixels, so every thread
-// but 256 - G T has a tile.  The staged vectors are stored by component
-// (V[f][pixel], an odd row stride): a thread's staging stores are consecutive
-// words, and the product's reads of one component at neighbouring groups'
-// pixels fall in different banks.  Sums
+// tid = group T + tile sums its tile over its group's pixels (two 16-byte
+// shared loads feed 16 FMAs), so every thread but 256 - G T has a tile.  Sums
 // over a group's pixels are plain float32; they are added to the thread's
 // compensated totals, and the G groups of a tile are merged in group order, so
 // the partials are deterministic.
-constexpr int VSTR = 20;  // components staged per pixel: >= 4 nt for nf <= 19
+constexpr int VSTR = 20;  // row stride of the staged pixel vectors: >= 4 nt for nf <= 19
 static_assert(GF_MAX_FREE + 1 <= VSTR, "bordered vector longer than the staged row");
-constexpr int VPAD = RED_THREADS + 1;  // pixel stride of a staged component
+constexpr int RSTR = 17;  // row stride of the per-thread tile sums (odd: the 16 stores of a
+                          // thread's row land in distinct banks across the warp)
 
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
 {
     pdl_entry();
-    __shared__ float V[VSTR][VPAD];  // pixel vectors v = (J, r), by component
+    __shared__ __align__(16) float V[RED_THREADS][VSTR];  // pixel vectors v = (J, r)
     __shared__ float Wt[RED_THREADS];                     // weights 1/sigma^2
     __shared__ ChanInfo ci;
     __shared__ float msky;
-    __shared__ float red[RED_THREADS][16];  // per (group, tile), its 4 x 4 sums
+    __shared__ float red[RED_THREADS][RSTR];  // per (group, tile), its 4 x 4 sums
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_RED * (a.count + 1);
     const int tot = pre[n];
@@ -115,19 +113,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
             for (int k = 0; k < a.nchan; ++k) {
                 const float yk = Y[(long long)k * HW + px];
                 if (ci.mw[k] != 0.0f) m = fmaf(ci.mw[k], yk, m);
-                if (ci.jc[k] >= 0) V[ci.jc[k]][tid] = yk;
+                if (ci.jc[k] >= 0) V[tid][ci.jc[k]] = yk;
             }
-            if (skyc >= 0) V[skyc][tid] = psum;
-            V[nf][tid] = valid ? d - m : 0.0f;
+            if (skyc >= 0) V[tid][skyc] = psum;
+            V[tid][nf] = valid ? d - m : 0.0f;
             Wt[tid] = valid ? 1.0f / (s * s) : 0.0f;
             if (a.m_out) a.m_out[st.pix_off + px] = m;
             if (a.J_out)
-                for (int f = 0; f < nf; ++f) a.J_out[(long long)f * HW + px] = V[f][tid];
+                for (int f = 0; f < nf; ++f) a.J_out[(long long)f * HW + px] = V[tid][f];
         } else {
-            for (int f = 0; f < nv; ++f) V[f][tid] = 0.0f;
+            for (int f = 0; f < nv; ++f) V[tid][f] = 0.0f;
             Wt[tid] = 0.0f;
         }
-        for (int f = nv; f < VSTR; ++f) V[f][tid] = 0.0f;
+        for (int f = nv; f < VSTR; ++f) V[tid][f] = 0.0f;
         __syncthreads();
         if (active_tile) {
             float sum[4][4];
@@ -138,12 +136,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
             const int i0 = 4 * ti, j0 = 4 * tj;
             for (int p = pg0; p < pg1; ++p) {
                 const float w = Wt[p];
-                float vi[4], vj[4];
-#pragma unroll
-                for (int x = 0; x < 4; ++x) {
-                    vi[x] = w * V[i0 + x][p];
-                    vj[x] = V[j0 + x][p];
-                }
+                const float4 a4 = *reinterpret_cast<const float4*>(&V[p][i0]);
+                const float4 b4 = *reinterpret_cast<const float4*>(&V[p][j0]);
+                const float vi[4] = {w * a4.x, w * a4.y, w * a4.z, w * a4.w};
+                const float vj[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
                 for (int x = 0; x < 4; ++x)
 #pragma unroll
