@@ -77,9 +77,11 @@ TRAFFIC = {
 # once), so the bench scales it by the outputs of its average launch.  Null
 # once the kernel source differs from the one captured.
 CONV_DIRECT_TRAFFIC = {
-    "bytes_per_output": 3.2688e9 / (7 * 8192 * 4096),
+    # the 7-channel Jacobian launch of the profiled step (2352.2 MB read + 911.5 MB
+    # written); a fused trial launch moves 1219.6 MB for 2 rungs (18.2 B per output)
+    "bytes_per_output": 3.2637e9 / (7 * 8192 * 4096),
     "profile": "profiles/k_conv_direct_learned8192.md",
-    "sources": {"paper_1101_2254_gb300/csrc/conv_direct.cu": "3575d48ac804129d96c9a4b8b9e128ba25923c195f8697891e7bb06bec10c3d3"},
+    "sources": {"paper_1101_2254_gb300/csrc/conv_direct.cu": "a0211dbd9cfc3e4a1c525d857c037a90f20008686be10873a8531cbb69679dfc"},
 }
 
 
@@ -221,11 +223,6 @@ def measured_peaks():
             return json.load(fh), "measured"
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
-
-
-def fp32_peak_tflops(sm_count, mhz):
-    # 128 FP32 lanes per SM, one FMA (2 FLOP) per lane per clock
-    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
 
 
 # ------------------------------------------------------------------ the GPU arm
@@ -442,14 +439,13 @@ def run_gf(args):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     if dom == "conv":
         achieved = pr["conv"]["work"] / (pr["conv"]["ms"] / 1e3) / 1e12
-        peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+        peak = gf.fma_peak(False)
         kname = ("k_fft_rows_fwd_w + k_fft_cols + k_fft_rows_inv_w (5 N log2 N FLOP per transform)"
                  if st.P >= 41 else "k_conv_direct (2 P^2 FLOP per output)")
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic_of(args.workload) if st.P >= 41 else None,
-                "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 "
-                               f"FLOP x {sm_max:.0f} MHz (max clock)",
+                "peak_source": "measured FP32 FMA loop (gf_fma_peak) in this run",
                 "launches": pr["conv"]["launches"],
                 "avg_launch_ms": pr["conv"]["ms"] / max(pr["conv"]["launches"], 1)}
     else:
@@ -855,7 +851,7 @@ def run_cube(args):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     # one launch per step: the kernel's duration is the step's
     ach = pr["conv"]["work"] / (pr["conv"]["ms"] / 1e3) / 1e12
-    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    peak = gf.fma_peak(False)
     rr = gf.spec_results(res)
     iters = np.array([r["iters"] for r in rr])
     status = np.array([r["status"] for r in rr])
@@ -908,6 +904,7 @@ def run_cube(args):
                          "kernel": "k_spec (useful FLOPs: LSF sums of the model and Jacobian "
                                    "columns, the normal-matrix triangle, trial chi^2)",
                          "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "peak_source": "measured FP32 FMA loop (gf_fma_peak) in this run",
                          "traffic": None},
             "kernel_ms_per_step": {k: v["ms"] for k, v in pr.items()},
             "lm": {"iters_median": float(np.median(iters)), "iters_max": int(iters.max()),
@@ -1125,7 +1122,9 @@ def run_learned(args):
                          "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": ach / fp32_peak,
                          "traffic": conv_direct_traffic(conv_out / max(pr["conv"]["launches"], 1)),
-                         "traffic_note": "bytes per launch: 13.9 B per output (ncu capture, "
+                         "traffic_note": "bytes per launch: 13.9 B per output (ncu capture of "
+                                         "the Jacobian launch, the dominant one; a fused trial "
+                                         "launch moves 18.2 B per output; "
                                          "profiles/k_conv_direct_learned8192.md) x the outputs "
                                          "of the average launch",
                          "alg_bytes_per_launch": 4.0 * (96 * 96 / 4096 + 1) * conv_out
