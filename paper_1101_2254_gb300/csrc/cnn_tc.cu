@@ -12,15 +12,13 @@
 // K-major layout.
 //
 // A CTA of 256 threads stages B whole in shared memory once, then walks tiles
-// of 128 rows (persistent grid) in K chunks of 96: each chunk of the A tile is
-// gathered by cp.async into the canonical K-major layout (two chunk buffers,
-// one step ahead), one thread issues the MMAs (M 128, N, K 16) into one of two
-// tensor-memory accumulators of 128 lanes x N columns and commits them to an
-// mbarrier (bounded waits); a tile's epilogue reads its accumulator
-// (tcgen05.ld), adds the bias, applies the ReLU, rounds to bf16 and stores NHWC
-// (layers 2-3) or NCHW (layer 4, the layout the first fully connected layer
-// reads) while the next tile's MMAs run.  Layer 1 (one input channel: K = 9)
-// stays a SIMT loop.
+// of 128 rows (persistent grid): per K chunk of 288 values it gathers the A
+// tile into the canonical K-major layout, one thread issues the MMAs
+// (M 128, N, K 16) into a tensor-memory accumulator of 128 lanes x N columns and
+// commits them to an mbarrier (bounded wait); the epilogue reads the
+// accumulator (tcgen05.ld), adds the bias, applies the ReLU, rounds to bf16 and
+// stores NHWC (layers 2-3) or NCHW (layer 4, the layout the first fully
+// connected layer reads).  Layer 1 (one input channel: K = 9) stays a SIMT loop.
 //
 // Arithmetic is the network's specified one: bf16 weights and activations,
 // float32 accumulation, in the tensor cores' summation order.  The training
@@ -38,7 +36,7 @@ namespace {
 
 constexpr int CT_THREADS = 256;
 constexpr int CT_TM = 128;  // rows per tile (the MMA's M)
-constexpr int CT_KC = 96;   // K per staged chunk of A (two chunk buffers)
+constexpr int CT_KC = 288;  // K per staged chunk of A
 
 struct ConvTC {
     const __nv_bfloat16* x;  // input, NHWC: B x hin x hin x cin
@@ -48,23 +46,16 @@ struct ConvTC {
     int B, cin, hin, hout, out_nchw;
 };
 
-// The CTA's work is a sequence of steps s = (tile, K chunk) over its tiles
-// (blockIdx.x, blockIdx.x + gridDim.x, ...).  Step s's A chunk is gathered
-// (cp.async) into buffer s & 1 one step ahead, its MMAs accumulate into the
-// tile's tensor-memory accumulator (tiles alternate between two) and commit to
-// mbarrier s & 1; a tile's epilogue runs one step after its last MMAs were
-// issued.  So while the tensor cores work on step s, the CTA's threads gather
-// step s + 1 and write out the previous tile.
 template <int N>
 __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(ConvTC a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int K = 9 * a.cin, nchunk = K / CT_KC;
     __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // N x K
-    __nv_bfloat16* As = Bs + N * K;                                    // 2 x (128 x CT_KC)
+    __nv_bfloat16* As = Bs + N * K;                                    // 128 x CT_KC
     // B whole, once: row n of the weights is K contiguous bf16
     for (int i = tid; i < N * (K / 8); i += CT_THREADS) {
         const int n = i / (K / 8), k8 = (i - n * (K / 8)) * 8;
@@ -74,68 +65,86 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(ConvTC a)
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_addr(&tmem_base)),
-                     "r"(2 * N));
+                     "r"(N));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[1])));
-    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)));
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
+    const uint32_t bar_a = smem_addr(&bar);
     const uint32_t idesc = idesc_bf16(CT_TM, N);
     const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
     const int hw = a.hout * a.hout;
     const long long M = (long long)a.B * hw;
     const long long tiles = (M + CT_TM - 1) / CT_TM;
-    const long long my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const long long S = my_tiles * nchunk;
-
-    // step s's A chunk into buffer s & 1: (row, 8 consecutive k of one tap) per
-    // item, a warp 8 rows x 4 consecutive 8-k groups (the 8 lanes of a 16-byte
-    // store phase write 8 different rows: distinct banks; a row's 4 groups are
-    // 64 contiguous bytes of the input), 16 bytes by cp.async with zeros
-    // outside the input
-    static_assert(CT_KC % 32 == 0 && CT_THREADS % 32 == 0, "lane mapping");
-    auto gather = [&](long long step) {
-        const long long m0 = (blockIdx.x + (step / nchunk) * gridDim.x) * CT_TM;
-        const int kc0 = (int)(step % nchunk) * CT_KC;
-        __nv_bfloat16* Ab = As + (step & 1) * (CT_TM * CT_KC);
-        for (int i = tid; i < CT_TM * (CT_KC / 8); i += CT_THREADS) {
-            const int lane_i = i & 31, rest = i >> 5;
-            const int kq = rest % (CT_KC / 32), rg = rest / (CT_KC / 32);
-            const int row = rg * 8 + (lane_i & 7), k8 = (kq * 4 + (lane_i >> 3)) * 8;
-            const int k = kc0 + k8;
-            const long long m = m0 + row;
-            const __nv_bfloat16* src = a.x;  // (not read when the copy is a zero fill)
-            bool in = false;
-            if (m < M) {
-                const int b = (int)(m / hw), pix = (int)(m - (long long)b * hw);
-                const int oy = pix / a.hout, ox = pix - oy * a.hout;
-                const int tap = k / a.cin, ci = k - tap * a.cin;
-                const int iy = 2 * oy - 1 + tap / 3, ix = 2 * ox - 1 + tap % 3;
-                in = iy >= 0 && iy < a.hin && ix >= 0 && ix < a.hin;
-                if (in) src = a.x + (((long long)b * a.hin + iy) * a.hin + ix) * a.cin + ci;
+    uint32_t parity = 0;
+    bool failed = false;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long long m0 = tile * CT_TM;
+        for (int c = 0; c < nchunk && !failed; ++c) {
+            const int kc0 = c * CT_KC;
+            // gather the A chunk: (row, 8 consecutive k of one tap) per item.  A
+            // warp takes 8 rows x 4 consecutive 8-k groups: the 8 lanes of each
+            // 16-byte store phase write 8 different rows of one core matrix
+            // (distinct banks), and each row's 4 groups are 64 contiguous bytes
+            // of the input.
+            static_assert(CT_KC % 32 == 0 && CT_THREADS % 32 == 0, "lane mapping");
+            for (int i = tid; i < CT_TM * (CT_KC / 8); i += CT_THREADS) {
+                const int lane_i = i & 31, rest = i >> 5;
+                const int kq = rest % (CT_KC / 32), rg = rest / (CT_KC / 32);
+                const int row = rg * 8 + (lane_i & 7), k8 = (kq * 4 + (lane_i >> 3)) * 8;
+                const int k = kc0 + k8;
+                const long long m = m0 + row;
+                const __nv_bfloat16* src = a.x;  // (not read when the copy is a zero fill)
+                bool in = false;
+                if (m < M) {
+                    const int b = (int)(m / hw), pix = (int)(m - (long long)b * hw);
+                    const int oy = pix / a.hout, ox = pix - oy * a.hout;
+                    const int tap = k / a.cin, ci = k - tap * a.cin;
+                    const int iy = 2 * oy - 1 + tap / 3, ix = 2 * ox - 1 + tap % 3;
+                    in = iy >= 0 && iy < a.hin && ix >= 0 && ix < a.hin;
+                    if (in) src = a.x + (((long long)b * a.hin + iy) * a.hin + ix) * a.cin + ci;
+                }
+                // 16 bytes by cp.async (zeros outside the input): every item of the
+                // chunk is in flight at once
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(
+                                 smem_addr(As + cofs(row, k8, CT_KC))),
+                             "l"(src), "r"(in ? 16 : 0)
+                             : "memory");
             }
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(
-                             smem_addr(Ab + cofs(row, k8, CT_KC))),
-                         "l"(src), "r"(in ? 16 : 0)
-                         : "memory");
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (tid == 0) {
+                for (int ks = 0; ks < CT_KC / 16; ++ks)
+                    umma(tmem, mdesc(a0 + ks * 256, 128, CT_KC * 16),
+                         mdesc(b0 + (uint32_t)(kc0 + ks * 16) * 16, 128, (uint32_t)K * 16), idesc,
+                         (c > 0 || ks > 0) ? 1 : 0);
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        bar_a));
+            }
+            const bool done = mbar_wait(bar_a, parity);
+            parity ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (!__syncthreads_and(done ? 1 : 0)) {
+                // the MMAs did not complete in the bounded wait: from here on
+                // this CTA issues no MMA and writes its tiles' outputs as NaN
+                // (a non-finite network output makes the caller fall back to
+                // the default start)
+                failed = true;
+                break;
+            }
         }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
-    // the tile of step `last` (its last chunk): warp w reads lane quarter w % 4,
-    // column half w / 4 of the tile's accumulator; adds the bias, applies the
-    // ReLU, rounds to bf16 and stores (NaN where the MMAs did not complete)
-    auto epilogue = [&](long long last, bool fail) {
-        const long long tidx = last / nchunk;
-        const long long m0 = (blockIdx.x + tidx * gridDim.x) * CT_TM;
+        // epilogue: warp w reads lane quarter w % 4, column half w / 4
         const int quarter = warp & 3, nhalf = warp >> 2;
         const int row = quarter * 32 + lane;
         const long long m = m0 + row;
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((tidx & 1) * N);
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
         int b = 0, pix = 0;
         if (m < M) {
             b = (int)(m / hw);
@@ -143,12 +152,20 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(ConvTC a)
         }
         for (int n0 = nhalf * (N / 2); n0 < (nhalf + 1) * (N / 2); n0 += 8) {
             float v[8];
-            if (!fail) tmem_ld8(taddr + n0, v);
+            if (!failed) {
+                tmem_ld8(taddr + n0, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = NAN;
+            }
             if (m >= M) continue;
             __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                o[j] = __float2bfloat16_rn(fail ? NAN : fmaxf(v[j] + a.bias[n0 + j], 0.0f));
+            for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16_rn(fmaxf(v[j] + a.bias[n0 + j], 0.0f));
+            if (failed) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16_rn(NAN);
+            }
             if (a.out_nchw) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) a.y[((long long)b * N + n0 + j) * hw + pix] = o[j];
@@ -156,71 +173,16 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(ConvTC a)
                 *reinterpret_cast<uint4*>(a.y + m * N + n0) = *reinterpret_cast<const uint4*>(o);
             }
         }
-    };
-
-    uint32_t ph0 = 0u, ph1 = 0u;  // phases of the two mbarriers' next completions
-    bool failed = false;
-    int fail_bar = -1;  // the commit a failed wait gave up on (the only one in flight)
-    uint32_t fail_ph = 0u;
-    // wait for the MMAs of step `step` (bounded); a timeout fails the CTA
-    auto wait_mma = [&](long long step) {
-        const int j = (int)(step & 1);
-        const uint32_t phase = j ? ph1 : ph0;
-        const bool ok = mbar_wait(smem_addr(&bar[j]), phase);
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (!__syncthreads_and(ok ? 1 : 0)) {
-            // from here on this CTA issues no MMA and writes its tiles as NaN
-            // (a non-finite network output makes the caller fall back to the
-            // default start)
-            failed = true;
-            fail_bar = j;
-            fail_ph = phase;
-        }
-        if (j)
-            ph1 ^= 1u;
-        else
-            ph0 ^= 1u;
-    };
-    if (S > 0) gather(0);
-    for (long long s = 0; s < S; ++s) {
-        if (s >= 1 && !failed) wait_mma(s - 1);  // buffer (s + 1) & 1 is free, tile s - 1 may be done
-        if (s + 1 < S) {
-            if (!failed) gather(s + 1);
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        }
-        if (s >= 1 && (s - 1) % nchunk == nchunk - 1) epilogue(s - 1, failed);
-        asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+        __syncthreads();  // the accumulator is read before the next tile's MMAs
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (!failed && tid == 0) {
-            const int c = (int)(s % nchunk);
-            const uint32_t acc_col = (uint32_t)(((s / nchunk) & 1) * N);
-            const uint32_t abuf = a0 + (uint32_t)((s & 1) * CT_TM * CT_KC * 2);
-            for (int ks = 0; ks < CT_KC / 16; ++ks)
-                umma(tmem + acc_col, mdesc(abuf + ks * 256, 128, CT_KC * 16),
-                     mdesc(b0 + (uint32_t)(c * CT_KC + ks * 16) * 16, 128, (uint32_t)K * 16), idesc,
-                     (c > 0 || ks > 0) ? 1 : 0);
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_addr(&bar[s & 1])));
-        }
     }
-    if (S > 0) {
-        if (!failed) wait_mma(S - 1);
-        epilogue(S - 1, failed);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    // free the tensor memory once no MMA can still be writing it: every commit
-    // was waited for, or after a timeout the one in flight is waited for once
-    // more (bounded)
+    // free the tensor memory once no MMA can still be writing it: on the normal
+    // path every commit was waited for; after a timeout, wait (bounded) once more
     bool drained = true;
-    if (failed) drained = __syncthreads_and(mbar_wait(smem_addr(&bar[fail_bar]), fail_ph) ? 1 : 0);
+    if (failed) drained = __syncthreads_and(mbar_wait(bar_a, parity ^ 1u) ? 1 : 0);
     if (drained && warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * N));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(N));
 }
 
 // layer 1 (one input channel), channels-last output: thread = (sample, 8
@@ -271,7 +233,7 @@ cudaError_t launch_tc(const ConvTC& a, cudaStream_t s)
 {
     static int optin[64];
     const int K = 9 * a.cin;
-    const size_t smem = sizeof(__nv_bfloat16) * ((size_t)N * K + 2 * (size_t)CT_TM * CT_KC);
+    const size_t smem = sizeof(__nv_bfloat16) * ((size_t)N * K + (size_t)CT_TM * CT_KC);
     cudaError_t e = ensure_smem_optin((const void*)k_conv_tc<N>, (int)smem, optin);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
