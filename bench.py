@@ -1037,20 +1037,24 @@ def run_learned(args):
     dflt_ms = float(np.mean(dflt_step_ms))
     # end to end through the public calls: host (pinned) inputs in, parameters out
     img_h, sig_h, psf_h = img.cpu().pin_memory(), sig.cpu().pin_memory(), psf.cpu().pin_memory()
-    e2e_ms = []
+    e2e_ms, e2e_copy_ms = [], []
     for k in range(max(1, min(args.steps, 3)) + 1):  # the first is an untimed warm-up
         e0 = torch.cuda.Event(enable_timing=True)
+        ec = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         i_d = img_h.to(dev, non_blocking=True)
         s_d = sig_h.to(dev, non_blocking=True)
         p_d = psf_h.to(dev, non_blocking=True)
+        ec.record(stream)
         pe, _, _ = fit(True, i_d, s_d, p_d)
         e1.record(stream)
         e1.synchronize()
         if k > 0:
             e2e_ms.append(e0.elapsed_time(e1))
+            e2e_copy_ms.append(e0.elapsed_time(ec))
     e2e_ms = gd.max_over_ranks(float(np.mean(e2e_ms)), ws_)
+    e2e_copy_ms = float(np.mean(e2e_copy_ms))
     # one more step with the library's profiler on (per-class events; the LM
     # body is launched directly instead of through the graph), inside an NVTX
     # range "gf_profiled" that a profiler's launch list can keep to
@@ -1116,7 +1120,8 @@ def run_learned(args):
                     # batched fit takes host parameters); parameters and results out
                     "h2d_bytes_per_step": int(img.numel() * 4 * 2 + psf.numel() * 4
                                               + count * 9 * 8),
-                    "d2h_bytes_per_step": int(count * 9 * 8 * 2 + count * 32)},
+                    "d2h_bytes_per_step": int(count * 9 * 8 * 2 + count * 32),
+                    "ms_per_step": e2e_ms, "h2d_inputs_ms": e2e_copy_ms},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "kernel": "k_conv_direct (2 P^2 FLOP per output)",
                          "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",

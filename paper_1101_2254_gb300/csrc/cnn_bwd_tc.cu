@@ -420,6 +420,11 @@ cudaError_t launch_dx(const ConvBwd& a, cudaStream_t s)
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    // the largest shared-memory carveout, so that the occupancy query (and the
+    // launch) can place as many of these shared-memory-heavy CTAs as fit
+    if ((e = cudaFuncSetAttribute((const void*)k_conv_dx_tc<NCI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+        return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_dx_tc<NCI>, BT_THREADS, smem)) !=
         cudaSuccess)
         return e;

@@ -385,6 +385,33 @@ def _res(r: LMResult):
     return dict(chi2=r.chi2, lam=r.lam, iters=r.iters, accepted=r.accepted, status=r.status)
 
 
+class Results:
+    """Per-stamp results of a batched fit, over the library's result array without
+    a per-stamp conversion when the call returns: item i is stamp i's result dict
+    (built when read), and each field is a NumPy view (results.status, .iters,
+    .accepted, .chi2, .lam)."""
+
+    def __init__(self, arr):
+        self._arr = arr
+        self._np = np.ctypeslib.as_array(arr)  # structured view of the same memory
+
+    def __len__(self):
+        return len(self._arr)
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [_res(self._arr[k]) for k in range(*i.indices(len(self._arr)))]
+        return _res(self._arr[i])
+
+    def __iter__(self):
+        return (_res(r) for r in self._arr)
+
+    def __getattr__(self, name):
+        if name in ("chi2", "lam", "iters", "accepted", "status"):
+            return self._np[name]
+        raise AttributeError(name)
+
+
 def lm_fit(d: Desc, params, fixed, img, sig, psf, opts: LMOpts | None = None, lo=None, hi=None,
            ws=None, stream=None):
     """Steps 1-5 for one stamp: (params, result dict).  Synchronises the stream."""
@@ -437,7 +464,8 @@ def evaluate_batch(d: Desc, batch: Batch, params, img, sig, psf, want_model=Fals
 
 def lm_fit_batch(d: Desc, batch: Batch, params, fixed, img, sig, psf,
                  opts: LMOpts | None = None, ws=None, stream=None):
-    """Steps 1-5 for a batch of stamps: (params [count, nslots], list of result dicts)."""
+    """Steps 1-5 for a batch of stamps: (params [count, nslots], Results: the per-stamp
+    result dicts, and each field as an array)."""
     p = np.array(params, np.float64, copy=True)
     fb = _fixed(fixed)
     res = (LMResult * batch.count)()
@@ -445,13 +473,13 @@ def lm_fit_batch(d: Desc, batch: Batch, params, fixed, img, sig, psf,
     _check(lib().gf_lm_fit_batch(C.byref(d), C.byref(batch), _dp(p), fb, _ptr(img), _ptr(sig),
                                  _ptr(psf), C.byref(opts) if opts is not None else None, res,
                                  w, n, _stream(stream)))
-    return p, [_res(r) for r in res]
+    return p, Results(res)
 
 
 def lm_fit_multistart(d: Desc, batch: Batch, starts, fixed, img, sig, psf,
                       opts: LMOpts | None = None, ws=None, stream=None):
     """Multi-start fits: starts is count x K x nslots; returns (params [count, nslots],
-    list of result dicts, best start index per stamp)."""
+    Results (the per-stamp result dicts), best start index per stamp)."""
     st = np.ascontiguousarray(np.asarray(starts, np.float64))
     assert st.ndim == 3 and st.shape[0] == batch.count
     K = st.shape[1]
@@ -465,7 +493,7 @@ def lm_fit_multistart(d: Desc, batch: Batch, starts, fixed, img, sig, psf,
                                       C.byref(opts) if opts is not None else None,
                                       _dp(p), res, best.ctypes.data_as(C.POINTER(C.c_int)),
                                       w, n, _stream(stream)))
-    return p, [_res(r) for r in res], best
+    return p, Results(res), best
 
 
 def evaluate_batch_dev(d: Desc, batch: Batch, params_dev, img, sig, psf, want_model=False,
