@@ -460,6 +460,7 @@ struct Layout {
         y_trial, part_jac, part_trial, active, exp, ctl, blob_end, total;
     size_t ids_static, n_static;            // the all-stamps work list (in the blob)
     size_t wl_n[2], wl_ids[2], wl_pre[2];   // LM work lists: 0 Jacobian pass, 1 trial pass
+    size_t wl_blk;                          // their per-CTA sums
     size_t tw_x, tw_y, hhat, psfgrid, spec_jac, spec_trial;
     size_t dft_buf[2], dft_mat;  // DFT path: ping-pong complex buffers, bf16 DFT matrices
     int count, nchan, nacc, nslots;
@@ -613,6 +614,8 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
             L.wl_pre[w] = o;
             o += al(sizeof(int) * (size_t)WK_KINDS * (count + 1));
         }
+        L.wl_blk = o;
+        o += al(sizeof(int) * (size_t)worklist_blocks(count) * (1 + WK_KINDS));
     }
     pl->method = resolve_method(d);
     if (pl->method == GF_CONV_FFT) {
@@ -1626,7 +1629,7 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
             ProfScope ps(PROF_LM, s);
             GF_CUDA(launch_worklist(L.count, lm, PH_NEED_JAC, base.pre_static,
                                     at<int>(ws, L.wl_n[0]), at<int>(ws, L.wl_ids[0]),
-                                    at<int>(ws, L.wl_pre[0]), s));
+                                    at<int>(ws, L.wl_pre[0]), at<int>(ws, L.wl_blk), s));
         }
         gf_status rr = jac_pass(aj, pl, ws, nullptr, nullptr, nullptr, nullptr, s);
         if (rr != GF_OK) return rr;
@@ -1635,7 +1638,7 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
             GF_CUDA(launch_final_solve(aj, at<Channel>(ws, L.chan_trial), active, L.rungs, s));
             GF_CUDA(launch_worklist(L.count, lm, PH_TRIAL, base.pre_static,
                                     at<int>(ws, L.wl_n[1]), at<int>(ws, L.wl_ids[1]),
-                                    at<int>(ws, L.wl_pre[1]), s));
+                                    at<int>(ws, L.wl_pre[1]), at<int>(ws, L.wl_blk), s));
         }
         if ((rr = trial_pass(at_, pl, ws, s, nullptr)) != GF_OK) return rr;
         ProfScope ps(PROF_LM, s);

@@ -637,9 +637,11 @@ cudaError_t launch_loop_ctl(int count, LMState* lm, int* active, LoopCtl* c,
 cudaError_t launch_final_chi2(const PassArgs& a, double* chi2_out, cudaStream_t s);
 cudaError_t launch_psf_sum(int count, const StampInfo* st, const float* psf, float* out,
                            cudaStream_t s);
-// the work list of the stamps whose LM phase is `phase`
+// the work list of the stamps whose LM phase is `phase`; blk: scratch of
+// worklist_blocks(count) x (1 + WK_KINDS) ints
+int worklist_blocks(int count);
 cudaError_t launch_worklist(int count, const LMState* lm, int phase, const int* pre_static,
-                            int* n, int* ids, int* pre, cudaStream_t s);
+                            int* n, int* ids, int* pre, int* blk, cudaStream_t s);
 
 // parameter / channel preparation and the LM steps (lm.cu)
 cudaError_t launch_prep_sum(const PassArgs& a, const double* params, int use_trial,

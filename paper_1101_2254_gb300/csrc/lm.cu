@@ -841,71 +841,103 @@ __global__ void k_lm_export(int count, const Structure* Sp, const LMState* lm, d
     o[ns + 4] = L.status;
 }
 
-// One block builds a pass's work list: stamp b is listed when its LM phase is
-// `phase`; for each kernel kind, pre[k][i] sums the static block counts of the
-// listed stamps before the i-th (block-wide exclusive scans).
+// The work list of one LM phase: the ids of the stamps in that phase, in
+// increasing order, and for each work kind the exclusive prefix sums of their
+// blocks (pre[k][i] = blocks of kind k of the listed stamps before the i-th).
+// Two coalesced passes over the stamps, 1024 per CTA: k_worklist_count sums each
+// CTA's listed stamps and blocks, k_worklist_write adds the earlier CTAs' sums
+// and scans its own stamps (warp shuffles, then across warps).
 constexpr int WL_THREADS = 1024;
+constexpr int WLQ = 1 + WK_KINDS;  // listed stamps, then blocks of each kind
 
-__global__ void __launch_bounds__(WL_THREADS) k_worklist(int count, const LMState* lm, int phase,
-                                                         const int* pst, int* n_out, int* ids,
-                                                         int* pre)
+// this thread's stamp: 1 and its blocks of each kind if it is in `phase`
+__device__ __forceinline__ void wl_item(int count, const LMState* lm, int phase, const int* pst, int b,
+                                        int (&v)[WLQ])
 {
-    pdl_entry();
-    __shared__ int wsum[WL_THREADS / 32][1 + WK_KINDS];
-    const int per = (count + WL_THREADS - 1) / WL_THREADS;
-    const int b0 = min(count, (int)threadIdx.x * per), b1 = min(count, b0 + per);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int loc[1 + WK_KINDS];
-    for (int q = 0; q <= WK_KINDS; ++q) loc[q] = 0;
-    for (int b = b0; b < b1; ++b) {
-        if (lm[b].phase != phase) continue;
-        loc[0] += 1;
-        for (int k = 0; k < WK_KINDS; ++k)
-            loc[1 + k] += pst[k * (count + 1) + b + 1] - pst[k * (count + 1) + b];
+    for (int q = 0; q < WLQ; ++q) v[q] = 0;
+    if (b < count && lm[b].phase == phase) {
+        v[0] = 1;
+        for (int k = 0; k < WK_KINDS; ++k) v[1 + k] = pst[k * (count + 1) + b + 1] - pst[k * (count + 1) + b];
     }
-    int incl[1 + WK_KINDS];
-    for (int q = 0; q <= WK_KINDS; ++q) {
-        int v = loc[q];
+}
+
+// block-wide exclusive scan of v (excl) and the block's totals (tot)
+__device__ __forceinline__ void wl_block_scan(const int (&v)[WLQ], int (&excl)[WLQ], int (&tot)[WLQ],
+                                              int (*wsum)[WLQ])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl[WLQ];
+    for (int q = 0; q < WLQ; ++q) {
+        int x = v[q];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(kFull, v, o);
-            if (lane >= o) v += u;
+            const int u = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += u;
         }
-        incl[q] = v;
-        if (lane == 31) wsum[warp][q] = v;
+        incl[q] = x;
+        if (lane == 31) wsum[warp][q] = x;
     }
     __syncthreads();
     if (warp == 0) {
-        for (int q = 0; q <= WK_KINDS; ++q) {
-            const int x = wsum[lane][q];
-            int v = x;
+        for (int q = 0; q < WLQ; ++q) {
+            const int x0 = wsum[lane][q];
+            int x = x0;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(kFull, v, o);
-                if (lane >= o) v += u;
+                const int u = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += u;
             }
-            wsum[lane][q] = v - x;  // exclusive over warps
+            wsum[lane][q] = x - x0;  // exclusive over warps
+            if (lane == 31) wsum[32][q] = x;  // the block's total
         }
     }
     __syncthreads();
-    int excl[1 + WK_KINDS];
-    for (int q = 0; q <= WK_KINDS; ++q) excl[q] = incl[q] - loc[q] + wsum[warp][q];
-    int pos = excl[0];
-    int c[WK_KINDS];
-    for (int k = 0; k < WK_KINDS; ++k) c[k] = excl[1 + k];
-    for (int b = b0; b < b1; ++b) {
-        if (lm[b].phase != phase) continue;
-        ids[pos] = b;
-        for (int k = 0; k < WK_KINDS; ++k) {
-            pre[k * (count + 1) + pos] = c[k];
-            c[k] += pst[k * (count + 1) + b + 1] - pst[k * (count + 1) + b];
-        }
-        ++pos;
+    for (int q = 0; q < WLQ; ++q) {
+        excl[q] = incl[q] - v[q] + wsum[warp][q];
+        tot[q] = wsum[32][q];
     }
-    if (threadIdx.x == WL_THREADS - 1) {
-        const int n = excl[0] + loc[0];
+}
+
+__global__ void __launch_bounds__(WL_THREADS) k_worklist_count(int count, const LMState* lm, int phase,
+                                                               const int* pst, int* blk)
+{
+    pdl_entry();
+    __shared__ int wsum[WL_THREADS / 32 + 1][WLQ];
+    int v[WLQ], excl[WLQ], tot[WLQ];
+    wl_item(count, lm, phase, pst, blockIdx.x * WL_THREADS + threadIdx.x, v);
+    wl_block_scan(v, excl, tot, wsum);
+    if (threadIdx.x < WLQ) blk[blockIdx.x * WLQ + threadIdx.x] = tot[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(WL_THREADS) k_worklist_write(int count, const LMState* lm, int phase,
+                                                               const int* pst, const int* blk, int* n_out,
+                                                               int* ids, int* pre)
+{
+    pdl_entry();
+    __shared__ int wsum[WL_THREADS / 32 + 1][WLQ];
+    __shared__ int base[WLQ];
+    // the earlier CTAs' totals (a warp per quantity)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < WLQ) {
+        int x = 0;
+        for (int j = lane; j < (int)blockIdx.x; j += 32) x += blk[j * WLQ + warp];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        if (lane == 0) base[warp] = x;
+    }
+    const int b = blockIdx.x * WL_THREADS + threadIdx.x;
+    int v[WLQ], excl[WLQ], tot[WLQ];
+    wl_item(count, lm, phase, pst, b, v);
+    wl_block_scan(v, excl, tot, wsum);  // (its barriers also publish base)
+    if (v[0]) {
+        const int pos = base[0] + excl[0];
+        ids[pos] = b;
+        for (int k = 0; k < WK_KINDS; ++k) pre[k * (count + 1) + pos] = base[1 + k] + excl[1 + k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        const int n = base[0] + tot[0];
         *n_out = n;
-        for (int k = 0; k < WK_KINDS; ++k) pre[k * (count + 1) + n] = excl[1 + k] + loc[1 + k];
+        for (int k = 0; k < WK_KINDS; ++k) pre[k * (count + 1) + n] = base[1 + k] + tot[1 + k];
     }
 }
 
@@ -1023,10 +1055,16 @@ cudaError_t launch_lm_export(int count, const Structure* S, const LMState* lm, d
     return cudaGetLastError();
 }
 
+int worklist_blocks(int count) { return (count + WL_THREADS - 1) / WL_THREADS; }
+
 cudaError_t launch_worklist(int count, const LMState* lm, int phase, const int* pre_static,
-                            int* n, int* ids, int* pre, cudaStream_t s)
+                            int* n, int* ids, int* pre, int* blk, cudaStream_t s)
 {
-    GF_LAUNCH_PDL(k_worklist, dim3(1), dim3(WL_THREADS), 0, s, count, lm, phase, pre_static, n, ids, pre);
+    const int g = worklist_blocks(count);
+    GF_LAUNCH_PDL(k_worklist_count, dim3(g), dim3(WL_THREADS), 0, s, count, lm, phase, pre_static, blk);
+    GF_COUNT_LAUNCH();
+    GF_LAUNCH_PDL(k_worklist_write, dim3(g), dim3(WL_THREADS), 0, s, count, lm, phase, pre_static, blk, n,
+                  ids, pre);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
