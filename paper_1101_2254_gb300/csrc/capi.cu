@@ -468,6 +468,7 @@ struct Layout {
     int tot_model, tot_os, tot_conv, tot_red, tot_conv32;
     int max_red;  // most reduction blocks of one stamp
     long long tot_wb;  // 16 x 32 output blocks of all stamps (the fused trial chi^2's partials)
+    long long max_wb;  // ... and the most of one stamp
     int conv_ty, conv_cap;  // direct convolution: tile height, persistent CTAs per SM
     int eval_variant;  // the model kernels' evaluator: 0 Sersic / disk / Gaussian,
                        // 1 with Moffat, 2 with King, Nuker or point sources
@@ -496,7 +497,7 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     int* pr = pl->pre.data() + WK_RED * (count + 1);
     int* pc32 = pl->pre.data() + WK_CONV32 * (count + 1);
     int max_red = 0;
-    long long e1 = 0, y1 = 0, wb = 0;
+    long long e1 = 0, y1 = 0, wb = 0, max_wb = 0;
     const ConvShape shape = conv_shape(P);
     for (int b = 0; b < count; ++b) {
         StampInfo& s = pl->st[b];
@@ -529,12 +530,15 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         pc32[b + 1] = pc32[b] + (s.conv_tw == 32 ? conv_tiles : 0);
         pr[b + 1] = pr[b] + (int)(((long long)s.H * s.W + RED_PIX - 1) / RED_PIX);
         s.wb_off = (int)std::min<long long>(wb, INT32_MAX);
-        wb += (long long)((s.H + 15) / 16) * ((s.W + 31) / 32);
+        const long long nwb = (long long)((s.H + 15) / 16) * ((s.W + 31) / 32);
+        wb += nwb;
+        max_wb = std::max<long long>(max_wb, nwb);
         max_red = std::max(max_red, pr[b + 1] - pr[b]);
     }
     Layout& L = pl->L;
     memset(&L, 0, sizeof(L));
     L.max_red = max_red;
+    L.max_wb = max_wb;
     L.tot_wb = wb;
     L.conv_ty = shape.ty;
     L.conv_cap = shape.ctas_per_sm;
@@ -714,6 +718,7 @@ PassArgs base_args(void* ws, const Layout& L, const float* psf, const float* img
     const int* pre = at<int>(ws, L.pre);
     a.pre_static = pre;
     a.max_red = L.max_red;
+    a.max_trial_slots = L.max_red;
     a.wl.n = at<int>(ws, L.n_static);
     a.wl.ids = at<int>(ws, L.ids_static);
     a.wl.pre = pre;
@@ -1610,6 +1615,7 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     set_grids(at_, L, L.rungs);
     // the direct path reduces the trial chi^2 inside the convolution's epilogue
     at_.conv_chi2 = pl.method == GF_CONV_DIRECT ? 1 : 0;
+    if (at_.conv_chi2) at_.max_trial_slots = (int)std::min<long long>(L.max_wb, INT32_MAX);
     // each pass walks the list of stamps in its phase, rebuilt every body
     aj.wl.n = at<int>(ws, L.wl_n[0]);
     aj.wl.ids = at<int>(ws, L.wl_ids[0]);

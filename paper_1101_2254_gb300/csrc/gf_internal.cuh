@@ -546,6 +546,8 @@ struct PassArgs {
     int eval_variant;          // 0 Sersic/disk/Gaussian, 1 with Moffat, 2 with King/Nuker/point
     int os_ns;                 // sub-samples per oversampled pixel (os_factor^2)
     int conv_ty;               // direct-convolution tile height (32 or 16)
+    int max_trial_slots;       // most trial-pass partial slots of one stamp (reduce blocks, or
+                               // 16 x 32 output blocks with conv_chi2)
     int conv_chi2;             // an LM trial pass on the direct path: the convolution writes the
                                // chi^2 partial of each 16 x 32 output block per rung (channel),
                                // slot st.wb_off + block, instead of the convolved tile

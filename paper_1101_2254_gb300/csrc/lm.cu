@@ -743,50 +743,13 @@ __global__ void __launch_bounds__(32 * GF_MAX_LADDER) k_final_solve(PassArgs a, 
 // rung), then apply the rule rung by rung: a rejected trial grows lambda and
 // passes to the next rung, an accepted one (or a finishing criterion) ends the
 // walk.  Every stamp not yet done adds one to the active counter.
-__global__ void __launch_bounds__(RED_THREADS) k_final_update(PassArgs a, int* active)
+// The trial ladder's rule for one stamp, given each rung's chi^2 (x2r): a
+// rejected trial grows lambda and passes to the next rung, an accepted one (or
+// a finishing criterion) ends the walk; a stamp not yet done adds one to the
+// active counter.  One thread.
+__device__ void lm_apply_trials(const PassArgs& a, LMState& L, int phase, int nr, const double* x2r,
+                                int* active)
 {
-    pdl_entry();
-    __shared__ CSum wsum[RED_THREADS / 32];
-    __shared__ double x2r[GF_MAX_LADDER];
-    const int b = blockIdx.x;
-    LMState& L = a.lm[b];
-    const int phase = L.phase;
-    const int nr = a.nchan;  // rungs of the trial pass
-    if (phase == PH_TRIAL) {
-        // the stamp's partial slots: its reduce blocks, or its 16 x 32 output
-        // blocks when the direct convolution reduced the trial
-        int b0, b1;
-        if (a.conv_chi2) {
-            const StampInfo& st = a.st[b];
-            b0 = st.wb_off;
-            b1 = b0 + ((st.H + 15) / 16) * ((st.W + 31) / 32);
-        } else {
-            const int* pst = a.pre_static + WK_RED * (a.count + 1);
-            b0 = pst[b];
-            b1 = pst[b + 1];
-        }
-        for (int r = L.rung0; r < nr; ++r) {
-            CSum acc = {0.0f, 0.0f};
-            for (int k = b0 + threadIdx.x; k < b1; k += RED_THREADS)
-                csum_add(acc, a.partial[(long long)k * nr + r]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                CSum other;
-                other.s = __shfl_down_sync(kFull, acc.s, o);
-                other.c = __shfl_down_sync(kFull, acc.c, o);
-                acc = csum_merge(acc, other);
-            }
-            if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                CSum t = wsum[0];
-                for (int w = 1; w < RED_THREADS / 32; ++w) t = csum_merge(t, wsum[w]);
-                x2r[r] = (double)t.s + (double)t.c;
-            }
-            __syncthreads();
-        }
-    }
-    if (threadIdx.x != 0) return;
     const Structure& S = *a.S;
     if (phase == PH_TRIAL) {
         for (int r = L.rung0; r < nr; ++r) {
@@ -823,6 +786,92 @@ __global__ void __launch_bounds__(RED_THREADS) k_final_update(PassArgs a, int* a
         }
     }
     if (active && L.phase != PH_DONE) atomicAdd(active, 1);
+}
+
+// the stamp's partial slots of a trial pass: its reduce blocks, or its 16 x 32
+// output blocks when the direct convolution reduced the trial
+__device__ __forceinline__ void trial_slots(const PassArgs& a, int b, int& b0, int& b1)
+{
+    if (a.conv_chi2) {
+        const StampInfo& st = a.st[b];
+        b0 = st.wb_off;
+        b1 = b0 + ((st.H + 15) / 16) * ((st.W + 31) / 32);
+    } else {
+        const int* pst = a.pre_static + WK_RED * (a.count + 1);
+        b0 = pst[b];
+        b1 = pst[b + 1];
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_final_update(PassArgs a, int* active)
+{
+    pdl_entry();
+    __shared__ CSum wsum[RED_THREADS / 32];
+    __shared__ double x2r[GF_MAX_LADDER];
+    const int b = blockIdx.x;
+    LMState& L = a.lm[b];
+    const int phase = L.phase;
+    const int nr = a.nchan;  // rungs of the trial pass
+    if (phase == PH_TRIAL) {
+        int b0, b1;
+        trial_slots(a, b, b0, b1);
+        for (int r = L.rung0; r < nr; ++r) {
+            CSum acc = {0.0f, 0.0f};
+            for (int k = b0 + threadIdx.x; k < b1; k += RED_THREADS)
+                csum_add(acc, a.partial[(long long)k * nr + r]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                CSum other;
+                other.s = __shfl_down_sync(kFull, acc.s, o);
+                other.c = __shfl_down_sync(kFull, acc.c, o);
+                acc = csum_merge(acc, other);
+            }
+            if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                CSum t = wsum[0];
+                for (int w = 1; w < RED_THREADS / 32; ++w) t = csum_merge(t, wsum[w]);
+                x2r[r] = (double)t.s + (double)t.c;
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x != 0) return;
+    lm_apply_trials(a, L, phase, nr, x2r, active);
+}
+
+// The same for batches whose stamps have at most 32 partial slots each: a warp
+// per stamp, 8 stamps per CTA.  Lane l holds slot l, and the warp's shuffle
+// tree is the block-wide kernel's (whose other warps then add zeros), so the
+// chi^2 are the same bits.
+__global__ void __launch_bounds__(RED_THREADS) k_final_update_w(PassArgs a, int* active)
+{
+    pdl_entry();
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (RED_THREADS / 32) + (threadIdx.x >> 5);
+    if (b >= a.count) return;  // the whole warp
+    LMState& L = a.lm[b];
+    const int phase = L.phase;
+    const int nr = a.nchan;
+    double x2r[GF_MAX_LADDER];
+    if (phase == PH_TRIAL) {
+        int b0, b1;
+        trial_slots(a, b, b0, b1);
+        for (int r = L.rung0; r < nr; ++r) {
+            CSum acc = {0.0f, 0.0f};
+            if (b0 + lane < b1) csum_add(acc, a.partial[(long long)(b0 + lane) * nr + r]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                CSum other;
+                other.s = __shfl_down_sync(kFull, acc.s, o);
+                other.c = __shfl_down_sync(kFull, acc.c, o);
+                acc = csum_merge(acc, other);
+            }
+            x2r[r] = (double)acc.s + (double)acc.c;
+        }
+    }
+    if (lane != 0) return;
+    lm_apply_trials(a, L, phase, nr, x2r, active);
 }
 
 // compact per-stamp results: p[nslots], chi2, lambda, iters, accepted, status
@@ -1042,7 +1091,13 @@ cudaError_t launch_final_solve(const PassArgs& a, Channel* trial_chan, int* acti
 
 cudaError_t launch_final_update(const PassArgs& a, int* active_count, cudaStream_t s)
 {
-    GF_LAUNCH_PDL(k_final_update, dim3(a.count), dim3(RED_THREADS), 0, s, a, active_count);
+    if (a.max_trial_slots <= 32) {
+        const int per = RED_THREADS / 32;
+        GF_LAUNCH_PDL(k_final_update_w, dim3((a.count + per - 1) / per), dim3(RED_THREADS), 0, s, a,
+                      active_count);
+    } else {
+        GF_LAUNCH_PDL(k_final_update, dim3(a.count), dim3(RED_THREADS), 0, s, a, active_count);
+    }
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }

@@ -504,6 +504,55 @@ __global__ void __launch_bounds__(32 * FINAL_SEG_MAX) k_final_jac(PassArgs a, do
     }
 }
 
+// k_final_jac for batches whose stamps all sum in one segment (fewer than 8
+// reduce blocks each): a warp per (stamp, 32 accumulators), 8 stamps per CTA,
+// each summed in the order of the one-segment case above (the same bits).
+__global__ void __launch_bounds__(256) k_final_jac_w(PassArgs a, double* A_out, double* g_out,
+                                                     double* chi2_out)
+{
+    pdl_entry();
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (b >= a.count) return;
+    if (a.lm && a.lm[b].phase != a.phase) return;
+    const int nacc = a.nacc;
+    const int t = blockIdx.y * 32 + lane;
+    if (t >= nacc) return;
+    const int* pst = a.pre_static + WK_RED * (a.count + 1);
+    const int b0 = pst[b], b1 = pst[b + 1];
+    CSum acc = {0.0f, 0.0f};
+    const float* src = a.partial + t;
+    int k = b0;
+    for (; k + 3 < b1; k += 4) {
+        const float v0 = src[(long long)k * nacc];
+        const float v1 = src[(long long)(k + 1) * nacc];
+        const float v2 = src[(long long)(k + 2) * nacc];
+        const float v3 = src[(long long)(k + 3) * nacc];
+        csum_add(acc, v0);
+        csum_add(acc, v1);
+        csum_add(acc, v2);
+        csum_add(acc, v3);
+    }
+    for (; k < b1; ++k) csum_add(acc, src[(long long)k * nacc]);
+    const double v = (double)acc.s + (double)acc.c;
+    const int nf = a.S->nfree;
+    int i, j;
+    const int kind = decode_acc(t, nf, i, j);
+    double* A = a.lm ? a.lm[b].A : A_out + (long long)b * nf * nf;
+    double* g = a.lm ? a.lm[b].g : g_out + (long long)b * nf;
+    if (kind == 0) {
+        A[i * nf + j] = v;
+        A[j * nf + i] = v;
+    } else if (kind == 1) {
+        g[i] = v;
+    } else {
+        if (a.lm)
+            a.lm[b].chi2 = v;
+        else
+            chi2_out[b] = v;
+    }
+}
+
 __global__ void __launch_bounds__(RED_THREADS) k_final_chi2(PassArgs a, double* chi2_out)
 {
     pdl_entry();
@@ -599,6 +648,12 @@ cudaError_t launch_reduce_rungs(const PassArgs& a, cudaStream_t s)
 cudaError_t launch_final_jac(const PassArgs& a, double* A_out, double* g_out, double* chi2_out,
                              cudaStream_t s)
 {
+    if (final_nseg(a.max_red) == 1) {
+        const dim3 grid((a.count + 7) / 8, (a.nacc + 31) / 32);
+        GF_LAUNCH_PDL(k_final_jac_w, dim3(grid), dim3(256), 0, s, a, A_out, g_out, chi2_out);
+        GF_COUNT_LAUNCH();
+        return cudaGetLastError();
+    }
     const dim3 grid(a.count, (a.nacc + 31) / 32);
     GF_LAUNCH_PDL(k_final_jac, dim3(grid), dim3(32 * final_nseg(a.max_red)), 0, s, a, A_out, g_out, chi2_out);
     GF_COUNT_LAUNCH();
