@@ -24,6 +24,7 @@
 
 #include <algorithm>
 
+#include "bn.cuh"
 #include "cnn.cuh"
 #include "gf_internal.cuh"
 
@@ -501,28 +502,32 @@ __global__ void __launch_bounds__(256) k_train_sample(unsigned long long seed, d
     __shared__ double red[256];
     __shared__ double s_alpha;
     const int b = blockIdx.x;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // warp 0: every lane draws the same values; the warp solves for b_n
         const uint2 key = key_of(seed);
         const uint4 r0 = philox(make_uint4((unsigned)b, 0u, 2u, 0u), key);
         const uint4 r1 = philox(make_uint4((unsigned)b, 1u, 2u, 0u), key);
         const double c = 0.5 * (SIDE - 1);
         const double n = 0.5 + 5.5 * unit(r0.z);
+        const double bn = sersic_bn_warp(n, -1.0);
         const double re = exp(log(2.0) + (log(40.0) - log(2.0)) * unit(r0.w));
         const double q = 0.2 + 0.8 * unit(r1.x);
         const double pa = 180.0 * unit(r1.y);
         const double F = exp(log(1e2) + (log(1e5) - log(1e2)) * unit(r1.z));
         const double fwhm = 2.0 + 3.0 * unit(r1.w);
         double* p = params + 9 * (long long)b;
-        p[0] = c - 1.0 + 2.0 * unit(r0.x);
-        p[1] = c - 1.0 + 2.0 * unit(r0.y);
-        p[2] = F / sersic_flux(1.0, re, n, q);
-        p[3] = re;
-        p[4] = n;
-        p[5] = q;
-        p[6] = pa;
-        p[7] = 0.0;
-        p[8] = 0.05;
-        s_alpha = fwhm / (2.0 * sqrt(exp2(1.0 / 3.0) - 1.0));
+        if (threadIdx.x == 0) {
+            p[0] = c - 1.0 + 2.0 * unit(r0.x);
+            p[1] = c - 1.0 + 2.0 * unit(r0.y);
+            p[2] = F / sersic_flux_e(1.0, re, n, q, exp(bn + lgamma(2.0 * n) - 2.0 * n * log(bn)));
+            p[3] = re;
+            p[4] = n;
+            p[5] = q;
+            p[6] = pa;
+            p[7] = 0.0;
+            p[8] = 0.05;
+            s_alpha = fwhm / (2.0 * sqrt(exp2(1.0 / 3.0) - 1.0));
+        }
     }
     __syncthreads();
     const int c = psf_size / 2, np = psf_size * psf_size;
@@ -548,18 +553,22 @@ __global__ void __launch_bounds__(256) k_train_sample(unsigned long long seed, d
 }
 
 // targets of the first Sersic component (slots 0..6 of a stamp's parameters)
+// a warp per stamp (the warp solves for b_n), lane 0 writes the targets
 __global__ void k_encode(const double* __restrict__ params, int nslots, int count, int H, int W,
                          float* __restrict__ t)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= count) return;
+    const int b = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (b >= count) return;  // the whole warp
     const double* p = params + (long long)b * nslots;
+    const double bn = sersic_bn_warp(p[4], -1.0);
+    if ((threadIdx.x & 31) != 0) return;
     const double l10 = log(10.0);
     const double th = 2.0 * p[6] * M_PI / 180.0;
     float* o = t + (long long)b * NOUT;
     o[0] = (float)(p[0] - 0.5 * (W - 1));
     o[1] = (float)(p[1] - 0.5 * (H - 1));
-    o[2] = (float)((log(sersic_flux(p[2], p[3], p[4], p[5])) - 3.5 * l10) / (1.5 * l10));
+    const double e = exp(bn + lgamma(2.0 * p[4]) - 2.0 * p[4] * log(bn));
+    o[2] = (float)((log(sersic_flux_e(p[2], p[3], p[4], p[5], e)) - 3.5 * l10) / (1.5 * l10));
     o[3] = (float)((log(p[3]) - 0.5 * log(80.0)) / (0.5 * log(20.0)));
     o[4] = (float)((p[4] - 3.25) / 2.75);
     o[5] = (float)((p[5] - 0.6) / 0.4);
@@ -914,7 +923,7 @@ cudaError_t cnn_input(const float* img, const float* sig, int B, float* x, cudaS
 cudaError_t cnn_encode(const double* params, int nslots, int count, int H, int W, float* t,
                        cudaStream_t s)
 {
-    k_encode<<<blocks(count, 128), 128, 0, s>>>(params, nslots, count, H, W, t);
+    k_encode<<<blocks((long long)count * 32, 128), 128, 0, s>>>(params, nslots, count, H, W, t);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
