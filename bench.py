@@ -134,6 +134,9 @@ def parse():
                          "method's own) or analytic derivatives")
     ap.add_argument("--reach-sample", type=int, default=256,
                     help="learned65536: stamps the oracle checks for reaching its chi2")
+    ap.add_argument("--ladder", type=int, default=None,
+                    help="rungs of the LM trial ladder (gf_lm_opts.ladder; fits are the same "
+                         "for any value, only the passes differ); default: the library's")
     ap.add_argument("--lm-tol", type=float, default=BENCH_TOL,
                     help="LM ftol and xtol of the timed fits")
     ap.add_argument("--batch-sample", type=int, default=32,
@@ -223,6 +226,15 @@ def measured_peaks():
             return json.load(fh), "measured"
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def lm_opts(gf, args):
+    """The LM options of a workload: the benchmark's tolerance, Jacobian mode and
+    (when given) trial-ladder length."""
+    kw = dict(ftol=args.lm_tol, xtol=args.lm_tol, jac_mode=jac_mode(gf, args))
+    if args.ladder is not None:
+        kw["ladder"] = args.ladder
+    return gf.default_opts(**kw)
 
 
 # ------------------------------------------------------------------ the GPU arm
@@ -360,7 +372,7 @@ def run_gf(args):
 
     # the metric counts fits that reach the oracle's chi^2; ftol = xtol = 1e-6
     # does (tests/test_gpu_parity.py checks it on this stamp)
-    opts = gf.default_opts(ftol=args.lm_tol, xtol=args.lm_tol, jac_mode=jac_mode(gf, args))
+    opts = lm_opts(gf, args)
 
     def fit():
         return gf.lm_fit(d, p0, st.fixed, img_d, sig_d, psf_d, opts=opts, ws=ws)
@@ -636,7 +648,7 @@ def run_batch(args):
     ws = gf.Workspace(device=dev)
     stream = torch.cuda.current_stream()
 
-    opts = gf.default_opts(ftol=args.lm_tol, xtol=args.lm_tol, jac_mode=jac_mode(gf, args))
+    opts = lm_opts(gf, args)
 
     def fit(i_d=img_d, s_d=sig_d, p_d=psf_d):
         return gf.lm_fit_batch(d, batch, p0, s0.fixed, i_d, s_d, p_d, opts=opts, ws=ws)
@@ -723,6 +735,7 @@ def run_batch(args):
             "config": {"workload": "batch4096", "stamps": n,
                        "pixels": int(sum(h * w for h, w in zip(Hs, Ws))), "psf": s0.P,
                        "conv": "direct", "free_params": s0.nfree, "lm_tol": args.lm_tol,
+                       "ladder": int(opts.ladder),
                        "jacobian": args.jac,
                        "tile_width_by_class": tiles,
                        "tile_height": shape[1], "conv_ctas_per_sm": shape[2],
@@ -824,7 +837,7 @@ def run_cube(args):
     start = cube.guess()
     start_d = torch.as_tensor(start).to(dev)
     out_d = torch.empty_like(start_d)
-    opts = gf.default_opts(ftol=args.lm_tol, xtol=args.lm_tol, jac_mode=jac_mode(gf, args))
+    opts = lm_opts(gf, args)
     stream = torch.cuda.current_stream()
 
     def fit():
@@ -997,7 +1010,7 @@ def run_learned(args):
     d = learned.stamp_desc()
     fixed = np.zeros(9, np.uint8)
     fixed[7] = 1
-    opts = gf.default_opts(ftol=args.lm_tol, xtol=args.lm_tol, jac_mode=jac_mode(gf, args))
+    opts = lm_opts(gf, args)
     ws = gf.Workspace(device=dev)
     ws_lm = gf.Workspace(device=dev)
     # untimed setup: the direct convolution's launch shape tuned on these stamps
@@ -1117,6 +1130,7 @@ def run_learned(args):
             "config": {"workload": "learned65536" if count == 65536 else f"learned{count}",
                        "stamps": count, "side": 64, "train_stamps": train_steps * train_batch,
                        "psf": learned.PSF_SIZE, "free_params": 8, "lm_tol": args.lm_tol,
+                       "ladder": int(opts.ladder),
                        "jacobian": args.jac,
                        "start": "CNN (bf16) with default-guess fallback by chi2",
                        "conv_tile": {"width": shape[0], "height": shape[1],

@@ -51,7 +51,24 @@ __device__ __forceinline__ void load_channels(Channel* dst, const Channel* src, 
     }
 }
 
+// ceil(2^32 / d) for d > 1 (0 for d = 1): with it, div_mag gives floor(x / d)
+// by a multiply-high and one correction instead of a division
+__device__ __forceinline__ unsigned mag_of(int d)
+{
+    return d > 1 ? (unsigned)(((1ull << 32) + (unsigned long long)d - 1ull) / (unsigned long long)d) : 0u;
+}
+// floor(x / d) for 0 <= x < 2^31: the multiply-high is floor(x / d) or one more
+__device__ __forceinline__ int div_mag(int x, int d, unsigned mag)
+{
+    if (mag == 0u) return x;
+    int q = (int)__umulhi((unsigned)x, mag);
+    if ((long long)q * d > (long long)x) --q;
+    return q;
+}
+
 // Work item = (channel, block of MODEL_THREADS grid pixels of a listed stamp).
+// A CTA's items are consecutive, so the (channel, block) pair advances by a
+// counter instead of a division per item.
 template <int EV>
 __device__ __forceinline__ void body_model(const PassArgs& a, int vb, int vg)
 {
@@ -62,14 +79,26 @@ __device__ __forceinline__ void body_model(const PassArgs& a, int vb, int vg)
     const long long items = (long long)tot * a.nchan;
     int hint = -1, cur_b = -1, cur_k = -1;
     StampInfo st;
+    unsigned mag = 0u;
     const long long chunk = (items + vg - 1) / vg;
     const long long it0 = (long long)vb * chunk, it1 = min(items, it0 + chunk);
-    for (long long it = it0; it < it1; ++it) {
-        const int k = (int)(it / tot), blk = (int)(it - (long long)k * tot);
+    int k = 0, blk = 0;
+    if (it0 < it1) {
+        k = (int)(it0 / tot);
+        blk = (int)(it0 - (long long)k * tot);
+    }
+    for (long long it = it0; it < it1; ++it, ++blk) {
+        if (blk == tot) {
+            blk = 0;
+            ++k;
+        }
         const int li = wl_locate(pre, n, blk, hint);
         const int b = a.wl.ids[li];
         if (b != cur_b || k != cur_k) {
-            if (b != cur_b) st = a.st[b];  // the stamp's geometry, kept while it lasts
+            if (b != cur_b) {  // the stamp's geometry, kept while it lasts
+                st = a.st[b];
+                mag = mag_of(st.We);
+            }
             __syncthreads();
             load_channel(&ch, &a.chan[(long long)b * a.chan_stride + k]);
             __syncthreads();
@@ -81,7 +110,7 @@ __device__ __forceinline__ void body_model(const PassArgs& a, int vb, int vg)
         bool write = pix < npix;
         int i = 0, j = 0;
         if (write) {
-            const int ie = pix / st.We, je = pix - ie * st.We;
+            const int ie = div_mag(pix, st.We, mag), je = pix - ie * st.We;
             i = ie - st.c;
             j = je - st.c;
             write = !(st.os_factor > 1 && i >= st.os_y0 && i < st.os_y0 + st.os_box &&
@@ -110,8 +139,16 @@ __device__ __forceinline__ void body_model_os(const PassArgs& a, int vb, int vg)
     int hint = -1, cur_b = -1, cur_k = -1;
     const long long chunk = (items + vg - 1) / vg;
     const long long it0 = (long long)vb * chunk, it1 = min(items, it0 + chunk);
-    for (long long it = it0; it < it1; ++it) {
-        const int k = (int)(it / tot), blk = (int)(it - (long long)k * tot);
+    int k = 0, blk = 0;
+    if (it0 < it1) {
+        k = (int)(it0 / tot);
+        blk = (int)(it0 - (long long)k * tot);
+    }
+    for (long long it = it0; it < it1; ++it, ++blk) {
+        if (blk == tot) {
+            blk = 0;
+            ++k;
+        }
         const int li = wl_locate(pre, n, blk, hint);
         const int b = a.wl.ids[li];
         const StampInfo st = a.st[b];
@@ -184,6 +221,7 @@ __device__ __forceinline__ void body_model_jac(const PassArgs& a, int vb, int vg
     const int tot = pre[n];
     const int nch = a.nchan;
     int hint = -1, cur_b = -1;
+    unsigned mag = 0u;  // the stamp width's reciprocal for div_mag
     const int chunk = (tot + vg - 1) / vg;
     const int it0 = vb * chunk, it1 = min(tot, it0 + chunk);
     for (int blk = it0; blk < it1; ++blk) {
@@ -191,6 +229,7 @@ __device__ __forceinline__ void body_model_jac(const PassArgs& a, int vb, int vg
         const int b = a.wl.ids[li];
         const StampInfo st = a.st[b];
         if (b != cur_b) {
+            mag = mag_of(st.We);
             __syncthreads();
             load_channels(chs, &a.chan[(long long)b * a.chan_stride], nch);
             __syncthreads();
@@ -201,7 +240,7 @@ __device__ __forceinline__ void body_model_jac(const PassArgs& a, int vb, int vg
         bool write = pix < npix;
         int i = 0, j = 0;
         if (write) {
-            const int ie = pix / st.We, je = pix - ie * st.We;
+            const int ie = div_mag(pix, st.We, mag), je = pix - ie * st.We;
             i = ie - st.c;
             j = je - st.c;
             write = !(st.os_factor > 1 && i >= st.os_y0 && i < st.os_y0 + st.os_box &&
@@ -238,6 +277,7 @@ __device__ __forceinline__ void body_model_jac_an(const PassArgs& a, int vb, int
     const int tot = pre[n];
     const int nch = a.nchan;
     int hint = -1, cur_b = -1;
+    unsigned mag = 0u;  // the stamp width's reciprocal for div_mag
     StampInfo st;
     const int chunk = (tot + vg - 1) / vg;
     const int it0 = vb * chunk, it1 = min(tot, it0 + chunk);
@@ -246,6 +286,7 @@ __device__ __forceinline__ void body_model_jac_an(const PassArgs& a, int vb, int
         const int b = a.wl.ids[li];
         if (b != cur_b) {
             st = a.st[b];
+            mag = mag_of(st.We);
             __syncthreads();
             load_channels(chs, &a.chan[(long long)b * a.chan_stride], nch);
             __syncthreads();
@@ -273,7 +314,7 @@ __device__ __forceinline__ void body_model_jac_an(const PassArgs& a, int vb, int
         bool write = pix < npix;
         int i = 0, j = 0;
         if (write) {
-            const int ie = pix / st.We, je = pix - ie * st.We;
+            const int ie = div_mag(pix, st.We, mag), je = pix - ie * st.We;
             i = ie - st.c;
             j = je - st.c;
             write = !(st.os_factor > 1 && i >= st.os_y0 && i < st.os_y0 + st.os_box &&
