@@ -735,7 +735,7 @@ def run_batch(args):
             "config": {"workload": "batch4096", "stamps": n,
                        "pixels": int(sum(h * w for h, w in zip(Hs, Ws))), "psf": s0.P,
                        "conv": "direct", "free_params": s0.nfree, "lm_tol": args.lm_tol,
-                       "ladder": int(opts.ladder),
+                       "ladder": int(opts.ladder) or "auto",
                        "jacobian": args.jac,
                        "tile_width_by_class": tiles,
                        "tile_height": shape[1], "conv_ctas_per_sm": shape[2],
@@ -1130,7 +1130,7 @@ def run_learned(args):
             "config": {"workload": "learned65536" if count == 65536 else f"learned{count}",
                        "stamps": count, "side": 64, "train_stamps": train_steps * train_batch,
                        "psf": learned.PSF_SIZE, "free_params": 8, "lm_tol": args.lm_tol,
-                       "ladder": int(opts.ladder),
+                       "ladder": int(opts.ladder) or "auto",
                        "jacobian": args.jac,
                        "start": "CNN (bf16) with default-guess fallback by chi2",
                        "conv_tile": {"width": shape[0], "height": shape[1],

@@ -173,7 +173,9 @@ typedef struct {
     int jac_mode;        /* GF_JAC_FD: forward-difference columns for the nonlinear slots
                             (the default); GF_JAC_ANALYTIC: their analytic derivatives */
     int ladder;          /* trials evaluated together in one pass: the steps for lambda,
-                            lambda*up, ... (1 .. GF_MAX_LADDER; 0 = 2).  The fit takes
+                            lambda*up, ... (1 .. GF_MAX_LADDER; 0 = automatic: 1 when the
+                            call has at least as many stamps as the device has SMs, else
+                            2).  The fit takes
                             exactly the steps of the one-trial-at-a-time rule: the trials
                             after the first are the ones that rule would try next after
                             rejections, and only those it reaches are used. */
@@ -318,7 +320,7 @@ gf_status gf_jacobian_analytic(const gf_desc* d, const double* params_host,
 
 /* Fill opts with the library defaults (lambda0 1e-3, x10 / x0.1, [1e-12, 1e12],
  * ftol 1e-8, xtol 1e-8, fd_rel 1e-3, max_iter 200, jac_mode GF_JAC_FD,
- * ladder 2, no time budget). */
+ * ladder 0 = automatic, no time budget). */
 void gf_default_opts(gf_lm_opts* opts);
 
 /* Steps 1-5: Levenberg-Marquardt fit of one stamp.  params_host (nslots) is

@@ -295,8 +295,25 @@ void default_opts(gf_lm_opts* o)
     o->fd_rel = 1e-3;
     o->max_iter = 200;
     o->jac_mode = GF_JAC_FD;
-    o->ladder = 2;
+    o->ladder = 0;  // automatic: see auto_ladder
     o->time_budget_s = 0.0;
+}
+
+// The trial ladder of a fit left to the library (gf_lm_opts.ladder 0): one rung
+// when the call has at least as many stamps as the device has SMs (its passes
+// fill the GPU, and a second rung's model and convolution are mostly extra
+// work: it is used only after a rejection), else two (a few stamps are latency
+// bound, and a rejection followed by an acceptance then takes one LM body
+// instead of two).  The fits are the same for any ladder.
+int auto_ladder(int count)
+{
+    static int sms[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 2;
+    if (sms[dev] <= 0 &&
+        cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 2;
+    return count >= sms[dev] ? 1 : 2;
 }
 
 gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* lo,
@@ -405,9 +422,8 @@ gf_status make_structure(const gf_desc* d, const uint8_t* fixed, const double* l
                 S->kinds[k] == GF_SERSIC_F)
                 return fail(GF_EINVAL, "analytic Jacobian columns are not available for King, Nuker, "
                                        "point-source or Fourier-mode components (use GF_JAC_FD)");
-    if (S->opts.ladder == 0) S->opts.ladder = 2;
-    if (S->opts.ladder < 1 || S->opts.ladder > GF_MAX_LADDER)
-        return fail(GF_EINVAL, "LM ladder must be 1 .. " + std::to_string(GF_MAX_LADDER));
+    if (S->opts.ladder < 0 || S->opts.ladder > GF_MAX_LADDER)
+        return fail(GF_EINVAL, "LM ladder must be 0 (automatic) or 1 .. " + std::to_string(GF_MAX_LADDER));
     return GF_OK;
 }
 
@@ -573,7 +589,7 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
     o += al(sizeof(int));
     L.blob_end = o;
     // the trial pass: one channel per stamp, or one per rung of the LM ladder
-    const int R = (need & NEED_LM) ? S.opts.ladder : 1;
+    const int R = (need & NEED_LM) ? (S.opts.ladder > 0 ? S.opts.ladder : auto_ladder(count)) : 1;
     L.rungs = R;
     L.chan_trial = o;
     o += al(sizeof(Channel) * (size_t)count * R);

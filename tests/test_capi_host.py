@@ -108,7 +108,7 @@ def test_tile_width_setter_validates_before_touching_the_device():
 def test_lm_ladder_option_validated_before_launch(gf):
     L = gf.lib()
     o = gf.default_opts()
-    assert o.ladder == 2
+    assert o.ladder == 0  # automatic
     d = gf.make_desc(64, 64, 25, [1, 3])
     p = np.zeros(9)
     r = gf.LMResult()
