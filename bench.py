@@ -85,6 +85,54 @@ CONV_DIRECT_TRAFFIC = {
 }
 
 
+# DRAM bytes per transform of the one-CTA FFT convolution (k_conv_fft_small),
+# from the ncu capture of the Jacobian-pass launches on 8,192 stamps of the
+# learned workload; a launch's traffic grows in proportion to its transforms.
+CONV_FFT_SMALL_TRAFFIC = {
+    # the 7-channel Jacobian launch (57,344 transforms): 2423.5 MB read + 910.8 MB
+    # written = 58.1 KB per transform (the algorithmic grid + output: 53.2 KB)
+    "bytes_per_problem": (2423454720 + 910797312) / 57344,
+    "profile": "profiles/k_conv_fft_small_learned8192.md",
+    "sources": {
+        "paper_1101_2254_gb300/csrc/conv_fft.cu":
+            "cf0946c591e50f19e9686532079722dc84b852ead3f9d52640731b5485d5e4fb",
+        "paper_1101_2254_gb300/csrc/conv_fft.cuh":
+            "a4d55cbdda7c2a8fcfe95457b1242aa8b387019fe6ead7c9f7ad84830167549d",
+        "paper_1101_2254_gb300/csrc/warp_fft.cuh":
+            "968ef49fcdece8a3decab9e3bb9da728d116a1a103eff0d6437b5726e58de91b",
+        "paper_1101_2254_gb300/csrc/fft.cuh":
+            "f12874458fbb0310b0b5f890cdc2b7d57b76b09e959613bf60669b0bcd060f50",
+    },
+}
+
+
+def conv_fft_small_traffic(problems_per_launch):
+    import hashlib
+    t = CONV_FFT_SMALL_TRAFFIC
+    if t["bytes_per_problem"] is None or not t["sources"]:
+        return None
+    for path, digest in t["sources"].items():
+        try:
+            with open(os.path.join(ROOT, path), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return t["bytes_per_problem"] * problems_per_launch
+
+
+def fft_small_flops(He, We, H, W):
+    """Transform work one CTA of k_conv_fft_small counts (the library's own
+    figure, truncated as the kernel adds it): 5 N log2 N per row or column
+    transform, 6 Ny per column for the spectrum product."""
+    nx = next(32 * m for m in (3, 4, 5) if 32 * m >= We)
+    ny = next(32 * m for m in (3, 4, 5) if 32 * m >= He)
+    kx = nx // 2 + 1
+    f = np.float32(((He + 1) // 2 + (H + 1) // 2) * 5.0 * nx * math.log2(nx)
+                   + kx * (10.0 * ny * math.log2(ny) + 6.0 * ny))
+    return int(f), nx, ny
+
+
 def conv_direct_traffic(outputs_per_launch):
     import hashlib
     for path, digest in CONV_DIRECT_TRAFFIC["sources"].items():
@@ -143,6 +191,9 @@ def parse():
                     help="batch4096: stamps the oracle checks for reaching its chi2")
     ap.add_argument("--train-steps", type=int, default=2000,
                     help="learned65536: Adam steps of 512 stamps before the timed fits")
+    ap.add_argument("--conv", default="fft", choices=["fft", "direct"],
+                    help="learned65536: PSF convolution of the fits (fft: one CTA per "
+                         "96 x 96 transform; direct: the tiled direct sum)")
     return ap.parse_args()
 
 
@@ -1007,13 +1058,15 @@ def run_learned(args):
         sig.view(count, 64, 64)[:ns] = torch.as_tensor(sample["sig"]).to(dev)
     img, sig, psf = img.reshape(-1), sig.reshape(-1), psf.reshape(-1)
     b = learned.uniform_batch(count)
-    d = learned.stamp_desc()
+    conv_fft = args.conv == "fft"
+    d = learned.stamp_desc(conv_method=gf.CONV_FFT if conv_fft else gf.CONV_DIRECT)
     fixed = np.zeros(9, np.uint8)
     fixed[7] = 1
     opts = lm_opts(gf, args)
     ws = gf.Workspace(device=dev)
     ws_lm = gf.Workspace(device=dev)
     # untimed setup: the direct convolution's launch shape tuned on these stamps
+    # (nothing to tune for the FFT)
     gf.autotune(d, b, psf, ws=ws_lm)
     shape = gf.conv_tile_shape(learned.PSF_SIZE, 64)
 
@@ -1109,6 +1162,57 @@ def run_learned(args):
     fp32_peak, fp64_peak = gf.fma_peak(False), gf.fma_peak(True)
     ach = pr["conv"]["work"] / (pr["conv"]["ms"] / 1e3) / 1e12
     conv_out = pr["conv"]["work"] / (2.0 * learned.PSF_SIZE ** 2)  # outputs convolved
+    nconv = max(pr["conv"]["launches"], 1)
+    conv_ms_avg = pr["conv"]["ms"] / nconv
+    if conv_fft:
+        # transforms (one per stamp and channel) from the work the kernel counted
+        c = (learned.PSF_SIZE - 1) // 2
+        He = 64 + 2 * c
+        f1, nx, ny = fft_small_flops(He, He, 64, 64)
+        problems = pr["conv"]["work"] / f1
+        bytes_1 = 4.0 * (He * He + 64 * 64)  # grid in, valid region out
+        gbs = problems * bytes_1 / (pr["conv"]["ms"] / 1e3) / 1e9
+        hbm = peaks.get("hbm_gbs")
+        f_hbm = gbs / hbm if hbm else None
+        f_alu = ach / fp32_peak
+        roof = {"bound": "hbm" if (f_hbm or 0) >= f_alu else "alu",
+                "kernel": f"k_conv_fft_small<{nx // 32},{ny // 32}> (one CTA per {ny} x {nx} "
+                          "transform of a stamp's channel)"}
+        if roof["bound"] == "hbm":
+            roof.update(achieved=gbs, peak=hbm, unit="GB/s", frac=f_hbm,
+                        peak_source="MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind)
+        else:
+            roof.update(achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=f_alu,
+                        peak_source="measured FP32 FMA loop (gf_fma_peak) in this run")
+        roof.update({
+            "traffic": conv_fft_small_traffic(problems / nconv),
+            "traffic_note": "DRAM bytes per launch from the ncu capture of this kernel "
+                            "(profiles/k_conv_fft_small_learned8192.md), per transform x the "
+                            "transforms of the average launch; null if the source changed",
+            "alg_bytes_per_launch": bytes_1 * problems / nconv,
+            "alg_bytes_note": "4 (He We + H W) bytes per transform: the channel grid read, the "
+                              "valid region written (the PSF spectrum, one per stamp, is "
+                              "shared by its channels and not counted)",
+            "hbm_gbs": gbs, "hbm_frac": f_hbm, "tflops": ach, "alu_frac": f_alu,
+            "work_note": "5 N log2 N FLOP per length-N transform + 6 Ny per spectrum column",
+            "transforms": problems, "launches": pr["conv"]["launches"],
+            "avg_launch_ms": conv_ms_avg,
+            "share_of_device_time": pr["conv"]["ms"] / sum(v["ms"] for v in pr.values())})
+    else:
+        roof = {"bound": "alu", "kernel": "k_conv_direct (2 P^2 FLOP per output)",
+                "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak,
+                "traffic": conv_direct_traffic(conv_out / nconv),
+                "traffic_note": "bytes per launch: 13.9 B per output (ncu capture of "
+                                "the Jacobian launch, the dominant one; a fused trial "
+                                "launch moves 18.2 B per output; "
+                                "profiles/k_conv_direct_learned8192.md) x the outputs "
+                                "of the average launch",
+                "alg_bytes_per_launch": 4.0 * (96 * 96 / 4096 + 1) * conv_out / nconv,
+                "peak_source": "measured FP32 FMA loop (gf_fma_peak) in this run",
+                "launches": pr["conv"]["launches"],
+                "avg_launch_ms": conv_ms_avg,
+                "share_of_device_time": pr["conv"]["ms"] / sum(v["ms"] for v in pr.values())}
     it_l = np.array([r["iters"] for r in res])
     it_d = np.array([r["iters"] for r in rdf])
     st_l = np.array([r["status"] for r in res])
@@ -1133,8 +1237,10 @@ def run_learned(args):
                        "ladder": int(opts.ladder) or "auto",
                        "jacobian": args.jac,
                        "start": "CNN (bf16) with default-guess fallback by chi2",
-                       "conv_tile": {"width": shape[0], "height": shape[1],
-                                     "ctas_per_sm": shape[2], "tuned": True},
+                       "conv": "fft: one CTA per 96 x 96 transform" if conv_fft else "direct",
+                       "conv_tile": None if conv_fft else {
+                           "width": shape[0], "height": shape[1], "ctas_per_sm": shape[2],
+                           "tuned": True},
                        "value_counts": "fits reaching the oracle chi2 (fraction from the "
                                        "seeded oracle sample in reach_oracle_chi2)",
                        "l2": "inputs (2.4 GB) larger than L2", "parallelism": f"replicas{ws_}"},
@@ -1148,21 +1254,7 @@ def run_learned(args):
                     "d2h_bytes_per_step": int(count * 9 * 8 * 2 + count * 32),
                     "ms_per_step": e2e_ms, "h2d_inputs_ms": e2e_copy_ms},
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "kernel": "k_conv_direct (2 P^2 FLOP per output)",
-                         "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": ach / fp32_peak,
-                         "traffic": conv_direct_traffic(conv_out / max(pr["conv"]["launches"], 1)),
-                         "traffic_note": "bytes per launch: 13.9 B per output (ncu capture of "
-                                         "the Jacobian launch, the dominant one; a fused trial "
-                                         "launch moves 18.2 B per output; "
-                                         "profiles/k_conv_direct_learned8192.md) x the outputs "
-                                         "of the average launch",
-                         "alg_bytes_per_launch": 4.0 * (96 * 96 / 4096 + 1) * conv_out
-                                                 / max(pr["conv"]["launches"], 1),
-                         "peak_source": "measured FP32 FMA loop (gf_fma_peak) in this run",
-                         "launches": pr["conv"]["launches"],
-                         "avg_launch_ms": pr["conv"]["ms"] / max(pr["conv"]["launches"], 1),
-                         "share_of_device_time": pr["conv"]["ms"] / sum(v["ms"] for v in pr.values())},
+            "roofline": roof,
             "measured_peaks_tflops": {"fp32_fma": fp32_peak, "fp64_fma": fp64_peak},
             "kernel_ms_per_step": {k: v["ms"] for k, v in pr.items()},
             "lm": {"iters_median": float(np.median(it_l)), "iters_mean": float(it_l.mean()),

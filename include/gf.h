@@ -126,10 +126,16 @@ typedef enum {
 } gf_comp_kind;
 
 typedef enum {
-    GF_CONV_AUTO = 0,   /* direct for P < GF_AUTO_FFT_PSF, else FFT */
+    GF_CONV_AUTO = 0,   /* direct for P < GF_AUTO_FFT_PSF, else FFT.  (For extended
+                           grids up to 160 x 160 the FFT is one CTA per transform and
+                           overtakes the direct sum from about P = 15 on 64x64 and
+                           96x96 stamps, P = 33 on 32x32: name GF_CONV_FFT there.) */
     GF_CONV_DIRECT = 1, /* tiled direct sum, PSF and halo tile in shared memory */
     GF_CONV_FFT = 2,    /* shared-memory mixed-radix FFT, 2^a 3^b 5^c sizes up to 4096;
-                           the stamps of one call must share H and W */
+                           the stamps of one call must share H and W.  Extended grids
+                           up to 160 x 160 are padded to Nx, Ny in {96, 128, 160} and
+                           each channel is transformed, multiplied and transformed back
+                           by one CTA with its spectrum in shared memory */
     GF_CONV_DFT_TC = 3  /* Fourier transforms as dense DFT contractions on the tensor cores
                            (split-precision bf16 operands, float32 accumulation); sizes
                            N = R1 R2 with R1, R2 <= 64; stamps of one call share H and W */
@@ -430,7 +436,8 @@ gf_status gf_set_conv_tile_shape(int psf_size, int tile_h, int ctas_per_sm);
  *     each array rounded up to 256 bytes, plus a few KB of tables):
  *       direct:  4 He We + 4 H W
  *       FFT:     the direct terms + 8 Ny (Nx/2+1) + 4 Ny Nx + 8 He (Nx/2+1)
- *                + 8 (Nx + Ny)
+ *                + 8 (Nx + Ny); without the 8 He (Nx/2+1) spectrum scratch when
+ *                He, We <= 160 (one CTA per transform, Nx, Ny in {96, 128, 160})
  *       DFT_TC:  the direct terms + 8 Ny Nx + 4 Ny Nx + 2 x 8 Ny Nx
  *                + 8 (Nx + Ny) + 256 KiB of DFT matrices
  *     With a 65x65 PSF, GF_CONV_AUTO takes the FFT (P >= GF_AUTO_FFT_PSF):

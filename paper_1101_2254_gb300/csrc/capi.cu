@@ -497,6 +497,7 @@ struct Plan {
     std::vector<int> pre;  // 4 * (count + 1): model, os, conv, red
     int method;            // GF_CONV_DIRECT, GF_CONV_FFT or GF_CONV_DFT_TC
     int Nx, Ny, cpc;       // FFT geometry (method FFT)
+    int small = 0;         // FFT: one CTA per transform (Nx, Ny in 32 x {3, 4, 5})
     DftFactor fx, fy;      // DFT geometry (method DFT_TC)
 };
 
@@ -643,6 +644,14 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         pl->Nx = fft_len(s0.We, true);
         pl->Ny = fft_len(s0.He, false);
         pl->cpc = choose_cpc(pl->Ny);
+        // grids up to 160 x 160: padded to 32 M and transformed one CTA each,
+        // the spectrum kept in shared memory (no spectrum scratch)
+        const int sx = fft_small_len(s0.We), sy = fft_small_len(s0.He);
+        pl->small = sx > 0 && sy > 0;
+        if (pl->small) {
+            pl->Nx = sx;
+            pl->Ny = sy;
+        }
         const size_t Kx = pl->Nx / 2 + 1;
         L.tw_x = o;
         o += al(sizeof(float2) * pl->Nx);
@@ -652,14 +661,15 @@ void plan_batch(const gf_desc* d, const Structure& S, int count, const int* H, c
         o += al(sizeof(float2) * (size_t)count * pl->Ny * Kx);
         L.psfgrid = o;
         o += al(sizeof(float) * (size_t)count * pl->Ny * pl->Nx);
+        const size_t spec_rows = pl->small ? 0 : (size_t)s0.He * Kx;
         if (need & (NEED_JAC | NEED_LM)) {
             L.spec_jac = o;
-            o += al(sizeof(float2) * (size_t)count * S.nchan * s0.He * Kx);
+            o += al(sizeof(float2) * (size_t)count * S.nchan * spec_rows);
         }
         // gf_eval and gf_convolve use one channel per stamp, the LM trial pass
         // one per rung
         L.spec_trial = o;
-        o += al(sizeof(float2) * (size_t)count * R * s0.He * Kx);
+        o += al(sizeof(float2) * (size_t)count * R * spec_rows);
     }
     if (pl->method == GF_CONV_DFT_TC) {
         const StampInfo& s0 = pl->st[0];
@@ -803,6 +813,7 @@ FFTArgs fft_args(void* ws, const Plan& pl)
     f.Nx = pl.Nx;
     f.Ny = pl.Ny;
     f.cpc = pl.cpc;
+    f.small = pl.small;
     f.px = make_fft_plan(pl.Nx);
     f.py = make_fft_plan(pl.Ny);
     f.tw_x = at<float2>(ws, pl.L.tw_x);
@@ -1023,8 +1034,6 @@ gf_status run_conv(const PassArgs& a, const Plan& pl, void* ws, size_t spec_off,
         return GF_OK;
     }
     if (pl.method == GF_CONV_DFT_TC) return run_conv_dft(a, pl, ws, s);
-    if ((long long)a.count * a.nchan > 65535)
-        return fail(GF_EINVAL, "FFT convolution: stamps x channels per call must be <= 65535");
     GF_CUDA(launch_conv_fft(a, fft_args(ws, pl), at<float2>(ws, spec_off), s));
     return GF_OK;
 }

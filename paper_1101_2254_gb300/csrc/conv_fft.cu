@@ -49,34 +49,36 @@ __device__ __forceinline__ void load_tw(float2* dst, const float2* src, int n)
 // ((v - c) mod Ny, (u - c) mod Nx); the grid was zeroed by the caller.
 __global__ void k_psf_wrap(FFTArgs f, int count, const StampInfo* st, const float* psf)
 {
-    const int b = blockIdx.y;
+    const int b = blockIdx.x >> 3, part = blockIdx.x & 7;  // 8 CTAs per stamp
     if (b >= count) return;
     const int P = st[b].P, c = st[b].c;
     const float scale = (float)(1.0 / ((double)f.Ny * (double)f.Nx));
     float* g = f.psfgrid + (long long)b * f.Ny * f.Nx;
     const float* p = psf + st[b].psf_off;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < P * P; t += gridDim.x * blockDim.x) {
+    for (int t = part * blockDim.x + threadIdx.x; t < P * P; t += 8 * blockDim.x) {
         const int v = t / P, u = t - v * P;
         const int y = ((v - c) % f.Ny + f.Ny) % f.Ny, x = ((u - c) % f.Nx + f.Nx) % f.Nx;
         g[(long long)y * f.Nx + x] = p[t] * scale;
     }
 }
 
-// Forward row pass.  Problem p = blockIdx.y covers one real grid (rows `rows`
+// Forward row pass.  Problem p = blockIdx.x / io.nblk covers one real grid (rows `rows`
 // valid of row stride `ld`, `width` valid columns) and one half-spectrum array
-// (Kx = Nx/2 + 1 bins per row).  Block x handles rows 2x and 2x + 1.
+// (Kx = Nx/2 + 1 bins per row).  Block x of the problem handles rows 2x and 2x + 1.
+// (Every FFT pass numbers its CTAs problem-major in one grid dimension: a
+// problem count of count * channels may exceed the 65,535 of the y dimension.)
 __global__ void __launch_bounds__(ROW_THREADS) k_fft_rows_fwd(FFTArgs f, RowIO io, PassArgs a)
 {
     pdl_entry();
     extern __shared__ __align__(16) float2 sm[];
-    const int p = blockIdx.y;
+    const int p = blockIdx.x / io.nblk, bx = blockIdx.x - p * io.nblk;
     if (a.lm && a.lm[p / io.nchan].phase != a.phase) return;
     const int Nx = f.Nx, Kx = Nx / 2 + 1;
     float2* bufA = sm;
     float2* bufB = sm + Nx;
     float2* tw = sm + 2 * Nx;
     load_tw(tw, f.tw_x, Nx);
-    const int y0 = 2 * blockIdx.x, y1 = y0 + 1;
+    const int y0 = 2 * bx, y1 = y0 + 1;
     const float* in = io.in + (long long)p * io.in_stride;
     for (int x = threadIdx.x; x < Nx; x += blockDim.x) {
         const bool cx = x < io.width;
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(COL_THREADS) k_fft_cols(FFTArgs f, ColIO io, P
 {
     pdl_entry();
     extern __shared__ __align__(16) float2 sm[];
-    const int p = blockIdx.y;
+    const int p = blockIdx.x / io.nblk, bx = blockIdx.x - p * io.nblk;
     const int b = p / io.nchan;
     if (a.lm && a.lm[b].phase != a.phase) return;
     const int Ny = f.Ny, Kx = f.Nx / 2 + 1, B = f.cpc, logB = __ffs(B) - 1;  // B a power of two
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(COL_THREADS) k_fft_cols(FFTArgs f, ColIO io, P
     float2* bufB = sm + Ny * B;
     float2* tw = sm + 2 * Ny * B;
     load_tw(tw, f.tw_y, Ny);
-    const int kx0 = blockIdx.x * B;
+    const int kx0 = bx * B;
     float2* spec = io.spec + (long long)p * io.spec_stride;
     const int total = Ny * B;
     // the column block: eight loads per thread in flight before their stores
@@ -183,14 +185,14 @@ __global__ void __launch_bounds__(ROW_THREADS) k_fft_rows_inv(FFTArgs f, RowInvI
 {
     pdl_entry();
     extern __shared__ __align__(16) float2 sm[];
-    const int p = blockIdx.y;
+    const int p = blockIdx.x / io.nblk, bx = blockIdx.x - p * io.nblk;
     if (a.lm && a.lm[p / io.nchan].phase != a.phase) return;
     const int Nx = f.Nx, Kx = Nx / 2 + 1;
     float2* bufA = sm;
     float2* bufB = sm + Nx;
     float2* tw = sm + 2 * Nx;
     load_tw(tw, f.tw_x, Nx);
-    const int i0 = 2 * blockIdx.x, i1 = i0 + 1;
+    const int i0 = 2 * bx, i1 = i0 + 1;
     const bool has1 = i1 < io.H;
     const float2* spec = io.spec + (long long)p * io.spec_stride;
     const float2* sa = spec + (long long)(io.row0 + i0) * Kx;
@@ -232,13 +234,13 @@ __global__ void __launch_bounds__(WROW_WARPS * 32) k_fft_rows_fwd_w(FFTArgs f, R
     pdl_entry();
     constexpr int N = 32 * M, Kx = N / 2 + 1;
     extern __shared__ __align__(16) float2 sm[];
-    const int p = blockIdx.y;
+    const int p = blockIdx.x / io.nblk, bx = blockIdx.x - p * io.nblk;
     if (a.lm && a.lm[p / io.nchan].phase != a.phase) return;
     float2* tws = sm;
     for (int t = threadIdx.x; t < N; t += blockDim.x) tws[warp_fft_pad(t)] = f.tw_x[t];
     __syncthreads();
     const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int y0 = 2 * (blockIdx.x * WROW_WARPS + warp), y1 = y0 + 1;
+    const int y0 = 2 * (bx * WROW_WARPS + warp), y1 = y0 + 1;
     if (y0 >= io.out_rows) return;
     const float* in = io.in + (long long)p * io.in_stride;
     float2 v[M];
@@ -273,13 +275,13 @@ __global__ void __launch_bounds__(WROW_WARPS * 32) k_fft_rows_inv_w(FFTArgs f, R
     pdl_entry();
     constexpr int N = 32 * M, Kx = N / 2 + 1;
     extern __shared__ __align__(16) float2 sm[];
-    const int p = blockIdx.y;
+    const int p = blockIdx.x / io.nblk, bx = blockIdx.x - p * io.nblk;
     if (a.lm && a.lm[p / io.nchan].phase != a.phase) return;
     float2* tws = sm;
     for (int t = threadIdx.x; t < N; t += blockDim.x) tws[warp_fft_pad(t)] = f.tw_x[t];
     __syncthreads();
     const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int i0 = 2 * (blockIdx.x * WROW_WARPS + warp), i1 = i0 + 1;
+    const int i0 = 2 * (bx * WROW_WARPS + warp), i1 = i0 + 1;
     if (i0 >= io.H) return;
     const bool has1 = i1 < io.H;
     const float2* spec = io.spec + (long long)p * io.spec_stride;
@@ -314,6 +316,228 @@ __global__ void __launch_bounds__(WROW_WARPS * 32) k_fft_rows_inv_w(FFTArgs f, R
     if (a.work && l == 0) atomicAdd(&a.work[PROF_CONV], (unsigned long long)f.flops_row);
 }
 
+// ------------------------------------------- one CTA per transform (small grids)
+// For Nx = 32 MX and Ny = 32 MY with MX, MY in {3, 4, 5} (grids up to 160 x 160)
+// the whole convolution of one channel runs in one CTA: its half spectrum
+// (Ny x Kx complex values, at most 104 KB) stays in shared memory between the
+// three stages, so the only global traffic is the grid read, the PSF spectrum
+// read and the valid region written.  Every transform is a warp register FFT:
+//   rows     a warp per pair of grid rows, packed and unpacked as in the row
+//            kernels above;
+//   columns  a warp per spectrum column: forward FFT along y, product with the
+//            PSF spectrum, inverse FFT; the rows [row0, row0 + H) kept in place;
+//   rows     a warp per pair of output rows, inverse of the packing.
+// The PSF spectrum is made by the same kernel (psf_mode): the wrapped PSF
+// through the row pass and the forward column FFT, stored per column in the
+// order the warp FFT leaves it in (lane l, register k2 holds bin
+// k2 + MY bitrev5(l)), so that the product reads it coalesced and needs no
+// reordering: hperm[k][MY l + k2] = Hhat[k2 + MY bitrev5(l)][k].
+constexpr int SMALL_WARPS = 8;
+
+struct SmallIO {
+    const float* in;      // grids: problem p at in + p in_stride, rows x width, row stride ld
+    long long in_stride;
+    int ld, width, rows;
+    float* out;           // results: problem p at out + p out_stride, H x W
+    long long out_stride;
+    int row0, col0, H, W;
+    float2* hperm;        // per stamp Kx * Ny values (written in psf_mode)
+    int nchan;
+    int psf_mode;
+    float flops;          // one CTA's transform work (profiling)
+};
+
+// the column transforms' register twiddles: the row set itself when Nx = Ny
+template <int MX, int MY>
+__device__ __forceinline__ const WarpTw<MY>& select_tw(const WarpTw<MX>& rx, const WarpTw<MY>& ry)
+{
+    if constexpr (MX == MY)
+        return rx;
+    else
+        return ry;
+}
+
+// CTAs per SM that the kernel's shared memory allows (227 KB per SM), which
+// its register budget is held to
+constexpr size_t small_smem(int Nx, int Ny);
+template <int MX, int MY>
+constexpr int small_ctas_per_sm()
+{
+    const int n = (int)((227u * 1024u) / small_smem(32 * MX, 32 * MY));
+    return n < 1 ? 1 : (n > 5 ? 5 : n);
+}
+
+template <int MX, int MY>
+__global__ void __launch_bounds__(SMALL_WARPS * 32, small_ctas_per_sm<MX, MY>()) k_conv_fft_small(SmallIO io, PassArgs a,
+                                                                     const float2* tw_x,
+                                                                     const float2* tw_y)
+{
+    pdl_entry();
+    constexpr int Nx = 32 * MX, Ny = 32 * MY, Kx = Nx / 2 + 1;
+    constexpr int NZ = Nx > Ny ? Nx : Ny;
+    extern __shared__ __align__(16) float2 sm[];
+    const int p = blockIdx.x;
+    const int b = p / io.nchan;
+    if (a.lm && a.lm[b].phase != a.phase) return;  // whole CTA
+    float2* twx = sm;
+    float2* twy = twx + warp_fft_table_len(Nx);
+    float2* spec = twy + warp_fft_table_len(Ny);  // Ny x Kx (row stride Kx: odd)
+    const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    float2* z = spec + Ny * Kx + warp * NZ;       // the warp's reordering buffer
+    for (int t = threadIdx.x; t < Nx; t += blockDim.x) twx[warp_fft_pad(t)] = tw_x[t];
+    for (int t = threadIdx.x; t < Ny; t += blockDim.x) twy[warp_fft_pad(t)] = tw_y[t];
+    __syncthreads();
+    // the lane's twiddles for every transform of the CTA (one set when Nx = Ny)
+    WarpTw<MX> rx;
+    warp_tw_load<MX>(rx, twx);
+    WarpTw<MY> ry_own;
+    if constexpr (MX != MY) warp_tw_load<MY>(ry_own, twy);
+    const WarpTw<MY>& ry = select_tw<MX, MY>(rx, ry_own);
+    const int br = bitrev5(l);
+    // rows: pairs (y0, y0 + 1) of the grid; rows >= rows are zeros
+    const int npair = (io.rows + 1) / 2, hw = 2 * npair;  // spectrum rows written
+    const float* in = io.in + (long long)p * io.in_stride;
+    // the warp's next row pair is loaded while the current one is transformed
+    auto load_pair = [&](int pr, float2 (&w)[MX]) {
+        const int y0 = 2 * pr, y1 = y0 + 1;
+#pragma unroll
+        for (int j = 0; j < MX; ++j) {
+            const int x = l + 32 * j;
+            const bool cx = x < io.width;
+            const float va = cx ? in[(long long)y0 * io.ld + x] : 0.0f;
+            const float vb = (cx && y1 < io.rows) ? in[(long long)y1 * io.ld + x] : 0.0f;
+            w[j] = make_float2(va, vb);
+        }
+    };
+    float2 vn[MX];
+    if (warp < npair) load_pair(warp, vn);
+    for (int pr = warp; pr < npair; pr += SMALL_WARPS) {
+        const int y0 = 2 * pr, y1 = y0 + 1;
+        float2 v[MX];
+#pragma unroll
+        for (int j = 0; j < MX; ++j) v[j] = vn[j];
+        if (pr + SMALL_WARPS < npair) load_pair(pr + SMALL_WARPS, vn);
+        warp_fft_r<MX, false>(v, rx);
+#pragma unroll
+        for (int k2 = 0; k2 < MX; ++k2) z[k2 + MX * br] = v[k2];
+        __syncwarp();
+        for (int k = l; k < Kx; k += 32) {
+            const float2 zk = z[k], zm = cconj(z[(Nx - k) % Nx]);
+            const float2 s = cadd(zk, zm), d = csub(zk, zm);
+            // A = (Z[k] + conj Z[N-k]) / 2,  B = (Z[k] - conj Z[N-k]) / (2i)
+            spec[y0 * Kx + k] = make_float2(0.5f * s.x, 0.5f * s.y);
+            spec[y1 * Kx + k] = make_float2(0.5f * d.y, -0.5f * d.x);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // columns
+    float2* hp = io.hperm + (long long)b * Kx * Ny;
+    for (int k = warp; k < Kx; k += SMALL_WARPS) {
+        float2* hk = hp + (long long)k * Ny + MY * l;
+        float2 h[MY];  // the PSF spectrum's column, loaded before the transform
+        if (!io.psf_mode) {
+#pragma unroll
+            for (int k2 = 0; k2 < MY; ++k2) h[k2] = hk[k2];
+        }
+        float2 v[MY];
+#pragma unroll
+        for (int j = 0; j < MY; ++j) {
+            const int y = l + 32 * j;
+            v[j] = y < hw ? spec[y * Kx + k] : make_float2(0.0f, 0.0f);
+        }
+        warp_fft_r<MY, false>(v, ry);
+        if (io.psf_mode) {
+#pragma unroll
+            for (int k2 = 0; k2 < MY; ++k2) hk[k2] = v[k2];
+            continue;
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < MY; ++k2) z[k2 + MY * br] = cmul(v[k2], h[k2]);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < MY; ++j) v[j] = z[l + 32 * j];
+        __syncwarp();
+        warp_fft_r<MY, true>(v, ry);
+#pragma unroll
+        for (int k2 = 0; k2 < MY; ++k2) {
+            const int y = k2 + MY * br;
+            if (y >= io.row0 && y < io.row0 + io.H) spec[y * Kx + k] = v[k2];
+        }
+    }
+    if (io.psf_mode) return;
+    __syncthreads();
+    // rows: inverse of the packing, output rows (i0, i0 + 1)
+    float* out = io.out + (long long)p * io.out_stride;
+    for (int pr = warp; 2 * pr < io.H; pr += SMALL_WARPS) {
+        const int i0 = 2 * pr, i1 = i0 + 1;
+        const bool has1 = i1 < io.H;
+        const float2* sa = spec + (io.row0 + i0) * Kx;
+        const float2* sb = spec + (io.row0 + (has1 ? i1 : i0)) * Kx;
+        float2 v[MX];
+#pragma unroll
+        for (int j = 0; j < MX; ++j) {
+            const int k = l + 32 * j;
+            float2 A, Bv;
+            if (k < Kx) {
+                A = sa[k];
+                Bv = sb[k];
+            } else {
+                A = cconj(sa[Nx - k]);
+                Bv = cconj(sb[Nx - k]);
+            }
+            if (!has1) Bv = make_float2(0.0f, 0.0f);
+            v[j] = make_float2(A.x - Bv.y, A.y + Bv.x);  // A + i B
+        }
+        warp_fft_r<MX, true>(v, rx);
+#pragma unroll
+        for (int k2 = 0; k2 < MX; ++k2) z[k2 + MX * br] = v[k2];
+        __syncwarp();
+        for (int j = l; j < io.W; j += 32) {
+            const float2 w = z[io.col0 + j];
+            out[(long long)i0 * io.W + j] = w.x;
+            if (has1) out[(long long)i1 * io.W + j] = w.y;
+        }
+        __syncwarp();
+    }
+    if (a.work && threadIdx.x == 0) atomicAdd(&a.work[PROF_CONV], (unsigned long long)io.flops);
+}
+
+constexpr size_t small_smem(int Nx, int Ny)
+{
+    // tables, the half spectrum, one reordering row per warp
+    return sizeof(float2) * ((size_t)warp_fft_table_len(Nx) + (size_t)warp_fft_table_len(Ny) +
+                             (size_t)Ny * (Nx / 2 + 1) + (size_t)SMALL_WARPS * (Nx > Ny ? Nx : Ny));
+}
+
+template <int MX, int MY>
+cudaError_t launch_small_t(const SmallIO& io, const PassArgs& a, const FFTArgs& f, int nprob,
+                           cudaStream_t s)
+{
+    static int optin[64];
+    const size_t smem = small_smem(32 * MX, 32 * MY);
+    cudaError_t e = ensure_smem_optin((const void*)k_conv_fft_small<MX, MY>, (int)smem, optin);
+    if (e != cudaSuccess) return e;
+    GF_LAUNCH_PDL(k_conv_fft_small<MX, MY>, dim3(nprob), dim3(SMALL_WARPS * 32), smem, s, io, a,
+                  (const float2*)f.tw_x, (const float2*)f.tw_y);
+    GF_COUNT_LAUNCH();
+    return cudaSuccess;
+}
+
+cudaError_t launch_small(const SmallIO& io, const PassArgs& a, const FFTArgs& f, int nprob,
+                         cudaStream_t s)
+{
+    switch ((f.Nx / 32) * 8 + f.Ny / 32) {
+#define SMALL_CASE(MX_, MY_) \
+    case MX_ * 8 + MY_: return launch_small_t<MX_, MY_>(io, a, f, nprob, s);
+        SMALL_CASE(3, 3) SMALL_CASE(3, 4) SMALL_CASE(3, 5)
+        SMALL_CASE(4, 3) SMALL_CASE(4, 4) SMALL_CASE(4, 5)
+        SMALL_CASE(5, 3) SMALL_CASE(5, 4) SMALL_CASE(5, 5)
+#undef SMALL_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 size_t warp_row_smem(int N) { return sizeof(float2) * ((size_t)warp_fft_table_len(N) + (size_t)WROW_WARPS * N); }
 
 // the warp row kernels exist for these Nx
@@ -334,6 +558,13 @@ bool warp_rows_ok(int Nx)
 }  // namespace
 
 size_t fft_row_smem(int Nx) { return sizeof(float2) * 3 * (size_t)Nx; }
+
+int fft_small_len(int n)
+{
+    for (int M = 3; M <= 5; ++M)
+        if (32 * M >= n) return 32 * M;
+    return 0;
+}
 size_t fft_col_smem(int Ny, int cpc) { return sizeof(float2) * ((size_t)2 * Ny * cpc + Ny); }
 
 cudaError_t launch_fft_twiddles(const FFTArgs& f, cudaStream_t s)
@@ -358,11 +589,16 @@ static cudaError_t optin_all(const FFTArgs& f)
 
 // forward / inverse row pass over `pairs` row pairs of each of nprob problems:
 // the warp kernels where Nx allows, else the shared-memory Stockham kernels
-static cudaError_t rows_fwd(const FFTArgs& f, const RowIO& r, const PassArgs& a, int pairs,
+// a one-dimensional grid of nblk CTAs for each of nprob problems
+static bool grid_ok(long long nblk, long long nprob) { return nblk * nprob <= 0x7fffffffLL; }
+
+static cudaError_t rows_fwd(const FFTArgs& f, RowIO r, const PassArgs& a, int pairs,
                             int nprob, cudaStream_t s)
 {
     if (warp_rows_ok(f.Nx)) {
-        const dim3 grid((pairs + WROW_WARPS - 1) / WROW_WARPS, nprob);
+        r.nblk = (pairs + WROW_WARPS - 1) / WROW_WARPS;
+        if (!grid_ok(r.nblk, nprob)) return cudaErrorInvalidConfiguration;
+        const dim3 grid((unsigned)((long long)r.nblk * nprob));
         switch (f.Nx / 32) {
 #define WF_CASE(M_)                                                                          \
     case M_:                                                                                 \
@@ -374,15 +610,17 @@ static cudaError_t rows_fwd(const FFTArgs& f, const RowIO& r, const PassArgs& a,
         default: return cudaErrorInvalidValue;
         }
     } else {
-        GF_LAUNCH_PDL(k_fft_rows_fwd, dim3(pairs, nprob), dim3(ROW_THREADS), fft_row_smem(f.Nx), s,
-                      f, r, a);
+        r.nblk = pairs;
+        if (!grid_ok(r.nblk, nprob)) return cudaErrorInvalidConfiguration;
+        GF_LAUNCH_PDL(k_fft_rows_fwd, dim3((unsigned)((long long)pairs * nprob)), dim3(ROW_THREADS),
+                      fft_row_smem(f.Nx), s, f, r, a);
     }
     GF_COUNT_LAUNCH();
     return cudaSuccess;
 }
 
 // column pass (mode 1: transform, PSF product, inverse; mode 0: forward only)
-static cudaError_t cols_pass(const FFTArgs& f, const ColIO& c, const PassArgs& a, int nprob,
+static cudaError_t cols_pass(const FFTArgs& f, ColIO c, const PassArgs& a, int nprob,
                              int mode, cudaStream_t s)
 {
     const int Kx = f.Nx / 2 + 1;
@@ -392,17 +630,21 @@ static cudaError_t cols_pass(const FFTArgs& f, const ColIO& c, const PassArgs& a
     if (mode == 1)
         while (fc.cpc > 2 && (long long)nprob * ((Kx + fc.cpc - 1) / fc.cpc) < 4 * 152) fc.cpc /= 2;
     fc.flops_col = f.flops_col * (float)fc.cpc / (float)f.cpc;
-    GF_LAUNCH_PDL(k_fft_cols, dim3((Kx + fc.cpc - 1) / fc.cpc, nprob), dim3(COL_THREADS),
+    c.nblk = (Kx + fc.cpc - 1) / fc.cpc;
+    if (!grid_ok(c.nblk, nprob)) return cudaErrorInvalidConfiguration;
+    GF_LAUNCH_PDL(k_fft_cols, dim3((unsigned)((long long)c.nblk * nprob)), dim3(COL_THREADS),
                   fft_col_smem(fc.Ny, fc.cpc), s, fc, c, a, mode);
     GF_COUNT_LAUNCH();
     return cudaSuccess;
 }
 
-static cudaError_t rows_inv(const FFTArgs& f, const RowInvIO& v, const PassArgs& a, int pairs,
+static cudaError_t rows_inv(const FFTArgs& f, RowInvIO v, const PassArgs& a, int pairs,
                             int nprob, cudaStream_t s)
 {
     if (warp_rows_ok(f.Nx)) {
-        const dim3 grid((pairs + WROW_WARPS - 1) / WROW_WARPS, nprob);
+        v.nblk = (pairs + WROW_WARPS - 1) / WROW_WARPS;
+        if (!grid_ok(v.nblk, nprob)) return cudaErrorInvalidConfiguration;
+        const dim3 grid((unsigned)((long long)v.nblk * nprob));
         switch (f.Nx / 32) {
 #define WF_CASE(M_)                                                                          \
     case M_:                                                                                 \
@@ -414,8 +656,10 @@ static cudaError_t rows_inv(const FFTArgs& f, const RowInvIO& v, const PassArgs&
         default: return cudaErrorInvalidValue;
         }
     } else {
-        GF_LAUNCH_PDL(k_fft_rows_inv, dim3(pairs, nprob), dim3(ROW_THREADS), fft_row_smem(f.Nx), s,
-                      f, v, a);
+        v.nblk = pairs;
+        if (!grid_ok(v.nblk, nprob)) return cudaErrorInvalidConfiguration;
+        GF_LAUNCH_PDL(k_fft_rows_inv, dim3((unsigned)((long long)pairs * nprob)), dim3(ROW_THREADS),
+                      fft_row_smem(f.Nx), s, f, v, a);
     }
     GF_COUNT_LAUNCH();
     return cudaSuccess;
@@ -424,7 +668,7 @@ static cudaError_t rows_inv(const FFTArgs& f, const RowInvIO& v, const PassArgs&
 cudaError_t launch_psf_wrap(const FFTArgs& f, int count, const StampInfo* st, const float* psf,
                             cudaStream_t s)
 {
-    k_psf_wrap<<<dim3(8, count), 256, 0, s>>>(f, count, st, psf);
+    k_psf_wrap<<<dim3(8 * count), 256, 0, s>>>(f, count, st, psf);
     GF_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -434,14 +678,29 @@ cudaError_t launch_psf_wrap(const FFTArgs& f, int count, const StampInfo* st, co
 cudaError_t launch_fft_psf(const FFTArgs& f, int count, const StampInfo* st, const float* psf,
                            cudaStream_t s)
 {
-    cudaError_t e = optin_all(f);
+    cudaError_t e = f.small ? cudaSuccess : optin_all(f);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(f.psfgrid, 0, sizeof(float) * (size_t)count * f.Ny * f.Nx, s);
     if (e != cudaSuccess) return e;
-    k_psf_wrap<<<dim3(8, count), 256, 0, s>>>(f, count, st, psf);
+    k_psf_wrap<<<dim3(8 * count), 256, 0, s>>>(f, count, st, psf);
     GF_COUNT_LAUNCH();
     PassArgs none;
     memset(&none, 0, sizeof(none));
+    if (f.small) {
+        SmallIO io;
+        memset(&io, 0, sizeof(io));
+        io.in = f.psfgrid;
+        io.in_stride = (long long)f.Ny * f.Nx;
+        io.ld = f.Nx;
+        io.width = f.Nx;
+        io.rows = f.Ny;
+        io.hperm = f.hhat;
+        io.nchan = 1;
+        io.psf_mode = 1;
+        e = launch_small(io, none, f, count, s);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     const int Kx = f.Nx / 2 + 1;
     RowIO r;
     r.in = f.psfgrid;
@@ -471,11 +730,33 @@ cudaError_t launch_fft_psf(const FFTArgs& f, int count, const StampInfo* st, con
 // scratch `spec` (count * nchan * He * Kx complex values).
 cudaError_t launch_conv_fft(const PassArgs& a, const FFTArgs& f, float2* spec, cudaStream_t s)
 {
-    cudaError_t e = optin_all(f);
-    if (e != cudaSuccess) return e;
     const StampInfo& s0 = f.st0;  // uniform stamp geometry (host copy)
     const int Kx = f.Nx / 2 + 1;
     const int nprob = a.count * a.nchan;
+    if (f.small) {
+        SmallIO io;
+        io.in = a.ext;
+        io.in_stride = (long long)s0.He * s0.We;
+        io.ld = s0.We;
+        io.width = s0.We;
+        io.rows = s0.He;
+        io.out = a.y;
+        io.out_stride = (long long)s0.H * s0.W;
+        io.row0 = s0.c;
+        io.col0 = s0.c;
+        io.H = s0.H;
+        io.W = s0.W;
+        io.hperm = f.hhat;
+        io.nchan = a.nchan;
+        io.psf_mode = 0;
+        io.flops = (float)(((s0.He + 1) / 2 + (s0.H + 1) / 2) * 5.0 * f.Nx * log2((double)f.Nx) +
+                           Kx * (10.0 * f.Ny * log2((double)f.Ny) + 6.0 * f.Ny));
+        cudaError_t e = launch_small(io, a, f, nprob, s);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+    cudaError_t e = optin_all(f);
+    if (e != cudaSuccess) return e;
     RowIO r;
     r.in = a.ext;
     r.in_stride = (long long)s0.He * s0.We;

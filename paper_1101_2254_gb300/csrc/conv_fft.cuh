@@ -9,6 +9,8 @@
 struct FFTArgs {
     int Nx, Ny;          // padded transform sizes (Nx even)
     int cpc;             // spectrum columns per CTA in the column pass
+    int small;           // 1: one CTA per transform (Nx, Ny in 32 x {3, 4, 5});
+                         // hhat then holds each column in warp-FFT order
     FFTPlan px, py;
     float2* tw_x;        // exp(-2 pi i k / Nx), k < Nx
     float2* tw_y;        // exp(-2 pi i k / Ny), k < Ny
@@ -27,12 +29,14 @@ struct RowIO {
     long long spec_stride;
     int out_rows;
     int nchan;
+    int nblk;            // CTAs per problem (set by the launcher)
 };
 
 struct ColIO {
     float2* spec;
     long long spec_stride;
     int rows_in, row0, nrows_out, nchan;
+    int nblk;            // CTAs per problem (set by the launcher)
 };
 
 struct RowInvIO {
@@ -42,9 +46,12 @@ struct RowInvIO {
     float* out;
     long long out_stride;
     int nchan;
+    int nblk;            // CTAs per problem (set by the launcher)
 };
 
 size_t fft_row_smem(int Nx);
+// the smallest 32 M >= n with M in {3, 4, 5} (the one-CTA transform), else 0
+int fft_small_len(int n);
 size_t fft_col_smem(int Ny, int cpc);
 cudaError_t launch_fft_twiddles(const FFTArgs& f, cudaStream_t s);
 cudaError_t launch_fft_psf(const FFTArgs& f, int count, const StampInfo* st, const float* psf,

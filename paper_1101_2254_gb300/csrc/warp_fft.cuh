@@ -133,3 +133,65 @@ __device__ __forceinline__ void warp_fft(float2 (&v)[M], const float2* tws)
 }
 
 __device__ __forceinline__ int bitrev5(int l) { return (int)(__brev((unsigned)l) >> 27); }
+
+// The twiddles one lane's warp_fft reads, kept in registers by a kernel that
+// runs many transforms of one length.  The butterfly of stage d then becomes
+// a = p + sg v (sg = -1 on the upper lane of the pair, +1 on the lower) and
+// v = a ws: the lower lane's factor is 1, and the last stage (d = 1, factor 1
+// on both lanes) has no product.  Every value is the one warp_fft computes.
+template <int M>
+struct WarpTw {
+    float2 rm[M];  // e^{-2 pi i k / M}
+    float2 tl[M];  // e^{-2 pi i l k2 / N}
+    float2 ws[4];  // stages d = 16, 8, 4, 2: the upper lane's twiddle, 1 on the lower
+    float sg[5];   // stages d = 16 .. 1: -1 on the upper lane, +1 on the lower
+};
+
+template <int M>
+__device__ __forceinline__ void warp_tw_load(WarpTw<M>& t, const float2* tws)
+{
+    constexpr int N = 32 * M;
+    const int l = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        t.rm[k] = wf_tw<false>(tws, 32 * k);
+        t.tl[k] = wf_tw<false>(tws, l * k);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int d = 16 >> i;
+        const bool upper = (l & d) != 0;
+        t.sg[i] = upper ? -1.0f : 1.0f;
+        if (i < 4) t.ws[i] = upper ? wf_tw<false>(tws, (l & (d - 1)) * (N / (2 * d))) : make_float2(1.0f, 0.0f);
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 wf_dir(float2 w)
+{
+    return INV ? make_float2(w.x, -w.y) : w;
+}
+
+// warp_fft with the lane's twiddles in registers (same layout in and out,
+// same values)
+template <int M, bool INV>
+__device__ __forceinline__ void warp_fft_r(float2 (&v)[M], const WarpTw<M>& t)
+{
+    float2 rm[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) rm[k] = wf_dir<INV>(t.rm[k]);
+    wf_reg_dft<M>(v, rm);
+#pragma unroll
+    for (int k2 = 1; k2 < M; ++k2) v[k2] = cmul(v[k2], wf_dir<INV>(t.tl[k2]));
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int d = 16 >> i;
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) {
+            const float px = __shfl_xor_sync(0xffffffffu, v[k2].x, d);
+            const float py = __shfl_xor_sync(0xffffffffu, v[k2].y, d);
+            const float2 a = make_float2(fmaf(t.sg[i], v[k2].x, px), fmaf(t.sg[i], v[k2].y, py));
+            v[k2] = i < 4 ? cmul(a, wf_dir<INV>(t.ws[i])) : a;
+        }
+    }
+}

@@ -335,6 +335,26 @@ def test_fft_equals_direct_on_gpu(gf):
     assert_pix_close(a, b, rel=1e-5, floor=FFT_FLOOR, what="fft vs direct")
 
 
+def test_fft_batch_of_more_problems_than_grid_rows(gf):
+    """66,000 stamps in one FFT evaluation: more transforms per pass than the
+    65,535 a grid's y dimension holds.  Every stamp equals the direct sum."""
+    import torch
+    from paper_1101_2254_gb300 import learned
+    count = 66000
+    p, psf = gf.train_sample(11, count, learned.PSF_SIZE)
+    b = learned.uniform_batch(count)
+    out = {}
+    for m in (gf.CONV_DIRECT, gf.CONV_FFT):
+        _, out[m] = gf.evaluate_batch_dev(learned.stamp_desc(conv_method=m), b, p, None, None,
+                                          psf.reshape(-1))
+    o = out[gf.CONV_DIRECT].view(count, -1).double()
+    g = out[gf.CONV_FFT].view(count, -1).double()
+    bound = 1e-5 * o.abs() + FFT_FLOOR * o.abs().amax(dim=1, keepdim=True)
+    bad = (g - o).abs() > bound
+    assert not bad.any(), (int(bad.sum()), torch.nonzero(bad)[:4].tolist())
+    assert bool((o.abs().amax(dim=1) > 0).all())  # every stamp was rendered
+
+
 def test_lm_fit_stamp64_fft_matches_oracle(gf):
     st = synth.stamp64()
     m_true, img, sig = noisy_image(st)
@@ -502,6 +522,63 @@ def test_convolve_fft_warp_rows(gf, M):
     g = gf.convolve(d, cuda(ext), cuda(psf)).cpu().numpy()
     o = oracle.convolve_direct(ext.astype(np.float64), psf.astype(np.float64))
     assert_pix_close(g, o, rel=1e-5, floor=FFT_FLOOR, what=f"fft conv 32x{M} rows")
+
+
+# Extended grids up to 160 x 160 are transformed one CTA each (the spectrum in
+# shared memory, padded to Nx, Ny in {96, 128, 160}): every (Nx, Ny) pair, with
+# odd grid and output heights (the last row pair has one row) and ragged widths.
+@pytest.mark.parametrize("He,We", [(95, 88), (95, 127), (95, 160), (127, 70), (128, 128),
+                                   (127, 159), (159, 96), (159, 121), (160, 160)])
+def test_convolve_fft_one_cta(gf, He, We):
+    P = 9
+    c = (P - 1) // 2
+    H, W = He - 2 * c, We - 2 * c
+    rng = np.random.default_rng(He * 1000 + We)
+    ext = rng.uniform(0.0, 2.0, (He, We)).astype(np.float32)
+    psf = synth.random_psf(P, He + We)
+    d = gf.make_desc(H, W, P, [synth.SERSIC], conv_method=gf.CONV_FFT)
+    g = gf.convolve(d, cuda(ext), cuda(psf)).cpu().numpy()
+    o = oracle.convolve_direct(ext.astype(np.float64), psf.astype(np.float64))
+    assert_pix_close(g, o, rel=1e-5, floor=FFT_FLOOR, what=f"fft conv one CTA {He}x{We}")
+
+
+# Grids taller than 160 rows take the three-pass kernels also for Nx = 96..160.
+@pytest.mark.parametrize("M", [3, 4, 5])
+def test_convolve_fft_three_pass_narrow(gf, M):
+    P = 9
+    c = (P - 1) // 2
+    W = 32 * M - 2 * c
+    H = 171
+    rng = np.random.default_rng(50 + M)
+    ext = rng.uniform(0.0, 2.0, (H + 2 * c, W + 2 * c)).astype(np.float32)
+    psf = synth.random_psf(P, 3 * M)
+    d = gf.make_desc(H, W, P, [synth.SERSIC], conv_method=gf.CONV_FFT)
+    g = gf.convolve(d, cuda(ext), cuda(psf)).cpu().numpy()
+    o = oracle.convolve_direct(ext.astype(np.float64), psf.astype(np.float64))
+    assert_pix_close(g, o, rel=1e-5, floor=FFT_FLOOR, what=f"fft conv three-pass 32x{M}")
+
+
+def test_lm_fft_batch_equals_single_stamp_fits(gf):
+    """Uniform 64 x 64 stamps through the one-CTA transform: the batched fit
+    (all channels and rungs of all stamps per launch, stamps leaving the loop at
+    different bodies) equals each stamp fitted alone, bit for bit."""
+    sts = synth.batch_stamps(5, seed=9, smin=64, smax=64, psf_size=25)
+    d0 = sts[0]
+    imgs, sigs, psfs, p0 = [], [], [], []
+    for st in sts:
+        m, img, sig = noisy_image(st)
+        imgs.append(img.ravel()); sigs.append(sig.ravel()); psfs.append(st.psf.ravel())
+        p0.append(st.guess())
+    d = gf.make_desc(64, 64, d0.P, d0.kinds, d0.os_factor, 8, conv_method=gf.CONV_FFT)
+    b = gf.make_batch([64] * len(sts), [64] * len(sts), psf_size=d0.P)
+    pb, rb = gf.lm_fit_batch(d, b, np.array(p0), d0.fixed, cuda(np.concatenate(imgs)),
+                             cuda(np.concatenate(sigs)), cuda(np.concatenate(psfs)))
+    assert len({r["iters"] for r in rb}) > 1  # the stamps leave at different bodies
+    for i, st in enumerate(sts):
+        ps, rs = gf.lm_fit(d, p0[i], st.fixed, cuda(imgs[i]), cuda(sigs[i]), cuda(st.psf))
+        assert np.array_equal(pb[i], ps), (i, pb[i], ps)
+        assert rb[i]["iters"] == rs["iters"] and rb[i]["status"] == rs["status"]
+        assert rb[i]["chi2"] == rs["chi2"]
 
 
 # Column lengths Ny = 32 M with the Stockham column pass (widths give a ragged
