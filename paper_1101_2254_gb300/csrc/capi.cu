@@ -1638,8 +1638,9 @@ static gf_status lm_fit_impl(const gf_desc* d, const gf_batch* b, double* params
     at_.phase = PH_TRIAL;
     at_.nchan = at_.chan_stride = L.rungs;  // one trial channel per rung of the ladder
     set_grids(at_, L, L.rungs);
-    // the direct path reduces the trial chi^2 inside the convolution's epilogue
-    at_.conv_chi2 = pl.method == GF_CONV_DIRECT ? 1 : 0;
+    // the direct path and the one-CTA FFT reduce the trial chi^2 inside the
+    // convolution (no convolved trial model written)
+    at_.conv_chi2 = (pl.method == GF_CONV_DIRECT || (pl.method == GF_CONV_FFT && pl.small)) ? 1 : 0;
     if (at_.conv_chi2) at_.max_trial_slots = (int)std::min<long long>(L.max_wb, INT32_MAX);
     // each pass walks the list of stamps in its phase, rebuilt every body
     aj.wl.n = at<int>(ws, L.wl_n[0]);

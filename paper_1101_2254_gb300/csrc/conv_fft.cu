@@ -360,6 +360,7 @@ __device__ __forceinline__ const WarpTw<MY>& select_tw(const WarpTw<MX>& rx, con
 // CTAs per SM that the kernel's shared memory allows (227 KB per SM), which
 // its register budget is held to
 constexpr size_t small_smem(int Nx, int Ny);
+constexpr size_t small_part_extra(int Nx, int Ny);
 template <int MX, int MY>
 constexpr int small_ctas_per_sm()
 {
@@ -467,8 +468,26 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32, small_ctas_per_sm<MX, MY>())
     }
     if (io.psf_mode) return;
     __syncthreads();
-    // rows: inverse of the packing, output rows (i0, i0 + 1)
+    // rows: inverse of the packing, output rows (i0, i0 + 1).  In an LM trial
+    // pass (a.conv_chi2) nothing is written: each row pair's chi^2 per 32
+    // columns goes to part[pair][column block] (the twiddle tables' space,
+    // free by now), and the 16 x 32 blocks' sums to the stamp's partial slots.
     float* out = io.out + (long long)p * io.out_stride;
+    static_assert(sizeof(CSum) == sizeof(float2), "a partial takes one float2 slot");
+    CSum* part = reinterpret_cast<CSum*>(small_part_extra(Nx, Ny) == 0 ? sm
+                                         : spec + Ny * Kx + SMALL_WARPS * NZ);
+    const int nbx = (io.W + 31) / 32;
+    const float* img = nullptr;
+    const float* sig = nullptr;
+    float tmw = 0.0f, tmsky = 0.0f;
+    if (a.conv_chi2) {
+        const StampInfo& st = a.st[b];
+        const Channel& chn = a.chan[(long long)b * a.chan_stride + (p - b * io.nchan)];
+        tmw = chn.mweight;
+        tmsky = chn.msky;
+        img = a.img + st.pix_off;
+        sig = a.sig + st.pix_off;
+    }
     for (int pr = warp; 2 * pr < io.H; pr += SMALL_WARPS) {
         const int i0 = 2 * pr, i1 = i0 + 1;
         const bool has1 = i1 < io.H;
@@ -493,21 +512,73 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32, small_ctas_per_sm<MX, MY>())
 #pragma unroll
         for (int k2 = 0; k2 < MX; ++k2) z[k2 + MX * br] = v[k2];
         __syncwarp();
-        for (int j = l; j < io.W; j += 32) {
-            const float2 w = z[io.col0 + j];
-            out[(long long)i0 * io.W + j] = w.x;
-            if (has1) out[(long long)i1 * io.W + j] = w.y;
+        if (a.conv_chi2) {
+            for (int t = 0; t < nbx; ++t) {
+                const int j = l + 32 * t;
+                CSum cs = {0.0f, 0.0f};
+                if (j < io.W) {
+                    const float2 w = z[io.col0 + j];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        if (r == 1 && !has1) break;
+                        const long long px = (long long)(i0 + r) * io.W + j;
+                        const float d = __ldg(&img[px]), sg = __ldg(&sig[px]);
+                        if (isfinite(d) && isfinite(sg) && sg > 0.0f) {
+                            const float zr = (d - fmaf(tmw, r ? w.y : w.x, tmsky)) / sg;
+                            csum_add(cs, zr * zr);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    CSum other;
+                    other.s = __shfl_down_sync(0xffffffffu, cs.s, o);
+                    other.c = __shfl_down_sync(0xffffffffu, cs.c, o);
+                    cs = csum_merge(cs, other);
+                }
+                if (l == 0) part[pr * nbx + t] = cs;
+            }
+        } else {
+            for (int j = l; j < io.W; j += 32) {
+                const float2 w = z[io.col0 + j];
+                out[(long long)i0 * io.W + j] = w.x;
+                if (has1) out[(long long)i1 * io.W + j] = w.y;
+            }
         }
         __syncwarp();
     }
+    if (a.conv_chi2) {
+        // each 16 x 32 block: its 8 row pairs' partials merged in row order
+        __syncthreads();
+        const int npo = (io.H + 1) / 2, nby = (io.H + 15) / 16;
+        const StampInfo& st = a.st[b];
+        for (int q = threadIdx.x; q < nby * nbx; q += blockDim.x) {
+            const int by = q / nbx, bx = q - by * nbx;
+            CSum cs = part[(8 * by) * nbx + bx];
+            for (int pr = 8 * by + 1; pr < min(npo, 8 * by + 8); ++pr)
+                cs = csum_merge(cs, part[pr * nbx + bx]);
+            a.partial[((long long)st.wb_off + q) * io.nchan + (p - b * io.nchan)] = cs.s + cs.c;
+        }
+    }
     if (a.work && threadIdx.x == 0) atomicAdd(&a.work[PROF_CONV], (unsigned long long)io.flops);
+}
+
+// the trial pass's row-pair chi^2 partials, (Ny / 2) x (Nx / 32) CSum values:
+// in the twiddle tables' space where they fit (no extra bytes), else in a
+// region of their own after the reordering rows
+constexpr size_t small_part_extra(int Nx, int Ny)
+{
+    const size_t need = (size_t)(Ny / 2) * (Nx / 32) * sizeof(float2);
+    const size_t have = sizeof(float2) * ((size_t)warp_fft_table_len(Nx) + (size_t)warp_fft_table_len(Ny));
+    return need > have ? need : 0;
 }
 
 constexpr size_t small_smem(int Nx, int Ny)
 {
     // tables, the half spectrum, one reordering row per warp
     return sizeof(float2) * ((size_t)warp_fft_table_len(Nx) + (size_t)warp_fft_table_len(Ny) +
-                             (size_t)Ny * (Nx / 2 + 1) + (size_t)SMALL_WARPS * (Nx > Ny ? Nx : Ny));
+                             (size_t)Ny * (Nx / 2 + 1) + (size_t)SMALL_WARPS * (Nx > Ny ? Nx : Ny)) +
+           small_part_extra(Nx, Ny);
 }
 
 template <int MX, int MY>

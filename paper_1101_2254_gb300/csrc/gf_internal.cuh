@@ -548,9 +548,10 @@ struct PassArgs {
     int conv_ty;               // direct-convolution tile height (32 or 16)
     int max_trial_slots;       // most trial-pass partial slots of one stamp (reduce blocks, or
                                // 16 x 32 output blocks with conv_chi2)
-    int conv_chi2;             // an LM trial pass on the direct path: the convolution writes the
-                               // chi^2 partial of each 16 x 32 output block per rung (channel),
-                               // slot st.wb_off + block, instead of the convolved tile
+    int conv_chi2;             // an LM trial pass on the direct path or the one-CTA FFT: the
+                               // convolution writes the chi^2 partial of each 16 x 32 output
+                               // block per rung (channel), slot st.wb_off + block, instead of
+                               // the convolved tile
     float* ext;                // channel grids: ext + ext_index(st[b], nchan, k)
     float* y;                  // convolved channels: y + y_index(st[b], nchan, k)
     const float* psf;

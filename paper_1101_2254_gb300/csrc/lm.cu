@@ -731,7 +731,7 @@ __device__ void lm_apply_trials(const PassArgs& a, LMState& L, int phase, int nr
 }
 
 // the stamp's partial slots of a trial pass: its reduce blocks, or its 16 x 32
-// output blocks when the direct convolution reduced the trial
+// output blocks when the convolution (direct, or the one-CTA FFT) reduced the trial
 __device__ __forceinline__ void trial_slots(const PassArgs& a, int b, int& b0, int& b1)
 {
     if (a.conv_chi2) {
