@@ -68,7 +68,7 @@ __host__ __device__ __forceinline__ int comp_nslots(int kind)
 #define GF_COMP_MAXSLOTS 14
 
 // Float32 constants of one component at one parameter vector.
-struct CompConst {
+struct __align__(16) CompConst {  // 112 bytes; aligned so that field loads combine
     float x0h, x0l, y0h, y0l;  // centre split hi + lo so that x - x0 keeps ~48 bits
     float cs, sn, invq;        // rotation and axis ratio
     float C, invC;             // generalised-radius exponent C = c + 2
@@ -88,6 +88,7 @@ struct CompConst {
                                // cos 4 phi_4, sin 4 phi_4 (e4..e8)
     int pad_c[3];
 };
+static_assert(sizeof(CompConst) == 112, "CompConst layout");
 
 struct Channel {
     int type;       // CH_*
@@ -262,6 +263,62 @@ static __device__ __noinline__ float comp_eval_ext(const CompConst& k, float xi,
 // point-source components (those take comp_eval_ext).  The kernels are
 // compiled for each, so that calls without the longer forms keep the shorter
 // evaluator.
+// comp_eval's arithmetic in three steps (the same operations in the same
+// order, so the same floats), for a Jacobian pass that reuses the first ones
+// for a finite-difference channel whose perturbed slot enters only later:
+//   the generalised radius r from the pixel, centre, rotation and axis ratio;
+//   log2 t for t = r / r_e (log2(1 + t^2) for a Moffat);
+//   the profile from t and that logarithm.
+// comp_eval (below) keeps its one-piece form, which compiles to fewer
+// registers in the one-channel passes.
+template <int EV>
+__device__ __forceinline__ float comp_radius(const CompConst& k, float xi, float yi, float ox,
+                                             float oy)
+{
+    // dx = x - x0 with x = xi + ox: the integer part against the hi word is exact
+    // near the centre (Sterbenz), the sub-pixel offset absorbs the lo word.
+    float dx = (xi - k.x0h) + (ox - k.x0l);
+    float dy = (yi - k.y0h) + (oy - k.y0l);
+    float xp = fmaf(dx, k.cs, dy * k.sn);
+    float yp = fmaf(dy, k.cs, -dx * k.sn) * k.invq;
+    float r;
+    if (k.ellipse) {
+        r = sqrtf(fmaf(xp, xp, yp * yp));
+    } else {
+        float ax = exp2f(k.C * log2f(fabsf(xp)));
+        float ay = exp2f(k.C * log2f(fabsf(yp)));
+        r = exp2f(k.invC * log2f(ax + ay));
+    }
+    return r;
+}
+
+template <int EV>
+__device__ __forceinline__ float comp_log_t(const CompConst& k, float t)
+{
+    if (EV >= 1) {
+        const bool moffat = k.kind == GF_MOFFAT;
+        return log2f(moffat ? fmaf(t, t, 1.0f) : t);
+    }
+    return log2f(t);
+}
+
+template <int EV>
+__device__ __forceinline__ float comp_tail(const CompConst& k, float t, float lt)
+{
+    float u;
+    if (EV >= 1) {
+        // one logarithm for every kind: log2 t (Sersic, Gaussian) or
+        // log2(1 + t^2) (Moffat), chosen by selects so the loop body stays
+        // branch-free
+        const bool moffat = k.kind == GF_MOFFAT;
+        u = (k.invn == 1.0f) ? t : exp2f(k.invn * lt);
+        u = moffat ? lt : u;
+    } else {
+        u = (k.invn == 1.0f) ? t : exp2f(k.invn * lt);
+    }
+    return k.amp * expf(fmaf(-k.b, u, k.b0));
+}
+
 template <int EV>
 __device__ __forceinline__ float comp_eval(const CompConst& k, float xi, float yi, float ox,
                                            float oy)
@@ -295,6 +352,43 @@ __device__ __forceinline__ float comp_eval(const CompConst& k, float xi, float y
         u = (k.invn == 1.0f) ? t : exp2f(k.invn * log2f(t));
     }
     return k.amp * expf(fmaf(-k.b, u, k.b0));
+}
+
+// A component evaluated once per pixel in a Jacobian pass, with the radius,
+// t and log2 t its finite-difference channels may reuse
+struct EvalCursor {
+    int comp;        // the component held (-1: none yet)
+    float v, r, t, lt;
+};
+
+template <int EV>
+__device__ __forceinline__ void comp_eval_keep(const CompConst& k, float xi, float yi, float ox,
+                                               float oy, EvalCursor& e)
+{
+    if (EV == 2 && k.kind >= GF_KING) {
+        e.v = comp_eval_ext(k, xi, yi, ox, oy);
+        return;
+    }
+    e.r = comp_radius<EV>(k, xi, yi, ox, oy);
+    e.t = e.r * k.invr;
+    e.lt = comp_log_t<EV>(k, e.t);
+    e.v = comp_tail<EV>(k, e.t, e.lt);
+}
+
+// What a finite-difference channel's perturbed component shares with the
+// component at p (the same floats, so the reused steps give the values a full
+// evaluation gives): 2 radius and r_e (only the profile's tail differs: n,
+// beta, b_n), 1 the radius (r_e too differs), 0 nothing reused.
+__device__ __forceinline__ int fd_reuse_level(const CompConst& k, const CompConst& p)
+{
+    if (is_sky_kind(k.kind) || k.kind != p.kind || k.kind >= GF_KING) return 0;
+    auto same = [](float u, float v) { return __float_as_int(u) == __float_as_int(v); };
+    // the radius's inputs
+    if (!(same(k.x0h, p.x0h) && same(k.x0l, p.x0l) && same(k.y0h, p.y0h) && same(k.y0l, p.y0l) &&
+          same(k.cs, p.cs) && same(k.sn, p.sn) && same(k.invq, p.invq) && same(k.C, p.C) &&
+          same(k.invC, p.invC) && k.ellipse == p.ellipse))
+        return 0;
+    return __float_as_int(k.invr) == __float_as_int(p.invr) ? 2 : 1;
 }
 
 // The unit-amplitude profile of component k at grid point (xi + ox, yi + oy)
@@ -421,6 +515,72 @@ __device__ __forceinline__ float channel_value(const Channel& ch, float xi, floa
     float a = comp_eval<EV>(ch.pert, xi, yi, ox, oy);
     float b = comp_eval<EV>(ch.cc[ch.comp], xi, yi, ox, oy);
     return (a - b) * ch.scale;
+}
+
+// comp_eval at two points, the two evaluations' steps interleaved (two
+// independent dependency chains for the scheduler); each value is the float
+// comp_eval gives for its point.
+template <int EV>
+__device__ __forceinline__ void comp_eval2(const CompConst& k, float x0, float y0, float x1,
+                                           float y1, float& v0, float& v1)
+{
+    if (EV == 2 && k.kind >= GF_KING) {
+        v0 = comp_eval_ext(k, x0, y0, 0.0f, 0.0f);
+        v1 = comp_eval_ext(k, x1, y1, 0.0f, 0.0f);
+        return;
+    }
+    const float dx0 = (x0 - k.x0h) + (0.0f - k.x0l), dy0 = (y0 - k.y0h) + (0.0f - k.y0l);
+    const float dx1 = (x1 - k.x0h) + (0.0f - k.x0l), dy1 = (y1 - k.y0h) + (0.0f - k.y0l);
+    const float xp0 = fmaf(dx0, k.cs, dy0 * k.sn), xp1 = fmaf(dx1, k.cs, dy1 * k.sn);
+    const float yp0 = fmaf(dy0, k.cs, -dx0 * k.sn) * k.invq;
+    const float yp1 = fmaf(dy1, k.cs, -dx1 * k.sn) * k.invq;
+    float r0, r1;
+    if (k.ellipse) {
+        r0 = sqrtf(fmaf(xp0, xp0, yp0 * yp0));
+        r1 = sqrtf(fmaf(xp1, xp1, yp1 * yp1));
+    } else {
+        const float ax0 = exp2f(k.C * log2f(fabsf(xp0))), ax1 = exp2f(k.C * log2f(fabsf(xp1)));
+        const float ay0 = exp2f(k.C * log2f(fabsf(yp0))), ay1 = exp2f(k.C * log2f(fabsf(yp1)));
+        r0 = exp2f(k.invC * log2f(ax0 + ay0));
+        r1 = exp2f(k.invC * log2f(ax1 + ay1));
+    }
+    const float t0 = r0 * k.invr, t1 = r1 * k.invr;
+    float u0, u1;
+    if (EV >= 1) {
+        const bool moffat = k.kind == GF_MOFFAT;
+        const float lt0 = log2f(moffat ? fmaf(t0, t0, 1.0f) : t0);
+        const float lt1 = log2f(moffat ? fmaf(t1, t1, 1.0f) : t1);
+        u0 = (k.invn == 1.0f) ? t0 : exp2f(k.invn * lt0);
+        u1 = (k.invn == 1.0f) ? t1 : exp2f(k.invn * lt1);
+        u0 = moffat ? lt0 : u0;
+        u1 = moffat ? lt1 : u1;
+    } else {
+        u0 = (k.invn == 1.0f) ? t0 : exp2f(k.invn * log2f(t0));
+        u1 = (k.invn == 1.0f) ? t1 : exp2f(k.invn * log2f(t1));
+    }
+    v0 = k.amp * expf(fmaf(-k.b, u0, k.b0));
+    v1 = k.amp * expf(fmaf(-k.b, u1, k.b0));
+}
+
+// channel_value at two pixel centres (ox = oy = 0)
+template <int EV>
+__device__ __forceinline__ void channel_value2(const Channel& ch, float x0, float y0, float x1,
+                                               float y1, float& v0, float& v1)
+{
+    if (ch.type != CH_SUM) {
+        v0 = channel_value<EV>(ch, x0, y0, 0.0f, 0.0f);
+        v1 = channel_value<EV>(ch, x1, y1, 0.0f, 0.0f);
+        return;
+    }
+    v0 = fmaf(ch.tgy, y0 - ch.pyc, fmaf(ch.tgx, x0 - ch.pxc, ch.sky));
+    v1 = fmaf(ch.tgy, y1 - ch.pyc, fmaf(ch.tgx, x1 - ch.pxc, ch.sky));
+    for (int k = 0; k < ch.ncomp; ++k)
+        if (!is_sky_kind(ch.cc[k].kind)) {
+            float a0, a1;
+            comp_eval2<EV>(ch.cc[k], x0, y0, x1, y1, a0, a1);
+            v0 += a0;
+            v1 += a1;
+        }
 }
 
 // Neumaier compensated accumulation in float32

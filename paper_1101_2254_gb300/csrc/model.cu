@@ -66,6 +66,18 @@ __device__ __forceinline__ int div_mag(int x, int d, unsigned mag)
     return q;
 }
 
+// Grid pixel pix of the stamp's extended grid: its stamp coordinates (i, j),
+// and whether the plain body evaluates it (false inside the oversampling
+// block, which the block bodies evaluate).
+__device__ __forceinline__ bool grid_pixel(const StampInfo& st, unsigned mag, int pix, int& i, int& j)
+{
+    const int ie = div_mag(pix, st.We, mag), je = pix - ie * st.We;
+    i = ie - st.c;
+    j = je - st.c;
+    return !(st.os_factor > 1 && i >= st.os_y0 && i < st.os_y0 + st.os_box && j >= st.os_x0 &&
+             j < st.os_x0 + st.os_box);
+}
+
 // Work item = (channel, block of MODEL_THREADS grid pixels of a listed stamp).
 // A CTA's items are consecutive, so the (channel, block) pair advances by a
 // counter instead of a division per item.
@@ -87,7 +99,10 @@ __device__ __forceinline__ void body_model(const PassArgs& a, int vb, int vg)
         k = (int)(it0 / tot);
         blk = (int)(it0 - (long long)k * tot);
     }
-    for (long long it = it0; it < it1; ++it, ++blk) {
+    // Two consecutive items of the same stamp and channel are evaluated
+    // together (a thread's two pixels are independent chains the scheduler
+    // interleaves); a lone item at a stamp's end or the range's end alone.
+    for (long long it = it0; it < it1;) {
         if (blk == tot) {
             blk = 0;
             ++k;
@@ -105,24 +120,26 @@ __device__ __forceinline__ void body_model(const PassArgs& a, int vb, int vg)
             cur_b = b;
             cur_k = k;
         }
+        const bool two = it + 1 < it1 && blk + 1 < pre[li + 1];
         const int npix = st.He * st.We;  // stamps are validated below 2^31 pixels
-        const int pix = (blk - pre[li]) * MODEL_THREADS + threadIdx.x;
-        bool write = pix < npix;
-        int i = 0, j = 0;
-        if (write) {
-            const int ie = div_mag(pix, st.We, mag), je = pix - ie * st.We;
-            i = ie - st.c;
-            j = je - st.c;
-            write = !(st.os_factor > 1 && i >= st.os_y0 && i < st.os_y0 + st.os_box &&
-                      j >= st.os_x0 && j < st.os_x0 + st.os_box);
+        const int pix0 = (blk - pre[li]) * MODEL_THREADS + threadIdx.x;
+        const int pix1 = pix0 + MODEL_THREADS;
+        int i0 = 0, j0 = 0, i1 = 0, j1 = 0;
+        const bool w0 = pix0 < npix && grid_pixel(st, mag, pix0, i0, j0);
+        const bool w1 = two && pix1 < npix && grid_pixel(st, mag, pix1, i1, j1);
+        if (w0 || w1) {
+            float v0, v1;
+            channel_value2<EV>(ch, (float)j0, (float)i0, (float)j1, (float)i1, v0, v1);
+            float* E = a.ext + ext_index(st, a.nchan, k);
+            if (w0) E[pix0] = v0;
+            if (w1) E[pix1] = v1;
         }
-        if (write)
-            a.ext[ext_index(st, a.nchan, k) + pix] =
-                channel_value<EV>(ch, (float)j, (float)i, 0.0f, 0.0f);
         if (a.work) {
-            const int cnt = __syncthreads_count(write);
+            const int cnt = __syncthreads_count(w0) + __syncthreads_count(w1);
             if (threadIdx.x == 0) atomicAdd(&a.work[PROF_MODEL], 4ull * (unsigned long long)cnt);
         }
+        it += two ? 2 : 1;
+        blk += two ? 2 : 1;
     }
 }
 
@@ -211,11 +228,62 @@ __device__ __forceinline__ void comp_base(const Channel& c0, float* base, float 
                                                                  : 0.0f;
 }
 
+// Jacobian-pass value of channel c.  The cursor holds the last component
+// evaluated at p (with its radius and log2 t): a channel of the same component
+// reuses it, and a finite-difference channel reuses as much of it as its
+// perturbed slot leaves unchanged (lvl, from fd_reuse_level).  Every value is
+// the float a full evaluation gives.
+template <int EV>
+__device__ __forceinline__ float jac_value(const Channel* chs, int c, int lvl, EvalCursor& e,
+                                           float xi, float yi, float ox, float oy)
+{
+    const Channel& ch = chs[c];
+    if (ch.type == CH_PLANE) return ch.dslot == 0 ? xi - ch.pxc : yi - ch.pyc;  // pixel centre
+    if (ch.type == CH_DERIV) {
+        float g[8];
+        comp_grad(ch.cc[ch.comp], xi, yi, ox, oy, ch.dbdn, g);
+        return grad_pick(g, ch.dslot) * ch.scale;
+    }
+    if (ch.comp != e.comp) {
+        e.comp = ch.comp;
+        const CompConst& k = chs[0].cc[ch.comp];
+        if (ch.comp < chs[0].ncomp && !is_sky_kind(k.kind))
+            comp_eval_keep<EV>(k, xi, yi, ox, oy, e);
+        else
+            e.v = 0.0f;
+    }
+    if (ch.type == CH_SHAPE) return e.v;
+    float pv;
+    if (lvl == 2) {
+        pv = comp_tail<EV>(ch.pert, e.t, e.lt);
+    } else if (lvl == 1) {
+        const float t = e.r * ch.pert.invr;
+        pv = comp_tail<EV>(ch.pert, t, comp_log_t<EV>(ch.pert, t));
+    } else {
+        pv = comp_eval<EV>(ch.pert, xi, yi, ox, oy);
+    }
+    return (pv - e.v) * ch.scale;
+}
+
+// the reuse level of each channel of a Jacobian pass (after its channels are
+// in shared memory; one barrier)
+__device__ __forceinline__ void fd_levels(const Channel* chs, int nch, int* lvl)
+{
+    const int c = threadIdx.x;
+    if (c < nch) {
+        const Channel& ch = chs[c];
+        lvl[c] = (ch.type == CH_FD && ch.comp < chs[0].ncomp) ? fd_reuse_level(chs[0].cc[ch.comp], ch.pert)
+                                                              : 0;
+    }
+    __syncthreads();
+}
+
 // Work item = block of MODEL_THREADS grid pixels of a listed stamp (all channels).
 template <int EV>
 __device__ __forceinline__ void body_model_jac(const PassArgs& a, int vb, int vg)
 {
     __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
+    __shared__ int lvl[GF_MAX_CHAN];  // finite-difference reuse level per channel
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_MODEL * (a.count + 1);
     const int tot = pre[n];
@@ -233,6 +301,7 @@ __device__ __forceinline__ void body_model_jac(const PassArgs& a, int vb, int vg
             __syncthreads();
             load_channels(chs, &a.chan[(long long)b * a.chan_stride], nch);
             __syncthreads();
+            fd_levels(chs, nch, lvl);
             cur_b = b;
         }
         const int npix = st.He * st.We;
@@ -247,12 +316,12 @@ __device__ __forceinline__ void body_model_jac(const PassArgs& a, int vb, int vg
                       j >= st.os_x0 && j < st.os_x0 + st.os_box);
         }
         if (write) {
-            float base[GF_MAX_COMP];
-            comp_base<EV>(chs[0], base, (float)j, (float)i, 0.0f, 0.0f);
+            EvalCursor e;
+            e.comp = -1;
             float* E = a.ext + ext_index(st, nch, 0) + pix;
             const long long cs = (long long)st.He * st.We;
             for (int c = 0; c < nch; ++c)
-                E[c * cs] = jac_channel<EV>(chs[c], base, (float)j, (float)i, 0.0f, 0.0f);
+                E[c * cs] = jac_value<EV>(chs, c, lvl[c], e, (float)j, (float)i, 0.0f, 0.0f);
         }
         if (a.work) {
             const int cnt = __syncthreads_count(write);
@@ -542,8 +611,15 @@ __device__ __forceinline__ void body_model_os_jac_an(const PassArgs& a, int vb, 
 // (a launch of oversampled blocks alone).  OS: 0 none, 1 a warp per (channel,
 // block pixel), 2 a warp per block pixel with every channel, 3 the same with
 // analytic channels, 4 as 2 for blocks of at most 32 sub-samples.
+// the plain Jacobian pass keeps four CTAs per SM (64 registers, no spills)
 template <int PIX, int OS, int EV>
-__global__ void __launch_bounds__(MODEL_THREADS) k_model_pass(PassArgs a, int g_os)
+constexpr int model_min_blocks()
+{
+    return (PIX == 1 && OS == 0 && EV <= 1) ? 4 : 0;  // 0: no minimum
+}
+
+template <int PIX, int OS, int EV>
+__global__ void __launch_bounds__(MODEL_THREADS, (model_min_blocks<PIX, OS, EV>())) k_model_pass(PassArgs a, int g_os)
 {
     static_assert(MODEL_THREADS == OS_WARPS * 32, "one block size for both kinds of item");
     pdl_entry();
