@@ -89,13 +89,13 @@ CONV_DIRECT_TRAFFIC = {
 # from the ncu capture of the Jacobian-pass launches on 8,192 stamps of the
 # learned workload; a launch's traffic grows in proportion to its transforms.
 CONV_FFT_SMALL_TRAFFIC = {
-    # the 7-channel Jacobian launch (57,344 transforms): 2423.5 MB read + 910.8 MB
+    # the 7-channel Jacobian launch (57,344 transforms): 2423.4 MB read + 910.5 MB
     # written = 58.1 KB per transform (the algorithmic grid + output: 53.2 KB)
-    "bytes_per_problem": (2423454720 + 910797312) / 57344,
+    "bytes_per_problem": (2423425792 + 910539520) / 57344,
     "profile": "profiles/k_conv_fft_small_learned8192.md",
     "sources": {
         "paper_1101_2254_gb300/csrc/conv_fft.cu":
-            "cf0946c591e50f19e9686532079722dc84b852ead3f9d52640731b5485d5e4fb",
+            "dd70eadbbb39b5421baa4f997e7869f43e12684d6efc86db7dfe734485b925aa",
         "paper_1101_2254_gb300/csrc/conv_fft.cuh":
             "a4d55cbdda7c2a8fcfe95457b1242aa8b387019fe6ead7c9f7ad84830167549d",
         "paper_1101_2254_gb300/csrc/warp_fft.cuh":
