@@ -51,7 +51,13 @@ static_assert(GF_MAX_FREE + 1 <= VSTR, "bordered vector longer than the staged r
 constexpr int RSTR = 17;  // row stride of the per-thread tile sums (odd: the 16 stores of a
                           // thread's row land in distinct banks across the warp)
 
-__global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
+// PF > 0 (passes of at most PF channels): each thread loads its next chunk's
+// image, sigma and channel values into registers before the current chunk's
+// tile sums, so the loads of one chunk overlap the arithmetic of the last; and
+// three CTAs share an SM (80 registers, a few spilled, against 121 for two).
+// The values and the order of every sum are the same either way.
+template <int PF>
+__global__ void __launch_bounds__(RED_THREADS, PF > 0 ? 3 : 0) k_reduce_jac(PassArgs a)
 {
     pdl_entry();
     __shared__ __align__(16) float V[RED_THREADS][VSTR];  // pixel vectors v = (J, r)
@@ -104,16 +110,39 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
 #pragma unroll
         for (int y = 0; y < 4; ++y) acc[x][y] = CSum{0.0f, 0.0f};
     const long long base = (long long)local * RED_PIX;
+    constexpr int NPF = PF > 0 ? PF : 1;
+    float nd = 0.0f, ns = 0.0f, ny[NPF];  // the next chunk's pixel (PF > 0)
+    auto fetch = [&](int q) {
+        const long long px = base + (long long)q * RED_THREADS + tid;
+        if (px < HW) {
+            nd = img[px];
+            ns = sig[px];
+#pragma unroll
+            for (int k = 0; k < NPF; ++k)
+                if (k < a.nchan) ny[k] = Y[(long long)k * HW + px];
+        }
+    };
+    if (PF > 0) fetch(0);
     for (int q = 0; q < RED_CHUNKS; ++q) {
         const long long px = base + (long long)q * RED_THREADS + tid;
         if (px < HW) {
-            const float d = img[px], s = sig[px];
+            const float d = PF > 0 ? nd : img[px], s = PF > 0 ? ns : sig[px];
             const bool valid = isfinite(d) && isfinite(s) && s > 0.0f;
             float m = msky;
-            for (int k = 0; k < a.nchan; ++k) {
-                const float yk = Y[(long long)k * HW + px];
-                if (ci.mw[k] != 0.0f) m = fmaf(ci.mw[k], yk, m);
-                if (ci.jc[k] >= 0) V[tid][ci.jc[k]] = yk;
+            if (PF > 0) {
+#pragma unroll
+                for (int k = 0; k < NPF; ++k) {
+                    if (k >= a.nchan) break;
+                    const float yk = ny[k];
+                    if (ci.mw[k] != 0.0f) m = fmaf(ci.mw[k], yk, m);
+                    if (ci.jc[k] >= 0) V[tid][ci.jc[k]] = yk;
+                }
+            } else {
+                for (int k = 0; k < a.nchan; ++k) {
+                    const float yk = Y[(long long)k * HW + px];
+                    if (ci.mw[k] != 0.0f) m = fmaf(ci.mw[k], yk, m);
+                    if (ci.jc[k] >= 0) V[tid][ci.jc[k]] = yk;
+                }
             }
             if (skyc >= 0) V[tid][skyc] = psum;
             V[tid][nf] = valid ? d - m : 0.0f;
@@ -126,6 +155,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_jac(PassArgs a)
             Wt[tid] = 0.0f;
         }
         for (int f = nv; f < VSTR; ++f) V[tid][f] = 0.0f;
+        if (PF > 0 && q + 1 < RED_CHUNKS) fetch(q + 1);
         __syncthreads();
         if (active_tile) {
             float sum[4][4];
@@ -617,7 +647,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_psf_sum(int count, const StampI
 cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s)
 {
     if (a.maxitems[WK_RED] > 0) {
-        GF_LAUNCH_PDL(k_reduce_jac, dim3(a.grid[WK_RED]), dim3(RED_THREADS), 0, s, a);
+        if (a.nchan <= 8)
+            GF_LAUNCH_PDL(k_reduce_jac<8>, dim3(a.grid[WK_RED]), dim3(RED_THREADS), 0, s, a);
+        else
+            GF_LAUNCH_PDL(k_reduce_jac<0>, dim3(a.grid[WK_RED]), dim3(RED_THREADS), 0, s, a);
         GF_COUNT_LAUNCH();
     }
     return cudaGetLastError();
