@@ -423,6 +423,7 @@ template <int EV>
 __device__ __forceinline__ void body_model_os_jac32(const PassArgs& a, int vb, int vg)
 {
     __shared__ __align__(16) Channel chs[GF_MAX_CHAN];
+    __shared__ int lvl[GF_MAX_CHAN];  // finite-difference reuse level per channel
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_OS * (a.count + 1);
     const int tot = pre[n];
@@ -439,6 +440,7 @@ __device__ __forceinline__ void body_model_os_jac32(const PassArgs& a, int vb, i
             __syncthreads();
             load_channels(chs, &a.chan[(long long)b * a.chan_stride], nch);
             __syncthreads();
+            fd_levels(chs, nch, lvl);
             cur_b = b;
         }
         const int q = (blk - pre[li]) * OS_WARPS + warp;
@@ -457,11 +459,11 @@ __device__ __forceinline__ void body_model_os_jac32(const PassArgs& a, int vb, i
             oy = ((float)ay + 0.5f) / fs - 0.5f;
             ox = ((float)bx + 0.5f) / fs - 0.5f;
         }
-        float base[GF_MAX_COMP];
-        comp_base<EV>(chs[0], base, (float)j, (float)i, ox, oy);
+        EvalCursor e;
+        e.comp = -1;
         for (int c = 0; c < nch; ++c) {
             // (the same sums, in the same order, as the general body's)
-            float v = on ? jac_channel<EV>(chs[c], base, (float)j, (float)i, ox, oy) : 0.0f;
+            float v = on ? jac_value<EV>(chs, c, lvl[c], e, (float)j, (float)i, ox, oy) : 0.0f;
             v += 0.0f;  // an idle lane adds +0, as the general body's accumulator
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -611,11 +613,16 @@ __device__ __forceinline__ void body_model_os_jac_an(const PassArgs& a, int vb, 
 // (a launch of oversampled blocks alone).  OS: 0 none, 1 a warp per (channel,
 // block pixel), 2 a warp per block pixel with every channel, 3 the same with
 // analytic channels, 4 as 2 for blocks of at most 32 sub-samples.
-// the plain Jacobian pass keeps four CTAs per SM (64 registers, no spills)
+// CTAs per SM the register budget is held to: four for the plain and the
+// oversampled Jacobian passes (64 registers; the latter spills 8 bytes), five
+// for the one-channel pass with its oversampled blocks (48 registers, 48 bytes
+// spilled): measured faster than the counts their free allocation gives
 template <int PIX, int OS, int EV>
 constexpr int model_min_blocks()
 {
-    return (PIX == 1 && OS == 0 && EV <= 1) ? 4 : 0;  // 0: no minimum
+    return (PIX == 1 && OS == 0 && EV <= 1) || (PIX == 3 && OS == 4 && EV <= 1) ? 4
+           : (PIX == 0 && OS == 1 && EV == 0)                                   ? 5
+                                                                                : 0;  // 0: no minimum
 }
 
 template <int PIX, int OS, int EV>
