@@ -134,3 +134,44 @@ def test_static_eval_matches_workspace_eval_twice(gf):
             assert np.all(np.abs(a - m_o) <= REL * np.abs(m_o) + floor * np.abs(m_o).max()), \
                 (st.name, method, call)
             assert abs(chi2.item() - x_o) <= CHI2_REL * x_o, (st.name, call)
+
+
+def _al(x):
+    return (x + 255) // 256 * 256
+
+
+def _fft_len(n, even):
+    m = max(n, 1)
+    while True:
+        if not (even and m % 2):
+            r = m
+            for f in (2, 3, 5):
+                while r % f == 0:
+                    r //= f
+            if r == 1:
+                return m
+        m += 1
+
+
+@pytest.mark.parametrize("H,W,P", [(64, 64, 33), (37, 53, 7), (128, 100, 33),  # one CTA
+                                   (200, 90, 17), (64, 200, 33), (511, 512, 65)])  # three passes
+def test_fft_scratch_formula(gf, H, W, P):
+    """The FFT terms of the scratch formula in the header, per array rounded up
+    to 256 bytes: 8 Ny (Nx/2+1) PSF spectra + 4 Ny Nx wrapped PSF + 8 (Nx + Ny)
+    twiddles, and 8 He (Nx/2+1) of spectrum scratch only where the extended
+    grid exceeds 160 x 160 (else Nx, Ny are padded to 96, 128 or 160 and the
+    transform stays in shared memory)."""
+    c = (P - 1) // 2
+    He, We = H + 2 * c, W + 2 * c
+    small = He <= 160 and We <= 160
+    if small:
+        Nx = next(32 * m for m in (3, 4, 5) if 32 * m >= We)
+        Ny = next(32 * m for m in (3, 4, 5) if 32 * m >= He)
+    else:
+        Nx, Ny = _fft_len(We, True), _fft_len(He, False)
+    Kx = Nx // 2 + 1
+    extra = _al(8 * Nx) + _al(8 * Ny) + _al(8 * Ny * Kx) + _al(4 * Ny * Nx)
+    extra += 0 if small else _al(8 * He * Kx)
+    fft = _eval_need(gf, H, W, P, gf.CONV_FFT)
+    direct = _eval_need(gf, H, W, P, gf.CONV_DIRECT)
+    assert fft - direct == extra, (fft - direct, extra, small)
