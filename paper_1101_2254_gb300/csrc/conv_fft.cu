@@ -6,8 +6,13 @@
 // Ny x Nx (smallest 2^a 3^b 5^c >= He, and the smallest even one >= We); with
 // the PSF wrapped so that its centre sits at (0, 0), the circular result equals
 // the direct sum on the valid region, because every output pixel reads only
-// grid pixels inside the extended grid.  Three passes per channel, all through
-// shared-memory Stockham FFTs (fft.cuh):
+// grid pixels inside the extended grid.
+//
+// Extended grids up to 160 x 160 are padded to Nx, Ny in {96, 128, 160} and
+// convolved by k_conv_fft_small, one CTA per channel with the half spectrum in
+// shared memory (its own comment below).  Larger ones take three passes per
+// channel, through shared-memory Stockham or warp register FFTs (fft.cuh,
+// warp_fft.cuh), the half spectra held in a global scratch between passes:
 //   rows    two real grid rows packed as one complex row, forward FFT, unpacked
 //           into the two half spectra (Nx/2 + 1 bins each);
 //   columns CPC adjacent spectrum columns per CTA (coalesced), forward FFT along
