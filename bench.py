@@ -95,7 +95,7 @@ CONV_FFT_SMALL_TRAFFIC = {
     "profile": "profiles/k_conv_fft_small_learned8192.md",
     "sources": {
         "paper_1101_2254_gb300/csrc/conv_fft.cu":
-            "dd70eadbbb39b5421baa4f997e7869f43e12684d6efc86db7dfe734485b925aa",
+            "fef3a2378e2ffcc867225f42a211bb56e6e494202b5c4dd0d8c8c910a0c5982c",
         "paper_1101_2254_gb300/csrc/conv_fft.cuh":
             "a4d55cbdda7c2a8fcfe95457b1242aa8b387019fe6ead7c9f7ad84830167549d",
         "paper_1101_2254_gb300/csrc/warp_fft.cuh":
