@@ -54,17 +54,19 @@ L2_FLUSH_BYTES = 256 << 20
 # capture is repeated.
 TRAFFIC = {
     "stamp512": {
-        "bytes_per_launch": 2203449,
+        # mean DRAM bytes per FFT launch of the fits (Jacobian and trial passes,
+        # PSF spectra), from the capture in profiles/fft_traffic_stamp512.md
+        "bytes_per_launch": 1662083,
         "profile": "profiles/fft_traffic_stamp512.md",
         "sources": {
             "paper_1101_2254_gb300/csrc/conv_fft.cu":
-                "a6368f6afa29bca36317261ae0e88f824569964aca7fcd81f73adfc400ebc7dd",
+                "fef3a2378e2ffcc867225f42a211bb56e6e494202b5c4dd0d8c8c910a0c5982c",
             "paper_1101_2254_gb300/csrc/conv_fft.cuh":
-                "cc39d60c2f708eaf28116d5402bcfb600ac0984f20a2c73726ba9808f1e9e697",
+                "a4d55cbdda7c2a8fcfe95457b1242aa8b387019fe6ead7c9f7ad84830167549d",
             "paper_1101_2254_gb300/csrc/fft.cuh":
                 "f12874458fbb0310b0b5f890cdc2b7d57b76b09e959613bf60669b0bcd060f50",
             "paper_1101_2254_gb300/csrc/warp_fft.cuh":
-                "5cd51caf03a826a4ca884a2ced8c80a271b735265c4ee4c1d82ac9584705d2c4",
+                "968ef49fcdece8a3decab9e3bb9da728d116a1a103eff0d6437b5726e58de91b",
         },
     },
 }
