@@ -16,9 +16,10 @@ per component is
 
 Parity status: every function here is pinned by the tests in
 ``tests/test_oracle_*.py`` against closed forms, library special functions,
-brute force or invariants -- except the generalised-radius boxiness term
-(c != 0), whose flux factor has no closed form in the paper: parity unpinned
-beyond self-consistency (two-resolution grid integration).  The analytic
+brute force or invariants.  The generalised-radius boxiness term (c != 0),
+whose flux factor the paper does not give, is pinned by the radius on the
+diagonal and by the total flux: the area of the unit superellipse, 4 Gamma(1 +
+1/C)^2 / Gamma(1 + 2/C), times the elliptical closed form over pi.  The analytic
 derivatives (``comp_grad``, ``model_ext_grad``, ``jacobian(analytic=True)``)
 are pinned by central differences of the definitions, and db_n/dn by scipy's
 inverse of the incomplete gamma and the Ciotti-Bertin expansion.
