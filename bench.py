@@ -60,7 +60,7 @@ TRAFFIC = {
         "profile": "profiles/fft_traffic_stamp512.md",
         "sources": {
             "paper_1101_2254_gb300/csrc/conv_fft.cu":
-                "fef3a2378e2ffcc867225f42a211bb56e6e494202b5c4dd0d8c8c910a0c5982c",
+                "73ee748bbf63c92a06fc42eabd4aca15b7a5157dd557086529372e4065dc134e",
             "paper_1101_2254_gb300/csrc/conv_fft.cuh":
                 "a4d55cbdda7c2a8fcfe95457b1242aa8b387019fe6ead7c9f7ad84830167549d",
             "paper_1101_2254_gb300/csrc/fft.cuh":
@@ -97,7 +97,7 @@ CONV_FFT_SMALL_TRAFFIC = {
     "profile": "profiles/k_conv_fft_small_learned8192.md",
     "sources": {
         "paper_1101_2254_gb300/csrc/conv_fft.cu":
-            "fef3a2378e2ffcc867225f42a211bb56e6e494202b5c4dd0d8c8c910a0c5982c",
+            "73ee748bbf63c92a06fc42eabd4aca15b7a5157dd557086529372e4065dc134e",
         "paper_1101_2254_gb300/csrc/conv_fft.cuh":
             "a4d55cbdda7c2a8fcfe95457b1242aa8b387019fe6ead7c9f7ad84830167549d",
         "paper_1101_2254_gb300/csrc/warp_fft.cuh":

@@ -326,7 +326,9 @@ __global__ void __launch_bounds__(WROW_WARPS * 32) k_fft_rows_inv_w(FFTArgs f, R
 // the whole convolution of one channel runs in one CTA: its half spectrum
 // (Ny x Kx complex values, at most 104 KB) stays in shared memory between the
 // three stages, so the only global traffic is the grid read, the PSF spectrum
-// read and the valid region written.  Every transform is a warp register FFT:
+// read and the valid region written (in an LM trial pass, the image and sigma
+// read and the chi^2 partials of the 16 x 32 output blocks written instead of
+// the region).  Every transform is a warp register FFT:
 //   rows     a warp per pair of grid rows, packed and unpacked as in the row
 //            kernels above;
 //   columns  a warp per spectrum column: forward FFT along y, product with the
