@@ -56,21 +56,25 @@ constexpr int RSTR = 17;  // row stride of the per-thread tile sums (odd: the 16
 // tile sums, so the loads of one chunk overlap the arithmetic of the last; and
 // three CTAs share an SM (80 registers, a few spilled, against 121 for two).
 // The values and the order of every sum are the same either way.
-template <int PF>
-__global__ void __launch_bounds__(RED_THREADS, PF > 0 ? 3 : 0) k_reduce_jac(PassArgs a)
+// TS: the tile side, 4 or 3.  Both cover the bordered matrix with the same
+// number of tiles per side where the host picks 3 (ceil(nv/3) = ceil(nv/4),
+// e.g. nv = 9), so the groups and every entry's sums are the same and only
+// fewer padded products are formed.
+template <int PF, int TS>
+__global__ void __launch_bounds__(RED_THREADS, PF > 0 ? 3 : 2) k_reduce_jac(PassArgs a)
 {
     pdl_entry();
     __shared__ __align__(16) float V[RED_THREADS][VSTR];  // pixel vectors v = (J, r)
     __shared__ float Wt[RED_THREADS];                     // weights 1/sigma^2
     __shared__ ChanInfo ci;
     __shared__ float msky;
-    __shared__ float red[RED_THREADS][RSTR];  // per (group, tile), its 4 x 4 sums
+    __shared__ float red[RED_THREADS][RSTR];  // per (group, tile), its TS x TS sums
     const int n = *a.wl.n;
     const int* pre = a.wl.pre + WK_RED * (a.count + 1);
     const int tot = pre[n];
     const int nf = a.S->nfree, skyc = a.S->sky_jcol;
     const int nv = nf + 1;                 // bordered size
-    const int nt = (nv + 3) / 4;           // tiles per side
+    const int nt = (nv + TS - 1) / TS;     // tiles per side
     int hint = -1;
     const int chunk = (tot + gridDim.x - 1) / gridDim.x;
     const int it0 = blockIdx.x * chunk, it1 = min(tot, it0 + chunk);
@@ -104,11 +108,11 @@ __global__ void __launch_bounds__(RED_THREADS, PF > 0 ? 3 : 0) k_reduce_jac(Pass
     }
     const bool active_tile = grp < G;
     const int pg0 = grp * RED_THREADS / G, pg1 = (grp + 1) * RED_THREADS / G;  // the group's pixels
-    CSum acc[4][4];
+    CSum acc[TS][TS];
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
+    for (int x = 0; x < TS; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = CSum{0.0f, 0.0f};
+        for (int y = 0; y < TS; ++y) acc[x][y] = CSum{0.0f, 0.0f};
     const long long base = (long long)local * RED_PIX;
     constexpr int NPF = PF > 0 ? PF : 1;
     float nd = 0.0f, ns = 0.0f, ny[NPF];  // the next chunk's pixel (PF > 0)
@@ -158,27 +162,36 @@ __global__ void __launch_bounds__(RED_THREADS, PF > 0 ? 3 : 0) k_reduce_jac(Pass
         if (PF > 0 && q + 1 < RED_CHUNKS) fetch(q + 1);
         __syncthreads();
         if (active_tile) {
-            float sum[4][4];
+            float sum[TS][TS];
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+            for (int x = 0; x < TS; ++x)
 #pragma unroll
-                for (int y = 0; y < 4; ++y) sum[x][y] = 0.0f;
-            const int i0 = 4 * ti, j0 = 4 * tj;
+                for (int y = 0; y < TS; ++y) sum[x][y] = 0.0f;
+            const int i0 = TS * ti, j0 = TS * tj;
             for (int p = pg0; p < pg1; ++p) {
                 const float w = Wt[p];
-                const float4 a4 = *reinterpret_cast<const float4*>(&V[p][i0]);
-                const float4 b4 = *reinterpret_cast<const float4*>(&V[p][j0]);
-                const float vi[4] = {w * a4.x, w * a4.y, w * a4.z, w * a4.w};
-                const float vj[4] = {b4.x, b4.y, b4.z, b4.w};
+                float vi[TS], vj[TS];
+                if constexpr (TS == 4) {
+                    const float4 a4 = *reinterpret_cast<const float4*>(&V[p][i0]);
+                    const float4 b4 = *reinterpret_cast<const float4*>(&V[p][j0]);
+                    vi[0] = w * a4.x, vi[1] = w * a4.y, vi[2] = w * a4.z, vi[3] = w * a4.w;
+                    vj[0] = b4.x, vj[1] = b4.y, vj[2] = b4.z, vj[3] = b4.w;
+                } else {
 #pragma unroll
-                for (int x = 0; x < 4; ++x)
+                    for (int x = 0; x < TS; ++x) {
+                        vi[x] = w * V[p][i0 + x];
+                        vj[x] = V[p][j0 + x];
+                    }
+                }
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) sum[x][y] = fmaf(vi[x], vj[y], sum[x][y]);
+                for (int x = 0; x < TS; ++x)
+#pragma unroll
+                    for (int y = 0; y < TS; ++y) sum[x][y] = fmaf(vi[x], vj[y], sum[x][y]);
             }
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+            for (int x = 0; x < TS; ++x)
 #pragma unroll
-                for (int y = 0; y < 4; ++y) csum_add(acc[x][y], sum[x][y]);
+                for (int y = 0; y < TS; ++y) csum_add(acc[x][y], sum[x][y]);
         }
         __syncthreads();
     }
@@ -186,9 +199,9 @@ __global__ void __launch_bounds__(RED_THREADS, PF > 0 ? 3 : 0) k_reduce_jac(Pass
     // in the accumulator order of decode_acc (A pairs, g, chi^2)
     if (active_tile)
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
+        for (int x = 0; x < TS; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) red[tid][x * 4 + y] = acc[x][y].s + acc[x][y].c;
+            for (int y = 0; y < TS; ++y) red[tid][x * TS + y] = acc[x][y].s + acc[x][y].c;
     __syncthreads();
     for (int t = tid; t < a.nacc; t += RED_THREADS) {
         int i, j;
@@ -204,12 +217,12 @@ __global__ void __launch_bounds__(RED_THREADS, PF > 0 ? 3 : 0) k_reduce_jac(Pass
             r_ = nf;
             c_ = nf;
         }
-        const int I = r_ / 4, J = c_ / 4;
+        const int I = r_ / TS, J = c_ / TS;
         int slot = 0;
         for (int II = 0; II < I; ++II) slot += nt - II;
         slot += J - I;
         CSum tot = {0.0f, 0.0f};
-        for (int gq = 0; gq < G; ++gq) csum_add(tot, red[gq * T + slot][(r_ % 4) * 4 + (c_ % 4)]);
+        for (int gq = 0; gq < G; ++gq) csum_add(tot, red[gq * T + slot][(r_ % TS) * TS + (c_ % TS)]);
         a.partial[(long long)blk * a.nacc + t] = tot.s + tot.c;
     }
     if (a.work && tid == 0) {
@@ -647,10 +660,22 @@ __global__ void __launch_bounds__(RED_THREADS) k_psf_sum(int count, const StampI
 cudaError_t launch_reduce_jac(const PassArgs& a, cudaStream_t s)
 {
     if (a.maxitems[WK_RED] > 0) {
-        if (a.nchan <= 8)
-            GF_LAUNCH_PDL(k_reduce_jac<8>, dim3(a.grid[WK_RED]), dim3(RED_THREADS), 0, s, a);
-        else
-            GF_LAUNCH_PDL(k_reduce_jac<0>, dim3(a.grid[WK_RED]), dim3(RED_THREADS), 0, s, a);
+        // tiles of side 3 where they need no more tiles per side than 4 does
+        int nv = 1;  // the bordered size: nacc = nv (nv + 1) / 2
+        while (nv * (nv + 1) / 2 < a.nacc) ++nv;
+        const bool ts3 = (nv + 2) / 3 == (nv + 3) / 4;
+        const dim3 g(a.grid[WK_RED]), t(RED_THREADS);
+        if (a.nchan <= 8) {
+            if (ts3)
+                GF_LAUNCH_PDL((k_reduce_jac<8, 3>), g, t, 0, s, a);
+            else
+                GF_LAUNCH_PDL((k_reduce_jac<8, 4>), g, t, 0, s, a);
+        } else {
+            if (ts3)
+                GF_LAUNCH_PDL((k_reduce_jac<0, 3>), g, t, 0, s, a);
+            else
+                GF_LAUNCH_PDL((k_reduce_jac<0, 4>), g, t, 0, s, a);
+        }
         GF_COUNT_LAUNCH();
     }
     return cudaGetLastError();
