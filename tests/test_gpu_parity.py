@@ -498,7 +498,7 @@ def test_lm_ladder_batch_equals_single_rung(gf):
     b = gf.make_batch(Hs, Ws, psf_size=d0.P)
     args = (cuda(np.concatenate(imgs)), cuda(np.concatenate(sigs)), cuda(np.concatenate(psfs)))
     p1, r1 = gf.lm_fit_batch(d, b, np.array(p0), d0.fixed, *args, opts=gf.default_opts(ladder=1))
-    for ladder in (2, 4):
+    for ladder in (0, 2, 4):  # 0: the library's choice (two rungs for a batch this small)
         pk, rk = gf.lm_fit_batch(d, b, np.array(p0), d0.fixed, *args,
                                  opts=gf.default_opts(ladder=ladder))
         assert np.array_equal(pk, p1), ladder
