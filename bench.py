@@ -1197,6 +1197,10 @@ def run_learned(args):
                               "shared by its channels and not counted)",
             "hbm_gbs": gbs, "hbm_frac": f_hbm, "tflops": ach, "alu_frac": f_alu,
             "work_note": "5 N log2 N FLOP per length-N transform + 6 Ny per spectrum column",
+            "issue_note": "bound by instruction issue: ncu measured smsp__issue_active at "
+                          "84.5 % of the issue rate on the Jacobian launch, the register "
+                          "FFT's shuffles and butterflies "
+                          "(profiles/k_conv_fft_small_learned8192.md)",
             "transforms": problems, "launches": pr["conv"]["launches"],
             "avg_launch_ms": conv_ms_avg,
             "share_of_device_time": pr["conv"]["ms"] / sum(v["ms"] for v in pr.values())})
